@@ -1,0 +1,355 @@
+"""Plain FP64 CPU oracle for the exterior NMF (eNMF) hot path.
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously correct
+reference the CUDA path is checked against.  Only the test-suite, the smoke
+check and the benchmark's CPU-baseline leg may import it; the library never
+does, and it shares no code with the CUDA kernels.
+
+Convention (App. I): X is m x n and nonnegative, U is m x r, V is n x r and
+X ~ U V^T.  All arithmetic is IEEE double.  Library primitives used as steps:
+``numpy`` matrix products and ``numpy.linalg.svd`` (the LAPACK SVD).
+
+Sections and equations cited are those of "An Exterior Method for Nonnegative
+Matrix Factorization" (ICML 2026).  Where the paper leaves a value open, the
+reading taken is named in the function's docstring (readings R1..R12; the
+same list is kept with the design notes of the repository).
+
+Parity status: every function below is pinned by a CPU test against a closed
+form, an invariant or brute force (tests/test_oracle_pins.py), except the
+exact ADMM and PBCD trajectories, which the paper does not print; those are
+pinned only through their invariants (orthogonality, level-set invariance,
+brute force at r = 2, optimal step size by line search).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# Defaults for the values the paper leaves open (readings R3..R7).
+RHO_SCALE = 3.0         # R3: rho = RHO_SCALE / RMS(W)
+ADMM_MAX_ITER = 200     # R4
+ADMM_TOL = 1e-12        # R4: stop when ||R_{k+1} - R_k||_F <= ADMM_TOL * sqrt(r)
+N_SHIFT = 10            # R5: shift step = max(-U) / (N_SHIFT - 1/2)
+PBCD_EPS = 1e-4         # R6
+PBCD_MAX_ITER = 50      # R6
+
+
+def _check(X, r):
+    """Input rules of Eq. 1: X finite and nonnegative, 1 <= r <= min(m, n)."""
+    X = np.asarray(X, dtype=np.float64)
+    if X.ndim != 2:
+        raise ValueError("X must be a matrix")
+    if not np.all(np.isfinite(X)) or np.any(X < 0):
+        raise ValueError("X must be finite and nonnegative")
+    if not (1 <= r <= min(X.shape)):
+        raise ValueError("need 1 <= r <= min(m, n)")
+    return X
+
+
+# --------------------------------------------------------------------------
+# Eq. 1 and the error measures.
+def objective(X, U, V):
+    """f(U, V) = 1/2 ||X - U V^T||_F^2 (Eq. 1), with the error matrix formed."""
+    E = X - U @ V.T
+    return 0.5 * float(np.sum(E * E))
+
+
+def rel_err(X, U, V):
+    """||X - U V^T||_F / ||X||_F (relative error against the data, App. D)."""
+    return math.sqrt(2.0 * objective(X, U, V)) / float(np.linalg.norm(X))
+
+
+# --------------------------------------------------------------------------
+# Sec. 4: start from the truncated SVD.
+def truncated_svd(X, r):
+    """Rank-r truncated SVD start: U* = U_r S_r^(1/2), V* = V_r S_r^(1/2) (Sec. 4).
+
+    Reading R2 (the paper fixes no signs): column j of both factors is negated
+    when sum_i U*_ij + sum_i V*_ij < 0, so the leading pair of a nonnegative X
+    comes out nonnegative (Perron-Frobenius).
+    Returns (U*, V*, sigma) with sigma all singular values, descending.
+    """
+    Ur, s, Vt = np.linalg.svd(X, full_matrices=False)
+    root = np.sqrt(s[:r])
+    Us = Ur[:, :r] * root
+    Vs = Vt[:r, :].T * root
+    flip = (Us.sum(axis=0) + Vs.sum(axis=0)) < 0
+    Us[:, flip] *= -1.0
+    Vs[:, flip] *= -1.0
+    return Us, Vs, s
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.1, Algorithm 1: ADMM rotation toward the orthant.
+def h(q):
+    """Negative part h(q) = max(0, -q) (Sec. 4.2)."""
+    return np.maximum(0.0, -q)
+
+
+def neg_mass(W):
+    """sum_ij h(W_ij): the objective of the rotation problem (Sec. 4.1)."""
+    return float(np.sum(h(W)))
+
+
+def prox_h(b, rho):
+    """Z update of Eq. 7: entrywise minimiser of h(z) + rho/2 (z - b)^2."""
+    return np.where(b > 0, b, np.where(b >= -1.0 / rho, 0.0, b + 1.0 / rho))
+
+
+def procrustes(M):
+    """R update of Sec. 4.1.2: with M = W^T B = C S D^T, R = C D^T."""
+    C, _, Dt = np.linalg.svd(M)
+    return C @ Dt
+
+
+@dataclass
+class RotateInfo:
+    steps: int = 0
+    converged: bool = False
+    rho: float = 0.0
+    dR: float = 0.0
+
+
+def rotate(Us, Vs, rho=None, R0=None, Y0=None, max_iter=ADMM_MAX_ITER, tol=ADMM_TOL):
+    """Algorithm 1: ADMM for min sum h(Z) s.t. Z = W R, R^T R = I.
+
+    W stacks U* over V* (Eq. w).  One step: Z from Eq. 7 with b = W R - Y/rho;
+    R from the Procrustes problem with B = Z + Y/rho; Y <- Y + rho (Z - W R_new).
+    The output is (U* R, V* R) with the last R (Algorithm 1 outputs UR, VR).
+
+    Reading R3: R0 = I, Y0 = 0, rho = RHO_SCALE / RMS(W).
+    Reading R4: stop when ||R_{k+1} - R_k||_F <= tol * sqrt(r), or after
+    max_iter steps.
+    """
+    W = np.vstack([Us, Vs])
+    r = W.shape[1]
+    if rho is None:
+        rms = math.sqrt(float(np.mean(W * W)))
+        rho = RHO_SCALE / rms if rms > 0 else 1.0
+    R = np.eye(r) if R0 is None else np.array(R0, dtype=np.float64)
+    Y = np.zeros_like(W) if Y0 is None else np.array(Y0, dtype=np.float64)
+    info = RotateInfo(rho=rho)
+    for k in range(max_iter):
+        b = W @ R - Y / rho
+        Z = prox_h(b, rho)
+        B = Z + Y / rho
+        R_new = procrustes(W.T @ B)
+        Y = Y + rho * (Z - W @ R_new)
+        info.dR = float(np.linalg.norm(R_new - R))
+        R = R_new
+        info.steps = k + 1
+        if info.dR <= tol * math.sqrt(r):
+            info.converged = True
+            break
+    return Us @ R, Vs @ R, R, info
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.2: exterior penalty / ascent stage.
+def shift_step(F, n_shift=N_SHIFT):
+    """Fixed step rho_u*delta_u of Eq. 8 (reading R5).
+
+    The paper fixes no value.  The step is max(-F) / (n_shift - 1/2): the most
+    negative entry turns nonnegative after n_shift shifts, with half a step of
+    margin so that the count does not hinge on rounding.  Zero when F >= 0.
+    """
+    worst = float(max(0.0, -F.min()))
+    return worst / (n_shift - 0.5)
+
+
+def shift_negative(F, s):
+    """Eq. 8 / Eq. 9 (negative-entry update): F_ij += s for F_ij < 0."""
+    return np.where(F < 0, F + s, F)
+
+
+@dataclass
+class PbcdInfo:
+    iters: int = 0
+    g0: float = 0.0
+    pg: float = 0.0
+
+
+def pbcd(X, U, V, mask, eps=PBCD_EPS, max_iter=PBCD_MAX_ITER):
+    """Algorithm 2 (PBCD) for U with V fixed, M_E = 1.
+
+    Gradient (Sec. 4.2): grad_U f = (U V^T - X) V, masked by M_{U+}.  Each sweep
+    updates every row i (rows are independent, so the row loop has no order):
+    d_i = ||g_i||^2 / ||g_i V^T||^2 (Eq. 10), U_ij <- (U_ij - d_i g_ij)_+ on the
+    mask (Eq. 9 pbcdu).  Stop when the masked gradient norm falls below
+    eps * ||grad_init||_F, or after max_iter sweeps.
+
+    Reading R6: d_i = 0 when g_i = 0 or ||g_i V^T|| = 0; the loop also stops
+    once the masked gradient is exactly zero (nothing can move).
+    """
+    U = np.array(U, dtype=np.float64)
+    Mk = mask.astype(np.float64)
+    g = Mk * ((U @ V.T - X) @ V)
+    info = PbcdInfo(g0=float(np.linalg.norm(g)))
+    for t in range(max_iter):
+        num = np.sum(g * g, axis=1)
+        a = g @ V.T
+        den = np.sum(a * a, axis=1)
+        d = np.where((num > 0) & (den > 0), num / np.where(den > 0, den, 1.0), 0.0)
+        step = np.maximum(U - d[:, None] * g, 0.0)
+        U = np.where(mask, step, U)
+        g = Mk * ((U @ V.T - X) @ V)
+        info.pg = float(np.linalg.norm(g))
+        info.iters = t + 1
+        if info.pg < eps * info.g0 or info.pg == 0.0:
+            break
+    return U, info
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.3: descent by HALS (Cichocki & Phan 2009), stated as mathematics.
+def hals_update(X, U, V):
+    """One HALS sweep over the columns of U with V fixed.
+
+    With A = X V and B = V^T V, for j = 1..r in order:
+    U_:j <- max(0, U_:j + (A_:j - U B_:j) / B_jj), using the columns already
+    updated.  Reading R7: floor 0; a column with B_jj = 0 is left unchanged.
+    """
+    U = np.array(U, dtype=np.float64)
+    A = X @ V
+    B = V.T @ V
+    for j in range(U.shape[1]):
+        if B[j, j] <= 0.0:
+            continue
+        U[:, j] = np.maximum(0.0, U[:, j] + (A[:, j] - U @ B[:, j]) / B[j, j])
+    return U
+
+
+# --------------------------------------------------------------------------
+# Algorithm 3: the eNMF iteration after the rotation.
+@dataclass
+class IterState:
+    """Resumable state of Algorithm 3's loops: stage, fixed shift steps, count."""
+    stage: str = "asc"          # "asc" (lines 5-11) or "hals" (line 12)
+    s_u: float | None = None
+    s_v: float | None = None
+    k: int = 0
+    asc_iters: int = 0
+    hals_iters: int = 0
+    pbcd_iters: list = field(default_factory=list)
+
+
+def iterate(X, U, V, n_iter, state=None, eps=PBCD_EPS, pbcd_max_iter=PBCD_MAX_ITER,
+            n_shift=N_SHIFT, trace_every=1):
+    """Run n_iter alternations of Algorithm 3 from (U, V).
+
+    An alternation (reading R9) is one U-half and one V-half: in the ascent
+    stage (while U or V has a negative entry) a shift (Eq. 8 / 9), the mask
+    M_+ = [F >= 0] and PBCD for U, then the same for V with X^T; once both are
+    nonnegative, a HALS sweep of U then of V.  The objective of Eq. 1 is
+    recorded after every V-half (reading R10).  Following Algorithm 3 the HALS
+    descent starts only after the ascent loop ends (reading R8).
+    Returns (U, V, trace, state).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    U = np.array(U, dtype=np.float64)
+    V = np.array(V, dtype=np.float64)
+    st = state if state is not None else IterState()
+    trace = []
+    for _ in range(n_iter):
+        if st.stage == "asc" and not (np.any(U < 0) or np.any(V < 0)):
+            st.stage = "hals"
+        if st.stage == "asc":
+            if st.s_u is None:
+                st.s_u = shift_step(U, n_shift)
+                st.s_v = shift_step(V, n_shift)
+            U = shift_negative(U, st.s_u)
+            U, iu = pbcd(X, U, V, U >= 0, eps, pbcd_max_iter)
+            V = shift_negative(V, st.s_v)
+            V, iv = pbcd(X.T, V, U, V >= 0, eps, pbcd_max_iter)
+            st.pbcd_iters.append((iu.iters, iv.iters))
+            st.asc_iters += 1
+        else:
+            U = hals_update(X, U, V)
+            V = hals_update(X.T, V, U)
+            st.hals_iters += 1
+        st.k += 1
+        if trace_every and (st.k % trace_every == 0):
+            trace.append(objective(X, U, V))
+    return U, V, np.asarray(trace), st
+
+
+# --------------------------------------------------------------------------
+# App. G: KKT conditions.
+@dataclass
+class KktReport:
+    min_w: float
+    min_grad: float
+    delta: float       # max(grad_W * W), Table 10
+    sigma: float       # sum(grad_W * W), Table 10
+    pg_norm: float     # ||P(grad)||_F, projected gradient
+    pg_rel: float      # pg_norm / (||XV|| + ||U V^T V|| + ||X^T U|| + ||V U^T U||)
+
+
+def kkt(X, U, V):
+    """KKT measures of App. G for f of Eq. 1.
+
+    grad_U = (U V^T - X) V and grad_V = (U V^T - X)^T U; W stacks U over V.
+    delta_W = max(grad_W * W) and sigma_W = sum(grad_W * W) as in Table 10.
+    The projected gradient P takes grad_ij where W_ij > 0 and min(0, grad_ij)
+    where W_ij = 0 (zero exactly at a KKT point); reading R11 scales its norm
+    by the norms of the four terms of the gradient so that it is scale free.
+    """
+    E = U @ V.T - X
+    GU = E @ V
+    GV = E.T @ U
+    W = np.vstack([U, V])
+    G = np.vstack([GU, GV])
+    prod = G * W
+    P = np.where(W > 0, G, np.minimum(G, 0.0))
+    pg = float(np.linalg.norm(P))
+    scale = (np.linalg.norm(X @ V) + np.linalg.norm(U @ (V.T @ V))
+             + np.linalg.norm(X.T @ U) + np.linalg.norm(V @ (U.T @ U)))
+    return KktReport(min_w=float(W.min()), min_grad=float(G.min()),
+                     delta=float(prod.max()), sigma=float(prod.sum()),
+                     pg_norm=pg, pg_rel=pg / scale if scale > 0 else 0.0)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 3 end to end.
+@dataclass
+class EnmfResult:
+    U: np.ndarray
+    V: np.ndarray
+    Us: np.ndarray
+    Vs: np.ndarray
+    sigma: np.ndarray
+    R: np.ndarray
+    rot: RotateInfo
+    trace: np.ndarray
+    state: IterState
+
+
+def enmf(X, r, n_iter, **kw):
+    """Algorithm 3: SVD start, Algorithm 1 rotation, ascent loop, then HALS."""
+    X = _check(X, r)
+    Us, Vs, s = truncated_svd(X, r)
+    rk = {k: kw[k] for k in ("rho", "max_iter", "tol") if k in kw}
+    U, V, R, rinfo = rotate(Us, Vs, **rk)
+    ik = {k: kw[k] for k in ("eps", "pbcd_max_iter", "n_shift") if k in kw}
+    U, V, trace, st = iterate(X, U, V, n_iter, **ik)
+    return EnmfResult(U, V, Us, Vs, s, R, rinfo, trace, st)
+
+
+# --------------------------------------------------------------------------
+# Row sharding of the V-half (rows of X split over P ranks).
+def xtu_sharded(X, U, P):
+    """X^T U as the rank-ordered sum of P row-panel partials X_p^T U_p.
+
+    The U-half is row-local (Sec. 4.2: rows do not interact), so row panels
+    can live on different ranks; only the n x r partials of X^T U (and the
+    r x r partials of U^T U) need a sum across ranks.  Summed in rank order.
+    """
+    bounds = np.linspace(0, X.shape[0], P + 1).astype(int)
+    out = np.zeros((X.shape[1], U.shape[1]))
+    for p in range(P):
+        a, b = bounds[p], bounds[p + 1]
+        out = out + X[a:b].T @ U[a:b]
+    return out

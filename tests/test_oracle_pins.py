@@ -1,0 +1,308 @@
+"""Pins for the FP64 oracle: what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself -- a closed
+form, an invariant of the method, brute force on a tiny case, or a textbook
+special case -- so that a dropped term, a wrong sign or a transposed operand
+anywhere in the oracle fails at least one of them (tests/test_oracle_mutants.py
+plants such mistakes and checks that they are caught).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import enmf_oracle as O
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- SVD start
+def test_svd_start_eckart_young_tail():
+    """Sec. 4: U* V*^T is the best rank-r approximation; its squared error is
+    the sum of the discarded squared singular values (Eckart-Young)."""
+    X, r = synth.config_small(0)
+    Us, Vs, s = O.truncated_svd(X, r)
+    err = np.sum((X - Us @ Vs.T) ** 2)
+    assert err == pytest.approx(np.sum(s[r:] ** 2), rel=1e-10)
+
+
+def test_svd_start_balanced_factors():
+    """U* = U_r S^(1/2), V* = V_r S^(1/2): both Grams equal diag(sigma_1..r)."""
+    X, r = synth.config_small(1)
+    Us, Vs, s = O.truncated_svd(X, r)
+    np.testing.assert_allclose(Us.T @ Us, np.diag(s[:r]), atol=1e-10 * s[0])
+    np.testing.assert_allclose(Vs.T @ Vs, np.diag(s[:r]), atol=1e-10 * s[0])
+    # the residual is orthogonal to both factor spans
+    Rres = X - Us @ Vs.T
+    assert np.abs(Rres.T @ Us).max() < 1e-10 * s[0]
+    assert np.abs(Rres @ Vs).max() < 1e-10 * s[0]
+
+
+def test_svd_start_rank_one_closed_form():
+    """X = a b^T (a, b > 0): U* = a sqrt(|b|/|a|), V* = b sqrt(|a|/|b|), both >= 0
+    after the sign rule (reading R2)."""
+    rng = _rng(3)
+    a = rng.random(17) + 0.1
+    b = rng.random(11) + 0.1
+    Us, Vs, s = O.truncated_svd(np.outer(a, b), 1)
+    na, nb = np.linalg.norm(a), np.linalg.norm(b)
+    np.testing.assert_allclose(Us[:, 0], a * math.sqrt(nb / na), rtol=1e-12)
+    np.testing.assert_allclose(Vs[:, 0], b * math.sqrt(na / nb), rtol=1e-12)
+    assert s[0] == pytest.approx(na * nb, rel=1e-13)
+
+
+def test_svd_start_linear_map_to_planted_factors():
+    """Sec. 3 / App. A.1: for noise-free X = U0 V0^T, U0 = U* A and
+    V0 = V* A^{-T} with A = S^{-1/2} U_r^T U0 (Eq. gen_4)."""
+    X, U0, V0 = synth.planted(60, 40, 4, seed=2, zero_frac=0.3, noise=0.0)
+    Us, Vs, s = O.truncated_svd(X, 4)
+    Ur = Us / np.sqrt(s[:4])
+    A = np.diag(s[:4] ** -0.5) @ Ur.T @ U0
+    np.testing.assert_allclose(Us @ A, U0, atol=1e-10)
+    np.testing.assert_allclose(Vs @ np.linalg.inv(A).T, V0, atol=1e-10)
+
+
+def test_svd_sign_rule():
+    X, r = synth.config_small(0)
+    Us, Vs, _ = O.truncated_svd(X, r)
+    assert np.all(Us.sum(0) + Vs.sum(0) >= 0)
+    # leading pair of a nonnegative matrix is nonnegative (Perron-Frobenius)
+    assert Us[:, 0].min() >= -1e-12 and Vs[:, 0].min() >= -1e-12
+
+
+# ---------------------------------------------------------------- rotation
+def test_prox_matches_dense_1d_minimisation():
+    """Eq. 7 is the minimiser of h(z) + rho/2 (z - b)^2: compare with a grid."""
+    rho = 2.5
+    z = np.linspace(-3, 3, 600001)
+    for b in [-2.0, -0.7, -0.4, -0.2, 0.0, 0.3, 1.7]:
+        obj = np.maximum(0.0, -z) + 0.5 * rho * (z - b) ** 2
+        zstar = z[np.argmin(obj)]
+        assert O.prox_h(np.array([b]), rho)[0] == pytest.approx(zstar, abs=2e-5)
+
+
+def test_procrustes_matches_brute_force_r2():
+    """R = C D^T minimises ||B - W R||_F over orthogonal R (Sec. 4.1.2):
+    compare with a scan over all 2x2 rotations and reflections."""
+    rng = _rng(4)
+    W = rng.standard_normal((30, 2))
+    B = rng.standard_normal((30, 2))
+    R = O.procrustes(W.T @ B)
+    best = np.inf
+    for th in np.linspace(0, 2 * np.pi, 200001):
+        c, s = math.cos(th), math.sin(th)
+        for Q in (np.array([[c, -s], [s, c]]), np.array([[c, s], [s, -c]])):
+            best = min(best, np.sum((B - W @ Q) ** 2))
+    assert np.sum((B - W @ R) ** 2) <= best + 1e-8
+    np.testing.assert_allclose(R.T @ R, np.eye(2), atol=1e-14)
+
+
+def test_rotation_keeps_level_set_and_orthogonality():
+    """Eq. 4.4: f(U* R, V* R) = f(U*, V*) for orthogonal R; R^T R = I
+    (the paper prints ||R^T R - I|| ~ 0 after the ADMM, App. J tables)."""
+    X, r = synth.config_small(0)
+    Us, Vs, _ = O.truncated_svd(X, r)
+    U, V, R, info = O.rotate(Us, Vs)
+    assert np.linalg.norm(R.T @ R - np.eye(r)) < 1e-13
+    assert O.objective(X, U, V) == pytest.approx(O.objective(X, Us, Vs), rel=1e-12)
+    # the rotation moves toward the orthant
+    assert O.neg_mass(np.vstack([U, V])) < 0.05 * O.neg_mass(np.vstack([Us, Vs]))
+
+
+def _negmass_rot(W, th, refl):
+    c, s = math.cos(th), math.sin(th)
+    Q = np.array([[c, s], [s, -c]]) if refl else np.array([[c, -s], [s, c]])
+    return O.neg_mass(W @ Q)
+
+
+def _scan_min(W):
+    """Grid over theta (rotations and reflections), then golden-section refine."""
+    from scipy.optimize import minimize_scalar
+    grid = np.linspace(0, 2 * np.pi, 100001)
+    step = grid[1] - grid[0]
+    best = np.inf
+    for f in (0, 1):
+        vals = np.array([_negmass_rot(W, t, f) for t in grid])
+        t0 = grid[int(np.argmin(vals))]
+        res = minimize_scalar(lambda t: _negmass_rot(W, t, f), bounds=(t0 - step, t0 + step),
+                              method="bounded", options={"xatol": 1e-14})
+        best = min(best, vals.min(), res.fun)
+    return best
+
+
+def test_rotation_brute_force_r2():
+    """r = 2: scan theta over rotations and reflections.  ADMM's R is
+    orthogonal, so its negative mass cannot beat the scan; on an instance whose
+    minimum is 0 (a rotated nonnegative W0) ADMM reaches the orthant."""
+    rng = _rng(5)
+    W0 = rng.random((80, 2)) * (rng.random((80, 2)) > 0.3)
+    th0 = 0.9
+    Q0 = np.array([[math.cos(th0), -math.sin(th0)], [math.sin(th0), math.cos(th0)]])
+    W = W0 @ Q0.T
+    # the minimum 0 is attained at the planted rotation only; the scan comes
+    # within its grid spacing of it
+    assert _scan_min(W) < 1e-6
+    U, V, R, _ = O.rotate(W[:50], W[50:])
+    assert O.neg_mass(np.vstack([U, V])) < 1e-9
+    # a generic instance: ADMM can be no better than the true minimum
+    W = rng.standard_normal((80, 2)) + 0.8
+    scan = _scan_min(W)
+    U, V, R, _ = O.rotate(W[:40], W[40:])
+    nm = O.neg_mass(np.vstack([U, V]))
+    assert nm >= scan - 1e-12
+    assert nm <= 1.5 * scan + 1e-12
+
+
+# ---------------------------------------------------------------- ascent
+def test_row_step_matches_line_search():
+    """Eq. 10 / App. B: one PBCD sweep moves each row to the exact minimiser of
+    ||X_i - (U_i - d g_i) V^T||^2 over d (no projection active here)."""
+    from scipy.optimize import minimize_scalar
+    rng = _rng(6)
+    V = rng.random((30, 3))
+    Ut = rng.random((5, 3)) + 1.0
+    X = Ut @ V.T + 0.01 * rng.random((5, 30))
+    U = Ut + 0.05 * rng.standard_normal((5, 3))
+    mask = np.ones_like(U, dtype=bool)
+    U1, _ = O.pbcd(X, U, V, mask, max_iter=1)
+    assert np.all(U1 > 0)          # the projection did not act
+    g = (U @ V.T - X) @ V
+    for i in range(5):
+        res = minimize_scalar(lambda d: np.sum((X[i] - (U[i] - d * g[i]) @ V.T) ** 2),
+                              bracket=(0.0, 1e-3), tol=1e-12)
+        np.testing.assert_allclose(U1[i], U[i] - res.x * g[i], rtol=1e-9, atol=1e-12)
+
+
+def test_pbcd_decreases_objective_and_keeps_mask():
+    """Alg. 2: masked entries stay >= 0, unmasked (negative) entries are not
+    touched, and each row step cannot increase the row objective."""
+    rng = _rng(7)
+    X = rng.random((40, 30))
+    U = rng.standard_normal((40, 4))
+    V = rng.random((30, 4))
+    U = O.shift_negative(U, 0.1)
+    mask = U >= 0
+    U1, info = O.pbcd(X, U, V, mask, max_iter=1)
+    assert np.all(U1[mask] >= 0)
+    np.testing.assert_array_equal(U1[~mask], U[~mask])
+    # with no projection active, one step is the exact line minimum per row
+    rows_before = np.sum((X - U @ V.T) ** 2, axis=1)
+    rows_after = np.sum((X - U1 @ V.T) ** 2, axis=1)
+    assert np.all(rows_after <= rows_before * (1 + 1e-14) + 1e-14)
+
+
+def test_shift_step_and_count():
+    """Eq. 8 with reading R5: the worst entry needs exactly N_SHIFT shifts."""
+    rng = _rng(8)
+    U = rng.standard_normal((50, 5))
+    s = O.shift_step(U)
+    k = 0
+    while np.any(U < 0):
+        U = O.shift_negative(U, s)
+        k += 1
+    assert k == O.N_SHIFT
+
+
+# ---------------------------------------------------------------- HALS
+def test_hals_half_steps_are_monotone():
+    """Each HALS half-step is an exact block minimisation: f cannot grow."""
+    X, r = synth.config_small(2)
+    rng = _rng(9)
+    U = rng.random((X.shape[0], r))
+    V = rng.random((X.shape[1], r))
+    f = O.objective(X, U, V)
+    for _ in range(20):
+        U = O.hals_update(X, U, V)
+        f1 = O.objective(X, U, V)
+        assert f1 <= f * (1 + 1e-14)
+        V = O.hals_update(X.T, V, U)
+        f2 = O.objective(X, U, V)
+        assert f2 <= f1 * (1 + 1e-14)
+        f = f2
+
+
+def test_hals_column_is_exact_nnls_minimiser():
+    """The HALS column update is the closed-form minimiser of f over U_:j >= 0
+    with the other columns fixed: brute-force check on one entry."""
+    rng = _rng(10)
+    X = rng.random((6, 8))
+    U = rng.random((6, 3))
+    V = rng.random((8, 3))
+    U1 = O.hals_update(X, U.copy(), V)
+    # only column 0 changes first; check its entries against a 1D scan
+    Ucol = U.copy()
+    for i in range(6):
+        best, bestv = np.inf, None
+        for t in np.linspace(0, 3, 30001):
+            Ucol[i, 0] = t
+            val = np.sum((X[i] - Ucol[i] @ V.T) ** 2)
+            if val < best:
+                best, bestv = val, t
+        assert U1[i, 0] == pytest.approx(bestv, abs=2e-4)
+
+
+# ---------------------------------------------------------------- whole method
+def test_enmf_reaches_kkt_point():
+    """App. G, Table 10: at the end of eNMF the KKT conditions hold."""
+    X, r = synth.config_small(0)
+    res = O.enmf(X, r, 600)
+    rep = O.kkt(X, res.U, res.V)
+    assert rep.min_w >= 0.0
+    assert rep.pg_rel < 1e-6
+    assert abs(rep.delta) < 1e-6 * np.linalg.norm(X) ** 2
+    # the error is never below the unconstrained optimum (RE_svd >= 1, Fig. 2)
+    assert O.objective(X, res.U, res.V) >= O.objective(X, res.Us, res.Vs) * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("sparsity", [0.3, 0.5])
+def test_enmf_recovers_planted_factors(sparsity):
+    """Fig. 1B / App. H: on noise-free exact-NMF data with sparsity 0.3-0.5
+    eNMF reaches the global minimum and the planted factors up to
+    permutation and scale."""
+    from scipy.optimize import linear_sum_assignment
+    X, U0, V0 = synth.planted(120, 90, 4, seed=0, zero_frac=sparsity, noise=0.0)
+    res = O.enmf(X, 4, 1500)
+    assert O.rel_err(X, res.U, res.V) < 1e-9
+    un = res.U / np.linalg.norm(res.U, axis=0)
+    u0 = U0 / np.linalg.norm(U0, axis=0)
+    C = un.T @ u0
+    ri, ci = linear_sum_assignment(-C)
+    assert C[ri, ci].min() > 1 - 1e-9
+
+
+def test_rank_one_is_perron_pair():
+    """r = 1: the sign-fixed SVD start is already nonnegative, so no ascent step
+    runs and HALS leaves the optimum in place."""
+    X, _ = synth.config_small(3)
+    res = O.enmf(X, 1, 5)
+    assert res.state.asc_iters == 0
+    np.testing.assert_allclose(res.U @ res.V.T, res.Us @ res.Vs.T, rtol=1e-10, atol=1e-12)
+
+
+def test_ascent_stage_ends_in_n_shift_iterations():
+    X, r = synth.config_small(0)
+    res = O.enmf(X, r, 30)
+    assert res.state.asc_iters == O.N_SHIFT
+    assert res.state.hals_iters == 30 - O.N_SHIFT
+
+
+def test_sharded_xtu_is_rank_ordered_sum():
+    rng = _rng(11)
+    X = rng.random((37, 23))
+    U = rng.random((37, 4))
+    for P in (1, 2, 3, 5):
+        np.testing.assert_allclose(O.xtu_sharded(X, U, P), X.T @ U, rtol=1e-13)
+
+
+def test_input_checks():
+    with pytest.raises(ValueError):
+        O.enmf(-np.ones((4, 4)), 2, 1)
+    with pytest.raises(ValueError):
+        O.enmf(np.ones((4, 4)), 5, 1)
+    X = np.ones((4, 4))
+    X[0, 0] = np.nan
+    with pytest.raises(ValueError):
+        O.enmf(X, 2, 1)
