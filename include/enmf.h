@@ -1,0 +1,212 @@
+/*
+ * enmf.h -- C ABI of the GB300 exterior-NMF (eNMF) library, libenmf.so.
+ *
+ * The library computes the Frobenius-norm nonnegative factorisation
+ *     minimise 1/2 ||X - U V^T||_F^2  subject to U >= 0, V >= 0      (Eq. 1)
+ * with the exterior method of "An Exterior Method for Nonnegative Matrix
+ * Factorization" (ICML 2026), Algorithm 3:
+ *   1. enmf_svd_init  -- truncated SVD start U* = U_r S^(1/2), V* = V_r S^(1/2)
+ *                        (Sec. 4; randomized range finder, Sec. 4.3 remark);
+ *   2. enmf_rotate    -- orthogonal R toward the orthant by ADMM (Algorithm 1,
+ *                        Eq. 7 prox, Procrustes R update, Sec. 4.1);
+ *   3. enmf_iterate   -- ascent stage (Eq. 8/9 shifts + PBCD, Algorithm 2,
+ *                        step sizes Eq. 10/11) until U, V >= 0, then HALS
+ *                        descent (Sec. 4.3);
+ *   4. enmf_residual  -- f(U, V) of Eq. 1 and ||X - UV^T||_F / ||X||_F;
+ *   5. enmf_kkt       -- the KKT measures of App. G (Table 10).
+ *
+ * Conventions (App. I): X is m x n, U is m x r, V is n x r, X ~ U V^T.
+ * All matrices are ROW-MAJOR.  X has leading dimension ldx >= n (elements);
+ * U and V are dense with leading dimension r.
+ *
+ * Pointers: unless stated otherwise, matrix and vector arguments are DEVICE
+ * pointers on the context's device, owned by the caller, and must stay valid
+ * until the work enqueued on the context stream has finished.  X must be
+ * aligned to 16 bytes.  The library never frees caller memory.
+ *
+ * Streams: every call enqueues its work on the stream given to enmf_create
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
+ * that return host values (info structs, residuals, KKT reports) synchronise
+ * that stream before returning; the others return as soon as the work is
+ * enqueued.
+ *
+ * Errors: every call returns an enmf_status.  Arguments are checked before
+ * any launch (ENMF_EINVAL, nothing enqueued).  Device-side failures (a
+ * bounded wait that expired, a non-finite value) are reported through a
+ * device status word read at the next synchronising call; after ENMF_ECUDA or
+ * ENMF_ETIMEOUT the context is poisoned and later calls return that code.
+ * No call throws, exits or falls back to host arithmetic.
+ */
+#ifndef ENMF_H
+#define ENMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ENMF_OK = 0,
+  ENMF_EINVAL = 1,      /* bad argument (shape, rank, dtype, null pointer)   */
+  ENMF_EDOMAIN = 2,     /* X has a negative or non-finite entry               */
+  ENMF_ENOMEM = 3,      /* device allocation failed                           */
+  ENMF_ECUDA = 4,       /* a CUDA call failed; context poisoned               */
+  ENMF_ETIMEOUT = 5,    /* a bounded device-side wait expired; poisoned       */
+  ENMF_ENOTCONV = 6,    /* an iteration did not converge within its budget    */
+  ENMF_EBUSY = 7,       /* context in use by another call                     */
+  ENMF_ESTATE = 8       /* call out of order (e.g. rotate before svd_init)    */
+} enmf_status;
+
+/* Element types.  The "form" of a problem is (x_dtype, f_dtype):
+ *   plain FP64:  X F64, factors F64 (all arithmetic FP64);
+ *   FP32:        X F32, factors F32 (FP32 arithmetic, FP64 scalar sums);
+ *   BF16 / F16:  X BF16 or F16, factors F32; X products on the tensor cores
+ *                with FP32 accumulation. */
+typedef enum { ENMF_F64 = 0, ENMF_F32 = 1, ENMF_BF16 = 2, ENMF_F16 = 3 } enmf_dtype;
+
+/* Largest supported rank (the SVD start works on r + oversample <= 80). */
+#define ENMF_MAX_RANK 64
+
+typedef struct {
+  int64_t m;        /* rows of X, >= 1                                        */
+  int64_t n;        /* columns of X, >= 1                                     */
+  int64_t ldx;      /* row stride of X in elements, >= n                      */
+  int32_t r;        /* rank, 1 <= r <= min(m, n, ENMF_MAX_RANK)               */
+  int32_t x_dtype;  /* enmf_dtype of X                                        */
+  int32_t f_dtype;  /* enmf_dtype of U and V: ENMF_F64 with X F64, else F32   */
+} enmf_problem;
+
+typedef struct enmf_ctx enmf_ctx;
+
+/* Bytes of device workspace a context for *p allocates (for admission by
+ * memory footprint; X, U and V are the caller's and not included). */
+enmf_status enmf_workspace_size(const enmf_problem* p, size_t* bytes);
+
+/* Create a context on the current device.  Allocates the workspace (owned by
+ * the context, freed by enmf_destroy).  `stream` is a cudaStream_t or NULL. */
+enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx** out);
+void enmf_destroy(enmf_ctx* ctx);
+const char* enmf_status_string(enmf_status s);
+
+/* ---- 1. SVD start (Sec. 4) ---------------------------------------------
+ * Randomized subspace iteration with oversampling p: Q spans X*Omega, then
+ * alternately X^T Q and X Q2 are orthonormalised (Gram eigen-decomposition,
+ * two passes, numerical-rank truncation) and the top-r Ritz triplets of the
+ * Rayleigh-Ritz matrix are taken by one-sided Jacobi SVD in FP64.  Iterates
+ * until ||X V_r - U_r S_r||_F <= tol * sigma_1, at most max_iters times.
+ * Output: U (m x r) = U_r S^(1/2), V (n x r) = V_r S^(1/2), with column j of
+ * both negated when sum_i U_ij + sum_i V_ij < 0; sigma (device, r doubles)
+ * = the top r singular values, descending.  Omega's entries are
+ * uniform(-1, 1) from a counter-based hash of (seed, i, j).
+ * Returns ENMF_ENOTCONV (outputs still written) if tol is not met. */
+typedef struct {
+  int32_t oversample;   /* p, default 10                                   */
+  int32_t max_iters;    /* default 40                                      */
+  double tol;           /* default 1e-12                                   */
+  uint64_t seed;        /* default 0x5eed                                  */
+} enmf_svd_opts;
+typedef struct {
+  int32_t iters;        /* power iterations taken                          */
+  int32_t rank;         /* numerical rank kept (<= r + oversample)         */
+  double residual;      /* ||X V_r - U_r S_r||_F / sigma_1 at exit          */
+} enmf_svd_info;
+enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void* V, double* sigma,
+                          const enmf_svd_opts* opts /* NULL = defaults */,
+                          enmf_svd_info* info /* NULL ok */);
+
+/* ---- 2. Rotation toward the orthant (Algorithm 1) -----------------------
+ * W = [U; V].  Each ADMM step: b = W R - Y / rho; Z = prox(b) (Eq. 7);
+ * M = W^T (Z + Y / rho); R = C D^T from M = C S D^T (Procrustes, FP64 r x r
+ * one-sided Jacobi SVD on the device); Y += rho (Z - W R).  R0 = I, Y0 = 0.
+ * rho = rho_scale / RMS(W) unless rho > 0 is given.  Stops when
+ * ||R_k+1 - R_k||_F <= tol * sqrt(r) or after max_iter steps.  On exit U and V
+ * are overwritten in place by U R and V R; R (device, r x r row-major FP64)
+ * receives R if non-NULL.  Resets the iteration state (a new ascent stage). */
+typedef struct {
+  double rho;           /* <= 0: use rho_scale / RMS(W)                    */
+  double rho_scale;     /* default 3                                       */
+  int32_t max_iter;     /* default 200                                     */
+  double tol;           /* default 1e-12                                   */
+} enmf_admm_opts;
+typedef struct {
+  int32_t steps;
+  int32_t converged;
+  double rho;
+  double dR;            /* ||R_k+1 - R_k||_F of the last step               */
+  double neg_mass_in;   /* sum h(W) before                                  */
+  double neg_mass_out;  /* sum h(W R) after                                 */
+} enmf_rotate_info;
+enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* R,
+                        const enmf_admm_opts* opts, enmf_rotate_info* info);
+
+/* ---- 3. Exterior iteration (Algorithm 3 lines 5-12) ---------------------
+ * Runs n_iter alternations from the context's iteration state.  One
+ * alternation = U-half then V-half.  While U or V has a negative entry it is
+ * an ascent step: negative entries += s (Eq. 8/9; s = max(-F) / (n_shift -
+ * 1/2), fixed at the first ascent step), mask M+ = [F >= 0], then PBCD
+ * (Algorithm 2) with d_i = ||g_i||^2 / (g_i G g_i^T) (Eq. 10/11), stopping at
+ * ||M+ o grad|| < eps ||grad_init|| or pbcd_max_iter sweeps.  Afterwards it is
+ * a HALS sweep of U's columns then V's columns.  Each alternation reads X
+ * once for X V and once for X^T U.  trace (device, FP64, n_iter entries, may
+ * be NULL) receives f(U, V) of Eq. 1 after every V-half, from the expansion
+ * 1/2 ||X||^2 - <X^T U, V> + 1/2 <U^T U, V^T V> summed in FP64. */
+typedef struct {
+  int32_t n_iter;         /* alternations to run, >= 0                     */
+  int32_t pbcd_max_iter;  /* default 5                                     */
+  double eps;             /* default 1e-4                                  */
+  int32_t n_shift;        /* default 3                                     */
+  double* trace;          /* device FP64 [n_iter] or NULL                  */
+  int32_t reset;          /* 1: start a new ascent stage from (U, V)       */
+  int32_t sync_info;      /* 1: synchronise and fill *info                 */
+} enmf_iter_opts;
+typedef struct {
+  int32_t iters;          /* alternations done in total (this state)       */
+  int32_t asc_iters;      /* of which ascent steps                         */
+  int32_t hals_iters;     /* of which HALS steps                           */
+  int32_t stage;          /* 0 ascent, 1 HALS                              */
+  double s_u, s_v;        /* shift steps of Eq. 8 / 9                      */
+} enmf_iter_info;
+enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void* V,
+                         const enmf_iter_opts* opts, enmf_iter_info* info);
+
+/* PBCD sweep counts of the ascent steps run so far: out[2k] (U-half) and
+ * out[2k+1] (V-half) for ascent step k; *count = number of ascent steps.
+ * Host buffer of `cap` ints.  Synchronises. */
+enmf_status enmf_pbcd_counts(enmf_ctx* ctx, int32_t* out, int32_t cap, int32_t* count);
+
+/* ---- 4. Residual (Eq. 1) -------------------------------------------------
+ * out[0] = f = 1/2 ||X - U V^T||_F^2, out[1] = ||X - U V^T||_F / ||X||_F,
+ * out[2] = ||X||_F^2 (host doubles).  direct = 1: one pass over X forming each
+ * entry of X - U V^T (FP64 sums); direct = 0: the Gram expansion.  Syncs. */
+enmf_status enmf_residual(enmf_ctx* ctx, const void* X, const void* U, const void* V,
+                          double* out3, int32_t direct);
+
+/* ---- 5. KKT measures (App. G, Eq. kkt-nmf, Table 10) ---------------------
+ * grad_U = U (V^T V) - X V, grad_V = V (U^T U) - X^T U; W stacks U over V.
+ * delta = max(grad_W o W), sigma = sum(grad_W o W), min W, min grad_W, the
+ * projected-gradient norm (grad where W > 0, min(0, grad) where W = 0) and
+ * that norm over ||XV|| + ||U V^T V|| + ||X^T U|| + ||V U^T U||.  Syncs. */
+typedef struct {
+  double min_w, min_grad, delta, sigma, pg_norm, pg_rel;
+} enmf_kkt_report;
+enmf_status enmf_kkt(enmf_ctx* ctx, const void* X, const void* U, const void* V,
+                     enmf_kkt_report* out);
+
+/* ---- One call, host or device buffers -------------------------------------
+ * The whole of Algorithm 3: svd_init, rotate, iterate(n_iter), residual.  X,
+ * U and V may be host or device pointers (told apart by the CUDA runtime);
+ * host data is copied through context-owned device buffers inside the call.
+ * out3 as for enmf_residual (host).  NULL opts = defaults.  Syncs. */
+enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V, int32_t n_iter,
+                       const enmf_svd_opts* svd, const enmf_admm_opts* admm,
+                       const enmf_iter_opts* iter, double* out3);
+
+/* Library version string. */
+const char* enmf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENMF_H */

@@ -32,9 +32,9 @@ import numpy as np
 RHO_SCALE = 3.0         # R3: rho = RHO_SCALE / RMS(W)
 ADMM_MAX_ITER = 200     # R4
 ADMM_TOL = 1e-12        # R4: stop when ||R_{k+1} - R_k||_F <= ADMM_TOL * sqrt(r)
-N_SHIFT = 10            # R5: shift step = max(-U) / (N_SHIFT - 1/2)
+N_SHIFT = 3             # R5: shift step = max(-U) / (N_SHIFT - 1/2)
 PBCD_EPS = 1e-4         # R6
-PBCD_MAX_ITER = 50      # R6
+PBCD_MAX_ITER = 5       # R6
 
 
 def _check(X, r):

@@ -1,0 +1,201 @@
+"""ctypes binding of libenmf.so: the C ABI of include/enmf.h, same names.
+
+Argument marshalling only -- every step of the factorisation runs in the CUDA
+kernels of the library.  Tensors are passed as device pointers; PyTorch is
+used for device memory and streams.  If the library is missing this module
+raises on import: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libenmf.so")
+
+ENMF_F64, ENMF_F32, ENMF_BF16, ENMF_F16 = 0, 1, 2, 3
+ENMF_MAX_RANK = 64
+
+STATUS = {0: "ok", 1: "EINVAL", 2: "EDOMAIN", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT",
+          6: "ENOTCONV", 7: "EBUSY", 8: "ESTATE"}
+
+
+class EnmfError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+class enmf_problem(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("ldx", C.c_int64), ("r", C.c_int32),
+                ("x_dtype", C.c_int32), ("f_dtype", C.c_int32)]
+
+
+class enmf_svd_opts(C.Structure):
+    _fields_ = [("oversample", C.c_int32), ("max_iters", C.c_int32), ("tol", C.c_double),
+                ("seed", C.c_uint64)]
+
+
+class enmf_svd_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("rank", C.c_int32), ("residual", C.c_double)]
+
+
+class enmf_admm_opts(C.Structure):
+    _fields_ = [("rho", C.c_double), ("rho_scale", C.c_double), ("max_iter", C.c_int32),
+                ("tol", C.c_double)]
+
+
+class enmf_rotate_info(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("converged", C.c_int32), ("rho", C.c_double),
+                ("dR", C.c_double), ("neg_mass_in", C.c_double), ("neg_mass_out", C.c_double)]
+
+
+class enmf_iter_opts(C.Structure):
+    _fields_ = [("n_iter", C.c_int32), ("pbcd_max_iter", C.c_int32), ("eps", C.c_double),
+                ("n_shift", C.c_int32), ("trace", C.c_void_p), ("reset", C.c_int32),
+                ("sync_info", C.c_int32)]
+
+
+class enmf_iter_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("asc_iters", C.c_int32), ("hals_iters", C.c_int32),
+                ("stage", C.c_int32), ("s_u", C.c_double), ("s_v", C.c_double)]
+
+
+class enmf_kkt_report(C.Structure):
+    _fields_ = [("min_w", C.c_double), ("min_grad", C.c_double), ("delta", C.c_double),
+                ("sigma", C.c_double), ("pg_norm", C.c_double), ("pg_rel", C.c_double)]
+
+
+_SIGS = {
+    "enmf_workspace_size": (C.c_int, [C.POINTER(enmf_problem), C.POINTER(C.c_size_t)]),
+    "enmf_create": (C.c_int, [C.POINTER(enmf_problem), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "enmf_destroy": (None, [C.c_void_p]),
+    "enmf_status_string": (C.c_char_p, [C.c_int]),
+    "enmf_svd_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.POINTER(enmf_svd_opts), C.POINTER(enmf_svd_info)]),
+    "enmf_rotate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.POINTER(enmf_admm_opts), C.POINTER(enmf_rotate_info)]),
+    "enmf_iterate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(enmf_iter_opts), C.POINTER(enmf_iter_info)]),
+    "enmf_pbcd_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
+                                   C.POINTER(C.c_int32)]),
+    "enmf_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.POINTER(C.c_double), C.c_int32]),
+    "enmf_kkt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.POINTER(enmf_kkt_report)]),
+    "enmf_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                             C.POINTER(enmf_svd_opts), C.POINTER(enmf_admm_opts),
+                             C.POINTER(enmf_iter_opts), C.POINTER(C.c_double)]),
+    "enmf_version": (C.c_char_p, []),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def load(path=LIB_PATH):
+    """Load libenmf.so and declare its signatures; raise if it is missing."""
+    if not os.path.exists(path):
+        raise ImportError(f"libenmf.so not built ({path}); run paper_2605_19325_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def check(code, where):
+    if code != 0:
+        raise EnmfError(code, where)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------- C ABI mirror
+def enmf_workspace_size(problem):
+    out = C.c_size_t(0)
+    check(lib().enmf_workspace_size(C.byref(problem), C.byref(out)), "enmf_workspace_size")
+    return out.value
+
+
+def enmf_create(problem, stream=None):
+    h = C.c_void_p()
+    check(lib().enmf_create(C.byref(problem), _stream(stream), C.byref(h)), "enmf_create")
+    return h
+
+
+def enmf_destroy(ctx):
+    lib().enmf_destroy(ctx)
+
+
+def enmf_svd_init(ctx, X, U, V, sigma=None, opts=None):
+    info = enmf_svd_info()
+    code = lib().enmf_svd_init(ctx, _ptr(X), _ptr(U), _ptr(V), _ptr(sigma),
+                               C.byref(opts) if opts is not None else None, C.byref(info))
+    if code not in (0, 6):
+        check(code, "enmf_svd_init")
+    return info, code
+
+
+def enmf_rotate(ctx, U, V, R=None, opts=None):
+    info = enmf_rotate_info()
+    code = lib().enmf_rotate(ctx, _ptr(U), _ptr(V), _ptr(R),
+                             C.byref(opts) if opts is not None else None, C.byref(info))
+    if code not in (0, 6):
+        check(code, "enmf_rotate")
+    return info, code
+
+
+def enmf_iterate(ctx, X, U, V, n_iter, trace=None, reset=0, eps=1e-4, pbcd_max_iter=5,
+                 n_shift=3, sync_info=1):
+    o = enmf_iter_opts(n_iter, pbcd_max_iter, eps, n_shift,
+                       None if trace is None else trace.data_ptr(), reset, sync_info)
+    info = enmf_iter_info()
+    check(lib().enmf_iterate(ctx, _ptr(X), _ptr(U), _ptr(V), C.byref(o),
+                             C.byref(info) if sync_info else None), "enmf_iterate")
+    return info
+
+
+def enmf_pbcd_counts(ctx, cap=8192):
+    buf = (C.c_int32 * cap)()
+    cnt = C.c_int32(0)
+    check(lib().enmf_pbcd_counts(ctx, buf, cap, C.byref(cnt)), "enmf_pbcd_counts")
+    return [(buf[2 * i], buf[2 * i + 1]) for i in range(min(cnt.value, cap // 2))]
+
+
+def enmf_residual(ctx, X, U, V, direct=1):
+    out = (C.c_double * 3)()
+    check(lib().enmf_residual(ctx, _ptr(X), _ptr(U), _ptr(V), out, direct), "enmf_residual")
+    return out[0], out[1], out[2]
+
+
+def enmf_kkt(ctx, X, U, V):
+    rep = enmf_kkt_report()
+    check(lib().enmf_kkt(ctx, _ptr(X), _ptr(U), _ptr(V), C.byref(rep)), "enmf_kkt")
+    return rep
+
+
+def enmf_solve(ctx, X_ptr, U_ptr, V_ptr, n_iter):
+    """Whole Algorithm 3 through one call; pointers may be host or device."""
+    out = (C.c_double * 3)()
+    check(lib().enmf_solve(ctx, C.c_void_p(X_ptr), C.c_void_p(U_ptr), C.c_void_p(V_ptr),
+                           n_iter, None, None, None, out), "enmf_solve")
+    return out[0], out[1], out[2]

@@ -1,0 +1,642 @@
+// C ABI of libenmf: context, workspace and the five calls of the eNMF path.
+// Every step of the path runs in the kernels of sweep.cu, rows.cu, small.cu
+// (and tc_sweep.cu for the tensor-core form); this file only checks
+// arguments, carves the workspace and enqueues launches.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.h"
+
+using namespace enmf;
+
+struct enmf_ctx {
+  enmf_problem p;
+  cudaStream_t stream;
+  int device;
+  int num_sms;
+  int fdt;                  // factor/accumulate type code
+  int xdt;                  // X type code
+  enmf_status poison;       // ENMF_OK unless poisoned
+  bool state_valid;         // iteration state initialised
+  int grid_u, grid_v;       // cooperative half-step grids
+  // workspace
+  void* ws;
+  size_t ws_bytes;
+  DevState* st;
+  int* err;
+  int* kept;
+  int* counts;
+  int counts_cap;
+  void* M0; void* M1; void* M2;  // m x LMAX
+  void* N0; void* N1; void* N2;  // n x LMAX
+  void* Zb; void* Yb;            // (m + n) x r
+  unsigned long long* mask;      // max(m, n)
+  void* splitk;
+  size_t splitk_bytes;
+  double* part;                  // NPART * (LMAX^2 + 8)
+  double* dot_part;              // 4096
+  double* pb_part;               // 2 * 4096
+  double* Gu; double* Gv; double* Msm; double* R;
+  double* T1; double* T2; double* Ut; double* Wt; double* sig;
+  double* Tu; double* Tv; double* Wr; double* UrS; double* csQ; double* csQ2;
+  double* scal;                  // 64 scratch scalars
+  // host-data staging for enmf_solve
+  void* hX; void* hU; void* hV;
+  size_t hX_bytes;
+};
+
+static const char* kStatus[] = {"ok", "invalid argument", "X has a negative or non-finite entry",
+                                "out of device memory", "CUDA error", "device wait timed out",
+                                "did not converge", "context busy", "call out of order"};
+
+extern "C" const char* enmf_status_string(enmf_status s) {
+  int i = (int)s;
+  return (i >= 0 && i <= 8) ? kStatus[i] : "unknown status";
+}
+
+extern "C" const char* enmf_version(void) { return "enmf-gb300 0.1"; }
+
+static bool valid_problem(const enmf_problem* p) {
+  if (!p) return false;
+  if (p->m < 1 || p->n < 1 || p->ldx < p->n) return false;
+  if (p->r < 1 || p->r > ENMF_MAX_RANK || p->r > p->m || p->r > p->n) return false;
+  if (p->x_dtype < ENMF_F64 || p->x_dtype > ENMF_F16) return false;
+  if (p->f_dtype == ENMF_F64) return p->x_dtype == ENMF_F64;
+  return p->f_dtype == ENMF_F32;
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t off[40];
+  size_t total;
+};
+
+// Workspace plan; the order here defines the carving in enmf_create.
+static size_t plan(const enmf_problem* p, int num_sms, size_t* splitk_out) {
+  const size_t fs = p->f_dtype == ENMF_F64 ? 8 : 4;
+  const int bm = p->f_dtype == ENMF_F64 ? 32 : 64;
+  const size_t mm = (size_t)p->m, nn = (size_t)p->n, r = (size_t)p->r;
+  // split-K scratch: the largest splits x rows x k over every width k used
+  size_t sk = 256;
+  for (int k = 1; k <= LMAX; ++k) {
+    int sv = choose_splits(p->m, p->n, k, bm, num_sms);
+    int st = choose_splits(p->n, p->m, k, bm, num_sms);
+    if (sv > 1 && (size_t)sv * mm * k * fs > sk) sk = (size_t)sv * mm * k * fs;
+    if (st > 1 && (size_t)st * nn * k * fs > sk) sk = (size_t)st * nn * k * fs;
+  }
+  if (splitk_out) *splitk_out = sk;
+  size_t t = 0;
+  t += al256(sizeof(DevState)) + al256(64) + al256(8192 * sizeof(int));
+  t += 3 * al256(mm * LMAX * fs) + 3 * al256(nn * LMAX * fs);
+  t += 2 * al256((mm + nn) * r * fs);
+  t += al256((mm > nn ? mm : nn) * 8);
+  t += al256(sk);
+  t += al256((size_t)NPART * (LMAX * LMAX + 8) * 8);
+  t += al256(4096 * 8) + al256(2 * 4096 * 8);
+  t += 9 * al256((size_t)LMAX * LMAX * 8) + 2 * al256((size_t)LMAX * RMAX * 8);
+  t += 2 * al256((size_t)LMAX * RMAX * 8) + 3 * al256(LMAX * 8) + al256(64 * 8);
+  return t;
+}
+
+extern "C" enmf_status enmf_workspace_size(const enmf_problem* p, size_t* bytes) {
+  if (!valid_problem(p) || !bytes) return ENMF_EINVAL;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *bytes = plan(p, sms, nullptr);
+  return ENMF_OK;
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) { ctx->poison = ENMF_ECUDA; return ENMF_ECUDA; } \
+  } while (0)
+
+static enmf_status check_launch(enmf_ctx* ctx) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->poison = ENMF_ECUDA;
+    return ENMF_ECUDA;
+  }
+  return ENMF_OK;
+}
+
+// Synchronise and translate the device status word.
+static enmf_status sync_status(enmf_ctx* ctx, bool clear_notconv = true) {
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    ctx->poison = ENMF_ECUDA;
+    return ENMF_ECUDA;
+  }
+  int err = 0;
+  e = cudaMemcpy(&err, ctx->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    ctx->poison = ENMF_ECUDA;
+    return ENMF_ECUDA;
+  }
+  if (err & ERR_TIMEOUT) {
+    ctx->poison = ENMF_ETIMEOUT;
+    return ENMF_ETIMEOUT;
+  }
+  if (err & (ERR_DOMAIN | ERR_NOTCONV | ERR_NONFINITE)) {
+    int keep = 0;
+    cudaMemcpy(ctx->err, &keep, sizeof(int), cudaMemcpyHostToDevice);
+    if (err & ERR_DOMAIN) return ENMF_EDOMAIN;
+    if ((err & ERR_NOTCONV) && clear_notconv) return ENMF_ENOTCONV;
+  }
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx** out) {
+  if (!valid_problem(p) || !out) return ENMF_EINVAL;
+  *out = nullptr;
+  enmf_ctx* ctx = new (std::nothrow) enmf_ctx();
+  if (!ctx) return ENMF_ENOMEM;
+  memset(ctx, 0, sizeof(*ctx));
+  ctx->p = *p;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->fdt = p->f_dtype == ENMF_F64 ? T_F64 : T_F32;
+  ctx->xdt = p->x_dtype;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) { delete ctx; return ENMF_ECUDA; }
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  size_t sk = 0;
+  ctx->ws_bytes = plan(p, ctx->num_sms, &sk);
+  if (cudaMalloc(&ctx->ws, ctx->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return ENMF_ENOMEM;
+  }
+  const size_t fs = type_size(ctx->fdt);
+  const size_t mm = (size_t)p->m, nn = (size_t)p->n, r = (size_t)p->r;
+  char* b = (char*)ctx->ws;
+  auto take = [&](size_t bytes) { void* q = b; b += al256(bytes); return q; };
+  ctx->st = (DevState*)take(sizeof(DevState));
+  ctx->err = (int*)take(64);
+  ctx->kept = ctx->err + 4;
+  ctx->counts = (int*)take(8192 * sizeof(int));
+  ctx->counts_cap = 8192;
+  ctx->M0 = take(mm * LMAX * fs); ctx->M1 = take(mm * LMAX * fs); ctx->M2 = take(mm * LMAX * fs);
+  ctx->N0 = take(nn * LMAX * fs); ctx->N1 = take(nn * LMAX * fs); ctx->N2 = take(nn * LMAX * fs);
+  ctx->Zb = take((mm + nn) * r * fs);
+  ctx->Yb = take((mm + nn) * r * fs);
+  ctx->mask = (unsigned long long*)take((mm > nn ? mm : nn) * 8);
+  ctx->splitk = take(sk);
+  ctx->splitk_bytes = sk;
+  ctx->part = (double*)take((size_t)NPART * (LMAX * LMAX + 8) * 8);
+  ctx->dot_part = (double*)take(4096 * 8);
+  ctx->pb_part = (double*)take(2 * 4096 * 8);
+  ctx->Gu = (double*)take(LMAX * LMAX * 8);
+  ctx->Gv = (double*)take(LMAX * LMAX * 8);
+  ctx->Msm = (double*)take(LMAX * LMAX * 8);
+  ctx->R = (double*)take(LMAX * LMAX * 8);
+  ctx->T1 = (double*)take(LMAX * LMAX * 8);
+  ctx->T2 = (double*)take(LMAX * LMAX * 8);
+  ctx->Ut = (double*)take(LMAX * LMAX * 8);
+  ctx->Wt = (double*)take(LMAX * LMAX * 8);
+  (void)take(LMAX * LMAX * 8);
+  ctx->Tu = (double*)take(LMAX * RMAX * 8);
+  ctx->Tv = (double*)take(LMAX * RMAX * 8);
+  ctx->Wr = (double*)take(LMAX * RMAX * 8);
+  ctx->UrS = (double*)take(LMAX * RMAX * 8);
+  ctx->sig = (double*)take(LMAX * 8);
+  ctx->csQ = (double*)take(LMAX * 8);
+  ctx->csQ2 = (double*)take(LMAX * 8);
+  ctx->scal = (double*)take(64 * 8);
+  if ((size_t)(b - (char*)ctx->ws) > ctx->ws_bytes) {
+    cudaFree(ctx->ws);
+    delete ctx;
+    return ENMF_EINVAL;
+  }
+  cudaMemsetAsync(ctx->ws, 0, ctx->ws_bytes, ctx->stream);
+  ctx->grid_u = half_step_grid(ctx->fdt, p->r, ctx->num_sms);
+  ctx->grid_v = ctx->grid_u;
+  if (ctx->grid_u > 4096) ctx->grid_u = ctx->grid_v = 4096;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaFree(ctx->ws);
+    delete ctx;
+    return ENMF_ECUDA;
+  }
+  *out = ctx;
+  return ENMF_OK;
+}
+
+extern "C" void enmf_destroy(enmf_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->hX) cudaFree(ctx->hX);
+  if (ctx->hU) cudaFree(ctx->hU);
+  if (ctx->hV) cudaFree(ctx->hV);
+  delete ctx;
+}
+
+#define GUARD(ctx)                           \
+  do {                                       \
+    if (!(ctx)) return ENMF_EINVAL;          \
+    if ((ctx)->poison) return (ctx)->poison; \
+  } while (0)
+
+// ------------------------------------------------------------ orthonormalise
+// F (rows x k, ld LMAX) -> orthonormal columns spanning its range, through
+// `tmp`: two passes of the Gram eigen map (numerical-rank truncation).
+static void orth2(enmf_ctx* ctx, void* F, void* tmp, int64_t rows, int k) {
+  const double tau = ctx->fdt == T_F64 ? 1e-13 : 1e-11;
+  cudaStream_t s = ctx->stream;
+  launch_gram(F, LMAX, k, F, LMAX, k, rows, ctx->fdt, ctx->part, ctx->Gu, s);
+  launch_eig_orth(ctx->Gu, k, tau, ctx->T1, ctx->kept, ctx->err, s);
+  launch_row_transform(F, LMAX, k, tmp, LMAX, k, rows, ctx->fdt, ctx->T1, s);
+  launch_gram(tmp, LMAX, k, tmp, LMAX, k, rows, ctx->fdt, ctx->part, ctx->Gu, s);
+  launch_eig_orth(ctx->Gu, k, tau, ctx->T1, ctx->kept, ctx->err, s);
+  launch_row_transform(tmp, LMAX, k, F, LMAX, k, rows, ctx->fdt, ctx->T1, s);
+}
+
+// ------------------------------------------------------------------ 1. SVD
+extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void* V,
+                                     double* sigma, const enmf_svd_opts* opts,
+                                     enmf_svd_info* info) {
+  GUARD(ctx);
+  if (!X || !U || !V) return ENMF_EINVAL;
+  enmf_svd_opts o = {10, 40, ctx->fdt == T_F64 ? 1e-12 : 1e-5, 0x5eedull};
+  if (opts) {
+    o = *opts;
+    if (o.oversample < 0 || o.max_iters < 1 || !(o.tol >= 0)) return ENMF_EINVAL;
+  }
+  const enmf_problem& p = ctx->p;
+  const int r = p.r;
+  int l = r + o.oversample;
+  if (l > LMAX) l = LMAX;
+  if (l > p.m) l = (int)p.m;
+  if (l > p.n) l = (int)p.n;
+  cudaStream_t s = ctx->stream;
+  const int fdt = ctx->fdt, xdt = ctx->xdt;
+  const int64_t m = p.m, n = p.n;
+  launch_normx2(X, xdt, m, n, p.ldx, ctx->part, &ctx->st->normX2, ctx->err, s);
+  // Q = orth(X Omega)
+  launch_omega(ctx->N0, fdt, n, LMAX, o.seed, s);
+  launch_xv(X, xdt, m, n, p.ldx, ctx->N0, LMAX, l, ctx->M0, LMAX, fdt, ctx->splitk, ctx->num_sms, s);
+  orth2(ctx, ctx->M0, ctx->M1, m, l);
+  enmf_status rc = check_launch(ctx);
+  if (rc) return rc;
+  double res = INFINITY;
+  int it = 0;
+  for (; it < o.max_iters; ++it) {
+    // Bt = X^T Q ; Q2 = orth(Bt) ; P = Q2^T Bt
+    launch_xtu(X, xdt, m, n, p.ldx, ctx->M0, LMAX, l, ctx->N1, LMAX, fdt, ctx->splitk, ctx->num_sms, s);
+    launch_gram(ctx->N1, LMAX, l, ctx->N1, LMAX, l, n, fdt, ctx->part, ctx->Gu, s);
+    launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->kept, ctx->err, s);
+    launch_row_transform(ctx->N1, LMAX, l, ctx->N0, LMAX, l, n, fdt, ctx->T1, s);
+    launch_gram(ctx->N0, LMAX, l, ctx->N0, LMAX, l, n, fdt, ctx->part, ctx->Gu, s);
+    launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->kept, ctx->err, s);
+    launch_row_transform(ctx->N0, LMAX, l, ctx->N2, LMAX, l, n, fdt, ctx->T1, s);
+    launch_gram(ctx->N2, LMAX, l, ctx->N1, LMAX, l, n, fdt, ctx->part, ctx->Msm, s);
+    launch_rr_svd(ctx->Msm, l, l, ctx->sig, ctx->Ut, ctx->Wt, ctx->err, s);
+    // Y = X Q2 (the next power iterate) and the residual ||Y W_r - Q U_r S_r||
+    launch_xv(X, xdt, m, n, p.ldx, ctx->N2, LMAX, l, ctx->M1, LMAX, fdt, ctx->splitk, ctx->num_sms, s);
+    launch_rr_prep(ctx->sig, ctx->Ut, ctx->Wt, l, l, r, ctx->Wr, ctx->UrS, ctx->st, s);
+    launch_rr_residual(ctx->M1, LMAX, l, ctx->M0, LMAX, l, m, r, fdt, ctx->Wr, ctx->UrS,
+                       ctx->part, &ctx->scal[0], s);
+    rc = check_launch(ctx);
+    if (rc) return rc;
+    double hv[2];
+    CK(cudaMemcpyAsync(&hv[0], &ctx->scal[0], sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hv[1], &ctx->st->sigma1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    rc = sync_status(ctx, false);
+    if (rc && rc != ENMF_ENOTCONV) return rc;
+    res = hv[1] > 0 ? sqrt(hv[0]) / hv[1] : 0.0;
+    if (res <= o.tol) { ++it; break; }
+    if (it + 1 < o.max_iters) {
+      // Q = orth(Y)
+      launch_gram(ctx->M1, LMAX, l, ctx->M1, LMAX, l, m, fdt, ctx->part, ctx->Gu, s);
+      launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->kept, ctx->err, s);
+      launch_row_transform(ctx->M1, LMAX, l, ctx->M2, LMAX, l, m, fdt, ctx->T1, s);
+      launch_gram(ctx->M2, LMAX, l, ctx->M2, LMAX, l, m, fdt, ctx->part, ctx->Gu, s);
+      launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->kept, ctx->err, s);
+      launch_row_transform(ctx->M2, LMAX, l, ctx->M0, LMAX, l, m, fdt, ctx->T1, s);
+    }
+  }
+  // U* = Q Tu, V* = Q2 Tv with the sign rule
+  launch_colsum(ctx->M0, m, LMAX, l, fdt, ctx->part, ctx->csQ, s);
+  launch_colsum(ctx->N2, n, LMAX, l, fdt, ctx->part, ctx->csQ2, s);
+  launch_svd_finish(ctx->sig, ctx->Ut, ctx->Wt, l, l, r, ctx->csQ, ctx->csQ2, ctx->Tu, ctx->Tv,
+                    sigma, s);
+  launch_row_transform(ctx->M0, LMAX, l, U, r, r, m, fdt, ctx->Tu, s);
+  launch_row_transform(ctx->N2, LMAX, l, V, r, r, n, fdt, ctx->Tv, s);
+  rc = check_launch(ctx);
+  if (rc) return rc;
+  int kept = l;
+  CK(cudaMemcpyAsync(&kept, ctx->kept, sizeof(int), cudaMemcpyDeviceToHost, s));
+  rc = sync_status(ctx);
+  if (info) {
+    info->iters = it;
+    info->rank = kept;
+    info->residual = res;
+  }
+  ctx->state_valid = false;
+  if (rc) return rc;
+  return res <= o.tol ? ENMF_OK : ENMF_ENOTCONV;
+}
+
+// ------------------------------------------------------------- 2. rotation
+__global__ void rot_start_kernel(double* R, int k, DevState* st) {
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) R[e] = (e / k == e % k) ? 1.0 : 0.0;
+  if (threadIdx.x == 0) {
+    st->admm_done = 0;
+    st->admm_steps = 0;
+    st->dR = 0.0;
+  }
+}
+
+extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout,
+                                   const enmf_admm_opts* opts, enmf_rotate_info* info) {
+  GUARD(ctx);
+  if (!U || !V) return ENMF_EINVAL;
+  enmf_admm_opts o = {0.0, 3.0, 200, 1e-12};
+  if (opts) {
+    o = *opts;
+    if (o.max_iter < 1 || !(o.tol >= 0) || (o.rho <= 0 && !(o.rho_scale > 0))) return ENMF_EINVAL;
+  }
+  const enmf_problem& p = ctx->p;
+  const int k = p.r, fdt = ctx->fdt;
+  const int64_t m = p.m, n = p.n;
+  cudaStream_t s = ctx->stream;
+  // negative mass before and ||W||_F^2 for rho
+  launch_negmass(U, m, k, fdt, ctx->part, &ctx->scal[1], 0, s);
+  launch_negmass(V, n, k, fdt, ctx->part, &ctx->scal[1], 1, s);
+  launch_dot(U, k, U, k, k, m, fdt, ctx->part, &ctx->scal[2], s);
+  launch_dot(V, k, V, k, k, n, fdt, ctx->part, &ctx->scal[3], s);
+  double hs[4];
+  CK(cudaMemcpyAsync(hs, ctx->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  enmf_status rc = sync_status(ctx);
+  if (rc) return rc;
+  double rho = o.rho;
+  if (!(rho > 0)) {
+    double rms = sqrt((hs[2] + hs[3]) / ((double)(m + n) * k));
+    rho = rms > 0 ? o.rho_scale / rms : 1.0;
+  }
+  CK(cudaMemsetAsync(ctx->Yb, 0, (size_t)(m + n) * k * type_size(fdt), s));
+  rot_start_kernel<<<1, 256, 0, s>>>(ctx->R, k, ctx->st);
+  int steps_launched = 0;
+  const int check_every = 16;
+  for (int it = 0; it < o.max_iter; ++it) {
+    launch_admm_pass(U, V, m, n, k, fdt, ctx->R, ctx->Zb, ctx->Yb, rho, it == 0, ctx->st,
+                     ctx->part, s);
+    launch_part_reduce(ctx->part, k * k, ctx->Msm, s);   // M = W^T B, fixed order
+    launch_polar(ctx->Msm, k, ctx->R, nullptr, o.tol, ctx->st, ctx->err, s);
+    ++steps_launched;
+    if ((it + 1) % check_every == 0 && it + 1 < o.max_iter) {
+      rc = check_launch(ctx);
+      if (rc) return rc;
+      int done = 0;
+      CK(cudaMemcpyAsync(&done, &ctx->st->admm_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (done) break;
+    }
+  }
+  launch_apply_square(U, m, k, fdt, ctx->R, s);
+  launch_apply_square(V, n, k, fdt, ctx->R, s);
+  launch_negmass(U, m, k, fdt, ctx->part, &ctx->scal[4], 0, s);
+  launch_negmass(V, n, k, fdt, ctx->part, &ctx->scal[4], 1, s);
+  if (Rout) CK(cudaMemcpyAsync(Rout, ctx->R, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  rc = check_launch(ctx);
+  if (rc) return rc;
+  DevState hst;
+  double nm_out = 0;
+  CK(cudaMemcpyAsync(&hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&nm_out, &ctx->scal[4], sizeof(double), cudaMemcpyDeviceToHost, s));
+  rc = sync_status(ctx);
+  if (info) {
+    info->steps = hst.admm_steps;
+    info->converged = hst.admm_done;
+    info->rho = rho;
+    info->dR = hst.dR;
+    info->neg_mass_in = hs[1];
+    info->neg_mass_out = nm_out;
+  }
+  ctx->state_valid = false;
+  return rc;
+}
+
+// ------------------------------------------------------------ 3. iterate
+static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const double* G, int64_t rows,
+                 const enmf_iter_opts& o, bool dot) {
+  HalfArgs a;
+  memset(&a, 0, sizeof(a));
+  a.F = F;
+  a.A = A;
+  a.G = G;
+  a.gbuf = which == 0 ? ctx->M1 : ctx->N1;
+  a.mask = ctx->mask;
+  a.rows = rows;
+  a.k = ctx->p.r;
+  a.fdt = ctx->fdt;
+  a.which = which;
+  a.pbcd_max_iter = o.pbcd_max_iter;
+  a.eps = o.eps;
+  a.st = ctx->st;
+  a.part = ctx->pb_part;
+  a.err = ctx->err;
+  a.counts = ctx->counts;
+  a.counts_cap = ctx->counts_cap;
+  a.dotA = dot ? A : nullptr;
+  a.dot_part = dot ? ctx->dot_part : nullptr;
+  launch_half_step(a, which == 0 ? ctx->grid_u : ctx->grid_v, ctx->stream);
+}
+
+static int half_grid(enmf_ctx* ctx, int64_t rows, int grid) {
+  int64_t need = (rows + 63) / 64;
+  return (int)((int64_t)grid > need ? need : grid);
+}
+
+extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void* V,
+                                    const enmf_iter_opts* opts, enmf_iter_info* info) {
+  GUARD(ctx);
+  if (!X || !U || !V) return ENMF_EINVAL;
+  enmf_iter_opts o = {0, 5, 1e-4, 3, nullptr, 0, 1};
+  if (opts) o = *opts;
+  if (o.n_iter < 0 || o.pbcd_max_iter < 0 || !(o.eps >= 0) || o.n_shift < 1) return ENMF_EINVAL;
+  const enmf_problem& p = ctx->p;
+  const int k = p.r, fdt = ctx->fdt, xdt = ctx->xdt;
+  const int64_t m = p.m, n = p.n;
+  cudaStream_t s = ctx->stream;
+  if (o.reset || !ctx->state_valid) {
+    launch_state_init(U, V, m, n, k, fdt, o.n_shift, ctx->st, ctx->part, s);
+    ctx->state_valid = true;
+  }
+  launch_normx2(X, xdt, m, n, p.ldx, ctx->part, &ctx->st->normX2, ctx->err, s);
+  launch_gram(V, k, k, V, k, k, n, fdt, ctx->part, ctx->Gv, s);
+  const int ndot = half_grid(ctx, n, ctx->grid_v);
+  for (int it = 0; it < o.n_iter; ++it) {
+    launch_xv(X, xdt, m, n, p.ldx, V, k, k, ctx->M0, k, fdt, ctx->splitk, ctx->num_sms, s);
+    run_half(ctx, 0, U, ctx->M0, ctx->Gv, m, o, false);
+    launch_gram(U, k, k, U, k, k, m, fdt, ctx->part, ctx->Gu, s);
+    launch_xtu(X, xdt, m, n, p.ldx, U, k, k, ctx->N0, k, fdt, ctx->splitk, ctx->num_sms, s);
+    run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true);
+    launch_gram(V, k, k, V, k, k, n, fdt, ctx->part, ctx->Gv, s);
+    launch_iter_finalize(ctx->st, ctx->dot_part, ndot, ctx->Gu, ctx->Gv, k, o.trace, it, s);
+  }
+  enmf_status rc = check_launch(ctx);
+  if (rc) return rc;
+  if (o.sync_info || info) {
+    DevState hst;
+    CK(cudaMemcpyAsync(&hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    rc = sync_status(ctx);
+    if (info) {
+      info->iters = hst.k;
+      info->asc_iters = hst.asc_iters;
+      info->hals_iters = hst.hals_iters;
+      info->stage = hst.stage;
+      info->s_u = hst.s_u;
+      info->s_v = hst.s_v;
+    }
+    return rc;
+  }
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_pbcd_counts(enmf_ctx* ctx, int32_t* out, int32_t cap, int32_t* count) {
+  GUARD(ctx);
+  if (!out || !count || cap < 0) return ENMF_EINVAL;
+  DevState hst;
+  CK(cudaMemcpyAsync(&hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int nasc = hst.asc_iters;
+  int ncopy = 2 * nasc;
+  if (ncopy > cap) ncopy = cap;
+  if (ncopy > ctx->counts_cap) ncopy = ctx->counts_cap;
+  if (ncopy > 0) CK(cudaMemcpy(out, ctx->counts, ncopy * sizeof(int), cudaMemcpyDeviceToHost));
+  *count = nasc;
+  return ENMF_OK;
+}
+
+// ------------------------------------------------------------ 4. residual
+extern "C" enmf_status enmf_residual(enmf_ctx* ctx, const void* X, const void* U, const void* V,
+                                     double* out3, int32_t direct) {
+  GUARD(ctx);
+  if (!X || !U || !V || !out3) return ENMF_EINVAL;
+  const enmf_problem& p = ctx->p;
+  const int k = p.r, fdt = ctx->fdt, xdt = ctx->xdt;
+  const int64_t m = p.m, n = p.n;
+  cudaStream_t s = ctx->stream;
+  launch_normx2(X, xdt, m, n, p.ldx, ctx->part, &ctx->scal[8], ctx->err, s);
+  if (direct) {
+    launch_residual_direct(X, xdt, m, n, p.ldx, U, V, k, fdt, ctx->part, &ctx->scal[9], s);
+  } else {
+    launch_xtu(X, xdt, m, n, p.ldx, U, k, k, ctx->N0, k, fdt, ctx->splitk, ctx->num_sms, s);
+    launch_dot(ctx->N0, k, V, k, k, n, fdt, ctx->part, &ctx->scal[10], s);
+    launch_gram(U, k, k, U, k, k, m, fdt, ctx->part, ctx->Gu, s);
+    launch_gram(V, k, k, V, k, k, n, fdt, ctx->part, ctx->Gv, s);
+    launch_dot(ctx->Gu, k, ctx->Gv, k, k, k, T_F64, ctx->part, &ctx->scal[11], s);
+  }
+  enmf_status rc = check_launch(ctx);
+  if (rc) return rc;
+  double h[4];
+  CK(cudaMemcpyAsync(h, &ctx->scal[8], 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  rc = sync_status(ctx);
+  if (rc) return rc;
+  double e2 = direct ? h[1] : h[0] - 2.0 * h[2] + h[3];
+  out3[0] = 0.5 * e2;
+  out3[1] = h[0] > 0 ? sqrt(e2 > 0 ? e2 : 0.0) / sqrt(h[0]) : 0.0;
+  out3[2] = h[0];
+  return ENMF_OK;
+}
+
+// ----------------------------------------------------------------- 5. KKT
+extern "C" enmf_status enmf_kkt(enmf_ctx* ctx, const void* X, const void* U, const void* V,
+                                enmf_kkt_report* out) {
+  GUARD(ctx);
+  if (!X || !U || !V || !out) return ENMF_EINVAL;
+  const enmf_problem& p = ctx->p;
+  const int k = p.r, fdt = ctx->fdt, xdt = ctx->xdt;
+  const int64_t m = p.m, n = p.n;
+  cudaStream_t s = ctx->stream;
+  launch_xv(X, xdt, m, n, p.ldx, V, k, k, ctx->M0, k, fdt, ctx->splitk, ctx->num_sms, s);
+  launch_xtu(X, xdt, m, n, p.ldx, U, k, k, ctx->N0, k, fdt, ctx->splitk, ctx->num_sms, s);
+  launch_gram(U, k, k, U, k, k, m, fdt, ctx->part, ctx->Gu, s);
+  launch_gram(V, k, k, V, k, k, n, fdt, ctx->part, ctx->Gv, s);
+  launch_kkt_rows(U, ctx->M0, ctx->Gv, m, k, fdt, ctx->part, &ctx->scal[16], s);
+  launch_kkt_rows(V, ctx->N0, ctx->Gu, n, k, fdt, ctx->part, &ctx->scal[24], s);
+  launch_kkt_final(&ctx->scal[16], &ctx->scal[24], &ctx->scal[32], s);
+  enmf_status rc = check_launch(ctx);
+  if (rc) return rc;
+  double h[6];
+  CK(cudaMemcpyAsync(h, &ctx->scal[32], 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  rc = sync_status(ctx);
+  if (rc) return rc;
+  out->min_w = h[0];
+  out->min_grad = h[1];
+  out->delta = h[2];
+  out->sigma = h[3];
+  out->pg_norm = h[4];
+  out->pg_rel = h[5];
+  return ENMF_OK;
+}
+
+// ------------------------------------------------------------- one call
+static bool is_device_ptr(const void* q) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+extern "C" enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V, int32_t n_iter,
+                                  const enmf_svd_opts* svd, const enmf_admm_opts* admm,
+                                  const enmf_iter_opts* iter, double* out3) {
+  GUARD(ctx);
+  if (!X || !U || !V || n_iter < 0) return ENMF_EINVAL;
+  const enmf_problem& p = ctx->p;
+  const size_t xs = type_size(ctx->xdt), fs = type_size(ctx->fdt);
+  const size_t xbytes = (size_t)((p.m - 1) * p.ldx + p.n) * xs;
+  const size_t ub = (size_t)p.m * p.r * fs, vb = (size_t)p.n * p.r * fs;
+  cudaStream_t s = ctx->stream;
+  const void* dX = X;
+  void* dU = U;
+  void* dV = V;
+  bool hostU = !is_device_ptr(U), hostV = !is_device_ptr(V);
+  if (!is_device_ptr(X)) {
+    if (!ctx->hX || ctx->hX_bytes < xbytes) {
+      if (ctx->hX) cudaFree(ctx->hX);
+      ctx->hX = nullptr;
+      if (cudaMalloc(&ctx->hX, xbytes) != cudaSuccess) { cudaGetLastError(); return ENMF_ENOMEM; }
+      ctx->hX_bytes = xbytes;
+    }
+    CK(cudaMemcpyAsync(ctx->hX, X, xbytes, cudaMemcpyHostToDevice, s));
+    dX = ctx->hX;
+  }
+  if (hostU) {
+    if (!ctx->hU && cudaMalloc(&ctx->hU, ub) != cudaSuccess) { cudaGetLastError(); return ENMF_ENOMEM; }
+    dU = ctx->hU;
+  }
+  if (hostV) {
+    if (!ctx->hV && cudaMalloc(&ctx->hV, vb) != cudaSuccess) { cudaGetLastError(); return ENMF_ENOMEM; }
+    dV = ctx->hV;
+  }
+  enmf_status rc = enmf_svd_init(ctx, dX, dU, dV, nullptr, svd, nullptr);
+  if (rc && rc != ENMF_ENOTCONV) return rc;
+  rc = enmf_rotate(ctx, dU, dV, nullptr, admm, nullptr);
+  if (rc && rc != ENMF_ENOTCONV) return rc;
+  enmf_iter_opts io = {n_iter, 5, 1e-4, 3, nullptr, 1, 0};
+  if (iter) {
+    io = *iter;
+    io.n_iter = n_iter;
+    io.reset = 1;
+    io.sync_info = 0;
+  }
+  rc = enmf_iterate(ctx, dX, dU, dV, &io, nullptr);
+  if (rc) return rc;
+  double o3[3];
+  rc = enmf_residual(ctx, dX, dU, dV, o3, 1);
+  if (rc) return rc;
+  if (hostU) CK(cudaMemcpyAsync(U, dU, ub, cudaMemcpyDeviceToHost, s));
+  if (hostV) CK(cudaMemcpyAsync(V, dV, vb, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (out3) memcpy(out3, o3, sizeof(o3));
+  return ENMF_OK;
+}

@@ -1,0 +1,147 @@
+// Internal declarations shared by the library's translation units: the
+// device-resident iteration state, the context, and the host-side launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/enmf.h"
+#include "common.cuh"
+
+namespace enmf {
+
+// Type codes for runtime dispatch.
+enum : int { T_F64 = 0, T_F32 = 1, T_BF16 = 2, T_F16 = 3 };
+
+inline size_t type_size(int t) { return t == T_F64 ? 8 : t == T_F32 ? 4 : 2; }
+
+// Iteration state of Algorithm 3, resident in device memory so that the
+// stage decision (ascent vs HALS) never needs a host round trip.
+struct DevState {
+  int stage;          // 0 ascent (Alg. 3 lines 5-11), 1 HALS (line 12)
+  int k;              // alternations done
+  int asc_iters;
+  int hals_iters;
+  int negU, negV;     // a negative entry remains after this half (ascent)
+  int admm_done;
+  int admm_steps;
+  int svd_rank;
+  int pad_;
+  double s_u, s_v;            // shift steps of Eq. 8 / 9
+  double maxneg_u, maxneg_v;  // max(-U), max(-V) when the stage started
+  double normX2;              // ||X||_F^2
+  double dR;                  // last ADMM ||R_k+1 - R_k||_F
+  double rho;                 // ADMM penalty
+  double negmass;             // sum h(.) scratch
+  double svd_res;             // SVD start residual
+  double sigma1;
+  GridBarrier bar;
+};
+
+// Number of fixed-order partial sums used by the reduction kernels.  It does
+// not depend on the device, so results are reproducible across GPUs.
+constexpr int NPART = 256;
+
+// Split-K choice for the SIMT sweeps (also used to size the workspace).
+int choose_splits(int64_t rows_out, int64_t red_len, int k, int bm, int num_sms);
+
+// ---------------------------------------------------------------- sweep.cu
+// C (rows_out x k, leading dim ldc) = X B (xv) or X^T B (xtu), FP64 or FP32
+// accumulation by fdt; X element type xdt.  `part` is split-K scratch.
+void launch_xv(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, const void* B, int ldb,
+               int k, void* C, int ldc, int fdt, void* part, int num_sms, cudaStream_t s);
+void launch_xtu(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, const void* B, int ldb,
+                int k, void* C, int ldc, int fdt, void* part, int num_sms, cudaStream_t s);
+// G (ka x kb, FP64, row-major) = A^T B over `rows` rows.
+void launch_gram(const void* A, int lda, int ka, const void* B, int ldb, int kb, int64_t rows,
+                 int fdt, double* part, double* G, cudaStream_t s);
+// out[0] = sum_ij A_ij B_ij (FP64).
+void launch_dot(const void* A, int lda, const void* B, int ldb, int k, int64_t rows, int fdt,
+                double* part, double* out, cudaStream_t s);
+// out[0] = ||X||_F^2, and ERR_DOMAIN if X has a negative/non-finite entry.
+void launch_normx2(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, double* part,
+                   double* out, int* err, cudaStream_t s);
+// out[0] = ||X - U V^T||_F^2 formed entry by entry.
+void launch_residual_direct(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx,
+                            const void* U, const void* V, int r, int fdt, double* part,
+                            double* out, cudaStream_t s);
+// out[e] = sum over NPART blocks of part[b * width + e], in block order.
+void launch_part_reduce(const double* part, int width, double* out, cudaStream_t s);
+// Omega (rows x k, ld k) uniform(-1, 1) from (seed, i, j).
+void launch_omega(void* F, int fdt, int64_t rows, int k, uint64_t seed, cudaStream_t s);
+
+// ----------------------------------------------------------------- rows.cu
+struct HalfArgs {
+  void* F;            // factor being updated (rows x k)
+  const void* A;      // X V or X^T U for this half (rows x k, ld k)
+  const double* G;    // Gram of the other factor (k x k)
+  void* gbuf;         // PBCD gradient scratch (rows x k)
+  unsigned long long* mask;  // PBCD mask bits (rows)
+  int64_t rows;
+  int k;
+  int fdt;
+  int which;          // 0: U-half, 1: V-half
+  int pbcd_max_iter;
+  double eps;
+  DevState* st;
+  double* part;       // NPART x 2 scratch
+  int* err;
+  int* counts;        // PBCD sweep counts per ascent step (2 per step)
+  int counts_cap;
+  const void* dotA;   // if non-null: V-half also sums <dotA, F> into dot_part
+  double* dot_part;
+};
+void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);
+int half_step_grid(int fdt, int k, int num_sms);
+void launch_state_init(const void* U, const void* V, int64_t m, int64_t n, int k, int fdt,
+                       int n_shift, DevState* st, double* part, cudaStream_t s);
+void launch_iter_finalize(DevState* st, const double* dot_part, int ndot, const double* Gu,
+                          const double* Gv, int k, double* trace, int trace_idx, cudaStream_t s);
+// ADMM pass of Algorithm 1 over W = [U; V] (see rows.cu).
+void launch_admm_pass(const void* U, const void* V, int64_t m, int64_t n, int k, int fdt,
+                      const double* R, void* Z, void* Y, double rho, int first, DevState* st,
+                      double* part, cudaStream_t s);
+// out rows = in rows * T (k_in x k_out, FP64 row-major); in/out may not alias.
+void launch_row_transform(const void* in, int ld_in, int k_in, void* out, int ld_out, int k_out,
+                          int64_t rows, int fdt, const double* T, cudaStream_t s);
+// In-place rows * R (k x k).
+void launch_apply_square(void* F, int64_t rows, int k, int fdt, const double* R, cudaStream_t s);
+// out[0] = sum h(F) over rows (negative mass), in FP64.
+void launch_negmass(const void* F, int64_t rows, int k, int fdt, double* part, double* out,
+                    int accumulate, cudaStream_t s);
+// Column sums of the first k columns of F (rows x ld) into out (k doubles).
+void launch_colsum(const void* F, int64_t rows, int ld, int k, int fdt, double* part, double* out,
+                   cudaStream_t s);
+// SVD-start residual: sum_i ||Y_i Wr - Q_i Ur S||^2 (see rows.cu).
+void launch_rr_residual(const void* Y, int ldy, int ky, const void* Q, int ldq, int kq,
+                        int64_t rows, int r, int fdt, const double* Wr, const double* UrS,
+                        double* part, double* out, cudaStream_t s);
+// KKT partial measures for one factor (see rows.cu); out gets 8 doubles.
+void launch_kkt_rows(const void* F, const void* A, const double* G, int64_t rows, int k, int fdt,
+                     double* part, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- small.cu
+// R_new = polar(sum of NPART partial M's); dR, convergence, ADMM step count.
+void launch_polar(const double* part, int k, double* R, double* R_prev, double tol,
+                  DevState* st, int* err, cudaStream_t s);
+// Orthonormalising transform of a Gram G (k x k): eigen-decomposition by
+// one-sided Jacobi, keep eigenvalues > tau * lambda_1, T = V_k diag(l^-1/2).
+// Writes T (k x k, unused columns zero) and *kept.
+void launch_eig_orth(const double* G, int k, double tau, double* T, int* kept, int* err,
+                     cudaStream_t s);
+// SVD of the (k2 x k1) matrix R2^T given R2 = P (k2 x k1 row-major):
+// R2^T = Ut S Wt^T, sorted descending.  Writes sigma (k1), Ut (k1 x k1),
+// Wt (k2 x k1).  See small.cu for layouts.
+void launch_rr_svd(const double* P, int k2, int k1, double* sigma, double* Ut, double* Wt,
+                   int* err, cudaStream_t s);
+// Final SVD-start transforms with the sign rule (see small.cu).
+void launch_svd_finish(const double* sigma, const double* Ut, const double* Wt, int k1, int k2,
+                       int r, const double* colsumQ, const double* colsumQ2, double* Tu,
+                       double* Tv, double* sigma_out, cudaStream_t s);
+void launch_rr_prep(const double* sigma, const double* Ut, const double* Wt, int k1, int k2,
+                    int r, double* Wr, double* UrS, DevState* st, cudaStream_t s);
+// KKT finalisation: combine the two factors' partial measures.
+void launch_kkt_final(const double* pu, const double* pv, double* out, cudaStream_t s);
+
+}  // namespace enmf

@@ -1,0 +1,586 @@
+// Row-local kernels of the eNMF path.
+//
+// The U-half of an alternation is row separable (Sec. 4.2: rows do not
+// interact with V fixed): row i needs only its row of X V, the r x r Gram
+// V^T V and its own row of U.  So every update here is one thread per factor
+// row, with the Gram staged in shared memory:
+//   * half_step_kernel -- the ascent step of Algorithm 3 (Eq. 8/9 shift,
+//     mask, Algorithm 2 PBCD with the Eq. 10/11 step) or a HALS sweep;
+//   * admm_pass_kernel -- one ADMM pass of Algorithm 1 over W = [U; V];
+//   * transforms, negative mass, column sums and the KKT measures (App. G).
+// Cost per row is O(r^2); all of these are small next to the O(m n r) sweeps.
+#include "internal.h"
+
+namespace enmf {
+
+// ----------------------------------------------------------- half step
+constexpr int HS_T = 64;
+
+static size_t half_step_smem(int fdt, int k) {
+  size_t e = type_size(fdt);
+  return e * ((size_t)k * k + 2 * (size_t)k * HS_T);
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(HS_T) half_step_kernel(HalfArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TF* Gs = reinterpret_cast<TF*>(smraw);
+  TF* us = Gs + a.k * a.k;          // us[j * HS_T + t]
+  TF* gs = us + a.k * HS_T;         // gs[j * HS_T + t]
+  __shared__ double sh[HS_T];
+  __shared__ double bc;
+
+  const int k = a.k;
+  for (int e = threadIdx.x; e < k * k; e += HS_T) Gs[e] = (TF)a.G[e];
+  __syncthreads();
+
+  DevState* st = a.st;
+  const int stage = *(volatile int*)&st->stage;
+  TF* F = (TF*)a.F;
+  const TF* A = (const TF*)a.A;
+  TF* gb = (TF*)a.gbuf;
+  const int64_t rows = a.rows;
+  const int64_t nth = (int64_t)gridDim.x * HS_T;
+  const int64_t tid = (int64_t)blockIdx.x * HS_T + threadIdx.x;
+  const int t = threadIdx.x;
+  TF* u = us + t;   // u[j * HS_T]
+  TF* g = gs + t;
+  double dotacc = 0.0;
+
+  if (stage == 1) {
+    // HALS: for j in order, u_j <- max(0, u_j + (a_j - sum_l u_l G_lj) / G_jj)
+    for (int64_t i = tid; i < rows; i += nth) {
+      for (int j = 0; j < k; ++j) u[j * HS_T] = F[i * k + j];
+      for (int j = 0; j < k; ++j) {
+        TF gjj = Gs[j * k + j];
+        if (!(gjj > TF(0))) continue;
+        TF s = TF(0);
+        for (int l = 0; l < k; ++l) s = fma(u[l * HS_T], Gs[l * k + j], s);
+        TF v = u[j * HS_T] + (A[i * k + j] - s) / gjj;
+        u[j * HS_T] = v > TF(0) ? v : TF(0);
+      }
+      for (int j = 0; j < k; ++j) F[i * k + j] = u[j * HS_T];
+      if (a.dot_part)
+        for (int j = 0; j < k; ++j) dotacc = fma((double)A[i * k + j], (double)u[j * HS_T], dotacc);
+    }
+  } else {
+    // Ascent step: shift, mask, PBCD (Algorithm 2).
+    const double sft = a.which == 0 ? st->s_u : st->s_v;
+    const TF s = (TF)sft;
+    double acc = 0.0;
+    for (int64_t i = tid; i < rows; i += nth) {
+      unsigned long long mk = 0ull;
+      for (int j = 0; j < k; ++j) {
+        TF v = F[i * k + j];
+        if (v < TF(0)) v = v + s;                // Eq. 8 / 9, literal (no clamp)
+        u[j * HS_T] = v;
+        if (v >= TF(0)) mk |= (1ull << j);
+      }
+      for (int j = 0; j < k; ++j) {
+        TF gj = TF(0);
+        if ((mk >> j) & 1ull) {
+          TF sdot = TF(0);
+          for (int l = 0; l < k; ++l) sdot = fma(u[l * HS_T], Gs[l * k + j], sdot);
+          gj = sdot - A[i * k + j];
+        }
+        g[j * HS_T] = gj;
+        acc = fma((double)gj, (double)gj, acc);
+      }
+      for (int j = 0; j < k; ++j) {
+        F[i * k + j] = u[j * HS_T];
+        gb[i * k + j] = g[j * HS_T];
+      }
+      a.mask[i] = mk;
+    }
+    double bsum = block_sum(acc, sh);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = bsum;
+    grid_sync(&st->bar, a.err);
+    if (threadIdx.x == 0) {
+      double tsum = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) tsum += a.part[b];
+      bc = tsum;
+    }
+    __syncthreads();
+    const double g0 = sqrt(bc);
+    int iters = 0;
+    for (int it = 0; it < a.pbcd_max_iter; ++it) {
+      acc = 0.0;
+      for (int64_t i = tid; i < rows; i += nth) {
+        const unsigned long long mk = a.mask[i];
+        for (int j = 0; j < k; ++j) {
+          u[j * HS_T] = F[i * k + j];
+          g[j * HS_T] = gb[i * k + j];
+        }
+        // d_i = ||g_i||^2 / (g_i G g_i^T)   (Eq. 10; App. B)
+        TF num = TF(0), den = TF(0);
+        for (int j = 0; j < k; ++j) {
+          TF gj = g[j * HS_T];
+          num = fma(gj, gj, num);
+          TF row = TF(0);
+          for (int l = 0; l < k; ++l) row = fma(Gs[j * k + l], g[l * HS_T], row);
+          den = fma(gj, row, den);
+        }
+        TF d = (num > TF(0) && den > TF(0)) ? num / den : TF(0);
+        for (int j = 0; j < k; ++j)
+          if ((mk >> j) & 1ull) {
+            TF v = u[j * HS_T] - d * g[j * HS_T];
+            u[j * HS_T] = v > TF(0) ? v : TF(0);   // (.)_+ of Eq. 9 pbcdu
+          }
+        for (int j = 0; j < k; ++j) {
+          TF gj = TF(0);
+          if ((mk >> j) & 1ull) {
+            TF sdot = TF(0);
+            for (int l = 0; l < k; ++l) sdot = fma(u[l * HS_T], Gs[l * k + j], sdot);
+            gj = sdot - A[i * k + j];
+          }
+          g[j * HS_T] = gj;
+          acc = fma((double)gj, (double)gj, acc);
+        }
+        for (int j = 0; j < k; ++j) {
+          F[i * k + j] = u[j * HS_T];
+          gb[i * k + j] = g[j * HS_T];
+        }
+      }
+      double* pbuf = a.part + (size_t)((it + 1) & 1) * gridDim.x;
+      bsum = block_sum(acc, sh);
+      if (threadIdx.x == 0) pbuf[blockIdx.x] = bsum;
+      grid_sync(&st->bar, a.err);
+      if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) tsum += pbuf[b];
+        bc = tsum;
+      }
+      __syncthreads();
+      const double pg = sqrt(bc);
+      iters = it + 1;
+      if (pg < a.eps * g0 || bc == 0.0) break;
+    }
+    // entries still negative (unmasked) keep the ascent stage going
+    int neg = 0;
+    for (int64_t i = tid; i < rows; i += nth) {
+      const unsigned long long mk = a.mask[i];
+      if (~mk & ((k == 64) ? ~0ull : ((1ull << k) - 1ull))) neg = 1;
+      if (a.dot_part)
+        for (int j = 0; j < k; ++j) dotacc = fma((double)A[i * k + j], (double)F[i * k + j], dotacc);
+    }
+    if (neg) atomicOr(a.which == 0 ? &st->negU : &st->negV, 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      int q = st->asc_iters;
+      if (a.counts && 2 * q + a.which < a.counts_cap) a.counts[2 * q + a.which] = iters;
+    }
+  }
+  if (a.dot_part) {
+    double bsum = block_sum(dotacc, sh);
+    if (threadIdx.x == 0) a.dot_part[blockIdx.x] = bsum;
+  }
+}
+
+int half_step_grid(int fdt, int k, int num_sms) {
+  int per = 0;
+  size_t smem = half_step_smem(fdt, k);
+  if (fdt == T_F64) {
+    cudaFuncSetAttribute(half_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, half_step_kernel<double>, HS_T, smem);
+  } else {
+    cudaFuncSetAttribute(half_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, half_step_kernel<float>, HS_T, smem);
+  }
+  if (per < 1) per = 1;
+  return per * num_sms;
+}
+
+void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s) {
+  int64_t need = (a.rows + HS_T - 1) / HS_T;
+  if ((int64_t)grid > need) grid = (int)need;
+  if (grid < 1) grid = 1;
+  size_t smem = half_step_smem(a.fdt, a.k);
+  void* args[] = {(void*)&a};
+  if (a.fdt == T_F64)
+    cudaLaunchCooperativeKernel((void*)half_step_kernel<double>, dim3(grid), dim3(HS_T), args, smem, s);
+  else
+    cudaLaunchCooperativeKernel((void*)half_step_kernel<float>, dim3(grid), dim3(HS_T), args, smem, s);
+}
+
+// ----------------------------------------------------------- stage start
+__global__ void state_reset_kernel(DevState* st) {
+  st->maxneg_u = 0.0;
+  st->maxneg_v = 0.0;
+  st->k = 0;
+  st->asc_iters = 0;
+  st->hals_iters = 0;
+  st->negU = 0;
+  st->negV = 0;
+}
+
+template <typename TF>
+__global__ void maxneg_kernel(const TF* __restrict__ F, int64_t total, double* out) {
+  __shared__ double sh[256];
+  double mx = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    mx = fmax(mx, -(double)F[e]);
+  mx = block_max(mx, sh);
+  if (threadIdx.x == 0 && mx > 0.0) atomic_max_nonneg(out, mx);
+}
+
+__global__ void state_start_kernel(DevState* st, int n_shift) {
+  // Eq. 8 / 9 step (reading: max(-F) / (n_shift - 1/2)), fixed for the stage
+  st->s_u = st->maxneg_u / ((double)n_shift - 0.5);
+  st->s_v = st->maxneg_v / ((double)n_shift - 0.5);
+  st->stage = (st->maxneg_u > 0.0 || st->maxneg_v > 0.0) ? 0 : 1;
+}
+
+void launch_state_init(const void* U, const void* V, int64_t m, int64_t n, int k, int fdt,
+                       int n_shift, DevState* st, double* part, cudaStream_t s) {
+  (void)part;
+  state_reset_kernel<<<1, 1, 0, s>>>(st);
+  int bu = (int)min((int64_t)1024, (m * k + 255) / 256);
+  int bv = (int)min((int64_t)1024, (n * k + 255) / 256);
+  if (fdt == T_F64) {
+    maxneg_kernel<double><<<bu, 256, 0, s>>>((const double*)U, m * k, &st->maxneg_u);
+    maxneg_kernel<double><<<bv, 256, 0, s>>>((const double*)V, n * k, &st->maxneg_v);
+  } else {
+    maxneg_kernel<float><<<bu, 256, 0, s>>>((const float*)U, m * k, &st->maxneg_u);
+    maxneg_kernel<float><<<bv, 256, 0, s>>>((const float*)V, n * k, &st->maxneg_v);
+  }
+  state_start_kernel<<<1, 1, 0, s>>>(st, n_shift);
+}
+
+// f = 1/2 ||X||^2 - <X^T U, V> + 1/2 <U^T U, V^T V>, then the stage update.
+__global__ void iter_finalize_kernel(DevState* st, const double* dot_part, int ndot,
+                                     const double* Gu, const double* Gv, int k, double* trace,
+                                     int trace_idx) {
+  __shared__ double sh[256];
+  double g = 0.0;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) g = fma(Gu[e], Gv[e], g);
+  g = block_sum(g, sh);
+  if (threadIdx.x == 0) {
+    double d = 0.0;
+    for (int b = 0; b < ndot; ++b) d += dot_part[b];
+    double f = 0.5 * st->normX2 - d + 0.5 * g;
+    if (trace) trace[trace_idx] = f;
+    if (st->stage == 0) st->asc_iters += 1;
+    else st->hals_iters += 1;
+    st->k += 1;
+    if (st->stage == 0 && !(st->negU || st->negV)) st->stage = 1;
+    st->negU = 0;
+    st->negV = 0;
+  }
+}
+
+void launch_iter_finalize(DevState* st, const double* dot_part, int ndot, const double* Gu,
+                          const double* Gv, int k, double* trace, int trace_idx, cudaStream_t s) {
+  iter_finalize_kernel<<<1, 256, 0, s>>>(st, dot_part, ndot, Gu, Gv, k, trace, trace_idx);
+}
+
+// -------------------------------------------------------------- ADMM pass
+constexpr int AP_T = 128;       // threads = rows per tile
+constexpr int AP_S = AP_T + 1;  // padded stride of the staged tiles
+constexpr int AP_PER_T = (RMAX * RMAX + AP_T - 1) / AP_T;
+
+template <typename TF>
+__global__ void __launch_bounds__(AP_T)
+admm_pass_kernel(const TF* __restrict__ U, const TF* __restrict__ V, int64_t m, int64_t n, int k,
+                 const double* __restrict__ R, TF* __restrict__ Z, TF* __restrict__ Y, double rho_d,
+                 int first, DevState* st, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TF* Rs = reinterpret_cast<TF*>(smraw);        // k x k
+  TF* Ws = Rs + k * k;                          // Ws[j * AP_S + t]
+  TF* Bs = Ws + k * AP_S;                       // Bs[j * AP_S + t]
+  __shared__ double sh[AP_T];
+  if (*(volatile int*)&st->admm_done) return;
+  for (int e = threadIdx.x; e < k * k; e += AP_T) Rs[e] = (TF)R[e];
+  const TF rho = (TF)rho_d;
+  const TF thr = TF(-1) / rho;
+  const int64_t rows = m + n;
+  const int t = threadIdx.x;
+  double acc[AP_PER_T];
+#pragma unroll
+  for (int q = 0; q < AP_PER_T; ++q) acc[q] = 0.0;
+  double negm = 0.0;
+  for (int64_t t0 = (int64_t)blockIdx.x * AP_T; t0 < rows; t0 += (int64_t)gridDim.x * AP_T) {
+    __syncthreads();
+    const int64_t i = t0 + t;
+    if (i < rows) {
+      const TF* w = i < m ? U + i * k : V + (i - m) * k;
+      for (int j = 0; j < k; ++j) Ws[j * AP_S + t] = w[j];
+      for (int j = 0; j < k; ++j) {
+        TF p = TF(0);
+        for (int l = 0; l < k; ++l) p = fma(Ws[l * AP_S + t], Rs[l * k + j], p);
+        negm += p < TF(0) ? -(double)p : 0.0;
+        TF y = Y[i * k + j];
+        if (!first) y = y + rho * (Z[i * k + j] - p);   // Y update of Algorithm 1
+        TF b = p - y / rho;                             // b = W R - Y / rho
+        TF z = b > TF(0) ? b : (b >= thr ? TF(0) : b + TF(1) / rho);   // Eq. 7
+        Z[i * k + j] = z;
+        Y[i * k + j] = y;
+        Bs[j * AP_S + t] = z + y / rho;                 // B = Z + Y / rho
+      }
+    } else {
+      for (int j = 0; j < k; ++j) {
+        Ws[j * AP_S + t] = TF(0);
+        Bs[j * AP_S + t] = TF(0);
+      }
+    }
+    __syncthreads();
+    // M += W_tile^T B_tile
+#pragma unroll
+    for (int q = 0; q < AP_PER_T; ++q) {
+      int e = t + q * AP_T;
+      if (e < k * k) {
+        int a = e / k, b = e % k;
+        double sacc = acc[q];
+        for (int rr = 0; rr < AP_T; ++rr)
+          sacc = fma((double)Ws[a * AP_S + rr], (double)Bs[b * AP_S + rr], sacc);
+        acc[q] = sacc;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < AP_PER_T; ++q) {
+    int e = t + q * AP_T;
+    if (e < k * k) part[(int64_t)blockIdx.x * k * k + e] = acc[q];
+  }
+  negm = block_sum(negm, sh);
+  if (t == 0) part[(int64_t)NPART * k * k + blockIdx.x] = negm;
+}
+
+void launch_admm_pass(const void* U, const void* V, int64_t m, int64_t n, int k, int fdt,
+                      const double* R, void* Z, void* Y, double rho, int first, DevState* st,
+                      double* part, cudaStream_t s) {
+  size_t smem = type_size(fdt) * ((size_t)k * k + 2 * (size_t)k * AP_S);
+  if (fdt == T_F64) {
+    cudaFuncSetAttribute(admm_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    admm_pass_kernel<double><<<NPART, AP_T, smem, s>>>((const double*)U, (const double*)V, m, n, k, R,
+                                                       (double*)Z, (double*)Y, rho, first, st, part);
+  } else {
+    cudaFuncSetAttribute(admm_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    admm_pass_kernel<float><<<NPART, AP_T, smem, s>>>((const float*)U, (const float*)V, m, n, k, R,
+                                                      (float*)Z, (float*)Y, rho, first, st, part);
+  }
+}
+
+// -------------------------------------------------------- row transforms
+constexpr int RT_T = 64;
+
+template <typename TF>
+__global__ void __launch_bounds__(RT_T)
+row_transform_kernel(const TF* in, int ld_in, int k_in, TF* out, int ld_out, int k_out,
+                     int64_t rows, const double* __restrict__ T) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TF* Ts = reinterpret_cast<TF*>(smraw);       // k_in x k_out
+  TF* xs = Ts + k_in * k_out;                  // xs[l * RT_T + t]
+  for (int e = threadIdx.x; e < k_in * k_out; e += RT_T) Ts[e] = (TF)T[e];
+  __syncthreads();
+  const int t = threadIdx.x;
+  for (int64_t i = (int64_t)blockIdx.x * RT_T + t; i < rows; i += (int64_t)gridDim.x * RT_T) {
+    for (int l = 0; l < k_in; ++l) xs[l * RT_T + t] = in[i * ld_in + l];
+    for (int j = 0; j < k_out; ++j) {
+      TF s = TF(0);
+      for (int l = 0; l < k_in; ++l) s = fma(xs[l * RT_T + t], Ts[l * k_out + j], s);
+      out[i * ld_out + j] = s;
+    }
+  }
+}
+
+void launch_row_transform(const void* in, int ld_in, int k_in, void* out, int ld_out, int k_out,
+                          int64_t rows, int fdt, const double* T, cudaStream_t s) {
+  size_t smem = type_size(fdt) * ((size_t)k_in * k_out + (size_t)k_in * RT_T);
+  int blocks = (int)min((int64_t)1024, (rows + RT_T - 1) / RT_T);
+  if (blocks < 1) blocks = 1;
+  if (fdt == T_F64) {
+    cudaFuncSetAttribute(row_transform_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    row_transform_kernel<double><<<blocks, RT_T, smem, s>>>((const double*)in, ld_in, k_in, (double*)out,
+                                                            ld_out, k_out, rows, T);
+  } else {
+    cudaFuncSetAttribute(row_transform_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    row_transform_kernel<float><<<blocks, RT_T, smem, s>>>((const float*)in, ld_in, k_in, (float*)out,
+                                                           ld_out, k_out, rows, T);
+  }
+}
+
+void launch_apply_square(void* F, int64_t rows, int k, int fdt, const double* R, cudaStream_t s) {
+  // each thread stages its row before writing, so in place is safe
+  launch_row_transform(F, k, k, F, k, k, rows, fdt, R, s);
+}
+
+// ----------------------------------------------------- small reductions
+template <typename TF>
+__global__ void __launch_bounds__(256)
+negmass_partial(const TF* __restrict__ F, int64_t total, double* part) {
+  __shared__ double sh[256];
+  const int64_t chunk = (total + NPART - 1) / NPART;
+  const int64_t e0 = (int64_t)blockIdx.x * chunk, e1 = min(total, e0 + chunk);
+  double s = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += 256) {
+    double v = (double)F[e];
+    s += v < 0.0 ? -v : 0.0;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void part_sum_to(const double* part, int count, double* out, int accumulate) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < count; ++b) s += part[b];
+    out[0] = accumulate ? out[0] + s : s;
+  }
+}
+
+void launch_negmass(const void* F, int64_t rows, int k, int fdt, double* part, double* out,
+                    int accumulate, cudaStream_t s) {
+  if (fdt == T_F64) negmass_partial<double><<<NPART, 256, 0, s>>>((const double*)F, rows * k, part);
+  else negmass_partial<float><<<NPART, 256, 0, s>>>((const float*)F, rows * k, part);
+  part_sum_to<<<1, 32, 0, s>>>(part, NPART, out, accumulate);
+}
+
+template <typename TF>
+__global__ void colsum_partial(const TF* __restrict__ F, int64_t rows, int ld, int k, double* part) {
+  const int64_t chunk = (rows + NPART - 1) / NPART;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double s = 0.0;
+    for (int64_t i = r0; i < r1; ++i) s += (double)F[i * ld + j];
+    part[(int64_t)blockIdx.x * k + j] = s;
+  }
+}
+
+__global__ void colsum_reduce(const double* part, int k, double* out) {
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < NPART; ++b) s += part[(int64_t)b * k + j];
+    out[j] = s;
+  }
+}
+
+void launch_colsum(const void* F, int64_t rows, int ld, int k, int fdt, double* part, double* out,
+                   cudaStream_t s) {
+  if (fdt == T_F64) colsum_partial<double><<<NPART, 128, 0, s>>>((const double*)F, rows, ld, k, part);
+  else colsum_partial<float><<<NPART, 128, 0, s>>>((const float*)F, rows, ld, k, part);
+  colsum_reduce<<<1, 128, 0, s>>>(part, k, out);
+}
+
+// sum over rows of || Y_i Wr - Q_i UrS ||^2 (r columns), in FP64.
+template <typename TF>
+__global__ void __launch_bounds__(RT_T)
+rr_residual_kernel(const TF* Y, int ldy, int ky, const TF* Q, int ldq, int kq, int64_t rows, int r,
+                   const double* __restrict__ Wr, const double* __restrict__ UrS, double* part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* W_s = reinterpret_cast<double*>(smraw);   // ky x r
+  double* U_s = W_s + ky * r;                       // kq x r
+  __shared__ double sh[RT_T];
+  for (int e = threadIdx.x; e < ky * r; e += RT_T) W_s[e] = Wr[e];
+  for (int e = threadIdx.x; e < kq * r; e += RT_T) U_s[e] = UrS[e];
+  __syncthreads();
+  const int64_t chunk = (rows + NPART - 1) / NPART;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+  double acc = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += RT_T) {
+    for (int j = 0; j < r; ++j) {
+      double a = 0.0, b = 0.0;
+      for (int l = 0; l < ky; ++l) a = fma((double)Y[i * ldy + l], W_s[l * r + j], a);
+      for (int l = 0; l < kq; ++l) b = fma((double)Q[i * ldq + l], U_s[l * r + j], b);
+      acc = fma(a - b, a - b, acc);
+    }
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+void launch_rr_residual(const void* Y, int ldy, int ky, const void* Q, int ldq, int kq,
+                        int64_t rows, int r, int fdt, const double* Wr, const double* UrS,
+                        double* part, double* out, cudaStream_t s) {
+  size_t smem = sizeof(double) * ((size_t)ky * r + (size_t)kq * r);
+  if (fdt == T_F64) {
+    cudaFuncSetAttribute(rr_residual_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rr_residual_kernel<double><<<NPART, RT_T, smem, s>>>((const double*)Y, ldy, ky, (const double*)Q, ldq, kq, rows, r, Wr, UrS, part);
+  } else {
+    cudaFuncSetAttribute(rr_residual_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rr_residual_kernel<float><<<NPART, RT_T, smem, s>>>((const float*)Y, ldy, ky, (const float*)Q, ldq, kq, rows, r, Wr, UrS, part);
+  }
+  part_sum_to<<<1, 32, 0, s>>>(part, NPART, out, 0);
+}
+
+// ------------------------------------------------------------- KKT rows
+// Per block: min F, min grad, max(grad * F), sum(grad * F), ||P(grad)||^2,
+// ||A||^2, ||F G||^2 with grad = F G - A (App. G).
+template <typename TF>
+__global__ void __launch_bounds__(RT_T)
+kkt_rows_kernel(const TF* __restrict__ F, const TF* __restrict__ A, const double* __restrict__ G,
+                int64_t rows, int k, double* part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* Gs = reinterpret_cast<double*>(smraw);
+  __shared__ double sh[RT_T];
+  for (int e = threadIdx.x; e < k * k; e += RT_T) Gs[e] = G[e];
+  __syncthreads();
+  const int64_t chunk = (rows + NPART - 1) / NPART;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+  double mnw = INFINITY, mng = INFINITY, mxp = -INFINITY, sp = 0.0, pg = 0.0, aa = 0.0, fg = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += RT_T) {
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < k; ++l) s = fma((double)F[i * k + l], Gs[l * k + j], s);
+      double a = (double)A[i * k + j], w = (double)F[i * k + j];
+      double gr = s - a;
+      mnw = fmin(mnw, w);
+      mng = fmin(mng, gr);
+      mxp = fmax(mxp, gr * w);
+      sp += gr * w;
+      double p = w > 0.0 ? gr : fmin(0.0, gr);
+      pg = fma(p, p, pg);
+      aa = fma(a, a, aa);
+      fg = fma(s, s, fg);
+    }
+  }
+  double* o = part + (int64_t)blockIdx.x * 8;
+  double v;
+  v = block_min(mnw, sh); if (threadIdx.x == 0) o[0] = v;
+  v = block_min(mng, sh); if (threadIdx.x == 0) o[1] = v;
+  v = block_max(mxp, sh); if (threadIdx.x == 0) o[2] = v;
+  v = block_sum(sp, sh);  if (threadIdx.x == 0) o[3] = v;
+  v = block_sum(pg, sh);  if (threadIdx.x == 0) o[4] = v;
+  v = block_sum(aa, sh);  if (threadIdx.x == 0) o[5] = v;
+  v = block_sum(fg, sh);  if (threadIdx.x == 0) o[6] = v;
+}
+
+__global__ void kkt_reduce(const double* part, double* out) {
+  if (threadIdx.x != 0) return;
+  double o[7] = {INFINITY, INFINITY, -INFINITY, 0, 0, 0, 0};
+  for (int b = 0; b < NPART; ++b) {
+    const double* p = part + b * 8;
+    o[0] = fmin(o[0], p[0]);
+    o[1] = fmin(o[1], p[1]);
+    o[2] = fmax(o[2], p[2]);
+    for (int q = 3; q < 7; ++q) o[q] += p[q];
+  }
+  for (int q = 0; q < 7; ++q) out[q] = o[q];
+}
+
+void launch_kkt_rows(const void* F, const void* A, const double* G, int64_t rows, int k, int fdt,
+                     double* part, double* out, cudaStream_t s) {
+  size_t smem = sizeof(double) * (size_t)k * k;
+  if (fdt == T_F64)
+    kkt_rows_kernel<double><<<NPART, RT_T, smem, s>>>((const double*)F, (const double*)A, G, rows, k, part);
+  else
+    kkt_rows_kernel<float><<<NPART, RT_T, smem, s>>>((const float*)F, (const float*)A, G, rows, k, part);
+  kkt_reduce<<<1, 32, 0, s>>>(part, out);
+}
+
+__global__ void kkt_final_kernel(const double* pu, const double* pv, double* out) {
+  // out: min_w, min_grad, delta, sigma, pg_norm, pg_rel
+  out[0] = fmin(pu[0], pv[0]);
+  out[1] = fmin(pu[1], pv[1]);
+  out[2] = fmax(pu[2], pv[2]);
+  out[3] = pu[3] + pv[3];
+  double pg = sqrt(pu[4] + pv[4]);
+  double scale = sqrt(pu[5]) + sqrt(pu[6]) + sqrt(pv[5]) + sqrt(pv[6]);
+  out[4] = pg;
+  out[5] = scale > 0.0 ? pg / scale : 0.0;
+}
+
+void launch_kkt_final(const double* pu, const double* pv, double* out, cudaStream_t s) {
+  kkt_final_kernel<<<1, 1, 0, s>>>(pu, pv, out);
+}
+
+}  // namespace enmf

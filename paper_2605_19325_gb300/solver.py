@@ -1,0 +1,103 @@
+"""Python convenience layer over the C ABI: one Solver per (X, r) problem.
+
+Only marshalling: tensors are allocated with PyTorch on the current CUDA
+device and their pointers handed to libenmf.  All arithmetic happens in the
+library's CUDA kernels.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import binding as B
+
+_XDT = {torch.float64: B.ENMF_F64, torch.float32: B.ENMF_F32, torch.bfloat16: B.ENMF_BF16,
+        torch.float16: B.ENMF_F16}
+
+
+def problem_for(X, r, f_dtype=None):
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a row-major matrix (unit column stride)")
+    xdt = _XDT.get(X.dtype)
+    if xdt is None:
+        raise ValueError(f"unsupported X dtype {X.dtype}")
+    if f_dtype is None:
+        f_dtype = torch.float64 if X.dtype == torch.float64 else torch.float32
+    fdt = B.ENMF_F64 if f_dtype == torch.float64 else B.ENMF_F32
+    return B.enmf_problem(X.shape[0], X.shape[1], X.stride(0), r, xdt, fdt), f_dtype
+
+
+@dataclass
+class SolveResult:
+    U: torch.Tensor
+    V: torch.Tensor
+    sigma: torch.Tensor
+    R: torch.Tensor
+    trace: torch.Tensor
+    svd: object
+    rot: object
+    it: object
+
+
+class Solver:
+    """eNMF on one matrix: svd_init -> rotate -> iterate (Algorithm 3)."""
+
+    def __init__(self, X: torch.Tensor, r: int, f_dtype=None, stream=None):
+        if not X.is_cuda:
+            raise ValueError("X must be a CUDA tensor")
+        self.X = X
+        self.r = r
+        self.problem, self.f_dtype = problem_for(X, r, f_dtype)
+        self.stream = stream
+        self.ctx = B.enmf_create(self.problem, stream)
+        dev = X.device
+        self.U = torch.zeros(X.shape[0], r, dtype=self.f_dtype, device=dev)
+        self.V = torch.zeros(X.shape[1], r, dtype=self.f_dtype, device=dev)
+        self.sigma = torch.zeros(r, dtype=torch.float64, device=dev)
+        self.R = torch.zeros(r, r, dtype=torch.float64, device=dev)
+
+    def close(self):
+        if self.ctx is not None:
+            B.enmf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def svd_init(self, opts=None):
+        info, code = B.enmf_svd_init(self.ctx, self.X, self.U, self.V, self.sigma, opts)
+        return info
+
+    def rotate(self, opts=None):
+        info, code = B.enmf_rotate(self.ctx, self.U, self.V, self.R, opts)
+        return info
+
+    def iterate(self, n_iter, trace=True, reset=0, **kw):
+        tr = torch.zeros(max(n_iter, 1), dtype=torch.float64, device=self.X.device) if trace else None
+        info = B.enmf_iterate(self.ctx, self.X, self.U, self.V, n_iter, trace=tr, reset=reset, **kw)
+        return (tr[:n_iter] if trace else None), info
+
+    def residual(self, direct=True):
+        return B.enmf_residual(self.ctx, self.X, self.U, self.V, 1 if direct else 0)
+
+    def kkt(self):
+        return B.enmf_kkt(self.ctx, self.X, self.U, self.V)
+
+    def pbcd_counts(self):
+        return B.enmf_pbcd_counts(self.ctx)
+
+
+def solve(X: torch.Tensor, r: int, n_iter: int, f_dtype=None) -> SolveResult:
+    """Algorithm 3 end to end on the GPU."""
+    s = Solver(X, r, f_dtype)
+    try:
+        si = s.svd_init()
+        ri = s.rotate()
+        tr, ii = s.iterate(n_iter, reset=1)
+        return SolveResult(s.U, s.V, s.sigma, s.R, tr, si, ri, ii)
+    finally:
+        s.close()

@@ -1,0 +1,69 @@
+"""The C ABI library builds, loads and exports every entry point of include/*.h.
+
+CPU only: nvcc cross-compiles for sm_103a without a GPU and the library loads
+without touching a device.  No compute call is made here.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2605_19325_gb300 import build
+    return build.build()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(enmf_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_five_calls():
+    names = declared_functions()
+    for f in ("enmf_svd_init", "enmf_rotate", "enmf_iterate", "enmf_residual", "enmf_kkt"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(libpath):
+    from paper_2605_19325_gb300 import binding
+    assert set(declared_functions()) <= set(binding.EXPORTED)
+    lib = binding.load(libpath)
+    assert lib.enmf_version().decode().startswith("enmf")
+
+
+def test_status_strings_and_invalid_arguments(libpath):
+    """Argument checks run before any device work, so they work without a GPU."""
+    from paper_2605_19325_gb300 import binding as B
+    lib = B.load(libpath)
+    assert lib.enmf_status_string(0) == b"ok"
+    assert b"invalid" in lib.enmf_status_string(1)
+    bad = [B.enmf_problem(0, 5, 5, 1, B.ENMF_F64, B.ENMF_F64),      # m = 0
+           B.enmf_problem(5, 5, 4, 1, B.ENMF_F64, B.ENMF_F64),      # ldx < n
+           B.enmf_problem(5, 5, 5, 6, B.ENMF_F64, B.ENMF_F64),      # r > min(m, n)
+           B.enmf_problem(500, 500, 500, 65, B.ENMF_F64, B.ENMF_F64),  # r > max rank
+           B.enmf_problem(5, 5, 5, 2, B.ENMF_F32, B.ENMF_F64)]      # FP64 factors need FP64 X
+    for p in bad:
+        size = ctypes.c_size_t(0)
+        assert lib.enmf_workspace_size(ctypes.byref(p), ctypes.byref(size)) == 1
+        h = ctypes.c_void_p()
+        assert lib.enmf_create(ctypes.byref(p), None, ctypes.byref(h)) == 1
+    # null context
+    assert lib.enmf_iterate(None, None, None, None, None, None) == 1
