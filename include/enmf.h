@@ -203,6 +203,20 @@ enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V, int32_t n
                        const enmf_svd_opts* svd, const enmf_admm_opts* admm,
                        const enmf_iter_opts* iter, double* out3);
 
+/* ---- Measurement (no counterpart in the paper) ---------------------------
+ * enmf_profile: every > 0 records CUDA events around the X V and X^T U sweeps
+ * of every `every`-th alternation in enmf_iterate (on the context stream, up
+ * to 128 alternations per call); 0 turns it off.  enmf_profile_read returns
+ * the summed sweep time (ms) and the number of timed sweeps, optionally
+ * resetting them; it synchronises the stream.
+ * enmf_probe_fma_peak: measured FMA throughput (flop/s) of the current device
+ * for ENMF_F64 or ENMF_F32 (a throughput kernel timed with CUDA events).
+ * enmf_launch_count: kernel launches issued by the library since load. */
+enmf_status enmf_profile(enmf_ctx* ctx, int32_t every);
+enmf_status enmf_profile_read(enmf_ctx* ctx, double* sweep_ms, int64_t* sweeps, int32_t reset);
+enmf_status enmf_probe_fma_peak(int32_t dtype, double* flops_per_s);
+long long enmf_launch_count(void);
+
 /* Library version string. */
 const char* enmf_version(void);
 

@@ -86,6 +86,11 @@ _SIGS = {
     "enmf_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                              C.POINTER(enmf_svd_opts), C.POINTER(enmf_admm_opts),
                              C.POINTER(enmf_iter_opts), C.POINTER(C.c_double)]),
+    "enmf_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "enmf_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                    C.c_int32]),
+    "enmf_probe_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
+    "enmf_launch_count": (C.c_longlong, []),
     "enmf_version": (C.c_char_p, []),
 }
 
@@ -191,6 +196,27 @@ def enmf_kkt(ctx, X, U, V):
     rep = enmf_kkt_report()
     check(lib().enmf_kkt(ctx, _ptr(X), _ptr(U), _ptr(V), C.byref(rep)), "enmf_kkt")
     return rep
+
+
+def enmf_profile(ctx, every):
+    check(lib().enmf_profile(ctx, every), "enmf_profile")
+
+
+def enmf_profile_read(ctx, reset=1):
+    ms = C.c_double(0)
+    n = C.c_int64(0)
+    check(lib().enmf_profile_read(ctx, C.byref(ms), C.byref(n), reset), "enmf_profile_read")
+    return ms.value, n.value
+
+
+def enmf_probe_fma_peak(dtype):
+    out = C.c_double(0)
+    check(lib().enmf_probe_fma_peak(dtype, C.byref(out)), "enmf_probe_fma_peak")
+    return out.value
+
+
+def enmf_launch_count():
+    return int(lib().enmf_launch_count())
 
 
 def enmf_solve(ctx, X_ptr, U_ptr, V_ptr, n_iter):

@@ -46,7 +46,32 @@ struct enmf_ctx {
   // host-data staging for enmf_solve
   void* hX; void* hU; void* hV;
   size_t hX_bytes;
+  // event timing of the X sweeps (enmf_profile)
+  int prof_every;
+  int npev;
+  cudaEvent_t pev[2 * 256];
+  double prof_ms;
+  long long prof_n;
 };
+
+constexpr int PROF_PAIRS = 256;
+
+// Accumulate the recorded (start, stop) event pairs into the sweep totals.
+static enmf_status prof_harvest(enmf_ctx* ctx) {
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    ctx->poison = ENMF_ECUDA;
+    return ENMF_ECUDA;
+  }
+  for (int i = 0; i + 1 < ctx->npev; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->pev[i], ctx->pev[i + 1]) == cudaSuccess) {
+      ctx->prof_ms += ms;
+      ctx->prof_n += 1;
+    }
+  }
+  ctx->npev = 0;
+  return ENMF_OK;
+}
 
 static const char* kStatus[] = {"ok", "invalid argument", "X has a negative or non-finite entry",
                                 "out of device memory", "CUDA error", "device wait timed out",
@@ -232,6 +257,8 @@ extern "C" void enmf_destroy(enmf_ctx* ctx) {
   if (ctx->hX) cudaFree(ctx->hX);
   if (ctx->hU) cudaFree(ctx->hU);
   if (ctx->hV) cudaFree(ctx->hV);
+  if (ctx->prof_every >= 0 && ctx->pev[0])
+    for (int i = 0; i < 2 * PROF_PAIRS; ++i) cudaEventDestroy(ctx->pev[i]);
   delete ctx;
 }
 
@@ -342,8 +369,12 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
 }
 
 // ------------------------------------------------------------- 2. rotation
-__global__ void rot_start_kernel(double* R, int k, DevState* st) {
+// R0 = I and the polar kernel's warm-start basis D = I (Np x Np, Np = k
+// rounded up to even).
+__global__ void rot_start_kernel(double* R, double* D, int k, DevState* st) {
+  const int Np = k + (k & 1);
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) R[e] = (e / k == e % k) ? 1.0 : 0.0;
+  for (int e = threadIdx.x; e < Np * Np; e += blockDim.x) D[e] = (e / Np == e % Np) ? 1.0 : 0.0;
   if (threadIdx.x == 0) {
     st->admm_done = 0;
     st->admm_steps = 0;
@@ -379,14 +410,15 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
     rho = rms > 0 ? o.rho_scale / rms : 1.0;
   }
   CK(cudaMemsetAsync(ctx->Yb, 0, (size_t)(m + n) * k * type_size(fdt), s));
-  rot_start_kernel<<<1, 256, 0, s>>>(ctx->R, k, ctx->st);
+  rot_start_kernel<<<1, 256, 0, s>>>(ctx->R, ctx->T2, k, ctx->st);
+  note_launch(1);
   int steps_launched = 0;
   const int check_every = 16;
   for (int it = 0; it < o.max_iter; ++it) {
     launch_admm_pass(U, V, m, n, k, fdt, ctx->R, ctx->Zb, ctx->Yb, rho, it == 0, ctx->st,
                      ctx->part, s);
     launch_part_reduce(ctx->part, k * k, ctx->Msm, s);   // M = W^T B, fixed order
-    launch_polar(ctx->Msm, k, ctx->R, nullptr, o.tol, ctx->st, ctx->err, s);
+    launch_polar(ctx->Msm, k, ctx->R, ctx->T2, o.tol, ctx->st, ctx->err, s);
     ++steps_launched;
     if ((it + 1) % check_every == 0 && it + 1 < o.max_iter) {
       rc = check_launch(ctx);
@@ -471,16 +503,26 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
   launch_gram(V, k, k, V, k, k, n, fdt, ctx->part, ctx->Gv, s);
   const int ndot = half_grid(ctx, n, ctx->grid_v);
   for (int it = 0; it < o.n_iter; ++it) {
+    const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 &&
+                     ctx->npev + 4 <= 2 * PROF_PAIRS;
+    if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
     launch_xv(X, xdt, m, n, p.ldx, V, k, k, ctx->M0, k, fdt, ctx->splitk, ctx->num_sms, s);
+    if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
     run_half(ctx, 0, U, ctx->M0, ctx->Gv, m, o, false);
     launch_gram(U, k, k, U, k, k, m, fdt, ctx->part, ctx->Gu, s);
+    if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
     launch_xtu(X, xdt, m, n, p.ldx, U, k, k, ctx->N0, k, fdt, ctx->splitk, ctx->num_sms, s);
+    if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
     run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true);
     launch_gram(V, k, k, V, k, k, n, fdt, ctx->part, ctx->Gv, s);
     launch_iter_finalize(ctx->st, ctx->dot_part, ndot, ctx->Gu, ctx->Gv, k, o.trace, it, s);
   }
   enmf_status rc = check_launch(ctx);
   if (rc) return rc;
+  if (ctx->npev > 0) {
+    rc = prof_harvest(ctx);
+    if (rc) return rc;
+  }
   if (o.sync_info || info) {
     DevState hst;
     CK(cudaMemcpyAsync(&hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -494,6 +536,35 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
       info->s_v = hst.s_v;
     }
     return rc;
+  }
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_profile(enmf_ctx* ctx, int32_t every) {
+  GUARD(ctx);
+  if (every < 0) return ENMF_EINVAL;
+  if (every > 0 && !ctx->pev[0]) {
+    for (int i = 0; i < 2 * PROF_PAIRS; ++i)
+      if (cudaEventCreate(&ctx->pev[i]) != cudaSuccess) return ENMF_ECUDA;
+  }
+  ctx->prof_every = every;
+  ctx->npev = 0;
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_profile_read(enmf_ctx* ctx, double* sweep_ms, int64_t* sweeps,
+                                         int32_t reset) {
+  GUARD(ctx);
+  if (!sweep_ms || !sweeps) return ENMF_EINVAL;
+  if (ctx->npev > 0) {
+    enmf_status rc = prof_harvest(ctx);
+    if (rc) return rc;
+  }
+  *sweep_ms = ctx->prof_ms;
+  *sweeps = ctx->prof_n;
+  if (reset) {
+    ctx->prof_ms = 0.0;
+    ctx->prof_n = 0;
   }
   return ENMF_OK;
 }

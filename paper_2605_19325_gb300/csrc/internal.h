@@ -27,7 +27,7 @@ struct DevState {
   int admm_done;
   int admm_steps;
   int svd_rank;
-  int pad_;
+  int jac_sweeps;      // Jacobi sweeps of the last polar update (diagnostic)
   double s_u, s_v;            // shift steps of Eq. 8 / 9
   double maxneg_u, maxneg_v;  // max(-U), max(-V) when the stage started
   double normX2;              // ||X||_F^2
@@ -42,6 +42,9 @@ struct DevState {
 // Number of fixed-order partial sums used by the reduction kernels.  It does
 // not depend on the device, so results are reproducible across GPUs.
 constexpr int NPART = 256;
+
+// Host-side count of kernel launches (measurement only).
+void note_launch(int n);
 
 // Split-K choice for the SIMT sweeps (also used to size the workspace).
 int choose_splits(int64_t rows_out, int64_t red_len, int k, int bm, int num_sms);
@@ -123,7 +126,7 @@ void launch_kkt_rows(const void* F, const void* A, const double* G, int64_t rows
 
 // ---------------------------------------------------------------- small.cu
 // R_new = polar(sum of NPART partial M's); dR, convergence, ADMM step count.
-void launch_polar(const double* part, int k, double* R, double* R_prev, double tol,
+void launch_polar(const double* M, int k, double* R, double* D, double tol,
                   DevState* st, int* err, cudaStream_t s);
 // Orthonormalising transform of a Gram G (k x k): eigen-decomposition by
 // one-sided Jacobi, keep eigenvalues > tau * lambda_1, T = V_k diag(l^-1/2).

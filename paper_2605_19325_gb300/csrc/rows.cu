@@ -190,6 +190,7 @@ int half_step_grid(int fdt, int k, int num_sms) {
 }
 
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s) {
+  note_launch(1);
   int64_t need = (a.rows + HS_T - 1) / HS_T;
   if ((int64_t)grid > need) grid = (int)need;
   if (grid < 1) grid = 1;
@@ -233,6 +234,7 @@ __global__ void state_start_kernel(DevState* st, int n_shift) {
 void launch_state_init(const void* U, const void* V, int64_t m, int64_t n, int k, int fdt,
                        int n_shift, DevState* st, double* part, cudaStream_t s) {
   (void)part;
+  note_launch(4);
   state_reset_kernel<<<1, 1, 0, s>>>(st);
   int bu = (int)min((int64_t)1024, (m * k + 255) / 256);
   int bv = (int)min((int64_t)1024, (n * k + 255) / 256);
@@ -270,6 +272,7 @@ __global__ void iter_finalize_kernel(DevState* st, const double* dot_part, int n
 
 void launch_iter_finalize(DevState* st, const double* dot_part, int ndot, const double* Gu,
                           const double* Gv, int k, double* trace, int trace_idx, cudaStream_t s) {
+  note_launch(1);
   iter_finalize_kernel<<<1, 256, 0, s>>>(st, dot_part, ndot, Gu, Gv, k, trace, trace_idx);
 }
 
@@ -294,9 +297,11 @@ admm_pass_kernel(const TF* __restrict__ U, const TF* __restrict__ V, int64_t m, 
   const TF thr = TF(-1) / rho;
   const int64_t rows = m + n;
   const int t = threadIdx.x;
-  double acc[AP_PER_T];
+  // W^T B is summed in TF within the block (the pass runs in the form's
+  // precision) and in FP64 across blocks.
+  TF acc[AP_PER_T];
 #pragma unroll
-  for (int q = 0; q < AP_PER_T; ++q) acc[q] = 0.0;
+  for (int q = 0; q < AP_PER_T; ++q) acc[q] = TF(0);
   double negm = 0.0;
   for (int64_t t0 = (int64_t)blockIdx.x * AP_T; t0 < rows; t0 += (int64_t)gridDim.x * AP_T) {
     __syncthreads();
@@ -329,9 +334,8 @@ admm_pass_kernel(const TF* __restrict__ U, const TF* __restrict__ V, int64_t m, 
       int e = t + q * AP_T;
       if (e < k * k) {
         int a = e / k, b = e % k;
-        double sacc = acc[q];
-        for (int rr = 0; rr < AP_T; ++rr)
-          sacc = fma((double)Ws[a * AP_S + rr], (double)Bs[b * AP_S + rr], sacc);
+        TF sacc = acc[q];
+        for (int rr = 0; rr < AP_T; ++rr) sacc = fma(Ws[a * AP_S + rr], Bs[b * AP_S + rr], sacc);
         acc[q] = sacc;
       }
     }
@@ -339,7 +343,7 @@ admm_pass_kernel(const TF* __restrict__ U, const TF* __restrict__ V, int64_t m, 
 #pragma unroll
   for (int q = 0; q < AP_PER_T; ++q) {
     int e = t + q * AP_T;
-    if (e < k * k) part[(int64_t)blockIdx.x * k * k + e] = acc[q];
+    if (e < k * k) part[(int64_t)blockIdx.x * k * k + e] = (double)acc[q];
   }
   negm = block_sum(negm, sh);
   if (t == 0) part[(int64_t)NPART * k * k + blockIdx.x] = negm;
@@ -348,6 +352,7 @@ admm_pass_kernel(const TF* __restrict__ U, const TF* __restrict__ V, int64_t m, 
 void launch_admm_pass(const void* U, const void* V, int64_t m, int64_t n, int k, int fdt,
                       const double* R, void* Z, void* Y, double rho, int first, DevState* st,
                       double* part, cudaStream_t s) {
+  note_launch(1);
   size_t smem = type_size(fdt) * ((size_t)k * k + 2 * (size_t)k * AP_S);
   if (fdt == T_F64) {
     cudaFuncSetAttribute(admm_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -385,6 +390,7 @@ row_transform_kernel(const TF* in, int ld_in, int k_in, TF* out, int ld_out, int
 
 void launch_row_transform(const void* in, int ld_in, int k_in, void* out, int ld_out, int k_out,
                           int64_t rows, int fdt, const double* T, cudaStream_t s) {
+  note_launch(1);
   size_t smem = type_size(fdt) * ((size_t)k_in * k_out + (size_t)k_in * RT_T);
   int blocks = (int)min((int64_t)1024, (rows + RT_T - 1) / RT_T);
   if (blocks < 1) blocks = 1;
@@ -430,6 +436,7 @@ __global__ void part_sum_to(const double* part, int count, double* out, int accu
 
 void launch_negmass(const void* F, int64_t rows, int k, int fdt, double* part, double* out,
                     int accumulate, cudaStream_t s) {
+  note_launch(2);
   if (fdt == T_F64) negmass_partial<double><<<NPART, 256, 0, s>>>((const double*)F, rows * k, part);
   else negmass_partial<float><<<NPART, 256, 0, s>>>((const float*)F, rows * k, part);
   part_sum_to<<<1, 32, 0, s>>>(part, NPART, out, accumulate);
@@ -456,6 +463,7 @@ __global__ void colsum_reduce(const double* part, int k, double* out) {
 
 void launch_colsum(const void* F, int64_t rows, int ld, int k, int fdt, double* part, double* out,
                    cudaStream_t s) {
+  note_launch(2);
   if (fdt == T_F64) colsum_partial<double><<<NPART, 128, 0, s>>>((const double*)F, rows, ld, k, part);
   else colsum_partial<float><<<NPART, 128, 0, s>>>((const float*)F, rows, ld, k, part);
   colsum_reduce<<<1, 128, 0, s>>>(part, k, out);
@@ -491,6 +499,7 @@ rr_residual_kernel(const TF* Y, int ldy, int ky, const TF* Q, int ldq, int kq, i
 void launch_rr_residual(const void* Y, int ldy, int ky, const void* Q, int ldq, int kq,
                         int64_t rows, int r, int fdt, const double* Wr, const double* UrS,
                         double* part, double* out, cudaStream_t s) {
+  note_launch(2);
   size_t smem = sizeof(double) * ((size_t)ky * r + (size_t)kq * r);
   if (fdt == T_F64) {
     cudaFuncSetAttribute(rr_residual_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -559,6 +568,7 @@ __global__ void kkt_reduce(const double* part, double* out) {
 
 void launch_kkt_rows(const void* F, const void* A, const double* G, int64_t rows, int k, int fdt,
                      double* part, double* out, cudaStream_t s) {
+  note_launch(2);
   size_t smem = sizeof(double) * (size_t)k * k;
   if (fdt == T_F64)
     kkt_rows_kernel<double><<<NPART, RT_T, smem, s>>>((const double*)F, (const double*)A, G, rows, k, part);
@@ -580,6 +590,7 @@ __global__ void kkt_final_kernel(const double* pu, const double* pv, double* out
 }
 
 void launch_kkt_final(const double* pu, const double* pv, double* out, cudaStream_t s) {
+  note_launch(1);
   kkt_final_kernel<<<1, 1, 0, s>>>(pu, pv, out);
 }
 

@@ -15,7 +15,7 @@
 
 namespace enmf {
 
-constexpr int SM_T = 256;
+constexpr int SM_T = 1024;   // one warp per column pair of a round (up to 32 pairs)
 constexpr int SM_WARPS = SM_T / 32;
 constexpr int JAC_MAX_SWEEPS = 40;
 
@@ -24,52 +24,95 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Column pair of slot pi in round rnd of the round-robin (circle) ordering:
+// every pair of the Np columns meets once per sweep, and the pairs of a round
+// are disjoint.
+__device__ __forceinline__ void rr_pair(int pi, int rnd, int Np, int& p, int& q) {
+  p = pi == 0 ? 0 : 1 + (pi - 1 + rnd) % (Np - 1);
+  q = 1 + (Np - 2 - pi + rnd) % (Np - 1);
+  if (p > q) { int t = p; p = q; q = t; }
+}
+
 // Column-major A (rows x Np) and V (Np x Np) in shared memory, Np even (a
-// padding column is zero).  Returns the number of sweeps (JAC_MAX_SWEEPS+1 if
-// it did not converge).
+// padding column is zero), rows <= LMAX, Np <= LMAX.  Returns the number of
+// sweeps run (JAC_MAX_SWEEPS if it did not converge).
+//
+// FP64 issue rate is the limit on this GPU, so each round keeps the FP64
+// instruction count low: lanes form partial products of their rows, one
+// thread per (pair, quantity) sums the 32 partials in lane order, one thread
+// per pair computes the rotation, then one warp per pair applies it.
 __device__ int jacobi_osvd(double* A, int rows, int Np, double* V) {
   __shared__ int rotated;
+  __shared__ double part[LMAX / 2][3][33];
+  __shared__ double rot[LMAX / 2][2];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int npairs = Np / 2;
   const double tol = 1e-15 * (double)(rows > 8 ? rows : 8);
   int sweep = 0;
   for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
-    __syncthreads();
     for (int rnd = 0; rnd < Np - 1; ++rnd) {
-      for (int pi = warp; pi < Np / 2; pi += SM_WARPS) {
-        int p = pi == 0 ? 0 : 1 + (pi - 1 + rnd) % (Np - 1);
-        int qj = Np - 1 - pi;
-        int q = 1 + (qj - 1 + rnd) % (Np - 1);
-        if (p > q) { int tmp = p; p = q; q = tmp; }
-        double* ap = A + (size_t)p * rows;
-        double* aq = A + (size_t)q * rows;
+      // partial products: lane l takes rows l, l + 32, ...
+      for (int pi = warp; pi < npairs; pi += SM_WARPS) {
+        int p, q;
+        rr_pair(pi, rnd, Np, p, q);
+        const double* ap = A + (size_t)p * rows;
+        const double* aq = A + (size_t)q * rows;
         double al = 0.0, be = 0.0, ga = 0.0;
         for (int i = lane; i < rows; i += 32) {
-          al = fma(ap[i], ap[i], al);
-          be = fma(aq[i], aq[i], be);
-          ga = fma(ap[i], aq[i], ga);
+          const double x = ap[i], y = aq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
+        part[pi][0][lane] = al;
+        part[pi][1][lane] = be;
+        part[pi][2][lane] = ga;
+      }
+      __syncthreads();
+      // one thread per (pair, quantity): fixed lane-order sum
+      for (int t = threadIdx.x; t < 3 * npairs; t += SM_T) {
+        const int pi = t / 3, qq = t % 3;
+        double s = 0.0;
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) s += part[pi][qq][l];
+        part[pi][qq][32] = s;
+      }
+      __syncthreads();
+      // one thread per pair: the rotation (c, s), or (1, 0) when the pair is
+      // already orthogonal to working precision
+      for (int pi = threadIdx.x; pi < npairs; pi += SM_T) {
+        const double al = part[pi][0][32], be = part[pi][1][32], ga = part[pi][2][32];
+        double c = 1.0, s = 0.0;
         if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
-          double z = (be - al) / (2.0 * ga);
-          double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
-          double c = 1.0 / sqrt(1.0 + t * t);
-          double s = c * t;
-          for (int i = lane; i < rows; i += 32) {
-            double x = ap[i], y = aq[i];
-            ap[i] = c * x - s * y;
-            aq[i] = s * x + c * y;
-          }
-          double* vp = V + (size_t)p * Np;
-          double* vq = V + (size_t)q * Np;
-          for (int i = lane; i < Np; i += 32) {
-            double x = vp[i], y = vq[i];
-            vp[i] = c * x - s * y;
-            vq[i] = s * x + c * y;
-          }
-          if (lane == 0) rotated = 1;
+          const double z = (be - al) / (2.0 * ga);
+          const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = c * t;
+          rotated = 1;
+        }
+        rot[pi][0] = c;
+        rot[pi][1] = s;
+      }
+      __syncthreads();
+      for (int pi = warp; pi < npairs; pi += SM_WARPS) {
+        const double c = rot[pi][0], s = rot[pi][1];
+        if (s == 0.0) continue;
+        int p, q;
+        rr_pair(pi, rnd, Np, p, q);
+        double* ap = A + (size_t)p * rows;
+        double* aq = A + (size_t)q * rows;
+        for (int i = lane; i < rows; i += 32) {
+          const double x = ap[i], y = aq[i];
+          ap[i] = c * x - s * y;
+          aq[i] = s * x + c * y;
+        }
+        double* vp = V + (size_t)p * Np;
+        double* vq = V + (size_t)q * Np;
+        for (int i = lane; i < Np; i += 32) {
+          const double x = vp[i], y = vq[i];
+          vp[i] = c * x - s * y;
+          vq[i] = s * x + c * y;
         }
       }
       __syncthreads();
@@ -105,8 +148,13 @@ __device__ void set_identity(double* V, int Np) {
 // M (k x k row-major) -> R = C D^T with M = C S D^T.  With the one-sided
 // Jacobi on the columns of M: M V = A (orthogonal columns), so C = A S^-1 and
 // D = V, R = sum_c (a_c / s_c) v_c^T.
+// Warm start: successive ADMM steps change M little, so the rotation starts
+// from the previous step's right singular vectors D (Np x Np column-major,
+// identity at the first step): A = M D is already nearly column-orthogonal and
+// the sweeps converge in a few passes.  D is updated in place.
 __global__ void __launch_bounds__(SM_T)
-polar_kernel(const double* __restrict__ Mg, int k, double* R, double tol, DevState* st, int* err) {
+polar_kernel(const double* __restrict__ Mg, int k, double* R, double* D, double tol, DevState* st,
+             int* err) {
   extern __shared__ double smd[];
   __shared__ double red[SM_T];
   if (*(volatile int*)&st->admm_done) return;
@@ -115,22 +163,40 @@ polar_kernel(const double* __restrict__ Mg, int k, double* R, double tol, DevSta
   double* V = A + (size_t)Np * k;  // Np x Np
   double* nrm = V + (size_t)Np * Np;
   double* Rn = nrm + Np;           // k x k
-  int* ord = reinterpret_cast<int*>(Rn + (size_t)k * k);
+  double* Ms = Rn + (size_t)k * k; // k x k
+  for (int e = threadIdx.x; e < k * k; e += SM_T) Ms[e] = Mg[e];
+  for (int e = threadIdx.x; e < Np * Np; e += SM_T) V[e] = D[e];
+  __syncthreads();
   for (int e = threadIdx.x; e < Np * k; e += SM_T) {
-    int c = e / k, i = e % k;
-    A[e] = c < k ? Mg[i * k + c] : 0.0;   // column c of M
+    int c = e / k, i = e % k;      // A_ic = sum_j M_ij V_jc (padding row/column of V is e_k)
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s = fma(Ms[i * k + j], V[(size_t)c * Np + j], s);
+    A[e] = s;
   }
-  set_identity(V, Np);
   __syncthreads();
   int sw = jacobi_osvd(A, k, Np, V);
-  sort_desc(A, k, Np, nrm, ord);
-  // R_ij = sum_c A_ic V_jc / s_c over c < k (singular values of M)
-  double smin = nrm[ord[k - 1]];
+  for (int c = threadIdx.x; c < Np; c += SM_T) {
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s = fma(A[(size_t)c * k + i], A[(size_t)c * k + i], s);
+    nrm[c] = sqrt(s);
+  }
+  for (int e = threadIdx.x; e < Np * Np; e += SM_T) D[e] = V[e];
+  __syncthreads();
+  // R_ij = sum_c A_ic V_jc / s_c over the k singular values of M (the
+  // padding column, if any, has s = 0 and is skipped)
+  double smin = INFINITY;
+  for (int c = 0; c < Np; ++c)
+    if (!(k & 1) || c != k) smin = fmin(smin, nrm[c]);
+  for (int e = threadIdx.x; e < Np * k; e += SM_T) {   // C = A S^-1, one division per column
+    const int c = e / k;
+    const double inv = nrm[c] > 0.0 ? 1.0 / nrm[c] : 0.0;
+    A[e] *= inv;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < k * k; e += SM_T) {
     int i = e / k, j = e % k;
     double s = 0.0;
-    for (int c = 0; c < Np; ++c)
-      if (nrm[c] > 0.0) s = fma(A[(size_t)c * k + i] / nrm[c], V[(size_t)c * Np + j], s);
+    for (int c = 0; c < Np; ++c) s = fma(A[(size_t)c * k + i], V[(size_t)c * Np + j], s);
     Rn[e] = s;
   }
   __syncthreads();
@@ -145,6 +211,7 @@ polar_kernel(const double* __restrict__ Mg, int k, double* R, double tol, DevSta
     double dR = sqrt(d);
     st->dR = dR;
     st->admm_steps += 1;
+    st->jac_sweeps = sw;
     if (sw > JAC_MAX_SWEEPS - 1 || !(smin > 0.0)) atomicOr(err, ERR_NOTCONV);
     if (dR <= tol * sqrt((double)k)) st->admm_done = 1;
   }
@@ -155,13 +222,13 @@ static size_t small_smem(int rows, int Np) {
          sizeof(int) * Np + 64;
 }
 
-void launch_polar(const double* M, int k, double* R, double* R_prev, double tol, DevState* st,
+void launch_polar(const double* M, int k, double* R, double* D, double tol, DevState* st,
                   int* err, cudaStream_t s) {
-  (void)R_prev;
+  note_launch(1);
   int Np = k + (k & 1);
-  size_t smem = small_smem(k, Np);
+  size_t smem = sizeof(double) * ((size_t)Np * k + (size_t)Np * Np + Np + 2 * (size_t)k * k) + 64;
   cudaFuncSetAttribute(polar_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  polar_kernel<<<1, SM_T, smem, s>>>(M, k, R, tol, st, err);
+  polar_kernel<<<1, SM_T, smem, s>>>(M, k, R, D, tol, st, err);
 }
 
 // ------------------------------------------------------ Gram -> orth map
@@ -203,6 +270,7 @@ eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, int*
 
 void launch_eig_orth(const double* G, int k, double tau, double* T, int* kept, int* err,
                      cudaStream_t s) {
+  note_launch(1);
   int Np = k + (k & 1);
   size_t smem = small_smem(k, Np);
   cudaFuncSetAttribute(eig_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -245,6 +313,7 @@ rr_svd_kernel(const double* __restrict__ P, int k2, int k1, double* sigma, doubl
 
 void launch_rr_svd(const double* P, int k2, int k1, double* sigma, double* Ut, double* Wt,
                    int* err, cudaStream_t s) {
+  note_launch(1);
   int Np = k2 + (k2 & 1);
   size_t smem = small_smem(k1 > Np ? k1 : Np, Np);
   cudaFuncSetAttribute(rr_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -262,6 +331,7 @@ __global__ void rr_prep_kernel(const double* sigma, const double* Ut, const doub
 
 void launch_rr_prep(const double* sigma, const double* Ut, const double* Wt, int k1, int k2,
                     int r, double* Wr, double* UrS, DevState* st, cudaStream_t s) {
+  note_launch(1);
   rr_prep_kernel<<<1, 256, 0, s>>>(sigma, Ut, Wt, k1, k2, r, Wr, UrS, st);
 }
 
@@ -294,6 +364,7 @@ __global__ void svd_finish_kernel(const double* sigma, const double* Ut, const d
 void launch_svd_finish(const double* sigma, const double* Ut, const double* Wt, int k1, int k2,
                        int r, const double* colsumQ, const double* colsumQ2, double* Tu,
                        double* Tv, double* sigma_out, cudaStream_t s) {
+  note_launch(1);
   svd_finish_kernel<<<1, 256, 0, s>>>(sigma, Ut, Wt, k1, k2, r, colsumQ, colsumQ2, Tu, Tv,
                                       sigma_out);
 }

@@ -134,6 +134,7 @@ static void sweep_launch(const void* X, int64_t m, int64_t n, int64_t ldx, const
   dim3 grid((unsigned)((rows_out + T::BM - 1) / T::BM), (k + T::KT - 1) / T::KT, splits);
   int nt = (T::BM / T::TM) * (T::KT / T::TN);
   TF* p = splits > 1 ? (TF*)part : nullptr;
+  note_launch(splits > 1 ? 2 : 1);
   sweep_kernel<TX, TF, TRANS><<<grid, nt, 0, s>>>((const TX*)X, m, n, ldx, (const TF*)B, ldb, k,
                                                   (TF*)C, ldc, per, p);
   if (splits > 1) {
@@ -176,28 +177,31 @@ constexpr int GRAM_T = 256;
 constexpr int GRAM_ROWS = 32;
 constexpr int GRAM_PER_T = (LMAX * LMAX + GRAM_T - 1) / GRAM_T;
 
+// Within a block the products are summed in the factor type TF (FP64 for the
+// plain form; FP32 for the FP32 form, whose factors carry FP32 precision
+// anyway); the NPART block partials are then summed in FP64.
 template <typename TF>
 __global__ void __launch_bounds__(GRAM_T)
 gram_partial(const TF* __restrict__ A, int lda, int ka, const TF* __restrict__ B, int ldb, int kb,
              int64_t rows, double* __restrict__ part) {
-  __shared__ double As[GRAM_ROWS][LMAX];
-  __shared__ double Bs[GRAM_ROWS][LMAX];
+  __shared__ TF As[GRAM_ROWS][LMAX];
+  __shared__ TF Bs[GRAM_ROWS][LMAX];
   const int64_t chunk = (rows + NPART - 1) / NPART;
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int64_t r1 = min(rows, r0 + chunk);
   const int nk = ka * kb;
-  double acc[GRAM_PER_T];
+  TF acc[GRAM_PER_T];
 #pragma unroll
-  for (int q = 0; q < GRAM_PER_T; ++q) acc[q] = 0.0;
+  for (int q = 0; q < GRAM_PER_T; ++q) acc[q] = TF(0);
   for (int64_t t0 = r0; t0 < r1; t0 += GRAM_ROWS) {
     int nr = (int)min((int64_t)GRAM_ROWS, r1 - t0);
     for (int e = threadIdx.x; e < GRAM_ROWS * ka; e += GRAM_T) {
       int rr = e / ka, cc = e % ka;
-      As[rr][cc] = rr < nr ? (double)A[(t0 + rr) * lda + cc] : 0.0;
+      As[rr][cc] = rr < nr ? A[(t0 + rr) * lda + cc] : TF(0);
     }
     for (int e = threadIdx.x; e < GRAM_ROWS * kb; e += GRAM_T) {
       int rr = e / kb, cc = e % kb;
-      Bs[rr][cc] = rr < nr ? (double)B[(t0 + rr) * ldb + cc] : 0.0;
+      Bs[rr][cc] = rr < nr ? B[(t0 + rr) * ldb + cc] : TF(0);
     }
     __syncthreads();
 #pragma unroll
@@ -205,7 +209,7 @@ gram_partial(const TF* __restrict__ A, int lda, int ka, const TF* __restrict__ B
       int e = threadIdx.x + q * GRAM_T;
       if (e < nk) {
         int i = e / kb, j = e % kb;
-        double s = acc[q];
+        TF s = acc[q];
         for (int rr = 0; rr < nr; ++rr) s = fma(As[rr][i], Bs[rr][j], s);
         acc[q] = s;
       }
@@ -215,24 +219,32 @@ gram_partial(const TF* __restrict__ A, int lda, int ka, const TF* __restrict__ B
 #pragma unroll
   for (int q = 0; q < GRAM_PER_T; ++q) {
     int e = threadIdx.x + q * GRAM_T;
-    if (e < nk) part[(int64_t)blockIdx.x * nk + e] = acc[q];
+    if (e < nk) part[(int64_t)blockIdx.x * nk + e] = (double)acc[q];
   }
 }
 
+// Eight interleaved accumulators (partial b goes to accumulator b % 8), then a
+// fixed pairwise combine: the order is fixed, so the sum is reproducible, and
+// the eight independent chains hide the load latency.
 __global__ void part_reduce(const double* __restrict__ part, int width, double* __restrict__ out) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < width; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < NPART; ++b) s += part[(int64_t)b * width + e];
-    out[e] = s;
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int b = 0; b < NPART; b += 8)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] += part[(int64_t)(b + q) * width + e];
+    out[e] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
 }
 
 void launch_part_reduce(const double* part, int width, double* out, cudaStream_t s) {
+  note_launch(1);
   part_reduce<<<(width + 255) / 256, 256, 0, s>>>(part, width, out);
 }
 
 void launch_gram(const void* A, int lda, int ka, const void* B, int ldb, int kb, int64_t rows,
                  int fdt, double* part, double* G, cudaStream_t s) {
+  note_launch(2);
   if (fdt == T_F64)
     gram_partial<double><<<NPART, GRAM_T, 0, s>>>((const double*)A, lda, ka, (const double*)B, ldb, kb, rows, part);
   else
@@ -262,6 +274,7 @@ dot_partial(const TF* __restrict__ A, int lda, const TF* __restrict__ B, int ldb
 
 void launch_dot(const void* A, int lda, const void* B, int ldb, int k, int64_t rows, int fdt,
                 double* part, double* out, cudaStream_t s) {
+  note_launch(2);
   if (fdt == T_F64)
     dot_partial<double><<<NPART, 256, 0, s>>>((const double*)A, lda, (const double*)B, ldb, k, rows, part);
   else
@@ -292,6 +305,7 @@ normx2_partial(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
 
 void launch_normx2(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, double* part,
                    double* out, int* err, cudaStream_t s) {
+  note_launch(2);
   if (xdt == T_F64) normx2_partial<double><<<NPART, 256, 0, s>>>((const double*)X, m, n, ldx, part, err);
   else if (xdt == T_F32) normx2_partial<float><<<NPART, 256, 0, s>>>((const float*)X, m, n, ldx, part, err);
   else if (xdt == T_BF16) normx2_partial<__nv_bfloat16><<<NPART, 256, 0, s>>>((const __nv_bfloat16*)X, m, n, ldx, part, err);
@@ -348,6 +362,7 @@ residual_partial(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
 void launch_residual_direct(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx,
                             const void* U, const void* V, int r, int fdt, double* part,
                             double* out, cudaStream_t s) {
+  note_launch(2);
 #define RD_LAUNCH(TX, TF) \
   residual_partial<TX, TF><<<NPART, RD_COLS, 0, s>>>((const TX*)X, m, n, ldx, (const TF*)U, (const TF*)V, r, part)
   if (fdt == T_F64) {
@@ -375,6 +390,7 @@ __global__ void omega_kernel(TF* F, int64_t rows, int k, uint64_t seed) {
 }
 
 void launch_omega(void* F, int fdt, int64_t rows, int k, uint64_t seed, cudaStream_t s) {
+  note_launch(1);
   int64_t total = rows * k;
   int blocks = (int)min((int64_t)4096, (total + 255) / 256);
   if (fdt == T_F64) omega_kernel<double><<<blocks, 256, 0, s>>>((double*)F, rows, k, seed);
