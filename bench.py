@@ -4,8 +4,9 @@ Workload: X = U0 V0^T + E, 8192 x 6144, r = 32 (Exponential(1) factors with
 50% zeros, 1% clamped Gaussian noise), 500 alternations.  One step = one
 whole solve of Algorithm 3 on the GPU: SVD start, ADMM rotation, ascent +
 HALS iterations (500), direct residual and KKT check.  The metric is solves/s
-of the fast form next to its time to reach the plain FP64 GPU form's final
-relative error, plus p50/p99 per-solve latency.
+of the precision form (X streamed in BF16 through the tensor cores, FP32
+factors, X_lo correction) next to its time to reach the plain FP64 GPU form's
+final relative error, plus p50/p99 per-solve latency.
 
 Timing: W warm-up solves, then K timed solves bracketed by a barrier and a
 device synchronisation, CUDA events on the launching stream; X (201 MB in
@@ -44,10 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-f32", action="store_true")
     return ap.parse_args()
 
 
@@ -180,6 +182,14 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- GPU
+FORMS = {
+    # name: (X dtype given to the library, factor dtype, stream dtype, X element bytes swept)
+    "bf16": ("f32", "f32", "bf16", 2),
+    "f32": ("f32", "f32", None, 4),
+    "f64": ("f64", "f64", None, 8),
+}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -196,14 +206,23 @@ def run_ours(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2605_19325_gb300 import binding as B
-    from paper_2605_19325_gb300.solver import Solver
+    from paper_2605_19325_gb300.solver import Solver, problem_for
 
     X64, r = make_inputs()
     X32 = X64.astype(np.float32)
     dev = torch.device("cuda", local)
-    form = args.form
-    Xd = torch.as_tensor(X32 if form == "f32" else X64, device=dev)
     stream = torch.cuda.current_stream()
+    Xd32 = torch.as_tensor(X32, device=dev)
+    Xd64 = None
+
+    def make_solver(form):
+        nonlocal Xd64
+        xdt, _, sdt, _ = FORMS[form]
+        if xdt == "f64":
+            if Xd64 is None:
+                Xd64 = torch.as_tensor(X64, device=dev)
+            return Solver(Xd64, r)
+        return Solver(Xd32, r, x_stream=torch.bfloat16 if sdt == "bf16" else None)
 
     def solve_once(s, n_iter):
         s.svd_init()
@@ -213,7 +232,8 @@ def run_ours(args):
         kk = s.kkt()
         return rel, kk
 
-    s = Solver(Xd, r)
+    form = args.form
+    s = make_solver(form)
     for _ in range(args.warmup):
         solve_once(s, ITERS)
     torch.cuda.synchronize()
@@ -254,27 +274,29 @@ def run_ours(args):
     V_host = s.V.double().cpu().numpy()
     s.close()
 
-    # plain FP64 GPU form: the target error and its time
-    f64 = None
-    if not args.no_f64 and form != "f64":
-        X64d = torch.as_tensor(X64, device=dev)
-        s64 = Solver(X64d, r)
-        solve_once(s64, ITERS)
+    # the other forms, timed once after one warm solve each: the plain FP64
+    # form fixes the target error; the FP32 (SIMT) form is context
+    others = {}
+    for other in ("f64", "f32"):
+        if other == form or (other == "f64" and args.no_f64) or (other == "f32" and args.no_f32):
+            continue
+        so = make_solver(other)
+        solve_once(so, ITERS)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rel64, kk64 = solve_once(s64, ITERS)
+        rel_o, kk_o = solve_once(so, ITERS)
         torch.cuda.synchronize()
-        f64 = {"ms_per_solve": 1e3 * (time.perf_counter() - t0), "rel_err": rel64,
-               "kkt_pg_rel": kk64.pg_rel}
-        s64.close()
-        del X64d
+        others[other] = {"ms_per_solve": 1e3 * (time.perf_counter() - t0), "rel_err": rel_o,
+                         "kkt_pg_rel": kk_o.pg_rel}
+        so.close()
 
     # end to end through the C ABI with host buffers (pinned), one call per solve
     e2e = None
     if not args.no_e2e:
-        prob, fdt = __import__("paper_2605_19325_gb300.solver", fromlist=["problem_for"]).problem_for(Xd, r)
+        xsrc = X64 if FORMS[form][0] == "f64" else X32
+        Xh = torch.from_numpy(xsrc).pin_memory()
+        prob, fdt = problem_for(Xh, r, None, torch.bfloat16 if FORMS[form][2] == "bf16" else None)
         ctx = B.enmf_create(prob, stream)
-        Xh = torch.from_numpy(X32 if form == "f32" else X64).pin_memory()
         Uh = torch.empty(M, r, dtype=fdt).pin_memory()
         Vh = torch.empty(N, r, dtype=fdt).pin_memory()
         B.enmf_solve(ctx, Xh.data_ptr(), Uh.data_ptr(), Vh.data_ptr(), ITERS)
@@ -286,7 +308,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / ne
         B.enmf_destroy(ctx)
-        e2e = {"value": 1.0 / dt, "unit": "solves/s", "h2d_bytes_per_step": Xh.numel() * Xh.element_size(),
+        e2e = {"value": 1.0 / dt, "unit": "solves/s",
+               "h2d_bytes_per_step": Xh.numel() * Xh.element_size(),
                "d2h_bytes_per_step": (Uh.numel() + Vh.numel()) * Uh.element_size()}
 
     if rank != 0:
@@ -295,48 +318,63 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel: the X sweep (X V or X^T U)
+    # roofline of the dominant kernel, the X sweep (X V or X^T U), timed live
+    # with CUDA events on the library stream over the timed solves
     pk = peaks()
-    esize = 4 if form == "f32" else 8
-    flops_per_sweep = 2.0 * M * N * r
+    esize = FORMS[form][3]
     avg_sweep_s = (sweep_ms / max(sweeps, 1)) / 1e3
-    achieved = flops_per_sweep / avg_sweep_s / 1e12 if sweeps else None
-    probe = B.enmf_probe_fma_peak(B.ENMF_F32 if form == "f32" else B.ENMF_F64) / 1e12
-    sm_max = (clk or {}).get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
-    lanes = 128 if form == "f32" else None
-    peak_alu = 152 * lanes * 2 * sm_max * 1e6 / 1e12 if lanes else probe
-    roof = {"kernel": "sweep (X V / X^T U, SIMT FMA)", "bound": "alu",
-            "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-            "frac": (achieved / peak_alu) if achieved else None, "traffic": None,
-            "peak_measured_probe": probe, "hbm_bytes_per_sweep": M * N * esize,
-            "sweep_ms_avg": avg_sweep_s * 1e3, "sweeps_timed": sweeps,
-            "peak_source": ("152 SMs x 128 FP32 lanes x 2 flop x max SM clock" if lanes
-                            else "measured FP64 FMA probe")}
+    if FORMS[form][2] == "bf16":
+        bytes_per_sweep = M * N * esize
+        achieved = bytes_per_sweep / avg_sweep_s / 1e9 if sweeps else None
+        peak = pk.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "tensor-core X sweep (TMA + tcgen05, BF16 X)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "algorithmic_bytes_per_launch": bytes_per_sweep,
+                "sweep_us_avg": avg_sweep_s * 1e6, "sweeps_timed": sweeps,
+                "peak_source": "measured HBM copy (burst)" + (" [fallback]" if pk.get("fallback") else ""),
+                "timed_span": "split/transpose of the factor + tensor-core sweep + split reduction"}
+    else:
+        flops_per_sweep = 2.0 * M * N * r
+        achieved = flops_per_sweep / avg_sweep_s / 1e12 if sweeps else None
+        probe = B.enmf_probe_fma_peak(B.ENMF_F32 if form == "f32" else B.ENMF_F64) / 1e12
+        sm_max = (clk or {}).get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12 if form == "f32" else probe
+        roof = {"kernel": "SIMT X sweep (X V / X^T U)", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": None, "peak_measured_probe": probe,
+                "sweep_us_avg": avg_sweep_s * 1e6, "sweeps_timed": sweeps,
+                "peak_source": ("152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+                                if form == "f32" else "measured FP64 FMA probe")}
 
     cb = None
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_oracle_sample(X64, r, np.maximum(U_host, 0), np.maximum(V_host, 0))
 
-    gap = None
     ttt = None
-    if f64 is not None:
-        gap = abs(rel - f64["rel_err"]) / f64["rel_err"]
-        ttt = {"f64_gpu_ms": f64["ms_per_solve"], "f64_rel_err": f64["rel_err"],
+    if "f64" in others or form == "f64":
+        ref = others["f64"] if form != "f64" else {"ms_per_solve": ms_per_step, "rel_err": rel}
+        gap = abs(rel - ref["rel_err"]) / ref["rel_err"]
+        ttt = {"target": "final rel. Frobenius error of the plain FP64 GPU form (500 alternations)",
+               "f64_gpu_ms": ref["ms_per_solve"], "f64_rel_err": ref["rel_err"],
                form + "_ms": ms_per_step, form + "_rel_err": rel, "rel_err_gap": gap,
-               "meets_1e-3": gap <= 1e-3}
+               "meets_1e-3": gap <= 1e-3,
+               "speedup_vs_f64_gpu": ref["ms_per_solve"] / ms_per_step}
     sorted_ms = sorted(step_ms)
     p99 = sorted_ms[min(len(sorted_ms) - 1, int(math.ceil(0.99 * len(sorted_ms))) - 1)]
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": form, "data": "synthetic",
+            "dtype": {"bf16": "bf16", "f32": "f32", "f64": "f64"}[form], "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": form, "m": M, "n": N, "r": r,
-                       "iterations": ITERS, "l2": "inputs larger than L2 (X %d MB)" % (M * N * esize // 2**20),
+                       "iterations": ITERS,
+                       "l2": "inputs larger than L2 (X %d MB FP32 + BF16 copies)" % (M * N * 4 // 2**20)
+                       if form == "bf16" else "inputs larger than L2 (X %d MB)" % (M * N * esize // 2**20),
                        "parallelism": "replicas" if world > 1 else "single"},
             "p50_ms": statistics.median(step_ms), "p99_ms": p99,
             "time_to_target": ttt, "final": {"rel_err": rel, "kkt_pg_rel": kk.pg_rel},
-            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches}
+            "other_forms": others, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+            "clocks": clk, "gpu_launches": launches}
     print(json.dumps(line))
     if world > 1:
         dist.barrier()

@@ -76,6 +76,13 @@ typedef struct {
   int32_t r;        /* rank, 1 <= r <= min(m, n, ENMF_MAX_RANK)               */
   int32_t x_dtype;  /* enmf_dtype of X                                        */
   int32_t f_dtype;  /* enmf_dtype of U and V: ENMF_F64 with X F64, else F32   */
+  int32_t stream_dtype; /* type the iteration's X sweeps read:                */
+                    /*   = x_dtype (or 0 with F64 X): the SIMT sweeps;        */
+                    /*   ENMF_BF16 with F32 X: the precision form -- the      */
+                    /*   tensor-core sweeps read X_hi = bf16(X) and apply     */
+                    /*   X_lo = bf16(X - X_hi) every correct_every steps;     */
+                    /*   ENMF_BF16 with BF16 X: tensor-core sweeps on X as    */
+                    /*   given (no correction).  F32 factors required.        */
 } enmf_problem;
 
 typedef struct enmf_ctx enmf_ctx;
@@ -160,6 +167,8 @@ typedef struct {
   double* trace;          /* device FP64 [n_iter] or NULL                  */
   int32_t reset;          /* 1: start a new ascent stage from (U, V)       */
   int32_t sync_info;      /* 1: synchronise and fill *info                 */
+  int32_t correct_every;  /* precision form: refresh X_lo V and X_lo^T U   */
+                          /* every this many alternations (default 10)     */
 } enmf_iter_opts;
 typedef struct {
   int32_t iters;          /* alternations done in total (this state)       */
@@ -193,6 +202,24 @@ typedef struct {
 } enmf_kkt_report;
 enmf_status enmf_kkt(enmf_ctx* ctx, const void* X, const void* U, const void* V,
                      enmf_kkt_report* out);
+
+/* ---- Tensor-core staging (precision form) --------------------------------
+ * With stream_dtype = ENMF_BF16, stage X once before svd_init / iterate /
+ * sweep: F32 X is split into context-owned X_hi = bf16(X) and
+ * X_lo = bf16(X - X_hi) (row stride rounded up to 8 elements) and TMA
+ * descriptors are built; BF16 X is used in place (it must be 16-byte aligned
+ * with ldx a multiple of 8).  Later calls must pass the same X pointer
+ * (ENMF_ESTATE otherwise).  ENMF_EDOMAIN if X has a negative or non-finite
+ * entry.  Enqueued on the context stream. */
+enmf_status enmf_stage_x(enmf_ctx* ctx, const void* X);
+
+/* ---- The core NMF kernel (App. I): X V and X^T U --------------------------
+ * XV (m x r) = X V and XtU (n x r) = X^T U in the context's form, FP32 or
+ * FP64 like the factors, device pointers, row-major with leading dimension r.
+ * Either output may be NULL.  Precision form: exact = 1 adds the X_lo terms
+ * (two passes), exact = 0 uses X_hi only.  Enqueued, no sync. */
+enmf_status enmf_sweep(enmf_ctx* ctx, const void* X, const void* U, const void* V, void* XV,
+                       void* XtU, int32_t exact);
 
 /* ---- One call, host or device buffers -------------------------------------
  * The whole of Algorithm 3: svd_init, rotate, iterate(n_iter), residual.  X,

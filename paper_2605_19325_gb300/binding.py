@@ -28,7 +28,7 @@ class EnmfError(RuntimeError):
 
 class enmf_problem(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("ldx", C.c_int64), ("r", C.c_int32),
-                ("x_dtype", C.c_int32), ("f_dtype", C.c_int32)]
+                ("x_dtype", C.c_int32), ("f_dtype", C.c_int32), ("stream_dtype", C.c_int32)]
 
 
 class enmf_svd_opts(C.Structure):
@@ -53,7 +53,7 @@ class enmf_rotate_info(C.Structure):
 class enmf_iter_opts(C.Structure):
     _fields_ = [("n_iter", C.c_int32), ("pbcd_max_iter", C.c_int32), ("eps", C.c_double),
                 ("n_shift", C.c_int32), ("trace", C.c_void_p), ("reset", C.c_int32),
-                ("sync_info", C.c_int32)]
+                ("sync_info", C.c_int32), ("correct_every", C.c_int32)]
 
 
 class enmf_iter_info(C.Structure):
@@ -86,6 +86,9 @@ _SIGS = {
     "enmf_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                              C.POINTER(enmf_svd_opts), C.POINTER(enmf_admm_opts),
                              C.POINTER(enmf_iter_opts), C.POINTER(C.c_double)]),
+    "enmf_stage_x": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "enmf_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_int32]),
     "enmf_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "enmf_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                     C.c_int32]),
@@ -169,10 +172,20 @@ def enmf_rotate(ctx, U, V, R=None, opts=None):
     return info, code
 
 
+def enmf_stage_x(ctx, X):
+    check(lib().enmf_stage_x(ctx, _ptr(X)), "enmf_stage_x")
+
+
+def enmf_sweep(ctx, X, U, V, XV=None, XtU=None, exact=1):
+    check(lib().enmf_sweep(ctx, _ptr(X), _ptr(U), _ptr(V), _ptr(XV), _ptr(XtU), exact),
+          "enmf_sweep")
+
+
 def enmf_iterate(ctx, X, U, V, n_iter, trace=None, reset=0, eps=1e-4, pbcd_max_iter=5,
-                 n_shift=3, sync_info=1):
+                 n_shift=3, sync_info=1, correct_every=10):
     o = enmf_iter_opts(n_iter, pbcd_max_iter, eps, n_shift,
-                       None if trace is None else trace.data_ptr(), reset, sync_info)
+                       None if trace is None else trace.data_ptr(), reset, sync_info,
+                       correct_every)
     info = enmf_iter_info()
     check(lib().enmf_iterate(ctx, _ptr(X), _ptr(U), _ptr(V), C.byref(o),
                              C.byref(info) if sync_info else None), "enmf_iterate")

@@ -52,7 +52,25 @@ struct enmf_ctx {
   cudaEvent_t pev[2 * 256];
   double prof_ms;
   long long prof_n;
+  // precision form (tensor-core sweeps on BF16 X)
+  int tc;
+  int rp;
+  int64_t ldh, ldn, ldm;
+  int sv, st_split;
+  void* tcws;
+  size_t tcws_bytes;
+  const void* xh;                // X_hi (context-owned, or the caller's BF16 X)
+  void* xl;                      // X_lo (context-owned; null for BF16 input)
+  void* own_xh;
+  void* vth; void* vtl;          // V^T as a BF16 pair (rp x ldn)
+  void* uth; void* utl;          // U^T as a BF16 pair (rp x ldm)
+  float* tcpart;                 // split partials
+  float* cv; float* cu;          // X_lo V, X_lo^T U (correction)
+  const void* staged_src;        // X pointer the staged copy belongs to
+  alignas(64) unsigned char maps[6][128];   // X_hi, X_lo, Vt hi/lo, Ut hi/lo
 };
+
+enum { MAP_XH = 0, MAP_XL = 1, MAP_VH = 2, MAP_VL = 3, MAP_UH = 4, MAP_UL = 5 };
 
 constexpr int PROF_PAIRS = 256;
 
@@ -84,13 +102,56 @@ extern "C" const char* enmf_status_string(enmf_status s) {
 
 extern "C" const char* enmf_version(void) { return "enmf-gb300 0.1"; }
 
+// Tensor-core (BF16 stream) form?
+static bool tc_form(const enmf_problem* p) { return p->stream_dtype == ENMF_BF16; }
+
 static bool valid_problem(const enmf_problem* p) {
   if (!p) return false;
   if (p->m < 1 || p->n < 1 || p->ldx < p->n) return false;
   if (p->r < 1 || p->r > ENMF_MAX_RANK || p->r > p->m || p->r > p->n) return false;
   if (p->x_dtype < ENMF_F64 || p->x_dtype > ENMF_F16) return false;
+  if (tc_form(p)) {
+    if (p->f_dtype != ENMF_F32) return false;
+    if (p->x_dtype != ENMF_F32 && p->x_dtype != ENMF_BF16) return false;
+    if (p->x_dtype == ENMF_BF16 && (p->ldx % 8) != 0) return false;
+    if (p->m > 0x7fffffffLL || p->n > 0x7fffffffLL) return false;
+  } else if (p->stream_dtype != 0 && p->stream_dtype != p->x_dtype) {
+    return false;
+  }
   if (p->f_dtype == ENMF_F64) return p->x_dtype == ENMF_F64;
   return p->f_dtype == ENMF_F32;
+}
+
+// Tensor-core buffers of the precision form (a separate allocation).
+struct TcPlan {
+  int rp;
+  int64_t ldh, ldn, ldm;
+  int sv, st;          // split arguments for X V and X^T U
+  size_t xh, vt, ut, part, cv, cu, total;
+};
+
+static TcPlan tc_plan(const enmf_problem* p, int num_sms) {
+  TcPlan t;
+  memset(&t, 0, sizeof(t));
+  if (!tc_form(p)) return t;
+  const int64_t m = p->m, n = p->n;
+  t.rp = tc_rank_pad(p->r);
+  t.ldh = (n + 7) / 8 * 8;
+  t.ldn = (n + 7) / 8 * 8;
+  t.ldm = (m + 7) / 8 * 8;
+  t.sv = tc_splits(m, n, TC_KB_XV, num_sms);
+  t.st = tc_splits(n, m, TC_KB_XT, num_sms);
+  const int nsv = tc_nsplit(n, t.sv, 0), nst = tc_nsplit(m, t.st, 1);
+  t.xh = p->x_dtype == ENMF_F32 ? (size_t)m * t.ldh * 2 : 0;
+  t.vt = (size_t)t.rp * t.ldn * 2;
+  t.ut = (size_t)t.rp * t.ldm * 2;
+  size_t pv = (size_t)nsv * m * p->r * 4, pt = (size_t)nst * n * p->r * 4;
+  t.part = pv > pt ? pv : pt;
+  t.cv = (size_t)m * p->r * 4;
+  t.cu = (size_t)n * p->r * 4;
+  auto a = [](size_t b) { return (b + 1023) & ~(size_t)1023; };
+  t.total = 2 * a(t.xh) + 2 * a(t.vt) + 2 * a(t.ut) + a(t.part) + a(t.cv) + a(t.cu) + 1024;
+  return t;
 }
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -132,7 +193,7 @@ extern "C" enmf_status enmf_workspace_size(const enmf_problem* p, size_t* bytes)
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  *bytes = plan(p, sms, nullptr);
+  *bytes = plan(p, sms, nullptr) + tc_plan(p, sms).total;
   return ENMF_OK;
 }
 
@@ -240,13 +301,81 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
   cudaMemsetAsync(ctx->ws, 0, ctx->ws_bytes, ctx->stream);
   ctx->grid_u = half_step_grid(ctx->fdt, p->r, ctx->num_sms);
   ctx->grid_v = ctx->grid_u;
-  if (ctx->grid_u > 4096) ctx->grid_u = ctx->grid_v = 4096;
+  // at most 256 blocks: the fused Gram keeps one k x k partial per block in
+  // the NPART x (LMAX^2 + 8) partial buffer
+  if (ctx->grid_u > 256) ctx->grid_u = ctx->grid_v = 256;
+  if (tc_form(p)) {
+    const TcPlan t = tc_plan(p, ctx->num_sms);
+    ctx->tc = 1;
+    ctx->rp = t.rp;
+    ctx->ldh = t.ldh;
+    ctx->ldn = t.ldn;
+    ctx->ldm = t.ldm;
+    ctx->sv = t.sv;
+    ctx->st_split = t.st;
+    ctx->tcws_bytes = t.total;
+    if (cudaMalloc(&ctx->tcws, t.total) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ctx->ws);
+      delete ctx;
+      return ENMF_ENOMEM;
+    }
+    cudaMemsetAsync(ctx->tcws, 0, t.total, ctx->stream);
+    char* q = (char*)(((uintptr_t)ctx->tcws + 1023) & ~(uintptr_t)1023);
+    auto grab = [&](size_t bytes) { void* o = q; q += (bytes + 1023) & ~(size_t)1023; return o; };
+    ctx->own_xh = t.xh ? grab(t.xh) : nullptr;
+    ctx->xl = t.xh ? grab(t.xh) : nullptr;
+    ctx->vth = grab(t.vt);
+    ctx->vtl = grab(t.vt);
+    ctx->uth = grab(t.ut);
+    ctx->utl = grab(t.ut);
+    ctx->tcpart = (float*)grab(t.part);
+    ctx->cv = (float*)grab(t.cv);
+    ctx->cu = (float*)grab(t.cu);
+    bool ok = tc_make_map(ctx->maps[MAP_VH], ctx->vth, t.rp, p->n, t.ldn, 64, t.rp) &&
+              tc_make_map(ctx->maps[MAP_VL], ctx->vtl, t.rp, p->n, t.ldn, 64, t.rp) &&
+              tc_make_map(ctx->maps[MAP_UH], ctx->uth, t.rp, p->m, t.ldm, 64, t.rp) &&
+              tc_make_map(ctx->maps[MAP_UL], ctx->utl, t.rp, p->m, t.ldm, 64, t.rp);
+    if (!ok) {
+      cudaFree(ctx->tcws);
+      cudaFree(ctx->ws);
+      delete ctx;
+      return ENMF_ECUDA;
+    }
+  }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    if (ctx->tcws) cudaFree(ctx->tcws);
     cudaFree(ctx->ws);
     delete ctx;
     return ENMF_ECUDA;
   }
   *out = ctx;
+  return ENMF_OK;
+}
+
+// ------------------------------------------------------ precision form
+extern "C" enmf_status enmf_stage_x(enmf_ctx* ctx, const void* X) {
+  if (!ctx || !X) return ENMF_EINVAL;
+  if (ctx->poison) return ctx->poison;
+  if (!ctx->tc) return ENMF_ESTATE;
+  const enmf_problem& p = ctx->p;
+  if (p.x_dtype == ENMF_F32) {
+    launch_split_x((const float*)X, p.m, p.n, p.ldx, ctx->own_xh, ctx->xl, ctx->ldh, ctx->err,
+                   ctx->stream);
+    if (cudaGetLastError() != cudaSuccess) {
+      ctx->poison = ENMF_ECUDA;
+      return ENMF_ECUDA;
+    }
+    ctx->xh = ctx->own_xh;
+    if (!tc_make_map(ctx->maps[MAP_XH], ctx->xh, p.m, p.n, ctx->ldh, 64, 128) ||
+        !tc_make_map(ctx->maps[MAP_XL], ctx->xl, p.m, p.n, ctx->ldh, 64, 128))
+      return ENMF_ECUDA;
+  } else {
+    if (((uintptr_t)X & 15) != 0) return ENMF_EINVAL;
+    ctx->xh = X;
+    if (!tc_make_map(ctx->maps[MAP_XH], X, p.m, p.n, p.ldx, 64, 128)) return ENMF_ECUDA;
+  }
+  ctx->staged_src = X;
   return ENMF_OK;
 }
 
@@ -257,6 +386,7 @@ extern "C" void enmf_destroy(enmf_ctx* ctx) {
   if (ctx->hX) cudaFree(ctx->hX);
   if (ctx->hU) cudaFree(ctx->hU);
   if (ctx->hV) cudaFree(ctx->hV);
+  if (ctx->tcws) cudaFree(ctx->tcws);
   if (ctx->prof_every >= 0 && ctx->pev[0])
     for (int i = 0; i < 2 * PROF_PAIRS; ++i) cudaEventDestroy(ctx->pev[i]);
   delete ctx;
@@ -418,7 +548,10 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
     launch_admm_pass(U, V, m, n, k, fdt, ctx->R, ctx->Zb, ctx->Yb, rho, it == 0, ctx->st,
                      ctx->part, s);
     launch_part_reduce(ctx->part, k * k, ctx->Msm, s);   // M = W^T B, fixed order
-    launch_polar(ctx->Msm, k, ctx->R, ctx->T2, o.tol, ctx->st, ctx->err, s);
+    if (fdt == T_F64)
+      launch_polar(ctx->Msm, k, ctx->R, ctx->T2, o.tol, ctx->st, ctx->err, s);
+    else
+      launch_polar_ns(ctx->Msm, k, ctx->R, o.tol, ctx->st, ctx->err, s);
     ++steps_launched;
     if ((it + 1) % check_every == 0 && it + 1 < o.max_iter) {
       rc = check_launch(ctx);
@@ -454,8 +587,11 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
 }
 
 // ------------------------------------------------------------ 3. iterate
+// One half of an alternation: the row updates of F (U or V), the Gram of the
+// new F into G_out and, for the V-half, the end-of-alternation bookkeeping.
 static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const double* G, int64_t rows,
-                 const enmf_iter_opts& o, bool dot) {
+                     const enmf_iter_opts& o, bool dot, double* G_out, const double* Gu,
+                     double* trace, int trace_idx) {
   HalfArgs a;
   memset(&a, 0, sizeof(a));
   a.F = F;
@@ -476,6 +612,12 @@ static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const dou
   a.counts_cap = ctx->counts_cap;
   a.dotA = dot ? A : nullptr;
   a.dot_part = dot ? ctx->dot_part : nullptr;
+  a.G_out = G_out;
+  a.gpart = ctx->part;
+  a.finalize = which == 1 ? 1 : 0;
+  a.Gu = Gu;
+  a.trace = trace;
+  a.trace_idx = trace_idx;
   launch_half_step(a, which == 0 ? ctx->grid_u : ctx->grid_v, ctx->stream);
 }
 
@@ -484,40 +626,119 @@ static int half_grid(enmf_ctx* ctx, int64_t rows, int grid) {
   return (int)((int64_t)grid > need ? need : grid);
 }
 
+// ------------------------------------------------------------ the sweeps
+// corr: 0 = X_hi only, 1 = add the stored X_lo term, 2 = refresh the X_lo
+// term with the current factor first (tensor-core form; ignored otherwise).
+static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int corr) {
+  const enmf_problem& p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  const int r = p.r;
+  if (!ctx->tc) {
+    launch_xv(X, ctx->xdt, p.m, p.n, p.ldx, V, r, r, out, r, ctx->fdt, ctx->splitk, ctx->num_sms, s);
+    return;
+  }
+  const int ns = tc_nsplit(p.n, ctx->sv, 0);
+  launch_split_transpose((const float*)V, p.n, r, ctx->vth, ctx->vtl, ctx->ldn, s);
+  if (corr == 2 && ctx->xl) {
+    launch_tc_sweep(0, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_VH], ctx->maps[MAP_VL], p.m, p.n,
+                    r, ctx->tcpart, ctx->sv, ctx->err, s);
+    launch_tc_reduce(ctx->tcpart, ns, p.m, r, nullptr, ctx->cv, s);
+  }
+  launch_tc_sweep(0, ctx->rp, ctx->maps[MAP_XH], ctx->maps[MAP_VH], ctx->maps[MAP_VL], p.m, p.n, r,
+                  ctx->tcpart, ctx->sv, ctx->err, s);
+  launch_tc_reduce(ctx->tcpart, ns, p.m, r, (corr >= 1 && ctx->xl) ? ctx->cv : nullptr,
+                   (float*)out, s);
+}
+
+static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, int corr) {
+  const enmf_problem& p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  const int r = p.r;
+  if (!ctx->tc) {
+    launch_xtu(X, ctx->xdt, p.m, p.n, p.ldx, U, r, r, out, r, ctx->fdt, ctx->splitk, ctx->num_sms, s);
+    return;
+  }
+  const int ns = tc_nsplit(p.m, ctx->st_split, 1);
+  launch_split_transpose((const float*)U, p.m, r, ctx->uth, ctx->utl, ctx->ldm, s);
+  if (corr == 2 && ctx->xl) {
+    launch_tc_sweep(1, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_UH], ctx->maps[MAP_UL], p.n, p.m,
+                    r, ctx->tcpart, ctx->st_split, ctx->err, s);
+    launch_tc_reduce(ctx->tcpart, ns, p.n, r, nullptr, ctx->cu, s);
+  }
+  launch_tc_sweep(1, ctx->rp, ctx->maps[MAP_XH], ctx->maps[MAP_UH], ctx->maps[MAP_UL], p.n, p.m, r,
+                  ctx->tcpart, ctx->st_split, ctx->err, s);
+  launch_tc_reduce(ctx->tcpart, ns, p.n, r, (corr >= 1 && ctx->xl) ? ctx->cu : nullptr,
+                   (float*)out, s);
+}
+
+static enmf_status check_staged(enmf_ctx* ctx, const void* X) {
+  if (ctx->tc && ctx->staged_src != X) return ENMF_ESTATE;
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_sweep(enmf_ctx* ctx, const void* X, const void* U, const void* V,
+                                  void* XV, void* XtU, int32_t exact) {
+  GUARD(ctx);
+  if (!X || (XV && !V) || (XtU && !U)) return ENMF_EINVAL;
+  enmf_status rc = check_staged(ctx, X);
+  if (rc) return rc;
+  if (XV) sweep_xv(ctx, X, V, XV, exact ? 2 : 0);
+  if (XtU) sweep_xtu(ctx, X, U, XtU, exact ? 2 : 0);
+  return check_launch(ctx);
+}
+
 extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void* V,
                                     const enmf_iter_opts* opts, enmf_iter_info* info) {
   GUARD(ctx);
   if (!X || !U || !V) return ENMF_EINVAL;
-  enmf_iter_opts o = {0, 5, 1e-4, 3, nullptr, 0, 1};
+  enmf_iter_opts o = {0, 5, 1e-4, 3, nullptr, 0, 1, 10};
   if (opts) o = *opts;
   if (o.n_iter < 0 || o.pbcd_max_iter < 0 || !(o.eps >= 0) || o.n_shift < 1) return ENMF_EINVAL;
+  if (o.correct_every < 1) o.correct_every = 10;
   const enmf_problem& p = ctx->p;
   const int k = p.r, fdt = ctx->fdt, xdt = ctx->xdt;
   const int64_t m = p.m, n = p.n;
   cudaStream_t s = ctx->stream;
+  enmf_status rc = check_staged(ctx, X);
+  if (rc) return rc;
   if (o.reset || !ctx->state_valid) {
     launch_state_init(U, V, m, n, k, fdt, o.n_shift, ctx->st, ctx->part, s);
     ctx->state_valid = true;
   }
   launch_normx2(X, xdt, m, n, p.ldx, ctx->part, &ctx->st->normX2, ctx->err, s);
-  launch_gram(V, k, k, V, k, k, n, fdt, ctx->part, ctx->Gv, s);
-  const int ndot = half_grid(ctx, n, ctx->grid_v);
+  {
+    // V^T V with the V-half kernel's own decomposition (bitwise equal to the
+    // Gram the previous call ended with, so calls can be split freely)
+    HalfArgs g;
+    memset(&g, 0, sizeof(g));
+    g.F = V;
+    g.rows = n;
+    g.k = k;
+    g.fdt = fdt;
+    g.which = 1;
+    g.st = ctx->st;
+    g.err = ctx->err;
+    g.G = ctx->Gu;   // unused (read into shared memory only)
+    g.G_out = ctx->Gv;
+    g.gpart = ctx->part;
+    g.gram_only = 1;
+    launch_half_step(g, ctx->grid_v, s);
+  }
   for (int it = 0; it < o.n_iter; ++it) {
-    const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 &&
+    // precision form: refresh the X_lo terms every correct_every alternations
+    const int corr = (it % o.correct_every == 0) ? 2 : 1;
+    const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
                      ctx->npev + 4 <= 2 * PROF_PAIRS;
     if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
-    launch_xv(X, xdt, m, n, p.ldx, V, k, k, ctx->M0, k, fdt, ctx->splitk, ctx->num_sms, s);
+    sweep_xv(ctx, X, V, ctx->M0, corr);
     if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
-    run_half(ctx, 0, U, ctx->M0, ctx->Gv, m, o, false);
-    launch_gram(U, k, k, U, k, k, m, fdt, ctx->part, ctx->Gu, s);
+    run_half(ctx, 0, U, ctx->M0, ctx->Gv, m, o, false, ctx->Gu, nullptr, nullptr, 0);
     if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
-    launch_xtu(X, xdt, m, n, p.ldx, U, k, k, ctx->N0, k, fdt, ctx->splitk, ctx->num_sms, s);
+    sweep_xtu(ctx, X, U, ctx->N0, corr);
     if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
-    run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true);
-    launch_gram(V, k, k, V, k, k, n, fdt, ctx->part, ctx->Gv, s);
-    launch_iter_finalize(ctx->st, ctx->dot_part, ndot, ctx->Gu, ctx->Gv, k, o.trace, it, s);
+    run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu, o.trace, it);
   }
-  enmf_status rc = check_launch(ctx);
+  rc = check_launch(ctx);
   if (rc) return rc;
   if (ctx->npev > 0) {
     rc = prof_harvest(ctx);
@@ -689,11 +910,16 @@ extern "C" enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V
     if (!ctx->hV && cudaMalloc(&ctx->hV, vb) != cudaSuccess) { cudaGetLastError(); return ENMF_ENOMEM; }
     dV = ctx->hV;
   }
-  enmf_status rc = enmf_svd_init(ctx, dX, dU, dV, nullptr, svd, nullptr);
+  enmf_status rc = ENMF_OK;
+  if (ctx->tc) {
+    rc = enmf_stage_x(ctx, dX);
+    if (rc) return rc;
+  }
+  rc = enmf_svd_init(ctx, dX, dU, dV, nullptr, svd, nullptr);
   if (rc && rc != ENMF_ENOTCONV) return rc;
   rc = enmf_rotate(ctx, dU, dV, nullptr, admm, nullptr);
   if (rc && rc != ENMF_ENOTCONV) return rc;
-  enmf_iter_opts io = {n_iter, 5, 1e-4, 3, nullptr, 1, 0};
+  enmf_iter_opts io = {n_iter, 5, 1e-4, 3, nullptr, 1, 0, 10};
   if (iter) {
     io = *iter;
     io.n_iter = n_iter;

@@ -94,6 +94,20 @@ struct HalfArgs {
   int counts_cap;
   const void* dotA;   // if non-null: V-half also sums <dotA, F> into dot_part
   double* dot_part;
+  // fused Gram of the updated factor: G_out (k x k, FP64) = F^T F, summed from
+  // per-block partials gpart (grid x k x k) in block order after a grid barrier
+  double* G_out;
+  double* gpart;
+  // fused end of the alternation (V-half): objective into trace[trace_idx]
+  // from Gu (U^T U) and G_out (V^T V), then the stage update
+  int finalize;
+  const double* Gu;
+  double* trace;
+  int trace_idx;
+  // gram_only: skip the row updates and only form G_out = F^T F with the same
+  // block decomposition (so a Gram taken at the start of a call is bitwise the
+  // one the previous call's last half-step produced)
+  int gram_only;
 };
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);
 int half_step_grid(int fdt, int k, int num_sms);
@@ -128,6 +142,10 @@ void launch_kkt_rows(const void* F, const void* A, const double* G, int64_t rows
 // R_new = polar(sum of NPART partial M's); dR, convergence, ADMM step count.
 void launch_polar(const double* M, int k, double* R, double* D, double tol,
                   DevState* st, int* err, cudaStream_t s);
+// Same update for the reduced-precision forms: FP32 Newton-Schulz polar
+// iteration plus one FP64 Newton-Schulz step.
+void launch_polar_ns(const double* M, int k, double* R, double tol, DevState* st, int* err,
+                     cudaStream_t s);
 // Orthonormalising transform of a Gram G (k x k): eigen-decomposition by
 // one-sided Jacobi, keep eigenvalues > tau * lambda_1, T = V_k diag(l^-1/2).
 // Writes T (k x k, unused columns zero) and *kept.
@@ -144,6 +162,27 @@ void launch_svd_finish(const double* sigma, const double* Ut, const double* Wt, 
                        double* Tv, double* sigma_out, cudaStream_t s);
 void launch_rr_prep(const double* sigma, const double* Ut, const double* Wt, int k1, int k2,
                     int r, double* Wr, double* UrS, DevState* st, cudaStream_t s);
+// ------------------------------------------------------------- tc_sweep.cu
+// 2D BF16 tensor map (CUtensorMap, 128 bytes at `map`) over a row-major
+// (rows x cols, ld) array, box box_cols x box_rows, 128-byte swizzle.
+bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                 int box_cols, int box_rows);
+int tc_rank_pad(int r);
+int tc_splits(int64_t rows_out, int64_t red, int kb, int num_sms);
+int tc_nsplit(int64_t red, int splits, int mode);
+// mode 0: part = X B (rows_out m, red n); mode 1: part = X^T B (rows_out n,
+// red m).  Maps: X (box 64 x 128), B^T hi and lo (box 64 x rp).
+void launch_tc_sweep(int mode, int rp, const void* mapX, const void* mapBh, const void* mapBl,
+                     int64_t rows_out, int64_t red, int r, float* part, int splits, int* err,
+                     cudaStream_t s);
+void launch_split_transpose(const float* F, int64_t rows, int r, void* hi, void* lo, int64_t ldt,
+                            cudaStream_t s);
+void launch_tc_reduce(const float* part, int splits, int64_t rows, int r, const float* corr,
+                      float* C, cudaStream_t s);
+void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh, void* xl,
+                    int64_t ldh, int* err, cudaStream_t s);
+constexpr int TC_KB_XV = 64, TC_KB_XT = 128;
+
 // KKT finalisation: combine the two factors' partial measures.
 void launch_kkt_final(const double* pu, const double* pv, double* out, cudaStream_t s);
 

@@ -1,0 +1,469 @@
+// Tensor-core sweeps over a BF16 copy of X for the reduced-precision form:
+//   X V   (A = X tile, K-major)       and
+//   X^T U (A = X tile read MN-major),
+// each on the 5th-generation tensor cores (tcgen05.mma, kind::f16, BF16
+// operands, FP32 accumulator in tensor memory).  X tiles are streamed by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) through a multi-stage shared-memory
+// ring; one elected thread issues the TMA copies, one issues the MMAs, and
+// tcgen05.commit releases each stage back to the producer.
+//
+// The factor operand is held as a BF16 pair F = F_hi + F_lo (F_hi = bf16(F),
+// F_lo = bf16(F - F_hi)), transposed so that the reduction index is
+// contiguous (K-major B); two MMAs per K step accumulate X F_hi + X F_lo, which
+// keeps about 16 bits of the FP32 factor.  X itself is BF16 (X_hi); the
+// remainder X_lo = bf16(X - X_hi) is applied every few iterations by the
+// same kernels (the correction of the precision form).
+//
+// Per CTA: one 128-row output tile and a range of the reduction index; the
+// FP32 partials of the splits are summed in a fixed order by tc_reduce.
+// The sweep reads X once per product, so at small rank it is bound by HBM
+// bandwidth: algorithmic bytes per sweep = m n * 2.
+#include <cuda.h>
+
+#include "internal.h"
+
+namespace enmf {
+
+namespace tc {
+
+constexpr int TILE = 128;     // output rows per CTA (UMMA M)
+constexpr int KB_XV = 64;     // reduction columns per stage, X V
+constexpr int KB_XT = 128;    // reduction rows per stage, X^T U
+constexpr int THREADS = 128;  // 4 warps: producer (w0), MMA (w1), epilogue (all)
+constexpr long long WAIT_BUDGET = 4000000000LL;  // cycles (~2 s)
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false (and ERR_TIMEOUT recorded) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > WAIT_BUDGET) {
+      atomicOr(err, ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                         int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4}], [%2];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, 128-byte swizzle (tcgen05 layout):
+// start address, leading / stride byte offsets (all >> 4), version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// MODE 0: C = X V (rows_out = m, reduction over n).
+// MODE 1: C = X^T U (rows_out = n, reduction over m).
+// Bt_hi / Bt_lo: the factor transposed (RP x red, BF16).  part: FP32
+// partials [split][rows_out][r].
+template <int MODE, int RP>
+__global__ void __launch_bounds__(THREADS, 1)
+sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapBh,
+                const __grid_constant__ CUtensorMap mapBl, int64_t rows_out, int64_t red,
+                int64_t red_per_split, int r, int stages, float* __restrict__ part, int* err) {
+  constexpr int KB = MODE == 0 ? KB_XV : KB_XT;
+  constexpr uint32_t A_BYTES = TILE * KB * 2;                 // 16 KB or 32 KB
+  constexpr uint32_t B_BYTES = RP * KB * 2;                   // one of hi / lo
+  constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
+  constexpr uint32_t IDESC = idesc_bf16(TILE, RP, MODE);
+  constexpr uint32_t TMEM_COLS = RP <= 32 ? 32 : (RP <= 64 ? 64 : 128);
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[8];
+  __shared__ __align__(8) uint64_t empty_bar[8];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int aborted;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t tile0 = (int64_t)blockIdx.x * TILE;
+  const int64_t kb0 = (int64_t)blockIdx.y * red_per_split;
+  const int64_t kb1 = min(red, kb0 + red_per_split);
+  const int nkb = kb1 > kb0 ? (int)((kb1 - kb0 + KB - 1) / KB) : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    aborted = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % stages;
+      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u, err)) {
+        aborted = 1;
+        break;
+      }
+      uint8_t* sa = smem + (size_t)s * STAGE;
+      uint8_t* sbh = sa + A_BYTES;
+      uint8_t* sbl = sbh + B_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE);
+      const int k0 = (int)(kb0 + (int64_t)kb * KB);
+      if (MODE == 0) {
+        tma_load(sa, &mapX, &full_bar[s], k0, (int)tile0);
+        tma_load(sbh, &mapBh, &full_bar[s], k0, 0);
+        tma_load(sbl, &mapBl, &full_bar[s], k0, 0);
+      } else {
+        tma_load(sa, &mapX, &full_bar[s], (int)tile0, k0);
+        tma_load(sa + A_BYTES / 2, &mapX, &full_bar[s], (int)tile0 + 64, k0);
+        tma_load(sbh, &mapBh, &full_bar[s], k0, 0);
+        tma_load(sbh + B_BYTES / 2, &mapBh, &full_bar[s], k0 + 64, 0);
+        tma_load(sbl, &mapBl, &full_bar[s], k0, 0);
+        tma_load(sbl + B_BYTES / 2, &mapBl, &full_bar[s], k0 + 64, 0);
+      }
+      ++issued;
+    }
+    if (aborted) {
+      // let the copies already issued land before the CTA exits
+      for (int kb = issued - stages < 0 ? 0 : issued - stages; kb < issued; ++kb)
+        mbar_wait(&full_bar[kb % stages], (uint32_t)(kb / stages) & 1u, err);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // --------------------------------------------------------- MMA issue
+    uint32_t accum = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % stages;
+      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
+      if (!mbar_wait(&full_bar[s], ph, err)) {
+        aborted = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = saddr(smem + (size_t)s * STAGE);
+      const uint32_t bh0 = a0 + A_BYTES;
+      const uint32_t bl0 = bh0 + B_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < KB / 16; ++kk) {
+        uint64_t da, dbh, dbl;
+        if (MODE == 0) {
+          // K-major A and B: 16 elements = 32 bytes along the swizzled row
+          da = sdesc(a0 + kk * 32, 16, 1024);
+          dbh = sdesc(bh0 + kk * 32, 16, 1024);
+          dbl = sdesc(bl0 + kk * 32, 16, 1024);
+        } else {
+          // MN-major A: 16 reduction rows = 2 x 1024 B; two 64-wide atoms
+          // along the output index, 16 KB apart.  B: 64-element K atoms.
+          da = sdesc(a0 + kk * 2048, A_BYTES / 2, 1024);
+          const uint32_t boff = (uint32_t)(kk / 4) * (B_BYTES / 2) + (uint32_t)(kk % 4) * 32;
+          dbh = sdesc(bh0 + boff, 16, 1024);
+          dbl = sdesc(bl0 + boff, 16, 1024);
+        }
+        mma_bf16(tmem, da, dbh, IDESC, accum);
+        mma_bf16(tmem, da, dbl, IDESC, 1u);
+        accum = 1u;
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&done_bar);
+  }
+  __syncthreads();
+  // ------------------------------------------------------------ epilogue
+  // the MMA thread always commits done_bar, so wait for it (bounded) even
+  // after an abort: no MMA may still be writing tensor memory at dealloc
+  bool ok = nkb > 0 ? mbar_wait(&done_bar, 0, err) : true;
+  ok = ok && aborted == 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int64_t row = tile0 + warp * 32 + lane;
+  float* out = part + ((int64_t)blockIdx.y * rows_out + row) * r;
+#pragma unroll
+  for (int c0 = 0; c0 < RP; c0 += 16) {
+    float v[16];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+    tmem_ld16(taddr, v);
+    if (row < rows_out) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j < r) out[c0 + j] = (ok && nkb > 0) ? v[j] : 0.0f;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// F (rows x r, FP32) -> F^T as a BF16 pair (RP x ldt): hi = bf16(F),
+// lo = bf16(F - hi).  Rows r..RP-1 of the outputs stay zero.
+__global__ void split_transpose_kernel(const float* __restrict__ F, int64_t rows, int r,
+                                       __nv_bfloat16* __restrict__ hi,
+                                       __nv_bfloat16* __restrict__ lo, int64_t ldt) {
+  __shared__ float tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int64_t i = i0 + q;
+    const int j = j0 + threadIdx.x;
+    tile[q][threadIdx.x] = (i < rows && j < r) ? F[i * r + j] : 0.0f;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int j = j0 + q;
+    const int64_t i = i0 + threadIdx.x;
+    if (j < r && i < rows) {
+      const float v = tile[threadIdx.x][q];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hi[(int64_t)j * ldt + i] = h;
+      lo[(int64_t)j * ldt + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+  }
+}
+
+// C[i][j] = sum_s part[s][i][j] (+ corr[i][j]), FP32, fixed split order.
+__global__ void tc_reduce_kernel(const float* __restrict__ part, int splits, int64_t rows, int r,
+                                 const float* __restrict__ corr, float* __restrict__ C) {
+  const int64_t total = rows * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = part[e];
+    for (int q = 1; q < splits; ++q) s += part[(int64_t)q * total + e];
+    if (corr) s += corr[e];
+    C[e] = s;
+  }
+}
+
+// X (FP32, m x n, ldx) -> X_hi = bf16(X), X_lo = bf16(X - X_hi), both m x ldh.
+__global__ void split_x_kernel(const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
+                               __nv_bfloat16* __restrict__ xh, __nv_bfloat16* __restrict__ xl,
+                               int64_t ldh, int* err) {
+  const int64_t total = m * n;
+  int bad = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    const float v = X[i * ldx + j];
+    if (!(v >= 0.0f) || isinf(v)) bad = 1;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    xh[i * ldh + j] = h;
+    xl[i * ldh + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+  if (bad) atomicOr(err, ERR_DOMAIN);
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------- host
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D BF16 tensor map over a row-major (rows x cols, ld elements) array with a
+// box of box_cols x box_rows and 128-byte swizzle.  Out-of-range reads give 0.
+bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                 int box_cols, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if (((uintptr_t)base & 15) || ((ld * 2) & 15)) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int tc_rank_pad(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : (r <= 48 ? 48 : 64)); }
+
+int tc_splits(int64_t rows_out, int64_t red, int kb, int num_sms) {
+  int64_t tiles = (rows_out + tc::TILE - 1) / tc::TILE;
+  int64_t s = (2LL * num_sms + tiles - 1) / tiles;
+  int64_t max_s = (red + 4 * kb - 1) / (4 * kb);   // at least 4 stages of work per split
+  if (s > max_s) s = max_s;
+  if (s > 64) s = 64;
+  if (s < 1) s = 1;
+  return (int)s;
+}
+
+static size_t tc_smem(int mode, int rp, int stages) {
+  const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
+  return (size_t)stages * ((size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2) + 1024;
+}
+
+static int tc_stages(int mode, int rp) {
+  const size_t budget = 200 * 1024;
+  const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
+  const size_t st = (size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2;
+  int s = (int)((budget - 1024) / st);
+  return s > 8 ? 8 : (s < 2 ? 2 : s);
+}
+
+template <int MODE, int RP>
+static void launch_tc(const void* mapX, const void* mapBh, const void* mapBl, int64_t rows_out,
+                      int64_t red, int r, float* part, int splits, int* err, cudaStream_t s) {
+  const int kb = MODE == 0 ? tc::KB_XV : tc::KB_XT;
+  int64_t per = (red + splits - 1) / splits;
+  per = ((per + kb - 1) / kb) * kb;
+  const int nsplit = (int)((red + per - 1) / per);
+  const int stages = tc_stages(MODE, RP);
+  const size_t smem = tc_smem(MODE, RP, stages);
+  cudaFuncSetAttribute(tc::sweep_tc_kernel<MODE, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  dim3 grid((unsigned)((rows_out + tc::TILE - 1) / tc::TILE), (unsigned)nsplit);
+  tc::sweep_tc_kernel<MODE, RP><<<grid, tc::THREADS, smem, s>>>(
+      *reinterpret_cast<const CUtensorMap*>(mapX), *reinterpret_cast<const CUtensorMap*>(mapBh),
+      *reinterpret_cast<const CUtensorMap*>(mapBl), rows_out, red, per, r, stages, part, err);
+}
+
+// Effective number of splits after rounding the split length to whole stages.
+int tc_nsplit(int64_t red, int splits, int mode) {
+  const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
+  int64_t per = (red + splits - 1) / splits;
+  per = ((per + kb - 1) / kb) * kb;
+  return (int)((red + per - 1) / per);
+}
+
+void launch_tc_sweep(int mode, int rp, const void* mapX, const void* mapBh, const void* mapBl,
+                     int64_t rows_out, int64_t red, int r, float* part, int splits, int* err,
+                     cudaStream_t s) {
+  note_launch(1);
+#define TCL(M, P) launch_tc<M, P>(mapX, mapBh, mapBl, rows_out, red, r, part, splits, err, s)
+  if (mode == 0) {
+    if (rp == 16) TCL(0, 16); else if (rp == 32) TCL(0, 32); else if (rp == 48) TCL(0, 48); else TCL(0, 64);
+  } else {
+    if (rp == 16) TCL(1, 16); else if (rp == 32) TCL(1, 32); else if (rp == 48) TCL(1, 48); else TCL(1, 64);
+  }
+#undef TCL
+}
+
+void launch_split_transpose(const float* F, int64_t rows, int r, void* hi, void* lo, int64_t ldt,
+                            cudaStream_t s) {
+  note_launch(1);
+  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((r + 31) / 32));
+  tc::split_transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(F, rows, r, (__nv_bfloat16*)hi,
+                                                           (__nv_bfloat16*)lo, ldt);
+}
+
+void launch_tc_reduce(const float* part, int splits, int64_t rows, int r, const float* corr,
+                      float* C, cudaStream_t s) {
+  note_launch(1);
+  int64_t total = rows * r;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  tc::tc_reduce_kernel<<<blocks, 256, 0, s>>>(part, splits, rows, r, corr, C);
+}
+
+void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh, void* xl,
+                    int64_t ldh, int* err, cudaStream_t s) {
+  note_launch(1);
+  int64_t total = m * n;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 8192) blocks = 8192;
+  tc::split_x_kernel<<<blocks, 256, 0, s>>>(X, m, n, ldx, (__nv_bfloat16*)xh, (__nv_bfloat16*)xl,
+                                            ldh, err);
+}
+
+}  // namespace enmf

@@ -16,7 +16,12 @@ _XDT = {torch.float64: B.ENMF_F64, torch.float32: B.ENMF_F32, torch.bfloat16: B.
         torch.float16: B.ENMF_F16}
 
 
-def problem_for(X, r, f_dtype=None):
+def problem_for(X, r, f_dtype=None, stream=None):
+    """C problem descriptor for X (m x n, row-major) at rank r.
+
+    stream=torch.bfloat16 selects the precision form: the iteration's X sweeps
+    run on the tensor cores over a BF16 copy of X (with the X_lo correction
+    when X is FP32)."""
     if X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a row-major matrix (unit column stride)")
     xdt = _XDT.get(X.dtype)
@@ -25,7 +30,8 @@ def problem_for(X, r, f_dtype=None):
     if f_dtype is None:
         f_dtype = torch.float64 if X.dtype == torch.float64 else torch.float32
     fdt = B.ENMF_F64 if f_dtype == torch.float64 else B.ENMF_F32
-    return B.enmf_problem(X.shape[0], X.shape[1], X.stride(0), r, xdt, fdt), f_dtype
+    sdt = B.ENMF_BF16 if stream == torch.bfloat16 else 0
+    return B.enmf_problem(X.shape[0], X.shape[1], X.stride(0), r, xdt, fdt, sdt), f_dtype
 
 
 @dataclass
@@ -43,14 +49,16 @@ class SolveResult:
 class Solver:
     """eNMF on one matrix: svd_init -> rotate -> iterate (Algorithm 3)."""
 
-    def __init__(self, X: torch.Tensor, r: int, f_dtype=None, stream=None):
+    def __init__(self, X: torch.Tensor, r: int, f_dtype=None, stream=None, x_stream=None):
         if not X.is_cuda:
             raise ValueError("X must be a CUDA tensor")
         self.X = X
         self.r = r
-        self.problem, self.f_dtype = problem_for(X, r, f_dtype)
+        self.problem, self.f_dtype = problem_for(X, r, f_dtype, x_stream)
         self.stream = stream
         self.ctx = B.enmf_create(self.problem, stream)
+        if x_stream == torch.bfloat16:
+            B.enmf_stage_x(self.ctx, X)
         dev = X.device
         self.U = torch.zeros(X.shape[0], r, dtype=self.f_dtype, device=dev)
         self.V = torch.zeros(X.shape[1], r, dtype=self.f_dtype, device=dev)
@@ -87,13 +95,22 @@ class Solver:
     def kkt(self):
         return B.enmf_kkt(self.ctx, self.X, self.U, self.V)
 
+    def sweep(self, U=None, V=None, exact=1):
+        """(X V, X^T U) for the given (or current) factors, in this form."""
+        U = self.U if U is None else U
+        V = self.V if V is None else V
+        XV = torch.empty(self.X.shape[0], self.r, dtype=self.f_dtype, device=self.X.device)
+        XtU = torch.empty(self.X.shape[1], self.r, dtype=self.f_dtype, device=self.X.device)
+        B.enmf_sweep(self.ctx, self.X, U, V, XV, XtU, exact)
+        return XV, XtU
+
     def pbcd_counts(self):
         return B.enmf_pbcd_counts(self.ctx)
 
 
-def solve(X: torch.Tensor, r: int, n_iter: int, f_dtype=None) -> SolveResult:
+def solve(X: torch.Tensor, r: int, n_iter: int, f_dtype=None, x_stream=None) -> SolveResult:
     """Algorithm 3 end to end on the GPU."""
-    s = Solver(X, r, f_dtype)
+    s = Solver(X, r, f_dtype, x_stream=x_stream)
     try:
         si = s.svd_init()
         ri = s.rotate()

@@ -1,0 +1,142 @@
+"""Tensor-core sweeps (precision form) through the C ABI.
+
+enmf_sweep in the BF16 stream form computes X V and X^T U on tcgen05 from
+X_hi = bf16(X) (+ X_lo = bf16(X - X_hi) when exact) and the factor as a BF16
+pair.  The reference is the same BF16 decomposition multiplied in FP64 on the
+CPU, so the only difference allowed is FP32 accumulation: relative error
+(to the largest output entry) below 2e-6.  Against the FP32 product of the
+undecomposed data the pair representation keeps ~16 bits: below 5e-5.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import enmf_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2605_19325_gb300 import build
+    build.build()
+
+
+def _bf16_pair(a32):
+    t = torch.as_tensor(a32, dtype=torch.float32)
+    hi = t.to(torch.bfloat16).to(torch.float32)
+    lo = (t - hi).to(torch.bfloat16).to(torch.float32)
+    return hi.double().numpy(), lo.double().numpy()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+SHAPES = [(300, 200, 5), (1000, 700, 32), (513, 1031, 49), (128, 128, 16), (1025, 4097, 64),
+          (129, 3, 2), (1, 64, 1), (4100, 260, 20)]
+
+
+@pytest.mark.parametrize("m,n,r", SHAPES)
+def test_tc_sweep_matches_decomposed_reference(m, n, r):
+    from paper_2605_19325_gb300.solver import Solver
+    rng = np.random.default_rng(m * 7 + n)
+    X = rng.random((m, n)).astype(np.float32) * 3.0
+    U = rng.random((m, r)).astype(np.float32)
+    V = rng.random((n, r)).astype(np.float32)
+    Xt = torch.as_tensor(X, device="cuda")
+    s = Solver(Xt, r, x_stream=torch.bfloat16)
+    Ud = torch.as_tensor(U, device="cuda")
+    Vd = torch.as_tensor(V, device="cuda")
+    xh, xl = _bf16_pair(X)
+    uh, ul = _bf16_pair(U)
+    vh, vl = _bf16_pair(V)
+    for exact in (1, 0):
+        XV, XtU = s.sweep(Ud, Vd, exact=exact)
+        torch.cuda.synchronize()
+        Xe = xh + xl if exact else xh
+        ref_xv = Xe @ (vh + vl)
+        ref_xtu = Xe.T @ (uh + ul)
+        assert _rel(XV.double().cpu().numpy(), ref_xv) < 2e-6
+        assert _rel(XtU.double().cpu().numpy(), ref_xtu) < 2e-6
+    XV, XtU = s.sweep(Ud, Vd, exact=1)
+    assert _rel(XV.double().cpu().numpy(), X.astype(np.float64) @ V) < 5e-5
+    assert _rel(XtU.double().cpu().numpy(), X.astype(np.float64).T @ U) < 5e-5
+    s.close()
+
+
+def test_tc_sweep_twice_is_deterministic():
+    from paper_2605_19325_gb300.solver import Solver
+    rng = np.random.default_rng(3)
+    X = rng.random((2000, 1500)).astype(np.float32)
+    Xt = torch.as_tensor(X, device="cuda")
+    s = Solver(Xt, 24, x_stream=torch.bfloat16)
+    U = torch.rand(2000, 24, device="cuda")
+    V = torch.rand(1500, 24, device="cuda")
+    a = s.sweep(U, V)
+    b = s.sweep(U, V)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    s.close()
+
+
+def test_unstaged_x_is_rejected():
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+    X = torch.rand(256, 128, device="cuda")
+    s = Solver(X, 8, x_stream=torch.bfloat16)
+    other = torch.rand(256, 128, device="cuda")
+    with pytest.raises(B.EnmfError) as ei:
+        B.enmf_sweep(s.ctx, other, s.U, s.V, torch.empty(256, 8, device="cuda"), None, 1)
+    assert ei.value.code == 8
+    s.close()
+
+
+def test_precision_form_error_gap_small():
+    """The BF16-stream form with X_lo correction: final relative error within
+    1e-3 (relative) of the FP64 oracle's (the stated target), and in practice
+    within 1e-5."""
+    X, r = synth.config_small(0)
+    res = O.enmf(X, r, 200)
+    from paper_2605_19325_gb300.solver import Solver
+    Xt = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+    s = Solver(Xt, r, x_stream=torch.bfloat16)
+    s.svd_init()
+    s.rotate()
+    tr, info = s.iterate(200, reset=1)
+    _, rel, _ = s.residual()
+    ref = O.rel_err(X, res.U, res.V)
+    gap = abs(rel - ref) / ref
+    assert gap < 1e-3, gap
+    assert gap < 1e-5, gap
+    s.close()
+
+
+def test_precision_form_image_stack_sampled():
+    """Image-stack workload (10304 x 4096, r = 49, padded to 64 on the tensor
+    cores): one alternation from the GPU state, checked row by row against the
+    oracle's HALS update on sampled rows using the exact FP32 X."""
+    X, r = synth.image_stack(seed=0, dtype=np.float32)
+    from paper_2605_19325_gb300.solver import Solver
+    Xt = torch.as_tensor(X, device="cuda")
+    s = Solver(Xt, r, x_stream=torch.bfloat16)
+    s.svd_init()
+    s.rotate()
+    tr, info = s.iterate(12, reset=1)
+    assert np.all(np.isfinite(tr.cpu().numpy()))
+    U0 = s.U.double().cpu().numpy()
+    V0 = s.V.double().cpu().numpy()
+    s.iterate(1, correct_every=1)
+    U1 = s.U.double().cpu().numpy()
+    G = V0.T @ V0
+    rows = np.random.default_rng(0).choice(X.shape[0], 10, replace=False)
+    X64 = X.astype(np.float64)
+    for i in rows:
+        a = X64[i] @ V0
+        u = U0[i].copy()
+        for j in range(r):
+            if G[j, j] > 0:
+                u[j] = max(0.0, u[j] + (a[j] - u @ G[:, j]) / G[j, j])
+        np.testing.assert_allclose(U1[i], u, rtol=2e-4, atol=2e-4 * np.abs(U1).max())
+    s.close()
