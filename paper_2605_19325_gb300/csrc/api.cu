@@ -64,7 +64,8 @@ struct enmf_ctx {
   void* own_xh;
   void* vth; void* vtl;          // V^T as a BF16 pair (rp x ldn)
   void* uth; void* utl;          // U^T as a BF16 pair (rp x ldm)
-  float* tcpart;                 // split partials
+  float* tcpart;                 // stream-K partial slots
+  int* tccount;                  // per-tile arrival counters (after the slots)
   float* cv; float* cu;          // X_lo V, X_lo^T U (correction)
   const void* staged_src;        // X pointer the staged copy belongs to
   alignas(64) unsigned char maps[6][128];   // X_hi, X_lo, Vt hi/lo, Ut hi/lo
@@ -139,14 +140,15 @@ static TcPlan tc_plan(const enmf_problem* p, int num_sms) {
   t.ldh = (n + 7) / 8 * 8;
   t.ldn = (n + 7) / 8 * 8;
   t.ldm = (m + 7) / 8 * 8;
-  t.sv = tc_splits(m, n, TC_KB_XV, num_sms);
-  t.st = tc_splits(n, m, TC_KB_XT, num_sms);
-  const int nsv = tc_nsplit(n, t.sv, 0), nst = tc_nsplit(m, t.st, 1);
+  t.sv = tc_grid(m, n, 0, num_sms);
+  t.st = tc_grid(n, m, 1, num_sms);
   t.xh = p->x_dtype == ENMF_F32 ? (size_t)m * t.ldh * 2 : 0;
   t.vt = (size_t)t.rp * t.ldn * 2;
   t.ut = (size_t)t.rp * t.ldm * 2;
-  size_t pv = (size_t)nsv * m * p->r * 4, pt = (size_t)nst * n * p->r * 4;
-  t.part = pv > pt ? pv : pt;
+  // stream-K partial slots: grid x 2 x 128 rows x r, and one arrival counter
+  // per output tile (kept in the same buffer, after the slots)
+  t.part = (size_t)(t.sv > t.st ? t.sv : t.st) * 2 * 128 * p->r * 4 +
+           (size_t)(((m > n ? m : n) + 127) / 128 + 1) * 4;
   t.cv = (size_t)m * p->r * 4;
   t.cu = (size_t)n * p->r * 4;
   auto a = [](size_t b) { return (b + 1023) & ~(size_t)1023; };
@@ -330,6 +332,7 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
     ctx->uth = grab(t.ut);
     ctx->utl = grab(t.ut);
     ctx->tcpart = (float*)grab(t.part);
+    ctx->tccount = (int*)(ctx->tcpart + (size_t)(t.sv > t.st ? t.sv : t.st) * 2 * 128 * p->r);
     ctx->cv = (float*)grab(t.cv);
     ctx->cu = (float*)grab(t.cu);
     bool ok = tc_make_map(ctx->maps[MAP_VH], ctx->vth, t.rp, p->n, t.ldn, 64, t.rp) &&
@@ -637,17 +640,13 @@ static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int
     launch_xv(X, ctx->xdt, p.m, p.n, p.ldx, V, r, r, out, r, ctx->fdt, ctx->splitk, ctx->num_sms, s);
     return;
   }
-  const int ns = tc_nsplit(p.n, ctx->sv, 0);
   launch_split_transpose((const float*)V, p.n, r, ctx->vth, ctx->vtl, ctx->ldn, s);
-  if (corr == 2 && ctx->xl) {
+  if (corr == 2 && ctx->xl)
     launch_tc_sweep(0, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_VH], ctx->maps[MAP_VL], p.m, p.n,
-                    r, ctx->tcpart, ctx->sv, ctx->err, s);
-    launch_tc_reduce(ctx->tcpart, ns, p.m, r, nullptr, ctx->cv, s);
-  }
+                    r, ctx->cv, nullptr, ctx->tcpart, ctx->tccount, ctx->num_sms, ctx->err, s);
   launch_tc_sweep(0, ctx->rp, ctx->maps[MAP_XH], ctx->maps[MAP_VH], ctx->maps[MAP_VL], p.m, p.n, r,
-                  ctx->tcpart, ctx->sv, ctx->err, s);
-  launch_tc_reduce(ctx->tcpart, ns, p.m, r, (corr >= 1 && ctx->xl) ? ctx->cv : nullptr,
-                   (float*)out, s);
+                  (float*)out, (corr >= 1 && ctx->xl) ? ctx->cv : nullptr, ctx->tcpart,
+                  ctx->tccount, ctx->num_sms, ctx->err, s);
 }
 
 static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, int corr) {
@@ -658,17 +657,13 @@ static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, in
     launch_xtu(X, ctx->xdt, p.m, p.n, p.ldx, U, r, r, out, r, ctx->fdt, ctx->splitk, ctx->num_sms, s);
     return;
   }
-  const int ns = tc_nsplit(p.m, ctx->st_split, 1);
   launch_split_transpose((const float*)U, p.m, r, ctx->uth, ctx->utl, ctx->ldm, s);
-  if (corr == 2 && ctx->xl) {
+  if (corr == 2 && ctx->xl)
     launch_tc_sweep(1, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_UH], ctx->maps[MAP_UL], p.n, p.m,
-                    r, ctx->tcpart, ctx->st_split, ctx->err, s);
-    launch_tc_reduce(ctx->tcpart, ns, p.n, r, nullptr, ctx->cu, s);
-  }
+                    r, ctx->cu, nullptr, ctx->tcpart, ctx->tccount, ctx->num_sms, ctx->err, s);
   launch_tc_sweep(1, ctx->rp, ctx->maps[MAP_XH], ctx->maps[MAP_UH], ctx->maps[MAP_UL], p.n, p.m, r,
-                  ctx->tcpart, ctx->st_split, ctx->err, s);
-  launch_tc_reduce(ctx->tcpart, ns, p.n, r, (corr >= 1 && ctx->xl) ? ctx->cu : nullptr,
-                   (float*)out, s);
+                  (float*)out, (corr >= 1 && ctx->xl) ? ctx->cu : nullptr, ctx->tcpart,
+                  ctx->tccount, ctx->num_sms, ctx->err, s);
 }
 
 static enmf_status check_staged(enmf_ctx* ctx, const void* X) {

@@ -168,20 +168,20 @@ void launch_rr_prep(const double* sigma, const double* Ut, const double* Wt, int
 bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
                  int box_cols, int box_rows);
 int tc_rank_pad(int r);
-int tc_splits(int64_t rows_out, int64_t red, int kb, int num_sms);
-int tc_nsplit(int64_t red, int splits, int mode);
-// mode 0: part = X B (rows_out m, red n); mode 1: part = X^T B (rows_out n,
-// red m).  Maps: X (box 64 x 128), B^T hi and lo (box 64 x rp).
+// CTAs of the persistent sweep (<= num_sms); part needs grid x 2 x 128 x r floats.
+int tc_grid(int64_t rows_out, int64_t red, int mode, int num_sms);
+// mode 0: out = X B (+ corr) (rows_out m, red n); mode 1: out = X^T B (+ corr)
+// (rows_out n, red m).  Maps: X (box 64 x 128), B^T hi and lo (box 64 x rp).
+// counters: one int per output tile, zero between launches (the kernel resets
+// the ones it uses).
 void launch_tc_sweep(int mode, int rp, const void* mapX, const void* mapBh, const void* mapBl,
-                     int64_t rows_out, int64_t red, int r, float* part, int splits, int* err,
-                     cudaStream_t s);
+                     int64_t rows_out, int64_t red, int r, float* out, const float* corr,
+                     float* part, int* counters, int num_sms, int* err, cudaStream_t s);
 void launch_split_transpose(const float* F, int64_t rows, int r, void* hi, void* lo, int64_t ldt,
                             cudaStream_t s);
-void launch_tc_reduce(const float* part, int splits, int64_t rows, int r, const float* corr,
-                      float* C, cudaStream_t s);
 void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh, void* xl,
                     int64_t ldh, int* err, cudaStream_t s);
-constexpr int TC_KB_XV = 64, TC_KB_XT = 128;
+constexpr int TC_KB_XV = 128, TC_KB_XT = 128;
 
 // KKT finalisation: combine the two factors' partial measures.
 void launch_kkt_final(const double* pu, const double* pv, double* out, cudaStream_t s);

@@ -14,8 +14,9 @@
 // remainder X_lo = bf16(X - X_hi) is applied every few iterations by the
 // same kernels (the correction of the precision form).
 //
-// Per CTA: one 128-row output tile and a range of the reduction index; the
-// FP32 partials of the splits are summed in a fixed order by tc_reduce.
+// Persistent, stream-K schedule: one CTA per SM, each owning an equal
+// contiguous range of the (output tile, k-block) space; two tensor-memory
+// accumulators let the epilogue of one tile overlap the MMAs of the next.
 // The sweep reads X once per product, so at small rank it is bound by HBM
 // bandwidth: algorithmic bytes per sweep = m n * 2.
 #include <cuda.h>
@@ -27,10 +28,11 @@ namespace enmf {
 namespace tc {
 
 constexpr int TILE = 128;     // output rows per CTA (UMMA M)
-constexpr int KB_XV = 64;     // reduction columns per stage, X V
+constexpr int KB_XV = 128;    // reduction columns per stage, X V (two 64-column boxes)
 constexpr int KB_XT = 128;    // reduction rows per stage, X^T U
-constexpr int THREADS = 128;  // 4 warps: producer (w0), MMA (w1), epilogue (all)
+constexpr int THREADS = 192;  // warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 epilogue
 constexpr long long WAIT_BUDGET = 4000000000LL;  // cycles (~2 s)
+constexpr int MAX_GRID = 256;  // CTAs of the persistent sweep at most
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -127,43 +129,74 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// MODE 0: C = X V (rows_out = m, reduction over n).
-// MODE 1: C = X^T U (rows_out = n, reduction over m).
-// Bt_hi / Bt_lo: the factor transposed (RP x red, BF16).  part: FP32
-// partials [split][rows_out][r].
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Work split (stream-K): the (tile, k-block) space, tile-major, is cut into
+// G contiguous ranges of equal length, one per CTA.  A CTA walks its range as
+// segments of consecutive k-blocks of one tile; a segment that covers a whole
+// tile writes the result directly, the (at most two) partial segments at the
+// ends of a range write FP32 partial slots; the last CTA to finish a cut tile
+// (a per-tile arrival counter) sums its slots in CTA order.
+__host__ __device__ __forceinline__ int64_t sk_begin(int64_t c, int64_t W, int64_t G) {
+  return (c * W) / G;
+}
+
+// MODE 0: C = X V (rows_out = m, reduction over n; A = X tile, K-major).
+// MODE 1: C = X^T U (rows_out = n, reduction over m; A = X tile, MN-major).
+// mapBh / mapBl: the factor transposed as a BF16 pair (RP x red).
+// out (rows_out x r, FP32) receives whole tiles (+ corr when given);
+// part [G][2][TILE][r] receives the partial segments.
 template <int MODE, int RP>
 __global__ void __launch_bounds__(THREADS, 1)
 sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapBh,
-                const __grid_constant__ CUtensorMap mapBl, int64_t rows_out, int64_t red,
-                int64_t red_per_split, int r, int stages, float* __restrict__ part, int* err) {
+                const __grid_constant__ CUtensorMap mapBl, int64_t rows_out, int64_t red, int r,
+                int stages, float* __restrict__ out, const float* __restrict__ corr,
+                float* __restrict__ part, int* __restrict__ counters, int* err) {
   constexpr int KB = MODE == 0 ? KB_XV : KB_XT;
   constexpr uint32_t A_BYTES = TILE * KB * 2;                 // 16 KB or 32 KB
   constexpr uint32_t B_BYTES = RP * KB * 2;                   // one of hi / lo
   constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
   constexpr uint32_t IDESC = idesc_bf16(TILE, RP, MODE);
-  constexpr uint32_t TMEM_COLS = RP <= 32 ? 32 : (RP <= 64 ? 64 : 128);
+  constexpr uint32_t TMEM_COLS = RP <= 32 ? 64 : 128;        // two accumulators
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[8];
   __shared__ __align__(8) uint64_t empty_bar[8];
-  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int aborted;
+  __shared__ int last_cta;
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t tile0 = (int64_t)blockIdx.x * TILE;
-  const int64_t kb0 = (int64_t)blockIdx.y * red_per_split;
-  const int64_t kb1 = min(red, kb0 + red_per_split);
-  const int nkb = kb1 > kb0 ? (int)((kb1 - kb0 + KB - 1) / KB) : 0;
+  const int64_t tiles = (rows_out + TILE - 1) / TILE;
+  const int64_t nkb = (red + KB - 1) / KB;
+  const int64_t W = tiles * nkb;
+  const int64_t G = gridDim.x;
+  const int64_t w0 = sk_begin(blockIdx.x, W, G), w1 = sk_begin(blockIdx.x + 1, W, G);
 
   if (threadIdx.x == 0) {
+    prefetch_map(&mapX);
+    prefetch_map(&mapBh);
+    prefetch_map(&mapBl);
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], 4);
+    }
+    mbar_init(&drain_bar, 1);
     aborted = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -179,99 +212,185 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------------------------------------------------- producer
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % stages;
-      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
-      if (!mbar_wait(&empty_bar[s], ph ^ 1u, err)) {
-        aborted = 1;
-        break;
-      }
-      uint8_t* sa = smem + (size_t)s * STAGE;
-      uint8_t* sbh = sa + A_BYTES;
-      uint8_t* sbl = sbh + B_BYTES;
-      mbar_expect_tx(&full_bar[s], STAGE);
-      const int k0 = (int)(kb0 + (int64_t)kb * KB);
-      if (MODE == 0) {
-        tma_load(sa, &mapX, &full_bar[s], k0, (int)tile0);
-        tma_load(sbh, &mapBh, &full_bar[s], k0, 0);
-        tma_load(sbl, &mapBl, &full_bar[s], k0, 0);
-      } else {
-        tma_load(sa, &mapX, &full_bar[s], (int)tile0, k0);
-        tma_load(sa + A_BYTES / 2, &mapX, &full_bar[s], (int)tile0 + 64, k0);
-        tma_load(sbh, &mapBh, &full_bar[s], k0, 0);
-        tma_load(sbh + B_BYTES / 2, &mapBh, &full_bar[s], k0 + 64, 0);
-        tma_load(sbl, &mapBl, &full_bar[s], k0, 0);
-        tma_load(sbl + B_BYTES / 2, &mapBl, &full_bar[s], k0 + 64, 0);
-      }
-      ++issued;
-    }
-    if (aborted) {
-      // let the copies already issued land before the CTA exits
-      for (int kb = issued - stages < 0 ? 0 : issued - stages; kb < issued; ++kb)
-        mbar_wait(&full_bar[kb % stages], (uint32_t)(kb / stages) & 1u, err);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // --------------------------------------------------------- MMA issue
-    uint32_t accum = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % stages;
-      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
-      if (!mbar_wait(&full_bar[s], ph, err)) {
-        aborted = 1;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = saddr(smem + (size_t)s * STAGE);
-      const uint32_t bh0 = a0 + A_BYTES;
-      const uint32_t bl0 = bh0 + B_BYTES;
-#pragma unroll
-      for (int kk = 0; kk < KB / 16; ++kk) {
-        uint64_t da, dbh, dbl;
-        if (MODE == 0) {
-          // K-major A and B: 16 elements = 32 bytes along the swizzled row
-          da = sdesc(a0 + kk * 32, 16, 1024);
-          dbh = sdesc(bh0 + kk * 32, 16, 1024);
-          dbl = sdesc(bl0 + kk * 32, 16, 1024);
-        } else {
-          // MN-major A: 16 reduction rows = 2 x 1024 B; two 64-wide atoms
-          // along the output index, 16 KB apart.  B: 64-element K atoms.
-          da = sdesc(a0 + kk * 2048, A_BYTES / 2, 1024);
-          const uint32_t boff = (uint32_t)(kk / 4) * (B_BYTES / 2) + (uint32_t)(kk % 4) * 32;
-          dbh = sdesc(bh0 + boff, 16, 1024);
-          dbl = sdesc(bl0 + boff, 16, 1024);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- producer
+      int64_t i = 0;
+      for (int64_t w = w0; w < w1 && !*(volatile int*)&aborted; ++w, ++i) {
+        const int s = (int)(i % stages);
+        const uint32_t ph = (uint32_t)(i / stages) & 1u;
+        if (!mbar_wait(&empty_bar[s], ph ^ 1u, err)) {
+          aborted = 1;
+          break;
         }
-        mma_bf16(tmem, da, dbh, IDESC, accum);
-        mma_bf16(tmem, da, dbl, IDESC, 1u);
-        accum = 1u;
+        const int64_t tile = w / nkb, kb = w % nkb;
+        const int t0 = (int)(tile * TILE);
+        const int k0 = (int)(kb * KB);
+        uint8_t* sa = smem + (size_t)s * STAGE;
+        uint8_t* sbh = sa + A_BYTES;
+        uint8_t* sbl = sbh + B_BYTES;
+        mbar_expect_tx(&full_bar[s], STAGE);
+        if (MODE == 0) {
+          // two adjacent 64-column boxes: 256 contiguous bytes of each X row
+          tma_load(sa, &mapX, &full_bar[s], k0, t0);
+          tma_load(sa + A_BYTES / 2, &mapX, &full_bar[s], k0 + 64, t0);
+          tma_load(sbh, &mapBh, &full_bar[s], k0, 0);
+          tma_load(sbh + B_BYTES / 2, &mapBh, &full_bar[s], k0 + 64, 0);
+          tma_load(sbl, &mapBl, &full_bar[s], k0, 0);
+          tma_load(sbl + B_BYTES / 2, &mapBl, &full_bar[s], k0 + 64, 0);
+        } else {
+          tma_load(sa, &mapX, &full_bar[s], t0, k0);
+          tma_load(sa + A_BYTES / 2, &mapX, &full_bar[s], t0 + 64, k0);
+          tma_load(sbh, &mapBh, &full_bar[s], k0, 0);
+          tma_load(sbh + B_BYTES / 2, &mapBh, &full_bar[s], k0 + 64, 0);
+          tma_load(sbl, &mapBl, &full_bar[s], k0, 0);
+          tma_load(sbl + B_BYTES / 2, &mapBl, &full_bar[s], k0 + 64, 0);
+        }
       }
-      mma_commit(&empty_bar[s]);
+      if (aborted) {
+        // let copies already issued land before the CTA can exit
+        const int64_t issued = i;
+        for (int64_t q = issued - stages < 0 ? 0 : issued - stages; q < issued; ++q)
+          mbar_wait(&full_bar[q % stages], (uint32_t)(q / stages) & 1u, err);
+      }
     }
-    mma_commit(&done_bar);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // --------------------------------------------------------- MMA issue
+      int64_t i = 0;
+      int64_t seg = 0;
+      for (int64_t w = w0; w < w1 && !*(volatile int*)&aborted; ++seg) {
+        const int64_t tile = w / nkb;
+        const int64_t wend = min(w1, (tile + 1) * nkb);
+        const int b = (int)(seg & 1);
+        const uint32_t up = (uint32_t)(seg >> 1) & 1u;
+        if (!mbar_wait(&acce_bar[b], up ^ 1u, err)) {
+          aborted = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dcol = tmem + (uint32_t)(b * RP);
+        uint32_t accum = 0;
+        for (; w < wend; ++w, ++i) {
+          const int s = (int)(i % stages);
+          const uint32_t ph = (uint32_t)(i / stages) & 1u;
+          if (!mbar_wait(&full_bar[s], ph, err)) {
+            aborted = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = saddr(smem + (size_t)s * STAGE);
+          const uint32_t bh0 = a0 + A_BYTES;
+          const uint32_t bl0 = bh0 + B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < KB / 16; ++kk) {
+            uint64_t da, dbh, dbl;
+            if (MODE == 0) {
+              // K-major A and B: 16 elements = 32 bytes along the swizzled row;
+              // K steps 4..7 live in the second 64-column box
+              const uint32_t aoff = (uint32_t)(kk / 4) * (A_BYTES / 2) + (uint32_t)(kk % 4) * 32;
+              const uint32_t boff = (uint32_t)(kk / 4) * (B_BYTES / 2) + (uint32_t)(kk % 4) * 32;
+              da = sdesc(a0 + aoff, 16, 1024);
+              dbh = sdesc(bh0 + boff, 16, 1024);
+              dbl = sdesc(bl0 + boff, 16, 1024);
+            } else {
+              // MN-major A: 16 reduction rows = 2 x 1024 B; two 64-wide atoms
+              // along the output index, 16 KB apart.  B: 64-element K atoms.
+              da = sdesc(a0 + kk * 2048, A_BYTES / 2, 1024);
+              const uint32_t boff = (uint32_t)(kk / 4) * (B_BYTES / 2) + (uint32_t)(kk % 4) * 32;
+              dbh = sdesc(bh0 + boff, 16, 1024);
+              dbl = sdesc(bl0 + boff, 16, 1024);
+            }
+            mma_bf16(dcol, da, dbh, IDESC, accum);
+            mma_bf16(dcol, da, dbl, IDESC, 1u);
+            accum = 1u;
+          }
+          mma_commit(&empty_bar[s]);
+        }
+        if (aborted) break;
+        mma_commit(&accf_bar[b]);
+      }
+      mma_commit(&drain_bar);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    // warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= tile rows)
+    const int quarter = warp & 3;
+    int64_t seg = 0;
+    for (int64_t w = w0; w < w1; ++seg) {
+      const int64_t tile = w / nkb;
+      const int64_t kb_a = w % nkb;
+      const int64_t wend = min(w1, (tile + 1) * nkb);
+      const int64_t kb_b = wend - tile * nkb;
+      w = wend;
+      const int b = (int)(seg & 1);
+      const uint32_t up = (uint32_t)(seg >> 1) & 1u;
+      const bool ok = mbar_wait(&accf_bar[b], up, err);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const bool whole = kb_a == 0 && kb_b == nkb;
+      const int64_t row = tile * TILE + quarter * 32 + lane;
+      float* dst;
+      const float* add = nullptr;
+      if (whole) {
+        dst = out + row * r;
+        if (corr) add = corr + row * r;
+      } else {
+        const int slot = seg == 0 ? 0 : 1;
+        dst = part + (((int64_t)blockIdx.x * 2 + slot) * TILE + quarter * 32 + lane) * r;
+      }
+#pragma unroll
+      for (int c0 = 0; c0 < RP; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * RP + c0), v);
+        if (ok && row < rows_out) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < r) dst[c0 + j] = add ? v[j] + add[c0 + j] : v[j];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar[b]);
+      // (no early exit on a failed wait: the four epilogue warps must all
+      // reach the named barriers below; the failed stores are skipped)
+      if (!whole) {
+        // A tile cut by range boundaries: the last of its CTAs to get here
+        // sums every contributor's slot, in CTA order (so the result does not
+        // depend on which CTA is last), adds corr and writes the tile.
+        __threadfence();
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        int64_t c_lo = blockIdx.x, c_hi = blockIdx.x;
+        while (c_lo > 0 && sk_begin(c_lo, W, G) > tile * nkb) --c_lo;
+        while (c_hi + 1 < G && sk_begin(c_hi + 1, W, G) < (tile + 1) * nkb) ++c_hi;
+        if (warp == 2 && lane == 0) {
+          const int old = atomicAdd(&counters[tile], 1);
+          last_cta = old == (int)(c_hi - c_lo);
+          if (last_cta) counters[tile] = 0;   // ready for the next launch
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (last_cta && row < rows_out) {
+          __threadfence();
+          float acc[RP];
+#pragma unroll
+          for (int j = 0; j < RP; ++j) acc[j] = 0.f;
+          for (int64_t q = c_lo; q <= c_hi; ++q) {
+            const int slot = sk_begin(q, W, G) >= tile * nkb ? 0 : 1;
+            const float* src = part + ((q * 2 + slot) * TILE + quarter * 32 + lane) * r;
+#pragma unroll
+            for (int j = 0; j < RP; ++j)
+              if (j < r) acc[j] += __ldcg(&src[j]);
+          }
+#pragma unroll
+          for (int j = 0; j < RP; ++j)
+            if (j < r) out[row * r + j] = corr ? acc[j] + corr[row * r + j] : acc[j];
+        }
+      }
+    }
   }
   __syncthreads();
-  // ------------------------------------------------------------ epilogue
-  // the MMA thread always commits done_bar, so wait for it (bounded) even
-  // after an abort: no MMA may still be writing tensor memory at dealloc
-  bool ok = nkb > 0 ? mbar_wait(&done_bar, 0, err) : true;
-  ok = ok && aborted == 0;
+  // every MMA the CTA issued has completed before tensor memory is freed
+  mbar_wait(&drain_bar, 0, err);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int64_t row = tile0 + warp * 32 + lane;
-  float* out = part + ((int64_t)blockIdx.y * rows_out + row) * r;
-#pragma unroll
-  for (int c0 = 0; c0 < RP; c0 += 16) {
-    float v[16];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-    tmem_ld16(taddr, v);
-    if (row < rows_out) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (c0 + j < r) out[c0 + j] = (ok && nkb > 0) ? v[j] : 0.0f;
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -306,18 +425,6 @@ __global__ void split_transpose_kernel(const float* __restrict__ F, int64_t rows
   }
 }
 
-// C[i][j] = sum_s part[s][i][j] (+ corr[i][j]), FP32, fixed split order.
-__global__ void tc_reduce_kernel(const float* __restrict__ part, int splits, int64_t rows, int r,
-                                 const float* __restrict__ corr, float* __restrict__ C) {
-  const int64_t total = rows * r;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    float s = part[e];
-    for (int q = 1; q < splits; ++q) s += part[(int64_t)q * total + e];
-    if (corr) s += corr[e];
-    C[e] = s;
-  }
-}
 
 // X (FP32, m x n, ldx) -> X_hi = bf16(X), X_lo = bf16(X - X_hi), both m x ldh.
 __global__ void split_x_kernel(const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
@@ -378,16 +485,6 @@ bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_
 
 int tc_rank_pad(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : (r <= 48 ? 48 : 64)); }
 
-int tc_splits(int64_t rows_out, int64_t red, int kb, int num_sms) {
-  int64_t tiles = (rows_out + tc::TILE - 1) / tc::TILE;
-  int64_t s = (2LL * num_sms + tiles - 1) / tiles;
-  int64_t max_s = (red + 4 * kb - 1) / (4 * kb);   // at least 4 stages of work per split
-  if (s > max_s) s = max_s;
-  if (s > 64) s = 64;
-  if (s < 1) s = 1;
-  return (int)s;
-}
-
 static size_t tc_smem(int mode, int rp, int stages) {
   const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
   return (size_t)stages * ((size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2) + 1024;
@@ -401,36 +498,36 @@ static int tc_stages(int mode, int rp) {
   return s > 8 ? 8 : (s < 2 ? 2 : s);
 }
 
+// Grid of the persistent sweep: one CTA per SM, fewer when there are fewer
+// k-blocks than SMs.
+int tc_grid(int64_t rows_out, int64_t red, int mode, int num_sms) {
+  const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
+  const int64_t W = ((rows_out + tc::TILE - 1) / tc::TILE) * ((red + kb - 1) / kb);
+  int64_t g = W < num_sms ? W : num_sms;
+  return (int)(g > tc::MAX_GRID ? tc::MAX_GRID : g);
+}
+
 template <int MODE, int RP>
 static void launch_tc(const void* mapX, const void* mapBh, const void* mapBl, int64_t rows_out,
-                      int64_t red, int r, float* part, int splits, int* err, cudaStream_t s) {
-  const int kb = MODE == 0 ? tc::KB_XV : tc::KB_XT;
-  int64_t per = (red + splits - 1) / splits;
-  per = ((per + kb - 1) / kb) * kb;
-  const int nsplit = (int)((red + per - 1) / per);
+                      int64_t red, int r, float* out, const float* corr, float* part,
+                      int* counters, int grid, int* err, cudaStream_t s) {
   const int stages = tc_stages(MODE, RP);
   const size_t smem = tc_smem(MODE, RP, stages);
   cudaFuncSetAttribute(tc::sweep_tc_kernel<MODE, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
-  dim3 grid((unsigned)((rows_out + tc::TILE - 1) / tc::TILE), (unsigned)nsplit);
   tc::sweep_tc_kernel<MODE, RP><<<grid, tc::THREADS, smem, s>>>(
       *reinterpret_cast<const CUtensorMap*>(mapX), *reinterpret_cast<const CUtensorMap*>(mapBh),
-      *reinterpret_cast<const CUtensorMap*>(mapBl), rows_out, red, per, r, stages, part, err);
-}
-
-// Effective number of splits after rounding the split length to whole stages.
-int tc_nsplit(int64_t red, int splits, int mode) {
-  const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
-  int64_t per = (red + splits - 1) / splits;
-  per = ((per + kb - 1) / kb) * kb;
-  return (int)((red + per - 1) / per);
+      *reinterpret_cast<const CUtensorMap*>(mapBl), rows_out, red, r, stages, out, corr, part,
+      counters, err);
 }
 
 void launch_tc_sweep(int mode, int rp, const void* mapX, const void* mapBh, const void* mapBl,
-                     int64_t rows_out, int64_t red, int r, float* part, int splits, int* err,
-                     cudaStream_t s) {
+                     int64_t rows_out, int64_t red, int r, float* out, const float* corr,
+                     float* part, int* counters, int num_sms, int* err, cudaStream_t s) {
+  const int grid = tc_grid(rows_out, red, mode, num_sms);
   note_launch(1);
-#define TCL(M, P) launch_tc<M, P>(mapX, mapBh, mapBl, rows_out, red, r, part, splits, err, s)
+#define TCL(M, P) \
+  launch_tc<M, P>(mapX, mapBh, mapBl, rows_out, red, r, out, corr, part, counters, grid, err, s)
   if (mode == 0) {
     if (rp == 16) TCL(0, 16); else if (rp == 32) TCL(0, 32); else if (rp == 48) TCL(0, 48); else TCL(0, 64);
   } else {
@@ -445,15 +542,6 @@ void launch_split_transpose(const float* F, int64_t rows, int r, void* hi, void*
   dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((r + 31) / 32));
   tc::split_transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(F, rows, r, (__nv_bfloat16*)hi,
                                                            (__nv_bfloat16*)lo, ldt);
-}
-
-void launch_tc_reduce(const float* part, int splits, int64_t rows, int r, const float* corr,
-                      float* C, cudaStream_t s) {
-  note_launch(1);
-  int64_t total = rows * r;
-  int blocks = (int)((total + 255) / 256);
-  if (blocks > 4096) blocks = 4096;
-  tc::tc_reduce_kernel<<<blocks, 256, 0, s>>>(part, splits, rows, r, corr, C);
 }
 
 void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh, void* xl,
