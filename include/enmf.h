@@ -244,6 +244,62 @@ enmf_status enmf_profile_read(enmf_ctx* ctx, double* sweep_ms, int64_t* sweeps, 
 enmf_status enmf_probe_fma_peak(int32_t dtype, double* flops_per_s);
 long long enmf_launch_count(void);
 
+/* ---- Allocation-free residual (no counterpart in the paper) --------------
+ * The paper has no such call.  enmf_residual_noalloc computes the three
+ * numbers of enmf_residual with direct = 1 (Eq. 1):
+ *   out3[0] = f = 1/2 ||X - U V^T||_F^2,
+ *   out3[1] = ||X - U V^T||_F / ||X||_F   (0 when ||X|| = 0),
+ *   out3[2] = ||X||_F^2,
+ * without a context and without allocating any memory.
+ *
+ * Who needs it.  Two kinds of callers cannot allocate, so they cannot use
+ * enmf_create.  First, a caller whose device memory is already committed: a
+ * large X and a running solve's workspace can fill the device, and then any
+ * allocation may fail in the middle of a run.  Second, a caller that must not
+ * stall other streams: cudaFree synchronises the whole device, and a caching
+ * allocator may free memory at any time.  An example is a monitor that checks
+ * factors written by a solve on another stream while that solve runs.
+ *
+ * Arguments.  X is m x n, row-major, with row stride ldx >= n elements, of
+ * type x_dtype.  U (m x r) and V (n x r) are dense, row-major, of type f_dtype.
+ * The forms are those of enmf_problem: ENMF_F64 factors need ENMF_F64 X;
+ * ENMF_F32 factors take X of type ENMF_F32, ENMF_BF16 or ENMF_F16.  X, U, V and
+ * out3 are DEVICE pointers on the current device, owned by the caller.  out3
+ * receives 3 doubles.  stream is a cudaStream_t passed as void* (NULL = the
+ * legacy default stream).  The call only enqueues work and does not
+ * synchronise: out3 holds the result once the stream reaches the work.  The
+ * sign of X is not checked.  m = 0 or n = 0 gives {0, 0, 0}.  The arithmetic
+ * matches enmf_residual with direct = 1 except for the order of the FP64 sums.
+ *
+ * Limits.  m <= ENMF_RESIDUAL_NOALLOC_MAX_ROWS (4096 panels of 64 rows each)
+ * and 1 <= r <= ENMF_MAX_RANK.  A larger m, or any other bad argument, returns
+ * ENMF_EINVAL before anything is enqueued.  The current device index must be
+ * below 64 (ENMF_EINVAL otherwise).
+ *
+ * Scratch.  The call sums through one fixed array in the library's static
+ * device memory: 65,792 bytes per device (two FP64 sums per panel and one
+ * arrival counter).  The counter must start at zero, so each call clears it
+ * on `stream` before its kernel.  Nothing else needs clearing.
+ *
+ * Set-up.  The first call on each device, made with that device current, does
+ * one-time set-up: it looks up the scratch array's address and loads the
+ * kernels.  Make that first call before any stream capture.  Later calls only
+ * enqueue a memset and one kernel.
+ *
+ * Concurrency.  All calls on one device share the same scratch.  Calls that
+ * overlap on the device race on it and give wrong results.  Overlap happens
+ * with calls on different streams that no event orders, or with calls from
+ * several host threads.  Put such calls on one stream, or order them with
+ * events.
+ *
+ * Errors: ENMF_EINVAL as above; ENMF_ECUDA if the set-up, the memset or the
+ * launch fails.  A fault while the kernel runs shows up at the caller's next
+ * synchronisation. */
+#define ENMF_RESIDUAL_NOALLOC_MAX_ROWS 262144
+enmf_status enmf_residual_noalloc(const void* X, int32_t x_dtype, int64_t m, int64_t n,
+                                  int64_t ldx, const void* U, const void* V, int32_t r,
+                                  int32_t f_dtype, double* out3, void* stream);
+
 /* Library version string. */
 const char* enmf_version(void);
 

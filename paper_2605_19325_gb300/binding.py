@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libenmf.so")
 
 ENMF_F64, ENMF_F32, ENMF_BF16, ENMF_F16 = 0, 1, 2, 3
 ENMF_MAX_RANK = 64
+ENMF_RESIDUAL_NOALLOC_MAX_ROWS = 262144
 
 STATUS = {0: "ok", 1: "EINVAL", 2: "EDOMAIN", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT",
           6: "ENOTCONV", 7: "EBUSY", 8: "ESTATE"}
@@ -94,6 +95,9 @@ _SIGS = {
                                     C.c_int32]),
     "enmf_probe_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
     "enmf_launch_count": (C.c_longlong, []),
+    "enmf_residual_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
+                                        C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                        C.c_void_p]),
     "enmf_version": (C.c_char_p, []),
 }
 
@@ -238,3 +242,36 @@ def enmf_solve(ctx, X_ptr, U_ptr, V_ptr, n_iter):
     check(lib().enmf_solve(ctx, C.c_void_p(X_ptr), C.c_void_p(U_ptr), C.c_void_p(V_ptr),
                            n_iter, None, None, None, out), "enmf_solve")
     return out[0], out[1], out[2]
+
+
+_TORCH_DT = None
+
+
+def _dtype_code(t):
+    global _TORCH_DT
+    if _TORCH_DT is None:
+        import torch
+        _TORCH_DT = {torch.float64: ENMF_F64, torch.float32: ENMF_F32,
+                     torch.bfloat16: ENMF_BF16, torch.float16: ENMF_F16}
+    if t.dtype not in _TORCH_DT:
+        raise ValueError(f"unsupported dtype {t.dtype}")
+    return _TORCH_DT[t.dtype]
+
+
+def enmf_residual_noalloc(X, U, V, out3, stream=None):
+    """Allocation-free residual into the device tensor out3 (3 doubles).
+
+    Enqueues on `stream` (default: the current torch stream) and returns
+    without synchronising.  X is (m, n) with unit column stride; U (m, r) and
+    V (n, r) are contiguous."""
+    m, n = X.shape
+    r = U.shape[1]
+    if X.stride(1) != 1 and n > 1:
+        raise ValueError("X must be a row-major matrix (unit column stride)")
+    code = lib().enmf_residual_noalloc(
+        _ptr(X), _dtype_code(X), m, n, max(X.stride(0), n), _ptr(U), _ptr(V), r,
+        _dtype_code(U), _ptr(out3), _stream(stream))
+    if code == 1 and m > ENMF_RESIDUAL_NOALLOC_MAX_ROWS:
+        raise EnmfError(code, f"enmf_residual_noalloc: m = {m} exceeds "
+                              f"ENMF_RESIDUAL_NOALLOC_MAX_ROWS = {ENMF_RESIDUAL_NOALLOC_MAX_ROWS}")
+    check(code, "enmf_residual_noalloc")
