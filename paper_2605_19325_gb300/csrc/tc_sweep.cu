@@ -314,8 +314,18 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    // warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= tile rows)
+    // Warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= tile rows).
+    // The accumulator passes through a shared-memory tile with an odd row
+    // stride (conflict-free), so that every global access below is a flat,
+    // coalesced run: a 128-row tile of a dense rows x r array (out, corr, a
+    // partial slot) is one contiguous block of 128 r floats.
+    constexpr int SS = RP + 1;
+    float* stg = reinterpret_cast<float*>(smem + (size_t)stages * STAGE);
     const int quarter = warp & 3;
+    const int lrow = quarter * 32 + lane;
+    const int et = threadIdx.x - 64;                 // 0..127
+    const int q128 = 128 / r, r128 = 128 % r;        // a flat step of 128 as (rows, cols)
+    const int rr0 = et / r, cc0 = et % r;
     int64_t seg = 0;
     for (int64_t w = w0; w < w1; ++seg) {
       const int64_t tile = w / nkb;
@@ -328,31 +338,45 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
       const bool ok = mbar_wait(&accf_bar[b], up, err);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const bool whole = kb_a == 0 && kb_b == nkb;
-      const int64_t row = tile * TILE + quarter * 32 + lane;
-      float* dst;
-      const float* add = nullptr;
-      if (whole) {
-        dst = out + row * r;
-        if (corr) add = corr + row * r;
-      } else {
-        const int slot = seg == 0 ? 0 : 1;
-        dst = part + (((int64_t)blockIdx.x * 2 + slot) * TILE + quarter * 32 + lane) * r;
-      }
+      // (no early exit on a failed wait: the four epilogue warps must all
+      // reach the named barriers; the failed stores are skipped)
+      asm volatile("bar.sync 1, 128;" ::: "memory");   // previous copy-out done
 #pragma unroll
       for (int c0 = 0; c0 < RP; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * RP + c0), v);
-        if (ok && row < rows_out) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c0 + j < r) dst[c0 + j] = add ? v[j] + add[c0 + j] : v[j];
-        }
+        for (int j = 0; j < 16; ++j) stg[lrow * SS + c0 + j] = v[j];
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acce_bar[b]);
-      // (no early exit on a failed wait: the four epilogue warps must all
-      // reach the named barriers below; the failed stores are skipped)
+      if (lane == 0) mbar_arrive(&acce_bar[b]);        // accumulator b free again
+      asm volatile("bar.sync 1, 128;" ::: "memory");   // staging tile complete
+      const int64_t row0 = tile * TILE;
+      const int cnt = (int)min((int64_t)TILE, rows_out - row0) * r;
+      float* dst;
+      const float* add = nullptr;
+      if (whole) {
+        dst = out + row0 * r;
+        if (corr) add = corr + row0 * r;
+      } else {
+        const int slot = seg == 0 ? 0 : 1;
+        dst = part + ((int64_t)blockIdx.x * 2 + slot) * TILE * r;
+      }
+      if (ok) {
+        int rr = rr0, cc = cc0;
+        for (int f = et; f < cnt; f += 128) {
+          float v = stg[rr * SS + cc];
+          if (add) v += add[f];
+          dst[f] = v;
+          rr += q128;
+          cc += r128;
+          if (cc >= r) {
+            cc -= r;
+            ++rr;
+          }
+        }
+      }
       if (!whole) {
         // A tile cut by range boundaries: the last of its CTAs to get here
         // sums every contributor's slot, in CTA order (so the result does not
@@ -362,27 +386,34 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         int64_t c_lo = blockIdx.x, c_hi = blockIdx.x;
         while (c_lo > 0 && sk_begin(c_lo, W, G) > tile * nkb) --c_lo;
         while (c_hi + 1 < G && sk_begin(c_hi + 1, W, G) < (tile + 1) * nkb) ++c_hi;
-        if (warp == 2 && lane == 0) {
+        if (et == 0) {
           const int old = atomicAdd(&counters[tile], 1);
           last_cta = old == (int)(c_hi - c_lo);
           if (last_cta) counters[tile] = 0;   // ready for the next launch
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (last_cta && row < rows_out) {
+        if (last_cta && ok) {
           __threadfence();
+          // thread et owns flat elements et + 128 i, i < r (cnt <= 128 r)
           float acc[RP];
 #pragma unroll
-          for (int j = 0; j < RP; ++j) acc[j] = 0.f;
+          for (int i = 0; i < RP; ++i) acc[i] = 0.f;
           for (int64_t q = c_lo; q <= c_hi; ++q) {
             const int slot = sk_begin(q, W, G) >= tile * nkb ? 0 : 1;
-            const float* src = part + ((q * 2 + slot) * TILE + quarter * 32 + lane) * r;
+            const float* src = part + (q * 2 + slot) * TILE * r;
 #pragma unroll
-            for (int j = 0; j < RP; ++j)
-              if (j < r) acc[j] += __ldcg(&src[j]);
+            for (int i = 0; i < RP; ++i) {
+              const int f = et + 128 * i;
+              if (f < cnt) acc[i] += __ldcg(&src[f]);
+            }
           }
+          float* o = out + row0 * r;
+          const float* cr = corr ? corr + row0 * r : nullptr;
 #pragma unroll
-          for (int j = 0; j < RP; ++j)
-            if (j < r) out[row * r + j] = corr ? acc[j] + corr[row * r + j] : acc[j];
+          for (int i = 0; i < RP; ++i) {
+            const int f = et + 128 * i;
+            if (f < cnt) o[f] = cr ? acc[i] + cr[f] : acc[i];
+          }
         }
       }
     }
@@ -485,16 +516,23 @@ bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_
 
 int tc_rank_pad(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : (r <= 48 ? 48 : 64)); }
 
+// Dynamic shared memory: the stage ring (1024-byte aligned) and the
+// epilogue's staging tile (TILE x (rp + 1) floats).
+static size_t tc_staging(int rp) { return (size_t)tc::TILE * (rp + 1) * sizeof(float); }
+
 static size_t tc_smem(int mode, int rp, int stages) {
   const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
-  return (size_t)stages * ((size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2) + 1024;
+  return (size_t)stages * ((size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2) + 1024 +
+         tc_staging(rp);
 }
 
+// As many stages as fit in 227 KB per CTA (less 1 KB for static shared
+// memory), between 2 and 8.
 static int tc_stages(int mode, int rp) {
-  const size_t budget = 200 * 1024;
+  const size_t budget = 227 * 1024 - 1024 - 1024 - tc_staging(rp);
   const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
   const size_t st = (size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2;
-  int s = (int)((budget - 1024) / st);
+  int s = (int)(budget / st);
   return s > 8 ? 8 : (s < 2 ? 2 : s);
 }
 
