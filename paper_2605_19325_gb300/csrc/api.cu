@@ -619,6 +619,7 @@ static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const dou
   a.gpart = ctx->part;
   a.finalize = which == 1 ? 1 : 0;
   a.Gu = Gu;
+  a.obj_part = ctx->dot_part + 2048;
   a.trace = trace;
   a.trace_idx = trace_idx;
   launch_half_step(a, which == 0 ? ctx->grid_u : ctx->grid_v, ctx->stream);

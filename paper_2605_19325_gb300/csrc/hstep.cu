@@ -1,0 +1,430 @@
+// One half of an alternation of Algorithm 3: the rows of one factor F (U or
+// V) updated with the other factor fixed.  Row i needs only its own row of F,
+// its row of A (= X V or X^T U) and the r x r Gram G of the other factor
+// (Sec. 4.2: the rows do not interact), so the rows run in parallel:
+//   * HALS stage (Sec. 4.3): one sweep of the column updates
+//       u_j <- max(0, u_j + (a_j - u . G_:j) / G_jj),  j = 1..r in order;
+//   * ascent stage: the Eq. 8/9 shift of the negative entries, the mask of
+//     Algorithm 2, and PBCD steps d_i = ||g_i||^2 / (g_i G g_i^T) (Eq. 10)
+//     with the global stopping test of Algorithm 2 (a grid barrier);
+// then the Gram F^T F of the updated factor, and at the end of the
+// alternation (V-half) the objective f of Eq. 1 by the Gram expansion
+//   f = 1/2 ||X||^2 - <X^T U, V> + 1/2 <U^T U, V^T V>
+// and the stage decision, all inside one cooperative kernel.
+//
+// Mapping: eight lanes share a row; lane `sub` owns the entries
+// l = sub + 8 e (e < KP / 8) of u, a and the gradient, in registers, for a
+// rank padded to KP (16, 32, 48 or 64; padded entries are zero).  The HALS
+// sweep keeps q = a - u G up to date: after u_j moves by delta the whole
+// vector takes q <- q - delta G_j:, a rank-one update whose KP/8 FMAs per lane
+// are independent, so a column step costs one shuffle and no dependent
+// reduction chain.  Sums of a full row (u G, ||g||^2, g G g^T) combine the
+// eight lanes by shuffles in a fixed pattern.
+//
+// The Gram of the block's rows is accumulated in TF by 16 x 16 threads, each
+// owning a (KP/16) x (KP/16) sub-block, then written as an FP64 partial per
+// block; after the grid barrier the partials are summed in block order.  The
+// objective needs <U^T U, V^T V>, which is linear in the V^T V partials, so
+// each block contributes <U^T U, its partial> and block 0 sums those scalars
+// after the same barrier: one barrier per half step in the HALS stage.
+#include "internal.h"
+
+namespace enmf {
+namespace {
+
+constexpr int HT = 256;          // threads per block
+constexpr int LPR = 8;           // lanes per row
+constexpr int RPB = HT / LPR;    // rows per block per pass
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T shfl8(T v, int src) {
+  return __shfl_sync(FULL, v, src, LPR);
+}
+
+// Sum over the eight lanes of a row.  The butterfly gives every lane the same
+// bits: each step adds a pair whose order only commutes.
+template <typename T>
+__device__ __forceinline__ T sum8(T v) {
+  v += __shfl_xor_sync(FULL, v, 4, LPR);
+  v += __shfl_xor_sync(FULL, v, 2, LPR);
+  v += __shfl_xor_sync(FULL, v, 1, LPR);
+  return v;
+}
+
+// Sum of n cross-block partials written before a grid barrier, by the whole
+// block in a fixed order (L1 bypassed).  Every thread gets the result.
+__device__ __forceinline__ double sum_partials(const double* p, int n, double* sh) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < n; b += HT) s += __ldcg(&p[b]);
+  return block_sum(s, sh);
+}
+
+template <typename TF, int E>
+__device__ __forceinline__ void load_row(const TF* P, int64_t i, bool live, int k, int sub,
+                                         TF (&v)[E]) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int l = sub + LPR * e;
+    v[e] = (live && l < k) ? P[i * k + l] : TF(0);
+  }
+}
+
+template <typename TF, int E>
+__device__ __forceinline__ void store_row(TF* P, int64_t i, bool live, int k, int sub,
+                                          const TF (&v)[E]) {
+  if (!live) return;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int l = sub + LPR * e;
+    if (l < k) P[i * k + l] = v[e];
+  }
+}
+
+// s_l = sum_m u_m G_ml for the lane's entries l (G symmetric, KP x KP in
+// shared memory), m in increasing order; u_m comes from its owner lane.
+template <typename TF, int KP>
+__device__ __forceinline__ void row_times_gram(const TF* Gs, const TF (&u)[KP / LPR], int k,
+                                               int sub, TF (&s)[KP / LPR]) {
+  constexpr int E = KP / LPR;
+#pragma unroll
+  for (int e = 0; e < E; ++e) s[e] = TF(0);
+#pragma unroll
+  for (int m = 0; m < KP; ++m) {
+    if (m < k) {
+      const TF um = shfl8(u[m / LPR], m % LPR);
+#pragma unroll
+      for (int e = 0; e < E; ++e) s[e] = fma(um, Gs[m * KP + sub + LPR * e], s[e]);
+    }
+  }
+}
+
+// Adds the block's pass of rows (staged in `us`) to the thread's Gram
+// sub-block.  Rows not present are zero.
+template <typename TF, int KP>
+__device__ __forceinline__ void gram_pass(TF* us, const TF (&u)[KP / LPR], int rloc, int sub,
+                                          TF (&gacc)[KP / 16][KP / 16]) {
+  constexpr int E = KP / LPR, S = KP / 16;
+  __syncthreads();   // the previous pass has been consumed
+#pragma unroll
+  for (int e = 0; e < E; ++e) us[rloc * KP + sub + LPR * e] = u[e];
+  __syncthreads();
+  const int bi = threadIdx.x / 16, bj = threadIdx.x % 16;
+  for (int rr = 0; rr < RPB; ++rr) {
+    TF x[S], y[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      x[s] = us[rr * KP + bi * S + s];
+      y[s] = us[rr * KP + bj * S + s];
+    }
+#pragma unroll
+    for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) gacc[s1][s2] = fma(x[s1], y[s2], gacc[s1][s2]);
+  }
+}
+
+template <typename TF, int KP>
+__global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
+  constexpr int E = KP / LPR, S = KP / 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TF* Gs = reinterpret_cast<TF*>(smraw);   // KP x KP, zero padded
+  TF* us = Gs + KP * KP;                   // RPB x KP rows of the current pass
+  __shared__ double sh[HT];
+
+  const int k = a.k;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int sub = lane & (LPR - 1);
+  const int rloc = warp * (32 / LPR) + (lane / LPR);
+  if (a.G) {
+#pragma unroll
+    for (int q = 0; q < (KP * KP + HT - 1) / HT; ++q) {
+      const int e = t + q * HT;
+      if (e < KP * KP) {
+        const int p = e / KP, c = e % KP;
+        Gs[e] = (p < k && c < k) ? (TF)a.G[p * k + c] : TF(0);
+      }
+    }
+  }
+  __syncthreads();
+
+  DevState* st = a.st;
+  const int stage = *(volatile int*)&st->stage;
+  TF* F = (TF*)a.F;
+  const TF* A = (const TF*)a.A;
+  const int64_t rows = a.rows;
+  const int64_t passes = (rows + (int64_t)gridDim.x * RPB - 1) / ((int64_t)gridDim.x * RPB);
+  TF gacc[S][S];
+#pragma unroll
+  for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) gacc[s1][s2] = TF(0);
+  double dotacc = 0.0;
+
+  if (a.gram_only) {
+    for (int64_t ps = 0; ps < passes; ++ps) {
+      const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+      TF u[E];
+      load_row(F, i, i < rows, k, sub, u);
+      gram_pass<TF, KP>(us, u, rloc, sub, gacc);
+    }
+  } else if (stage == 1) {
+    // ---- HALS sweep over the columns, q = a - u G kept current
+    for (int64_t ps = 0; ps < passes; ++ps) {
+      const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+      const bool live = i < rows;
+      TF u[E], av[E], q[E];
+      load_row(F, i, live, k, sub, u);
+      load_row(A, i, live, k, sub, av);
+      row_times_gram<TF, KP>(Gs, u, k, sub, q);
+#pragma unroll
+      for (int e = 0; e < E; ++e) q[e] = av[e] - q[e];
+#pragma unroll
+      for (int j = 0; j < KP; ++j) {
+        if (j < k) {
+          const int e = j / LPR, own = j % LPR;
+          const TF gjj = Gs[j * KP + j];
+          TF v = u[e], dl = TF(0);
+          if (gjj > TF(0)) {
+            v = u[e] + q[e] / gjj;
+            v = v > TF(0) ? v : TF(0);
+            dl = v - u[e];
+          }
+          dl = shfl8(dl, own);
+          if (sub == own) u[e] = v;
+#pragma unroll
+          for (int ee = 0; ee < E; ++ee) q[ee] = fma(-dl, Gs[j * KP + sub + LPR * ee], q[ee]);
+        }
+      }
+      store_row(F, i, live, k, sub, u);
+      if (a.dot_part) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) dotacc = fma((double)av[e], (double)u[e], dotacc);
+      }
+      gram_pass<TF, KP>(us, u, rloc, sub, gacc);
+    }
+  } else {
+    // ---- ascent step: shift (Eq. 8/9), mask, PBCD (Algorithm 2)
+    const TF sft = (TF)(a.which == 0 ? st->s_u : st->s_v);
+    TF* gb = (TF*)a.gbuf;
+    unsigned char* mk = reinterpret_cast<unsigned char*>(a.mask);
+    double acc = 0.0;
+    for (int64_t ps = 0; ps < passes; ++ps) {
+      const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+      const bool live = i < rows;
+      TF u[E], av[E], g[E];
+      load_row(F, i, live, k, sub, u);
+      load_row(A, i, live, k, sub, av);
+      unsigned bits = 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if (u[e] < TF(0)) u[e] = u[e] + sft;   // Eq. 8 / 9, literal (no clamp)
+        if (u[e] >= TF(0)) bits |= 1u << e;
+      }
+      row_times_gram<TF, KP>(Gs, u, k, sub, g);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        g[e] = ((bits >> e) & 1u) ? g[e] - av[e] : TF(0);
+        acc = fma((double)g[e], (double)g[e], acc);
+      }
+      store_row(F, i, live, k, sub, u);
+      store_row(gb, i, live, k, sub, g);
+      if (live) mk[i * 8 + sub] = (unsigned char)bits;
+    }
+    double bsum = block_sum(acc, sh);
+    if (t == 0) a.part[blockIdx.x] = bsum;
+    grid_sync(&st->bar, a.err);
+    const double g0 = sqrt(sum_partials(a.part, gridDim.x, sh));
+    int iters = 0;
+    for (int it = 0; it < a.pbcd_max_iter; ++it) {
+      acc = 0.0;
+      for (int64_t ps = 0; ps < passes; ++ps) {
+        const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+        const bool live = i < rows;
+        TF u[E], av[E], g[E], tg[E];
+        load_row(F, i, live, k, sub, u);
+        load_row(gb, i, live, k, sub, g);
+        load_row(A, i, live, k, sub, av);
+        const unsigned bits = live ? mk[i * 8 + sub] : 0u;
+        // d_i = ||g_i||^2 / (g_i G g_i^T)   (Eq. 10; App. B)
+        row_times_gram<TF, KP>(Gs, g, k, sub, tg);
+        TF num = TF(0), den = TF(0);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          num = fma(g[e], g[e], num);
+          den = fma(g[e], tg[e], den);
+        }
+        num = sum8(num);
+        den = sum8(den);
+        const TF d = (num > TF(0) && den > TF(0)) ? num / den : TF(0);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if ((bits >> e) & 1u) {
+            const TF v = u[e] - d * g[e];
+            u[e] = v > TF(0) ? v : TF(0);   // (.)_+ of the PBCD update
+          }
+        row_times_gram<TF, KP>(Gs, u, k, sub, g);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          g[e] = ((bits >> e) & 1u) ? g[e] - av[e] : TF(0);
+          acc = fma((double)g[e], (double)g[e], acc);
+        }
+        store_row(F, i, live, k, sub, u);
+        store_row(gb, i, live, k, sub, g);
+      }
+      double* pbuf = a.part + (size_t)((it + 1) & 1) * gridDim.x;
+      bsum = block_sum(acc, sh);
+      if (t == 0) pbuf[blockIdx.x] = bsum;
+      grid_sync(&st->bar, a.err);
+      const double bc = sum_partials(pbuf, gridDim.x, sh);
+      iters = it + 1;
+      if (sqrt(bc) < a.eps * g0 || bc == 0.0) break;
+    }
+    // entries still negative (unmasked) keep the ascent stage going
+    int neg = 0;
+    for (int64_t ps = 0; ps < passes; ++ps) {
+      const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+      const bool live = i < rows;
+      TF u[E];
+      load_row(F, i, live, k, sub, u);
+      if (live) {
+        const unsigned bits = mk[i * 8 + sub];
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (sub + LPR * e < k && !((bits >> e) & 1u)) neg = 1;
+        if (a.dot_part) {
+          TF av[E];
+          load_row(A, i, live, k, sub, av);
+#pragma unroll
+          for (int e = 0; e < E; ++e) dotacc = fma((double)av[e], (double)u[e], dotacc);
+        }
+      }
+      gram_pass<TF, KP>(us, u, rloc, sub, gacc);
+    }
+    if (neg) atomicOr(a.which == 0 ? &st->negU : &st->negV, 1);
+    if (blockIdx.x == 0 && t == 0) {
+      const int q = st->asc_iters;
+      if (a.counts && 2 * q + a.which < a.counts_cap) a.counts[2 * q + a.which] = iters;
+    }
+  }
+
+  // ---- block partials: Gram (FP64), <A, F> and <U^T U, Gram partial>
+  const int kk = k * k;
+  {
+    const int bi = t / 16, bj = t % 16;
+    double obj = 0.0;
+#pragma unroll
+    for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) {
+        const int p = bi * S + s1, c = bj * S + s2;
+        if (p < k && c < k) {
+          const double gv = (double)gacc[s1][s2];
+          a.gpart[(int64_t)blockIdx.x * kk + p * k + c] = gv;
+          if (a.finalize) obj = fma(a.Gu[p * k + c], gv, obj);
+        }
+      }
+    if (a.finalize) {
+      obj = block_sum(obj, sh);
+      if (t == 0) a.obj_part[blockIdx.x] = obj;
+    }
+  }
+  if (a.dot_part) {
+    const double dsum = block_sum(dotacc, sh);
+    if (t == 0) a.dot_part[blockIdx.x] = dsum;
+  }
+  grid_sync(&st->bar, a.err);
+
+  // ---- G_out = sum of the block partials in block order: each entry by
+  // eight consecutive lanes (lane g takes partials g, g + 8, ...), combined
+  // by a fixed shuffle tree.
+  {
+    const int grp = t & 7;
+    const int nb = (int)gridDim.x;
+    for (int e0 = (int)blockIdx.x * (HT / 8); e0 < kk; e0 += (int)gridDim.x * (HT / 8)) {
+      const int e = e0 + t / 8;
+      double s = 0.0;
+      if (e < kk)
+        for (int b = grp; b < nb; b += 8) s += __ldcg(&a.gpart[(int64_t)b * kk + e]);
+      s += __shfl_down_sync(FULL, s, 4, 8);
+      s += __shfl_down_sync(FULL, s, 2, 8);
+      s += __shfl_down_sync(FULL, s, 1, 8);
+      if (grp == 0 && e < kk) a.G_out[e] = s;
+    }
+  }
+  if (!a.finalize || blockIdx.x != 0) return;
+
+  // ---- end of the alternation (block 0): objective and stage update
+  const double gg = sum_partials(a.obj_part, gridDim.x, sh);
+  const double d = sum_partials(a.dot_part, gridDim.x, sh);
+  if (t == 0) {
+    const double f = 0.5 * st->normX2 - d + 0.5 * gg;
+    if (a.trace) a.trace[a.trace_idx] = f;
+    if (st->stage == 0) st->asc_iters += 1;
+    else st->hals_iters += 1;
+    st->k += 1;
+    if (st->stage == 0 && !(st->negU || st->negV)) st->stage = 1;
+    st->negU = 0;
+    st->negV = 0;
+  }
+}
+
+template <typename TF, int KP>
+size_t hstep_smem() {
+  return sizeof(TF) * ((size_t)KP * KP + (size_t)RPB * KP);
+}
+
+template <typename TF, int KP>
+int hstep_capacity(int num_sms) {
+  const size_t smem = hstep_smem<TF, KP>();
+  cudaFuncSetAttribute(hstep_kernel<TF, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, hstep_kernel<TF, KP>, HT, smem);
+  return (per < 1 ? 1 : per) * num_sms;
+}
+
+template <typename TF, int KP>
+void hstep_launch(const HalfArgs& a, int grid, cudaStream_t s) {
+  void* args[] = {(void*)&a};
+  cudaLaunchCooperativeKernel((void*)hstep_kernel<TF, KP>, dim3(grid), dim3(HT), args,
+                              hstep_smem<TF, KP>(), s);
+}
+
+int rank_pad16(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 48 ? 48 : 64)); }
+
+}  // namespace
+
+// Largest co-resident grid of the half step for this form and rank, at most
+// NPART blocks (the size of the partial buffers).
+int half_step_grid(int fdt, int k, int num_sms) {
+  const int kp = rank_pad16(k);
+  int cap;
+  if (fdt == T_F64)
+    cap = kp == 16 ? hstep_capacity<double, 16>(num_sms) : kp == 32 ? hstep_capacity<double, 32>(num_sms)
+          : kp == 48 ? hstep_capacity<double, 48>(num_sms) : hstep_capacity<double, 64>(num_sms);
+  else
+    cap = kp == 16 ? hstep_capacity<float, 16>(num_sms) : kp == 32 ? hstep_capacity<float, 32>(num_sms)
+          : kp == 48 ? hstep_capacity<float, 48>(num_sms) : hstep_capacity<float, 64>(num_sms);
+  return cap > NPART ? NPART : cap;
+}
+
+void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s) {
+  note_launch(1);
+  const int64_t need = (a.rows + RPB - 1) / RPB;
+  if ((int64_t)grid > need) grid = (int)need;
+  if (grid < 1) grid = 1;
+  const int kp = rank_pad16(a.k);
+  if (a.fdt == T_F64) {
+    if (kp == 16) hstep_launch<double, 16>(a, grid, s);
+    else if (kp == 32) hstep_launch<double, 32>(a, grid, s);
+    else if (kp == 48) hstep_launch<double, 48>(a, grid, s);
+    else hstep_launch<double, 64>(a, grid, s);
+  } else {
+    if (kp == 16) hstep_launch<float, 16>(a, grid, s);
+    else if (kp == 32) hstep_launch<float, 32>(a, grid, s);
+    else if (kp == 48) hstep_launch<float, 48>(a, grid, s);
+    else hstep_launch<float, 64>(a, grid, s);
+  }
+}
+
+}  // namespace enmf

@@ -80,7 +80,7 @@ struct HalfArgs {
   const void* A;      // X V or X^T U for this half (rows x k, ld k)
   const double* G;    // Gram of the other factor (k x k)
   void* gbuf;         // PBCD gradient scratch (rows x k)
-  unsigned long long* mask;  // PBCD mask bits (rows)
+  unsigned long long* mask;  // PBCD mask bits (rows x 8 bytes)
   int64_t rows;
   int k;
   int fdt;
@@ -102,6 +102,7 @@ struct HalfArgs {
   // from Gu (U^T U) and G_out (V^T V), then the stage update
   int finalize;
   const double* Gu;
+  double* obj_part;   // per-block <Gu, Gram partial> (grid doubles)
   double* trace;
   int trace_idx;
   // gram_only: skip the row updates and only form G_out = F^T F with the same
@@ -109,12 +110,11 @@ struct HalfArgs {
   // one the previous call's last half-step produced)
   int gram_only;
 };
+// hstep.cu: one cooperative launch per half step; grid <= half_step_grid().
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);
 int half_step_grid(int fdt, int k, int num_sms);
 void launch_state_init(const void* U, const void* V, int64_t m, int64_t n, int k, int fdt,
                        int n_shift, DevState* st, double* part, cudaStream_t s);
-void launch_iter_finalize(DevState* st, const double* dot_part, int ndot, const double* Gu,
-                          const double* Gv, int k, double* trace, int trace_idx, cudaStream_t s);
 // ADMM pass of Algorithm 1 over W = [U; V] (see rows.cu).
 void launch_admm_pass(const void* U, const void* V, int64_t m, int64_t n, int k, int fdt,
                       const double* R, void* Z, void* Y, double rho, int first, DevState* st,

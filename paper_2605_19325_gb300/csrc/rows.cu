@@ -1,273 +1,15 @@
-// Row-local kernels of the eNMF path.
+// Row-local kernels of the eNMF path (the half steps of the iteration are in
+// hstep.cu).
 //
-// The U-half of an alternation is row separable (Sec. 4.2: rows do not
-// interact with V fixed): row i needs only its row of X V, the r x r Gram
-// V^T V and its own row of U.  So every update here is one thread per factor
-// row, with the Gram staged in shared memory:
-//   * half_step_kernel -- the ascent step of Algorithm 3 (Eq. 8/9 shift,
-//     mask, Algorithm 2 PBCD with the Eq. 10/11 step) or a HALS sweep;
+// Rows are independent here (Sec. 4.2), so each kernel runs one thread per
+// factor row, with any r x r matrix it needs staged in shared memory:
+//   * stage start of the ascent (Eq. 8/9 step sizes from max(-F));
 //   * admm_pass_kernel -- one ADMM pass of Algorithm 1 over W = [U; V];
 //   * transforms, negative mass, column sums and the KKT measures (App. G).
 // Cost per row is O(r^2); all of these are small next to the O(m n r) sweeps.
 #include "internal.h"
 
 namespace enmf {
-
-// ----------------------------------------------------------- half step
-constexpr int HS_T = 64;
-constexpr int HS_S = HS_T + 1;   // padded stride of the per-thread rows in shared memory
-
-// Sum of n cross-block partials (written before a grid barrier), by the whole
-// block: thread t takes t, t + HS_T, ... and the block sums in a fixed tree.
-// The same value reaches every thread; L1 is bypassed for the cross-block data.
-__device__ __forceinline__ double sum_partials(const double* p, int n, double* sh) {
-  double s = 0.0;
-  for (int b = threadIdx.x; b < n; b += HS_T) s += __ldcg(&p[b]);
-  return block_sum(s, sh);
-}
-
-static size_t half_step_smem(int fdt, int k) {
-  size_t e = type_size(fdt);
-  return e * ((size_t)k * k + 2 * (size_t)k * HS_S);
-}
-
-template <typename TF>
-__global__ void __launch_bounds__(HS_T) half_step_kernel(HalfArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  TF* Gs = reinterpret_cast<TF*>(smraw);
-  TF* us = Gs + a.k * a.k;          // us[j * HS_S + t]
-  TF* gs = us + a.k * HS_S;         // gs[j * HS_S + t]
-  __shared__ double sh[HS_T];
-  __shared__ double bc;
-
-  const int k = a.k;
-  for (int e = threadIdx.x; e < k * k; e += HS_T) Gs[e] = (TF)a.G[e];
-  __syncthreads();
-
-  DevState* st = a.st;
-  const int stage = *(volatile int*)&st->stage;
-  TF* F = (TF*)a.F;
-  const TF* A = (const TF*)a.A;
-  TF* gb = (TF*)a.gbuf;
-  const int64_t rows = a.rows;
-  const int64_t nth = (int64_t)gridDim.x * HS_T;
-  const int64_t tid = (int64_t)blockIdx.x * HS_T + threadIdx.x;
-  const int t = threadIdx.x;
-  TF* u = us + t;   // u[j * HS_S]
-  TF* g = gs + t;
-  double dotacc = 0.0;
-
-  if (a.gram_only) {
-    // no update
-  } else if (stage == 1) {
-    // HALS: for j in order, u_j <- max(0, u_j + (a_j - sum_l u_l G_lj) / G_jj)
-    for (int64_t i = tid; i < rows; i += nth) {
-      for (int j = 0; j < k; ++j) u[j * HS_S] = F[i * k + j];
-      for (int j = 0; j < k; ++j) {
-        TF gjj = Gs[j * k + j];
-        if (!(gjj > TF(0))) continue;
-        TF s = TF(0);
-        for (int l = 0; l < k; ++l) s = fma(u[l * HS_S], Gs[l * k + j], s);
-        TF v = u[j * HS_S] + (A[i * k + j] - s) / gjj;
-        u[j * HS_S] = v > TF(0) ? v : TF(0);
-      }
-      for (int j = 0; j < k; ++j) F[i * k + j] = u[j * HS_S];
-      if (a.dot_part) {
-        double d4[4] = {0.0, 0.0, 0.0, 0.0};   // four independent chains
-        for (int j = 0; j < k; ++j) d4[j & 3] = fma((double)A[i * k + j], (double)u[j * HS_S], d4[j & 3]);
-        dotacc += (d4[0] + d4[1]) + (d4[2] + d4[3]);
-      }
-    }
-  } else {
-    // Ascent step: shift, mask, PBCD (Algorithm 2).
-    const double sft = a.which == 0 ? st->s_u : st->s_v;
-    const TF s = (TF)sft;
-    double acc = 0.0;
-    for (int64_t i = tid; i < rows; i += nth) {
-      unsigned long long mk = 0ull;
-      for (int j = 0; j < k; ++j) {
-        TF v = F[i * k + j];
-        if (v < TF(0)) v = v + s;                // Eq. 8 / 9, literal (no clamp)
-        u[j * HS_S] = v;
-        if (v >= TF(0)) mk |= (1ull << j);
-      }
-      for (int j = 0; j < k; ++j) {
-        TF gj = TF(0);
-        if ((mk >> j) & 1ull) {
-          TF sdot = TF(0);
-          for (int l = 0; l < k; ++l) sdot = fma(u[l * HS_S], Gs[l * k + j], sdot);
-          gj = sdot - A[i * k + j];
-        }
-        g[j * HS_S] = gj;
-        acc = fma((double)gj, (double)gj, acc);
-      }
-      for (int j = 0; j < k; ++j) {
-        F[i * k + j] = u[j * HS_S];
-        gb[i * k + j] = g[j * HS_S];
-      }
-      a.mask[i] = mk;
-    }
-    double bsum = block_sum(acc, sh);
-    if (threadIdx.x == 0) a.part[blockIdx.x] = bsum;
-    grid_sync(&st->bar, a.err);
-    bc = sum_partials(a.part, gridDim.x, sh);
-    const double g0 = sqrt(bc);
-    int iters = 0;
-    for (int it = 0; it < a.pbcd_max_iter; ++it) {
-      acc = 0.0;
-      for (int64_t i = tid; i < rows; i += nth) {
-        const unsigned long long mk = a.mask[i];
-        for (int j = 0; j < k; ++j) {
-          u[j * HS_S] = F[i * k + j];
-          g[j * HS_S] = gb[i * k + j];
-        }
-        // d_i = ||g_i||^2 / (g_i G g_i^T)   (Eq. 10; App. B)
-        TF num = TF(0), den = TF(0);
-        for (int j = 0; j < k; ++j) {
-          TF gj = g[j * HS_S];
-          num = fma(gj, gj, num);
-          TF row = TF(0);
-          for (int l = 0; l < k; ++l) row = fma(Gs[j * k + l], g[l * HS_S], row);
-          den = fma(gj, row, den);
-        }
-        TF d = (num > TF(0) && den > TF(0)) ? num / den : TF(0);
-        for (int j = 0; j < k; ++j)
-          if ((mk >> j) & 1ull) {
-            TF v = u[j * HS_S] - d * g[j * HS_S];
-            u[j * HS_S] = v > TF(0) ? v : TF(0);   // (.)_+ of Eq. 9 pbcdu
-          }
-        for (int j = 0; j < k; ++j) {
-          TF gj = TF(0);
-          if ((mk >> j) & 1ull) {
-            TF sdot = TF(0);
-            for (int l = 0; l < k; ++l) sdot = fma(u[l * HS_S], Gs[l * k + j], sdot);
-            gj = sdot - A[i * k + j];
-          }
-          g[j * HS_S] = gj;
-          acc = fma((double)gj, (double)gj, acc);
-        }
-        for (int j = 0; j < k; ++j) {
-          F[i * k + j] = u[j * HS_S];
-          gb[i * k + j] = g[j * HS_S];
-        }
-      }
-      double* pbuf = a.part + (size_t)((it + 1) & 1) * gridDim.x;
-      bsum = block_sum(acc, sh);
-      if (threadIdx.x == 0) pbuf[blockIdx.x] = bsum;
-      grid_sync(&st->bar, a.err);
-      bc = sum_partials(pbuf, gridDim.x, sh);
-      const double pg = sqrt(bc);
-      iters = it + 1;
-      if (pg < a.eps * g0 || bc == 0.0) break;
-    }
-    // entries still negative (unmasked) keep the ascent stage going
-    int neg = 0;
-    for (int64_t i = tid; i < rows; i += nth) {
-      const unsigned long long mk = a.mask[i];
-      if (~mk & ((k == 64) ? ~0ull : ((1ull << k) - 1ull))) neg = 1;
-      if (a.dot_part)
-        for (int j = 0; j < k; ++j) dotacc = fma((double)A[i * k + j], (double)F[i * k + j], dotacc);
-    }
-    if (neg) atomicOr(a.which == 0 ? &st->negU : &st->negV, 1);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      int q = st->asc_iters;
-      if (a.counts && 2 * q + a.which < a.counts_cap) a.counts[2 * q + a.which] = iters;
-    }
-  }
-  if (a.dot_part) {
-    double bsum = block_sum(dotacc, sh);
-    if (threadIdx.x == 0) a.dot_part[blockIdx.x] = bsum;
-  }
-  if (!a.G_out) return;
-
-  // ---- Gram of the updated factor, F^T F.  Each block sums the products of
-  // its own rows (in TF, staged a pass at a time in shared memory), writes a
-  // partial, and after a grid barrier the partials are summed in block order.
-  TF* gacc = gs;   // reuse: needs k * k <= k * HS_S entries (k <= 64)
-  __syncthreads();
-  for (int e = t; e < k * k; e += HS_T) gacc[e] = TF(0);
-  const int64_t passes = (rows + nth - 1) / nth;
-  for (int64_t ps = 0; ps < passes; ++ps) {
-    const int64_t i = tid + ps * nth;
-    __syncthreads();
-    for (int j = 0; j < k; ++j) u[j * HS_S] = i < rows ? F[i * k + j] : TF(0);
-    __syncthreads();
-    for (int e = t; e < k * k; e += HS_T) {
-      const int p = e / k, q = e % k;
-      TF s = gacc[e];
-      for (int tt = 0; tt < HS_T; ++tt) s = fma(us[p * HS_S + tt], us[q * HS_S + tt], s);
-      gacc[e] = s;
-    }
-  }
-  __syncthreads();
-  for (int e = t; e < k * k; e += HS_T) a.gpart[(int64_t)blockIdx.x * k * k + e] = (double)gacc[e];
-  grid_sync(&st->bar, a.err);
-  // Each entry is summed by 8 consecutive lanes (lane group g takes partials
-  // g, g + 8, ...), then combined by a fixed shuffle tree: a fixed order, with
-  // every partial load of a lane issued back to back.
-  {
-    const int grp = t & 7;
-    const int nb = (int)gridDim.x;
-    const int kk = k * k;
-    for (int e0 = (int)blockIdx.x * (HS_T / 8); e0 < kk; e0 += (int)gridDim.x * (HS_T / 8)) {
-      const int e = e0 + t / 8;
-      double s = 0.0;
-      if (e < kk)
-        for (int b = grp; b < nb; b += 8) s += __ldcg(&a.gpart[(int64_t)b * kk + e]);
-      s += __shfl_down_sync(0xffffffffu, s, 4, 8);
-      s += __shfl_down_sync(0xffffffffu, s, 2, 8);
-      s += __shfl_down_sync(0xffffffffu, s, 1, 8);
-      if (grp == 0 && e < kk) a.G_out[e] = s;
-    }
-  }
-  if (!a.finalize) return;
-
-  // ---- end of the alternation (block 0 after a grid barrier):
-  // f = 1/2 ||X||^2 - <X^T U, V> + 1/2 <U^T U, V^T V>, then the stage update.
-  grid_sync(&st->bar, a.err);
-  if (blockIdx.x != 0) return;
-  double gg = 0.0;
-  for (int e = t; e < k * k; e += HS_T) gg = fma(a.Gu[e], __ldcg(&a.G_out[e]), gg);
-  gg = block_sum(gg, sh);
-  const double d = sum_partials(a.dot_part, gridDim.x, sh);
-  if (t == 0) {
-    const double f = 0.5 * st->normX2 - d + 0.5 * gg;
-    if (a.trace) a.trace[a.trace_idx] = f;
-    if (st->stage == 0) st->asc_iters += 1;
-    else st->hals_iters += 1;
-    st->k += 1;
-    if (st->stage == 0 && !(st->negU || st->negV)) st->stage = 1;
-    st->negU = 0;
-    st->negV = 0;
-  }
-}
-
-int half_step_grid(int fdt, int k, int num_sms) {
-  int per = 0;
-  size_t smem = half_step_smem(fdt, k);
-  if (fdt == T_F64) {
-    cudaFuncSetAttribute(half_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, half_step_kernel<double>, HS_T, smem);
-  } else {
-    cudaFuncSetAttribute(half_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, half_step_kernel<float>, HS_T, smem);
-  }
-  if (per < 1) per = 1;
-  return per * num_sms;
-}
-
-void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s) {
-  note_launch(1);
-  int64_t need = (a.rows + HS_T - 1) / HS_T;
-  if ((int64_t)grid > need) grid = (int)need;
-  if (grid < 1) grid = 1;
-  size_t smem = half_step_smem(a.fdt, a.k);
-  void* args[] = {(void*)&a};
-  if (a.fdt == T_F64)
-    cudaLaunchCooperativeKernel((void*)half_step_kernel<double>, dim3(grid), dim3(HS_T), args, smem, s);
-  else
-    cudaLaunchCooperativeKernel((void*)half_step_kernel<float>, dim3(grid), dim3(HS_T), args, smem, s);
-}
 
 // ----------------------------------------------------------- stage start
 __global__ void state_reset_kernel(DevState* st) {
@@ -313,34 +55,6 @@ void launch_state_init(const void* U, const void* V, int64_t m, int64_t n, int k
     maxneg_kernel<float><<<bv, 256, 0, s>>>((const float*)V, n * k, &st->maxneg_v);
   }
   state_start_kernel<<<1, 1, 0, s>>>(st, n_shift);
-}
-
-// f = 1/2 ||X||^2 - <X^T U, V> + 1/2 <U^T U, V^T V>, then the stage update.
-__global__ void iter_finalize_kernel(DevState* st, const double* dot_part, int ndot,
-                                     const double* Gu, const double* Gv, int k, double* trace,
-                                     int trace_idx) {
-  __shared__ double sh[256];
-  double g = 0.0;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) g = fma(Gu[e], Gv[e], g);
-  g = block_sum(g, sh);
-  if (threadIdx.x == 0) {
-    double d = 0.0;
-    for (int b = 0; b < ndot; ++b) d += dot_part[b];
-    double f = 0.5 * st->normX2 - d + 0.5 * g;
-    if (trace) trace[trace_idx] = f;
-    if (st->stage == 0) st->asc_iters += 1;
-    else st->hals_iters += 1;
-    st->k += 1;
-    if (st->stage == 0 && !(st->negU || st->negV)) st->stage = 1;
-    st->negU = 0;
-    st->negV = 0;
-  }
-}
-
-void launch_iter_finalize(DevState* st, const double* dot_part, int ndot, const double* Gu,
-                          const double* Gv, int k, double* trace, int trace_idx, cudaStream_t s) {
-  note_launch(1);
-  iter_finalize_kernel<<<1, 256, 0, s>>>(st, dot_part, ndot, Gu, Gv, k, trace, trace_idx);
 }
 
 // -------------------------------------------------------------- ADMM pass
