@@ -117,6 +117,27 @@ def make_inputs():
     return X, r
 
 
+def sweep_traffic():
+    """DRAM bytes per launch of the tensor-core sweep, from the committed ncu
+    summary, if that summary was taken on the current kernel source (its
+    recorded SHA-256 of tc_sweep.cu matches); else None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2605_19325_gb300", "csrc", "tc_sweep.cu")
+    summ = os.path.join(ROOT, "profiles", "sweep_tc_kernel_8192x6144_r32.md")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        fields = {}
+        for line in open(summ):
+            if ":" in line and line.startswith("- "):
+                key, val = line[2:].split(":", 1)
+                fields[key.strip()] = val.strip().strip("`")
+        if fields.get("tc_sweep.cu sha256") != digest:
+            return None
+        return float(fields["dram bytes per launch (read + write)"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -329,11 +350,11 @@ def run_ours(args):
         peak = pk.get("hbm_gbs", 6800.0)
         roof = {"kernel": "tensor-core X sweep (TMA + tcgen05, BF16 X)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": sweep_traffic(),
                 "algorithmic_bytes_per_launch": bytes_per_sweep,
                 "sweep_us_avg": avg_sweep_s * 1e6, "sweeps_timed": sweeps,
                 "peak_source": "measured HBM copy (burst)" + (" [fallback]" if pk.get("fallback") else ""),
-                "timed_span": "split/transpose of the factor + tensor-core sweep + split reduction"}
+                "timed_span": "one tensor-core sweep kernel (X_hi pass incl. stream-K fix-up)"}
     else:
         flops_per_sweep = 2.0 * M * N * r
         achieved = flops_per_sweep / avg_sweep_s / 1e12 if sweeps else None

@@ -231,9 +231,10 @@ enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V, int32_t n
                        const enmf_iter_opts* iter, double* out3);
 
 /* ---- Measurement (no counterpart in the paper) ---------------------------
- * enmf_profile: every > 0 records CUDA events around the X V and X^T U sweeps
- * of every `every`-th alternation in enmf_iterate (on the context stream, up
- * to 128 alternations per call); 0 turns it off.  enmf_profile_read returns
+ * enmf_profile: every > 0 records CUDA events around the X V and X^T U sweep
+ * kernels (the main pass over X alone: not the factor split or the X_lo
+ * correction pass) of every `every`-th alternation in enmf_iterate (on the
+ * context stream, up to 128 alternations per call); 0 turns it off.  enmf_profile_read returns
  * the summed sweep time (ms) and the number of timed sweeps, optionally
  * resetting them; it synchronises the stream.
  * enmf_probe_fma_peak: measured FMA throughput (flop/s) of the current device

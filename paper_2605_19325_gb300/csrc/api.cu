@@ -633,38 +633,54 @@ static int half_grid(enmf_ctx* ctx, int64_t rows, int grid) {
 // ------------------------------------------------------------ the sweeps
 // corr: 0 = X_hi only, 1 = add the stored X_lo term, 2 = refresh the X_lo
 // term with the current factor first (tensor-core form; ignored otherwise).
-static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int corr) {
+// Profiling: with `rec`, CUDA events bracket the main X pass alone (not the
+// factor split or the X_lo correction pass).
+static void prof_mark(enmf_ctx* ctx, bool rec) {
+  if (rec) cudaEventRecord(ctx->pev[ctx->npev++], ctx->stream);
+}
+
+static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int corr,
+                     bool rec = false) {
   const enmf_problem& p = ctx->p;
   cudaStream_t s = ctx->stream;
   const int r = p.r;
   if (!ctx->tc) {
+    prof_mark(ctx, rec);
     launch_xv(X, ctx->xdt, p.m, p.n, p.ldx, V, r, r, out, r, ctx->fdt, ctx->splitk, ctx->num_sms, s);
+    prof_mark(ctx, rec);
     return;
   }
   launch_split_transpose((const float*)V, p.n, r, ctx->vth, ctx->vtl, ctx->ldn, s);
   if (corr == 2 && ctx->xl)
     launch_tc_sweep(0, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_VH], ctx->maps[MAP_VL], p.m, p.n,
                     r, ctx->cv, nullptr, ctx->tcpart, ctx->tccount, ctx->num_sms, ctx->err, s);
+  prof_mark(ctx, rec);
   launch_tc_sweep(0, ctx->rp, ctx->maps[MAP_XH], ctx->maps[MAP_VH], ctx->maps[MAP_VL], p.m, p.n, r,
                   (float*)out, (corr >= 1 && ctx->xl) ? ctx->cv : nullptr, ctx->tcpart,
                   ctx->tccount, ctx->num_sms, ctx->err, s);
+  prof_mark(ctx, rec);
 }
 
-static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, int corr) {
+static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, int corr,
+                      bool rec = false) {
   const enmf_problem& p = ctx->p;
   cudaStream_t s = ctx->stream;
   const int r = p.r;
   if (!ctx->tc) {
+    prof_mark(ctx, rec);
     launch_xtu(X, ctx->xdt, p.m, p.n, p.ldx, U, r, r, out, r, ctx->fdt, ctx->splitk, ctx->num_sms, s);
+    prof_mark(ctx, rec);
     return;
   }
   launch_split_transpose((const float*)U, p.m, r, ctx->uth, ctx->utl, ctx->ldm, s);
   if (corr == 2 && ctx->xl)
     launch_tc_sweep(1, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_UH], ctx->maps[MAP_UL], p.n, p.m,
                     r, ctx->cu, nullptr, ctx->tcpart, ctx->tccount, ctx->num_sms, ctx->err, s);
+  prof_mark(ctx, rec);
   launch_tc_sweep(1, ctx->rp, ctx->maps[MAP_XH], ctx->maps[MAP_UH], ctx->maps[MAP_UL], p.n, p.m, r,
                   (float*)out, (corr >= 1 && ctx->xl) ? ctx->cu : nullptr, ctx->tcpart,
                   ctx->tccount, ctx->num_sms, ctx->err, s);
+  prof_mark(ctx, rec);
 }
 
 static enmf_status check_staged(enmf_ctx* ctx, const void* X) {
@@ -725,13 +741,9 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
     const int corr = (it % o.correct_every == 0) ? 2 : 1;
     const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
                      ctx->npev + 4 <= 2 * PROF_PAIRS;
-    if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
-    sweep_xv(ctx, X, V, ctx->M0, corr);
-    if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
+    sweep_xv(ctx, X, V, ctx->M0, corr, rec);
     run_half(ctx, 0, U, ctx->M0, ctx->Gv, m, o, false, ctx->Gu, nullptr, nullptr, 0);
-    if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
-    sweep_xtu(ctx, X, U, ctx->N0, corr);
-    if (rec) cudaEventRecord(ctx->pev[ctx->npev++], s);
+    sweep_xtu(ctx, X, U, ctx->N0, corr, rec);
     run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu, o.trace, it);
   }
   rc = check_launch(ctx);

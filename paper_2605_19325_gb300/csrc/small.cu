@@ -323,10 +323,74 @@ void launch_polar(const double* M, int k, double* R, double* D, double tol, DevS
 }
 
 // ------------------------------------------------------ Gram -> orth map
-// G (k x k, symmetric PSD).  One-sided Jacobi on its columns gives G V = A
-// with orthogonal columns; for PSD G the columns of V are eigenvectors and
-// |a_c| the eigenvalues.  T = V_kept diag(lambda^-1/2) for lambda > tau *
+// G = Y^T Y (k x k, symmetric PSD) -> T (k x k) with Y T orthonormal.
+//
+// Fast path, scaled Cholesky: with D = diag(G)^-1/2 and D G D = L L^T,
+// T = D L^-T (then (Y T)^T (Y T) = L^-1 D G D L^-T = I).  It is taken when
+// every pivot of D G D is above tau (the diagonal is 1 after scaling), i.e. Y
+// has no direction near the truncation threshold; the caller runs two passes,
+// so the orthogonality lost to cond(G) in the first is restored by the second.
+//
+// Otherwise (a pivot at or below tau: Y numerically rank deficient), the
+// eigen path: one-sided Jacobi on the columns of G gives G V = A with
+// orthogonal columns; for PSD G the columns of V are eigenvectors and |a_c|
+// the eigenvalues.  T = V_kept diag(lambda^-1/2) for lambda > tau *
 // lambda_max (dropped directions give zero columns).
+__device__ bool chol_orth(const double* __restrict__ G, int k, double tau, double* C,
+                          double* Li, double* dsc, double* T) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = 1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += SM_T) {
+    const double g = G[i * k + i];
+    if (!(g > 0.0)) ok = 0;
+    dsc[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+  }
+  __syncthreads();
+  if (!ok) return false;
+  for (int e = threadIdx.x; e < k * k; e += SM_T) {
+    const int i = e / k, j = e % k;
+    C[e] = G[e] * dsc[i] * dsc[j];
+  }
+  __syncthreads();
+  // right-looking Cholesky, lower triangle of C (row-major) becomes L
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = C[j * k + j];
+      if (d > tau) C[j * k + j] = sqrt(d);
+      else ok = 0;
+    }
+    __syncthreads();
+    if (!ok) return false;
+    const double ljj = C[j * k + j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += SM_T) C[i * k + j] /= ljj;
+    __syncthreads();
+    const int w = k - j - 1;   // trailing block (j+1 .. k-1), lower triangle
+    for (int e = threadIdx.x; e < w * w; e += SM_T) {
+      const int i = j + 1 + e / w, c = j + 1 + e % w;
+      if (c <= i) C[i * k + c] = fma(-C[i * k + j], C[c * k + j], C[i * k + c]);
+    }
+    __syncthreads();
+  }
+  // L^-1 by forward substitution, one column per thread
+  for (int c = threadIdx.x; c < k; c += SM_T) {
+    for (int i = 0; i < c; ++i) Li[i * k + c] = 0.0;
+    Li[c * k + c] = 1.0 / C[c * k + c];
+    for (int i = c + 1; i < k; ++i) {
+      double s = 0.0;
+      for (int p = c; p < i; ++p) s = fma(C[i * k + p], Li[p * k + c], s);
+      Li[i * k + c] = -s / C[i * k + i];
+    }
+  }
+  __syncthreads();
+  // T_pq = D_p (L^-1)_qp
+  for (int e = threadIdx.x; e < k * k; e += SM_T) {
+    const int p = e / k, q = e % k;
+    T[e] = dsc[p] * Li[q * k + p];
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(SM_T)
 eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, int* kept, int* err) {
   extern __shared__ double smd[];
@@ -335,6 +399,11 @@ eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, int*
   double* V = A + (size_t)Np * k;
   double* nrm = V + (size_t)Np * Np;
   int* ord = reinterpret_cast<int*>(nrm + Np + (size_t)Np * Np);
+  if (chol_orth(G, k, tau, A, V, nrm, T)) {
+    if (threadIdx.x == 0) *kept = k;
+    return;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < Np * k; e += SM_T) {
     int c = e / k, i = e % k;
     A[e] = c < k ? G[i * k + c] : 0.0;
