@@ -545,17 +545,20 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
   CK(cudaMemsetAsync(ctx->Yb, 0, (size_t)(m + n) * k * type_size(fdt), s));
   rot_start_kernel<<<1, 256, 0, s>>>(ctx->R, ctx->T2, k, ctx->st);
   note_launch(1);
-  int steps_launched = 0;
   const int check_every = 16;
-  for (int it = 0; it < o.max_iter; ++it) {
+  if (fdt == T_F32) {
+    // every ADMM step in one persistent kernel (admm.cu)
+    launch_admm_f32((const float*)U, (const float*)V, m, n, k, ctx->R, (float*)ctx->Zb,
+                    (float*)ctx->Yb, rho, o.max_iter, o.tol, ctx->st, ctx->part, ctx->Msm,
+                    ctx->err, ctx->num_sms, s);
+  }
+  // FP64 factors: one ADMM pass, the fixed-order sum of M = W^T B and the
+  // warm-started FP64 Jacobi polar factor per step
+  for (int it = 0; fdt == T_F64 && it < o.max_iter; ++it) {
     launch_admm_pass(U, V, m, n, k, fdt, ctx->R, ctx->Zb, ctx->Yb, rho, it == 0, ctx->st,
                      ctx->part, s);
-    launch_part_reduce(ctx->part, k * k, ctx->Msm, s);   // M = W^T B, fixed order
-    if (fdt == T_F64)
-      launch_polar(ctx->Msm, k, ctx->R, ctx->T2, o.tol, ctx->st, ctx->err, s);
-    else
-      launch_polar_ns(ctx->Msm, k, ctx->R, o.tol, ctx->st, ctx->err, s);
-    ++steps_launched;
+    launch_part_reduce(ctx->part, k * k, ctx->Msm, s);
+    launch_polar(ctx->Msm, k, ctx->R, ctx->T2, o.tol, ctx->st, ctx->err, s);
     if ((it + 1) % check_every == 0 && it + 1 < o.max_iter) {
       rc = check_launch(ctx);
       if (rc) return rc;

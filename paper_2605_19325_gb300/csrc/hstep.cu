@@ -28,75 +28,22 @@
 // each block contributes <U^T U, its partial> and block 0 sums those scalars
 // after the same barrier: one barrier per half step in the HALS stage.
 #include "internal.h"
+#include "lanes.cuh"
 
 namespace enmf {
 namespace {
 
+using namespace lanes;
+
 constexpr int HT = 256;          // threads per block
-constexpr int LPR = 8;           // lanes per row
 constexpr int RPB = HT / LPR;    // rows per block per pass
-constexpr unsigned FULL = 0xffffffffu;
-
-template <typename T>
-__device__ __forceinline__ T shfl8(T v, int src) {
-  return __shfl_sync(FULL, v, src, LPR);
-}
-
-// Sum over the eight lanes of a row.  The butterfly gives every lane the same
-// bits: each step adds a pair whose order only commutes.
-template <typename T>
-__device__ __forceinline__ T sum8(T v) {
-  v += __shfl_xor_sync(FULL, v, 4, LPR);
-  v += __shfl_xor_sync(FULL, v, 2, LPR);
-  v += __shfl_xor_sync(FULL, v, 1, LPR);
-  return v;
-}
 
 // Sum of n cross-block partials written before a grid barrier, by the whole
 // block in a fixed order (L1 bypassed).  Every thread gets the result.
 __device__ __forceinline__ double sum_partials(const double* p, int n, double* sh) {
   double s = 0.0;
   for (int b = threadIdx.x; b < n; b += HT) s += __ldcg(&p[b]);
-  return block_sum(s, sh);
-}
-
-template <typename TF, int E>
-__device__ __forceinline__ void load_row(const TF* P, int64_t i, bool live, int k, int sub,
-                                         TF (&v)[E]) {
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int l = sub + LPR * e;
-    v[e] = (live && l < k) ? P[i * k + l] : TF(0);
-  }
-}
-
-template <typename TF, int E>
-__device__ __forceinline__ void store_row(TF* P, int64_t i, bool live, int k, int sub,
-                                          const TF (&v)[E]) {
-  if (!live) return;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int l = sub + LPR * e;
-    if (l < k) P[i * k + l] = v[e];
-  }
-}
-
-// s_l = sum_m u_m G_ml for the lane's entries l (G symmetric, KP x KP in
-// shared memory), m in increasing order; u_m comes from its owner lane.
-template <typename TF, int KP>
-__device__ __forceinline__ void row_times_gram(const TF* Gs, const TF (&u)[KP / LPR], int k,
-                                               int sub, TF (&s)[KP / LPR]) {
-  constexpr int E = KP / LPR;
-#pragma unroll
-  for (int e = 0; e < E; ++e) s[e] = TF(0);
-#pragma unroll
-  for (int m = 0; m < KP; ++m) {
-    if (m < k) {
-      const TF um = shfl8(u[m / LPR], m % LPR);
-#pragma unroll
-      for (int e = 0; e < E; ++e) s[e] = fma(um, Gs[m * KP + sub + LPR * e], s[e]);
-    }
-  }
+  return block_sum256(s, sh);
 }
 
 // Adds the block's pass of rows (staged in `us`) to the thread's Gram
@@ -104,24 +51,12 @@ __device__ __forceinline__ void row_times_gram(const TF* Gs, const TF (&u)[KP / 
 template <typename TF, int KP>
 __device__ __forceinline__ void gram_pass(TF* us, const TF (&u)[KP / LPR], int rloc, int sub,
                                           TF (&gacc)[KP / 16][KP / 16]) {
-  constexpr int E = KP / LPR, S = KP / 16;
+  constexpr int E = KP / LPR;
   __syncthreads();   // the previous pass has been consumed
 #pragma unroll
   for (int e = 0; e < E; ++e) us[rloc * KP + sub + LPR * e] = u[e];
   __syncthreads();
-  const int bi = threadIdx.x / 16, bj = threadIdx.x % 16;
-  for (int rr = 0; rr < RPB; ++rr) {
-    TF x[S], y[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      x[s] = us[rr * KP + bi * S + s];
-      y[s] = us[rr * KP + bj * S + s];
-    }
-#pragma unroll
-    for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) gacc[s1][s2] = fma(x[s1], y[s2], gacc[s1][s2]);
-  }
+  accumulate_outer<TF, KP>(us, us, RPB, gacc);
 }
 
 template <typename TF, int KP>
@@ -176,7 +111,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
       TF u[E], av[E], q[E];
       load_row(F, i, live, k, sub, u);
       load_row(A, i, live, k, sub, av);
-      row_times_gram<TF, KP>(Gs, u, k, sub, q);
+      row_times<TF, KP>(Gs, u, k, sub, q);
 #pragma unroll
       for (int e = 0; e < E; ++e) q[e] = av[e] - q[e];
 #pragma unroll
@@ -221,7 +156,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
         if (u[e] < TF(0)) u[e] = u[e] + sft;   // Eq. 8 / 9, literal (no clamp)
         if (u[e] >= TF(0)) bits |= 1u << e;
       }
-      row_times_gram<TF, KP>(Gs, u, k, sub, g);
+      row_times<TF, KP>(Gs, u, k, sub, g);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         g[e] = ((bits >> e) & 1u) ? g[e] - av[e] : TF(0);
@@ -231,7 +166,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
       store_row(gb, i, live, k, sub, g);
       if (live) mk[i * 8 + sub] = (unsigned char)bits;
     }
-    double bsum = block_sum(acc, sh);
+    double bsum = block_sum256(acc, sh);
     if (t == 0) a.part[blockIdx.x] = bsum;
     grid_sync(&st->bar, a.err);
     const double g0 = sqrt(sum_partials(a.part, gridDim.x, sh));
@@ -247,7 +182,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
         load_row(A, i, live, k, sub, av);
         const unsigned bits = live ? mk[i * 8 + sub] : 0u;
         // d_i = ||g_i||^2 / (g_i G g_i^T)   (Eq. 10; App. B)
-        row_times_gram<TF, KP>(Gs, g, k, sub, tg);
+        row_times<TF, KP>(Gs, g, k, sub, tg);
         TF num = TF(0), den = TF(0);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -263,7 +198,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
             const TF v = u[e] - d * g[e];
             u[e] = v > TF(0) ? v : TF(0);   // (.)_+ of the PBCD update
           }
-        row_times_gram<TF, KP>(Gs, u, k, sub, g);
+        row_times<TF, KP>(Gs, u, k, sub, g);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           g[e] = ((bits >> e) & 1u) ? g[e] - av[e] : TF(0);
@@ -273,7 +208,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
         store_row(gb, i, live, k, sub, g);
       }
       double* pbuf = a.part + (size_t)((it + 1) & 1) * gridDim.x;
-      bsum = block_sum(acc, sh);
+      bsum = block_sum256(acc, sh);
       if (t == 0) pbuf[blockIdx.x] = bsum;
       grid_sync(&st->bar, a.err);
       const double bc = sum_partials(pbuf, gridDim.x, sh);
@@ -325,33 +260,18 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
         }
       }
     if (a.finalize) {
-      obj = block_sum(obj, sh);
+      obj = block_sum256(obj, sh);
       if (t == 0) a.obj_part[blockIdx.x] = obj;
     }
   }
   if (a.dot_part) {
-    const double dsum = block_sum(dotacc, sh);
+    const double dsum = block_sum256(dotacc, sh);
     if (t == 0) a.dot_part[blockIdx.x] = dsum;
   }
   grid_sync(&st->bar, a.err);
 
-  // ---- G_out = sum of the block partials in block order: each entry by
-  // eight consecutive lanes (lane g takes partials g, g + 8, ...), combined
-  // by a fixed shuffle tree.
-  {
-    const int grp = t & 7;
-    const int nb = (int)gridDim.x;
-    for (int e0 = (int)blockIdx.x * (HT / 8); e0 < kk; e0 += (int)gridDim.x * (HT / 8)) {
-      const int e = e0 + t / 8;
-      double s = 0.0;
-      if (e < kk)
-        for (int b = grp; b < nb; b += 8) s += __ldcg(&a.gpart[(int64_t)b * kk + e]);
-      s += __shfl_down_sync(FULL, s, 4, 8);
-      s += __shfl_down_sync(FULL, s, 2, 8);
-      s += __shfl_down_sync(FULL, s, 1, 8);
-      if (grp == 0 && e < kk) a.G_out[e] = s;
-    }
-  }
+  // ---- G_out = sum of the block partials in block order
+  sum_block_partials<HT>(a.gpart, (int)gridDim.x, kk, a.G_out);
   if (!a.finalize || blockIdx.x != 0) return;
 
   // ---- end of the alternation (block 0): objective and stage update
@@ -389,8 +309,6 @@ void hstep_launch(const HalfArgs& a, int grid, cudaStream_t s) {
   cudaLaunchCooperativeKernel((void*)hstep_kernel<TF, KP>, dim3(grid), dim3(HT), args,
                               hstep_smem<TF, KP>(), s);
 }
-
-int rank_pad16(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 48 ? 48 : 64)); }
 
 }  // namespace
 

@@ -138,14 +138,19 @@ void launch_rr_residual(const void* Y, int ldy, int ky, const void* Q, int ldq, 
 void launch_kkt_rows(const void* F, const void* A, const double* G, int64_t rows, int k, int fdt,
                      double* part, double* out, cudaStream_t s);
 
+// ----------------------------------------------------------------- admm.cu
+// All steps of Algorithm 1 for FP32 factors in one cooperative launch: W =
+// [U; V], R (k x k FP64) from R_0 in / final R out, Z, Y ((m + n) x k, Y zero
+// at entry), part (>= NPART x k x k doubles), M (k x k).  Updates st->dR,
+// admm_steps, admm_done, jac_sweeps.
+void launch_admm_f32(const float* U, const float* V, int64_t m, int64_t n, int k, double* R,
+                     float* Z, float* Y, double rho, int max_iter, double tol, DevState* st,
+                     double* part, double* M, int* err, int num_sms, cudaStream_t s);
+
 // ---------------------------------------------------------------- small.cu
 // R_new = polar(sum of NPART partial M's); dR, convergence, ADMM step count.
 void launch_polar(const double* M, int k, double* R, double* D, double tol,
                   DevState* st, int* err, cudaStream_t s);
-// Same update for the reduced-precision forms: FP32 Newton-Schulz polar
-// iteration plus one FP64 Newton-Schulz step.
-void launch_polar_ns(const double* M, int k, double* R, double tol, DevState* st, int* err,
-                     cudaStream_t s);
 // Orthonormalising transform of a Gram G (k x k): eigen-decomposition by
 // one-sided Jacobi, keep eigenvalues > tau * lambda_1, T = V_k diag(l^-1/2).
 // Writes T (k x k, unused columns zero) and *kept.

@@ -1,0 +1,142 @@
+// Eight-lanes-per-row helpers shared by the row kernels (hstep.cu, admm.cu).
+//
+// A factor row of rank k (padded to KP = 16, 32, 48 or 64; padded entries are
+// zero) is held in registers by eight consecutive lanes: lane `sub` owns the
+// entries l = sub + 8 e, e < KP / 8.  Products with a KP x KP matrix in shared
+// memory take each entry from its owner lane by a shuffle, so the FMAs of a
+// lane are independent of each other.
+#pragma once
+
+#include "common.cuh"
+
+namespace enmf {
+namespace lanes {
+
+constexpr int LPR = 8;   // lanes per row
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T shfl8(T v, int src) {
+  return __shfl_sync(FULL, v, src, LPR);
+}
+
+// Sum over the eight lanes of a row.  The butterfly gives every lane the same
+// bits: each step adds a pair whose order only commutes.
+template <typename T>
+__device__ __forceinline__ T sum8(T v) {
+  v += __shfl_xor_sync(FULL, v, 4, LPR);
+  v += __shfl_xor_sync(FULL, v, 2, LPR);
+  v += __shfl_xor_sync(FULL, v, 1, LPR);
+  return v;
+}
+
+template <typename TF, int E>
+__device__ __forceinline__ void load_row(const TF* P, int64_t i, bool live, int k, int sub,
+                                         TF (&v)[E]) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int l = sub + LPR * e;
+    v[e] = (live && l < k) ? P[i * k + l] : TF(0);
+  }
+}
+
+template <typename TF, int E>
+__device__ __forceinline__ void store_row(TF* P, int64_t i, bool live, int k, int sub,
+                                          const TF (&v)[E]) {
+  if (!live) return;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int l = sub + LPR * e;
+    if (l < k) P[i * k + l] = v[e];
+  }
+}
+
+// s_l = sum_m u_m Ms[m][l] for the lane's entries l (Ms: KP x KP row-major in
+// shared memory), m in increasing order; u_m comes from its owner lane.
+template <typename TF, int KP>
+__device__ __forceinline__ void row_times(const TF* Ms, const TF (&u)[KP / LPR], int k, int sub,
+                                          TF (&s)[KP / LPR]) {
+  constexpr int E = KP / LPR;
+#pragma unroll
+  for (int e = 0; e < E; ++e) s[e] = TF(0);
+#pragma unroll
+  for (int m = 0; m < KP; ++m) {
+    if (m < k) {
+      const TF um = shfl8(u[m / LPR], m % LPR);
+#pragma unroll
+      for (int e = 0; e < E; ++e) s[e] = fma(um, Ms[m * KP + sub + LPR * e], s[e]);
+    }
+  }
+}
+
+// Adds sum over the block's staged rows of x_row^T y_row to the thread's
+// (KP/16) x (KP/16) sub-block (bi, bj) = (thread / 16, thread % 16) of a
+// KP x KP product, for a block of 256 threads; xs and ys hold `nrows` rows of
+// KP entries.  The caller stages the rows and synchronises.
+template <typename TF, int KP>
+__device__ __forceinline__ void accumulate_outer(const TF* xs, const TF* ys, int nrows,
+                                                 TF (&acc)[KP / 16][KP / 16]) {
+  constexpr int S = KP / 16;
+  const int bi = threadIdx.x / 16, bj = threadIdx.x % 16;
+  for (int rr = 0; rr < nrows; ++rr) {
+    TF x[S], y[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      x[s] = xs[rr * KP + bi * S + s];
+      y[s] = ys[rr * KP + bj * S + s];
+    }
+#pragma unroll
+    for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = fma(x[s1], y[s2], acc[s1][s2]);
+  }
+}
+
+// out[e] = sum over the nb blocks of part[b * kk + e] (FP64 partials written
+// before a grid barrier), for e < kk, spread over the grid: each entry by eight
+// consecutive lanes (lane g takes partials g, g + 8, ...) combined by a fixed
+// shuffle tree, so the order does not depend on timing.  Block of BT threads.
+template <int BT>
+__device__ __forceinline__ void sum_block_partials(const double* part, int nb, int kk,
+                                                   double* out) {
+  const int grp = threadIdx.x & 7;
+  for (int e0 = (int)blockIdx.x * (BT / 8); e0 < kk; e0 += (int)gridDim.x * (BT / 8)) {
+    const int e = e0 + (int)threadIdx.x / 8;
+    double s = 0.0;
+    if (e < kk) {
+      // four independent chains (partials g + 32 q + 8 c go to chain c), so
+      // four loads are in flight; then a fixed combine
+      double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+      int b = grp;
+      for (; b + 24 < nb; b += 32) {
+        c0 += __ldcg(&part[(int64_t)b * kk + e]);
+        c1 += __ldcg(&part[(int64_t)(b + 8) * kk + e]);
+        c2 += __ldcg(&part[(int64_t)(b + 16) * kk + e]);
+        c3 += __ldcg(&part[(int64_t)(b + 24) * kk + e]);
+      }
+      for (; b < nb; b += 8) c0 += __ldcg(&part[(int64_t)b * kk + e]);
+      s = (c0 + c1) + (c2 + c3);
+    }
+    s += __shfl_down_sync(FULL, s, 4, 8);
+    s += __shfl_down_sync(FULL, s, 2, 8);
+    s += __shfl_down_sync(FULL, s, 1, 8);
+    if (grp == 0 && e < kk) out[e] = s;
+  }
+}
+
+// Sum over a block of 256 threads with two barriers: a butterfly within each
+// warp (every lane gets the same bits), then the eight warp sums in warp
+// order.  Every thread returns the total; `sh` needs 8 doubles.
+__device__ __forceinline__ double block_sum256(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  __syncthreads();   // sh free from any previous use
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  return ((sh[0] + sh[1]) + (sh[2] + sh[3])) + ((sh[4] + sh[5]) + (sh[6] + sh[7]));
+}
+
+inline int rank_pad16(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 48 ? 48 : 64)); }
+
+}  // namespace lanes
+}  // namespace enmf

@@ -1,9 +1,11 @@
 // Small dense FP64 linear algebra on one CTA: the r x r and l x l steps of the
-// method, all by one-sided (Hestenes) Jacobi SVD in shared memory.
-//   * polar_kernel     -- R update of Algorithm 1: R = C D^T from the SVD of
-//                         M = W^T B (orthogonal Procrustes, Sec. 4.1.2);
+// method, in shared memory, mostly by one-sided (Hestenes) Jacobi SVD.
+//   * polar_kernel     -- R update of Algorithm 1 with FP64 factors: R = C D^T
+//                         from the SVD of M = W^T B (orthogonal Procrustes,
+//                         Sec. 4.1.2); the FP32 forms use admm.cu;
 //   * eig_orth_kernel  -- orthonormalising transform of a Gram matrix (SVD
-//                         start's range finder);
+//                         start's range finder): scaled Cholesky, or the
+//                         Jacobi eigen map when the Gram is near singular;
 //   * rr_svd_kernel    -- SVD of the Rayleigh-Ritz matrix of the SVD start;
 //   * svd_finish / rr_prep -- U* = U_r S^(1/2), V* = V_r S^(1/2) transforms
 //                         with the sign rule.
@@ -215,97 +217,6 @@ polar_kernel(const double* __restrict__ Mg, int k, double* R, double* D, double 
     if (sw > JAC_MAX_SWEEPS - 1 || !(smin > 0.0)) atomicOr(err, ERR_NOTCONV);
     if (dR <= tol * sqrt((double)k)) st->admm_done = 1;
   }
-}
-
-// ----------------------------------------------- polar by Newton-Schulz
-// Reduced-precision forms: the polar factor of M (k x k) by the Newton-Schulz
-// iteration X <- X (3 I - X^T X) / 2 from X0 = M / ||M||_F (every singular
-// value in (0, 1], each iteration maps s to s (3 - s^2) / 2, which tends to 1),
-// run in FP32 until ||X^T X - I||_F < 1e-5, then one step in FP64, which
-// squares the remaining orthogonality error.  M itself carries FP32
-// precision in these forms (it is summed from FP32 factors).
-__global__ void __launch_bounds__(SM_T)
-polar_ns_kernel(const double* __restrict__ Mg, int k, double* R, double tol, DevState* st,
-                int* err) {
-  extern __shared__ double smd[];
-  __shared__ double red[SM_T];
-  __shared__ int stop;
-  if (*(volatile int*)&st->admm_done) return;
-  double* Xd = smd;                                    // k x k
-  double* Pd = Xd + (size_t)k * k;                     // k x k
-  float* Xs = reinterpret_cast<float*>(Pd + (size_t)k * k);
-  float* Ps = Xs + (size_t)k * k;
-  float* Ys = Ps + (size_t)k * k;
-  double nf = 0.0;
-  for (int e = threadIdx.x; e < k * k; e += SM_T) nf = fma(Mg[e], Mg[e], nf);
-  nf = sqrt(block_sum(nf, red));
-  const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
-  for (int e = threadIdx.x; e < k * k; e += SM_T) Xs[e] = (float)(Mg[e] * inv);
-  __syncthreads();
-  int it = 0;
-  for (; it < 100; ++it) {
-    for (int e = threadIdx.x; e < k * k; e += SM_T) {   // P = X^T X
-      const int i = e / k, j = e % k;
-      float s = 0.f;
-      for (int l = 0; l < k; ++l) s = fmaf(Xs[l * k + i], Xs[l * k + j], s);
-      Ps[e] = s;
-    }
-    __syncthreads();
-    float d = 0.f;
-    for (int e = threadIdx.x; e < k * k; e += SM_T) {
-      const float x = Ps[e] - ((e / k == e % k) ? 1.f : 0.f);
-      d = fmaf(x, x, d);
-    }
-    const double dd = block_sum((double)d, red);
-    if (threadIdx.x == 0) stop = dd < 1e-10;
-    for (int e = threadIdx.x; e < k * k; e += SM_T) {   // Y = X (3 I - P) / 2
-      const int i = e / k, j = e % k;
-      float s = 0.f;
-      for (int l = 0; l < k; ++l) s = fmaf(Xs[i * k + l], Ps[l * k + j], s);
-      Ys[e] = 1.5f * Xs[e] - 0.5f * s;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < k * k; e += SM_T) Xs[e] = Ys[e];
-    __syncthreads();
-    if (stop) break;
-  }
-  // one FP64 step, X <- X (3 I - X^T X) / 2, then R_new = X
-  for (int e = threadIdx.x; e < k * k; e += SM_T) Xd[e] = (double)Xs[e];
-  __syncthreads();
-  for (int e = threadIdx.x; e < k * k; e += SM_T) {
-    const int i = e / k, j = e % k;
-    double s = 0.0;
-    for (int l = 0; l < k; ++l) s = fma(Xd[l * k + i], Xd[l * k + j], s);
-    Pd[e] = s;
-  }
-  __syncthreads();
-  double d = 0.0;
-  for (int e = threadIdx.x; e < k * k; e += SM_T) {
-    const int i = e / k, j = e % k;
-    double s = 0.0;
-    for (int l = 0; l < k; ++l) s = fma(Xd[i * k + l], Pd[l * k + j], s);
-    const double rn = 1.5 * Xd[e] - 0.5 * s;
-    const double x = rn - R[e];
-    d = fma(x, x, d);
-    R[e] = rn;
-  }
-  d = block_sum(d, red);
-  if (threadIdx.x == 0) {
-    const double dR = sqrt(d);
-    st->dR = dR;
-    st->admm_steps += 1;
-    st->jac_sweeps = it;
-    if (!(nf > 0.0) || it >= 100) atomicOr(err, ERR_NOTCONV);
-    if (dR <= tol * sqrt((double)k)) st->admm_done = 1;
-  }
-}
-
-void launch_polar_ns(const double* M, int k, double* R, double tol, DevState* st, int* err,
-                     cudaStream_t s) {
-  note_launch(1);
-  const size_t smem = (size_t)k * k * (2 * sizeof(double) + 3 * sizeof(float));
-  cudaFuncSetAttribute(polar_ns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  polar_ns_kernel<<<1, SM_T, smem, s>>>(M, k, R, tol, st, err);
 }
 
 static size_t small_smem(int rows, int Np) {
