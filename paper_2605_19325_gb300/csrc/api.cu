@@ -625,12 +625,12 @@ static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const dou
   a.obj_part = ctx->dot_part + 2048;
   a.trace = trace;
   a.trace_idx = trace_idx;
+  if (ctx->tc) {
+    a.th = which == 0 ? ctx->uth : ctx->vth;
+    a.tl = which == 0 ? ctx->utl : ctx->vtl;
+    a.ldt = which == 0 ? ctx->ldm : ctx->ldn;
+  }
   launch_half_step(a, which == 0 ? ctx->grid_u : ctx->grid_v, ctx->stream);
-}
-
-static int half_grid(enmf_ctx* ctx, int64_t rows, int grid) {
-  int64_t need = (rows + 63) / 64;
-  return (int)((int64_t)grid > need ? need : grid);
 }
 
 // ------------------------------------------------------------ the sweeps
@@ -642,8 +642,10 @@ static void prof_mark(enmf_ctx* ctx, bool rec) {
   if (rec) cudaEventRecord(ctx->pev[ctx->npev++], ctx->stream);
 }
 
+// split = false: the BF16 pair of the factor is already current (written by
+// the half step that produced the factor).
 static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int corr,
-                     bool rec = false) {
+                     bool rec = false, bool split = true) {
   const enmf_problem& p = ctx->p;
   cudaStream_t s = ctx->stream;
   const int r = p.r;
@@ -653,7 +655,7 @@ static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int
     prof_mark(ctx, rec);
     return;
   }
-  launch_split_transpose((const float*)V, p.n, r, ctx->vth, ctx->vtl, ctx->ldn, s);
+  if (split) launch_split_transpose((const float*)V, p.n, r, ctx->vth, ctx->vtl, ctx->ldn, s);
   if (corr == 2 && ctx->xl)
     launch_tc_sweep(0, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_VH], ctx->maps[MAP_VL], p.m, p.n,
                     r, ctx->cv, nullptr, ctx->tcpart, ctx->tccount, ctx->num_sms, ctx->err, s);
@@ -665,7 +667,7 @@ static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int
 }
 
 static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, int corr,
-                      bool rec = false) {
+                      bool rec = false, bool split = true) {
   const enmf_problem& p = ctx->p;
   cudaStream_t s = ctx->stream;
   const int r = p.r;
@@ -675,7 +677,7 @@ static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, in
     prof_mark(ctx, rec);
     return;
   }
-  launch_split_transpose((const float*)U, p.m, r, ctx->uth, ctx->utl, ctx->ldm, s);
+  if (split) launch_split_transpose((const float*)U, p.m, r, ctx->uth, ctx->utl, ctx->ldm, s);
   if (corr == 2 && ctx->xl)
     launch_tc_sweep(1, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_UH], ctx->maps[MAP_UL], p.n, p.m,
                     r, ctx->cu, nullptr, ctx->tcpart, ctx->tccount, ctx->num_sms, ctx->err, s);
@@ -737,6 +739,11 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
     g.G_out = ctx->Gv;
     g.gpart = ctx->part;
     g.gram_only = 1;
+    if (ctx->tc) {   // and the BF16 pair of V for the first sweep
+      g.th = ctx->vth;
+      g.tl = ctx->vtl;
+      g.ldt = ctx->ldn;
+    }
     launch_half_step(g, ctx->grid_v, s);
   }
   for (int it = 0; it < o.n_iter; ++it) {
@@ -744,9 +751,9 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
     const int corr = (it % o.correct_every == 0) ? 2 : 1;
     const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
                      ctx->npev + 4 <= 2 * PROF_PAIRS;
-    sweep_xv(ctx, X, V, ctx->M0, corr, rec);
+    sweep_xv(ctx, X, V, ctx->M0, corr, rec, false);
     run_half(ctx, 0, U, ctx->M0, ctx->Gv, m, o, false, ctx->Gu, nullptr, nullptr, 0);
-    sweep_xtu(ctx, X, U, ctx->N0, corr, rec);
+    sweep_xtu(ctx, X, U, ctx->N0, corr, rec, false);
     run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu, o.trace, it);
   }
   rc = check_launch(ctx);

@@ -83,30 +83,39 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 // Sense-by-generation barrier for cooperative launches (all blocks are
 // co-resident).  The spin is bounded: on expiry the barrier records
 // ERR_TIMEOUT in *err and lets the block continue, so no launch can hang.
+// Grid-wide barrier state of the cooperative kernels (zero at creation).
 struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
+  unsigned int word;
+  unsigned int unused;
 };
 
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch, one atomic per block: block 0
+// adds 2^31 - (nb - 1) and every other block adds 1, so over one barrier the
+// word grows by exactly 2^31 -- bit 31 flips at the last arrival, whatever
+// the order, and the low bits return to their value (any grid size may
+// follow).  Thread 0 of each block arrives after a fence that publishes the
+// block's writes (ordered by the preceding __syncthreads) and spins on an
+// acquire load until bit 31 differs from the value its own atomic returned.
+// The spin is bounded: past SPIN_BUDGET_CYCLES it records ERR_TIMEOUT.
 __device__ __forceinline__ void grid_sync(GridBarrier* bar, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &bar->gen;
-    unsigned int g = *vgen;
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    const bool lead = blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+    const unsigned int inc = lead ? 0x80000000u - (nb - 1u) : 1u;
     __threadfence();
-    unsigned int arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long t0 = clock64();
-      while (*vgen == g) {
-        if (clock64() - t0 > SPIN_BUDGET_CYCLES) {
-          atomicOr(err, ERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(64);
+    const unsigned int old = atomicAdd(&bar->word, inc);
+    const long long t0 = clock64();
+    while (((ld_acquire_gpu(&bar->word) ^ old) & 0x80000000u) == 0u) {
+      if (clock64() - t0 > SPIN_BUDGET_CYCLES) {
+        atomicOr(err, ERR_TIMEOUT);
+        break;
       }
     }
     __threadfence();

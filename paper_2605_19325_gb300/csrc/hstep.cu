@@ -27,6 +27,8 @@
 // objective needs <U^T U, V^T V>, which is linear in the V^T V partials, so
 // each block contributes <U^T U, its partial> and block 0 sums those scalars
 // after the same barrier: one barrier per half step in the HALS stage.
+#include <cuda_bf16.h>
+
 #include "internal.h"
 #include "lanes.cuh"
 
@@ -59,6 +61,28 @@ __device__ __forceinline__ void gram_pass(TF* us, const TF (&u)[KP / LPR], int r
   accumulate_outer<TF, KP>(us, us, RPB, gacc);
 }
 
+// The factor operand of the tensor-core sweeps: row i of F written to column
+// i of th = bf16(F^T) and tl = bf16(F^T - th), the same rounding as the
+// stand-alone split of tc_sweep.cu.  FP32 factors only.
+template <typename TF, int E>
+__device__ __forceinline__ void write_split(const HalfArgs& a, int64_t i, bool live, int k,
+                                            int sub, const TF (&u)[E]) {
+  if constexpr (sizeof(TF) == 4) {
+    if (!a.th || !live) return;
+    __nv_bfloat16* th = reinterpret_cast<__nv_bfloat16*>(a.th);
+    __nv_bfloat16* tl = reinterpret_cast<__nv_bfloat16*>(a.tl);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int l = sub + LPR * e;
+      if (l < k) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(u[e]);
+        th[(int64_t)l * a.ldt + i] = h;
+        tl[(int64_t)l * a.ldt + i] = __float2bfloat16_rn(u[e] - __bfloat162float(h));
+      }
+    }
+  }
+}
+
 template <typename TF, int KP>
 __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
   constexpr int E = KP / LPR, S = KP / 16;
@@ -66,6 +90,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
   TF* Gs = reinterpret_cast<TF*>(smraw);   // KP x KP, zero padded
   TF* us = Gs + KP * KP;                   // RPB x KP rows of the current pass
   __shared__ double sh[HT];
+  __shared__ TF ginv[KP];                  // 1 / G_jj (0 where G_jj <= 0)
 
   const int k = a.k;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -82,6 +107,11 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
     }
   }
   __syncthreads();
+  for (int j = t; j < KP; j += HT) {
+    const TF g = Gs[j * KP + j];
+    ginv[j] = g > TF(0) ? TF(1) / g : TF(0);
+  }
+  __syncthreads();
 
   DevState* st = a.st;
   const int stage = *(volatile int*)&st->stage;
@@ -95,12 +125,23 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
 #pragma unroll
     for (int s2 = 0; s2 < S; ++s2) gacc[s1][s2] = TF(0);
   double dotacc = 0.0;
+  // the FP64 U^T U entries of this thread's Gram sub-block, for the objective
+  // partial at the end (loaded now, off the critical path)
+  double guv[S][S];
+#pragma unroll
+  for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) {
+      const int p = (t / 16) * S + s1, c = (t % 16) * S + s2;
+      guv[s1][s2] = (a.finalize && p < k && c < k) ? a.Gu[p * k + c] : 0.0;
+    }
 
   if (a.gram_only) {
     for (int64_t ps = 0; ps < passes; ++ps) {
       const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
       TF u[E];
       load_row(F, i, i < rows, k, sub, u);
+      write_split(a, i, i < rows, k, sub, u);
       gram_pass<TF, KP>(us, u, rloc, sub, gacc);
     }
   } else if (stage == 1) {
@@ -118,10 +159,10 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
       for (int j = 0; j < KP; ++j) {
         if (j < k) {
           const int e = j / LPR, own = j % LPR;
-          const TF gjj = Gs[j * KP + j];
+          const TF gi = ginv[j];
           TF v = u[e], dl = TF(0);
-          if (gjj > TF(0)) {
-            v = u[e] + q[e] / gjj;
+          if (gi > TF(0)) {
+            v = fma(q[e], gi, u[e]);
             v = v > TF(0) ? v : TF(0);
             dl = v - u[e];
           }
@@ -132,6 +173,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
         }
       }
       store_row(F, i, live, k, sub, u);
+      write_split(a, i, live, k, sub, u);
       if (a.dot_part) {
 #pragma unroll
         for (int e = 0; e < E; ++e) dotacc = fma((double)av[e], (double)u[e], dotacc);
@@ -222,6 +264,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
       const bool live = i < rows;
       TF u[E];
       load_row(F, i, live, k, sub, u);
+      write_split(a, i, live, k, sub, u);
       if (live) {
         const unsigned bits = mk[i * 8 + sub];
 #pragma unroll
@@ -256,7 +299,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
         if (p < k && c < k) {
           const double gv = (double)gacc[s1][s2];
           a.gpart[(int64_t)blockIdx.x * kk + p * k + c] = gv;
-          if (a.finalize) obj = fma(a.Gu[p * k + c], gv, obj);
+          if (a.finalize) obj = fma(guv[s1][s2], gv, obj);
         }
       }
     if (a.finalize) {
@@ -270,8 +313,10 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
   }
   grid_sync(&st->bar, a.err);
 
-  // ---- G_out = sum of the block partials in block order
-  sum_block_partials<HT>(a.gpart, (int)gridDim.x, kk, a.G_out);
+  // ---- G_out = sum of the block partials in block order (block 0 left free
+  // for the end-of-alternation work when there are other blocks)
+  sum_block_partials<HT>(a.gpart, (int)gridDim.x, kk, a.G_out,
+                         (a.finalize && gridDim.x > 1) ? 1 : 0);
   if (!a.finalize || blockIdx.x != 0) return;
 
   // ---- end of the alternation (block 0): objective and stage update

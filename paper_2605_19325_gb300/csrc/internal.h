@@ -109,6 +109,12 @@ struct HalfArgs {
   // block decomposition (so a Gram taken at the start of a call is bitwise the
   // one the previous call's last half-step produced)
   int gram_only;
+  // FP32 factors, tensor-core sweeps: also write the updated F transposed as
+  // a BF16 pair, th = bf16(F^T), tl = bf16(F^T - th) (k x ldt), the operand
+  // of the next sweep (null: not written)
+  void* th;
+  void* tl;
+  int64_t ldt;
 };
 // hstep.cu: one cooperative launch per half step; grid <= half_step_grid().
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);

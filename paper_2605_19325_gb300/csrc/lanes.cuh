@@ -93,34 +93,32 @@ __device__ __forceinline__ void accumulate_outer(const TF* xs, const TF* ys, int
 }
 
 // out[e] = sum over the nb blocks of part[b * kk + e] (FP64 partials written
-// before a grid barrier), for e < kk, spread over the grid: each entry by eight
-// consecutive lanes (lane g takes partials g, g + 8, ...) combined by a fixed
-// shuffle tree, so the order does not depend on timing.  Block of BT threads.
+// before a grid barrier), for e < kk, one warp per entry, spread over blocks
+// first .. gridDim.x - 1 (block 0 may be left free for other work): lane l
+// takes partials l + 32 j in eight independent loads, then the eight are
+// combined pairwise and the lanes by a butterfly.  The order is fixed by nb,
+// so the sum does not depend on timing.  Block of BT threads.
 template <int BT>
 __device__ __forceinline__ void sum_block_partials(const double* part, int nb, int kk,
-                                                   double* out) {
-  const int grp = threadIdx.x & 7;
-  for (int e0 = (int)blockIdx.x * (BT / 8); e0 < kk; e0 += (int)gridDim.x * (BT / 8)) {
-    const int e = e0 + (int)threadIdx.x / 8;
+                                                   double* out, int first = 0) {
+  constexpr int WPB = BT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nbk = (int)gridDim.x - first;
+  if ((int)blockIdx.x < first || nbk <= 0) return;
+  for (int e = ((int)blockIdx.x - first) * WPB + warp; e < kk; e += nbk * WPB) {
     double s = 0.0;
-    if (e < kk) {
-      // four independent chains (partials g + 32 q + 8 c go to chain c), so
-      // four loads are in flight; then a fixed combine
-      double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
-      int b = grp;
-      for (; b + 24 < nb; b += 32) {
-        c0 += __ldcg(&part[(int64_t)b * kk + e]);
-        c1 += __ldcg(&part[(int64_t)(b + 8) * kk + e]);
-        c2 += __ldcg(&part[(int64_t)(b + 16) * kk + e]);
-        c3 += __ldcg(&part[(int64_t)(b + 24) * kk + e]);
+    for (int b0 = 0; b0 < nb; b0 += 256) {
+      double c[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int b = b0 + lane + 32 * j;
+        c[j] = b < nb ? __ldcg(&part[(int64_t)b * kk + e]) : 0.0;
       }
-      for (; b < nb; b += 8) c0 += __ldcg(&part[(int64_t)b * kk + e]);
-      s = (c0 + c1) + (c2 + c3);
+      s += ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
     }
-    s += __shfl_down_sync(FULL, s, 4, 8);
-    s += __shfl_down_sync(FULL, s, 2, 8);
-    s += __shfl_down_sync(FULL, s, 1, 8);
-    if (grp == 0 && e < kk) out[e] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) out[e] = s;
   }
 }
 

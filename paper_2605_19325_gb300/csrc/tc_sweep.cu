@@ -394,25 +394,72 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (last_cta && ok) {
           __threadfence();
-          // thread et owns flat elements et + 128 i, i < r (cnt <= 128 r)
-          float acc[RP];
-#pragma unroll
-          for (int i = 0; i < RP; ++i) acc[i] = 0.f;
-          for (int64_t q = c_lo; q <= c_hi; ++q) {
-            const int slot = sk_begin(q, W, G) >= tile * nkb ? 0 : 1;
-            const float* src = part + (q * 2 + slot) * TILE * r;
-#pragma unroll
-            for (int i = 0; i < RP; ++i) {
-              const int f = et + 128 * i;
-              if (f < cnt) acc[i] += __ldcg(&src[f]);
-            }
-          }
+          // Per element: 0, plus each contributor's slot in CTA order, plus
+          // corr.  float4 g of the flat tile goes to thread g % 128; the next
+          // contributor's slot is loaded while the current one is added, so
+          // the contributors' L2 round trips overlap.
           float* o = out + row0 * r;
           const float* cr = corr ? corr + row0 * r : nullptr;
+          const bool vec = ((reinterpret_cast<uintptr_t>(o) | reinterpret_cast<uintptr_t>(cr)) & 15) == 0;
+          const int n4 = vec ? cnt / 4 : 0;
+          auto slot_of = [&](int64_t q) {
+            const int slot = sk_begin(q, W, G) >= tile * nkb ? 0 : 1;
+            return reinterpret_cast<const float4*>(part + (q * 2 + slot) * TILE * r);
+          };
+          constexpr int CH = RP / 4 < 8 ? RP / 4 : 8;   // float4s per thread per chunk
+          for (int g0 = 0; g0 * 128 < n4; g0 += CH) {
+            float4 acc[CH], nxt[CH];
+            const float4* src = slot_of(c_lo);
 #pragma unroll
-          for (int i = 0; i < RP; ++i) {
-            const int f = et + 128 * i;
-            if (f < cnt) o[f] = cr ? acc[i] + cr[f] : acc[i];
+            for (int c = 0; c < CH; ++c) {
+              const int g = et + 128 * (g0 + c);
+              acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+              nxt[c] = g < n4 ? __ldcg(&src[g]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            for (int64_t q = c_lo; q <= c_hi; ++q) {
+              float4 cur[CH];
+#pragma unroll
+              for (int c = 0; c < CH; ++c) cur[c] = nxt[c];
+              if (q < c_hi) {
+                src = slot_of(q + 1);
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                  const int g = et + 128 * (g0 + c);
+                  if (g < n4) nxt[c] = __ldcg(&src[g]);
+                }
+              }
+#pragma unroll
+              for (int c = 0; c < CH; ++c) {
+                acc[c].x += cur[c].x;
+                acc[c].y += cur[c].y;
+                acc[c].z += cur[c].z;
+                acc[c].w += cur[c].w;
+              }
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+              const int g = et + 128 * (g0 + c);
+              if (g < n4) {
+                float4 v = acc[c];
+                if (cr) {
+                  const float4 a = reinterpret_cast<const float4*>(cr)[g];
+                  v.x += a.x;
+                  v.y += a.y;
+                  v.z += a.z;
+                  v.w += a.w;
+                }
+                reinterpret_cast<float4*>(o)[g] = v;
+              }
+            }
+          }
+          // elements past the last whole float4 (or all, when unaligned)
+          for (int f = 4 * n4 + et; f < cnt; f += 128) {
+            float sacc = 0.f;
+            for (int64_t q = c_lo; q <= c_hi; ++q) {
+              const int slot = sk_begin(q, W, G) >= tile * nkb ? 0 : 1;
+              sacc += __ldcg(&part[(q * 2 + slot) * TILE * r + f]);
+            }
+            o[f] = cr ? sacc + cr[f] : sacc;
           }
         }
       }
