@@ -46,6 +46,27 @@ struct enmf_ctx {
   // host-data staging for enmf_solve
   void* hX; void* hU; void* hV;
   size_t hX_bytes;
+  // the iteration loop of enmf_iterate as a CUDA graph (captured on a private
+  // stream, replayed while every argument of the call is unchanged)
+  struct IterKey {
+    const void* X;
+    void* U;
+    void* V;
+    double* trace;
+    int n_iter, pbcd_max_iter, n_shift, correct_every, prof_every;
+    double eps;
+    bool operator==(const IterKey& o) const {
+      return X == o.X && U == o.U && V == o.V && trace == o.trace && n_iter == o.n_iter &&
+             pbcd_max_iter == o.pbcd_max_iter && n_shift == o.n_shift &&
+             correct_every == o.correct_every && prof_every == o.prof_every && eps == o.eps;
+    }
+  };
+  cudaStream_t cap_stream;
+  cudaGraphExec_t iter_graph;
+  IterKey iter_key;
+  int iter_graph_kernels;   // kernel launches per replay
+  int iter_graph_npev;      // profiling events recorded per replay
+  bool no_graph;            // capture failed once: launch eagerly
   // event timing of the X sweeps (enmf_profile)
   int prof_every;
   int npev;
@@ -392,6 +413,8 @@ extern "C" void enmf_destroy(enmf_ctx* ctx) {
   if (ctx->tcws) cudaFree(ctx->tcws);
   if (ctx->prof_every >= 0 && ctx->pev[0])
     for (int i = 0; i < 2 * PROF_PAIRS; ++i) cudaEventDestroy(ctx->pev[i]);
+  if (ctx->iter_graph) cudaGraphExecDestroy(ctx->iter_graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -704,6 +727,64 @@ extern "C" enmf_status enmf_sweep(enmf_ctx* ctx, const void* X, const void* U, c
   return check_launch(ctx);
 }
 
+// Runs the alternation loop as a CUDA graph: captured once on a private
+// stream (the caller's stream may be the legacy default stream, which cannot
+// be captured), instantiated, and replayed on the caller's stream while the
+// key is unchanged.  Returns false (nothing enqueued) when graphs cannot be
+// used, so the caller launches the loop directly.
+template <typename Loop>
+static bool replay_iteration(enmf_ctx* ctx, const enmf_ctx::IterKey& key, Loop&& loop) {
+  if (ctx->no_graph || key.n_iter < 4) return false;
+  if (!ctx->iter_graph || !(ctx->iter_key == key)) {
+    if (ctx->iter_graph) {
+      cudaGraphExecDestroy(ctx->iter_graph);
+      ctx->iter_graph = nullptr;
+    }
+    if (!ctx->cap_stream &&
+        cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->no_graph = true;
+      return false;
+    }
+    cudaStream_t user = ctx->stream;
+    const int npev0 = ctx->npev;
+    const long long l0 = enmf_launch_count();
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) ==
+              cudaSuccess;
+    if (ok) {
+      ctx->stream = ctx->cap_stream;
+      loop();
+      ctx->stream = user;
+      ok = cudaStreamEndCapture(ctx->cap_stream, &g) == cudaSuccess && g;
+    }
+    const int kernels = (int)(enmf_launch_count() - l0);
+    note_launch(-kernels);   // captured, not launched
+    const int npev = ctx->npev - npev0;
+    ctx->npev = npev0;
+    cudaGraphExec_t exec = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      cudaGetLastError();
+      ctx->no_graph = true;
+      return false;
+    }
+    ctx->iter_graph = exec;
+    ctx->iter_key = key;
+    ctx->iter_graph_kernels = kernels;
+    ctx->iter_graph_npev = npev;
+  }
+  if (cudaGraphLaunch(ctx->iter_graph, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->no_graph = true;
+    return false;
+  }
+  note_launch(ctx->iter_graph_kernels);
+  ctx->npev += ctx->iter_graph_npev;
+  return true;
+}
+
 extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void* V,
                                     const enmf_iter_opts* opts, enmf_iter_info* info) {
   GUARD(ctx);
@@ -746,16 +827,23 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
     }
     launch_half_step(g, ctx->grid_v, s);
   }
-  for (int it = 0; it < o.n_iter; ++it) {
-    // precision form: refresh the X_lo terms every correct_every alternations
-    const int corr = (it % o.correct_every == 0) ? 2 : 1;
-    const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
-                     ctx->npev + 4 <= 2 * PROF_PAIRS;
-    sweep_xv(ctx, X, V, ctx->M0, corr, rec, false);
-    run_half(ctx, 0, U, ctx->M0, ctx->Gv, m, o, false, ctx->Gu, nullptr, nullptr, 0);
-    sweep_xtu(ctx, X, U, ctx->N0, corr, rec, false);
-    run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu, o.trace, it);
-  }
+  // the alternations: everything on the device, nothing read back
+  auto loop = [&]() {
+    for (int it = 0; it < o.n_iter; ++it) {
+      // precision form: refresh the X_lo terms every correct_every alternations
+      const int corr = (it % o.correct_every == 0) ? 2 : 1;
+      const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
+                       ctx->npev + 4 <= 2 * PROF_PAIRS;
+      sweep_xv(ctx, X, V, ctx->M0, corr, rec, false);
+      run_half(ctx, 0, U, ctx->M0, ctx->Gv, m, o, false, ctx->Gu, nullptr, nullptr, 0);
+      sweep_xtu(ctx, X, U, ctx->N0, corr, rec, false);
+      run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu, o.trace, it);
+    }
+  };
+  if (!replay_iteration(ctx, {X, U, V, o.trace, o.n_iter, o.pbcd_max_iter, o.n_shift,
+                              o.correct_every, ctx->prof_every, o.eps},
+                        loop))
+    loop();
   rc = check_launch(ctx);
   if (rc) return rc;
   if (ctx->npev > 0) {
