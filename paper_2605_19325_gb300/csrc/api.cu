@@ -107,6 +107,8 @@ static enmf_status prof_harvest(enmf_ctx* ctx) {
     if (cudaEventElapsedTime(&ms, ctx->pev[i], ctx->pev[i + 1]) == cudaSuccess) {
       ctx->prof_ms += ms;
       ctx->prof_n += 1;
+    } else {
+      cudaGetLastError();   // an unusable pair is skipped, not reported as a fault
     }
   }
   ctx->npev = 0;
@@ -662,7 +664,8 @@ static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const dou
 // Profiling: with `rec`, CUDA events bracket the main X pass alone (not the
 // factor split or the X_lo correction pass).
 static void prof_mark(enmf_ctx* ctx, bool rec) {
-  if (rec) cudaEventRecord(ctx->pev[ctx->npev++], ctx->stream);
+  // (external: inside a captured graph the record is a real event node)
+  if (rec) cudaEventRecordWithFlags(ctx->pev[ctx->npev++], ctx->stream, cudaEventRecordExternal);
 }
 
 // split = false: the BF16 pair of the factor is already current (written by
