@@ -46,6 +46,11 @@ struct enmf_ctx {
   // host-data staging for enmf_solve
   void* hX; void* hU; void* hV;
   size_t hX_bytes;
+  // tensor-core sweep descriptors (device, 8 slots) and their host copies:
+  // 0/1 X V main / X_lo pass and 2/3 X^T U main / X_lo pass of the iteration,
+  // 4..7 the same for enmf_sweep's caller buffers
+  SweepProb* dprob;
+  SweepProb hprob[8];
   // the iteration loop of enmf_iterate as a CUDA graph (captured on a private
   // stream, replayed while every argument of the call is unchanged)
   struct IterKey {
@@ -151,7 +156,7 @@ struct TcPlan {
   int rp;
   int64_t ldh, ldn, ldm;
   int sv, st;          // split arguments for X V and X^T U
-  size_t xh, vt, ut, part, cv, cu, total;
+  size_t xh, vt, ut, part, cv, cu, desc, total;
 };
 
 static TcPlan tc_plan(const enmf_problem* p, int num_sms) {
@@ -168,14 +173,16 @@ static TcPlan tc_plan(const enmf_problem* p, int num_sms) {
   t.xh = p->x_dtype == ENMF_F32 ? (size_t)m * t.ldh * 2 : 0;
   t.vt = (size_t)t.rp * t.ldn * 2;
   t.ut = (size_t)t.rp * t.ldm * 2;
-  // stream-K partial slots: grid x 2 x 128 rows x r, and one arrival counter
+  // stream-K partial slots: grid x 2 x 128 rows x rp, and one arrival counter
   // per output tile (kept in the same buffer, after the slots)
-  t.part = (size_t)(t.sv > t.st ? t.sv : t.st) * 2 * 128 * p->r * 4 +
+  t.part = (size_t)(t.sv > t.st ? t.sv : t.st) * 2 * 128 * t.rp * 4 +
            (size_t)(((m > n ? m : n) + 127) / 128 + 1) * 4;
   t.cv = (size_t)m * p->r * 4;
   t.cu = (size_t)n * p->r * 4;
+  t.desc = 8 * sizeof(SweepProb);
   auto a = [](size_t b) { return (b + 1023) & ~(size_t)1023; };
-  t.total = 2 * a(t.xh) + 2 * a(t.vt) + 2 * a(t.ut) + a(t.part) + a(t.cv) + a(t.cu) + 1024;
+  t.total = 2 * a(t.xh) + 2 * a(t.vt) + 2 * a(t.ut) + a(t.part) + a(t.cv) + a(t.cu) + a(t.desc) +
+            1024;
   return t;
 }
 
@@ -355,9 +362,10 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
     ctx->uth = grab(t.ut);
     ctx->utl = grab(t.ut);
     ctx->tcpart = (float*)grab(t.part);
-    ctx->tccount = (int*)(ctx->tcpart + (size_t)(t.sv > t.st ? t.sv : t.st) * 2 * 128 * p->r);
+    ctx->tccount = (int*)(ctx->tcpart + (size_t)(t.sv > t.st ? t.sv : t.st) * 2 * 128 * t.rp);
     ctx->cv = (float*)grab(t.cv);
     ctx->cu = (float*)grab(t.cu);
+    ctx->dprob = (SweepProb*)grab(t.desc);
     bool ok = tc_make_map(ctx->maps[MAP_VH], ctx->vth, t.rp, p->n, t.ldn, 64, t.rp) &&
               tc_make_map(ctx->maps[MAP_VL], ctx->vtl, t.rp, p->n, t.ldn, 64, t.rp) &&
               tc_make_map(ctx->maps[MAP_UH], ctx->uth, t.rp, p->m, t.ldm, 64, t.rp) &&
@@ -661,6 +669,39 @@ static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const dou
 // ------------------------------------------------------------ the sweeps
 // corr: 0 = X_hi only, 1 = add the stored X_lo term, 2 = refresh the X_lo
 // term with the current factor first (tensor-core form; ignored otherwise).
+// Descriptor slot `slot` of the one-problem tensor-core sweep (mode 0: X V,
+// mode 1: X^T U; lo: the X_lo pass), uploaded to the device only when it
+// changes -- so inside a captured iteration loop, where every slot was
+// refreshed before the capture, nothing is copied.
+static const SweepProb* tc_desc(enmf_ctx* ctx, int slot, int mode, bool lo, float* out,
+                                const float* corr) {
+  const enmf_problem& p = ctx->p;
+  SweepProb d;
+  memset(&d, 0, sizeof(d));
+  memcpy(d.mapX, ctx->maps[lo ? MAP_XL : MAP_XH], sizeof(d.mapX));
+  memcpy(d.mapBh, ctx->maps[mode == 0 ? MAP_VH : MAP_UH], sizeof(d.mapBh));
+  memcpy(d.mapBl, ctx->maps[mode == 0 ? MAP_VL : MAP_UL], sizeof(d.mapBl));
+  int64_t units, tiles;
+  tc_prob_sizes(mode, &d, mode == 0 ? p.m : p.n, mode == 0 ? p.n : p.m, p.r, 0, 0, &units, &tiles);
+  d.out = out;
+  d.corr = corr;
+  if (memcmp(&d, &ctx->hprob[slot], sizeof(d)) != 0) {
+    ctx->hprob[slot] = d;
+    cudaMemcpyAsync(ctx->dprob + slot, &ctx->hprob[slot], sizeof(d), cudaMemcpyHostToDevice,
+                    ctx->stream);
+  }
+  return ctx->dprob + slot;
+}
+
+// Work units (tiles x k-blocks) of the one-problem sweep in `mode`.
+static int64_t tc_units(enmf_ctx* ctx, int mode) {
+  SweepProb d;
+  int64_t units, tiles;
+  tc_prob_sizes(mode, &d, mode == 0 ? ctx->p.m : ctx->p.n, mode == 0 ? ctx->p.n : ctx->p.m,
+                ctx->p.r, 0, 0, &units, &tiles);
+  return units;
+}
+
 // Profiling: with `rec`, CUDA events bracket the main X pass alone (not the
 // factor split or the X_lo correction pass).
 static void prof_mark(enmf_ctx* ctx, bool rec) {
@@ -682,13 +723,17 @@ static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int
     return;
   }
   if (split) launch_split_transpose((const float*)V, p.n, r, ctx->vth, ctx->vtl, ctx->ldn, s);
-  if (corr == 2 && ctx->xl)
-    launch_tc_sweep(0, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_VH], ctx->maps[MAP_VL], p.m, p.n,
-                    r, ctx->cv, nullptr, ctx->tcpart, ctx->tccount, ctx->num_sms, ctx->err, s);
+  const int base = out == ctx->M0 ? 0 : 4;
+  if (corr == 2 && ctx->xl) {
+    const SweepProb* d = tc_desc(ctx, base + 1, 0, true, ctx->cv, nullptr);
+    launch_tc_group(0, ctx->rp, d, 1, tc_units(ctx, 0), ctx->tcpart, ctx->tccount, ctx->num_sms,
+                    ctx->err, s);
+  }
+  const SweepProb* d = tc_desc(ctx, base, 0, false, (float*)out,
+                               (corr >= 1 && ctx->xl) ? ctx->cv : nullptr);
   prof_mark(ctx, rec);
-  launch_tc_sweep(0, ctx->rp, ctx->maps[MAP_XH], ctx->maps[MAP_VH], ctx->maps[MAP_VL], p.m, p.n, r,
-                  (float*)out, (corr >= 1 && ctx->xl) ? ctx->cv : nullptr, ctx->tcpart,
-                  ctx->tccount, ctx->num_sms, ctx->err, s);
+  launch_tc_group(0, ctx->rp, d, 1, tc_units(ctx, 0), ctx->tcpart, ctx->tccount, ctx->num_sms,
+                  ctx->err, s);
   prof_mark(ctx, rec);
 }
 
@@ -704,13 +749,17 @@ static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, in
     return;
   }
   if (split) launch_split_transpose((const float*)U, p.m, r, ctx->uth, ctx->utl, ctx->ldm, s);
-  if (corr == 2 && ctx->xl)
-    launch_tc_sweep(1, ctx->rp, ctx->maps[MAP_XL], ctx->maps[MAP_UH], ctx->maps[MAP_UL], p.n, p.m,
-                    r, ctx->cu, nullptr, ctx->tcpart, ctx->tccount, ctx->num_sms, ctx->err, s);
+  const int base = out == ctx->N0 ? 2 : 6;
+  if (corr == 2 && ctx->xl) {
+    const SweepProb* d = tc_desc(ctx, base + 1, 1, true, ctx->cu, nullptr);
+    launch_tc_group(1, ctx->rp, d, 1, tc_units(ctx, 1), ctx->tcpart, ctx->tccount, ctx->num_sms,
+                    ctx->err, s);
+  }
+  const SweepProb* d = tc_desc(ctx, base, 1, false, (float*)out,
+                               (corr >= 1 && ctx->xl) ? ctx->cu : nullptr);
   prof_mark(ctx, rec);
-  launch_tc_sweep(1, ctx->rp, ctx->maps[MAP_XH], ctx->maps[MAP_UH], ctx->maps[MAP_UL], p.n, p.m, r,
-                  (float*)out, (corr >= 1 && ctx->xl) ? ctx->cu : nullptr, ctx->tcpart,
-                  ctx->tccount, ctx->num_sms, ctx->err, s);
+  launch_tc_group(1, ctx->rp, d, 1, tc_units(ctx, 1), ctx->tcpart, ctx->tccount, ctx->num_sms,
+                  ctx->err, s);
   prof_mark(ctx, rec);
 }
 
@@ -829,6 +878,13 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
       g.ldt = ctx->ldn;
     }
     launch_half_step(g, ctx->grid_v, s);
+  }
+  if (ctx->tc) {
+    // the iteration's sweep descriptors, current before any capture
+    tc_desc(ctx, 0, 0, false, (float*)ctx->M0, ctx->xl ? ctx->cv : nullptr);
+    tc_desc(ctx, 1, 0, true, ctx->cv, nullptr);
+    tc_desc(ctx, 2, 1, false, (float*)ctx->N0, ctx->xl ? ctx->cu : nullptr);
+    tc_desc(ctx, 3, 1, true, ctx->cu, nullptr);
   }
   // the alternations: everything on the device, nothing read back
   auto loop = [&]() {

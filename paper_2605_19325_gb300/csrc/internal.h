@@ -174,20 +174,40 @@ void launch_svd_finish(const double* sigma, const double* Ut, const double* Wt, 
 void launch_rr_prep(const double* sigma, const double* Ut, const double* Wt, int k1, int k2,
                     int r, double* Wr, double* UrS, DevState* st, cudaStream_t s);
 // ------------------------------------------------------------- tc_sweep.cu
+// One problem of a (grouped) tensor-core sweep, in device memory.  The sweep's
+// work is the concatenation over problems of each problem's (output tile,
+// k-block) units; w_begin / t_begin are this problem's first unit and first
+// tile in that order.  mode 0: out = X B (+ corr), rows_out = m, red = n;
+// mode 1: out = X^T B (+ corr), rows_out = n, red = m.  Maps: X (box 64 x 128),
+// B^T hi and lo (box 64 x rp).
+struct alignas(64) SweepProb {
+  unsigned char mapX[128];
+  unsigned char mapBh[128];
+  unsigned char mapBl[128];
+  int64_t rows_out, red;
+  int64_t w_begin, t_begin;
+  float* out;
+  const float* corr;
+  int r;
+  int pad_[3];
+};
+// Fills the sizes of d (maps and pointers set by the caller) and returns its
+// work units (tiles x k-blocks) and tiles through *units / *tiles.
+void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r, int64_t w_begin,
+                   int64_t t_begin, int64_t* units, int64_t* tiles);
+// Grouped sweep over np problems (descriptors in device memory, in work
+// order), W units in all; part needs grid x 2 x 128 x rp floats, counters one
+// int per tile of all problems (zero between launches).
+void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
+                     int* counters, int num_sms, int* err, cudaStream_t s);
+int tc_group_grid(int64_t W, int num_sms);
 // 2D BF16 tensor map (CUtensorMap, 128 bytes at `map`) over a row-major
 // (rows x cols, ld) array, box box_cols x box_rows, 128-byte swizzle.
 bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
                  int box_cols, int box_rows);
 int tc_rank_pad(int r);
-// CTAs of the persistent sweep (<= num_sms); part needs grid x 2 x 128 x r floats.
+// CTAs of a one-problem sweep (<= num_sms); part needs grid x 2 x 128 x rp floats.
 int tc_grid(int64_t rows_out, int64_t red, int mode, int num_sms);
-// mode 0: out = X B (+ corr) (rows_out m, red n); mode 1: out = X^T B (+ corr)
-// (rows_out n, red m).  Maps: X (box 64 x 128), B^T hi and lo (box 64 x rp).
-// counters: one int per output tile, zero between launches (the kernel resets
-// the ones it uses).
-void launch_tc_sweep(int mode, int rp, const void* mapX, const void* mapBh, const void* mapBl,
-                     int64_t rows_out, int64_t red, int r, float* out, const float* corr,
-                     float* part, int* counters, int num_sms, int* err, cudaStream_t s);
 void launch_split_transpose(const float* F, int64_t rows, int r, void* hi, void* lo, int64_t ldt,
                             cudaStream_t s);
 void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh, void* xl,

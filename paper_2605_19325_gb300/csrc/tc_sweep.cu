@@ -137,26 +137,50 @@ __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
-// Work split (stream-K): the (tile, k-block) space, tile-major, is cut into
+// Work split (stream-K): the work of all problems, each problem's (tile,
+// k-block) units tile-major and the problems one after another, is cut into
 // G contiguous ranges of equal length, one per CTA.  A CTA walks its range as
 // segments of consecutive k-blocks of one tile; a segment that covers a whole
 // tile writes the result directly, the (at most two) partial segments at the
 // ends of a range write FP32 partial slots; the last CTA to finish a cut tile
-// (a per-tile arrival counter) sums its slots in CTA order.
+// (a per-tile arrival counter) sums its slots in CTA order.  Problem
+// boundaries are tile boundaries, so this holds across problems.
 __host__ __device__ __forceinline__ int64_t sk_begin(int64_t c, int64_t W, int64_t G) {
   return (c * W) / G;
 }
 
+// The problem holding global unit w (descriptors in work order, np >= 1).
+__device__ __forceinline__ int prob_find(const SweepProb* probs, int np, int64_t w) {
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (probs[mid].w_begin <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// A CTA's view of the problem its current units belong to.
+template <int KB>
+struct ProbView {
+  const SweepProb* d;
+  int64_t wb, we, nkb;   // first unit, one past the last unit, k-blocks per tile
+  __device__ __forceinline__ void load(const SweepProb* probs, int np, int p, int64_t W) {
+    d = probs + p;
+    wb = d->w_begin;
+    we = p + 1 < np ? probs[p + 1].w_begin : W;
+    nkb = (d->red + KB - 1) / KB;
+  }
+};
+
 // MODE 0: C = X V (rows_out = m, reduction over n; A = X tile, K-major).
 // MODE 1: C = X^T U (rows_out = n, reduction over m; A = X tile, MN-major).
-// mapBh / mapBl: the factor transposed as a BF16 pair (RP x red).
-// out (rows_out x r, FP32) receives whole tiles (+ corr when given);
-// part [G][2][TILE][r] receives the partial segments.
+// Per problem (SweepProb): X map, the factor transposed as a BF16 pair
+// (mapBh / mapBl, RP x red), out (rows_out x r, FP32) receiving whole tiles
+// (+ corr when given).  part [G][2][TILE][RP] receives the partial segments.
 template <int MODE, int RP>
 __global__ void __launch_bounds__(THREADS, 1)
-sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapBh,
-                const __grid_constant__ CUtensorMap mapBl, int64_t rows_out, int64_t red, int r,
-                int stages, float* __restrict__ out, const float* __restrict__ corr,
+sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stages,
                 float* __restrict__ part, int* __restrict__ counters, int* err) {
   constexpr int KB = MODE == 0 ? KB_XV : KB_XT;
   constexpr uint32_t A_BYTES = TILE * KB * 2;                 // 16 KB or 32 KB
@@ -178,16 +202,16 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t tiles = (rows_out + TILE - 1) / TILE;
-  const int64_t nkb = (red + KB - 1) / KB;
-  const int64_t W = tiles * nkb;
   const int64_t G = gridDim.x;
   const int64_t w0 = sk_begin(blockIdx.x, W, G), w1 = sk_begin(blockIdx.x + 1, W, G);
+  const int p0 = w0 < w1 ? prob_find(probs, np, w0) : 0;
 
   if (threadIdx.x == 0) {
-    prefetch_map(&mapX);
-    prefetch_map(&mapBh);
-    prefetch_map(&mapBl);
+    if (w0 < w1) {
+      prefetch_map(reinterpret_cast<const CUtensorMap*>(probs[p0].mapX));
+      prefetch_map(reinterpret_cast<const CUtensorMap*>(probs[p0].mapBh));
+      prefetch_map(reinterpret_cast<const CUtensorMap*>(probs[p0].mapBl));
+    }
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
@@ -215,15 +239,28 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
   if (warp == 0) {
     if (lane == 0) {
       // ---------------------------------------------------------- producer
+      int p = p0;
+      ProbView<KB> pv;
+      pv.load(probs, np, p, W);
       int64_t i = 0;
       for (int64_t w = w0; w < w1 && !*(volatile int*)&aborted; ++w, ++i) {
+        if (w >= pv.we) {
+          pv.load(probs, np, ++p, W);
+          prefetch_map(reinterpret_cast<const CUtensorMap*>(pv.d->mapX));
+          prefetch_map(reinterpret_cast<const CUtensorMap*>(pv.d->mapBh));
+          prefetch_map(reinterpret_cast<const CUtensorMap*>(pv.d->mapBl));
+        }
+        const CUtensorMap* mapX = reinterpret_cast<const CUtensorMap*>(pv.d->mapX);
+        const CUtensorMap* mapBh = reinterpret_cast<const CUtensorMap*>(pv.d->mapBh);
+        const CUtensorMap* mapBl = reinterpret_cast<const CUtensorMap*>(pv.d->mapBl);
         const int s = (int)(i % stages);
         const uint32_t ph = (uint32_t)(i / stages) & 1u;
         if (!mbar_wait(&empty_bar[s], ph ^ 1u, err)) {
           aborted = 1;
           break;
         }
-        const int64_t tile = w / nkb, kb = w % nkb;
+        const int64_t lw = w - pv.wb;
+        const int64_t tile = lw / pv.nkb, kb = lw % pv.nkb;
         const int t0 = (int)(tile * TILE);
         const int k0 = (int)(kb * KB);
         uint8_t* sa = smem + (size_t)s * STAGE;
@@ -232,20 +269,16 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         mbar_expect_tx(&full_bar[s], STAGE);
         if (MODE == 0) {
           // two adjacent 64-column boxes: 256 contiguous bytes of each X row
-          tma_load(sa, &mapX, &full_bar[s], k0, t0);
-          tma_load(sa + A_BYTES / 2, &mapX, &full_bar[s], k0 + 64, t0);
-          tma_load(sbh, &mapBh, &full_bar[s], k0, 0);
-          tma_load(sbh + B_BYTES / 2, &mapBh, &full_bar[s], k0 + 64, 0);
-          tma_load(sbl, &mapBl, &full_bar[s], k0, 0);
-          tma_load(sbl + B_BYTES / 2, &mapBl, &full_bar[s], k0 + 64, 0);
+          tma_load(sa, mapX, &full_bar[s], k0, t0);
+          tma_load(sa + A_BYTES / 2, mapX, &full_bar[s], k0 + 64, t0);
         } else {
-          tma_load(sa, &mapX, &full_bar[s], t0, k0);
-          tma_load(sa + A_BYTES / 2, &mapX, &full_bar[s], t0 + 64, k0);
-          tma_load(sbh, &mapBh, &full_bar[s], k0, 0);
-          tma_load(sbh + B_BYTES / 2, &mapBh, &full_bar[s], k0 + 64, 0);
-          tma_load(sbl, &mapBl, &full_bar[s], k0, 0);
-          tma_load(sbl + B_BYTES / 2, &mapBl, &full_bar[s], k0 + 64, 0);
+          tma_load(sa, mapX, &full_bar[s], t0, k0);
+          tma_load(sa + A_BYTES / 2, mapX, &full_bar[s], t0 + 64, k0);
         }
+        tma_load(sbh, mapBh, &full_bar[s], k0, 0);
+        tma_load(sbh + B_BYTES / 2, mapBh, &full_bar[s], k0 + 64, 0);
+        tma_load(sbl, mapBl, &full_bar[s], k0, 0);
+        tma_load(sbl + B_BYTES / 2, mapBl, &full_bar[s], k0 + 64, 0);
       }
       if (aborted) {
         // let copies already issued land before the CTA can exit
@@ -257,11 +290,15 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
   } else if (warp == 1) {
     if (lane == 0) {
       // --------------------------------------------------------- MMA issue
+      int p = p0;
+      ProbView<KB> pv;
+      pv.load(probs, np, p, W);
       int64_t i = 0;
       int64_t seg = 0;
       for (int64_t w = w0; w < w1 && !*(volatile int*)&aborted; ++seg) {
-        const int64_t tile = w / nkb;
-        const int64_t wend = min(w1, (tile + 1) * nkb);
+        if (w >= pv.we) pv.load(probs, np, ++p, W);
+        const int64_t tile = (w - pv.wb) / pv.nkb;
+        const int64_t wend = min(w1, pv.wb + (tile + 1) * pv.nkb);
         const int b = (int)(seg & 1);
         const uint32_t up = (uint32_t)(seg >> 1) & 1u;
         if (!mbar_wait(&acce_bar[b], up ^ 1u, err)) {
@@ -324,14 +361,26 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
     const int quarter = warp & 3;
     const int lrow = quarter * 32 + lane;
     const int et = threadIdx.x - 64;                 // 0..127
-    const int q128 = 128 / r, r128 = 128 % r;        // a flat step of 128 as (rows, cols)
-    const int rr0 = et / r, cc0 = et % r;
+    int p = p0;
+    ProbView<KB> pv;
+    pv.load(probs, np, p, W);
     int64_t seg = 0;
     for (int64_t w = w0; w < w1; ++seg) {
-      const int64_t tile = w / nkb;
-      const int64_t kb_a = w % nkb;
-      const int64_t wend = min(w1, (tile + 1) * nkb);
-      const int64_t kb_b = wend - tile * nkb;
+      if (w >= pv.we) pv.load(probs, np, ++p, W);
+      const int r = pv.d->r;
+      const int64_t rows_out = pv.d->rows_out;
+      float* const out = pv.d->out;
+      const float* const corr = pv.d->corr;
+      const int q128 = 128 / r, r128 = 128 % r;      // a flat step of 128 as (rows, cols)
+      const int rr0 = et / r, cc0 = et % r;
+      const int64_t lw = w - pv.wb;
+      const int64_t tile = lw / pv.nkb;
+      const int64_t kb_a = lw % pv.nkb;
+      const int64_t wend = min(w1, pv.wb + (tile + 1) * pv.nkb);
+      const int64_t kb_b = wend - pv.wb - tile * pv.nkb;
+      const int64_t nkb = pv.nkb;
+      // the tile's first and one-past-last global units
+      const int64_t gs = pv.wb + tile * nkb, ge = gs + nkb;
       w = wend;
       const int b = (int)(seg & 1);
       const uint32_t up = (uint32_t)(seg >> 1) & 1u;
@@ -361,7 +410,7 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         if (corr) add = corr + row0 * r;
       } else {
         const int slot = seg == 0 ? 0 : 1;
-        dst = part + ((int64_t)blockIdx.x * 2 + slot) * TILE * r;
+        dst = part + ((int64_t)blockIdx.x * 2 + slot) * TILE * RP;
       }
       if (ok) {
         int rr = rr0, cc = cc0;
@@ -384,12 +433,13 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         __threadfence();
         asm volatile("bar.sync 1, 128;" ::: "memory");
         int64_t c_lo = blockIdx.x, c_hi = blockIdx.x;
-        while (c_lo > 0 && sk_begin(c_lo, W, G) > tile * nkb) --c_lo;
-        while (c_hi + 1 < G && sk_begin(c_hi + 1, W, G) < (tile + 1) * nkb) ++c_hi;
+        while (c_lo > 0 && sk_begin(c_lo, W, G) > gs) --c_lo;
+        while (c_hi + 1 < G && sk_begin(c_hi + 1, W, G) < ge) ++c_hi;
+        int* const cnt_t = &counters[pv.d->t_begin + tile];
         if (et == 0) {
-          const int old = atomicAdd(&counters[tile], 1);
+          const int old = atomicAdd(cnt_t, 1);
           last_cta = old == (int)(c_hi - c_lo);
-          if (last_cta) counters[tile] = 0;   // ready for the next launch
+          if (last_cta) *cnt_t = 0;   // ready for the next launch
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (last_cta && ok) {
@@ -403,8 +453,8 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
           const bool vec = ((reinterpret_cast<uintptr_t>(o) | reinterpret_cast<uintptr_t>(cr)) & 15) == 0;
           const int n4 = vec ? cnt / 4 : 0;
           auto slot_of = [&](int64_t q) {
-            const int slot = sk_begin(q, W, G) >= tile * nkb ? 0 : 1;
-            return reinterpret_cast<const float4*>(part + (q * 2 + slot) * TILE * r);
+            const int slot = sk_begin(q, W, G) >= gs ? 0 : 1;
+            return reinterpret_cast<const float4*>(part + (q * 2 + slot) * TILE * RP);
           };
           constexpr int CH = RP / 4 < 8 ? RP / 4 : 8;   // float4s per thread per chunk
           for (int g0 = 0; g0 * 128 < n4; g0 += CH) {
@@ -456,8 +506,8 @@ sweep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
           for (int f = 4 * n4 + et; f < cnt; f += 128) {
             float sacc = 0.f;
             for (int64_t q = c_lo; q <= c_hi; ++q) {
-              const int slot = sk_begin(q, W, G) >= tile * nkb ? 0 : 1;
-              sacc += __ldcg(&part[(q * 2 + slot) * TILE * r + f]);
+              const int slot = sk_begin(q, W, G) >= gs ? 0 : 1;
+              sacc += __ldcg(&part[(q * 2 + slot) * TILE * RP + f]);
             }
             o[f] = cr ? sacc + cr[f] : sacc;
           }
@@ -585,34 +635,46 @@ static int tc_stages(int mode, int rp) {
 
 // Grid of the persistent sweep: one CTA per SM, fewer when there are fewer
 // k-blocks than SMs.
+int tc_group_grid(int64_t W, int num_sms) {
+  int64_t g = W < num_sms ? W : num_sms;
+  if (g > tc::MAX_GRID) g = tc::MAX_GRID;
+  return (int)(g < 1 ? 1 : g);
+}
+
 int tc_grid(int64_t rows_out, int64_t red, int mode, int num_sms) {
   const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
-  const int64_t W = ((rows_out + tc::TILE - 1) / tc::TILE) * ((red + kb - 1) / kb);
-  int64_t g = W < num_sms ? W : num_sms;
-  return (int)(g > tc::MAX_GRID ? tc::MAX_GRID : g);
+  return tc_group_grid(((rows_out + tc::TILE - 1) / tc::TILE) * ((red + kb - 1) / kb), num_sms);
+}
+
+void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r, int64_t w_begin,
+                   int64_t t_begin, int64_t* units, int64_t* tiles) {
+  const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
+  d->rows_out = rows_out;
+  d->red = red;
+  d->r = r;
+  d->w_begin = w_begin;
+  d->t_begin = t_begin;
+  *tiles = (rows_out + tc::TILE - 1) / tc::TILE;
+  *units = *tiles * ((red + kb - 1) / kb);
 }
 
 template <int MODE, int RP>
-static void launch_tc(const void* mapX, const void* mapBh, const void* mapBl, int64_t rows_out,
-                      int64_t red, int r, float* out, const float* corr, float* part,
-                      int* counters, int grid, int* err, cudaStream_t s) {
+static void launch_tc(const SweepProb* probs, int np, int64_t W, float* part, int* counters,
+                      int grid, int* err, cudaStream_t s) {
   const int stages = tc_stages(MODE, RP);
   const size_t smem = tc_smem(MODE, RP, stages);
   cudaFuncSetAttribute(tc::sweep_tc_kernel<MODE, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
-  tc::sweep_tc_kernel<MODE, RP><<<grid, tc::THREADS, smem, s>>>(
-      *reinterpret_cast<const CUtensorMap*>(mapX), *reinterpret_cast<const CUtensorMap*>(mapBh),
-      *reinterpret_cast<const CUtensorMap*>(mapBl), rows_out, red, r, stages, out, corr, part,
-      counters, err);
+  tc::sweep_tc_kernel<MODE, RP><<<grid, tc::THREADS, smem, s>>>(probs, np, W, stages, part,
+                                                                 counters, err);
 }
 
-void launch_tc_sweep(int mode, int rp, const void* mapX, const void* mapBh, const void* mapBl,
-                     int64_t rows_out, int64_t red, int r, float* out, const float* corr,
-                     float* part, int* counters, int num_sms, int* err, cudaStream_t s) {
-  const int grid = tc_grid(rows_out, red, mode, num_sms);
+void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
+                     int* counters, int num_sms, int* err, cudaStream_t s) {
+  if (np < 1 || W < 1) return;
+  const int grid = tc_group_grid(W, num_sms);
   note_launch(1);
-#define TCL(M, P) \
-  launch_tc<M, P>(mapX, mapBh, mapBl, rows_out, red, r, out, corr, part, counters, grid, err, s)
+#define TCL(M, P) launch_tc<M, P>(probs, np, W, part, counters, grid, err, s)
   if (mode == 0) {
     if (rp == 16) TCL(0, 16); else if (rp == 32) TCL(0, 32); else if (rp == 48) TCL(0, 48); else TCL(0, 64);
   } else {
