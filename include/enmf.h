@@ -230,6 +230,51 @@ enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V, int32_t n
                        const enmf_svd_opts* svd, const enmf_admm_opts* admm,
                        const enmf_iter_opts* iter, double* out3);
 
+/* ---- Batching (no counterpart in the paper) --------------------------------
+ * A batch iterates many independent problems together.  Each phase of every
+ * alternation is one grouped launch over all members: X V sweep, U-half,
+ * X^T U sweep, V-half (plus the X_lo passes every correct_every
+ * alternations).  The sweeps run stream-K over the members' concatenated
+ * tensor-core work.  The half steps run each member on its own group of blocks
+ * of one cooperative grid.  A step of n_alt alternations is captured as a CUDA
+ * graph and replayed while the membership is unchanged.
+ *
+ * Members are contexts of the tensor-core form (stream_dtype ENMF_BF16, FP32
+ * factors) with X staged, whose U and V (device, caller-owned) are the
+ * starting point -- normally the output of enmf_svd_init and enmf_rotate.
+ * All members of a batch share the padded rank (r rounded up to 16, 32, 48
+ * or 64); a member of another padded rank is rejected with ENMF_EINVAL.
+ * The iteration options (pbcd_max_iter, eps, n_shift, correct_every; the
+ * trace, reset and sync_info fields are ignored) are fixed at creation.
+ *
+ * enmf_batch_add starts the member's iteration (state reset, as enmf_iterate
+ * with reset = 1) on the member's stream; the batch stream waits for it.
+ * ENMF_EBUSY: no free slot, or the grouped half step would exceed the
+ * co-resident capacity.  enmf_batch_remove makes the member's stream wait
+ * for the batch's work; U and V then hold the member's iterate.  Neither
+ * call synchronises.  A removed context may be destroyed or added again.
+ * enmf_batch_step enqueues n_alt alternations of every member on the batch
+ * stream; n_alt must be a multiple of correct_every (ENMF_EINVAL otherwise),
+ * so every member joins at the start of a correction period and refreshes
+ * its X_lo terms at the same alternations as it would alone.  enmf_batch_member synchronises the batch stream and reports a
+ * member's alternation count, stage and objective f (Eq. 1) after its last
+ * alternation.  enmf_batch_tune times the grouped sweeps of the current
+ * membership at several stream-K grid sizes and keeps the fastest (*grid,
+ * and the time of one X V + X^T U pair in ms); it synchronises.  A context
+ * may be in one batch at a time, and must not be used by other calls while
+ * it is a member. */
+typedef struct enmf_batch enmf_batch;
+enmf_status enmf_batch_create(const enmf_iter_opts* opts /* NULL = defaults */,
+                              int32_t max_members, void* stream, enmf_batch** out);
+void enmf_batch_destroy(enmf_batch* b);
+enmf_status enmf_batch_add(enmf_batch* b, enmf_ctx* ctx, const void* X, void* U, void* V,
+                           int32_t* slot);
+enmf_status enmf_batch_remove(enmf_batch* b, int32_t slot);
+int32_t enmf_batch_size(const enmf_batch* b);
+enmf_status enmf_batch_step(enmf_batch* b, int32_t n_alt);
+enmf_status enmf_batch_member(enmf_batch* b, int32_t slot, enmf_iter_info* info, double* f);
+enmf_status enmf_batch_tune(enmf_batch* b, int32_t* grid, float* ms);
+
 /* ---- Measurement (no counterpart in the paper) ---------------------------
  * enmf_profile: every > 0 records CUDA events around the X V and X^T U sweep
  * kernels (the main pass over X alone: not the factor split or the X_lo

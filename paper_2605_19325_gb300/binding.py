@@ -95,6 +95,15 @@ _SIGS = {
                                     C.c_int32]),
     "enmf_probe_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
     "enmf_launch_count": (C.c_longlong, []),
+    "enmf_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "enmf_batch_destroy": (None, [C.c_void_p]),
+    "enmf_batch_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.POINTER(C.c_int32)]),
+    "enmf_batch_remove": (C.c_int, [C.c_void_p, C.c_int32]),
+    "enmf_batch_size": (C.c_int32, [C.c_void_p]),
+    "enmf_batch_step": (C.c_int, [C.c_void_p, C.c_int32]),
+    "enmf_batch_member": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_double)]),
+    "enmf_batch_tune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     "enmf_residual_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                                         C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                         C.c_void_p]),
@@ -234,6 +243,51 @@ def enmf_probe_fma_peak(dtype):
 
 def enmf_launch_count():
     return int(lib().enmf_launch_count())
+
+
+def enmf_batch_create(max_members, stream=None, pbcd_max_iter=5, eps=1e-4, n_shift=3,
+                      correct_every=10):
+    o = enmf_iter_opts(0, pbcd_max_iter, eps, n_shift, None, 0, 0, correct_every)
+    h = C.c_void_p()
+    check(lib().enmf_batch_create(C.byref(o), max_members, _stream(stream), C.byref(h)),
+          "enmf_batch_create")
+    return h
+
+
+def enmf_batch_destroy(b):
+    lib().enmf_batch_destroy(b)
+
+
+def enmf_batch_add(b, ctx, X, U, V):
+    slot = C.c_int32(-1)
+    check(lib().enmf_batch_add(b, ctx, _ptr(X), _ptr(U), _ptr(V), C.byref(slot)), "enmf_batch_add")
+    return slot.value
+
+
+def enmf_batch_remove(b, slot):
+    check(lib().enmf_batch_remove(b, slot), "enmf_batch_remove")
+
+
+def enmf_batch_size(b):
+    return int(lib().enmf_batch_size(b))
+
+
+def enmf_batch_step(b, n_alt):
+    check(lib().enmf_batch_step(b, n_alt), "enmf_batch_step")
+
+
+def enmf_batch_member(b, slot):
+    info = enmf_iter_info()
+    f = C.c_double(0)
+    check(lib().enmf_batch_member(b, slot, C.byref(info), C.byref(f)), "enmf_batch_member")
+    return info, f.value
+
+
+def enmf_batch_tune(b):
+    g = C.c_int32(0)
+    ms = C.c_float(0)
+    check(lib().enmf_batch_tune(b, C.byref(g), C.byref(ms)), "enmf_batch_tune")
+    return g.value, ms.value
 
 
 def enmf_solve(ctx, X_ptr, U_ptr, V_ptr, n_iter):

@@ -8,98 +8,8 @@
 
 #include <new>
 
-#include "internal.h"
+#include "ctx.h"
 
-using namespace enmf;
-
-struct enmf_ctx {
-  enmf_problem p;
-  cudaStream_t stream;
-  int device;
-  int num_sms;
-  int fdt;                  // factor/accumulate type code
-  int xdt;                  // X type code
-  enmf_status poison;       // ENMF_OK unless poisoned
-  bool state_valid;         // iteration state initialised
-  int grid_u, grid_v;       // cooperative half-step grids
-  // workspace
-  void* ws;
-  size_t ws_bytes;
-  DevState* st;
-  int* err;
-  int* kept;
-  int* counts;
-  int counts_cap;
-  void* M0; void* M1; void* M2;  // m x LMAX
-  void* N0; void* N1; void* N2;  // n x LMAX
-  void* Zb; void* Yb;            // (m + n) x r
-  unsigned long long* mask;      // max(m, n)
-  void* splitk;
-  size_t splitk_bytes;
-  double* part;                  // NPART * (LMAX^2 + 8)
-  double* dot_part;              // 4096
-  double* pb_part;               // 2 * 4096
-  double* Gu; double* Gv; double* Msm; double* R;
-  double* T1; double* T2; double* Ut; double* Wt; double* sig;
-  double* Tu; double* Tv; double* Wr; double* UrS; double* csQ; double* csQ2;
-  double* scal;                  // 64 scratch scalars
-  // host-data staging for enmf_solve
-  void* hX; void* hU; void* hV;
-  size_t hX_bytes;
-  // tensor-core sweep descriptors (device, 8 slots) and their host copies:
-  // 0/1 X V main / X_lo pass and 2/3 X^T U main / X_lo pass of the iteration,
-  // 4..7 the same for enmf_sweep's caller buffers
-  SweepProb* dprob;
-  SweepProb hprob[8];
-  // the iteration loop of enmf_iterate as a CUDA graph (captured on a private
-  // stream, replayed while every argument of the call is unchanged)
-  struct IterKey {
-    const void* X;
-    void* U;
-    void* V;
-    double* trace;
-    int n_iter, pbcd_max_iter, n_shift, correct_every, prof_every;
-    double eps;
-    bool operator==(const IterKey& o) const {
-      return X == o.X && U == o.U && V == o.V && trace == o.trace && n_iter == o.n_iter &&
-             pbcd_max_iter == o.pbcd_max_iter && n_shift == o.n_shift &&
-             correct_every == o.correct_every && prof_every == o.prof_every && eps == o.eps;
-    }
-  };
-  cudaStream_t cap_stream;
-  cudaGraphExec_t iter_graph;
-  IterKey iter_key;
-  int iter_graph_kernels;   // kernel launches per replay
-  int iter_graph_npev;      // profiling events recorded per replay
-  bool no_graph;            // capture failed once: launch eagerly
-  // event timing of the X sweeps (enmf_profile)
-  int prof_every;
-  int npev;
-  cudaEvent_t pev[2 * 256];
-  double prof_ms;
-  long long prof_n;
-  // precision form (tensor-core sweeps on BF16 X)
-  int tc;
-  int rp;
-  int64_t ldh, ldn, ldm;
-  int sv, st_split;
-  void* tcws;
-  size_t tcws_bytes;
-  const void* xh;                // X_hi (context-owned, or the caller's BF16 X)
-  void* xl;                      // X_lo (context-owned; null for BF16 input)
-  void* own_xh;
-  void* vth; void* vtl;          // V^T as a BF16 pair (rp x ldn)
-  void* uth; void* utl;          // U^T as a BF16 pair (rp x ldm)
-  float* tcpart;                 // stream-K partial slots
-  int* tccount;                  // per-tile arrival counters (after the slots)
-  float* cv; float* cu;          // X_lo V, X_lo^T U (correction)
-  const void* staged_src;        // X pointer the staged copy belongs to
-  alignas(64) unsigned char maps[6][128];   // X_hi, X_lo, Vt hi/lo, Ut hi/lo
-};
-
-enum { MAP_XH = 0, MAP_XL = 1, MAP_VH = 2, MAP_VL = 3, MAP_UH = 4, MAP_UL = 5 };
-
-constexpr int PROF_PAIRS = 256;
 
 // Accumulate the recorded (start, stop) event pairs into the sweep totals.
 static enmf_status prof_harvest(enmf_ctx* ctx) {
@@ -628,9 +538,9 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
 // ------------------------------------------------------------ 3. iterate
 // One half of an alternation: the row updates of F (U or V), the Gram of the
 // new F into G_out and, for the V-half, the end-of-alternation bookkeeping.
-static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const double* G, int64_t rows,
-                     const enmf_iter_opts& o, bool dot, double* G_out, const double* Gu,
-                     double* trace, int trace_idx) {
+HalfArgs ctx_half_args(enmf_ctx* ctx, int which, void* F, const void* A, const double* G,
+                       int64_t rows, const enmf_iter_opts& o, bool dot, double* G_out,
+                       const double* Gu, double* trace, int trace_idx) {
   HalfArgs a;
   memset(&a, 0, sizeof(a));
   a.F = F;
@@ -658,11 +568,19 @@ static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const dou
   a.obj_part = ctx->dot_part + 2048;
   a.trace = trace;
   a.trace_idx = trace_idx;
+  a.bar = &ctx->st->bar;
   if (ctx->tc) {
     a.th = which == 0 ? ctx->uth : ctx->vth;
     a.tl = which == 0 ? ctx->utl : ctx->vtl;
     a.ldt = which == 0 ? ctx->ldm : ctx->ldn;
   }
+  return a;
+}
+
+static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const double* G, int64_t rows,
+                     const enmf_iter_opts& o, bool dot, double* G_out, const double* Gu,
+                     double* trace, int trace_idx) {
+  const HalfArgs a = ctx_half_args(ctx, which, F, A, G, rows, o, dot, G_out, Gu, trace, trace_idx);
   launch_half_step(a, which == 0 ? ctx->grid_u : ctx->grid_v, ctx->stream);
 }
 
@@ -837,6 +755,43 @@ static bool replay_iteration(enmf_ctx* ctx, const enmf_ctx::IterKey& key, Loop&&
   return true;
 }
 
+void ctx_iter_prologue(enmf_ctx* ctx, const void* X, void* U, void* V, int n_shift, bool reset) {
+  const enmf_problem& p = ctx->p;
+  const int k = p.r, fdt = ctx->fdt;
+  const int64_t m = p.m, n = p.n;
+  cudaStream_t s = ctx->stream;
+  if (reset || !ctx->state_valid) {
+    launch_state_init(U, V, m, n, k, fdt, n_shift, ctx->st, ctx->part, s);
+    ctx->state_valid = true;
+  }
+  launch_normx2(X, ctx->xdt, m, n, p.ldx, ctx->part, &ctx->st->normX2, ctx->err, s);
+  // V^T V with the V-half kernel's own decomposition (bitwise equal to the
+  // Gram the previous call ended with, so calls can be split freely)
+  HalfArgs g;
+  memset(&g, 0, sizeof(g));
+  g.F = V;
+  g.rows = n;
+  g.k = k;
+  g.fdt = fdt;
+  g.which = 1;
+  g.st = ctx->st;
+  g.err = ctx->err;
+  g.G = ctx->Gu;   // unused (read into shared memory only)
+  g.G_out = ctx->Gv;
+  g.gpart = ctx->part;
+  g.gram_only = 1;
+  g.bar = &ctx->st->bar;
+  if (ctx->tc) {   // and the BF16 pair of V for the first sweep
+    g.th = ctx->vth;
+    g.tl = ctx->vtl;
+    g.ldt = ctx->ldn;
+  }
+  launch_half_step(g, ctx->grid_v, s);
+}
+
+enmf_status ctx_check_launch(enmf_ctx* ctx) { return check_launch(ctx); }
+enmf_status ctx_sync_status(enmf_ctx* ctx) { return sync_status(ctx); }
+
 extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void* V,
                                     const enmf_iter_opts* opts, enmf_iter_info* info) {
   GUARD(ctx);
@@ -851,34 +806,7 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
   cudaStream_t s = ctx->stream;
   enmf_status rc = check_staged(ctx, X);
   if (rc) return rc;
-  if (o.reset || !ctx->state_valid) {
-    launch_state_init(U, V, m, n, k, fdt, o.n_shift, ctx->st, ctx->part, s);
-    ctx->state_valid = true;
-  }
-  launch_normx2(X, xdt, m, n, p.ldx, ctx->part, &ctx->st->normX2, ctx->err, s);
-  {
-    // V^T V with the V-half kernel's own decomposition (bitwise equal to the
-    // Gram the previous call ended with, so calls can be split freely)
-    HalfArgs g;
-    memset(&g, 0, sizeof(g));
-    g.F = V;
-    g.rows = n;
-    g.k = k;
-    g.fdt = fdt;
-    g.which = 1;
-    g.st = ctx->st;
-    g.err = ctx->err;
-    g.G = ctx->Gu;   // unused (read into shared memory only)
-    g.G_out = ctx->Gv;
-    g.gpart = ctx->part;
-    g.gram_only = 1;
-    if (ctx->tc) {   // and the BF16 pair of V for the first sweep
-      g.th = ctx->vth;
-      g.tl = ctx->vtl;
-      g.ldt = ctx->ldn;
-    }
-    launch_half_step(g, ctx->grid_v, s);
-  }
+  ctx_iter_prologue(ctx, X, U, V, o.n_shift, o.reset != 0);
   if (ctx->tc) {
     // the iteration's sweep descriptors, current before any capture
     tc_desc(ctx, 0, 0, false, (float*)ctx->M0, ctx->xl ? ctx->cv : nullptr);

@@ -83,14 +83,18 @@ __device__ __forceinline__ void write_split(const HalfArgs& a, int64_t i, bool l
   }
 }
 
+// The half step of one problem on its group of nb blocks (this block is lb
+// of them).  lock < 0: the problem has the grid to itself, so the PBCD loop
+// may stop as soon as its test is met.  lock >= 0: several problems share
+// the grid and every block must pass the same grid barriers: lock = 1 when
+// some problem of the grid is in the ascent stage -- then every block runs
+// all pbcd_max_iter barriered PBCD iterations (idle once its own problem has
+// stopped, or when it is not ascending).
 template <typename TF, int KP>
-__global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
+__device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, const int nb,
+                                           const int lock, TF* Gs, TF* us, TF* ginv,
+                                           double* sh) {
   constexpr int E = KP / LPR, S = KP / 16;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  TF* Gs = reinterpret_cast<TF*>(smraw);   // KP x KP, zero padded
-  TF* us = Gs + KP * KP;                   // RPB x KP rows of the current pass
-  __shared__ double sh[HT];
-  __shared__ TF ginv[KP];                  // 1 / G_jj (0 where G_jj <= 0)
 
   const int k = a.k;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -118,7 +122,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
   TF* F = (TF*)a.F;
   const TF* A = (const TF*)a.A;
   const int64_t rows = a.rows;
-  const int64_t passes = (rows + (int64_t)gridDim.x * RPB - 1) / ((int64_t)gridDim.x * RPB);
+  const int64_t passes = (rows + (int64_t)nb * RPB - 1) / ((int64_t)nb * RPB);
   TF gacc[S][S];
 #pragma unroll
   for (int s1 = 0; s1 < S; ++s1)
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
 
   if (a.gram_only) {
     for (int64_t ps = 0; ps < passes; ++ps) {
-      const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+      const int64_t i = (ps * nb + lb) * RPB + rloc;
       TF u[E];
       load_row(F, i, i < rows, k, sub, u);
       write_split(a, i, i < rows, k, sub, u);
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
   } else if (stage == 1) {
     // ---- HALS sweep over the columns, q = a - u G kept current
     for (int64_t ps = 0; ps < passes; ++ps) {
-      const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+      const int64_t i = (ps * nb + lb) * RPB + rloc;
       const bool live = i < rows;
       TF u[E], av[E], q[E];
       load_row(F, i, live, k, sub, u);
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
     unsigned char* mk = reinterpret_cast<unsigned char*>(a.mask);
     double acc = 0.0;
     for (int64_t ps = 0; ps < passes; ++ps) {
-      const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+      const int64_t i = (ps * nb + lb) * RPB + rloc;
       const bool live = i < rows;
       TF u[E], av[E], g[E];
       load_row(F, i, live, k, sub, u);
@@ -209,14 +213,15 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
       if (live) mk[i * 8 + sub] = (unsigned char)bits;
     }
     double bsum = block_sum256(acc, sh);
-    if (t == 0) a.part[blockIdx.x] = bsum;
-    grid_sync(&st->bar, a.err);
-    const double g0 = sqrt(sum_partials(a.part, gridDim.x, sh));
+    if (t == 0) a.part[lb] = bsum;
+    grid_sync(a.bar, a.err);
+    const double g0 = sqrt(sum_partials(a.part, nb, sh));
     int iters = 0;
+    bool stopped = false;
     for (int it = 0; it < a.pbcd_max_iter; ++it) {
       acc = 0.0;
-      for (int64_t ps = 0; ps < passes; ++ps) {
-        const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+      for (int64_t ps = 0; ps < (stopped ? 0 : passes); ++ps) {
+        const int64_t i = (ps * nb + lb) * RPB + rloc;
         const bool live = i < rows;
         TF u[E], av[E], g[E], tg[E];
         load_row(F, i, live, k, sub, u);
@@ -249,18 +254,21 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
         store_row(F, i, live, k, sub, u);
         store_row(gb, i, live, k, sub, g);
       }
-      double* pbuf = a.part + (size_t)((it + 1) & 1) * gridDim.x;
+      double* pbuf = a.part + (size_t)((it + 1) & 1) * nb;
       bsum = block_sum256(acc, sh);
-      if (t == 0) pbuf[blockIdx.x] = bsum;
-      grid_sync(&st->bar, a.err);
-      const double bc = sum_partials(pbuf, gridDim.x, sh);
-      iters = it + 1;
-      if (sqrt(bc) < a.eps * g0 || bc == 0.0) break;
+      if (t == 0) pbuf[lb] = bsum;
+      grid_sync(a.bar, a.err);
+      const double bc = sum_partials(pbuf, nb, sh);
+      if (!stopped) {
+        iters = it + 1;
+        stopped = sqrt(bc) < a.eps * g0 || bc == 0.0;
+      }
+      if (stopped && lock < 0) break;
     }
     // entries still negative (unmasked) keep the ascent stage going
     int neg = 0;
     for (int64_t ps = 0; ps < passes; ++ps) {
-      const int64_t i = (ps * gridDim.x + blockIdx.x) * RPB + rloc;
+      const int64_t i = (ps * nb + lb) * RPB + rloc;
       const bool live = i < rows;
       TF u[E];
       load_row(F, i, live, k, sub, u);
@@ -280,12 +288,17 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
       gram_pass<TF, KP>(us, u, rloc, sub, gacc);
     }
     if (neg) atomicOr(a.which == 0 ? &st->negU : &st->negV, 1);
-    if (blockIdx.x == 0 && t == 0) {
+    if (lb == 0 && t == 0) {
       const int q = st->asc_iters;
       if (a.counts && 2 * q + a.which < a.counts_cap) a.counts[2 * q + a.which] = iters;
     }
   }
 
+  if (lock > 0 && (a.gram_only || stage == 1)) {
+    // keep pace with the ascending problems of the grid: the barriers of the
+    // first PBCD pass and of every PBCD iteration
+    for (int it = 0; it <= a.pbcd_max_iter; ++it) grid_sync(a.bar, a.err);
+  }
   // ---- block partials: Gram (FP64), <A, F> and <U^T U, Gram partial>
   const int kk = k * k;
   {
@@ -298,32 +311,32 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
         const int p = bi * S + s1, c = bj * S + s2;
         if (p < k && c < k) {
           const double gv = (double)gacc[s1][s2];
-          a.gpart[(int64_t)blockIdx.x * kk + p * k + c] = gv;
+          a.gpart[(int64_t)lb * kk + p * k + c] = gv;
           if (a.finalize) obj = fma(guv[s1][s2], gv, obj);
         }
       }
     if (a.finalize) {
       obj = block_sum256(obj, sh);
-      if (t == 0) a.obj_part[blockIdx.x] = obj;
+      if (t == 0) a.obj_part[lb] = obj;
     }
   }
   if (a.dot_part) {
     const double dsum = block_sum256(dotacc, sh);
-    if (t == 0) a.dot_part[blockIdx.x] = dsum;
+    if (t == 0) a.dot_part[lb] = dsum;
   }
-  grid_sync(&st->bar, a.err);
+  grid_sync(a.bar, a.err);
 
   // ---- G_out = sum of the block partials in block order (block 0 left free
   // for the end-of-alternation work when there are other blocks)
-  sum_block_partials<HT>(a.gpart, (int)gridDim.x, kk, a.G_out,
-                         (a.finalize && gridDim.x > 1) ? 1 : 0);
-  if (!a.finalize || blockIdx.x != 0) return;
+  sum_block_partials<HT>(a.gpart, nb, kk, a.G_out, (a.finalize && nb > 1) ? 1 : 0, lb, nb);
+  if (!a.finalize || lb != 0) return;
 
   // ---- end of the alternation (block 0): objective and stage update
-  const double gg = sum_partials(a.obj_part, gridDim.x, sh);
-  const double d = sum_partials(a.dot_part, gridDim.x, sh);
+  const double gg = sum_partials(a.obj_part, nb, sh);
+  const double d = sum_partials(a.dot_part, nb, sh);
   if (t == 0) {
     const double f = 0.5 * st->normX2 - d + 0.5 * gg;
+    st->f_last = f;
     if (a.trace) a.trace[a.trace_idx] = f;
     if (st->stage == 0) st->asc_iters += 1;
     else st->hals_iters += 1;
@@ -332,6 +345,48 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
     st->negU = 0;
     st->negV = 0;
   }
+}
+
+template <typename TF, int KP>
+__global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TF* Gs = reinterpret_cast<TF*>(smraw);   // KP x KP, zero padded
+  TF* us = Gs + KP * KP;                   // RPB x KP rows of the current pass
+  __shared__ double sh[HT];
+  __shared__ TF ginv[KP];                  // 1 / G_jj (0 where G_jj <= 0)
+  hstep_body<TF, KP>(a, (int)blockIdx.x, (int)gridDim.x, -1, Gs, us, ginv, sh);
+}
+
+// Grouped half steps: problem p (descriptors in device memory) owns blocks
+// bbeg[p] .. bbeg[p + 1] - 1 of the grid; every descriptor's `bar` is the
+// same grid barrier.
+template <typename TF, int KP>
+__global__ void __launch_bounds__(HT) hstep_group_kernel(const HalfArgs* __restrict__ probs,
+                                                         const int* __restrict__ bbeg, int np) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TF* Gs = reinterpret_cast<TF*>(smraw);
+  TF* us = Gs + KP * KP;
+  __shared__ double sh[HT];
+  __shared__ TF ginv[KP];
+  __shared__ int p_s;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (bbeg[mid] <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    p_s = lo;
+  }
+  // some problem of the grid in the ascent stage (read before any barrier,
+  // so every block sees the same stages)
+  int asc = 0;
+  for (int q = threadIdx.x; q < np; q += HT)
+    if (!probs[q].gram_only && *(volatile int*)&probs[q].st->stage == 0) asc = 1;
+  const int lock = __syncthreads_or(asc) ? 1 : 0;
+  const int p = p_s;
+  hstep_body<TF, KP>(probs[p], (int)blockIdx.x - bbeg[p], bbeg[p + 1] - bbeg[p], lock, Gs, us,
+                     ginv, sh);
 }
 
 template <typename TF, int KP>
@@ -369,6 +424,37 @@ int half_step_grid(int fdt, int k, int num_sms) {
     cap = kp == 16 ? hstep_capacity<float, 16>(num_sms) : kp == 32 ? hstep_capacity<float, 32>(num_sms)
           : kp == 48 ? hstep_capacity<float, 48>(num_sms) : hstep_capacity<float, 64>(num_sms);
   return cap > NPART ? NPART : cap;
+}
+
+template <int K>
+static int group_capacity(int num_sms) {
+  const size_t smem = hstep_smem<float, K>();
+  cudaFuncSetAttribute(hstep_group_kernel<float, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, hstep_group_kernel<float, K>, HT, smem);
+  return (per < 1 ? 1 : per) * num_sms;
+}
+
+int half_group_capacity(int kp, int num_sms) {
+  return kp == 16 ? group_capacity<16>(num_sms)
+         : kp == 32 ? group_capacity<32>(num_sms)
+         : kp == 48 ? group_capacity<48>(num_sms)
+                    : group_capacity<64>(num_sms);
+}
+
+void launch_half_group(const HalfArgs* probs, const int* bbeg, int np, int grid, int kp,
+                       cudaStream_t s) {
+  note_launch(1);
+  void* args[] = {(void*)&probs, (void*)&bbeg, (void*)&np};
+#define HGL(K)                                                                                  \
+  cudaLaunchCooperativeKernel((void*)hstep_group_kernel<float, K>, dim3(grid), dim3(HT), args, \
+                              hstep_smem<float, K>(), s)
+  if (kp == 16) HGL(16);
+  else if (kp == 32) HGL(32);
+  else if (kp == 48) HGL(48);
+  else HGL(64);
+#undef HGL
 }
 
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s) {

@@ -36,6 +36,7 @@ struct DevState {
   double negmass;             // sum h(.) scratch
   double svd_res;             // SVD start residual
   double sigma1;
+  double f_last;              // objective after the last alternation
   GridBarrier bar;
 };
 
@@ -115,10 +116,20 @@ struct HalfArgs {
   void* th;
   void* tl;
   int64_t ldt;
+  // the grid barrier of the launch (&st->bar for one problem; one shared
+  // barrier for every problem of a grouped launch)
+  GridBarrier* bar;
 };
 // hstep.cu: one cooperative launch per half step; grid <= half_step_grid().
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);
 int half_step_grid(int fdt, int k, int num_sms);
+// Grouped half steps of np problems with FP32 factors (HalfArgs in device
+// memory, all with the same `bar`); problem p owns blocks bbeg[p] ..
+// bbeg[p + 1] - 1 (bbeg: np + 1 ints in device memory), rank padded to kp
+// for all.  Grid bbeg[np] <= half_group_capacity(kp).
+void launch_half_group(const HalfArgs* probs, const int* bbeg, int np, int grid, int kp,
+                       cudaStream_t s);
+int half_group_capacity(int kp, int num_sms);
 void launch_state_init(const void* U, const void* V, int64_t m, int64_t n, int k, int fdt,
                        int n_shift, DevState* st, double* part, cudaStream_t s);
 // ADMM pass of Algorithm 1 over W = [U; V] (see rows.cu).

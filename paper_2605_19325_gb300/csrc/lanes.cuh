@@ -98,14 +98,21 @@ __device__ __forceinline__ void accumulate_outer(const TF* xs, const TF* ys, int
 // takes partials l + 32 j in eight independent loads, then the eight are
 // combined pairwise and the lanes by a butterfly.  The order is fixed by nb,
 // so the sum does not depend on timing.  Block of BT threads.
+// The reduction runs on blocks bid = first .. nblk - 1 of a group of nblk
+// blocks (by default the whole grid).
 template <int BT>
 __device__ __forceinline__ void sum_block_partials(const double* part, int nb, int kk,
-                                                   double* out, int first = 0) {
+                                                   double* out, int first = 0, int bid = -1,
+                                                   int nblk = -1) {
   constexpr int WPB = BT / 32;
+  if (bid < 0) {
+    bid = (int)blockIdx.x;
+    nblk = (int)gridDim.x;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nbk = (int)gridDim.x - first;
-  if ((int)blockIdx.x < first || nbk <= 0) return;
-  for (int e = ((int)blockIdx.x - first) * WPB + warp; e < kk; e += nbk * WPB) {
+  const int nbk = nblk - first;
+  if (bid < first || nbk <= 0) return;
+  for (int e = (bid - first) * WPB + warp; e < kk; e += nbk * WPB) {
     double s = 0.0;
     for (int b0 = 0; b0 < nb; b0 += 256) {
       double c[8];
