@@ -1,0 +1,203 @@
+"""Serving: continuous batching of eNMF solves on one GPU.
+
+Requests (X, r) arrive over time.  A request is admitted when its device
+footprint fits the memory budget:
+  X in FP32, its BF16 pair X_hi / X_lo, U and V, and the context workspace
+  (enmf_workspace_size).
+On admission it gets the SVD start and the rotation, and then joins the batch
+of its padded rank (16, 32, 48 or 64).  Every batch advances all its members
+together, `chunk` alternations per step, in grouped launches under a
+replayed CUDA graph (enmf_batch_step).  So requests that arrive while others
+are running share the device with them, and each finished request frees its
+slot and memory for the next.
+
+A member is done when its objective, sampled after every step, has changed
+by less than `tol` (relative) over the last step while in the HALS stage, or
+after `max_iter` alternations.  X, U, V and the iteration state stay resident
+on the device from admission to completion.
+
+Everything runs on one CUDA stream, so the cooperative launches of different
+batches never run concurrently on the device.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .solver import Solver
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    X: np.ndarray        # m x n, nonnegative, host
+    r: int
+    arrival_s: float = 0.0
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    m: int
+    n: int
+    r: int
+    iters: int
+    f: float
+    rel_err: float
+    U: torch.Tensor      # host copies
+    V: torch.Tensor
+    arrival_s: float
+    admitted_s: float
+    done_s: float
+
+    @property
+    def latency_s(self):
+        return self.done_s - self.arrival_s
+
+
+def footprint(m, n, r):
+    """Device bytes a request holds while it is served."""
+    p = B.enmf_problem(m, n, n, r, B.ENMF_F32, B.ENMF_F32, B.ENMF_BF16)
+    return m * n * 4 + 2 * m * n * 2 + (m + n) * r * 4 + B.enmf_workspace_size(p)
+
+
+class _Slot:
+    __slots__ = ("req", "solver", "rp", "slot", "bytes", "f_prev", "admitted_s")
+
+
+class Server:
+    def __init__(self, budget_bytes=None, max_members=128, chunk=10, tol=1e-5, max_iter=500,
+                 min_iter=20, stream=None, tune=True):
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info()
+            budget_bytes = int(0.6 * free)
+        self.budget = budget_bytes
+        self.max_members = max_members
+        self.chunk = chunk
+        self.tol = tol
+        self.max_iter = max_iter
+        self.min_iter = min_iter
+        self.tune = tune
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.batches = {}            # padded rank -> batch handle
+        self.tuned = set()
+        self.pending = collections.deque()
+        self.active = []
+        self.used = 0
+        self.results = []
+        self.steps = 0
+
+    # ------------------------------------------------------------- requests
+    def submit(self, req: Request):
+        self.pending.append(req)
+
+    def _batch(self, rp):
+        b = self.batches.get(rp)
+        if b is None:
+            b = B.enmf_batch_create(self.max_members, stream=self.stream)
+            self.batches[rp] = b
+        return b
+
+    def _admit_one(self, req, now):
+        m, n = req.X.shape
+        with torch.cuda.stream(self.stream):
+            Xt = torch.from_numpy(np.ascontiguousarray(req.X, dtype=np.float32)).to(
+                "cuda", non_blocking=False)
+            s = Solver(Xt, req.r, stream=self.stream, x_stream=torch.bfloat16)
+            s.svd_init()
+            s.rotate()
+        rp = 16 if req.r <= 16 else 32 if req.r <= 32 else 48 if req.r <= 48 else 64
+        b = self._batch(rp)
+        sl = _Slot()
+        sl.req = req
+        sl.solver = s
+        sl.rp = rp
+        sl.slot = B.enmf_batch_add(b, s.ctx, s.X, s.U, s.V)
+        sl.bytes = footprint(m, n, req.r)
+        sl.f_prev = None
+        sl.admitted_s = now
+        self.used += sl.bytes
+        self.active.append(sl)
+
+    def _admit(self, now):
+        while self.pending and self.pending[0].arrival_s <= now:
+            req = self.pending[0]
+            need = footprint(req.X.shape[0], req.X.shape[1], req.r)
+            if self.active and self.used + need > self.budget:
+                break                   # wait for memory to free up
+            rp = 16 if req.r <= 16 else 32 if req.r <= 32 else 48 if req.r <= 48 else 64
+            b = self.batches.get(rp)
+            if b is not None and B.enmf_batch_size(b) >= self.max_members:
+                break
+            self.pending.popleft()
+            self._admit_one(req, now)
+
+    def _retire(self, now):
+        keep = []
+        for sl in self.active:
+            b = self.batches[sl.rp]
+            info, f = B.enmf_batch_member(b, sl.slot)
+            done = info.iters >= self.max_iter
+            if (not done and info.stage == 1 and info.iters >= self.min_iter
+                    and sl.f_prev is not None):
+                done = abs(sl.f_prev - f) <= self.tol * abs(f)
+            sl.f_prev = f
+            if not done:
+                keep.append(sl)
+                continue
+            B.enmf_batch_remove(b, sl.slot)
+            s = sl.solver
+            _, rel, _ = s.residual()
+            t = time.perf_counter() - self.t0
+            self.results.append(Result(sl.req.rid, s.X.shape[0], s.X.shape[1], sl.req.r,
+                                       info.iters, f, rel, s.U.cpu(), s.V.cpu(),
+                                       sl.req.arrival_s, sl.admitted_s, t))
+            s.close()
+            self.used -= sl.bytes
+        self.active = keep
+
+    # ----------------------------------------------------------------- loop
+    def run(self, requests=()):
+        """Serve `requests` (sorted by arrival) and whatever was submitted;
+        return the results in completion order."""
+        for req in sorted(requests, key=lambda q: q.arrival_s):
+            self.submit(req)
+        self.t0 = time.perf_counter()
+        while self.pending or self.active:
+            now = time.perf_counter() - self.t0
+            self._admit(now)
+            if not self.active:
+                if self.pending:
+                    wait = self.pending[0].arrival_s - (time.perf_counter() - self.t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+                continue
+            for rp, b in self.batches.items():
+                if B.enmf_batch_size(b) == 0:
+                    continue
+                if self.tune and rp not in self.tuned:
+                    B.enmf_batch_tune(b)
+                    self.tuned.add(rp)
+                B.enmf_batch_step(b, self.chunk)
+            self.steps += 1
+            self._retire(time.perf_counter() - self.t0)
+        return self.results
+
+    def close(self):
+        for b in self.batches.values():
+            B.enmf_batch_destroy(b)
+        self.batches = {}
+
+
+def stats(results, wall_s):
+    """solves/s and latency percentiles (ms) of a finished run."""
+    lat = np.array([r.latency_s for r in results]) * 1e3
+    return {"solves": len(results), "wall_s": wall_s,
+            "solves_per_s": len(results) / wall_s if wall_s > 0 else 0.0,
+            "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None}
