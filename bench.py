@@ -213,6 +213,19 @@ FORMS = {
 }
 
 
+def replica_throughput(total_ms, steps, world, device="cpu"):
+    """Replicas: every rank timed `steps` solves of its own; the job's time is
+    the slowest rank's (MAX over ranks), and the throughput counts every
+    rank's solves.  Returns (job time in ms, solves/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps / (total_ms / 1e3)
+
+
 def serving_leg(n_req):
     """Serving + batching workload: a Poisson stream of NMF requests with m, n
     log-uniform in [64, 4096] and r uniform in {4, 8, 16, 32, 64}, planted
@@ -357,12 +370,8 @@ def run_ours(args):
     clk = clocks.stop()
     sweep_ms, sweeps = B.enmf_profile_read(s.ctx, reset=1)
     B.enmf_profile(s.ctx, 0)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = replica_throughput(total_ms, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
     U_host = s.U.double().cpu().numpy()
     V_host = s.V.double().cpu().numpy()
     s.close()
