@@ -99,9 +99,11 @@ const char* enmf_status_string(enmf_status s);
 
 /* ---- 1. SVD start (Sec. 4) ---------------------------------------------
  * Randomized subspace iteration with oversampling p: Q spans X*Omega, then
- * alternately X^T Q and X Q2 are orthonormalised (Gram eigen-decomposition,
- * two passes, numerical-rank truncation) and the top-r Ritz triplets of the
- * Rayleigh-Ritz matrix are taken by one-sided Jacobi SVD in FP64.  Iterates
+ * alternately X^T Q and X Q2 are orthonormalised (two passes of T = D L^-T from
+ * the Cholesky factor L of the diagonally scaled Gram D G D; a Gram eigen map
+ * with numerical-rank truncation when a pivot is near zero) and the top-r Ritz
+ * triplets of the Rayleigh-Ritz matrix are taken by one-sided Jacobi SVD in
+ * FP64.  Iterates
  * until ||X V_r - U_r S_r||_F <= tol * sigma_1, at most max_iters times.
  * Output: U (m x r) = U_r S^(1/2), V (n x r) = V_r S^(1/2), with column j of
  * both negated when sum_i U_ij + sum_i V_ij < 0; sigma (device, r doubles)
@@ -125,8 +127,10 @@ enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void* V, double
 
 /* ---- 2. Rotation toward the orthant (Algorithm 1) -----------------------
  * W = [U; V].  Each ADMM step: b = W R - Y / rho; Z = prox(b) (Eq. 7);
- * M = W^T (Z + Y / rho); R = C D^T from M = C S D^T (Procrustes, FP64 r x r
- * one-sided Jacobi SVD on the device); Y += rho (Z - W R).  R0 = I, Y0 = 0.
+ * M = W^T (Z + Y / rho); R = polar(M) = C D^T from M = C S D^T (Procrustes;
+ * FP64 factors: warm-started one-sided Jacobi SVD in FP64; FP32 factors:
+ * Newton-Schulz in FP32 with a last step on X^T X formed in FP64, every step
+ * of the loop in one persistent launch); Y += rho (Z - W R).  R0 = I, Y0 = 0.
  * rho = rho_scale / RMS(W) unless rho > 0 is given.  Stops when
  * ||R_k+1 - R_k||_F <= tol * sqrt(r) or after max_iter steps.  On exit U and V
  * are overwritten in place by U R and V R; R (device, r x r row-major FP64)
