@@ -78,11 +78,15 @@ typedef struct {
   int32_t f_dtype;  /* enmf_dtype of U and V: ENMF_F64 with X F64, else F32   */
   int32_t stream_dtype; /* type the iteration's X sweeps read:                */
                     /*   = x_dtype (or 0 with F64 X): the SIMT sweeps;        */
-                    /*   ENMF_BF16 with F32 X: the precision form -- the      */
-                    /*   tensor-core sweeps read X_hi = bf16(X) and apply     */
-                    /*   X_lo = bf16(X - X_hi) every correct_every steps;     */
-                    /*   ENMF_BF16 with BF16 X: tensor-core sweeps on X as    */
-                    /*   given (no correction).  F32 factors required.        */
+                    /*   ENMF_BF16 / ENMF_F16 with F32 X: the precision form  */
+                    /*   -- the tensor-core sweeps read X_hi = t(X) and apply */
+                    /*   X_lo = t(X - X_hi) every correct_every steps, t the  */
+                    /*   rounding to that type (FP16: X <= 65504, else        */
+                    /*   ENMF_EDOMAIN at enmf_stage_x's next sync);           */
+                    /*   ENMF_BF16 / ENMF_F16 with X of that type: tensor-    */
+                    /*   core sweeps on X as given (no correction).  F32      */
+                    /*   factors required; with FP16 the factor entries must  */
+                    /*   stay within the FP16 range.                          */
 } enmf_problem;
 
 typedef struct enmf_ctx enmf_ctx;

@@ -42,7 +42,10 @@ extern "C" const char* enmf_status_string(enmf_status s) {
 extern "C" const char* enmf_version(void) { return "enmf-gb300 0.1"; }
 
 // Tensor-core (BF16 stream) form?
-static bool tc_form(const enmf_problem* p) { return p->stream_dtype == ENMF_BF16; }
+// Tensor-core (16-bit stream) form?  BF16 or FP16 X in the sweeps.
+static bool tc_form(const enmf_problem* p) {
+  return p->stream_dtype == ENMF_BF16 || p->stream_dtype == ENMF_F16;
+}
 
 static bool valid_problem(const enmf_problem* p) {
   if (!p) return false;
@@ -51,8 +54,9 @@ static bool valid_problem(const enmf_problem* p) {
   if (p->x_dtype < ENMF_F64 || p->x_dtype > ENMF_F16) return false;
   if (tc_form(p)) {
     if (p->f_dtype != ENMF_F32) return false;
-    if (p->x_dtype != ENMF_F32 && p->x_dtype != ENMF_BF16) return false;
-    if (p->x_dtype == ENMF_BF16 && (p->ldx % 8) != 0) return false;
+    // F32 X (split into a 16-bit pair) or X already of the stream type
+    if (p->x_dtype != ENMF_F32 && p->x_dtype != p->stream_dtype) return false;
+    if (p->x_dtype != ENMF_F32 && (p->ldx % 8) != 0) return false;
     if (p->m > 0x7fffffffLL || p->n > 0x7fffffffLL) return false;
   } else if (p->stream_dtype != 0 && p->stream_dtype != p->x_dtype) {
     return false;
@@ -276,10 +280,12 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
     ctx->cv = (float*)grab(t.cv);
     ctx->cu = (float*)grab(t.cu);
     ctx->dprob = (SweepProb*)grab(t.desc);
-    bool ok = tc_make_map(ctx->maps[MAP_VH], ctx->vth, t.rp, p->n, t.ldn, 64, t.rp) &&
-              tc_make_map(ctx->maps[MAP_VL], ctx->vtl, t.rp, p->n, t.ldn, 64, t.rp) &&
-              tc_make_map(ctx->maps[MAP_UH], ctx->uth, t.rp, p->m, t.ldm, 64, t.rp) &&
-              tc_make_map(ctx->maps[MAP_UL], ctx->utl, t.rp, p->m, t.ldm, 64, t.rp);
+    ctx->tf16 = p->stream_dtype == ENMF_F16;
+    const int f16 = ctx->tf16;
+    bool ok = tc_make_map(ctx->maps[MAP_VH], ctx->vth, t.rp, p->n, t.ldn, 64, t.rp, f16) &&
+              tc_make_map(ctx->maps[MAP_VL], ctx->vtl, t.rp, p->n, t.ldn, 64, t.rp, f16) &&
+              tc_make_map(ctx->maps[MAP_UH], ctx->uth, t.rp, p->m, t.ldm, 64, t.rp, f16) &&
+              tc_make_map(ctx->maps[MAP_UL], ctx->utl, t.rp, p->m, t.ldm, 64, t.rp, f16);
     if (!ok) {
       cudaFree(ctx->tcws);
       cudaFree(ctx->ws);
@@ -304,20 +310,21 @@ extern "C" enmf_status enmf_stage_x(enmf_ctx* ctx, const void* X) {
   if (!ctx->tc) return ENMF_ESTATE;
   const enmf_problem& p = ctx->p;
   if (p.x_dtype == ENMF_F32) {
-    launch_split_x((const float*)X, p.m, p.n, p.ldx, ctx->own_xh, ctx->xl, ctx->ldh, ctx->err,
+    launch_split_x((const float*)X, p.m, p.n, p.ldx, ctx->own_xh, ctx->xl, ctx->ldh, ctx->tf16,
+                   ctx->err,
                    ctx->stream);
     if (cudaGetLastError() != cudaSuccess) {
       ctx->poison = ENMF_ECUDA;
       return ENMF_ECUDA;
     }
     ctx->xh = ctx->own_xh;
-    if (!tc_make_map(ctx->maps[MAP_XH], ctx->xh, p.m, p.n, ctx->ldh, 64, 128) ||
-        !tc_make_map(ctx->maps[MAP_XL], ctx->xl, p.m, p.n, ctx->ldh, 64, 128))
+    if (!tc_make_map(ctx->maps[MAP_XH], ctx->xh, p.m, p.n, ctx->ldh, 64, 128, ctx->tf16) ||
+        !tc_make_map(ctx->maps[MAP_XL], ctx->xl, p.m, p.n, ctx->ldh, 64, 128, ctx->tf16))
       return ENMF_ECUDA;
   } else {
     if (((uintptr_t)X & 15) != 0) return ENMF_EINVAL;
     ctx->xh = X;
-    if (!tc_make_map(ctx->maps[MAP_XH], X, p.m, p.n, p.ldx, 64, 128)) return ENMF_ECUDA;
+    if (!tc_make_map(ctx->maps[MAP_XH], X, p.m, p.n, p.ldx, 64, 128, ctx->tf16)) return ENMF_ECUDA;
   }
   ctx->staged_src = X;
   return ENMF_OK;
@@ -573,6 +580,7 @@ HalfArgs ctx_half_args(enmf_ctx* ctx, int which, void* F, const void* A, const d
     a.th = which == 0 ? ctx->uth : ctx->vth;
     a.tl = which == 0 ? ctx->utl : ctx->vtl;
     a.ldt = which == 0 ? ctx->ldm : ctx->ldn;
+    a.t_f16 = ctx->tf16;
   }
   return a;
 }
@@ -603,6 +611,7 @@ static const SweepProb* tc_desc(enmf_ctx* ctx, int slot, int mode, bool lo, floa
   tc_prob_sizes(mode, &d, mode == 0 ? p.m : p.n, mode == 0 ? p.n : p.m, p.r, 0, 0, &units, &tiles);
   d.out = out;
   d.corr = corr;
+  d.f16 = ctx->tf16;
   if (memcmp(&d, &ctx->hprob[slot], sizeof(d)) != 0) {
     ctx->hprob[slot] = d;
     cudaMemcpyAsync(ctx->dprob + slot, &ctx->hprob[slot], sizeof(d), cudaMemcpyHostToDevice,
@@ -640,7 +649,8 @@ static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int
     prof_mark(ctx, rec);
     return;
   }
-  if (split) launch_split_transpose((const float*)V, p.n, r, ctx->vth, ctx->vtl, ctx->ldn, s);
+  if (split)
+    launch_split_transpose((const float*)V, p.n, r, ctx->vth, ctx->vtl, ctx->ldn, ctx->tf16, s);
   const int base = out == ctx->M0 ? 0 : 4;
   if (corr == 2 && ctx->xl) {
     const SweepProb* d = tc_desc(ctx, base + 1, 0, true, ctx->cv, nullptr);
@@ -666,7 +676,8 @@ static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, in
     prof_mark(ctx, rec);
     return;
   }
-  if (split) launch_split_transpose((const float*)U, p.m, r, ctx->uth, ctx->utl, ctx->ldm, s);
+  if (split)
+    launch_split_transpose((const float*)U, p.m, r, ctx->uth, ctx->utl, ctx->ldm, ctx->tf16, s);
   const int base = out == ctx->N0 ? 2 : 6;
   if (corr == 2 && ctx->xl) {
     const SweepProb* d = tc_desc(ctx, base + 1, 1, true, ctx->cu, nullptr);
@@ -781,10 +792,11 @@ void ctx_iter_prologue(enmf_ctx* ctx, const void* X, void* U, void* V, int n_shi
   g.gpart = ctx->part;
   g.gram_only = 1;
   g.bar = &ctx->st->bar;
-  if (ctx->tc) {   // and the BF16 pair of V for the first sweep
+  if (ctx->tc) {   // and the 16-bit pair of V for the first sweep
     g.th = ctx->vth;
     g.tl = ctx->vtl;
     g.ldt = ctx->ldn;
+    g.t_f16 = ctx->tf16;
   }
   launch_half_step(g, ctx->grid_v, s);
 }

@@ -120,6 +120,7 @@ enmf_status rebuild(enmf_batch* b) {
       float* lo_out = mode == 0 ? ctx->cv : ctx->cu;
       d.out = lo ? lo_out : main_out;
       d.corr = (!lo && ctx->xl) ? lo_out : nullptr;
+      d.f16 = ctx->tf16;
       b->h_sw[q].push_back(d);
       b->W[q] += units;
       tiles[q] += t;

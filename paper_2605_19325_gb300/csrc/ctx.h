@@ -72,8 +72,9 @@ struct enmf_ctx {
   cudaEvent_t pev[2 * 256];
   double prof_ms;
   long long prof_n;
-  // precision form (tensor-core sweeps on BF16 X)
+  // precision form (tensor-core sweeps on BF16 or FP16 X)
   int tc;
+  int tf16;                 // the 16-bit type is FP16 (else BF16)
   int rp;
   int64_t ldh, ldn, ldm;
   int sv, st_split;

@@ -28,6 +28,7 @@
 // each block contributes <U^T U, its partial> and block 0 sums those scalars
 // after the same barrier: one barrier per half step in the HALS stage.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.h"
 #include "lanes.cuh"
@@ -62,34 +63,33 @@ __device__ __forceinline__ void gram_pass(TF* us, const TF (&u)[KP / LPR], int r
 }
 
 // The factor operand of the tensor-core sweeps: row i of F written to column
-// i of th = bf16(F^T) and tl = bf16(F^T - th), the same rounding as the
-// stand-alone split of tc_sweep.cu.  FP32 factors only.
+// i of th = t(F^T) and tl = t(F^T - th), t the rounding to BF16 or FP16 --
+// the same rounding as the stand-alone split of tc_sweep.cu.  FP32 factors
+// only.
 template <typename TF, int E>
 __device__ __forceinline__ void write_split(const HalfArgs& a, int64_t i, bool live, int k,
                                             int sub, const TF (&u)[E]) {
   if constexpr (sizeof(TF) == 4) {
     if (!a.th || !live) return;
-    __nv_bfloat16* th = reinterpret_cast<__nv_bfloat16*>(a.th);
-    __nv_bfloat16* tl = reinterpret_cast<__nv_bfloat16*>(a.tl);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int l = sub + LPR * e;
       if (l < k) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(u[e]);
-        th[(int64_t)l * a.ldt + i] = h;
-        tl[(int64_t)l * a.ldt + i] = __float2bfloat16_rn(u[e] - __bfloat162float(h));
+        const int64_t o = (int64_t)l * a.ldt + i;
+        if (a.t_f16) {
+          const __half h = __float2half_rn(u[e]);
+          reinterpret_cast<__half*>(a.th)[o] = h;
+          reinterpret_cast<__half*>(a.tl)[o] = __float2half_rn(u[e] - __half2float(h));
+        } else {
+          const __nv_bfloat16 h = __float2bfloat16_rn(u[e]);
+          reinterpret_cast<__nv_bfloat16*>(a.th)[o] = h;
+          reinterpret_cast<__nv_bfloat16*>(a.tl)[o] = __float2bfloat16_rn(u[e] - __bfloat162float(h));
+        }
       }
     }
   }
 }
 
-// The half step of one problem on its group of nb blocks (this block is lb
-// of them).  lock < 0: the problem has the grid to itself, so the PBCD loop
-// may stop as soon as its test is met.  lock >= 0: several problems share
-// the grid and every block must pass the same grid barriers: lock = 1 when
-// some problem of the grid is in the ascent stage -- then every block runs
-// all pbcd_max_iter barriered PBCD iterations (idle once its own problem has
-// stopped, or when it is not ascending).
 template <typename TF, int KP>
 __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, const int nb,
                                            const int lock, TF* Gs, TF* us, TF* ginv,

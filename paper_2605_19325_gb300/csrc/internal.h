@@ -116,6 +116,7 @@ struct HalfArgs {
   void* th;
   void* tl;
   int64_t ldt;
+  int t_f16;          // th / tl in FP16 (else BF16)
   // the grid barrier of the launch (&st->bar for one problem; one shared
   // barrier for every problem of a grouped launch)
   GridBarrier* bar;
@@ -200,7 +201,8 @@ struct alignas(64) SweepProb {
   float* out;
   const float* corr;
   int r;
-  int pad_[3];
+  int f16;          // X and factor as FP16 (else BF16)
+  int pad_[2];
 };
 // Fills the sizes of d (maps and pointers set by the caller) and returns its
 // work units (tiles x k-blocks) and tiles through *units / *tiles.
@@ -215,14 +217,16 @@ int tc_group_grid(int64_t W, int num_sms);
 // 2D BF16 tensor map (CUtensorMap, 128 bytes at `map`) over a row-major
 // (rows x cols, ld) array, box box_cols x box_rows, 128-byte swizzle.
 bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
-                 int box_cols, int box_rows);
+                 int box_cols, int box_rows, int f16 = 0);
 int tc_rank_pad(int r);
 // CTAs of a one-problem sweep (<= num_sms); part needs grid x 2 x 128 x rp floats.
 int tc_grid(int64_t rows_out, int64_t red, int mode, int num_sms);
+// The 16-bit pairs (f16: FP16, else BF16).  split_x flags ERR_DOMAIN for a
+// negative or non-finite X entry, or one beyond the FP16 range.
 void launch_split_transpose(const float* F, int64_t rows, int r, void* hi, void* lo, int64_t ldt,
-                            cudaStream_t s);
+                            int f16, cudaStream_t s);
 void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh, void* xl,
-                    int64_t ldh, int* err, cudaStream_t s);
+                    int64_t ldh, int f16, int* err, cudaStream_t s);
 constexpr int TC_KB_XV = 128, TC_KB_XT = 128;
 
 // KKT finalisation: combine the two factors' partial measures.

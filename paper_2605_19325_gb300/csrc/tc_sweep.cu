@@ -20,6 +20,9 @@
 // The sweep reads X once per product, so at small rank it is bound by HBM
 // bandwidth: algorithmic bytes per sweep = m n * 2.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
 
 #include "internal.h"
 
@@ -92,13 +95,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
   return d;
 }
 
-// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor, kind::f16: FP32 accumulate, A and B both BF16 (type
+// code 1) or both FP16 (type code 0), M x N.
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, int a_mn_major, int f16) {
+  return (1u << 4) | ((uint32_t)(f16 ? 0 : 1) << 7) | ((uint32_t)(f16 ? 0 : 1) << 10) |
+         ((uint32_t)a_mn_major << 15) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+__device__ __forceinline__ void mma_f16kind(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -186,7 +190,8 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
   constexpr uint32_t A_BYTES = TILE * KB * 2;                 // 16 KB or 32 KB
   constexpr uint32_t B_BYTES = RP * KB * 2;                   // one of hi / lo
   constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
-  constexpr uint32_t IDESC = idesc_bf16(TILE, RP, MODE);
+  constexpr uint32_t IDESC_BF16 = idesc_f16kind(TILE, RP, MODE, 0);
+  constexpr uint32_t IDESC_F16 = idesc_f16kind(TILE, RP, MODE, 1);
   constexpr uint32_t TMEM_COLS = RP <= 32 ? 64 : 128;        // two accumulators
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -307,6 +312,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dcol = tmem + (uint32_t)(b * RP);
+        const uint32_t idesc = pv.d->f16 ? IDESC_F16 : IDESC_BF16;
         uint32_t accum = 0;
         for (; w < wend; ++w, ++i) {
           const int s = (int)(i % stages);
@@ -338,8 +344,8 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
               dbh = sdesc(bh0 + boff, 16, 1024);
               dbl = sdesc(bl0 + boff, 16, 1024);
             }
-            mma_bf16(dcol, da, dbh, IDESC, accum);
-            mma_bf16(dcol, da, dbl, IDESC, 1u);
+            mma_f16kind(dcol, da, dbh, idesc, accum);
+            mma_f16kind(dcol, da, dbl, idesc, 1u);
             accum = 1u;
           }
           mma_commit(&empty_bar[s]);
@@ -527,11 +533,17 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
   }
 }
 
-// F (rows x r, FP32) -> F^T as a BF16 pair (RP x ldt): hi = bf16(F),
-// lo = bf16(F - hi).  Rows r..RP-1 of the outputs stay zero.
+// 16-bit conversions of the pairs (round to nearest even).
+__device__ __forceinline__ __nv_bfloat16 to16(float v, __nv_bfloat16*) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ __half to16(float v, __half*) { return __float2half_rn(v); }
+__device__ __forceinline__ float from16(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float from16(__half v) { return __half2float(v); }
+
+// F (rows x r, FP32) -> F^T as a 16-bit pair (RP x ldt): hi = t(F),
+// lo = t(F - hi), t the rounding to T.  Rows r..RP-1 of the outputs stay zero.
+template <typename T>
 __global__ void split_transpose_kernel(const float* __restrict__ F, int64_t rows, int r,
-                                       __nv_bfloat16* __restrict__ hi,
-                                       __nv_bfloat16* __restrict__ lo, int64_t ldt) {
+                                       T* __restrict__ hi, T* __restrict__ lo, int64_t ldt) {
   __shared__ float tile[32][33];
   const int64_t i0 = (int64_t)blockIdx.x * 32;
   const int j0 = blockIdx.y * 32;
@@ -546,28 +558,30 @@ __global__ void split_transpose_kernel(const float* __restrict__ F, int64_t rows
     const int64_t i = i0 + threadIdx.x;
     if (j < r && i < rows) {
       const float v = tile[threadIdx.x][q];
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      const T h = to16(v, (T*)nullptr);
       hi[(int64_t)j * ldt + i] = h;
-      lo[(int64_t)j * ldt + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+      lo[(int64_t)j * ldt + i] = to16(v - from16(h), (T*)nullptr);
     }
   }
 }
 
-
-// X (FP32, m x n, ldx) -> X_hi = bf16(X), X_lo = bf16(X - X_hi), both m x ldh.
+// X (FP32, m x n, ldx) -> X_hi = t(X), X_lo = t(X - X_hi), both m x ldh.
+// ERR_DOMAIN for a negative or non-finite entry, or (FP16) one beyond the
+// largest finite FP16 value.
+template <typename T>
 __global__ void split_x_kernel(const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
-                               __nv_bfloat16* __restrict__ xh, __nv_bfloat16* __restrict__ xl,
-                               int64_t ldh, int* err) {
+                               T* __restrict__ xh, T* __restrict__ xl, int64_t ldh, float vmax,
+                               int* err) {
   const int64_t total = m * n;
   int bad = 0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / n, j = e % n;
     const float v = X[i * ldx + j];
-    if (!(v >= 0.0f) || isinf(v)) bad = 1;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    if (!(v >= 0.0f) || isinf(v) || v > vmax) bad = 1;
+    const T h = to16(v, (T*)nullptr);
     xh[i * ldh + j] = h;
-    xl[i * ldh + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+    xl[i * ldh + j] = to16(v - from16(h), (T*)nullptr);
   }
   if (bad) atomicOr(err, ERR_DOMAIN);
 }
@@ -596,7 +610,7 @@ static EncodeTiledFn encode_fn() {
 // 2D BF16 tensor map over a row-major (rows x cols, ld elements) array with a
 // box of box_cols x box_rows and 128-byte swizzle.  Out-of-range reads give 0.
 bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
-                 int box_cols, int box_rows) {
+                 int box_cols, int box_rows, int f16) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   if (((uintptr_t)base & 15) || ((ld * 2) & 15)) return false;
@@ -604,7 +618,8 @@ bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
   cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  CUresult r = fn(reinterpret_cast<CUtensorMap*>(map),
+                  f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -684,21 +699,30 @@ void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W
 }
 
 void launch_split_transpose(const float* F, int64_t rows, int r, void* hi, void* lo, int64_t ldt,
-                            cudaStream_t s) {
+                            int f16, cudaStream_t s) {
   note_launch(1);
   dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((r + 31) / 32));
-  tc::split_transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(F, rows, r, (__nv_bfloat16*)hi,
-                                                           (__nv_bfloat16*)lo, ldt);
+  if (f16)
+    tc::split_transpose_kernel<__half><<<grid, dim3(32, 8), 0, s>>>(F, rows, r, (__half*)hi,
+                                                                    (__half*)lo, ldt);
+  else
+    tc::split_transpose_kernel<__nv_bfloat16><<<grid, dim3(32, 8), 0, s>>>(
+        F, rows, r, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, ldt);
 }
 
 void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh, void* xl,
-                    int64_t ldh, int* err, cudaStream_t s) {
+                    int64_t ldh, int f16, int* err, cudaStream_t s) {
   note_launch(1);
   int64_t total = m * n;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 8192) blocks = 8192;
-  tc::split_x_kernel<<<blocks, 256, 0, s>>>(X, m, n, ldx, (__nv_bfloat16*)xh, (__nv_bfloat16*)xl,
-                                            ldh, err);
+  if (f16)
+    tc::split_x_kernel<__half><<<blocks, 256, 0, s>>>(X, m, n, ldx, (__half*)xh, (__half*)xl, ldh,
+                                                      65504.0f, err);
+  else
+    tc::split_x_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(X, m, n, ldx, (__nv_bfloat16*)xh,
+                                                             (__nv_bfloat16*)xl, ldh, INFINITY,
+                                                             err);
 }
 
 }  // namespace enmf

@@ -19,9 +19,9 @@ _XDT = {torch.float64: B.ENMF_F64, torch.float32: B.ENMF_F32, torch.bfloat16: B.
 def problem_for(X, r, f_dtype=None, stream=None):
     """C problem descriptor for X (m x n, row-major) at rank r.
 
-    stream=torch.bfloat16 selects the precision form: the iteration's X sweeps
-    run on the tensor cores over a BF16 copy of X (with the X_lo correction
-    when X is FP32)."""
+    stream=torch.bfloat16 (or torch.float16) selects the precision form: the
+    iteration's X sweeps run on the tensor cores over a BF16 (FP16) copy of X,
+    with the X_lo correction when X is FP32."""
     if X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a row-major matrix (unit column stride)")
     xdt = _XDT.get(X.dtype)
@@ -30,7 +30,7 @@ def problem_for(X, r, f_dtype=None, stream=None):
     if f_dtype is None:
         f_dtype = torch.float64 if X.dtype == torch.float64 else torch.float32
     fdt = B.ENMF_F64 if f_dtype == torch.float64 else B.ENMF_F32
-    sdt = B.ENMF_BF16 if stream == torch.bfloat16 else 0
+    sdt = {torch.bfloat16: B.ENMF_BF16, torch.float16: B.ENMF_F16}.get(stream, 0)
     return B.enmf_problem(X.shape[0], X.shape[1], X.stride(0), r, xdt, fdt, sdt), f_dtype
 
 
@@ -57,7 +57,7 @@ class Solver:
         self.problem, self.f_dtype = problem_for(X, r, f_dtype, x_stream)
         self.stream = stream
         self.ctx = B.enmf_create(self.problem, stream)
-        if x_stream == torch.bfloat16:
+        if x_stream in (torch.bfloat16, torch.float16):
             B.enmf_stage_x(self.ctx, X)
         dev = X.device
         self.U = torch.zeros(X.shape[0], r, dtype=self.f_dtype, device=dev)
