@@ -35,34 +35,42 @@ __device__ __forceinline__ void rr_pair(int pi, int rnd, int Np, int& p, int& q)
   if (p > q) { int t = p; p = q; q = t; }
 }
 
+// Scratch of the Jacobi rounds, shared by its FP32 and FP64 instances (one
+// allocation per kernel).
+__shared__ int jac_rotated;
+__shared__ double jac_part[LMAX / 2][3][33];
+__shared__ double jac_rot[LMAX / 2][2];
+
 // Column-major A (rows x Np) and V (Np x Np) in shared memory, Np even (a
-// padding column is zero), rows <= LMAX, Np <= LMAX.  Returns the number of
-// sweeps run (JAC_MAX_SWEEPS if it did not converge).
+// padding column is zero), rows <= LMAX, Np <= LMAX.  Runs at most
+// max_sweeps sweeps and returns the number run.  A pair is rotated when
+// |a_p . a_q| > tol * |a_p| |a_q|, tol = (1e-15 in FP64, 1e-6 in FP32) x
+// max(rows, 8): above the rounding of the dot products, so the sweeps end.
 //
 // FP64 issue rate is the limit on this GPU, so each round keeps the FP64
 // instruction count low: lanes form partial products of their rows, one
 // thread per (pair, quantity) sums the 32 partials in lane order, one thread
 // per pair computes the rotation, then one warp per pair applies it.
-__device__ int jacobi_osvd(double* A, int rows, int Np, double* V) {
-  __shared__ int rotated;
-  __shared__ double part[LMAX / 2][3][33];
-  __shared__ double rot[LMAX / 2][2];
+template <typename T>
+__device__ int jacobi_osvd(T* A, int rows, int Np, T* V, int max_sweeps) {
+  T (*part)[3][33] = reinterpret_cast<T (*)[3][33]>(jac_part);
+  T (*rot)[2] = reinterpret_cast<T (*)[2]>(jac_rot);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int npairs = Np / 2;
-  const double tol = 1e-15 * (double)(rows > 8 ? rows : 8);
+  const T tol = (T)((sizeof(T) == 8 ? 1e-15 : 1e-6) * (double)(rows > 8 ? rows : 8));
   int sweep = 0;
-  for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) jac_rotated = 0;
     for (int rnd = 0; rnd < Np - 1; ++rnd) {
       // partial products: lane l takes rows l, l + 32, ...
       for (int pi = warp; pi < npairs; pi += SM_WARPS) {
         int p, q;
         rr_pair(pi, rnd, Np, p, q);
-        const double* ap = A + (size_t)p * rows;
-        const double* aq = A + (size_t)q * rows;
-        double al = 0.0, be = 0.0, ga = 0.0;
+        const T* ap = A + (size_t)p * rows;
+        const T* aq = A + (size_t)q * rows;
+        T al = 0, be = 0, ga = 0;
         for (int i = lane; i < rows; i += 32) {
-          const double x = ap[i], y = aq[i];
+          const T x = ap[i], y = aq[i];
           al = fma(x, x, al);
           be = fma(y, y, be);
           ga = fma(x, y, ga);
@@ -75,7 +83,7 @@ __device__ int jacobi_osvd(double* A, int rows, int Np, double* V) {
       // one thread per (pair, quantity): fixed lane-order sum
       for (int t = threadIdx.x; t < 3 * npairs; t += SM_T) {
         const int pi = t / 3, qq = t % 3;
-        double s = 0.0;
+        T s = 0;
 #pragma unroll 8
         for (int l = 0; l < 32; ++l) s += part[pi][qq][l];
         part[pi][qq][32] = s;
@@ -84,45 +92,106 @@ __device__ int jacobi_osvd(double* A, int rows, int Np, double* V) {
       // one thread per pair: the rotation (c, s), or (1, 0) when the pair is
       // already orthogonal to working precision
       for (int pi = threadIdx.x; pi < npairs; pi += SM_T) {
-        const double al = part[pi][0][32], be = part[pi][1][32], ga = part[pi][2][32];
-        double c = 1.0, s = 0.0;
-        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
-          const double z = (be - al) / (2.0 * ga);
-          const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
-          c = 1.0 / sqrt(1.0 + t * t);
+        const T al = part[pi][0][32], be = part[pi][1][32], ga = part[pi][2][32];
+        T c = 1, s = 0;
+        if (ga != T(0) && fabs(ga) > tol * sqrt(al * be)) {
+          const T z = (be - al) / (T(2) * ga);
+          const T t = (z >= T(0) ? T(1) : T(-1)) / (fabs(z) + sqrt(T(1) + z * z));
+          c = T(1) / sqrt(T(1) + t * t);
           s = c * t;
-          rotated = 1;
+          jac_rotated = 1;
         }
         rot[pi][0] = c;
         rot[pi][1] = s;
       }
       __syncthreads();
       for (int pi = warp; pi < npairs; pi += SM_WARPS) {
-        const double c = rot[pi][0], s = rot[pi][1];
-        if (s == 0.0) continue;
+        const T c = rot[pi][0], s = rot[pi][1];
+        if (s == T(0)) continue;
         int p, q;
         rr_pair(pi, rnd, Np, p, q);
-        double* ap = A + (size_t)p * rows;
-        double* aq = A + (size_t)q * rows;
+        T* ap = A + (size_t)p * rows;
+        T* aq = A + (size_t)q * rows;
         for (int i = lane; i < rows; i += 32) {
-          const double x = ap[i], y = aq[i];
+          const T x = ap[i], y = aq[i];
           ap[i] = c * x - s * y;
           aq[i] = s * x + c * y;
         }
-        double* vp = V + (size_t)p * Np;
-        double* vq = V + (size_t)q * Np;
+        T* vp = V + (size_t)p * Np;
+        T* vq = V + (size_t)q * Np;
         for (int i = lane; i < Np; i += 32) {
-          const double x = vp[i], y = vq[i];
+          const T x = vp[i], y = vq[i];
           vp[i] = c * x - s * y;
           vq[i] = s * x + c * y;
         }
       }
       __syncthreads();
     }
-    if (!rotated) break;
+    if (!jac_rotated) break;
     __syncthreads();
   }
   return sweep;
+}
+
+// The same one-sided Jacobi in two precisions: sweeps in FP32 (64 times the
+// FP64 rate on this GPU) to single-precision orthogonality of A's columns,
+// then the accumulated rotation V32 -- orthogonal only to FP32 rounding -- is
+// made orthogonal in FP64 by one Newton-Schulz step V = V32 (3 I - V32^T V32)
+// / 2, A = A0 V is formed in FP64, and FP64 sweeps finish: from nearly
+// orthogonal columns they converge in one or two sweeps (Jacobi's quadratic
+// convergence).  A (FP64, in/out) as in jacobi_osvd, V (FP64, out) the
+// accumulated rotation; scratch: A32 (Np x rows floats), V32 (Np x Np
+// floats), T (Np x Np doubles).  Returns the FP64 sweeps run.
+__device__ int jacobi_osvd_mixed(double* A, int rows, int Np, double* V, float* A32, float* V32,
+                                 double* T) {
+  for (int e = threadIdx.x; e < Np * rows; e += SM_T) A32[e] = (float)A[e];
+  for (int e = threadIdx.x; e < Np * Np; e += SM_T) V32[e] = (e / Np == e % Np) ? 1.f : 0.f;
+  __syncthreads();
+  jacobi_osvd<float>(A32, rows, Np, V32, JAC_MAX_SWEEPS);
+  // two Newton-Schulz steps V <- V (3 I - V^T V) / 2 in FP64 from V = V32
+  // (an orthogonality error e becomes about e^2 per step); V^T V goes to T,
+  // the new V to registers first (column-major: V[c * Np + i] is entry (i, c))
+  constexpr int NV = (LMAX * LMAX + SM_T - 1) / SM_T;   // entries per thread
+  for (int e = threadIdx.x; e < Np * Np; e += SM_T) V[e] = (double)V32[e];
+  __syncthreads();
+  for (int step = 0; step < 2; ++step) {
+    for (int e = threadIdx.x; e < Np * Np; e += SM_T) {   // T = V^T V
+      const int c = e / Np, i = e % Np;
+      double acc = 0.0;
+      for (int j = 0; j < Np; ++j) acc = fma(V[(size_t)i * Np + j], V[(size_t)c * Np + j], acc);
+      T[e] = acc;
+    }
+    __syncthreads();
+    double nv[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int e = threadIdx.x + q * SM_T;
+      if (e < Np * Np) {
+        const int c = e / Np, i = e % Np;
+        double acc = 0.0;
+        for (int j = 0; j < Np; ++j) acc = fma(V[(size_t)j * Np + i], T[(size_t)c * Np + j], acc);
+        nv[q] = 1.5 * V[e] - 0.5 * acc;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int e = threadIdx.x + q * SM_T;
+      if (e < Np * Np) V[e] = nv[q];
+    }
+    __syncthreads();
+  }
+  // T = A0 V (column c of T = sum_j column j of A0 times V(j, c)), then A = T
+  for (int e = threadIdx.x; e < Np * rows; e += SM_T) {
+    const int c = e / rows, i = e % rows;
+    double acc = 0.0;
+    for (int j = 0; j < Np; ++j) acc = fma(A[(size_t)j * rows + i], V[(size_t)c * Np + j], acc);
+    T[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < Np * rows; e += SM_T) A[e] = T[e];
+  __syncthreads();
+  return jacobi_osvd<double>(A, rows, Np, V, JAC_MAX_SWEEPS);
 }
 
 // Column norms and the descending order (ties by index).
@@ -176,7 +245,7 @@ polar_kernel(const double* __restrict__ Mg, int k, double* R, double* D, double 
     A[e] = s;
   }
   __syncthreads();
-  int sw = jacobi_osvd(A, k, Np, V);
+  int sw = jacobi_osvd<double>(A, k, Np, V, JAC_MAX_SWEEPS);
   for (int c = threadIdx.x; c < Np; c += SM_T) {
     double s = 0.0;
     for (int i = 0; i < k; ++i) s = fma(A[(size_t)c * k + i], A[(size_t)c * k + i], s);
@@ -321,7 +390,7 @@ eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, int*
   }
   set_identity(V, Np);
   __syncthreads();
-  int sw = jacobi_osvd(A, k, Np, V);
+  int sw = jacobi_osvd<double>(A, k, Np, V, JAC_MAX_SWEEPS);
   sort_desc(A, k, Np, nrm, ord);
   const double lmax = nrm[ord[0]];
   for (int e = threadIdx.x; e < k * k; e += SM_T) {
@@ -360,14 +429,16 @@ rr_svd_kernel(const double* __restrict__ P, int k2, int k1, double* sigma, doubl
   double* A = smd;                  // Np columns x k1 rows
   double* V = A + (size_t)Np * k1;  // Np x Np
   double* nrm = V + (size_t)Np * Np;
+  double* T = nrm + Np;                                        // Np x k1 (k1 <= Np)
   int* ord = reinterpret_cast<int*>(nrm + Np + (size_t)Np * Np);
+  float* A32 = reinterpret_cast<float*>(ord + Np);            // Np x k1
+  float* V32 = A32 + (size_t)Np * k1;                          // Np x Np
   for (int e = threadIdx.x; e < Np * k1; e += SM_T) {
     int c = e / k1, i = e % k1;
     A[e] = c < k2 ? P[(size_t)c * k1 + i] : 0.0;
   }
-  set_identity(V, Np);
   __syncthreads();
-  int sw = jacobi_osvd(A, k1, Np, V);
+  int sw = jacobi_osvd_mixed(A, k1, Np, V, A32, V32, T);
   sort_desc(A, k1, Np, nrm, ord);
   for (int j = threadIdx.x; j < k2; j += SM_T) sigma[j] = nrm[ord[j]];
   for (int e = threadIdx.x; e < k1 * k2; e += SM_T) {
@@ -386,7 +457,8 @@ void launch_rr_svd(const double* P, int k2, int k1, double* sigma, double* Ut, d
                    int* err, cudaStream_t s) {
   note_launch(1);
   int Np = k2 + (k2 & 1);
-  size_t smem = small_smem(k1 > Np ? k1 : Np, Np);
+  // FP64 panels plus the FP32 copies of the mixed-precision Jacobi
+  size_t smem = small_smem(k1 > Np ? k1 : Np, Np) + sizeof(float) * ((size_t)Np * k1 + (size_t)Np * Np);
   cudaFuncSetAttribute(rr_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   rr_svd_kernel<<<1, SM_T, smem, s>>>(P, k2, k1, sigma, Ut, Wt, err);
 }
