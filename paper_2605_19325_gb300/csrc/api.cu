@@ -585,10 +585,25 @@ HalfArgs ctx_half_args(enmf_ctx* ctx, int which, void* F, const void* A, const d
   return a;
 }
 
+static int64_t tc_units(enmf_ctx* ctx, int mode);
+
+// The half steps of enmf_iterate: in the tensor-core form, A comes from a
+// main sweep pass run without fix-up, so the half step assembles its cut
+// tiles (HalfArgs::cut_part).
 static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const double* G, int64_t rows,
                      const enmf_iter_opts& o, bool dot, double* G_out, const double* Gu,
                      double* trace, int trace_idx) {
-  const HalfArgs a = ctx_half_args(ctx, which, F, A, G, rows, o, dot, G_out, Gu, trace, trace_idx);
+  HalfArgs a = ctx_half_args(ctx, which, F, A, G, rows, o, dot, G_out, Gu, trace, trace_idx);
+  if (ctx->tc) {
+    const int mode = which;   // U-half reads X V (mode 0), V-half X^T U (mode 1)
+    const int64_t red = mode == 0 ? ctx->p.n : ctx->p.m;
+    a.cut_part = ctx->tcpart;
+    a.cut_corr = ctx->xl ? (mode == 0 ? ctx->cv : ctx->cu) : nullptr;
+    a.cut_W = tc_units(ctx, mode);
+    a.cut_G = tc_group_grid(a.cut_W, ctx->num_sms);
+    a.cut_nkb = (int)((red + (mode == 0 ? TC_KB_XV : TC_KB_XT) - 1) / (mode == 0 ? TC_KB_XV : TC_KB_XT));
+    a.cut_rp = ctx->rp;
+  }
   launch_half_step(a, which == 0 ? ctx->grid_u : ctx->grid_v, ctx->stream);
 }
 
@@ -638,8 +653,10 @@ static void prof_mark(enmf_ctx* ctx, bool rec) {
 
 // split = false: the BF16 pair of the factor is already current (written by
 // the half step that produced the factor).
+// fixup = false: the main pass leaves its cut tiles to the consumer (the
+// half step of enmf_iterate, through ctx_half_args(..., cut = true)).
 static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int corr,
-                     bool rec = false, bool split = true) {
+                     bool rec = false, bool split = true, bool fixup = true) {
   const enmf_problem& p = ctx->p;
   cudaStream_t s = ctx->stream;
   const int r = p.r;
@@ -661,12 +678,12 @@ static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int
                                (corr >= 1 && ctx->xl) ? ctx->cv : nullptr);
   prof_mark(ctx, rec);
   launch_tc_group(0, ctx->rp, d, 1, tc_units(ctx, 0), ctx->tcpart, ctx->tccount, ctx->num_sms,
-                  ctx->err, s);
+                  ctx->err, s, fixup ? 1 : 0);
   prof_mark(ctx, rec);
 }
 
 static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, int corr,
-                      bool rec = false, bool split = true) {
+                      bool rec = false, bool split = true, bool fixup = true) {
   const enmf_problem& p = ctx->p;
   cudaStream_t s = ctx->stream;
   const int r = p.r;
@@ -688,7 +705,7 @@ static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, in
                                (corr >= 1 && ctx->xl) ? ctx->cu : nullptr);
   prof_mark(ctx, rec);
   launch_tc_group(1, ctx->rp, d, 1, tc_units(ctx, 1), ctx->tcpart, ctx->tccount, ctx->num_sms,
-                  ctx->err, s);
+                  ctx->err, s, fixup ? 1 : 0);
   prof_mark(ctx, rec);
 }
 
@@ -813,7 +830,6 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
   if (o.n_iter < 0 || o.pbcd_max_iter < 0 || !(o.eps >= 0) || o.n_shift < 1) return ENMF_EINVAL;
   if (o.correct_every < 1) o.correct_every = 10;
   const enmf_problem& p = ctx->p;
-  const int k = p.r, fdt = ctx->fdt, xdt = ctx->xdt;
   const int64_t m = p.m, n = p.n;
   cudaStream_t s = ctx->stream;
   enmf_status rc = check_staged(ctx, X);
@@ -833,9 +849,9 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
       const int corr = (it % o.correct_every == 0) ? 2 : 1;
       const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
                        ctx->npev + 4 <= 2 * PROF_PAIRS;
-      sweep_xv(ctx, X, V, ctx->M0, corr, rec, false);
+      sweep_xv(ctx, X, V, ctx->M0, corr, rec, false, false);
       run_half(ctx, 0, U, ctx->M0, ctx->Gv, m, o, false, ctx->Gu, nullptr, nullptr, 0);
-      sweep_xtu(ctx, X, U, ctx->N0, corr, rec, false);
+      sweep_xtu(ctx, X, U, ctx->N0, corr, rec, false, false);
       run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu, o.trace, it);
     }
   };

@@ -90,6 +90,46 @@ __device__ __forceinline__ void write_split(const HalfArgs& a, int64_t i, bool l
   }
 }
 
+// Row i of A (X V or X^T U).  When the sweep left its cut tiles to the
+// consumer (a.cut_part), a row of a cut tile is the sum of the contributing
+// CTAs' slots in CTA order plus the X_lo term -- the order of the sweep's
+// own fix-up, so the values are the same bits.  The contributors of the
+// tile's units [gs, ge) under the stream-K split sk(c) = floor(c W / G) are
+// c_lo = floor(((gs + 1) G - 1) / W) .. c_hi = floor((ge G - 1) / W).
+template <typename TF, int E>
+__device__ __forceinline__ void load_a_row(const HalfArgs& a, const TF* A, int64_t i, bool live,
+                                           int k, int sub, TF (&v)[E]) {
+  if constexpr (sizeof(TF) == 4) {
+    if (a.cut_part && live) {
+      const int64_t W = a.cut_W, G = a.cut_G;
+      const int64_t tile = i / 128;
+      const int64_t gs = tile * a.cut_nkb, ge = gs + a.cut_nkb;
+      const int64_t c_lo = ((gs + 1) * G - 1) / W, c_hi = (ge * G - 1) / W;
+      if (c_lo != c_hi) {
+        float acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        for (int64_t q = c_lo; q <= c_hi; ++q) {
+          const int slot = (q * W) / G >= gs ? 0 : 1;
+          const float* src = a.cut_part + (q * 2 + slot) * 128 * a.cut_rp + (i % 128) * k;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int l = sub + LPR * e;
+            if (l < k) acc[e] += src[l];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int l = sub + LPR * e;
+          v[e] = l < k ? (a.cut_corr ? acc[e] + a.cut_corr[i * k + l] : acc[e]) : TF(0);
+        }
+        return;
+      }
+    }
+  }
+  load_row(A, i, live, k, sub, v);
+}
+
 template <typename TF, int KP>
 __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, const int nb,
                                            const int lock, TF* Gs, TF* us, TF* ginv,
@@ -155,7 +195,7 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
       const bool live = i < rows;
       TF u[E], av[E], q[E];
       load_row(F, i, live, k, sub, u);
-      load_row(A, i, live, k, sub, av);
+      load_a_row(a, A, i, live, k, sub, av);
       row_times<TF, KP>(Gs, u, k, sub, q);
 #pragma unroll
       for (int e = 0; e < E; ++e) q[e] = av[e] - q[e];
@@ -195,7 +235,7 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
       const bool live = i < rows;
       TF u[E], av[E], g[E];
       load_row(F, i, live, k, sub, u);
-      load_row(A, i, live, k, sub, av);
+      load_a_row(a, A, i, live, k, sub, av);
       unsigned bits = 0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -226,7 +266,7 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
         TF u[E], av[E], g[E], tg[E];
         load_row(F, i, live, k, sub, u);
         load_row(gb, i, live, k, sub, g);
-        load_row(A, i, live, k, sub, av);
+        load_a_row(a, A, i, live, k, sub, av);
         const unsigned bits = live ? mk[i * 8 + sub] : 0u;
         // d_i = ||g_i||^2 / (g_i G g_i^T)   (Eq. 10; App. B)
         row_times<TF, KP>(Gs, g, k, sub, tg);
@@ -280,7 +320,7 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
           if (sub + LPR * e < k && !((bits >> e) & 1u)) neg = 1;
         if (a.dot_part) {
           TF av[E];
-          load_row(A, i, live, k, sub, av);
+          load_a_row(a, A, i, live, k, sub, av);
 #pragma unroll
           for (int e = 0; e < E; ++e) dotacc = fma((double)av[e], (double)u[e], dotacc);
         }

@@ -120,6 +120,15 @@ struct HalfArgs {
   // the grid barrier of the launch (&st->bar for one problem; one shared
   // barrier for every problem of a grouped launch)
   GridBarrier* bar;
+  // A came from a one-problem tensor-core sweep run without fix-up: rows of
+  // tiles cut by its stream-K ranges are the sum, in CTA order, of the
+  // contributors' partial slots (cut_part: [G][2][128][cut_rp] floats, each
+  // slot 128 rows x k flat) plus cut_corr; other rows are in A as is.
+  // cut_part null: A is complete.
+  const float* cut_part;
+  const float* cut_corr;
+  int64_t cut_W, cut_G;   // the sweep's work units and grid
+  int cut_nkb, cut_rp;    // k-blocks per tile, slot row stride
 };
 // hstep.cu: one cooperative launch per half step; grid <= half_step_grid().
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);
@@ -211,8 +220,10 @@ void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r,
 // Grouped sweep over np problems (descriptors in device memory, in work
 // order), W units in all; part needs grid x 2 x 128 x rp floats, counters one
 // int per tile of all problems (zero between launches).
+// fixup = 0 (one problem only): tiles cut by the stream-K ranges are left as
+// partial slots for the consumer (see CutTiles).
 void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
-                     int* counters, int num_sms, int* err, cudaStream_t s);
+                     int* counters, int num_sms, int* err, cudaStream_t s, int fixup = 1);
 int tc_group_grid(int64_t W, int num_sms);
 // 2D BF16 tensor map (CUtensorMap, 128 bytes at `map`) over a row-major
 // (rows x cols, ld) array, box box_cols x box_rows, 128-byte swizzle.

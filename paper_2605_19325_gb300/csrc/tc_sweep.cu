@@ -185,7 +185,7 @@ struct ProbView {
 template <int MODE, int RP>
 __global__ void __launch_bounds__(THREADS, 1)
 sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stages,
-                float* __restrict__ part, int* __restrict__ counters, int* err) {
+                float* __restrict__ part, int* __restrict__ counters, int fixup, int* err) {
   constexpr int KB = MODE == 0 ? KB_XV : KB_XT;
   constexpr uint32_t A_BYTES = TILE * KB * 2;                 // 16 KB or 32 KB
   constexpr uint32_t B_BYTES = RP * KB * 2;                   // one of hi / lo
@@ -432,10 +432,12 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
           }
         }
       }
-      if (!whole) {
+      if (!whole && fixup) {
         // A tile cut by range boundaries: the last of its CTAs to get here
         // sums every contributor's slot, in CTA order (so the result does not
         // depend on which CTA is last), adds corr and writes the tile.
+        // (Without fixup the slots are left for the consumer, which sums
+        // them in the same order: tc_cut_row below.)
         __threadfence();
         asm volatile("bar.sync 1, 128;" ::: "memory");
         int64_t c_lo = blockIdx.x, c_hi = blockIdx.x;
@@ -675,21 +677,21 @@ void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r,
 
 template <int MODE, int RP>
 static void launch_tc(const SweepProb* probs, int np, int64_t W, float* part, int* counters,
-                      int grid, int* err, cudaStream_t s) {
+                      int grid, int fixup, int* err, cudaStream_t s) {
   const int stages = tc_stages(MODE, RP);
   const size_t smem = tc_smem(MODE, RP, stages);
   cudaFuncSetAttribute(tc::sweep_tc_kernel<MODE, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   tc::sweep_tc_kernel<MODE, RP><<<grid, tc::THREADS, smem, s>>>(probs, np, W, stages, part,
-                                                                 counters, err);
+                                                                 counters, fixup, err);
 }
 
 void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
-                     int* counters, int num_sms, int* err, cudaStream_t s) {
+                     int* counters, int num_sms, int* err, cudaStream_t s, int fixup) {
   if (np < 1 || W < 1) return;
   const int grid = tc_group_grid(W, num_sms);
   note_launch(1);
-#define TCL(M, P) launch_tc<M, P>(probs, np, W, part, counters, grid, err, s)
+#define TCL(M, P) launch_tc<M, P>(probs, np, W, part, counters, grid, fixup, err, s)
   if (mode == 0) {
     if (rp == 16) TCL(0, 16); else if (rp == 32) TCL(0, 32); else if (rp == 48) TCL(0, 48); else TCL(0, 64);
   } else {
