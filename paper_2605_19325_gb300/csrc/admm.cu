@@ -6,10 +6,10 @@
 //                      the block's share of M = W^T (z + y / rho);
 //   M    (all blocks)  FP64 block partials, grid barrier, fixed-order sum;
 //   R    (block 0)     R = polar(M), the orthogonal Procrustes solution
-//                      (Sec. 4.1.2), by Newton-Schulz X <- X (3 I - X^T X) / 2
-//                      in FP32 from M / ||M||_F until ||X^T X - I||_F^2 < 1e-10
-//                      and one step more, then one step with X^T X in FP64:
-//                      E = X^T X - I is of the order of FP32 rounding, so
+//                      (Sec. 4.1.2), by scaled Newton-Schulz in FP32 from
+//                      M / ||M||_F until ||X^T X - I||_F^2 < 1e-10 and one
+//                      unscaled step more, then one step with X^T X - I summed
+//                      in double-FP32: E is of the order of FP32 rounding, so
 //                      R = X - X E / 2 needs X E only in FP32;
 //   stop               ||R_new - R||_F <= tol sqrt(r), or max_iter steps.
 // Rows use eight lanes per row with the entries in registers (lanes.cuh);
@@ -25,159 +25,216 @@ using namespace lanes;
 constexpr int AT = 256;          // threads per block
 constexpr int ARPB = AT / LPR;   // rows per block per pass
 
-// Dynamic shared memory (floats): Rs KP^2 | ws, bs 32 KP each | X, Y, P KP^2 each.
+// Dynamic shared memory (floats): Rs KP^2 | ws, bs 32 KP each | X, X^T, P
+// KP x PLD each (rows padded by 4 floats: 16-byte aligned, and the rows that
+// eight consecutive lanes read as float4 fall in distinct banks).
+template <int KP>
+constexpr int polar_ld() { return KP + 4; }
+
 template <int KP>
 constexpr size_t admm_smem() {
-  return sizeof(float) * (4 * (size_t)KP * KP + 2 * (size_t)ARPB * KP);
+  return sizeof(float) * ((size_t)KP * KP + 2 * (size_t)ARPB * KP + 3 * (size_t)KP * polar_ld<KP>());
 }
 
-// R = polar(M) on one block of AT threads (see the file comment).  X, Y, P:
-// KP x KP shared buffers.  Thread (bi, bj) = (t / 16, t % 16) owns the
-// S x S sub-block of every product.
+// acc[s1][s2] += sum_l A[ia_s1][l] B[jb_s2][l] over l < KP, with rows
+// ia_s = bi + 16 s of A and jb_s = bj + 16 s of B (row stride LD), read as
+// float4 along l.
+template <int KP, int LD>
+__device__ __forceinline__ void rows_dot(const float* __restrict__ A, const float* __restrict__ Bm,
+                                         int bi, int bj, float (&acc)[KP / 16][KP / 16]) {
+  constexpr int S = KP / 16;
+#pragma unroll
+  for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = 0.f;
+#pragma unroll 4
+  for (int l = 0; l < KP; l += 4) {
+    float4 x[S], y[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      x[s] = *reinterpret_cast<const float4*>(A + (bi + 16 * s) * LD + l);
+      y[s] = *reinterpret_cast<const float4*>(Bm + (bj + 16 * s) * LD + l);
+    }
+#pragma unroll
+    for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) {
+        float c = acc[s1][s2];
+        c = fmaf(x[s1].x, y[s2].x, c);
+        c = fmaf(x[s1].y, y[s2].y, c);
+        c = fmaf(x[s1].z, y[s2].z, c);
+        c = fmaf(x[s1].w, y[s2].w, c);
+        acc[s1][s2] = c;
+      }
+  }
+}
+
+// Power iteration on I - P (P = X_0^T X_0, symmetric, eigenvalues in [0, 1])
+// by warp 0, from the vector v of the previous call: the Rayleigh quotient mu
+// gives sigma_min(X_0)^2 ~ 1 - mu (from above).  v: KP floats, zero past k.
+template <int KP, int LD>
+__device__ float sigma_min_estimate(const float* __restrict__ P, float* v, int k, int iters) {
+  constexpr int E = (KP + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  float w[E], mu = 0.f;
+  for (int t = 0; t <= iters; ++t) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) w[e] = lane + 32 * e < KP ? v[lane + 32 * e] : 0.f;
+    for (int j = 0; j < k; ++j) {
+      const float vj = v[j];
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (lane + 32 * e < KP) w[e] = fmaf(-P[j * LD + lane + 32 * e], vj, w[e]);
+    }
+    float nn = 0.f, vw = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (lane + 32 * e < KP) {
+        nn = fmaf(w[e], w[e], nn);
+        vw = fmaf(v[lane + 32 * e], w[e], vw);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nn += __shfl_xor_sync(FULL, nn, o);
+      vw += __shfl_xor_sync(FULL, vw, o);
+    }
+    mu = vw;                                  // v is a unit vector
+    if (t == iters || !(nn > 0.f)) break;
+    const float inv = rsqrtf(nn);
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (lane + 32 * e < KP) v[lane + 32 * e] = w[e] * inv;
+    __syncwarp();
+  }
+  return sqrtf(fmaxf(1.f - mu, 0.f));
+}
+
+// R = polar(M) on one block of AT threads (see the file comment).  X, XT, P:
+// KP x PLD shared buffers; v: KP floats kept from step to step.  Thread
+// (bi, bj) = (t / 16, t % 16) owns the entries (bi + 16 s1, bj + 16 s2).
+//
+// The iteration is Newton-Schulz with the scaling of a lower bound l of the
+// singular values (X <- alpha X (3 I - alpha^2 X^T X) / 2, alpha^2 =
+// 3 / (1 + l + l^2), which maps [l, 1] into [l', 1] with l' = alpha l (3 -
+// alpha^2 l^2) / 2): for every singular value in (0, 1] it stays in (0, 1]
+// and grows at least as fast as the unscaled step, so the limit is the same
+// polar factor whatever l is; l only sets the speed.  l starts from a power
+// iteration on I - X_0^T X_0 and is raised to sqrt(1 - ||X^T X - I||_F) once
+// that bound holds; the step after convergence is unscaled.
 template <int KP>
 __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, double tol,
-                            DevState* st, int* err, float* X, float* Y, float* P, double* sh) {
-  constexpr int S = KP / 16;
+                            DevState* st, int* err, float* X, float* XT, float* P, float* v,
+                            bool first, double* sh) {
+  constexpr int S = KP / 16, LD = polar_ld<KP>();
   const int t = threadIdx.x, bi = t / 16, bj = t % 16;
   double nf = 0.0;
   for (int e = t; e < k * k; e += AT) {
-    const double v = __ldcg(&Mg[e]);
-    nf = fma(v, v, nf);
+    const double x = __ldcg(&Mg[e]);
+    nf = fma(x, x, nf);
   }
   nf = sqrt(block_sum256(nf, sh));
   const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
   for (int e = t; e < KP * KP; e += AT) {
     const int i = e / KP, j = e % KP;
-    X[e] = (i < k && j < k) ? (float)(__ldcg(&Mg[i * k + j]) * inv) : 0.f;
+    const float x = (i < k && j < k) ? (float)(__ldcg(&Mg[i * k + j]) * inv) : 0.f;
+    X[i * LD + j] = x;
+    XT[j * LD + i] = x;
   }
+  if (first)
+    for (int i = t; i < KP; i += AT) v[i] = i < k ? 1.f + 0.25f * (float)(i % 5) : 0.f;
   __syncthreads();
+  float* lsh = reinterpret_cast<float*>(sh) + 8;   // past block_sum256f's 8 floats
+  float lk = 0.f;
   int it = 0;
   for (; it < 100; ++it) {
-    // P = X^T X and ||P - I||^2 over the k x k block
-    float acc[S][S];
-#pragma unroll
-    for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = 0.f;
-#pragma unroll
-    for (int l = 0; l < KP; ++l) {
-      float xa[S], xb[S];
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        xa[s] = X[l * KP + bi * S + s];
-        xb[s] = X[l * KP + bj * S + s];
-      }
-#pragma unroll
-      for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-        for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = fmaf(xa[s1], xb[s2], acc[s1][s2]);
-    }
+    float acc[S][S], xo[S][S];
+    rows_dot<KP, LD>(XT, XT, bi, bj, acc);      // P = X^T X
     float dl = 0.f;
 #pragma unroll
     for (int s1 = 0; s1 < S; ++s1)
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) {
-        const int i = bi * S + s1, j = bj * S + s2;
-        P[i * KP + j] = acc[s1][s2];
+        const int i = bi + 16 * s1, j = bj + 16 * s2;
+        P[i * LD + j] = acc[s1][s2];
+        xo[s1][s2] = X[i * LD + j];
         if (i < k && j < k) {
           const float x = acc[s1][s2] - (i == j ? 1.f : 0.f);
           dl = fmaf(x, x, dl);
         }
       }
-    const double dd = block_sum256((double)dl, sh);   // also orders P before its use
-    // Y = 1.5 X - 0.5 X P
-#pragma unroll
-    for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = 0.f;
-#pragma unroll
-    for (int l = 0; l < KP; ++l) {
-      float xr[S], pc[S];
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        xr[s] = X[(bi * S + s) * KP + l];
-        pc[s] = P[l * KP + bj * S + s];
+    // ||P - I||_F^2 in FP32 (its threshold 1e-10 is far above FP32 rounding);
+    // the barriers inside also order P before its use
+    const float dd = block_sum256f(dl, reinterpret_cast<float*>(sh));
+    if (it == 0) {
+      if (t < 32) {
+        float l0 = sigma_min_estimate<KP, LD>(P, v, k, first ? 12 : 3);
+        if (t == 0) lsh[0] = fminf(fmaxf(0.9f * l0, 1e-4f), 1.f);
       }
-#pragma unroll
-      for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-        for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = fmaf(xr[s1], pc[s2], acc[s1][s2]);
+      __syncthreads();
+      lk = lsh[0];
     }
+    const bool conv = dd < 1e-10f;
+    if (dd < 1.f) lk = fmaxf(lk, sqrtf(fmaxf(1.f - sqrtf(dd), 0.f)));
+    const float al = conv ? 1.f : sqrtf(3.f / (1.f + lk + lk * lk));
+    const float ca = 1.5f * al, cb = 0.5f * al * al * al;
+    lk = 0.5f * al * lk * (3.f - al * al * lk * lk);
+    rows_dot<KP, LD>(X, P, bi, bj, acc);        // X P  (P symmetric)
+    __syncthreads();                            // every read of X, X^T, P done
 #pragma unroll
     for (int s1 = 0; s1 < S; ++s1)
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) {
-        const int e = (bi * S + s1) * KP + bj * S + s2;
-        Y[e] = 1.5f * X[e] - 0.5f * acc[s1][s2];
+        const int i = bi + 16 * s1, j = bj + 16 * s2;
+        const float y = ca * xo[s1][s2] - cb * acc[s1][s2];
+        X[i * LD + j] = y;
+        XT[j * LD + i] = y;
       }
     __syncthreads();
-    float* tmp = X;
-    X = Y;
-    Y = tmp;
-    if (dd < 1e-10) {
+    if (conv) {
       ++it;
       break;
     }
   }
-  // E = X^T X - I with FP64 sums of the exact products (symmetric: the
-  // sub-blocks with bi <= bj, mirrored), stored in FP32 in P
+  // E = X^T X - I to about 2^-44: each product split exactly (x y = p + e by
+  // one FMA) and the p summed with an exact two-sum, the errors in FP32 (the
+  // sub-blocks with bi <= bj, mirrored); E itself is of the order of FP32
+  // rounding, so R = X - X E / 2 needs X E only in FP32
   if (bi <= bj) {
-    double acc[S][S];
-#pragma unroll
-    for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = 0.0;
-#pragma unroll
-    for (int l = 0; l < KP; ++l) {
-      double xa[S], xb[S];
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        xa[s] = (double)X[l * KP + bi * S + s];
-        xb[s] = (double)X[l * KP + bj * S + s];
-      }
-#pragma unroll
-      for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-        for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = fma(xa[s1], xb[s2], acc[s1][s2]);
-    }
 #pragma unroll
     for (int s1 = 0; s1 < S; ++s1)
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) {
-        const int i = bi * S + s1, j = bj * S + s2;
-        const float e = (float)(acc[s1][s2] - (i == j && i < k ? 1.0 : 0.0));
-        P[i * KP + j] = e;
-        P[j * KP + i] = e;
+        const int i = bi + 16 * s1, j = bj + 16 * s2;
+        const float* xi = XT + i * LD;
+        const float* xj = XT + j * LD;
+        float hi = 0.f, lo = 0.f;
+        for (int l = 0; l < KP; ++l) {
+          const float p = __fmul_rn(xi[l], xj[l]);
+          const float pe = fmaf(xi[l], xj[l], -p);
+          const float sm = __fadd_rn(hi, p);
+          const float bv = __fsub_rn(sm, hi);
+          const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, bv)), __fsub_rn(p, bv));
+          hi = sm;
+          lo = __fadd_rn(lo, __fadd_rn(er, pe));
+        }
+        const float e = __fadd_rn(__fsub_rn(hi, (i == j && i < k) ? 1.f : 0.f), lo);
+        P[i * LD + j] = e;
+        P[j * LD + i] = e;
       }
   }
   __syncthreads();
-  // R_new = X - X E / 2, ||R_new - R||^2
+  // R_new = X - X E / 2 (E symmetric), ||R_new - R||^2
   float acc[S][S];
-#pragma unroll
-  for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-    for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = 0.f;
-#pragma unroll
-  for (int l = 0; l < KP; ++l) {
-    float xr[S], pc[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      xr[s] = X[(bi * S + s) * KP + l];
-      pc[s] = P[l * KP + bj * S + s];
-    }
-#pragma unroll
-    for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = fmaf(xr[s1], pc[s2], acc[s1][s2]);
-  }
+  rows_dot<KP, LD>(X, P, bi, bj, acc);
   double d2 = 0.0;
 #pragma unroll
   for (int s1 = 0; s1 < S; ++s1)
 #pragma unroll
     for (int s2 = 0; s2 < S; ++s2) {
-      const int i = bi * S + s1, j = bj * S + s2;
+      const int i = bi + 16 * s1, j = bj + 16 * s2;
       if (i < k && j < k) {
-        const double rn = (double)X[i * KP + j] - 0.5 * (double)acc[s1][s2];
+        const double rn = (double)X[i * LD + j] - 0.5 * (double)acc[s1][s2];
         const double x = rn - R[i * k + j];
         d2 = fma(x, x, d2);
         R[i * k + j] = rn;
@@ -219,9 +276,10 @@ __global__ void __launch_bounds__(AT) admm_kernel(AdmmArgs a) {
   float* ws = Rs + KP * KP;
   float* bs = ws + ARPB * KP;
   float* X = bs + ARPB * KP;
-  float* Yp = X + KP * KP;
-  float* P = Yp + KP * KP;
+  float* XT = X + KP * polar_ld<KP>();
+  float* P = XT + KP * polar_ld<KP>();
   __shared__ double sh[AT];
+  __shared__ float pv[KP];
 
   const int k = a.k, kk = k * k;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -288,7 +346,8 @@ __global__ void __launch_bounds__(AT) admm_kernel(AdmmArgs a) {
     grid_sync(&st->bar, a.err);
     sum_block_partials<AT>(a.part, (int)gridDim.x, kk, a.M);
     grid_sync(&st->bar, a.err);
-    if (blockIdx.x == 0) polar_block<KP>(a.M, k, a.R, a.tol, st, a.err, X, Yp, P, sh);
+    if (blockIdx.x == 0)
+      polar_block<KP>(a.M, k, a.R, a.tol, st, a.err, X, XT, P, pv, step == 0, sh);
     grid_sync(&st->bar, a.err);
   }
 }

@@ -141,6 +141,18 @@ __device__ __forceinline__ double block_sum256(double v, double* sh) {
   return ((sh[0] + sh[1]) + (sh[2] + sh[3])) + ((sh[4] + sh[5]) + (sh[6] + sh[7]));
 }
 
+// The same in FP32 (for sums whose FP32 rounding is far below what they are
+// compared with -- the FP64 adds of all 256 threads cost more than the data
+// warrants at this GPU's FP64 rate).  `sh` needs 8 floats.
+__device__ __forceinline__ float block_sum256f(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  return ((sh[0] + sh[1]) + (sh[2] + sh[3])) + ((sh[4] + sh[5]) + (sh[6] + sh[7]));
+}
+
 inline int rank_pad16(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 48 ? 48 : 64)); }
 
 }  // namespace lanes
