@@ -91,6 +91,9 @@ class Server:
         self.used = 0
         self.results = []
         self.steps = 0
+        # host wall time spent admitting (SVD start + rotation), stepping the
+        # batches and retiring finished requests
+        self.time_s = {"admit": 0.0, "step": 0.0, "retire": 0.0}
 
     # ------------------------------------------------------------- requests
     def submit(self, req: Request):
@@ -170,13 +173,16 @@ class Server:
         self.t0 = time.perf_counter()
         while self.pending or self.active:
             now = time.perf_counter() - self.t0
+            t = time.perf_counter()
             self._admit(now)
+            self.time_s["admit"] += time.perf_counter() - t
             if not self.active:
                 if self.pending:
                     wait = self.pending[0].arrival_s - (time.perf_counter() - self.t0)
                     if wait > 0:
                         time.sleep(min(wait, 0.01))
                 continue
+            t = time.perf_counter()
             for rp, b in self.batches.items():
                 if B.enmf_batch_size(b) == 0:
                     continue
@@ -185,7 +191,11 @@ class Server:
                     self.tuned.add(rp)
                 B.enmf_batch_step(b, self.chunk)
             self.steps += 1
-            self._retire(time.perf_counter() - self.t0)
+            t2 = time.perf_counter()
+            self._retire(t2 - self.t0)
+            t3 = time.perf_counter()
+            self.time_s["step"] += t2 - t
+            self.time_s["retire"] += t3 - t2
         return self.results
 
     def close(self):
