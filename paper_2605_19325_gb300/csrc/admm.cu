@@ -7,7 +7,7 @@
 //   M    (all blocks)  FP64 block partials, grid barrier, fixed-order sum;
 //   R    (block 0)     R = polar(M), the orthogonal Procrustes solution
 //                      (Sec. 4.1.2), by scaled Newton-Schulz in FP32 from
-//                      M / ||M||_F until ||X^T X - I||_F^2 < 1e-10 and one
+//                      M / ||M||_F until max |X^T X - I| < 1e-5 and one
 //                      unscaled step more, then one step with X^T X - I summed
 //                      in double-FP32: E is of the order of FP32 rounding, so
 //                      R = X - X E / 2 needs X E only in FP32;
@@ -25,15 +25,24 @@ using namespace lanes;
 constexpr int AT = 256;          // threads per block
 constexpr int ARPB = AT / LPR;   // rows per block per pass
 
-// Dynamic shared memory (floats): Rs KP^2 | ws, bs 32 KP each | X, X^T, P
-// KP x PLD each (rows padded by 4 floats: 16-byte aligned, and the rows that
-// eight consecutive lanes read as float4 fall in distinct banks).
+// Dynamic shared memory (floats): region A | X, X^T, P (KP x PLD each, rows
+// padded by 4 floats: 16-byte aligned, and the rows that eight consecutive
+// lanes read as float4 fall in distinct banks).  Region A holds Rs (KP^2) and
+// ws, bs (32 KP each) in the row phase and the second X, X^T pair of the
+// polar iteration on block 0.
 template <int KP>
 constexpr int polar_ld() { return KP + 4; }
 
 template <int KP>
+constexpr size_t admm_region_a() {
+  const size_t rows = (size_t)KP * KP + 2 * (size_t)ARPB * KP;
+  const size_t pol = 2 * (size_t)KP * polar_ld<KP>();
+  return rows > pol ? rows : pol;
+}
+
+template <int KP>
 constexpr size_t admm_smem() {
-  return sizeof(float) * ((size_t)KP * KP + 2 * (size_t)ARPB * KP + 3 * (size_t)KP * polar_ld<KP>());
+  return sizeof(float) * (admm_region_a<KP>() + 3 * (size_t)KP * polar_ld<KP>());
 }
 
 // acc[s1][s2] += sum_l A[ia_s1][l] B[jb_s2][l] over l < KP, with rows
@@ -47,7 +56,8 @@ __device__ __forceinline__ void rows_dot(const float* __restrict__ A, const floa
   for (int s1 = 0; s1 < S; ++s1)
 #pragma unroll
     for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = 0.f;
-#pragma unroll 4
+  constexpr int UR = S <= 2 ? 4 : 1;
+#pragma unroll UR
   for (int l = 0; l < KP; l += 4) {
     float4 x[S], y[S];
 #pragma unroll
@@ -110,9 +120,32 @@ __device__ float sigma_min_estimate(const float* __restrict__ P, float* v, int k
   return sqrtf(fmaxf(1.f - mu, 0.f));
 }
 
-// R = polar(M) on one block of AT threads (see the file comment).  X, XT, P:
-// KP x PLD shared buffers; v: KP floats kept from step to step.  Thread
-// (bi, bj) = (t / 16, t % 16) owns the entries (bi + 16 s1, bj + 16 s2).
+// Two-sum of the running pair (hi, lo) and the exact product x y: hi + lo +
+// x y = hi' + lo' up to the rounding of lo (the products are split by one
+// FMA, the sum by Knuth's two-sum).  Explicit _rn operations: nothing may be
+// contracted into an FMA.
+__device__ __forceinline__ void dfloat_fma(float x, float y, float& hi, float& lo) {
+  const float p = __fmul_rn(x, y);
+  const float pe = fmaf(x, y, -p);
+  const float sm = __fadd_rn(hi, p);
+  const float bv = __fsub_rn(sm, hi);
+  const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, bv)), __fsub_rn(p, bv));
+  hi = sm;
+  lo = __fadd_rn(lo, __fadd_rn(er, pe));
+}
+
+__device__ __forceinline__ void dfloat_add(float& hi, float& lo, float h2, float l2) {
+  const float sm = __fadd_rn(hi, h2);
+  const float bv = __fsub_rn(sm, hi);
+  const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, bv)), __fsub_rn(h2, bv));
+  hi = sm;
+  lo = __fadd_rn(__fadd_rn(lo, l2), er);
+}
+
+// R = polar(M) on one block of AT threads (see the file comment).  X, XT and
+// Y, YT: two KP x PLD buffer pairs (the iterate and the next one); P: KP x
+// PLD; v: KP floats kept from step to step.  Thread (bi, bj) = (t / 16,
+// t % 16) owns the entries (bi + 16 s1, bj + 16 s2).
 //
 // The iteration is Newton-Schulz with the scaling of a lower bound l of the
 // singular values (X <- alpha X (3 I - alpha^2 X^T X) / 2, alpha^2 =
@@ -120,26 +153,34 @@ __device__ float sigma_min_estimate(const float* __restrict__ P, float* v, int k
 // alpha^2 l^2) / 2): for every singular value in (0, 1] it stays in (0, 1]
 // and grows at least as fast as the unscaled step, so the limit is the same
 // polar factor whatever l is; l only sets the speed.  l starts from a power
-// iteration on I - X_0^T X_0 and is raised to sqrt(1 - ||X^T X - I||_F) once
-// that bound holds; the step after convergence is unscaled.
+// iteration on I - X_0^T X_0.  The loop ends after the unscaled step that
+// follows max |X^T X - I| < 1e-5 (the next step squares that deviation).
 template <int KP>
 __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, double tol,
-                            DevState* st, int* err, float* X, float* XT, float* P, float* v,
-                            bool first, double* sh) {
+                            DevState* st, int* err, float* X, float* XT, float* Y, float* YT,
+                            float* P, float* v, bool first, double* sh) {
   constexpr int S = KP / 16, LD = polar_ld<KP>();
+  constexpr int NM = (KP * KP + AT - 1) / AT;
   const int t = threadIdx.x, bi = t / 16, bj = t % 16;
-  double nf = 0.0;
-  for (int e = t; e < k * k; e += AT) {
-    const double x = __ldcg(&Mg[e]);
-    nf = fma(x, x, nf);
+  // M once (in FP32: any scale with sigma_max <= 1 serves)
+  float mv[NM];
+#pragma unroll
+  for (int q = 0; q < NM; ++q) {
+    const int e = t + AT * q, i = e / KP, j = e % KP;
+    mv[q] = (e < KP * KP && i < k && j < k) ? (float)__ldcg(&Mg[i * k + j]) : 0.f;
   }
-  nf = sqrt(block_sum256(nf, sh));
-  const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
-  for (int e = t; e < KP * KP; e += AT) {
-    const int i = e / KP, j = e % KP;
-    const float x = (i < k && j < k) ? (float)(__ldcg(&Mg[i * k + j]) * inv) : 0.f;
-    X[i * LD + j] = x;
-    XT[j * LD + i] = x;
+  float nl = 0.f;
+#pragma unroll
+  for (int q = 0; q < NM; ++q) nl = fmaf(mv[q], mv[q], nl);
+  const float nf2 = block_sum256f(nl, reinterpret_cast<float*>(sh));
+  const float inv = nf2 > 0.f ? 1.f / sqrtf(nf2) : 0.f;
+#pragma unroll
+  for (int q = 0; q < NM; ++q) {
+    const int e = t + AT * q, i = e / KP, j = e % KP;
+    if (e < KP * KP) {
+      X[i * LD + j] = mv[q] * inv;
+      XT[j * LD + i] = mv[q] * inv;
+    }
   }
   if (first)
     for (int i = t; i < KP; i += AT) v[i] = i < k ? 1.f + 0.25f * (float)(i % 5) : 0.f;
@@ -150,7 +191,7 @@ __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, dou
   for (; it < 100; ++it) {
     float acc[S][S], xo[S][S];
     rows_dot<KP, LD>(XT, XT, bi, bj, acc);      // P = X^T X
-    float dl = 0.f;
+    int ok = 1;
 #pragma unroll
     for (int s1 = 0; s1 < S; ++s1)
 #pragma unroll
@@ -158,14 +199,9 @@ __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, dou
         const int i = bi + 16 * s1, j = bj + 16 * s2;
         P[i * LD + j] = acc[s1][s2];
         xo[s1][s2] = X[i * LD + j];
-        if (i < k && j < k) {
-          const float x = acc[s1][s2] - (i == j ? 1.f : 0.f);
-          dl = fmaf(x, x, dl);
-        }
+        if (i < k && j < k && !(fabsf(acc[s1][s2] - (i == j ? 1.f : 0.f)) < 1e-5f)) ok = 0;
       }
-    // ||P - I||_F^2 in FP32 (its threshold 1e-10 is far above FP32 rounding);
-    // the barriers inside also order P before its use
-    const float dd = block_sum256f(dl, reinterpret_cast<float*>(sh));
+    const bool conv = __syncthreads_and(ok) != 0;   // also orders P before its use
     if (it == 0) {
       if (t < 32) {
         float l0 = sigma_min_estimate<KP, LD>(P, v, k, first ? 12 : 3);
@@ -174,54 +210,66 @@ __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, dou
       __syncthreads();
       lk = lsh[0];
     }
-    const bool conv = dd < 1e-10f;
-    if (dd < 1.f) lk = fmaxf(lk, sqrtf(fmaxf(1.f - sqrtf(dd), 0.f)));
     const float al = conv ? 1.f : sqrtf(3.f / (1.f + lk + lk * lk));
     const float ca = 1.5f * al, cb = 0.5f * al * al * al;
     lk = 0.5f * al * lk * (3.f - al * al * lk * lk);
     rows_dot<KP, LD>(X, P, bi, bj, acc);        // X P  (P symmetric)
-    __syncthreads();                            // every read of X, X^T, P done
 #pragma unroll
     for (int s1 = 0; s1 < S; ++s1)
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) {
         const int i = bi + 16 * s1, j = bj + 16 * s2;
         const float y = ca * xo[s1][s2] - cb * acc[s1][s2];
-        X[i * LD + j] = y;
-        XT[j * LD + i] = y;
+        Y[i * LD + j] = y;
+        YT[j * LD + i] = y;
       }
     __syncthreads();
+    float* tmp = X;
+    X = Y;
+    Y = tmp;
+    tmp = XT;
+    XT = YT;
+    YT = tmp;
     if (conv) {
       ++it;
       break;
     }
   }
-  // E = X^T X - I to about 2^-44: each product split exactly (x y = p + e by
-  // one FMA) and the p summed with an exact two-sum, the errors in FP32 (the
-  // sub-blocks with bi <= bj, mirrored); E itself is of the order of FP32
-  // rounding, so R = X - X E / 2 needs X E only in FP32
+  // the old R, loaded while E is summed
+  double rold[S][S];
+#pragma unroll
+  for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) {
+      const int i = bi + 16 * s1, j = bj + 16 * s2;
+      rold[s1][s2] = (i < k && j < k) ? __ldcg(&R[i * k + j]) : 0.0;
+    }
+  // E = X^T X - I to about 2^-44 (dfloat_fma, four chains over l mod 4; the
+  // sub-blocks with bi <= bj, mirrored): E is of the order of FP32 rounding,
+  // so R = X - X E / 2 needs X E only in FP32
   if (bi <= bj) {
-#pragma unroll
-    for (int s1 = 0; s1 < S; ++s1)
-#pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) {
-        const int i = bi + 16 * s1, j = bj + 16 * s2;
-        const float* xi = XT + i * LD;
-        const float* xj = XT + j * LD;
-        float hi = 0.f, lo = 0.f;
-        for (int l = 0; l < KP; ++l) {
-          const float p = __fmul_rn(xi[l], xj[l]);
-          const float pe = fmaf(xi[l], xj[l], -p);
-          const float sm = __fadd_rn(hi, p);
-          const float bv = __fsub_rn(sm, hi);
-          const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, bv)), __fsub_rn(p, bv));
-          hi = sm;
-          lo = __fadd_rn(lo, __fadd_rn(er, pe));
-        }
-        const float e = __fadd_rn(__fsub_rn(hi, (i == j && i < k) ? 1.f : 0.f), lo);
-        P[i * LD + j] = e;
-        P[j * LD + i] = e;
+#pragma unroll 1
+    for (int c = 0; c < S * S; ++c) {
+      const int i = bi + 16 * (c / S), j = bj + 16 * (c % S);
+      const float* xi = XT + i * LD;
+      const float* xj = XT + j * LD;
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
+#pragma unroll 2
+      for (int l = 0; l < KP; l += 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(xi + l);
+        const float4 b4 = *reinterpret_cast<const float4*>(xj + l);
+        dfloat_fma(a4.x, b4.x, h0, l0);
+        dfloat_fma(a4.y, b4.y, h1, l1);
+        dfloat_fma(a4.z, b4.z, h2, l2);
+        dfloat_fma(a4.w, b4.w, h3, l3);
       }
+      dfloat_add(h0, l0, h1, l1);
+      dfloat_add(h2, l2, h3, l3);
+      dfloat_add(h0, l0, h2, l2);
+      const float e = __fadd_rn(__fsub_rn(h0, (i == j && i < k) ? 1.f : 0.f), l0);
+      P[i * LD + j] = e;
+      P[j * LD + i] = e;
+    }
   }
   __syncthreads();
   // R_new = X - X E / 2 (E symmetric), ||R_new - R||^2
@@ -235,7 +283,7 @@ __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, dou
       const int i = bi + 16 * s1, j = bj + 16 * s2;
       if (i < k && j < k) {
         const double rn = (double)X[i * LD + j] - 0.5 * (double)acc[s1][s2];
-        const double x = rn - R[i * k + j];
+        const double x = rn - rold[s1][s2];
         d2 = fma(x, x, d2);
         R[i * k + j] = rn;
       }
@@ -246,7 +294,7 @@ __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, dou
     st->dR = dR;
     st->admm_steps += 1;
     st->jac_sweeps = it;
-    if (!(nf > 0.0) || it >= 100) atomicOr(err, ERR_NOTCONV);
+    if (!(nf2 > 0.f) || it >= 100) atomicOr(err, ERR_NOTCONV);
     if (dR <= tol * sqrt((double)k)) st->admm_done = 1;
   }
 }
@@ -269,15 +317,17 @@ struct AdmmArgs {
 };
 
 template <int KP>
-__global__ void __launch_bounds__(AT) admm_kernel(AdmmArgs a) {
+__global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) {
   constexpr int E = KP / LPR, S = KP / 16;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* Rs = reinterpret_cast<float*>(smraw);
   float* ws = Rs + KP * KP;
   float* bs = ws + ARPB * KP;
-  float* X = bs + ARPB * KP;
+  float* X = Rs + admm_region_a<KP>();
   float* XT = X + KP * polar_ld<KP>();
   float* P = XT + KP * polar_ld<KP>();
+  float* Y = Rs;                       // region A, polar only
+  float* YT = Y + KP * polar_ld<KP>();
   __shared__ double sh[AT];
   __shared__ float pv[KP];
 
@@ -347,7 +397,7 @@ __global__ void __launch_bounds__(AT) admm_kernel(AdmmArgs a) {
     sum_block_partials<AT>(a.part, (int)gridDim.x, kk, a.M);
     grid_sync(&st->bar, a.err);
     if (blockIdx.x == 0)
-      polar_block<KP>(a.M, k, a.R, a.tol, st, a.err, X, XT, P, pv, step == 0, sh);
+      polar_block<KP>(a.M, k, a.R, a.tol, st, a.err, X, XT, Y, YT, P, pv, step == 0, sh);
     grid_sync(&st->bar, a.err);
   }
 }
