@@ -105,6 +105,36 @@ __device__ __forceinline__ void load_a_row(const HalfArgs& a, const TF* A, int64
       const int64_t tile = i / 128;
       const int64_t gs = tile * a.cut_nkb, ge = gs + a.cut_nkb;
       const int64_t c_lo = ((gs + 1) * G - 1) / W, c_hi = (ge * G - 1) / W;
+      if (c_lo != c_hi && c_hi - c_lo < 4) {
+        // at most four contributors: every load issued before the first add
+        float sl[4][E], cr[E];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const int64_t q = c_lo + qq;
+          const int slot = (q * W) / G >= gs ? 0 : 1;
+          const float* src = a.cut_part + (q * 2 + slot) * 128 * a.cut_rp + (i % 128) * k;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int l = sub + LPR * e;
+            sl[qq][e] = (q <= c_hi && l < k) ? src[l] : 0.f;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int l = sub + LPR * e;
+          cr[e] = (a.cut_corr && l < k) ? a.cut_corr[i * k + l] : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int l = sub + LPR * e;
+          float acc = 0.f;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq)
+            if (c_lo + qq <= c_hi) acc += sl[qq][e];
+          v[e] = l < k ? (a.cut_corr ? acc + cr[e] : acc) : TF(0);
+        }
+        return;
+      }
       if (c_lo != c_hi) {
         float acc[E];
 #pragma unroll
@@ -140,6 +170,17 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int sub = lane & (LPR - 1);
   const int rloc = warp * (32 / LPR) + (lane / LPR);
+  DevState* st = a.st;
+  const int stage = *(volatile int*)&st->stage;
+  TF* F = (TF*)a.F;
+  const TF* A = (const TF*)a.A;
+  const int64_t rows = a.rows;
+  // the first pass's rows, requested before the Gram is staged so that the
+  // two load latencies overlap
+  const int64_t i_first = (int64_t)lb * RPB + rloc;
+  TF u_first[E], a_first[E];
+  load_row(F, i_first, i_first < rows, k, sub, u_first);
+  if (!a.gram_only) load_a_row(a, A, i_first, i_first < rows, k, sub, a_first);
   if (a.G) {
 #pragma unroll
     for (int q = 0; q < (KP * KP + HT - 1) / HT; ++q) {
@@ -157,11 +198,6 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
   }
   __syncthreads();
 
-  DevState* st = a.st;
-  const int stage = *(volatile int*)&st->stage;
-  TF* F = (TF*)a.F;
-  const TF* A = (const TF*)a.A;
-  const int64_t rows = a.rows;
   const int64_t passes = (rows + (int64_t)nb * RPB - 1) / ((int64_t)nb * RPB);
   TF gacc[S][S];
 #pragma unroll
@@ -184,7 +220,12 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
     for (int64_t ps = 0; ps < passes; ++ps) {
       const int64_t i = (ps * nb + lb) * RPB + rloc;
       TF u[E];
-      load_row(F, i, i < rows, k, sub, u);
+      if (ps == 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) u[e] = u_first[e];
+      } else {
+        load_row(F, i, i < rows, k, sub, u);
+      }
       write_split(a, i, i < rows, k, sub, u);
       gram_pass<TF, KP>(us, u, rloc, sub, gacc);
     }
@@ -194,16 +235,36 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
       const int64_t i = (ps * nb + lb) * RPB + rloc;
       const bool live = i < rows;
       TF u[E], av[E], q[E];
-      load_row(F, i, live, k, sub, u);
-      load_a_row(a, A, i, live, k, sub, av);
+      if (ps == 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          u[e] = u_first[e];
+          av[e] = a_first[e];
+        }
+      } else {
+        load_row(F, i, live, k, sub, u);
+        load_a_row(a, A, i, live, k, sub, av);
+      }
       row_times<TF, KP>(Gs, u, k, sub, q);
 #pragma unroll
       for (int e = 0; e < E; ++e) q[e] = av[e] - q[e];
+      // column j's G row entries and 1 / G_jj are read one column ahead, off
+      // the dependent chain (q_j -> u_j -> shuffle -> q update)
+      TF gcol[E], gi = ginv[0];
+#pragma unroll
+      for (int ee = 0; ee < E; ++ee) gcol[ee] = Gs[sub + LPR * ee];
 #pragma unroll
       for (int j = 0; j < KP; ++j) {
         if (j < k) {
           const int e = j / LPR, own = j % LPR;
-          const TF gi = ginv[j];
+          TF gnext[E], ginext = TF(0);
+#pragma unroll
+          for (int ee = 0; ee < E; ++ee) gnext[ee] = TF(0);
+          if (j + 1 < KP) {
+            ginext = ginv[j + 1];
+#pragma unroll
+            for (int ee = 0; ee < E; ++ee) gnext[ee] = Gs[(j + 1) * KP + sub + LPR * ee];
+          }
           TF v = u[e], dl = TF(0);
           if (gi > TF(0)) {
             v = fma(q[e], gi, u[e]);
@@ -213,7 +274,10 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
           dl = shfl8(dl, own);
           if (sub == own) u[e] = v;
 #pragma unroll
-          for (int ee = 0; ee < E; ++ee) q[ee] = fma(-dl, Gs[j * KP + sub + LPR * ee], q[ee]);
+          for (int ee = 0; ee < E; ++ee) q[ee] = fma(-dl, gcol[ee], q[ee]);
+#pragma unroll
+          for (int ee = 0; ee < E; ++ee) gcol[ee] = gnext[ee];
+          gi = ginext;
         }
       }
       store_row(F, i, live, k, sub, u);
@@ -234,8 +298,16 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
       const int64_t i = (ps * nb + lb) * RPB + rloc;
       const bool live = i < rows;
       TF u[E], av[E], g[E];
-      load_row(F, i, live, k, sub, u);
-      load_a_row(a, A, i, live, k, sub, av);
+      if (ps == 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          u[e] = u_first[e];
+          av[e] = a_first[e];
+        }
+      } else {
+        load_row(F, i, live, k, sub, u);
+        load_a_row(a, A, i, live, k, sub, av);
+      }
       unsigned bits = 0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
