@@ -245,11 +245,12 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
     return ENMF_EINVAL;
   }
   cudaMemsetAsync(ctx->ws, 0, ctx->ws_bytes, ctx->stream);
-  ctx->grid_u = half_step_grid(ctx->fdt, p->r, ctx->num_sms);
-  ctx->grid_v = ctx->grid_u;
+  ctx->grid_u = half_step_grid(ctx->fdt, p->r, ctx->num_sms, p->m);
+  ctx->grid_v = half_step_grid(ctx->fdt, p->r, ctx->num_sms, p->n);
   // at most 256 blocks: the fused Gram keeps one k x k partial per block in
   // the NPART x (LMAX^2 + 8) partial buffer
-  if (ctx->grid_u > 256) ctx->grid_u = ctx->grid_v = 256;
+  if (ctx->grid_u > 256) ctx->grid_u = 256;
+  if (ctx->grid_v > 256) ctx->grid_v = 256;
   if (tc_form(p)) {
     const TcPlan t = tc_plan(p, ctx->num_sms);
     ctx->tc = 1;

@@ -526,7 +526,7 @@ void hstep_launch(const HalfArgs& a, int grid, cudaStream_t s) {
 
 // Largest co-resident grid of the half step for this form and rank, at most
 // NPART blocks (the size of the partial buffers).
-int half_step_grid(int fdt, int k, int num_sms) {
+int half_step_grid(int fdt, int k, int num_sms, int64_t rows) {
   const int kp = rank_pad16(k);
   int cap;
   if (fdt == T_F64)
@@ -535,7 +535,10 @@ int half_step_grid(int fdt, int k, int num_sms) {
   else
     cap = kp == 16 ? hstep_capacity<float, 16>(num_sms) : kp == 32 ? hstep_capacity<float, 32>(num_sms)
           : kp == 48 ? hstep_capacity<float, 48>(num_sms) : hstep_capacity<float, 64>(num_sms);
-  return cap > NPART ? NPART : cap;
+  if (cap > NPART) cap = NPART;
+  // no more blocks than the rows fill in one pass
+  const int64_t need = (rows + RPB - 1) / RPB;
+  return need < 1 ? 1 : (need < cap ? (int)need : cap);
 }
 
 template <int K>

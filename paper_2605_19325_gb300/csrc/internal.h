@@ -132,7 +132,7 @@ struct HalfArgs {
 };
 // hstep.cu: one cooperative launch per half step; grid <= half_step_grid().
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);
-int half_step_grid(int fdt, int k, int num_sms);
+int half_step_grid(int fdt, int k, int num_sms, int64_t rows);
 // Grouped half steps of np problems with FP32 factors (HalfArgs in device
 // memory, all with the same `bar`); problem p owns blocks bbeg[p] ..
 // bbeg[p + 1] - 1 (bbeg: np + 1 ints in device memory), rank padded to kp
