@@ -405,7 +405,10 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
     launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->kept, ctx->err, s);
     launch_row_transform(ctx->N0, LMAX, l, ctx->N2, LMAX, l, n, fdt, ctx->T1, s);
     launch_gram(ctx->N2, LMAX, l, ctx->N1, LMAX, l, n, fdt, ctx->part, ctx->Msm, s);
-    launch_rr_svd(ctx->Msm, l, l, ctx->sig, ctx->Ut, ctx->Wt, ctx->err, s);
+    // with FP32 factors the stopping test below takes the FP32 Jacobi SVD
+    // (its residual sits far below the FP32 tolerance); the start itself is
+    // made from the FP64-finished SVD of the last P, after the loop
+    launch_rr_svd(ctx->Msm, l, l, ctx->sig, ctx->Ut, ctx->Wt, fdt == T_F32 ? 1 : 0, ctx->err, s);
     // Y = X Q2 (the next power iterate) and the residual ||Y W_r - Q U_r S_r||
     launch_xv(X, xdt, m, n, p.ldx, ctx->N2, LMAX, l, ctx->M1, LMAX, fdt, ctx->splitk, ctx->num_sms, s);
     launch_rr_prep(ctx->sig, ctx->Ut, ctx->Wt, l, l, r, ctx->Wr, ctx->UrS, ctx->st, s);
@@ -430,6 +433,7 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
       launch_row_transform(ctx->M2, LMAX, l, ctx->M0, LMAX, l, m, fdt, ctx->T1, s);
     }
   }
+  if (fdt == T_F32) launch_rr_svd(ctx->Msm, l, l, ctx->sig, ctx->Ut, ctx->Wt, 0, ctx->err, s);
   // U* = Q Tu, V* = Q2 Tv with the sign rule
   launch_colsum(ctx->M0, m, LMAX, l, fdt, ctx->part, ctx->csQ, s);
   launch_colsum(ctx->N2, n, LMAX, l, fdt, ctx->part, ctx->csQ2, s);

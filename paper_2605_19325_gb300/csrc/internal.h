@@ -185,9 +185,10 @@ void launch_eig_orth(const double* G, int k, double tau, double* T, int* kept, i
                      cudaStream_t s);
 // SVD of the (k2 x k1) matrix R2^T given R2 = P (k2 x k1 row-major):
 // R2^T = Ut S Wt^T, sorted descending.  Writes sigma (k1), Ut (k1 x k1),
-// Wt (k2 x k1).  See small.cu for layouts.
+// Wt (k2 x k1).  See small.cu for layouts.  fp32_only: FP32 Jacobi sweeps
+// only (for FP32-accurate P), else FP32 sweeps finished in FP64.
 void launch_rr_svd(const double* P, int k2, int k1, double* sigma, double* Ut, double* Wt,
-                   int* err, cudaStream_t s);
+                   int fp32_only, int* err, cudaStream_t s);
 // Final SVD-start transforms with the sign rule (see small.cu).
 void launch_svd_finish(const double* sigma, const double* Ut, const double* Wt, int k1, int k2,
                        int r, const double* colsumQ, const double* colsumQ2, double* Tu,

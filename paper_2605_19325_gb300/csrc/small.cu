@@ -421,9 +421,11 @@ void launch_eig_orth(const double* G, int k, double tau, double* T, int* kept, i
 // P = Q2^T Bt (k2 x k1, row-major).  The Rayleigh-Ritz matrix is
 // B = Q^T X = P^T Q2^T, and P^T (k1 x k2) = Ut S Wt^T.  Column c of P^T is
 // row c of P, so P's memory is P^T in column-major order.
+// fp32_only (the forms with FP32 factors, whose range-finder bases and P are
+// FP32-accurate): the FP32 sweeps alone, their A and V taken to FP64.
 __global__ void __launch_bounds__(SM_T)
 rr_svd_kernel(const double* __restrict__ P, int k2, int k1, double* sigma, double* Ut, double* Wt,
-              int* err) {
+              int fp32_only, int* err) {
   extern __shared__ double smd[];
   const int Np = k2 + (k2 & 1);
   double* A = smd;                  // Np columns x k1 rows
@@ -438,7 +440,18 @@ rr_svd_kernel(const double* __restrict__ P, int k2, int k1, double* sigma, doubl
     A[e] = c < k2 ? P[(size_t)c * k1 + i] : 0.0;
   }
   __syncthreads();
-  int sw = jacobi_osvd_mixed(A, k1, Np, V, A32, V32, T);
+  int sw;
+  if (fp32_only) {
+    for (int e = threadIdx.x; e < Np * k1; e += SM_T) A32[e] = (float)A[e];
+    for (int e = threadIdx.x; e < Np * Np; e += SM_T) V32[e] = (e / Np == e % Np) ? 1.f : 0.f;
+    __syncthreads();
+    sw = jacobi_osvd<float>(A32, k1, Np, V32, JAC_MAX_SWEEPS);
+    for (int e = threadIdx.x; e < Np * k1; e += SM_T) A[e] = (double)A32[e];
+    for (int e = threadIdx.x; e < Np * Np; e += SM_T) V[e] = (double)V32[e];
+    __syncthreads();
+  } else {
+    sw = jacobi_osvd_mixed(A, k1, Np, V, A32, V32, T);
+  }
   sort_desc(A, k1, Np, nrm, ord);
   for (int j = threadIdx.x; j < k2; j += SM_T) sigma[j] = nrm[ord[j]];
   for (int e = threadIdx.x; e < k1 * k2; e += SM_T) {
@@ -454,13 +467,13 @@ rr_svd_kernel(const double* __restrict__ P, int k2, int k1, double* sigma, doubl
 }
 
 void launch_rr_svd(const double* P, int k2, int k1, double* sigma, double* Ut, double* Wt,
-                   int* err, cudaStream_t s) {
+                   int fp32_only, int* err, cudaStream_t s) {
   note_launch(1);
   int Np = k2 + (k2 & 1);
   // FP64 panels plus the FP32 copies of the mixed-precision Jacobi
   size_t smem = small_smem(k1 > Np ? k1 : Np, Np) + sizeof(float) * ((size_t)Np * k1 + (size_t)Np * Np);
   cudaFuncSetAttribute(rr_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  rr_svd_kernel<<<1, SM_T, smem, s>>>(P, k2, k1, sigma, Ut, Wt, err);
+  rr_svd_kernel<<<1, SM_T, smem, s>>>(P, k2, k1, sigma, Ut, Wt, fp32_only, err);
 }
 
 // Residual inputs: Wr = Wt[:, :r] (k2 x r), UrS = Ut[:, :r] S_r (k1 x r).
