@@ -117,6 +117,11 @@ static size_t plan(const enmf_problem* p, int num_sms, size_t* splitk_out) {
   for (int k = 1; k <= LMAX; ++k) {
     int sv = choose_splits(p->m, p->n, k, bm, num_sms);
     int st = choose_splits(p->n, p->m, k, bm, num_sms);
+    if (fs == 4) {   // the FP32-factor sweep of FP32 / 16-bit X
+      const int sv2 = sweep_splits_f32(p->m, p->n, k, num_sms), st2 = sweep_splits_f32(p->n, p->m, k, num_sms);
+      if (sv2 > sv) sv = sv2;
+      if (st2 > st) st = st2;
+    }
     if (sv > 1 && (size_t)sv * mm * k * fs > sk) sk = (size_t)sv * mm * k * fs;
     if (st > 1 && (size_t)st * nn * k * fs > sk) sk = (size_t)st * nn * k * fs;
   }

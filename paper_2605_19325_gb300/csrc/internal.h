@@ -49,6 +49,8 @@ void note_launch(int n);
 
 // Split-K choice for the SIMT sweeps (also used to size the workspace).
 int choose_splits(int64_t rows_out, int64_t red_len, int k, int bm, int num_sms);
+// Split-K count of the FP32-factor SIMT sweep (FP32 / 16-bit X).
+int sweep_splits_f32(int64_t rows_out, int64_t red_len, int k, int num_sms);
 
 // ---------------------------------------------------------------- sweep.cu
 // C (rows_out x k, leading dim ldc) = X B (xv) or X^T B (xtu), FP64 or FP32

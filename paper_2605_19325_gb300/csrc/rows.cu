@@ -250,29 +250,50 @@ void launch_colsum(const void* F, int64_t rows, int ld, int k, int fdt, double* 
   colsum_reduce<<<1, 128, 0, s>>>(part, k, out);
 }
 
-// sum over rows of || Y_i Wr - Q_i UrS ||^2 (r columns), in FP64.
+// sum over rows of || Y_i Wr - Q_i UrS ||^2 (r columns): one warp per row,
+// the row's entries in registers (lane l holds l, l + 32, l + 64), Wr and UrS
+// transposed in shared memory in the factor type, one column of the row's
+// difference per butterfly sum; squares summed in FP64 in row order per warp.
+constexpr int RR_T = 256;
+constexpr int RR_E = (LMAX + 31) / 32;
+
 template <typename TF>
-__global__ void __launch_bounds__(RT_T)
+__global__ void __launch_bounds__(RR_T)
 rr_residual_kernel(const TF* Y, int ldy, int ky, const TF* Q, int ldq, int kq, int64_t rows, int r,
                    const double* __restrict__ Wr, const double* __restrict__ UrS, double* part) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* W_s = reinterpret_cast<double*>(smraw);   // ky x r
-  double* U_s = W_s + ky * r;                       // kq x r
-  __shared__ double sh[RT_T];
-  for (int e = threadIdx.x; e < ky * r; e += RT_T) W_s[e] = Wr[e];
-  for (int e = threadIdx.x; e < kq * r; e += RT_T) U_s[e] = UrS[e];
+  TF* Wt = reinterpret_cast<TF*>(smraw);   // r x ky: Wt[j * ky + l] = Wr(l, j)
+  TF* Ut = Wt + r * ky;                    // r x kq
+  __shared__ double sh[RR_T];
+  for (int e = threadIdx.x; e < ky * r; e += RR_T) Wt[(e % r) * ky + e / r] = (TF)Wr[e];
+  for (int e = threadIdx.x; e < kq * r; e += RR_T) Ut[(e % r) * kq + e / r] = (TF)UrS[e];
   __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t chunk = (rows + NPART - 1) / NPART;
   const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
   double acc = 0.0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += RT_T) {
+  for (int64_t i = r0 + warp; i < r1; i += RR_T / 32) {
+    TF y[RR_E], q[RR_E];
+#pragma unroll
+    for (int e = 0; e < RR_E; ++e) {
+      const int l = lane + 32 * e;
+      y[e] = l < ky ? Y[i * ldy + l] : TF(0);
+      q[e] = l < kq ? Q[i * ldq + l] : TF(0);
+    }
     for (int j = 0; j < r; ++j) {
-      double a = 0.0, b = 0.0;
-      for (int l = 0; l < ky; ++l) a = fma((double)Y[i * ldy + l], W_s[l * r + j], a);
-      for (int l = 0; l < kq; ++l) b = fma((double)Q[i * ldq + l], U_s[l * r + j], b);
-      acc = fma(a - b, a - b, acc);
+      TF d = TF(0);
+#pragma unroll
+      for (int e = 0; e < RR_E; ++e) {
+        const int l = lane + 32 * e;
+        if (l < ky) d = fma(y[e], Wt[j * ky + l], d);
+        if (l < kq) d = fma(-q[e], Ut[j * kq + l], d);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      acc = fma((double)d, (double)d, acc);   // the same in every lane
     }
   }
+  if (lane != 0) acc = 0.0;
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
@@ -281,13 +302,14 @@ void launch_rr_residual(const void* Y, int ldy, int ky, const void* Q, int ldq, 
                         int64_t rows, int r, int fdt, const double* Wr, const double* UrS,
                         double* part, double* out, cudaStream_t s) {
   note_launch(2);
-  size_t smem = sizeof(double) * ((size_t)ky * r + (size_t)kq * r);
   if (fdt == T_F64) {
+    const size_t smem = sizeof(double) * ((size_t)ky * r + (size_t)kq * r);
     cudaFuncSetAttribute(rr_residual_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rr_residual_kernel<double><<<NPART, RT_T, smem, s>>>((const double*)Y, ldy, ky, (const double*)Q, ldq, kq, rows, r, Wr, UrS, part);
+    rr_residual_kernel<double><<<NPART, RR_T, smem, s>>>((const double*)Y, ldy, ky, (const double*)Q, ldq, kq, rows, r, Wr, UrS, part);
   } else {
+    const size_t smem = sizeof(float) * ((size_t)ky * r + (size_t)kq * r);
     cudaFuncSetAttribute(rr_residual_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rr_residual_kernel<float><<<NPART, RT_T, smem, s>>>((const float*)Y, ldy, ky, (const float*)Q, ldq, kq, rows, r, Wr, UrS, part);
+    rr_residual_kernel<float><<<NPART, RR_T, smem, s>>>((const float*)Y, ldy, ky, (const float*)Q, ldq, kq, rows, r, Wr, UrS, part);
   }
   part_sum_to<<<1, 32, 0, s>>>(part, NPART, out, 0);
 }

@@ -145,6 +145,198 @@ static void sweep_launch(const void* X, int64_t m, int64_t n, int64_t ldx, const
   }
 }
 
+// ------------------------------------------------ FP32-factor sweep (SIMT)
+// C[rows_out x k] = op(X) B with FP32 factors and FP32 or 16-bit X (exact in
+// FP32), FP32 products and sums.  One CTA owns SW_BM output rows and SW_KT
+// columns (every column of the SVD start's widths up to 64 in one pass over
+// X) over a range of the reduction: 256 threads as 16 x 16, thread (tr, tc)
+// owning rows tr + 16 i (i < 8) and columns 4 tc .. 4 tc + 3.  Stages of
+// SW_BK reduction steps: the next stage's X and B values are loaded into
+// registers while the current stage is multiplied out of shared memory (two
+// buffers, one barrier per stage).  X sits in shared memory reduction-major.
+// Per output the products are summed in reduction order, then the split-K
+// partials in split order, so results are bitwise reproducible.
+constexpr int SW_BM = 128, SW_BK = 16, SW_KT = 64, SW_T = 256;
+
+int sweep_splits_f32(int64_t rows_out, int64_t red_len, int k, int num_sms) {
+  const int64_t tiles = ((rows_out + SW_BM - 1) / SW_BM) * ((k + SW_KT - 1) / SW_KT);
+  const int64_t target = 2LL * (num_sms > 0 ? num_sms : 152);
+  int64_t splits = (target + tiles - 1) / tiles;
+  const int64_t max_by_len = red_len / 256;
+  if (splits > max_by_len) splits = max_by_len;
+  if (splits > 16) splits = 16;
+  if (splits < 1) splits = 1;
+  return (int)splits;
+}
+
+template <typename TX> struct Ld4;
+template <> struct Ld4<float> {
+  static __device__ __forceinline__ float4 vec(const float* p) { return *reinterpret_cast<const float4*>(p); }
+};
+template <> struct Ld4<__nv_bfloat16> {
+  static __device__ __forceinline__ float4 vec(const __nv_bfloat16* p) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
+    return make_float4(__low2float(a), __high2float(a), __low2float(b), __high2float(b));
+  }
+};
+template <> struct Ld4<__half> {
+  static __device__ __forceinline__ float4 vec(const __half* p) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    const __half2 a = *reinterpret_cast<const __half2*>(&u.x);
+    const __half2 b = *reinterpret_cast<const __half2*>(&u.y);
+    return make_float4(__low2float(a), __high2float(a), __low2float(b), __high2float(b));
+  }
+};
+__device__ __forceinline__ float ld1(const float* p) { return *p; }
+__device__ __forceinline__ float ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ld1(const __half* p) { return __half2float(*p); }
+
+// Four consecutive entries p[0..3] of which those at offset >= lim read as 0
+// (whole vector when VEC and all four are in range).
+template <typename TX, bool VEC>
+__device__ __forceinline__ float4 load4(const TX* p, int64_t lim) {
+  if (VEC && lim >= 4) return Ld4<TX>::vec(p);
+  float4 v;
+  v.x = lim > 0 ? ld1(p) : 0.f;
+  v.y = lim > 1 ? ld1(p + 1) : 0.f;
+  v.z = lim > 2 ? ld1(p + 2) : 0.f;
+  v.w = lim > 3 ? ld1(p + 3) : 0.f;
+  return v;
+}
+
+template <typename TX, bool TRANS, bool VEC>
+__global__ void __launch_bounds__(SW_T)
+sweep32_kernel(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
+               const float* __restrict__ B, int ldb, int k, float* __restrict__ C, int ldc,
+               int64_t red_per_split, float* __restrict__ part) {
+  constexpr int BM = SW_BM, BK = SW_BK, KT = SW_KT, XLD = BM + 4;
+  __shared__ __align__(16) float Xs[2][BK][XLD];
+  __shared__ __align__(16) float Bs[2][BK][KT];
+  const int t = threadIdx.x, tr = t / 16, tc = t % 16;
+  const int64_t rows_out = TRANS ? n : m;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int col0 = blockIdx.y * KT;
+  const int64_t kb = (int64_t)blockIdx.z * red_per_split;
+  const int64_t ke = min(TRANS ? m : n, kb + red_per_split);
+
+  float4 xr[2], br;
+  // global -> registers for the stage starting at k0
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int q = t + SW_T * v;
+      if (!TRANS) {   // X rows row0 + q / 4, reduction columns k0 + 4 (q % 4) ..
+        const int64_t gr = row0 + q / 4, gc = k0 + 4 * (q % 4);
+        xr[v] = gr < m ? load4<TX, VEC>(X + gr * ldx + gc, ke - gc) : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {        // X row k0 + q / 32 (reduction), columns row0 + 4 (q % 32) ..
+        const int64_t gr = k0 + q / 32, gc = row0 + 4 * (q % 32);
+        xr[v] = gr < ke ? load4<TX, VEC>(X + gr * ldx + gc, n - gc) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    {   // B rows k0 + t / 16, columns col0 + 4 (t % 16) ..
+      const int64_t gr = k0 + t / 16;
+      const int gc = col0 + 4 * (t % 16);
+      br = gr < ke ? load4<float, VEC>(B + gr * ldb + gc, k - gc) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto stash = [&](int b) {
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int q = t + SW_T * v;
+      if (!TRANS) {
+        const int rr = q / 4, c4 = 4 * (q % 4);
+        Xs[b][c4 + 0][rr] = xr[v].x;
+        Xs[b][c4 + 1][rr] = xr[v].y;
+        Xs[b][c4 + 2][rr] = xr[v].z;
+        Xs[b][c4 + 3][rr] = xr[v].w;
+      } else {
+        *reinterpret_cast<float4*>(&Xs[b][q / 32][4 * (q % 32)]) = xr[v];
+      }
+    }
+    *reinterpret_cast<float4*>(&Bs[b][t / 16][4 * (t % 16)]) = br;
+  };
+
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+  int buf = 0;
+  if (kb < ke) {
+    fetch(kb);
+    stash(0);
+  }
+  __syncthreads();
+  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+    const bool more = k0 + BK < ke;
+    if (more) fetch(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = Xs[buf][kk][tr + 16 * i];
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tc]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
+        acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
+        acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
+        acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
+      }
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t gr = row0 + tr + 16 * i;
+    if (gr >= rows_out) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + 4 * tc + j;
+      if (gc >= k) continue;
+      if (part)
+        part[((int64_t)blockIdx.z * rows_out + gr) * k + gc] = acc[i][j];
+      else
+        C[gr * ldc + gc] = acc[i][j];
+    }
+  }
+}
+
+template <typename TX, bool TRANS>
+static void sweep32_launch(const void* X, int64_t m, int64_t n, int64_t ldx, const void* B, int ldb,
+                           int k, void* C, int ldc, void* part, int num_sms, cudaStream_t s) {
+  const int64_t rows_out = TRANS ? n : m, red = TRANS ? m : n;
+  int splits = sweep_splits_f32(rows_out, red, k, num_sms);
+  int64_t per = (red + splits - 1) / splits;
+  per = ((per + SW_BK - 1) / SW_BK) * SW_BK;
+  splits = (int)((red + per - 1) / per);
+  dim3 grid((unsigned)((rows_out + SW_BM - 1) / SW_BM), (k + SW_KT - 1) / SW_KT, splits);
+  float* p = splits > 1 ? (float*)part : nullptr;
+  // whole-vector loads need every row start and the base 16-byte (float) /
+  // 8-byte (16-bit) aligned
+  const size_t xa = sizeof(TX) * 4;
+  const bool vec = (ldx * (int64_t)sizeof(TX)) % (int64_t)xa == 0 && ((uintptr_t)X % xa) == 0 &&
+                   (ldb % 4) == 0 && ((uintptr_t)B % 16) == 0;
+  note_launch(splits > 1 ? 2 : 1);
+  if (vec)
+    sweep32_kernel<TX, TRANS, true><<<grid, SW_T, 0, s>>>((const TX*)X, m, n, ldx, (const float*)B,
+                                                          ldb, k, (float*)C, ldc, per, p);
+  else
+    sweep32_kernel<TX, TRANS, false><<<grid, SW_T, 0, s>>>((const TX*)X, m, n, ldx, (const float*)B,
+                                                           ldb, k, (float*)C, ldc, per, p);
+  if (splits > 1) {
+    const int64_t total = rows_out * k;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    splitk_reduce<float><<<blocks, 256, 0, s>>>((const float*)part, splits, rows_out, k, (float*)C, ldc);
+  }
+}
+
 template <bool TRANS>
 static void sweep_dispatch(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, const void* B,
                            int ldb, int k, void* C, int ldc, int fdt, void* part, int num_sms,
@@ -155,10 +347,10 @@ static void sweep_dispatch(const void* X, int xdt, int64_t m, int64_t n, int64_t
     else if (xdt == T_BF16) sweep_launch<__nv_bfloat16, double, TRANS>(X, m, n, ldx, B, ldb, k, C, ldc, part, num_sms, s);
     else sweep_launch<__half, double, TRANS>(X, m, n, ldx, B, ldb, k, C, ldc, part, num_sms, s);
   } else {
-    if (xdt == T_F32) sweep_launch<float, float, TRANS>(X, m, n, ldx, B, ldb, k, C, ldc, part, num_sms, s);
+    if (xdt == T_F32) sweep32_launch<float, TRANS>(X, m, n, ldx, B, ldb, k, C, ldc, part, num_sms, s);
     else if (xdt == T_F64) sweep_launch<double, float, TRANS>(X, m, n, ldx, B, ldb, k, C, ldc, part, num_sms, s);
-    else if (xdt == T_BF16) sweep_launch<__nv_bfloat16, float, TRANS>(X, m, n, ldx, B, ldb, k, C, ldc, part, num_sms, s);
-    else sweep_launch<__half, float, TRANS>(X, m, n, ldx, B, ldb, k, C, ldc, part, num_sms, s);
+    else if (xdt == T_BF16) sweep32_launch<__nv_bfloat16, TRANS>(X, m, n, ldx, B, ldb, k, C, ldc, part, num_sms, s);
+    else sweep32_launch<__half, TRANS>(X, m, n, ldx, B, ldb, k, C, ldc, part, num_sms, s);
   }
 }
 
@@ -283,6 +475,26 @@ void launch_dot(const void* A, int lda, const void* B, int ldb, int k, int64_t r
 }
 
 // ---------------------------------------------------------------- ||X||^2
+// Each block sums the squares of a chunk of rows; the domain check (x >= 0,
+// finite) rides along.  FP64 X: FP64 squares and sums.  FP32 and 16-bit X
+// (exact in FP32): the checks in FP32 and each thread's sum kept as an
+// unevaluated FP32 pair -- x^2 split exactly by one FMA, added by Knuth's
+// two-sum -- so the FP64 pipe (a small fraction of the FP32 rate on this
+// GPU) only sees the final pair; eight such pairs (rows i mod 8) per thread.
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+__device__ __forceinline__ void two_sum_sq(float x, float& hi, float& lo) {
+  const float p = __fmul_rn(x, x);
+  const float pe = fmaf(x, x, -p);
+  const float sm = __fadd_rn(hi, p);
+  const float bv = __fsub_rn(sm, hi);
+  const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, bv)), __fsub_rn(p, bv));
+  hi = sm;
+  lo = __fadd_rn(lo, __fadd_rn(er, pe));
+}
+
 template <typename TX>
 __global__ void __launch_bounds__(256)
 normx2_partial(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
@@ -290,14 +502,44 @@ normx2_partial(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
   __shared__ double sh[256];
   const int64_t chunk = (m + NPART - 1) / NPART;
   const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(m, r0 + chunk);
-  double s = 0.0;
   int bad = 0;
-  for (int64_t i = r0; i < r1; ++i)
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-      double x = to_d(X[i * ldx + j]);
-      if (!(x >= 0.0) || isinf(x)) bad = 1;
-      s = fma(x, x, s);
-    }
+  double s;
+  if constexpr (sizeof(TX) == 8) {
+    double s8[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s8[u] = 0.0;
+    for (int64_t i = r0; i < r1; i += 8)
+      for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = i + u < r1 ? to_d(X[(i + u) * ldx + j]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (!(x[u] >= 0.0) || isinf(x[u])) bad = 1;
+          s8[u] = fma(x[u], x[u], s8[u]);
+        }
+      }
+    s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+  } else {
+    float hi[8], lo[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) hi[u] = lo[u] = 0.f;
+    for (int64_t i = r0; i < r1; i += 8)
+      for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = i + u < r1 ? to_f(X[(i + u) * ldx + j]) : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (!(x[u] >= 0.f) || isinf(x[u])) bad = 1;
+          two_sum_sq(x[u], hi[u], lo[u]);
+        }
+      }
+    double d8[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) d8[u] = (double)hi[u] + (double)lo[u];
+    s = ((d8[0] + d8[1]) + (d8[2] + d8[3])) + ((d8[4] + d8[5]) + (d8[6] + d8[7]));
+  }
   if (bad) atomicOr(err, ERR_DOMAIN);
   s = block_sum(s, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
