@@ -601,6 +601,102 @@ residual_partial(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// The same for FP32 factors (FP32 or 16-bit X): the u . v dots in FP32 as
+// above, register-tiled.  A CTA keeps a 128-row tile of U in shared memory
+// (U^T, r rows) and walks 64-column tiles of V; thread (tr, tc) of 16 x 16
+// owns entries (tr + 16 i, tc + 16 j), i < 8, j < 4, and requests its X
+// entries before forming the dots.  Each entry's x - u . v is formed exactly
+// (as an FP32 pair: the value the FP64 difference gives) and its square
+// summed in an FP32 pair per thread to about 2^-48, so the FP64 pipe only
+// sees the pair totals; NPART partials.
+constexpr int RS_BM = 128, RS_BN = 64, RS_T = 256, RS_GY = NPART / 64;
+
+template <typename TX>
+__global__ void __launch_bounds__(RS_T)
+residual32_partial(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
+                   const float* __restrict__ U, const float* __restrict__ V, int r,
+                   double* __restrict__ part) {
+  extern __shared__ __align__(16) float rsm[];
+  float* Ut = rsm;                         // r x (RS_BM + 1): Ut[c * (RS_BM + 1) + i]
+  float* Vt = Ut + r * (RS_BM + 1);        // r x (RS_BN + 1)
+  __shared__ double sh[RS_T];
+  const int t = threadIdx.x, tr = t / 16, tc = t % 16;
+  const int64_t ntile_r = (m + RS_BM - 1) / RS_BM, ntile_c = (n + RS_BN - 1) / RS_BN;
+  float hi = 0.f, lo = 0.f;
+  for (int64_t ti = blockIdx.x; ti < ntile_r; ti += gridDim.x) {
+    const int64_t row0 = ti * RS_BM;
+    __syncthreads();
+    for (int e = t; e < RS_BM * r; e += RS_T) {
+      const int i = e / r, c = e % r;
+      Ut[c * (RS_BM + 1) + i] = row0 + i < m ? U[(row0 + i) * r + c] : 0.f;
+    }
+    for (int64_t tj = blockIdx.y; tj < ntile_c; tj += gridDim.y) {
+      const int64_t col0 = tj * RS_BN;
+      float x[8][4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int64_t gr = row0 + tr + 16 * i, gc = col0 + tc + 16 * j;
+          x[i][j] = (gr < m && gc < n) ? ld1(X + gr * ldx + gc) : 0.f;
+        }
+      __syncthreads();   // the previous tile's dots are done with Vt
+      for (int e = t; e < RS_BN * r; e += RS_T) {
+        const int jj = e / r, c = e % r;
+        Vt[c * (RS_BN + 1) + jj] = col0 + jj < n ? V[(col0 + jj) * r + c] : 0.f;
+      }
+      __syncthreads();
+      float d[8][4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[i][j] = 0.f;
+      for (int c = 0; c < r; ++c) {
+        float a[8], b[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = Ut[c * (RS_BM + 1) + tr + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Vt[c * (RS_BN + 1) + tc + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) d[i][j] = fmaf(a[i], b[j], d[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          // e = x - d exactly as eh + el (two-difference), then e^2 = p + pe
+          // + 2 eh el (+ el^2, below 2^-48 of e^2) into the pair (hi, lo);
+          // zero outside the matrix (both terms zero)
+          const float xv = x[i][j], nd = -d[i][j];
+          const float eh = __fadd_rn(xv, nd);
+          const float bv = __fsub_rn(eh, xv);
+          const float el = __fadd_rn(__fsub_rn(xv, __fsub_rn(eh, bv)), __fsub_rn(nd, bv));
+          const float p = __fmul_rn(eh, eh);
+          const float pe = fmaf(eh, eh, -p);
+          const float sm = __fadd_rn(hi, p);
+          const float bw = __fsub_rn(sm, hi);
+          const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, bw)), __fsub_rn(p, bw));
+          hi = sm;
+          lo = __fadd_rn(lo, __fadd_rn(er, __fadd_rn(pe, __fmul_rn(2.f * eh, el))));
+        }
+    }
+  }
+  double s = (double)hi + (double)lo;
+  s = block_sum(s, sh);
+  if (t == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+template <typename TX>
+static void residual32_launch(const void* X, int64_t m, int64_t n, int64_t ldx, const void* U,
+                              const void* V, int r, double* part, cudaStream_t s) {
+  const size_t smem = sizeof(float) * ((size_t)r * (RS_BM + 1) + (size_t)r * (RS_BN + 1));
+  cudaFuncSetAttribute(residual32_partial<TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  residual32_partial<TX><<<dim3(NPART / RS_GY, RS_GY), RS_T, smem, s>>>(
+      (const TX*)X, m, n, ldx, (const float*)U, (const float*)V, r, part);
+}
+
 void launch_residual_direct(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx,
                             const void* U, const void* V, int r, int fdt, double* part,
                             double* out, cudaStream_t s) {
@@ -614,9 +710,9 @@ void launch_residual_direct(const void* X, int xdt, int64_t m, int64_t n, int64_
     else RD_LAUNCH(__half, double);
   } else {
     if (xdt == T_F64) RD_LAUNCH(double, float);
-    else if (xdt == T_F32) RD_LAUNCH(float, float);
-    else if (xdt == T_BF16) RD_LAUNCH(__nv_bfloat16, float);
-    else RD_LAUNCH(__half, float);
+    else if (xdt == T_F32) residual32_launch<float>(X, m, n, ldx, U, V, r, part, s);
+    else if (xdt == T_BF16) residual32_launch<__nv_bfloat16>(X, m, n, ldx, U, V, r, part, s);
+    else residual32_launch<__half>(X, m, n, ldx, U, V, r, part, s);
   }
 #undef RD_LAUNCH
   part_reduce<<<1, 32, 0, s>>>(part, 1, out);
