@@ -443,17 +443,35 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
   sum_block_partials<HT>(a.gpart, nb, kk, a.G_out, (a.finalize && nb > 1) ? 1 : 0, lb, nb);
   if (!a.finalize || lb != 0) return;
 
-  // ---- end of the alternation (block 0): objective and stage update
-  const double gg = sum_partials(a.obj_part, nb, sh);
-  const double d = sum_partials(a.dot_part, nb, sh);
+  // ---- end of the alternation (block 0): objective and stage update.  The
+  // state is read in one go (its loads overlap the partial sums) and both
+  // sums share one block reduction (each in the order of sum_partials).
+  int stg = 0, nu = 0, nv = 0, asc = 0, hal = 0, kk0 = 0;
+  double nx2 = 0.0;
   if (t == 0) {
-    const double f = 0.5 * st->normX2 - d + 0.5 * gg;
+    const volatile DevState* vs = st;
+    stg = vs->stage;
+    nu = vs->negU;
+    nv = vs->negV;
+    asc = vs->asc_iters;
+    hal = vs->hals_iters;
+    kk0 = vs->k;
+    nx2 = vs->normX2;
+  }
+  double gg = 0.0, d = 0.0;
+  for (int b = t; b < nb; b += HT) {
+    gg += __ldcg(&a.obj_part[b]);
+    d += __ldcg(&a.dot_part[b]);
+  }
+  block_sum256x2(gg, d, sh);
+  if (t == 0) {
+    const double f = 0.5 * nx2 - d + 0.5 * gg;
     st->f_last = f;
     if (a.trace) a.trace[a.trace_idx] = f;
-    if (st->stage == 0) st->asc_iters += 1;
-    else st->hals_iters += 1;
-    st->k += 1;
-    if (st->stage == 0 && !(st->negU || st->negV)) st->stage = 1;
+    if (stg == 0) st->asc_iters = asc + 1;
+    else st->hals_iters = hal + 1;
+    st->k = kk0 + 1;
+    if (stg == 0 && !(nu || nv)) st->stage = 1;
     st->negU = 0;
     st->negV = 0;
   }

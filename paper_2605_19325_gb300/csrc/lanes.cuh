@@ -141,6 +141,24 @@ __device__ __forceinline__ double block_sum256(double v, double* sh) {
   return ((sh[0] + sh[1]) + (sh[2] + sh[3])) + ((sh[4] + sh[5]) + (sh[6] + sh[7]));
 }
 
+// Two such sums at once (each in the order of block_sum256): a and b come
+// back as the totals in every thread.  `sh` needs 16 doubles.
+__device__ __forceinline__ void block_sum256x2(double& a, double& b, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(FULL, a, o);
+    b += __shfl_xor_sync(FULL, b, o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = a;
+    sh[8 + (threadIdx.x >> 5)] = b;
+  }
+  __syncthreads();
+  a = ((sh[0] + sh[1]) + (sh[2] + sh[3])) + ((sh[4] + sh[5]) + (sh[6] + sh[7]));
+  b = ((sh[8] + sh[9]) + (sh[10] + sh[11])) + ((sh[12] + sh[13]) + (sh[14] + sh[15]));
+}
+
 // The same in FP32 (for sums whose FP32 rounding is far below what they are
 // compared with -- the FP64 adds of all 256 threads cost more than the data
 // warrants at this GPU's FP64 rate).  `sh` needs 8 floats.

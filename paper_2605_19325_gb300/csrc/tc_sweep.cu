@@ -390,9 +390,25 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       w = wend;
       const int b = (int)(seg & 1);
       const uint32_t up = (uint32_t)(seg >> 1) & 1u;
+      const bool whole = kb_a == 0 && kb_b == nkb;
+      const int64_t row0 = tile * TILE;
+      const int cnt = (int)min((int64_t)TILE, rows_out - row0) * r;
+      // at rank <= 32 the corr values of a whole tile are requested before
+      // its accumulator is ready (off the epilogue's critical path)
+      constexpr int NPF = RP <= 32 ? RP : 0;
+      float cpre[NPF > 0 ? NPF : 1];
+      if constexpr (NPF > 0) {
+        if (whole && corr) {
+          const float* cp = corr + row0 * r;
+#pragma unroll
+          for (int i = 0; i < NPF; ++i) {
+            const int f = et + 128 * i;
+            cpre[i] = f < cnt ? __ldcg(cp + f) : 0.f;
+          }
+        }
+      }
       const bool ok = mbar_wait(&accf_bar[b], up, err);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const bool whole = kb_a == 0 && kb_b == nkb;
       // (no early exit on a failed wait: the four epilogue warps must all
       // reach the named barriers; the failed stores are skipped)
       asm volatile("bar.sync 1, 128;" ::: "memory");   // previous copy-out done
@@ -407,8 +423,6 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce_bar[b]);        // accumulator b free again
       asm volatile("bar.sync 1, 128;" ::: "memory");   // staging tile complete
-      const int64_t row0 = tile * TILE;
-      const int cnt = (int)min((int64_t)TILE, rows_out - row0) * r;
       float* dst;
       const float* add = nullptr;
       if (whole) {
@@ -420,15 +434,33 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       }
       if (ok) {
         int rr = rr0, cc = cc0;
-        for (int f = et; f < cnt; f += 128) {
-          float v = stg[rr * SS + cc];
-          if (add) v += add[f];
-          dst[f] = v;
-          rr += q128;
-          cc += r128;
-          if (cc >= r) {
-            cc -= r;
-            ++rr;
+        if constexpr (NPF > 0) {
+#pragma unroll
+          for (int i = 0; i < NPF; ++i) {
+            const int f = et + 128 * i;
+            if (f < cnt) {
+              float v = stg[rr * SS + cc];
+              if (add) v += cpre[i];
+              dst[f] = v;
+            }
+            rr += q128;
+            cc += r128;
+            if (cc >= r) {
+              cc -= r;
+              ++rr;
+            }
+          }
+        } else {
+          for (int f = et; f < cnt; f += 128) {
+            float v = stg[rr * SS + cc];
+            if (add) v += add[f];
+            dst[f] = v;
+            rr += q128;
+            cc += r128;
+            if (cc >= r) {
+              cc -= r;
+              ++rr;
+            }
           }
         }
       }
