@@ -40,9 +40,15 @@ constexpr size_t admm_region_a() {
   return rows > pol ? rows : pol;
 }
 
+// ... followed, at KP <= 48, by the rows' w, z, y (ARPB x KP each) for when
+// they stay resident (at KP = 64 that space would cost a block per SM).
+template <int KP>
+constexpr bool admm_resident_ok() { return KP <= 48; }
+
 template <int KP>
 constexpr size_t admm_smem() {
-  return sizeof(float) * (admm_region_a<KP>() + 3 * (size_t)KP * polar_ld<KP>());
+  return sizeof(float) * (admm_region_a<KP>() + 3 * (size_t)KP * polar_ld<KP>() +
+                          (admm_resident_ok<KP>() ? 3 * (size_t)ARPB * KP : 0));
 }
 
 // acc[s1][s2] += sum_l A[ia_s1][l] B[jb_s2][l] over l < KP, with rows
@@ -328,6 +334,7 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
   float* P = XT + KP * polar_ld<KP>();
   float* Y = Rs;                       // region A, polar only
   float* YT = Y + KP * polar_ld<KP>();
+  float* wz = P + KP * polar_ld<KP>();  // resident rows: w | z | y, ARPB x KP each
   __shared__ double sh[AT];
   __shared__ float pv[KP];
 
@@ -341,12 +348,43 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
   const float rho = (float)a.rho;
   const float thr = -1.f / rho;
 
-  for (int step = 0; step < a.max_iter; ++step) {
-    if (*(volatile int*)&st->admm_done) break;   // same value in every block
-    for (int e = t; e < KP * KP; e += AT) {
-      const int i = e / KP, j = e % KP;
-      Rs[e] = (i < k && j < k) ? (float)__ldcg(&a.R[i * k + j]) : 0.f;
+  // when every row fits in one pass a block owns the same rows at every step:
+  // w, z and y then stay in shared memory from the first step to the last
+  // (z and y are written back once, at the end); each thread touches only its
+  // own entries there
+  constexpr int NR = (KP * KP + AT - 1) / AT;
+  const bool resident = admm_resident_ok<KP>() && passes == 1;
+  float* wrow = wz + rloc * KP + sub;
+  float* zrow = wrow + ARPB * KP;
+  float* yrow = zrow + ARPB * KP;
+  if (resident) {
+    const int64_t i = (int64_t)blockIdx.x * ARPB + rloc;
+    const bool live = i < rows;
+    float w[E], z[E], y[E];
+    if (i < m) load_row(a.U, i, live, k, sub, w);
+    else load_row(a.V, i - m, live, k, sub, w);
+    load_row(a.Z, i, live, k, sub, z);
+    load_row(a.Y, i, live, k, sub, y);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      wrow[LPR * e] = w[e];
+      zrow[LPR * e] = z[e];
+      yrow[LPR * e] = y[e];
     }
+  }
+  for (int step = 0; step < a.max_iter; ++step) {
+    // the stop flag (the same value in every block) and R in one round trip
+    const int done = *(volatile int*)&st->admm_done;
+    float rv[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const int e = t + AT * q, i = e / KP, j = e % KP;
+      rv[q] = (e < KP * KP && i < k && j < k) ? (float)__ldcg(&a.R[i * k + j]) : 0.f;
+    }
+    if (done) break;
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+      if (t + AT * q < KP * KP) Rs[t + AT * q] = rv[q];
     __syncthreads();
     float acc[S][S];
 #pragma unroll
@@ -357,10 +395,19 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
       const int64_t i = (ps * gridDim.x + blockIdx.x) * ARPB + rloc;
       const bool live = i < rows;
       float w[E], z[E], y[E], p[E], bv[E];
-      if (i < m) load_row(a.U, i, live, k, sub, w);
-      else load_row(a.V, i - m, live, k, sub, w);
-      load_row(a.Z, i, live, k, sub, z);
-      load_row(a.Y, i, live, k, sub, y);
+      if (resident) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          w[e] = wrow[LPR * e];
+          z[e] = zrow[LPR * e];
+          y[e] = yrow[LPR * e];
+        }
+      } else {
+        if (i < m) load_row(a.U, i, live, k, sub, w);
+        else load_row(a.V, i - m, live, k, sub, w);
+        load_row(a.Z, i, live, k, sub, z);
+        load_row(a.Y, i, live, k, sub, y);
+      }
       row_times<float, KP>(Rs, w, k, sub, p);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -372,8 +419,16 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
         y[e] = yy;
         bv[e] = zz + yy / rho;                          // B = Z + Y / rho
       }
-      store_row(a.Z, i, live, k, sub, z);
-      store_row(a.Y, i, live, k, sub, y);
+      if (resident) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          zrow[LPR * e] = z[e];
+          yrow[LPR * e] = y[e];
+        }
+      } else {
+        store_row(a.Z, i, live, k, sub, z);
+        store_row(a.Y, i, live, k, sub, y);
+      }
       __syncthreads();
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -399,6 +454,17 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
     if (blockIdx.x == 0)
       polar_block<KP>(a.M, k, a.R, a.tol, st, a.err, X, XT, Y, YT, P, pv, step == 0, sh);
     grid_sync(&st->bar, a.err);
+  }
+  if (resident) {
+    const int64_t i = (int64_t)blockIdx.x * ARPB + rloc;
+    float z[E], y[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      z[e] = zrow[LPR * e];
+      y[e] = yrow[LPR * e];
+    }
+    store_row(a.Z, i, i < rows, k, sub, z);
+    store_row(a.Y, i, i < rows, k, sub, y);
   }
 }
 
