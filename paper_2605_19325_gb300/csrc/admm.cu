@@ -150,7 +150,8 @@ __device__ __forceinline__ void dfloat_add(float& hi, float& lo, float h2, float
 
 // R = polar(M) on one block of AT threads (see the file comment).  X, XT and
 // Y, YT: two KP x PLD buffer pairs (the iterate and the next one); P: KP x
-// PLD; v: KP floats kept from step to step.  Thread (bi, bj) = (t / 16,
+// PLD; v: KP + 1 floats kept from step to step (the power-iteration vector
+// and, in v[KP], the sigma_min estimate).  Thread (bi, bj) = (t / 16,
 // t % 16) owns the entries (bi + 16 s1, bj + 16 s2).
 //
 // The iteration is Newton-Schulz with the scaling of a lower bound l of the
@@ -164,7 +165,8 @@ __device__ __forceinline__ void dfloat_add(float& hi, float& lo, float h2, float
 template <int KP>
 __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, double tol,
                             DevState* st, int* err, float* X, float* XT, float* Y, float* YT,
-                            float* P, float* v, bool first, double* sh) {
+                            float* P, float* v, int step, double* sh) {
+  const bool first = step == 0;
   constexpr int S = KP / 16, LD = polar_ld<KP>();
   constexpr int NM = (KP * KP + AT - 1) / AT;
   const int t = threadIdx.x, bi = t / 16, bj = t % 16;
@@ -191,7 +193,6 @@ __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, dou
   if (first)
     for (int i = t; i < KP; i += AT) v[i] = i < k ? 1.f + 0.25f * (float)(i % 5) : 0.f;
   __syncthreads();
-  float* lsh = reinterpret_cast<float*>(sh) + 8;   // past block_sum256f's 8 floats
   float lk = 0.f;
   int it = 0;
   for (; it < 100; ++it) {
@@ -209,12 +210,17 @@ __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, dou
       }
     const bool conv = __syncthreads_and(ok) != 0;   // also orders P before its use
     if (it == 0) {
-      if (t < 32) {
-        float l0 = sigma_min_estimate<KP, LD>(P, v, k, first ? 12 : 3);
-        if (t == 0) lsh[0] = fminf(fmaxf(0.9f * l0, 1e-4f), 1.f);
+      // the estimate of sigma_min(X_0), refreshed every eighth step (M, and
+      // with it the estimate, changes slowly from step to step) and kept in
+      // v[KP] in between
+      if (step % 8 == 0) {
+        if (t < 32) {
+          float l0 = sigma_min_estimate<KP, LD>(P, v, k, first ? 12 : 3);
+          if (t == 0) v[KP] = fminf(fmaxf(0.9f * l0, 1e-4f), 1.f);
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      lk = lsh[0];
+      lk = v[KP];
     }
     const float al = conv ? 1.f : sqrtf(3.f / (1.f + lk + lk * lk));
     const float ca = 1.5f * al, cb = 0.5f * al * al * al;
@@ -298,7 +304,7 @@ __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, dou
   if (t == 0) {
     const double dR = sqrt(d2);
     st->dR = dR;
-    st->admm_steps += 1;
+    st->admm_steps = step + 1;   // (reset to 0 before the launch)
     st->jac_sweeps = it;
     if (!(nf2 > 0.f) || it >= 100) atomicOr(err, ERR_NOTCONV);
     if (dR <= tol * sqrt((double)k)) st->admm_done = 1;
@@ -336,7 +342,7 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
   float* YT = Y + KP * polar_ld<KP>();
   float* wz = P + KP * polar_ld<KP>();  // resident rows: w | z | y, ARPB x KP each
   __shared__ double sh[AT];
-  __shared__ float pv[KP];
+  __shared__ float pv[KP + 1];
 
   const int k = a.k, kk = k * k;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -452,7 +458,7 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
     sum_block_partials<AT>(a.part, (int)gridDim.x, kk, a.M);
     grid_sync(&st->bar, a.err);
     if (blockIdx.x == 0)
-      polar_block<KP>(a.M, k, a.R, a.tol, st, a.err, X, XT, Y, YT, P, pv, step == 0, sh);
+      polar_block<KP>(a.M, k, a.R, a.tol, st, a.err, X, XT, Y, YT, P, pv, step, sh);
     grid_sync(&st->bar, a.err);
   }
   if (resident) {
