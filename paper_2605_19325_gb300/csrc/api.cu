@@ -235,7 +235,7 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
   ctx->T2 = (double*)take(LMAX * LMAX * 8);
   ctx->Ut = (double*)take(LMAX * LMAX * 8);
   ctx->Wt = (double*)take(LMAX * LMAX * 8);
-  (void)take(LMAX * LMAX * 8);
+  ctx->T1x = (double*)take(LMAX * LMAX * 8);
   ctx->Tu = (double*)take(LMAX * RMAX * 8);
   ctx->Tv = (double*)take(LMAX * RMAX * 8);
   ctx->Wr = (double*)take(LMAX * RMAX * 8);
@@ -364,11 +364,11 @@ static void orth2(enmf_ctx* ctx, void* F, void* tmp, int64_t rows, int k) {
   const double tau = ctx->fdt == T_F64 ? 1e-13 : 1e-11;
   cudaStream_t s = ctx->stream;
   launch_gram(F, LMAX, k, F, LMAX, k, rows, ctx->fdt, ctx->part, ctx->Gu, s);
-  launch_eig_orth(ctx->Gu, k, tau, ctx->T1, ctx->kept, ctx->err, s);
-  launch_row_transform(F, LMAX, k, tmp, LMAX, k, rows, ctx->fdt, ctx->T1, s);
+  launch_eig_orth(ctx->Gu, k, tau, ctx->T1, ctx->T1x, ctx->kept, ctx->err, s);
+  launch_row_orth(F, LMAX, tmp, LMAX, k, rows, ctx->fdt, ctx->T1, ctx->T1x, s);
   launch_gram(tmp, LMAX, k, tmp, LMAX, k, rows, ctx->fdt, ctx->part, ctx->Gu, s);
-  launch_eig_orth(ctx->Gu, k, tau, ctx->T1, ctx->kept, ctx->err, s);
-  launch_row_transform(tmp, LMAX, k, F, LMAX, k, rows, ctx->fdt, ctx->T1, s);
+  launch_eig_orth(ctx->Gu, k, tau, ctx->T1, ctx->T1x, ctx->kept, ctx->err, s);
+  launch_row_orth(tmp, LMAX, F, LMAX, k, rows, ctx->fdt, ctx->T1, ctx->T1x, s);
 }
 
 // ------------------------------------------------------------------ 1. SVD
@@ -404,11 +404,11 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
     // Bt = X^T Q ; Q2 = orth(Bt) ; P = Q2^T Bt
     launch_xtu(X, xdt, m, n, p.ldx, ctx->M0, LMAX, l, ctx->N1, LMAX, fdt, ctx->splitk, ctx->num_sms, s);
     launch_gram(ctx->N1, LMAX, l, ctx->N1, LMAX, l, n, fdt, ctx->part, ctx->Gu, s);
-    launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->kept, ctx->err, s);
-    launch_row_transform(ctx->N1, LMAX, l, ctx->N0, LMAX, l, n, fdt, ctx->T1, s);
+    launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->T1x, ctx->kept, ctx->err, s);
+    launch_row_orth(ctx->N1, LMAX, ctx->N0, LMAX, l, n, fdt, ctx->T1, ctx->T1x, s);
     launch_gram(ctx->N0, LMAX, l, ctx->N0, LMAX, l, n, fdt, ctx->part, ctx->Gu, s);
-    launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->kept, ctx->err, s);
-    launch_row_transform(ctx->N0, LMAX, l, ctx->N2, LMAX, l, n, fdt, ctx->T1, s);
+    launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->T1x, ctx->kept, ctx->err, s);
+    launch_row_orth(ctx->N0, LMAX, ctx->N2, LMAX, l, n, fdt, ctx->T1, ctx->T1x, s);
     launch_gram(ctx->N2, LMAX, l, ctx->N1, LMAX, l, n, fdt, ctx->part, ctx->Msm, s);
     // with FP32 factors the stopping test below takes the FP32 Jacobi SVD
     // (its residual sits far below the FP32 tolerance); the start itself is
@@ -431,11 +431,11 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
     if (it + 1 < o.max_iters) {
       // Q = orth(Y)
       launch_gram(ctx->M1, LMAX, l, ctx->M1, LMAX, l, m, fdt, ctx->part, ctx->Gu, s);
-      launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->kept, ctx->err, s);
-      launch_row_transform(ctx->M1, LMAX, l, ctx->M2, LMAX, l, m, fdt, ctx->T1, s);
+      launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->T1x, ctx->kept, ctx->err, s);
+      launch_row_orth(ctx->M1, LMAX, ctx->M2, LMAX, l, m, fdt, ctx->T1, ctx->T1x, s);
       launch_gram(ctx->M2, LMAX, l, ctx->M2, LMAX, l, m, fdt, ctx->part, ctx->Gu, s);
-      launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->kept, ctx->err, s);
-      launch_row_transform(ctx->M2, LMAX, l, ctx->M0, LMAX, l, m, fdt, ctx->T1, s);
+      launch_eig_orth(ctx->Gu, l, fdt == T_F64 ? 1e-13 : 1e-11, ctx->T1, ctx->T1x, ctx->kept, ctx->err, s);
+      launch_row_orth(ctx->M2, LMAX, ctx->M0, LMAX, l, m, fdt, ctx->T1, ctx->T1x, s);
     }
   }
   if (fdt == T_F32) launch_rr_svd(ctx->Msm, l, l, ctx->sig, ctx->Ut, ctx->Wt, 0, ctx->err, s);

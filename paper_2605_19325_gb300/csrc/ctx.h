@@ -35,6 +35,7 @@ struct enmf_ctx {
   double* pb_part;               // 2 * 4096
   double* Gu; double* Gv; double* Msm; double* R;
   double* T1; double* T2; double* Ut; double* Wt; double* sig;
+  double* T1x;   // eig_orth's companion of T1 (see launch_eig_orth)
   double* Tu; double* Tv; double* Wr; double* UrS; double* csQ; double* csQ2;
   double* scal;                  // 64 scratch scalars
   // host-data staging for enmf_solve

@@ -180,11 +180,17 @@ void launch_admm_f32(const float* U, const float* V, int64_t m, int64_t n, int k
 // R_new = polar(sum of NPART partial M's); dR, convergence, ADMM step count.
 void launch_polar(const double* M, int k, double* R, double* D, double tol,
                   DevState* st, int* err, cudaStream_t s);
-// Orthonormalising transform of a Gram G (k x k): eigen-decomposition by
-// one-sided Jacobi, keep eigenvalues > tau * lambda_1, T = V_k diag(l^-1/2).
-// Writes T (k x k, unused columns zero) and *kept.
-void launch_eig_orth(const double* G, int k, double tau, double* T, int* kept, int* err,
+// Orthonormalising map of a Gram G (k x k), applied by launch_row_orth:
+// scaled Cholesky (T = L, Tx = D, 1 / diag(L), mode 1), or when G is
+// numerically rank deficient the eigen map by one-sided Jacobi (eigenvalues
+// > tau * lambda_1 kept, T = V_k diag(l^-1/2), unused columns zero, mode 0).
+// Tx: 2 LMAX + 1 doubles.  Writes *kept.
+void launch_eig_orth(const double* G, int k, double tau, double* T, double* Tx, int* kept, int* err,
                      cudaStream_t s);
+// out = in mapped by eig_orth's (T, Tx) row by row (rows x k, leading
+// dimensions ld_in / ld_out; in place is safe).
+void launch_row_orth(const void* in, int ld_in, void* out, int ld_out, int k, int64_t rows, int fdt,
+                     const double* T, const double* Tx, cudaStream_t s);
 // SVD of the (k2 x k1) matrix R2^T given R2 = P (k2 x k1 row-major):
 // R2^T = Ut S Wt^T, sorted descending.  Writes sigma (k1), Ut (k1 x k1),
 // Wt (k2 x k1).  See small.cu for layouts.  fp32_only: FP32 Jacobi sweeps

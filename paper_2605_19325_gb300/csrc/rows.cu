@@ -186,6 +186,64 @@ void launch_row_transform(const void* in, int ld_in, int k_in, void* out, int ld
   }
 }
 
+// Rows of Y through the orthonormalising map of eig_orth (k x k, see
+// small.cu): mode 1 (Tx[2 LMAX]) solves z L^T = y D row by row by forward
+// substitution (z_i = (y_i d_i - sum_{p<i} L_ip z_p) / L_ii, in TF, 1 / L_ii
+// from Tx), mode 0 multiplies by T.  The row is staged per thread as in
+// row_transform_kernel; in place is safe.
+template <typename TF>
+__global__ void __launch_bounds__(RT_T)
+row_orth_kernel(const TF* in, int ld_in, TF* out, int ld_out, int k, int64_t rows,
+                const double* __restrict__ T, const double* __restrict__ Tx) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TF* Ts = reinterpret_cast<TF*>(smraw);       // k x k
+  TF* ds = Ts + k * k;                         // d (mode 1)
+  TF* iv = ds + k;                             // 1 / L_ii (mode 1)
+  TF* xs = iv + k;                             // xs[l * RT_T + t]
+  const bool tri = Tx[2 * LMAX] != 0.0;
+  for (int e = threadIdx.x; e < k * k; e += RT_T) Ts[e] = (TF)T[e];
+  for (int e = threadIdx.x; e < k; e += RT_T) {
+    ds[e] = (TF)Tx[e];
+    iv[e] = (TF)Tx[LMAX + e];
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  for (int64_t i = (int64_t)blockIdx.x * RT_T + t; i < rows; i += (int64_t)gridDim.x * RT_T) {
+    if (tri) {
+      for (int l = 0; l < k; ++l) {
+        TF sacc = in[i * ld_in + l] * ds[l];
+        for (int q = 0; q < l; ++q) sacc = fma(-Ts[l * k + q], xs[q * RT_T + t], sacc);
+        xs[l * RT_T + t] = sacc * iv[l];
+      }
+      for (int j = 0; j < k; ++j) out[i * ld_out + j] = xs[j * RT_T + t];
+    } else {
+      for (int l = 0; l < k; ++l) xs[l * RT_T + t] = in[i * ld_in + l];
+      for (int j = 0; j < k; ++j) {
+        TF sacc = TF(0);
+        for (int l = 0; l < k; ++l) sacc = fma(xs[l * RT_T + t], Ts[l * k + j], sacc);
+        out[i * ld_out + j] = sacc;
+      }
+    }
+  }
+}
+
+void launch_row_orth(const void* in, int ld_in, void* out, int ld_out, int k, int64_t rows, int fdt,
+                     const double* T, const double* Tx, cudaStream_t s) {
+  note_launch(1);
+  const size_t smem = type_size(fdt) * ((size_t)k * k + 2 * (size_t)k + (size_t)k * RT_T);
+  int blocks = (int)min((int64_t)1024, (rows + RT_T - 1) / RT_T);
+  if (blocks < 1) blocks = 1;
+  if (fdt == T_F64) {
+    cudaFuncSetAttribute(row_orth_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    row_orth_kernel<double><<<blocks, RT_T, smem, s>>>((const double*)in, ld_in, (double*)out, ld_out, k,
+                                                       rows, T, Tx);
+  } else {
+    cudaFuncSetAttribute(row_orth_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    row_orth_kernel<float><<<blocks, RT_T, smem, s>>>((const float*)in, ld_in, (float*)out, ld_out, k, rows,
+                                                      T, Tx);
+  }
+}
+
 void launch_apply_square(void* F, int64_t rows, int k, int fdt, const double* R, cudaStream_t s) {
   // each thread stages its row before writing, so in place is safe
   launch_row_transform(F, k, k, F, k, k, rows, fdt, R, s);

@@ -303,28 +303,48 @@ void launch_polar(const double* M, int k, double* R, double* D, double tol, DevS
 }
 
 // ------------------------------------------------------ Gram -> orth map
-// G = Y^T Y (k x k, symmetric PSD) -> T (k x k) with Y T orthonormal.
+// G = Y^T Y (k x k, symmetric PSD) -> the map with Y T orthonormal, applied
+// to the rows of Y by row_orth (rows.cu).
 //
-// Fast path, scaled Cholesky: with D = diag(G)^-1/2 and D G D = L L^T,
-// T = D L^-T (then (Y T)^T (Y T) = L^-1 D G D L^-T = I).  It is taken when
-// every pivot of D G D is above tau (the diagonal is 1 after scaling), i.e. Y
-// has no direction near the truncation threshold; the caller runs two passes,
-// so the orthogonality lost to cond(G) in the first is restored by the second.
+// Fast path, scaled Cholesky: with D = diag(G)^-1/2 and D G D = L L^T the map
+// is T = D L^-T (then (Y T)^T (Y T) = L^-1 D G D L^-T = I); it is not formed:
+// T receives L (row-major, lower triangle and diagonal) and Tx the diagonal of
+// D (Tx[0..k)), 1 / L_jj (Tx[LMAX..LMAX+k)) and the mode 1 (Tx[2 LMAX]), and
+// each row y of Y is mapped by the triangular solve  z L^T = y D.  It is taken
+// when every pivot of D G D is above tau (the diagonal is 1 after scaling),
+// i.e. Y has no direction near the truncation threshold; the caller runs two
+// passes, so the orthogonality lost to cond(G) in the first is restored by
+// the second.
 //
 // Otherwise (a pivot at or below tau: Y numerically rank deficient), the
 // eigen path: one-sided Jacobi on the columns of G gives G V = A with
 // orthogonal columns; for PSD G the columns of V are eigenvectors and |a_c|
 // the eigenvalues.  T = V_kept diag(lambda^-1/2) for lambda > tau *
-// lambda_max (dropped directions give zero columns).
+// lambda_max (dropped directions give zero columns), mode 0 (a product).
+//
+// 1 / sqrt(d), d > 0: an FP32 estimate refined by two Newton-Raphson steps
+// for the reciprocal square root, y <- y (3 - d y^2) / 2 (each step about
+// doubles the correct bits, 24 -> 48 -> FP64).  A dependent FP64 operation
+// costs on the order of a hundred cycles on this GPU; this chain is far
+// shorter than a square root followed by a division.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  if (!(d >= 1e-30 && d <= 1e30)) return 1.0 / sqrt(d);   // outside the FP32 start's range
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+
 __device__ bool chol_orth(const double* __restrict__ G, int k, double tau, double* C,
-                          double* Li, double* dsc, double* T) {
+                          double* dsc, double* T, double* Tx) {
   __shared__ int ok;
+  __shared__ double invd[LMAX];
   if (threadIdx.x == 0) ok = 1;
   __syncthreads();
   for (int i = threadIdx.x; i < k; i += SM_T) {
     const double g = G[i * k + i];
     if (!(g > 0.0)) ok = 0;
-    dsc[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+    dsc[i] = g > 0.0 ? rsqrt_nr(g) : 0.0;
   }
   __syncthreads();
   if (!ok) return false;
@@ -333,17 +353,23 @@ __device__ bool chol_orth(const double* __restrict__ G, int k, double tau, doubl
     C[e] = G[e] * dsc[i] * dsc[j];
   }
   __syncthreads();
-  // right-looking Cholesky, lower triangle of C (row-major) becomes L
+  // right-looking Cholesky, lower triangle of C (row-major) becomes L; the
+  // column is scaled by the reciprocal of its pivot (a multiplication)
   for (int j = 0; j < k; ++j) {
     if (threadIdx.x == 0) {
       const double d = C[j * k + j];
-      if (d > tau) C[j * k + j] = sqrt(d);
-      else ok = 0;
+      if (d > tau) {
+        const double y = rsqrt_nr(d);
+        C[j * k + j] = d * y;
+        invd[j] = y;
+      } else {
+        ok = 0;
+      }
     }
     __syncthreads();
     if (!ok) return false;
-    const double ljj = C[j * k + j];
-    for (int i = j + 1 + threadIdx.x; i < k; i += SM_T) C[i * k + j] /= ljj;
+    const double inv = invd[j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += SM_T) C[i * k + j] *= inv;
     __syncthreads();
     const int w = k - j - 1;   // trailing block (j+1 .. k-1), lower triangle
     for (int e = threadIdx.x; e < w * w; e += SM_T) {
@@ -352,34 +378,28 @@ __device__ bool chol_orth(const double* __restrict__ G, int k, double tau, doubl
     }
     __syncthreads();
   }
-  // L^-1 by forward substitution, one column per thread
-  for (int c = threadIdx.x; c < k; c += SM_T) {
-    for (int i = 0; i < c; ++i) Li[i * k + c] = 0.0;
-    Li[c * k + c] = 1.0 / C[c * k + c];
-    for (int i = c + 1; i < k; ++i) {
-      double s = 0.0;
-      for (int p = c; p < i; ++p) s = fma(C[i * k + p], Li[p * k + c], s);
-      Li[i * k + c] = -s / C[i * k + i];
-    }
-  }
-  __syncthreads();
-  // T_pq = D_p (L^-1)_qp
   for (int e = threadIdx.x; e < k * k; e += SM_T) {
-    const int p = e / k, q = e % k;
-    T[e] = dsc[p] * Li[q * k + p];
+    const int i = e / k, j = e % k;
+    T[e] = j <= i ? C[e] : 0.0;
   }
+  for (int i = threadIdx.x; i < k; i += SM_T) {
+    Tx[i] = dsc[i];
+    Tx[LMAX + i] = invd[i];
+  }
+  if (threadIdx.x == 0) Tx[2 * LMAX] = 1.0;
   return true;
 }
 
 __global__ void __launch_bounds__(SM_T)
-eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, int* kept, int* err) {
+eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, double* Tx, int* kept,
+                int* err) {
   extern __shared__ double smd[];
   const int Np = k + (k & 1);
   double* A = smd;
   double* V = A + (size_t)Np * k;
   double* nrm = V + (size_t)Np * Np;
   int* ord = reinterpret_cast<int*>(nrm + Np + (size_t)Np * Np);
-  if (chol_orth(G, k, tau, A, V, nrm, T)) {
+  if (chol_orth(G, k, tau, A, nrm, T, Tx)) {
     if (threadIdx.x == 0) *kept = k;
     return;
   }
@@ -404,17 +424,18 @@ eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, int*
     for (int j = 0; j < k; ++j)
       if (lmax > 0.0 && nrm[ord[j]] > tau * lmax) ++cnt;
     *kept = cnt;
+    Tx[2 * LMAX] = 0.0;   // T is the map itself
     if (sw > JAC_MAX_SWEEPS - 1) atomicOr(err, ERR_NOTCONV);
   }
 }
 
-void launch_eig_orth(const double* G, int k, double tau, double* T, int* kept, int* err,
+void launch_eig_orth(const double* G, int k, double tau, double* T, double* Tx, int* kept, int* err,
                      cudaStream_t s) {
   note_launch(1);
   int Np = k + (k & 1);
   size_t smem = small_smem(k, Np);
   cudaFuncSetAttribute(eig_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  eig_orth_kernel<<<1, SM_T, smem, s>>>(G, k, tau, T, kept, err);
+  eig_orth_kernel<<<1, SM_T, smem, s>>>(G, k, tau, T, Tx, kept, err);
 }
 
 // ------------------------------------------------------ Rayleigh-Ritz SVD
