@@ -353,3 +353,97 @@ def xtu_sharded(X, U, P):
         a, b = bounds[p], bounds[p + 1]
         out = out + X[a:b].T @ U[a:b]
     return out
+
+
+# --------------------------------------------------------------------------
+# Reduced-precision storage of X (the precision forms; no counterpart in the
+# paper, which computes in one precision throughout).  Plain definitions of
+# the number formats, written from their published specifications, on
+# float64 numbers that hold every value involved exactly.
+E4M3_MAX = 448.0             # OCP FP8 E4M3 ("fn"): largest finite value
+E4M3_MIN_NORMAL = 2.0 ** -6  # exponent field 1
+E4M3_QUANTUM_SUB = 2.0 ** -9  # spacing of the subnormals (exponent field 0)
+TILE_K_MIN, TILE_K_MAX = -100, 100   # limits of the tile scale exponent
+
+
+def e4m3_round(v):
+    """Nearest E4M3 value to each v >= 0, ties to the even significand,
+    values beyond 448 saturated to 448.  E4M3 has 3 mantissa bits and
+    exponent bias 7: normal values 2^(e-7) (1 + m/8), e = 1..15 (e = 15 only
+    up to m = 6), subnormals m 2^-9."""
+    v = np.asarray(v, dtype=np.float64)
+    if np.any(v < 0) or not np.all(np.isfinite(v)):
+        raise ValueError("e4m3_round takes finite v >= 0")
+    out = np.zeros_like(v)
+    sub = v < E4M3_MIN_NORMAL
+    # spacing of the grid at v: 2^(floor(log2 v) - 3) in the normal range
+    e = np.floor(np.log2(np.where(sub, 1.0, v)))
+    # floor(log2) of a float64 power-of-two boundary is exact; guard anyway
+    e = np.where(2.0 ** e > v, e - 1, e)
+    e = np.where(2.0 ** (e + 1) <= v, e + 1, e)
+    quantum = np.where(sub, E4M3_QUANTUM_SUB, 2.0 ** (e - 3))
+    out = np.rint(v / quantum) * quantum       # np.rint: half to even
+    return np.minimum(out, E4M3_MAX)
+
+
+def e4m3_code(q):
+    """The 8-bit code (sign 0) of each E4M3 value q >= 0."""
+    q = np.asarray(q, dtype=np.float64)
+    code = np.zeros(q.shape, dtype=np.int64)
+    sub = q < E4M3_MIN_NORMAL
+    code[sub] = np.rint(q[sub] / E4M3_QUANTUM_SUB).astype(np.int64)
+    qn = q[~sub]
+    e = np.floor(np.log2(qn)).astype(np.int64)
+    m = np.rint((qn / 2.0 ** e - 1.0) * 8).astype(np.int64)
+    code[~sub] = ((e + 7) << 3) | m
+    return code.astype(np.uint8)
+
+
+def bf16_round(x32):
+    """BF16 of FP32 values (the upper 16 bits of the FP32 pattern), round to
+    nearest, ties to even; returned as float64."""
+    b = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def tile_exponent(amax):
+    """Least k with amax <= 448 * 2^k, at least TILE_K_MIN (0 maps to it)."""
+    if amax <= 0:
+        return TILE_K_MIN
+    k = math.ceil(math.log2(amax / E4M3_MAX))
+    while E4M3_MAX * 2.0 ** (k - 1) >= amax:
+        k -= 1
+    while E4M3_MAX * 2.0 ** k < amax:
+        k += 1
+    if k > TILE_K_MAX:
+        raise ValueError("entry beyond 448 * 2^100")
+    return max(k, TILE_K_MIN)
+
+
+def quantize_fp8_tiles(X32, tile=128):
+    """The FP8 form's split of FP32 X, per tile x tile block (I, J):
+    k_IJ = tile_exponent(max of the block); q = e4m3_round(x 2^-k) with
+    values below the smallest normal (2^-6) set to 0; X_hi = q 2^k;
+    X_lo = bf16(x - X_hi).  Returns (codes uint8, k int array, X_hi, X_lo),
+    the last two float64."""
+    X32 = np.asarray(X32, dtype=np.float32)
+    m, n = X32.shape
+    X = X32.astype(np.float64)
+    if np.any(X < 0) or not np.all(np.isfinite(X)):
+        raise ValueError("X must be finite and nonnegative")
+    ti, tj = -(-m // tile), -(-n // tile)
+    K = np.zeros((ti, tj), dtype=np.int64)
+    Q = np.zeros_like(X)
+    for I in range(ti):
+        for J in range(tj):
+            blk = X[I * tile:(I + 1) * tile, J * tile:(J + 1) * tile]
+            k = tile_exponent(float(blk.max()))
+            K[I, J] = k
+            q = e4m3_round(blk * 2.0 ** -k)
+            q[q < E4M3_MIN_NORMAL] = 0.0
+            Q[I * tile:(I + 1) * tile, J * tile:(J + 1) * tile] = q
+    scale = 2.0 ** np.repeat(np.repeat(K, tile, 0), tile, 1)[:m, :n]
+    X_hi = Q * scale
+    X_lo = bf16_round((X - X_hi).astype(np.float32))
+    return e4m3_code(Q), K, X_hi, X_lo

@@ -306,3 +306,113 @@ def test_input_checks():
     X[0, 0] = np.nan
     with pytest.raises(ValueError):
         O.enmf(X, 2, 1)
+
+
+# ---------------------------------------------------------------- FP8 form
+def _e4m3_grid():
+    """Every nonnegative finite E4M3 value, by code, from the format's
+    definition (bias 7, 3 mantissa bits, code 0x7F is NaN)."""
+    vals = []
+    for code in range(127):
+        e, m = code >> 3, code & 7
+        vals.append(m * 2.0 ** -9 if e == 0 else 2.0 ** (e - 7) * (1 + m / 8))
+    return np.array(vals)
+
+
+def test_e4m3_round_is_nearest_with_ties_to_even():
+    """Brute force over the 127-value grid: the nearest value, ties to the
+    even code (= even significand); the grid's ends and codes round-trip."""
+    grid = _e4m3_grid()
+    assert grid[0] == 0 and grid[1] == 2.0 ** -9 and grid[8] == 2.0 ** -6 and grid[-1] == 448
+    assert np.all(np.diff(grid) > 0)
+    np.testing.assert_array_equal(O.e4m3_round(grid), grid)
+    np.testing.assert_array_equal(O.e4m3_code(grid), np.arange(127, dtype=np.uint8))
+    mids = 0.5 * (grid[:-1] + grid[1:])
+    even = np.where(np.arange(126) % 2 == 0, grid[:-1], grid[1:])
+    np.testing.assert_array_equal(O.e4m3_round(mids), even)
+    rng = np.random.default_rng(7)
+    v = np.concatenate([rng.uniform(0, 448, 4000), 2.0 ** rng.uniform(-12, 8.8, 4000)])
+    d = np.abs(v[:, None] - grid[None, :])
+    best = grid[np.argmin(d, axis=1)]
+    np.testing.assert_array_equal(O.e4m3_round(v), best)   # no exact ties in random data
+    assert np.all(O.e4m3_round(np.array([460.0, 1e6])) == 448)
+
+
+def test_e4m3_round_matches_torch_cast():
+    """Library pin: torch's float8_e4m3fn cast (round to nearest even)."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8_e4m3fn")
+    rng = np.random.default_rng(8)
+    v = np.concatenate([2.0 ** rng.uniform(-11, 8.8, 20000), 0.5 * (_e4m3_grid()[:-1] + _e4m3_grid()[1:])])
+    v = v.astype(np.float32).astype(np.float64)
+    t = torch.tensor(v, dtype=torch.float32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.e4m3_round(v), t)
+
+
+def test_bf16_round_is_nearest_with_ties_to_even():
+    """Brute force between the two BF16 neighbours of each FP32 value, and
+    the library cast of torch."""
+    rng = np.random.default_rng(9)
+    x = (rng.standard_normal(20000) * 10.0 ** rng.uniform(-30, 30, 20000)).astype(np.float32)
+    b = x.view(np.uint32)
+    lo = (b & 0xFFFF0000).view(np.float32).astype(np.float64)
+    hi_bits = (b & 0xFFFF0000) + 0x10000
+    hi = hi_bits.astype(np.uint32).view(np.float32).astype(np.float64)
+    xd = x.astype(np.float64)
+    dl, dh = np.abs(xd - lo), np.abs(hi - xd)
+    lo_even = ((b >> 16) & 1) == 0
+    want = np.where(dl < dh, lo, np.where(dh < dl, hi, np.where(lo_even, lo, hi)))
+    np.testing.assert_array_equal(O.bf16_round(x), want)
+    ties = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8], dtype=np.float32)   # exact midpoints
+    np.testing.assert_array_equal(O.bf16_round(ties), [1.0, 1 + 2 ** -6])
+    torch = pytest.importorskip("torch")
+    t = torch.tensor(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.bf16_round(x), t)
+
+
+def test_tile_exponent_is_least_power_covering_the_tile():
+    rng = np.random.default_rng(10)
+    for a in np.concatenate([2.0 ** rng.uniform(-60, 60, 300), [448.0, 449.0, 1.0, 0.875]]):
+        k = O.tile_exponent(float(a))
+        assert a <= 448 * 2.0 ** k and (a > 448 * 2.0 ** (k - 1) or k == O.TILE_K_MIN)
+    assert O.tile_exponent(0.0) == O.TILE_K_MIN
+    assert O.tile_exponent(448 * 2.0 ** -120) == O.TILE_K_MIN
+    with pytest.raises(ValueError):
+        O.tile_exponent(448 * 2.0 ** 101)
+
+
+def test_fp8_tile_split_bounds_and_per_tile_scales():
+    """Per tile the scaled maximum lies in (224, 448]; |X - X_hi| <=
+    2^-4 max(X, 2^(k-6)) where the code is normal, X < 2^(k-6) where it was
+    flushed; X_lo is X - X_hi
+    to BF16 (relative 2^-9); tiles of very different magnitude on a ragged,
+    non-square X get their own exponents (a transposed tile index fails)."""
+    rng = np.random.default_rng(11)
+    m, n = 300, 200
+    X = rng.random((m, n)) ** 3
+    X[:128, 128:] *= 2.0 ** 20          # tile (0, 1)
+    X[256:, :128] *= 2.0 ** -30         # tile (2, 0)
+    X[128:256, :] *= 0.0                # tile row 1 all zero
+    X32 = X.astype(np.float32)
+    codes, K, Xh, Xl = O.quantize_fp8_tiles(X32)
+    assert K.shape == (3, 2) and codes.shape == (m, n)
+    Xd = X32.astype(np.float64)
+    for I in range(3):
+        for J in range(2):
+            blk = Xd[I * 128:(I + 1) * 128, J * 128:(J + 1) * 128]
+            if blk.max() > 0:
+                assert 224 < blk.max() * 2.0 ** -K[I, J] <= 448
+    assert K[1, 0] == K[1, 1] == O.TILE_K_MIN
+    assert K[0, 1] - K[0, 0] in (19, 20, 21) and K[0, 0] - K[2, 0] in (29, 30, 31)
+    kk = np.repeat(np.repeat(K, 128, 0), 128, 1)[:m, :n].astype(float)
+    err = np.abs(Xd - Xh)
+    normal = codes >= 8
+    # half a quantum: 2^-4 of the binade's start, which for values just
+    # under 2^-6 (rounded up to the smallest normal) is 2^(k-6)
+    assert np.all(err[normal] <= 2.0 ** -4 * np.maximum(Xd[normal], 2.0 ** (kk[normal] - 6)))
+    assert np.all(codes[~normal] == 0) and np.all(Xh[~normal] == 0)
+    assert np.all(Xd[~normal] < 2.0 ** (kk[~normal] - 6))
+    assert np.all(np.abs(Xd - Xh - Xl) <= 2.0 ** -8 * err)   # BF16: 8 significant bits
+    # decoding the codes gives X_hi
+    np.testing.assert_array_equal(_e4m3_grid()[codes] * 2.0 ** kk, Xh)
