@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f32", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-fp8", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=64)
     return ap.parse_args()
 
@@ -224,6 +225,69 @@ def replica_throughput(total_ms, steps, world, device="cpu"):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     return total_ms, world * steps / (total_ms / 1e3)
+
+
+FP8_WORKLOAD = "spectrogram 1025x131072 r=64, 200 alternations"
+
+
+def fp8_leg():
+    """Precision form, large: the spectrogram-shaped workload (1025 x 131072,
+    r = 64; harmonic templates x sparse activations, Gamma(0.5) modulation)
+    solved with X streamed as FP8 (E4M3 codes, per-tile power-of-two scales,
+    BF16 X_lo every 10 alternations), as BF16, and in the FP32 SIMT form.
+    Per form: one warm solve, then one timed solve (SVD start, rotation, 200
+    alternations, direct residual), its final relative error, and for the
+    tensor-core forms the X_hi sweep's live CUDA-event time (every fourth
+    alternation) as achieved GB/s of its algorithmic bytes (m n x bytes per
+    element) over the measured HBM copy bandwidth."""
+    import torch
+
+    import synth
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+
+    X, r = synth.spectrogram(seed=0, dtype=np.float32)
+    m, n = X.shape
+    Xd = torch.as_tensor(X, device="cuda")
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    out = {"workload": FP8_WORKLOAD, "m": m, "n": n, "r": r, "iterations": 200}
+    for name, xs, esize in (("fp8", torch.float8_e4m3fn, 1), ("bf16", torch.bfloat16, 2),
+                            ("f32", None, 4)):
+        s = Solver(Xd, r, x_stream=xs)
+
+        def solve():
+            s.svd_init()
+            s.rotate()
+            s.iterate(200, trace=False, reset=1, sync_info=0)
+            return s.residual(direct=True)[1]
+
+        solve()
+        torch.cuda.synchronize()
+        if xs is not None:
+            B.enmf_profile(s.ctx, 4)
+            B.enmf_profile_read(s.ctx, reset=1)
+        t0 = time.perf_counter()
+        rel = solve()
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        rec = {"ms_per_solve": ms, "rel_err": rel}
+        if xs is not None:
+            sweep_ms, sweeps = B.enmf_profile_read(s.ctx, reset=1)
+            B.enmf_profile(s.ctx, 0)
+            if sweeps:
+                us = 1e3 * sweep_ms / sweeps
+                gbs = m * n * esize / (us * 1e-6) / 1e9
+                rec.update({"sweep_us_avg": us, "sweeps_timed": sweeps,
+                            "sweep_achieved_gbs": gbs, "sweep_frac_of_measured_hbm": gbs / hbm,
+                            "algorithmic_bytes_per_sweep": m * n * esize})
+        out[name] = rec
+        s.close()
+    ref = out["f32"]["rel_err"]
+    for name in ("fp8", "bf16"):
+        out[name]["rel_err_gap_vs_f32"] = abs(out[name]["rel_err"] - ref) / ref
+    out["speedup_fp8_vs_bf16"] = out["bf16"]["ms_per_solve"] / out["fp8"]["ms_per_solve"]
+    return out
 
 
 def serving_leg(n_req):
@@ -456,6 +520,9 @@ def run_ours(args):
     serving = None
     if world == 1 and not args.no_serve and args.serve_requests > 0:
         serving = serving_leg(args.serve_requests)
+    fp8 = None
+    if world == 1 and not args.no_fp8:
+        fp8 = fp8_leg()
 
     ttt = None
     if "f64" in others or form == "f64":
@@ -480,7 +547,7 @@ def run_ours(args):
             "p50_ms": statistics.median(step_ms), "p99_ms": p99,
             "time_to_target": ttt, "final": {"rel_err": rel, "kkt_pg_rel": kk.pg_rel},
             "other_forms": others, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-            "clocks": clk, "gpu_launches": launches, "serving": serving}
+            "clocks": clk, "gpu_launches": launches, "serving": serving, "fp8_form": fp8}
     print(json.dumps(line))
     if world > 1:
         dist.barrier()

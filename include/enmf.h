@@ -64,7 +64,8 @@ typedef enum {
  *   FP32:        X F32, factors F32 (FP32 arithmetic, FP64 scalar sums);
  *   BF16 / F16:  X BF16 or F16, factors F32; X products on the tensor cores
  *                with FP32 accumulation. */
-typedef enum { ENMF_F64 = 0, ENMF_F32 = 1, ENMF_BF16 = 2, ENMF_F16 = 3 } enmf_dtype;
+typedef enum { ENMF_F64 = 0, ENMF_F32 = 1, ENMF_BF16 = 2, ENMF_F16 = 3,
+               ENMF_E4M3 = 4 /* stream type only: OCP FP8 E4M3 codes */ } enmf_dtype;
 
 /* Largest supported rank (the SVD start works on r + oversample <= 80). */
 #define ENMF_MAX_RANK 64
@@ -87,6 +88,10 @@ typedef struct {
                     /*   core sweeps on X as given (no correction).  F32      */
                     /*   factors required; with FP16 the factor entries must  */
                     /*   stay within the FP16 range.                          */
+                    /*   ENMF_E4M3 with F32 X: the FP8 form -- X_hi is e4m3   */
+                    /*   codes with a power-of-two scale per 128 x 128 tile   */
+                    /*   and X_lo = bf16(X - X_hi) (see enmf_stage_x); X must */
+                    /*   stay <= 448 * 2^100.                                 */
 } enmf_problem;
 
 typedef struct enmf_ctx enmf_ctx;
@@ -220,6 +225,27 @@ enmf_status enmf_kkt(enmf_ctx* ctx, const void* X, const void* U, const void* V,
  * (ENMF_ESTATE otherwise).  ENMF_EDOMAIN if X has a negative or non-finite
  * entry.  Enqueued on the context stream. */
 enmf_status enmf_stage_x(enmf_ctx* ctx, const void* X);
+/* With stream_dtype = ENMF_E4M3 (the FP8 form, with per-tile scaling; no
+ * counterpart in the paper), staging splits F32 X per 128 x 128 tile
+ * (I, J) -- the last tiles of a ragged X are partial:
+ *   k_IJ = the least integer with max(tile) <= 448 * 2^k, at least -100;
+ *   q = e4m3(x * 2^-k) rounded to nearest even, with codes below 8 (values
+ *       under 2^-6, the E4M3 subnormals) replaced by 0;
+ *   X_hi = q * 2^k (exact in BF16), X_lo = bf16(x - X_hi), round to nearest
+ *       even.
+ * The sweeps stream the one-byte codes; X_lo is applied like the 16-bit
+ * forms' X_lo.  ENMF_EDOMAIN (at the next sync) for a negative or non-finite
+ * entry, or one beyond 448 * 2^100.
+ *
+ * enmf_stage_copy copies the staged decomposition of the tensor-core forms
+ * to caller buffers (device or host, told apart by the CUDA runtime; any may
+ * be NULL) and synchronises the context stream: hi = X_hi as m x n dense
+ * elements (BF16 / FP16 bits, or e4m3 codes), lo = X_lo as m x n dense
+ * 16-bit elements, tile_exp = the ceil(m/128) x ceil(n/128) exponents k
+ * (FP8 form only).  ENMF_ESTATE before staging; ENMF_EINVAL for a buffer the
+ * form does not have (lo with 16-bit X given as is, tile_exp outside the FP8
+ * form).  For inspection and tests; no counterpart in the paper. */
+enmf_status enmf_stage_copy(enmf_ctx* ctx, void* hi, void* lo, int32_t* tile_exp);
 
 /* ---- The core NMF kernel (App. I): X V and X^T U --------------------------
  * XV (m x r) = X V and XtU (n x r) = X^T U in the context's form, FP32 or

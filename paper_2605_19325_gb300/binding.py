@@ -13,7 +13,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libenmf.so")
 
-ENMF_F64, ENMF_F32, ENMF_BF16, ENMF_F16 = 0, 1, 2, 3
+ENMF_F64, ENMF_F32, ENMF_BF16, ENMF_F16, ENMF_E4M3 = 0, 1, 2, 3, 4
 ENMF_MAX_RANK = 64
 ENMF_RESIDUAL_NOALLOC_MAX_ROWS = 262144
 
@@ -88,6 +88,7 @@ _SIGS = {
                              C.POINTER(enmf_svd_opts), C.POINTER(enmf_admm_opts),
                              C.POINTER(enmf_iter_opts), C.POINTER(C.c_double)]),
     "enmf_stage_x": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "enmf_stage_copy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "enmf_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_int32]),
     "enmf_profile": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -187,6 +188,12 @@ def enmf_rotate(ctx, U, V, R=None, opts=None):
 
 def enmf_stage_x(ctx, X):
     check(lib().enmf_stage_x(ctx, _ptr(X)), "enmf_stage_x")
+
+
+def enmf_stage_copy(ctx, hi=None, lo=None, tile_exp=None):
+    """Copy the staged X_hi / X_lo (m x n dense) and, in the FP8 form, the
+    per-tile exponents (int32) into the given tensors (any may be None)."""
+    check(lib().enmf_stage_copy(ctx, _ptr(hi), _ptr(lo), _ptr(tile_exp)), "enmf_stage_copy")
 
 
 def enmf_sweep(ctx, X, U, V, XV=None, XtU=None, exact=1):

@@ -41,10 +41,10 @@ extern "C" const char* enmf_status_string(enmf_status s) {
 
 extern "C" const char* enmf_version(void) { return "enmf-gb300 0.1"; }
 
-// Tensor-core (BF16 stream) form?
-// Tensor-core (16-bit stream) form?  BF16 or FP16 X in the sweeps.
+// Tensor-core form?  BF16 or FP16 X, or e4m3 codes (FP8 form), in the sweeps.
 static bool tc_form(const enmf_problem* p) {
-  return p->stream_dtype == ENMF_BF16 || p->stream_dtype == ENMF_F16;
+  return p->stream_dtype == ENMF_BF16 || p->stream_dtype == ENMF_F16 ||
+         p->stream_dtype == ENMF_E4M3;
 }
 
 static bool valid_problem(const enmf_problem* p) {
@@ -56,6 +56,7 @@ static bool valid_problem(const enmf_problem* p) {
     if (p->f_dtype != ENMF_F32) return false;
     // F32 X (split into a 16-bit pair) or X already of the stream type
     if (p->x_dtype != ENMF_F32 && p->x_dtype != p->stream_dtype) return false;
+    // the FP8 form is staged from F32 X only
     if (p->x_dtype != ENMF_F32 && (p->ldx % 8) != 0) return false;
     if (p->m > 0x7fffffffLL || p->n > 0x7fffffffLL) return false;
   } else if (p->stream_dtype != 0 && p->stream_dtype != p->x_dtype) {
@@ -68,9 +69,9 @@ static bool valid_problem(const enmf_problem* p) {
 // Tensor-core buffers of the precision form (a separate allocation).
 struct TcPlan {
   int rp;
-  int64_t ldh, ldn, ldm;
+  int64_t ldh, ldn, ldm, ldq;
   int sv, st;          // split arguments for X V and X^T U
-  size_t xh, vt, ut, part, cv, cu, desc, total;
+  size_t xh, xl, xs, vt, ut, part, cv, cu, desc, total;
 };
 
 static TcPlan tc_plan(const enmf_problem* p, int num_sms) {
@@ -84,7 +85,17 @@ static TcPlan tc_plan(const enmf_problem* p, int num_sms) {
   t.ldm = (m + 7) / 8 * 8;
   t.sv = tc_grid(m, n, 0, num_sms);
   t.st = tc_grid(n, m, 1, num_sms);
-  t.xh = p->x_dtype == ENMF_F32 ? (size_t)m * t.ldh * 2 : 0;
+  t.ldq = (n + 15) / 16 * 16;
+  if (p->stream_dtype == ENMF_E4M3) {
+    // codes, X_lo in BF16, one int exponent per 128 x 128 tile
+    t.xh = (size_t)m * t.ldq;
+    t.xl = (size_t)m * t.ldh * 2;
+    t.xs = (size_t)((m + 127) / 128) * ((n + 127) / 128) * 4;
+  } else {
+    t.xh = p->x_dtype == ENMF_F32 ? (size_t)m * t.ldh * 2 : 0;
+    t.xl = t.xh;
+    t.xs = 0;
+  }
   t.vt = (size_t)t.rp * t.ldn * 2;
   t.ut = (size_t)t.rp * t.ldm * 2;
   // stream-K partial slots: grid x 2 x 128 rows x rp, and one arrival counter
@@ -95,8 +106,8 @@ static TcPlan tc_plan(const enmf_problem* p, int num_sms) {
   t.cu = (size_t)n * p->r * 4;
   t.desc = 8 * sizeof(SweepProb);
   auto a = [](size_t b) { return (b + 1023) & ~(size_t)1023; };
-  t.total = 2 * a(t.xh) + 2 * a(t.vt) + 2 * a(t.ut) + a(t.part) + a(t.cv) + a(t.cu) + a(t.desc) +
-            1024;
+  t.total = a(t.xh) + a(t.xl) + a(t.xs) + 2 * a(t.vt) + 2 * a(t.ut) + a(t.part) + a(t.cv) +
+            a(t.cu) + a(t.desc) + 1024;
   return t;
 }
 
@@ -276,7 +287,10 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
     char* q = (char*)(((uintptr_t)ctx->tcws + 1023) & ~(uintptr_t)1023);
     auto grab = [&](size_t bytes) { void* o = q; q += (bytes + 1023) & ~(size_t)1023; return o; };
     ctx->own_xh = t.xh ? grab(t.xh) : nullptr;
-    ctx->xl = t.xh ? grab(t.xh) : nullptr;
+    ctx->xl = t.xl ? grab(t.xl) : nullptr;
+    ctx->xexp = t.xs ? (int*)grab(t.xs) : nullptr;
+    ctx->xq = p->stream_dtype == ENMF_E4M3;
+    ctx->ldq = t.ldq;
     ctx->vth = grab(t.vt);
     ctx->vtl = grab(t.vt);
     ctx->uth = grab(t.ut);
@@ -315,7 +329,19 @@ extern "C" enmf_status enmf_stage_x(enmf_ctx* ctx, const void* X) {
   if (ctx->poison) return ctx->poison;
   if (!ctx->tc) return ENMF_ESTATE;
   const enmf_problem& p = ctx->p;
-  if (p.x_dtype == ENMF_F32) {
+  if (ctx->xq) {
+    launch_quant_x((const float*)X, p.m, p.n, p.ldx, ctx->own_xh, ctx->ldq, ctx->xl, ctx->ldh,
+                   ctx->xexp, ctx->err, ctx->stream);
+    if (cudaGetLastError() != cudaSuccess) {
+      ctx->poison = ENMF_ECUDA;
+      return ENMF_ECUDA;
+    }
+    ctx->xh = ctx->own_xh;
+    // codes: one 128 x 128 box per unit; X_lo: two 64-column BF16 boxes
+    if (!tc_make_map(ctx->maps[MAP_XH], ctx->xh, p.m, p.n, ctx->ldq, 128, 128, TC_MAP_U8) ||
+        !tc_make_map(ctx->maps[MAP_XL], ctx->xl, p.m, p.n, ctx->ldh, 64, 128, 0))
+      return ENMF_ECUDA;
+  } else if (p.x_dtype == ENMF_F32) {
     launch_split_x((const float*)X, p.m, p.n, p.ldx, ctx->own_xh, ctx->xl, ctx->ldh, ctx->tf16,
                    ctx->err,
                    ctx->stream);
@@ -637,6 +663,11 @@ static const SweepProb* tc_desc(enmf_ctx* ctx, int slot, int mode, bool lo, floa
   d.out = out;
   d.corr = corr;
   d.f16 = ctx->tf16;
+  if (ctx->xq && !lo) {
+    d.xq = 1;
+    d.ntj = (int)((p.n + 127) / 128);
+    d.xexp = ctx->xexp;
+  }
   if (memcmp(&d, &ctx->hprob[slot], sizeof(d)) != 0) {
     ctx->hprob[slot] = d;
     cudaMemcpyAsync(ctx->dprob + slot, &ctx->hprob[slot], sizeof(d), cudaMemcpyHostToDevice,
@@ -688,7 +719,7 @@ static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int
                                (corr >= 1 && ctx->xl) ? ctx->cv : nullptr);
   prof_mark(ctx, rec);
   launch_tc_group(0, ctx->rp, d, 1, tc_units(ctx, 0), ctx->tcpart, ctx->tccount, ctx->num_sms,
-                  ctx->err, s, fixup ? 1 : 0);
+                  ctx->err, s, fixup ? 1 : 0, ctx->xq);
   prof_mark(ctx, rec);
 }
 
@@ -715,13 +746,36 @@ static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, in
                                (corr >= 1 && ctx->xl) ? ctx->cu : nullptr);
   prof_mark(ctx, rec);
   launch_tc_group(1, ctx->rp, d, 1, tc_units(ctx, 1), ctx->tcpart, ctx->tccount, ctx->num_sms,
-                  ctx->err, s, fixup ? 1 : 0);
+                  ctx->err, s, fixup ? 1 : 0, ctx->xq);
   prof_mark(ctx, rec);
 }
 
 static enmf_status check_staged(enmf_ctx* ctx, const void* X) {
   if (ctx->tc && ctx->staged_src != X) return ENMF_ESTATE;
   return ENMF_OK;
+}
+
+// The staged decomposition, copied out densely (inspection and tests).
+extern "C" enmf_status enmf_stage_copy(enmf_ctx* ctx, void* hi, void* lo, int32_t* tile_exp) {
+  GUARD(ctx);
+  if (!ctx->tc || !ctx->staged_src) return ENMF_ESTATE;
+  if ((lo && !ctx->xl) || (tile_exp && !ctx->xq)) return ENMF_EINVAL;
+  const enmf_problem& p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  if (hi) {
+    const size_t es = ctx->xq ? 1 : 2;
+    const int64_t ld = ctx->xh == ctx->own_xh ? (ctx->xq ? ctx->ldq : ctx->ldh) : p.ldx;
+    CK(cudaMemcpy2DAsync(hi, (size_t)p.n * es, ctx->xh, (size_t)ld * es, (size_t)p.n * es,
+                         (size_t)p.m, cudaMemcpyDefault, s));
+  }
+  if (lo)
+    CK(cudaMemcpy2DAsync(lo, (size_t)p.n * 2, ctx->xl, (size_t)ctx->ldh * 2, (size_t)p.n * 2,
+                         (size_t)p.m, cudaMemcpyDefault, s));
+  if (tile_exp) {
+    const size_t tiles = (size_t)((p.m + 127) / 128) * (size_t)((p.n + 127) / 128);
+    CK(cudaMemcpyAsync(tile_exp, ctx->xexp, tiles * 4, cudaMemcpyDefault, s));
+  }
+  return sync_status(ctx);
 }
 
 extern "C" enmf_status enmf_sweep(enmf_ctx* ctx, const void* X, const void* U, const void* V,

@@ -258,6 +258,7 @@ extern "C" enmf_status enmf_batch_add(enmf_batch* b, enmf_ctx* ctx, const void* 
   if (!b || !ctx || !X || !U || !V || !slot) return ENMF_EINVAL;
   if (ctx->poison) return ctx->poison;
   if (!ctx->tc || ctx->staged_src != X) return ENMF_ESTATE;
+  if (ctx->xq) return ENMF_EINVAL;   // the FP8 form iterates alone
   const int rp = tc_rank_pad(ctx->p.r);
   if (b->rp && rp != b->rp) return ENMF_EINVAL;
   if (b->n_active >= half_group_capacity(rp, b->num_sms)) return ENMF_EBUSY;

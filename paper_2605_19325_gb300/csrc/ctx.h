@@ -76,6 +76,9 @@ struct enmf_ctx {
   // precision form (tensor-core sweeps on BF16 or FP16 X)
   int tc;
   int tf16;                 // the 16-bit type is FP16 (else BF16)
+  int xq;                   // FP8 form: X_hi as e4m3 codes, per-tile exponents
+  int* xexp;                // FP8 form: exponent of each 128 x 128 tile of X
+  int64_t ldq;              // FP8 form: row stride of the codes (bytes)
   int rp;
   int64_t ldh, ldn, ldm;
   int sv, st_split;

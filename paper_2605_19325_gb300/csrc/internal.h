@@ -220,7 +220,9 @@ struct alignas(64) SweepProb {
   const float* corr;
   int r;
   int f16;          // X and factor as FP16 (else BF16)
-  int pad_[2];
+  int xq;           // X as e4m3 codes with per-tile exponents (the FP8 form)
+  int ntj;          // FP8 form: column tiles of X (exponent row stride)
+  const int* xexp;  // FP8 form: exponent k of each 128 x 128 tile of X
 };
 // Fills the sizes of d (maps and pointers set by the caller) and returns its
 // work units (tiles x k-blocks) and tiles through *units / *tiles.
@@ -231,11 +233,15 @@ void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r,
 // int per tile of all problems (zero between launches).
 // fixup = 0 (one problem only): tiles cut by the stream-K ranges are left as
 // partial slots for the consumer (see CutTiles).
+// xq = 1: the FP8-form kernel (every descriptor's X is e4m3 codes).
 void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
-                     int* counters, int num_sms, int* err, cudaStream_t s, int fixup = 1);
+                     int* counters, int num_sms, int* err, cudaStream_t s, int fixup = 1,
+                     int xq = 0);
 int tc_group_grid(int64_t W, int num_sms);
 // 2D BF16 tensor map (CUtensorMap, 128 bytes at `map`) over a row-major
 // (rows x cols, ld) array, box box_cols x box_rows, 128-byte swizzle.
+// f16 = TC_MAP_U8: one-byte elements (FP8 codes).
+constexpr int TC_MAP_U8 = 2;
 bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
                  int box_cols, int box_rows, int f16 = 0);
 int tc_rank_pad(int r);
@@ -247,6 +253,11 @@ void launch_split_transpose(const float* F, int64_t rows, int r, void* hi, void*
                             int f16, cudaStream_t s);
 void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh, void* xl,
                     int64_t ldh, int f16, int* err, cudaStream_t s);
+// FP8 form staging: e4m3 codes (m x ldq bytes), X_lo (BF16, m x ldh) and one
+// exponent per 128 x 128 tile (row-major over tiles); ERR_DOMAIN for a
+// negative or non-finite entry or one beyond 448 * 2^100.
+void launch_quant_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xq, int64_t ldq,
+                    void* xl, int64_t ldh, int* xexp, int* err, cudaStream_t s);
 constexpr int TC_KB_XV = 128, TC_KB_XT = 128;
 
 // KKT finalisation: combine the two factors' partial measures.

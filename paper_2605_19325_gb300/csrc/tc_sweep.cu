@@ -19,9 +19,19 @@
 // accumulators let the epilogue of one tile overlap the MMAs of the next.
 // The sweep reads X once per product, so at small rank it is bound by HBM
 // bandwidth: algorithmic bytes per sweep = m n * 2.
+//
+// FP8 stream form (XQ): X_hi is held as e4m3 codes with one power-of-two
+// scale 2^k per 128 x 128 tile of X.  TMA streams the one-byte codes (half
+// the bytes of BF16); four converter warps rebuild each tile in shared
+// memory as the exact BF16 values q 2^k, in the same swizzled layout a TMA
+// copy of a BF16 tile would have, and the MMA path is the BF16 one.  The
+// factor's hi and lo rows sit side by side so that one MMA with N = 2 RP
+// covers both (the X tile is read once per K step).  Algorithmic bytes per
+// sweep = m n.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include "internal.h"
@@ -34,6 +44,9 @@ constexpr int TILE = 128;     // output rows per CTA (UMMA M)
 constexpr int KB_XV = 128;    // reduction columns per stage, X V (two 64-column boxes)
 constexpr int KB_XT = 128;    // reduction rows per stage, X^T U
 constexpr int THREADS = 192;  // warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 epilogue
+constexpr int THREADS_XQ = 320;  // the same, plus warps 6-9 converting FP8 tiles to BF16
+constexpr int NCW = 4;           // converter warps of the FP8 form
+constexpr uint32_t Q_BYTES = 128 * 128;  // one FP8 X tile (128 x 128 codes)
 constexpr long long WAIT_BUDGET = 4000000000LL;  // cycles (~2 s)
 constexpr int MAX_GRID = 256;  // CTAs of the persistent sweep at most
 
@@ -182,21 +195,33 @@ struct ProbView {
 // Per problem (SweepProb): X map, the factor transposed as a BF16 pair
 // (mapBh / mapBl, RP x red), out (rows_out x r, FP32) receiving whole tiles
 // (+ corr when given).  part [G][2][TILE][RP] receives the partial segments.
-template <int MODE, int RP>
-__global__ void __launch_bounds__(THREADS, 1)
+// XQ: the FP8 stream form (X tiles as e4m3 codes with per-tile exponents,
+// see the file comment); qstages = depth of its FP8 tile ring.
+template <int MODE, int RP, bool XQ = false>
+__global__ void __launch_bounds__(XQ ? THREADS_XQ : THREADS, 1)
 sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stages,
-                float* __restrict__ part, int* __restrict__ counters, int fixup, int* err) {
+                float* __restrict__ part, int* __restrict__ counters, int fixup, int* err,
+                int qstages) {
   constexpr int KB = MODE == 0 ? KB_XV : KB_XT;
   constexpr uint32_t A_BYTES = TILE * KB * 2;                 // 16 KB or 32 KB
   constexpr uint32_t B_BYTES = RP * KB * 2;                   // one of hi / lo
   constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
   constexpr uint32_t IDESC_BF16 = idesc_f16kind(TILE, RP, MODE, 0);
   constexpr uint32_t IDESC_F16 = idesc_f16kind(TILE, RP, MODE, 1);
-  constexpr uint32_t TMEM_COLS = RP <= 32 ? 64 : 128;        // two accumulators
+  // XQ: one MMA over [hi | lo] rows of the factor (N = 2 RP) into an
+  // accumulator of 2 RP columns (hi and lo products summed in the epilogue)
+  constexpr uint32_t IDESC_XQ = idesc_f16kind(TILE, 2 * RP, MODE, 0);
+  constexpr uint32_t ACC_COLS = XQ ? 2 * RP : RP;
+  constexpr uint32_t TMEM_COLS =
+      XQ ? (RP <= 16 ? 64 : (RP <= 32 ? 128 : 256)) : (RP <= 32 ? 64 : 128);  // two accumulators
+  constexpr int QB = XQ ? 8 : 1;
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[8];
   __shared__ __align__(8) uint64_t empty_bar[8];
+  __shared__ __align__(8) uint64_t bfull_bar[QB];    // XQ: factor tiles of a stage landed
+  __shared__ __align__(8) uint64_t qfull_bar[QB];    // XQ: FP8 tile landed
+  __shared__ __align__(8) uint64_t qempty_bar[QB];   // XQ: FP8 tile consumed
   __shared__ __align__(8) uint64_t accf_bar[2];
   __shared__ __align__(8) uint64_t acce_bar[2];
   __shared__ __align__(8) uint64_t drain_bar;
@@ -218,8 +243,16 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       prefetch_map(reinterpret_cast<const CUtensorMap*>(probs[p0].mapBl));
     }
     for (int s = 0; s < stages; ++s) {
-      mbar_init(&full_bar[s], 1);
+      // XQ: a stage's X tile is complete when every converter warp arrived
+      mbar_init(&full_bar[s], XQ ? NCW : 1);
       mbar_init(&empty_bar[s], 1);
+      if constexpr (XQ) mbar_init(&bfull_bar[s], 1);
+    }
+    if constexpr (XQ) {
+      for (int q = 0; q < qstages; ++q) {
+        mbar_init(&qfull_bar[q], 1);
+        mbar_init(&qempty_bar[q], NCW);
+      }
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf_bar[b], 1);
@@ -256,6 +289,24 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
           prefetch_map(reinterpret_cast<const CUtensorMap*>(pv.d->mapBl));
         }
         const CUtensorMap* mapX = reinterpret_cast<const CUtensorMap*>(pv.d->mapX);
+        if constexpr (XQ) {
+          // FP8 tile ring only (the converter loads the factor tiles of the
+          // stage it fills): one 128 x 128 box of codes per unit
+          const int q = (int)(i % qstages);
+          const uint32_t qph = (uint32_t)(i / qstages) & 1u;
+          if (!mbar_wait(&qempty_bar[q], qph ^ 1u, err)) {
+            aborted = 1;
+            break;
+          }
+          const int64_t lw = w - pv.wb;
+          const int t0 = (int)((lw / pv.nkb) * TILE);
+          const int k0 = (int)((lw % pv.nkb) * KB);
+          uint8_t* sq = smem + (size_t)stages * STAGE + (size_t)q * Q_BYTES;
+          mbar_expect_tx(&qfull_bar[q], Q_BYTES);
+          if (MODE == 0) tma_load(sq, mapX, &qfull_bar[q], k0, t0);
+          else tma_load(sq, mapX, &qfull_bar[q], t0, k0);
+          continue;
+        }
         const CUtensorMap* mapBh = reinterpret_cast<const CUtensorMap*>(pv.d->mapBh);
         const CUtensorMap* mapBl = reinterpret_cast<const CUtensorMap*>(pv.d->mapBl);
         const int s = (int)(i % stages);
@@ -288,8 +339,13 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       if (aborted) {
         // let copies already issued land before the CTA can exit
         const int64_t issued = i;
-        for (int64_t q = issued - stages < 0 ? 0 : issued - stages; q < issued; ++q)
-          mbar_wait(&full_bar[q % stages], (uint32_t)(q / stages) & 1u, err);
+        if constexpr (XQ) {
+          for (int64_t q = issued - qstages < 0 ? 0 : issued - qstages; q < issued; ++q)
+            mbar_wait(&qfull_bar[q % qstages], (uint32_t)(q / qstages) & 1u, err);
+        } else {
+          for (int64_t q = issued - stages < 0 ? 0 : issued - stages; q < issued; ++q)
+            mbar_wait(&full_bar[q % stages], (uint32_t)(q / stages) & 1u, err);
+        }
       }
     }
   } else if (warp == 1) {
@@ -311,13 +367,13 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t dcol = tmem + (uint32_t)(b * RP);
+        const uint32_t dcol = tmem + (uint32_t)(b * ACC_COLS);
         const uint32_t idesc = pv.d->f16 ? IDESC_F16 : IDESC_BF16;
         uint32_t accum = 0;
         for (; w < wend; ++w, ++i) {
           const int s = (int)(i % stages);
           const uint32_t ph = (uint32_t)(i / stages) & 1u;
-          if (!mbar_wait(&full_bar[s], ph, err)) {
+          if (!mbar_wait(&full_bar[s], ph, err) || (XQ && !mbar_wait(&bfull_bar[s], ph, err))) {
             aborted = 1;
             break;
           }
@@ -325,6 +381,24 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
           const uint32_t a0 = saddr(smem + (size_t)s * STAGE);
           const uint32_t bh0 = a0 + A_BYTES;
           const uint32_t bl0 = bh0 + B_BYTES;
+          if constexpr (XQ) {
+            // B region: [hi K 0-63 | lo K 0-63 | hi K 64-127 | lo K 64-127],
+            // each RP rows of 128 bytes, so the 2 RP rows of one 64-wide K
+            // atom are contiguous 8-row groups (stride 1024 bytes)
+#pragma unroll
+            for (int kk = 0; kk < KB / 16; ++kk) {
+              uint64_t da;
+              if (MODE == 0) {
+                const uint32_t aoff = (uint32_t)(kk / 4) * (A_BYTES / 2) + (uint32_t)(kk % 4) * 32;
+                da = sdesc(a0 + aoff, 16, 1024);
+              } else {
+                da = sdesc(a0 + kk * 2048, A_BYTES / 2, 1024);
+              }
+              const uint32_t boff = (uint32_t)(kk / 4) * B_BYTES + (uint32_t)(kk % 4) * 32;
+              mma_f16kind(dcol, da, sdesc(bh0 + boff, 16, 1024), IDESC_XQ, accum);
+              accum = 1u;
+            }
+          } else {
 #pragma unroll
           for (int kk = 0; kk < KB / 16; ++kk) {
             uint64_t da, dbh, dbl;
@@ -348,12 +422,105 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
             mma_f16kind(dcol, da, dbl, idesc, 1u);
             accum = 1u;
           }
+          }
           mma_commit(&empty_bar[s]);
         }
         if (aborted) break;
         mma_commit(&accf_bar[b]);
       }
       mma_commit(&drain_bar);
+    }
+  } else if (XQ && warp >= 6) {
+    // --------------------------------------------- FP8 -> BF16 converter
+    // Warps 6..9.  Thread ct owns row ct of every tile: it reads the row's
+    // 128 codes (eight 16-byte chunks, 128-byte swizzle: chunk c of row y
+    // sits at position c ^ (y % 8)) and writes the row's 128 BF16 values
+    // into the two 64-column boxes of the stage's A region with the same
+    // swizzle, as a TMA copy of the BF16 tile would.  A quarter warp covers
+    // eight consecutive rows, so both sides are free of bank conflicts.
+    //
+    // Codes are 0 or normal e4m3 (the staging flushes subnormal codes); for a
+    // normal code c (exponent field e, mantissa m) the value c 2^k of a tile
+    // with exponent k is 2^(e - 7 + k) (1 + m / 8), whose BF16 bits are
+    // (c << 4) + ((120 + k) << 7): exponent e + 120 + k, mantissa m << 4.
+    // Two codes are converted per 32-bit word as 16-bit lanes; the exponent
+    // term is added only in lanes whose code is >= 8.
+    const int ct = threadIdx.x - 192;
+    const int sw = ct & 7;
+    uint8_t* const qring = smem + (size_t)stages * STAGE;
+    int p = p0;
+    ProbView<KB> pv;
+    pv.load(probs, np, p, W);
+    int64_t i = 0;
+    int64_t issued_b = 0;    // units whose factor tiles this CTA requested
+    // (every exit from this loop is warp-uniform: the warp meets __syncwarp
+    // inside it)
+    for (int64_t w = w0; w < w1; ++w, ++i) {
+      if (__shfl_sync(0xffffffffu, *(volatile int*)&aborted, 0)) break;
+      if (w >= pv.we) pv.load(probs, np, ++p, W);
+      const int s = (int)(i % stages);
+      const uint32_t ph = (uint32_t)(i / stages) & 1u;
+      const int q = (int)(i % qstages);
+      const uint32_t qph = (uint32_t)(i / qstages) & 1u;
+      if (__any_sync(0xffffffffu, !mbar_wait(&empty_bar[s], ph ^ 1u, err))) {
+        aborted = 1;
+        break;
+      }
+      const int64_t lw = w - pv.wb;
+      const int64_t tile = lw / pv.nkb, kb = lw % pv.nkb;
+      const int k0 = (int)(kb * KB);
+      uint8_t* const sa = smem + (size_t)s * STAGE;
+      if (ct == 0) {
+        uint8_t* const sb = sa + A_BYTES;
+        const CUtensorMap* mapBh = reinterpret_cast<const CUtensorMap*>(pv.d->mapBh);
+        const CUtensorMap* mapBl = reinterpret_cast<const CUtensorMap*>(pv.d->mapBl);
+        mbar_expect_tx(&bfull_bar[s], 2 * B_BYTES);
+        tma_load(sb, mapBh, &bfull_bar[s], k0, 0);
+        tma_load(sb + B_BYTES / 2, mapBl, &bfull_bar[s], k0, 0);
+        tma_load(sb + B_BYTES, mapBh, &bfull_bar[s], k0 + 64, 0);
+        tma_load(sb + 3 * B_BYTES / 2, mapBl, &bfull_bar[s], k0 + 64, 0);
+        issued_b = i + 1;
+      }
+      // the tile's exponent: X tile (I, J) is (tile, kb) for X V and
+      // (kb, tile) for X^T U
+      const int64_t ti = MODE == 0 ? tile : kb, tj = MODE == 0 ? kb : tile;
+      const uint32_t e0 = (uint32_t)(120 + __ldg(pv.d->xexp + ti * pv.d->ntj + tj));
+      if (__any_sync(0xffffffffu, !mbar_wait(&qfull_bar[q], qph, err))) {
+        aborted = 1;
+        break;
+      }
+      const uint8_t* const src = qring + (size_t)q * Q_BYTES + ct * 128;
+      uint4 in[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) in[c] = *reinterpret_cast<const uint4*>(src + ((c ^ sw) << 4));
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const uint32_t wv[4] = {in[c].x, in[c].y, in[c].z, in[c].w};
+        uint32_t o[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t t = (wv[j] + 0x78787878u) & 0x80808080u;   // 0x80 where code >= 8
+          o[2 * j] = __byte_perm(wv[j], 0, 0x4140) * 16u + __byte_perm(t, 0, 0x4140) * e0;
+          o[2 * j + 1] = __byte_perm(wv[j], 0, 0x4342) * 16u + __byte_perm(t, 0, 0x4342) * e0;
+        }
+        // codes 16c..16c+15 = BF16 columns of box c / 4, chunks 2 (c % 4) and + 1
+        uint8_t* const d = sa + (uint32_t)(c >> 2) * (A_BYTES / 2) + ct * 128;
+        const int cc = (c & 3) * 2;
+        *reinterpret_cast<uint4*>(d + ((cc ^ sw) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<uint4*>(d + (((cc + 1) ^ sw) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
+      }
+      // generic-proxy writes made visible to the tensor core's reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&qempty_bar[q]);
+        mbar_arrive(&full_bar[s]);
+      }
+    }
+    if (aborted && ct == 0) {
+      // let the factor copies already requested land before the CTA exits
+      for (int64_t u = issued_b - stages < 0 ? 0 : issued_b - stages; u < issued_b; ++u)
+        mbar_wait(&bfull_bar[u % stages], (uint32_t)(u / stages) & 1u, err);
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -363,7 +530,9 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
     // coalesced run: a 128-row tile of a dense rows x r array (out, corr, a
     // partial slot) is one contiguous block of 128 r floats.
     constexpr int SS = RP + 1;
-    float* stg = reinterpret_cast<float*>(smem + (size_t)stages * STAGE);
+    // (after the stage ring and, in the FP8 form, the FP8 tile ring)
+    float* stg = reinterpret_cast<float*>(smem + (size_t)stages * STAGE +
+                                          (XQ ? (size_t)qstages * Q_BYTES : 0));
     const int quarter = warp & 3;
     const int lrow = quarter * 32 + lane;
     const int et = threadIdx.x - 64;                 // 0..127
@@ -395,7 +564,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       const int cnt = (int)min((int64_t)TILE, rows_out - row0) * r;
       // at rank <= 32 the corr values of a whole tile are requested before
       // its accumulator is ready (off the epilogue's critical path)
-      constexpr int NPF = RP <= 32 ? RP : 0;
+      constexpr int NPF = (RP <= 32 && !XQ) ? RP : 0;
       float cpre[NPF > 0 ? NPF : 1];
       if constexpr (NPF > 0) {
         if (whole && corr) {
@@ -415,7 +584,14 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
 #pragma unroll
       for (int c0 = 0; c0 < RP; c0 += 16) {
         float v[16];
-        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * RP + c0), v);
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * ACC_COLS + c0), v);
+        if constexpr (XQ) {
+          // X F_hi (columns 0..RP-1) + X F_lo (columns RP..2RP-1)
+          float v2[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * ACC_COLS + RP + c0), v2);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] += v2[j];
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) stg[lrow * SS + c0 + j] = v[j];
       }
@@ -620,6 +796,81 @@ __global__ void split_x_kernel(const float* __restrict__ X, int64_t m, int64_t n
   if (bad) atomicOr(err, ERR_DOMAIN);
 }
 
+// Exponent limits of the FP8 form's tile scales 2^k.  Below: tiles whose
+// largest entry is under 448 * 2^-100 keep k = -100 (their entries become
+// mostly zero codes and live in X_lo).  Above: X beyond 448 * 2^100 is
+// outside the form (ERR_DOMAIN).  Both keep every BF16 exponent built by the
+// converter (e + 120 + k, e in 1..15) inside the normal range.
+constexpr int XQ_KMIN = -100, XQ_KMAX = 100;
+
+// X (FP32, m x n, ldx) -> the FP8 stream form, one CTA per 128 x 128 tile
+// (I, J) = (blockIdx.y, blockIdx.x):
+//   k = min{k : amax <= 448 * 2^k} over the tile (exact, from frexp),
+//       clamped below at XQ_KMIN;  xexp[I * ntj + J] = k;
+//   q = e4m3_rn(x 2^-k) (x 2^-k <= 448, exact scaling); codes under 8
+//       (zero and the subnormals, values below 2^-6) become 0; xq = q;
+//   X_lo = bf16_rn(x - q 2^k) (the difference is exact in FP32).
+// ERR_DOMAIN for a negative or non-finite entry, or amax > 448 * 2^XQ_KMAX.
+__global__ void __launch_bounds__(256) quant_x_kernel(const float* __restrict__ X, int64_t m,
+                                                      int64_t n, int64_t ldx,
+                                                      uint8_t* __restrict__ xq, int64_t ldq,
+                                                      __nv_bfloat16* __restrict__ xl, int64_t ldh,
+                                                      int* __restrict__ xexp, int ntj, int* err) {
+  __shared__ float wmax[8];
+  __shared__ int kt;
+  const int64_t i0 = (int64_t)blockIdx.y * 128, j0 = (int64_t)blockIdx.x * 128;
+  const int rows = (int)min((int64_t)128, m - i0), cols = (int)min((int64_t)128, n - j0);
+  float amax = 0.0f;
+  int bad = 0;
+  for (int e = threadIdx.x; e < 128 * 128; e += blockDim.x) {
+    const int ii = e >> 7, jj = e & 127;
+    if (ii < rows && jj < cols) {
+      const float v = X[(i0 + ii) * ldx + j0 + jj];
+      if (!(v >= 0.0f) || isinf(v)) bad = 1;
+      else amax = fmaxf(amax, v);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = wmax[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) a = fmaxf(a, wmax[w]);
+    int k = XQ_KMIN;
+    if (a > 0.0f) {
+      // a = f 2^e, f in [0.5, 1); 448 = 0.875 2^9
+      int e;
+      const float f = frexpf(a, &e);
+      k = f <= 0.875f ? e - 9 : e - 8;
+      if (k < XQ_KMIN) k = XQ_KMIN;
+      if (k > XQ_KMAX) {
+        k = XQ_KMAX;
+        atomicOr(err, ERR_DOMAIN);
+      }
+    }
+    kt = k;
+    xexp[(int64_t)blockIdx.y * ntj + blockIdx.x] = k;
+  }
+  __syncthreads();
+  const int k = kt;
+  const float inv = __int_as_float((127 - k) << 23);   // 2^-k
+  const float sc = __int_as_float((127 + k) << 23);    // 2^k
+  for (int e = threadIdx.x; e < 128 * 128; e += blockDim.x) {
+    const int ii = e >> 7, jj = e & 127;
+    if (ii < rows && jj < cols) {
+      const float v = X[(i0 + ii) * ldx + j0 + jj];
+      uint8_t c = (uint8_t)(__nv_cvt_float_to_fp8(v * inv, __NV_SATFINITE, __NV_E4M3) & 0x7f);
+      if (c < 8) c = 0;
+      __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)c, __NV_E4M3);
+      const float hi = __half2float(__half(hr)) * sc;
+      xq[(i0 + ii) * ldq + j0 + jj] = c;
+      xl[(i0 + ii) * ldh + j0 + jj] = __float2bfloat16_rn(v - hi);
+    }
+  }
+  if (bad) atomicOr(err, ERR_DOMAIN);
+}
+
 }  // namespace tc
 
 // ------------------------------------------------------------------- host
@@ -643,17 +894,21 @@ static EncodeTiledFn encode_fn() {
 
 // 2D BF16 tensor map over a row-major (rows x cols, ld elements) array with a
 // box of box_cols x box_rows and 128-byte swizzle.  Out-of-range reads give 0.
+// f16: 0 = BF16, 1 = FP16, TC_MAP_U8 = one-byte codes (the FP8 form).
 bool tc_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
                  int box_cols, int box_rows, int f16) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  if (((uintptr_t)base & 15) || ((ld * 2) & 15)) return false;
+  const int64_t es = f16 == TC_MAP_U8 ? 1 : 2;
+  if (((uintptr_t)base & 15) || ((ld * es) & 15) || box_cols * es > 128) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
   cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(reinterpret_cast<CUtensorMap*>(map),
-                  f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  const CUtensorMapDataType dt = f16 == TC_MAP_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : f16            ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), dt, 2,
                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -666,10 +921,21 @@ int tc_rank_pad(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : (r <= 48 ? 48 : 6
 // epilogue's staging tile (TILE x (rp + 1) floats).
 static size_t tc_staging(int rp) { return (size_t)tc::TILE * (rp + 1) * sizeof(float); }
 
-static size_t tc_smem(int mode, int rp, int stages) {
+static size_t tc_smem(int mode, int rp, int stages, int qstages = 0) {
   const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
-  return (size_t)stages * ((size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2) + 1024 +
-         tc_staging(rp);
+  return (size_t)stages * ((size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2) +
+         (size_t)qstages * tc::Q_BYTES + 1024 + tc_staging(rp);
+}
+
+// FP8 form: two BF16 stages (the converter fills one while the MMAs read
+// the other) and as deep an FP8 tile ring as the rest of 227 KB allows
+// (2 to 8 tiles; 4 at rank pad 64, 7 at 32).
+static int tc_qstages(int mode, int rp) {
+  const size_t budget = 227 * 1024 - 1024 - 1024 - tc_staging(rp);
+  const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
+  const size_t st = (size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2;
+  const int q = (int)((budget - 2 * st) / tc::Q_BYTES);
+  return q > 8 ? 8 : (q < 2 ? 2 : q);
 }
 
 // As many stages as fit in 227 KB per CTA (less 1 KB for static shared
@@ -707,23 +973,26 @@ void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r,
   *units = *tiles * ((red + kb - 1) / kb);
 }
 
-template <int MODE, int RP>
+template <int MODE, int RP, bool XQ>
 static void launch_tc(const SweepProb* probs, int np, int64_t W, float* part, int* counters,
                       int grid, int fixup, int* err, cudaStream_t s) {
-  const int stages = tc_stages(MODE, RP);
-  const size_t smem = tc_smem(MODE, RP, stages);
-  cudaFuncSetAttribute(tc::sweep_tc_kernel<MODE, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  tc::sweep_tc_kernel<MODE, RP><<<grid, tc::THREADS, smem, s>>>(probs, np, W, stages, part,
-                                                                 counters, fixup, err);
+  const int stages = XQ ? 2 : tc_stages(MODE, RP);
+  const int qstages = XQ ? tc_qstages(MODE, RP) : 0;
+  const size_t smem = tc_smem(MODE, RP, stages, qstages);
+  cudaFuncSetAttribute(tc::sweep_tc_kernel<MODE, RP, XQ>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  tc::sweep_tc_kernel<MODE, RP, XQ><<<grid, XQ ? tc::THREADS_XQ : tc::THREADS, smem, s>>>(
+      probs, np, W, stages, part, counters, fixup, err, qstages);
 }
 
 void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
-                     int* counters, int num_sms, int* err, cudaStream_t s, int fixup) {
+                     int* counters, int num_sms, int* err, cudaStream_t s, int fixup, int xq) {
   if (np < 1 || W < 1) return;
   const int grid = tc_group_grid(W, num_sms);
   note_launch(1);
-#define TCL(M, P) launch_tc<M, P>(probs, np, W, part, counters, grid, fixup, err, s)
+#define TCL(M, P)                                                             \
+  (xq ? launch_tc<M, P, true>(probs, np, W, part, counters, grid, fixup, err, s) \
+      : launch_tc<M, P, false>(probs, np, W, part, counters, grid, fixup, err, s))
   if (mode == 0) {
     if (rp == 16) TCL(0, 16); else if (rp == 32) TCL(0, 32); else if (rp == 48) TCL(0, 48); else TCL(0, 64);
   } else {
@@ -757,6 +1026,15 @@ void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh,
     tc::split_x_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(X, m, n, ldx, (__nv_bfloat16*)xh,
                                                              (__nv_bfloat16*)xl, ldh, INFINITY,
                                                              err);
+}
+
+void launch_quant_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xq, int64_t ldq,
+                    void* xl, int64_t ldh, int* xexp, int* err, cudaStream_t s) {
+  note_launch(1);
+  const int ntj = (int)((n + 127) / 128);
+  dim3 grid((unsigned)ntj, (unsigned)((m + 127) / 128));
+  tc::quant_x_kernel<<<grid, 256, 0, s>>>(X, m, n, ldx, (uint8_t*)xq, ldq, (__nv_bfloat16*)xl,
+                                          ldh, xexp, ntj, err);
 }
 
 }  // namespace enmf

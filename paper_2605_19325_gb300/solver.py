@@ -21,7 +21,9 @@ def problem_for(X, r, f_dtype=None, stream=None):
 
     stream=torch.bfloat16 (or torch.float16) selects the precision form: the
     iteration's X sweeps run on the tensor cores over a BF16 (FP16) copy of X,
-    with the X_lo correction when X is FP32."""
+    with the X_lo correction when X is FP32.  stream=torch.float8_e4m3fn (FP32
+    X only) selects the FP8 form: e4m3 codes with a power-of-two scale per
+    128 x 128 tile, and a BF16 X_lo correction."""
     if X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a row-major matrix (unit column stride)")
     xdt = _XDT.get(X.dtype)
@@ -30,7 +32,8 @@ def problem_for(X, r, f_dtype=None, stream=None):
     if f_dtype is None:
         f_dtype = torch.float64 if X.dtype == torch.float64 else torch.float32
     fdt = B.ENMF_F64 if f_dtype == torch.float64 else B.ENMF_F32
-    sdt = {torch.bfloat16: B.ENMF_BF16, torch.float16: B.ENMF_F16}.get(stream, 0)
+    sdt = {torch.bfloat16: B.ENMF_BF16, torch.float16: B.ENMF_F16,
+           torch.float8_e4m3fn: B.ENMF_E4M3}.get(stream, 0)
     return B.enmf_problem(X.shape[0], X.shape[1], X.stride(0), r, xdt, fdt, sdt), f_dtype
 
 
@@ -57,7 +60,7 @@ class Solver:
         self.problem, self.f_dtype = problem_for(X, r, f_dtype, x_stream)
         self.stream = stream
         self.ctx = B.enmf_create(self.problem, stream)
-        if x_stream in (torch.bfloat16, torch.float16):
+        if x_stream in (torch.bfloat16, torch.float16, torch.float8_e4m3fn):
             B.enmf_stage_x(self.ctx, X)
         dev = X.device
         self.U = torch.zeros(X.shape[0], r, dtype=self.f_dtype, device=dev)
@@ -103,6 +106,24 @@ class Solver:
         XtU = torch.empty(self.X.shape[1], self.r, dtype=self.f_dtype, device=self.X.device)
         B.enmf_sweep(self.ctx, self.X, U, V, XV, XtU, exact)
         return XV, XtU
+
+    def staged(self):
+        """The staged decomposition of X (tensor-core forms): X_hi (e4m3 codes
+        as uint8 in the FP8 form, else BF16 / FP16), X_lo (16-bit, None when X
+        was given in the stream type) and the FP8 form's per-tile exponents
+        (int32, else None), copied to new device tensors."""
+        m, n = self.X.shape
+        dev = self.X.device
+        sdt = self.problem.stream_dtype
+        hi_dt = {B.ENMF_E4M3: torch.uint8, B.ENMF_F16: torch.float16}.get(sdt, torch.bfloat16)
+        lo_dt = torch.float16 if sdt == B.ENMF_F16 else torch.bfloat16
+        hi = torch.empty(m, n, dtype=hi_dt, device=dev)
+        lo = (torch.empty(m, n, dtype=lo_dt, device=dev)
+              if self.X.dtype == torch.float32 else None)
+        exps = (torch.empty((m + 127) // 128, (n + 127) // 128, dtype=torch.int32, device=dev)
+                if sdt == B.ENMF_E4M3 else None)
+        B.enmf_stage_copy(self.ctx, hi, lo, exps)
+        return hi, lo, exps
 
     def pbcd_counts(self):
         return B.enmf_pbcd_counts(self.ctx)

@@ -67,3 +67,28 @@ def test_status_strings_and_invalid_arguments(libpath):
         assert lib.enmf_create(ctypes.byref(p), None, ctypes.byref(h)) == 1
     # null context
     assert lib.enmf_iterate(None, None, None, None, None, None) == 1
+
+
+def test_fp8_form_problem_rules_and_footprint(libpath):
+    """The FP8 form takes F32 X and F32 factors only; its staged X (one-byte
+    codes, a BF16 X_lo and one exponent per 128 x 128 tile) is smaller than
+    the BF16 form's BF16 pair by about m n bytes."""
+    from paper_2605_19325_gb300 import binding as B
+    lib = B.load(libpath)
+
+    def ws(p):
+        size = ctypes.c_size_t(0)
+        code = lib.enmf_workspace_size(ctypes.byref(p), ctypes.byref(size))
+        return code, size.value
+
+    m, n = 1025, 4096
+    for bad in (B.enmf_problem(m, n, n, 64, B.ENMF_BF16, B.ENMF_F32, B.ENMF_E4M3),
+                B.enmf_problem(m, n, n, 64, B.ENMF_F64, B.ENMF_F64, B.ENMF_E4M3),
+                B.enmf_problem(m, n, n, 64, B.ENMF_F32, B.ENMF_F64, B.ENMF_E4M3),
+                B.enmf_problem(m, n, n, 64, B.ENMF_E4M3, B.ENMF_F32, B.ENMF_E4M3)):
+        assert ws(bad)[0] == 1
+    c8, s8 = ws(B.enmf_problem(m, n, n, 64, B.ENMF_F32, B.ENMF_F32, B.ENMF_E4M3))
+    c16, s16 = ws(B.enmf_problem(m, n, n, 64, B.ENMF_F32, B.ENMF_F32, B.ENMF_BF16))
+    assert c8 == 0 and c16 == 0
+    assert s16 - s8 >= m * n - 2 ** 20
+    assert s8 >= m * n + 2 * m * n + ((m + 127) // 128) * ((n + 127) // 128) * 4
