@@ -96,6 +96,15 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint
       : "memory");
 }
 
+// L2 prefetch of one tensor-map box (no shared memory written, no completion
+// to wait for).
+__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
+
 // Shared-memory matrix descriptor, 128-byte swizzle (tcgen05 layout):
 // start address, leading / stride byte offsets (all >> 4), version 1.
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -305,6 +314,17 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
           mbar_expect_tx(&qfull_bar[q], Q_BYTES);
           if (MODE == 0) tma_load(sq, mapX, &qfull_bar[q], k0, t0);
           else tma_load(sq, mapX, &qfull_bar[q], t0, k0);
+          // the unit's factor tiles are loaded by the converter only once its
+          // stage is free (two units ahead of the MMAs); warm them in L2 now,
+          // up to a ring's depth earlier
+          const CUtensorMap* mapBh = reinterpret_cast<const CUtensorMap*>(pv.d->mapBh);
+          const CUtensorMap* mapBl = reinterpret_cast<const CUtensorMap*>(pv.d->mapBl);
+          tma_prefetch_l2(mapBh, k0, 0);
+          tma_prefetch_l2(mapBl, k0, 0);
+          if (k0 + 64 < pv.d->red) {
+            tma_prefetch_l2(mapBh, k0 + 64, 0);
+            tma_prefetch_l2(mapBl, k0 + 64, 0);
+          }
           continue;
         }
         const CUtensorMap* mapBh = reinterpret_cast<const CUtensorMap*>(pv.d->mapBh);
@@ -627,15 +647,31 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
             }
           }
         } else {
-          for (int f = et; f < cnt; f += 128) {
-            float v = stg[rr * SS + cc];
-            if (add) v += add[f];
-            dst[f] = v;
-            rr += q128;
-            cc += r128;
-            if (cc >= r) {
-              cc -= r;
-              ++rr;
+          // sixteen loads of the corr term in flight per thread, then their
+          // stores (a load-add-store chain per element waits on one L2 round
+          // trip at a time)
+          constexpr int CHK = 16;
+          for (int f0 = et; f0 < cnt; f0 += 128 * CHK) {
+            float a[CHK];
+#pragma unroll
+            for (int u = 0; u < CHK; ++u) {
+              const int f = f0 + 128 * u;
+              a[u] = (add && f < cnt) ? __ldcg(add + f) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < CHK; ++u) {
+              const int f = f0 + 128 * u;
+              if (f < cnt) {
+                float v = stg[rr * SS + cc];
+                if (add) v += a[u];
+                dst[f] = v;
+                rr += q128;
+                cc += r128;
+                if (cc >= r) {
+                  cc -= r;
+                  ++rr;
+                }
+              }
             }
           }
         }
