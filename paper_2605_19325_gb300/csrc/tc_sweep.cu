@@ -25,9 +25,10 @@
 // the bytes of BF16); four converter warps rebuild each tile in shared
 // memory as the exact BF16 values q 2^k, in the same swizzled layout a TMA
 // copy of a BF16 tile would have, and the MMA path is the BF16 one.  The
-// factor's hi and lo rows sit side by side so that one MMA with N = 2 RP
-// covers both (the X tile is read once per K step).  Algorithmic bytes per
-// sweep = m n.
+// factor tiles have a ring of their own, filled by the producer ahead of the
+// MMAs; the factor's hi and lo rows sit side by side so that one MMA with
+// N = 2 RP covers both (the X tile is read once per K step).  Algorithmic
+// bytes per sweep = m n.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -94,15 +95,6 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint
       "[%0], [%1, {%3, %4}], [%2];" ::"r"(saddr(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(x), "r"(y)
       : "memory");
-}
-
-// L2 prefetch of one tensor-map box (no shared memory written, no completion
-// to wait for).
-__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap* map, int x, int y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(x), "r"(y)
-               : "memory");
 }
 
 // Shared-memory matrix descriptor, 128-byte swizzle (tcgen05 layout):
@@ -205,16 +197,20 @@ struct ProbView {
 // (mapBh / mapBl, RP x red), out (rows_out x r, FP32) receiving whole tiles
 // (+ corr when given).  part [G][2][TILE][RP] receives the partial segments.
 // XQ: the FP8 stream form (X tiles as e4m3 codes with per-tile exponents,
-// see the file comment); qstages = depth of its FP8 tile ring.
+// see the file comment); qstages / bstages = depths of its FP8 tile ring and
+// of its factor-tile ring.
 template <int MODE, int RP, bool XQ = false>
 __global__ void __launch_bounds__(XQ ? THREADS_XQ : THREADS, 1)
 sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stages,
                 float* __restrict__ part, int* __restrict__ counters, int fixup, int* err,
-                int qstages) {
+                int qstages, int bstages) {
   constexpr int KB = MODE == 0 ? KB_XV : KB_XT;
   constexpr uint32_t A_BYTES = TILE * KB * 2;                 // 16 KB or 32 KB
   constexpr uint32_t B_BYTES = RP * KB * 2;                   // one of hi / lo
   constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
+  // XQ: the factor tiles live in a ring of their own, so a stage is A only
+  constexpr uint32_t ASTAGE = XQ ? A_BYTES : STAGE;
+  constexpr uint32_t BSLOT = 2 * B_BYTES;   // [hi | lo | hi | lo] boxes of one unit
   constexpr uint32_t IDESC_BF16 = idesc_f16kind(TILE, RP, MODE, 0);
   constexpr uint32_t IDESC_F16 = idesc_f16kind(TILE, RP, MODE, 1);
   // XQ: one MMA over [hi | lo] rows of the factor (N = 2 RP) into an
@@ -228,7 +224,8 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[8];
   __shared__ __align__(8) uint64_t empty_bar[8];
-  __shared__ __align__(8) uint64_t bfull_bar[QB];    // XQ: factor tiles of a stage landed
+  __shared__ __align__(8) uint64_t bfull_bar[QB];    // XQ: factor tiles of a unit landed
+  __shared__ __align__(8) uint64_t bempty_bar[QB];   // XQ: factor slot consumed by the MMAs
   __shared__ __align__(8) uint64_t qfull_bar[QB];    // XQ: FP8 tile landed
   __shared__ __align__(8) uint64_t qempty_bar[QB];   // XQ: FP8 tile consumed
   __shared__ __align__(8) uint64_t accf_bar[2];
@@ -240,6 +237,9 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
+  // XQ: [A stages][factor ring][FP8 ring][epilogue staging]
+  uint8_t* const bring = smem + (size_t)stages * ASTAGE;
+  uint8_t* const qring = bring + (XQ ? (size_t)bstages * BSLOT : 0);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t G = gridDim.x;
   const int64_t w0 = sk_begin(blockIdx.x, W, G), w1 = sk_begin(blockIdx.x + 1, W, G);
@@ -255,12 +255,15 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       // XQ: a stage's X tile is complete when every converter warp arrived
       mbar_init(&full_bar[s], XQ ? NCW : 1);
       mbar_init(&empty_bar[s], 1);
-      if constexpr (XQ) mbar_init(&bfull_bar[s], 1);
     }
     if constexpr (XQ) {
       for (int q = 0; q < qstages; ++q) {
         mbar_init(&qfull_bar[q], 1);
         mbar_init(&qempty_bar[q], NCW);
+      }
+      for (int b = 0; b < bstages; ++b) {
+        mbar_init(&bfull_bar[b], 1);
+        mbar_init(&bempty_bar[b], 1);
       }
     }
     for (int b = 0; b < 2; ++b) {
@@ -290,6 +293,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       ProbView<KB> pv;
       pv.load(probs, np, p, W);
       int64_t i = 0;
+      int64_t q_issued = 0, b_issued = 0;   // XQ: units whose copies were requested
       for (int64_t w = w0; w < w1 && !*(volatile int*)&aborted; ++w, ++i) {
         if (w >= pv.we) {
           pv.load(probs, np, ++p, W);
@@ -299,8 +303,9 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
         }
         const CUtensorMap* mapX = reinterpret_cast<const CUtensorMap*>(pv.d->mapX);
         if constexpr (XQ) {
-          // FP8 tile ring only (the converter loads the factor tiles of the
-          // stage it fills): one 128 x 128 box of codes per unit
+          // one 128 x 128 box of codes per unit into the FP8 ring, then the
+          // unit's factor tiles into the factor ring (each ring runs ahead of
+          // its consumer by its depth)
           const int q = (int)(i % qstages);
           const uint32_t qph = (uint32_t)(i / qstages) & 1u;
           if (!mbar_wait(&qempty_bar[q], qph ^ 1u, err)) {
@@ -310,21 +315,26 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
           const int64_t lw = w - pv.wb;
           const int t0 = (int)((lw / pv.nkb) * TILE);
           const int k0 = (int)((lw % pv.nkb) * KB);
-          uint8_t* sq = smem + (size_t)stages * STAGE + (size_t)q * Q_BYTES;
+          uint8_t* sq = qring + (size_t)q * Q_BYTES;
           mbar_expect_tx(&qfull_bar[q], Q_BYTES);
           if (MODE == 0) tma_load(sq, mapX, &qfull_bar[q], k0, t0);
           else tma_load(sq, mapX, &qfull_bar[q], t0, k0);
-          // the unit's factor tiles are loaded by the converter only once its
-          // stage is free (two units ahead of the MMAs); warm them in L2 now,
-          // up to a ring's depth earlier
+          q_issued = i + 1;
+          const int bs = (int)(i % bstages);
+          const uint32_t bph = (uint32_t)(i / bstages) & 1u;
+          if (!mbar_wait(&bempty_bar[bs], bph ^ 1u, err)) {
+            aborted = 1;
+            break;
+          }
           const CUtensorMap* mapBh = reinterpret_cast<const CUtensorMap*>(pv.d->mapBh);
           const CUtensorMap* mapBl = reinterpret_cast<const CUtensorMap*>(pv.d->mapBl);
-          tma_prefetch_l2(mapBh, k0, 0);
-          tma_prefetch_l2(mapBl, k0, 0);
-          if (k0 + 64 < pv.d->red) {
-            tma_prefetch_l2(mapBh, k0 + 64, 0);
-            tma_prefetch_l2(mapBl, k0 + 64, 0);
-          }
+          uint8_t* sb = bring + (size_t)bs * BSLOT;
+          mbar_expect_tx(&bfull_bar[bs], BSLOT);
+          tma_load(sb, mapBh, &bfull_bar[bs], k0, 0);
+          tma_load(sb + B_BYTES / 2, mapBl, &bfull_bar[bs], k0, 0);
+          tma_load(sb + B_BYTES, mapBh, &bfull_bar[bs], k0 + 64, 0);
+          tma_load(sb + 3 * B_BYTES / 2, mapBl, &bfull_bar[bs], k0 + 64, 0);
+          b_issued = i + 1;
           continue;
         }
         const CUtensorMap* mapBh = reinterpret_cast<const CUtensorMap*>(pv.d->mapBh);
@@ -360,8 +370,10 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
         // let copies already issued land before the CTA can exit
         const int64_t issued = i;
         if constexpr (XQ) {
-          for (int64_t q = issued - qstages < 0 ? 0 : issued - qstages; q < issued; ++q)
+          for (int64_t q = q_issued - qstages < 0 ? 0 : q_issued - qstages; q < q_issued; ++q)
             mbar_wait(&qfull_bar[q % qstages], (uint32_t)(q / qstages) & 1u, err);
+          for (int64_t u = b_issued - bstages < 0 ? 0 : b_issued - bstages; u < b_issued; ++u)
+            mbar_wait(&bfull_bar[u % bstages], (uint32_t)(u / bstages) & 1u, err);
         } else {
           for (int64_t q = issued - stages < 0 ? 0 : issued - stages; q < issued; ++q)
             mbar_wait(&full_bar[q % stages], (uint32_t)(q / stages) & 1u, err);
@@ -393,18 +405,20 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
         for (; w < wend; ++w, ++i) {
           const int s = (int)(i % stages);
           const uint32_t ph = (uint32_t)(i / stages) & 1u;
-          if (!mbar_wait(&full_bar[s], ph, err) || (XQ && !mbar_wait(&bfull_bar[s], ph, err))) {
+          const int bs = XQ ? (int)(i % bstages) : 0;
+          const uint32_t bph = XQ ? (uint32_t)(i / bstages) & 1u : 0u;
+          if (!mbar_wait(&full_bar[s], ph, err) || (XQ && !mbar_wait(&bfull_bar[bs], bph, err))) {
             aborted = 1;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a0 = saddr(smem + (size_t)s * STAGE);
+          const uint32_t a0 = saddr(smem + (size_t)s * ASTAGE);
           const uint32_t bh0 = a0 + A_BYTES;
           const uint32_t bl0 = bh0 + B_BYTES;
           if constexpr (XQ) {
-            // B region: [hi K 0-63 | lo K 0-63 | hi K 64-127 | lo K 64-127],
-            // each RP rows of 128 bytes, so the 2 RP rows of one 64-wide K
-            // atom are contiguous 8-row groups (stride 1024 bytes)
+            // factor slot bs: [hi K 0-63 | lo K 0-63 | hi K 64-127 | lo K
+            // 64-127], each RP rows of 128 bytes, so the 2 RP rows of one
+            // 64-wide K atom are contiguous 8-row groups (stride 1024 bytes)
 #pragma unroll
             for (int kk = 0; kk < KB / 16; ++kk) {
               uint64_t da;
@@ -415,9 +429,11 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
                 da = sdesc(a0 + kk * 2048, A_BYTES / 2, 1024);
               }
               const uint32_t boff = (uint32_t)(kk / 4) * B_BYTES + (uint32_t)(kk % 4) * 32;
-              mma_f16kind(dcol, da, sdesc(bh0 + boff, 16, 1024), IDESC_XQ, accum);
+              mma_f16kind(dcol, da, sdesc(saddr(bring + (size_t)bs * BSLOT) + boff, 16, 1024),
+                          IDESC_XQ, accum);
               accum = 1u;
             }
+            mma_commit(&bempty_bar[bs]);   // factor slot free once these MMAs complete
           } else {
 #pragma unroll
           for (int kk = 0; kk < KB / 16; ++kk) {
@@ -467,12 +483,10 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
     // term is added only in lanes whose code is >= 8.
     const int ct = threadIdx.x - 192;
     const int sw = ct & 7;
-    uint8_t* const qring = smem + (size_t)stages * STAGE;
     int p = p0;
     ProbView<KB> pv;
     pv.load(probs, np, p, W);
     int64_t i = 0;
-    int64_t issued_b = 0;    // units whose factor tiles this CTA requested
     // (every exit from this loop is warp-uniform: the warp meets __syncwarp
     // inside it)
     for (int64_t w = w0; w < w1; ++w, ++i) {
@@ -482,65 +496,56 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       const uint32_t ph = (uint32_t)(i / stages) & 1u;
       const int q = (int)(i % qstages);
       const uint32_t qph = (uint32_t)(i / qstages) & 1u;
-      if (__any_sync(0xffffffffu, !mbar_wait(&empty_bar[s], ph ^ 1u, err))) {
-        aborted = 1;
-        break;
-      }
       const int64_t lw = w - pv.wb;
       const int64_t tile = lw / pv.nkb, kb = lw % pv.nkb;
-      const int k0 = (int)(kb * KB);
-      uint8_t* const sa = smem + (size_t)s * STAGE;
-      if (ct == 0) {
-        uint8_t* const sb = sa + A_BYTES;
-        const CUtensorMap* mapBh = reinterpret_cast<const CUtensorMap*>(pv.d->mapBh);
-        const CUtensorMap* mapBl = reinterpret_cast<const CUtensorMap*>(pv.d->mapBl);
-        mbar_expect_tx(&bfull_bar[s], 2 * B_BYTES);
-        tma_load(sb, mapBh, &bfull_bar[s], k0, 0);
-        tma_load(sb + B_BYTES / 2, mapBl, &bfull_bar[s], k0, 0);
-        tma_load(sb + B_BYTES, mapBh, &bfull_bar[s], k0 + 64, 0);
-        tma_load(sb + 3 * B_BYTES / 2, mapBl, &bfull_bar[s], k0 + 64, 0);
-        issued_b = i + 1;
-      }
       // the tile's exponent: X tile (I, J) is (tile, kb) for X V and
-      // (kb, tile) for X^T U
+      // (kb, tile) for X^T U (requested before the waits)
       const int64_t ti = MODE == 0 ? tile : kb, tj = MODE == 0 ? kb : tile;
       const uint32_t e0 = (uint32_t)(120 + __ldg(pv.d->xexp + ti * pv.d->ntj + tj));
       if (__any_sync(0xffffffffu, !mbar_wait(&qfull_bar[q], qph, err))) {
         aborted = 1;
         break;
       }
+      // Convert into registers while the MMAs still read the A stage: only
+      // the stores wait for it.
       const uint8_t* const src = qring + (size_t)q * Q_BYTES + ct * 128;
       uint4 in[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) in[c] = *reinterpret_cast<const uint4*>(src + ((c ^ sw) << 4));
+      uint32_t o[64];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const uint32_t wv[4] = {in[c].x, in[c].y, in[c].z, in[c].w};
-        uint32_t o[8];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const uint32_t t = (wv[j] + 0x78787878u) & 0x80808080u;   // 0x80 where code >= 8
-          o[2 * j] = __byte_perm(wv[j], 0, 0x4140) * 16u + __byte_perm(t, 0, 0x4140) * e0;
-          o[2 * j + 1] = __byte_perm(wv[j], 0, 0x4342) * 16u + __byte_perm(t, 0, 0x4342) * e0;
+          o[8 * c + 2 * j] = __byte_perm(wv[j], 0, 0x4140) * 16u + __byte_perm(t, 0, 0x4140) * e0;
+          o[8 * c + 2 * j + 1] =
+              __byte_perm(wv[j], 0, 0x4342) * 16u + __byte_perm(t, 0, 0x4342) * e0;
         }
+      }
+      // every lane's codes are in registers: the FP8 slot can be refilled
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&qempty_bar[q]);
+      if (__any_sync(0xffffffffu, !mbar_wait(&empty_bar[s], ph ^ 1u, err))) {
+        aborted = 1;
+        break;
+      }
+      uint8_t* const sa = smem + (size_t)s * ASTAGE;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
         // codes 16c..16c+15 = BF16 columns of box c / 4, chunks 2 (c % 4) and + 1
         uint8_t* const d = sa + (uint32_t)(c >> 2) * (A_BYTES / 2) + ct * 128;
         const int cc = (c & 3) * 2;
-        *reinterpret_cast<uint4*>(d + ((cc ^ sw) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
-        *reinterpret_cast<uint4*>(d + (((cc + 1) ^ sw) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
+        *reinterpret_cast<uint4*>(d + ((cc ^ sw) << 4)) =
+            make_uint4(o[8 * c], o[8 * c + 1], o[8 * c + 2], o[8 * c + 3]);
+        *reinterpret_cast<uint4*>(d + (((cc + 1) ^ sw) << 4)) =
+            make_uint4(o[8 * c + 4], o[8 * c + 5], o[8 * c + 6], o[8 * c + 7]);
       }
       // generic-proxy writes made visible to the tensor core's reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&qempty_bar[q]);
-        mbar_arrive(&full_bar[s]);
-      }
-    }
-    if (aborted && ct == 0) {
-      // let the factor copies already requested land before the CTA exits
-      for (int64_t u = issued_b - stages < 0 ? 0 : issued_b - stages; u < issued_b; ++u)
-        mbar_wait(&bfull_bar[u % stages], (uint32_t)(u / stages) & 1u, err);
+      if (lane == 0) mbar_arrive(&full_bar[s]);
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -551,8 +556,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
     // partial slot) is one contiguous block of 128 r floats.
     constexpr int SS = RP + 1;
     // (after the stage ring and, in the FP8 form, the FP8 tile ring)
-    float* stg = reinterpret_cast<float*>(smem + (size_t)stages * STAGE +
-                                          (XQ ? (size_t)qstages * Q_BYTES : 0));
+    float* stg = reinterpret_cast<float*>(qring + (XQ ? (size_t)qstages * Q_BYTES : 0));
     const int quarter = warp & 3;
     const int lrow = quarter * 32 + lane;
     const int et = threadIdx.x - 64;                 // 0..127
@@ -957,21 +961,27 @@ int tc_rank_pad(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : (r <= 48 ? 48 : 6
 // epilogue's staging tile (TILE x (rp + 1) floats).
 static size_t tc_staging(int rp) { return (size_t)tc::TILE * (rp + 1) * sizeof(float); }
 
-static size_t tc_smem(int mode, int rp, int stages, int qstages = 0) {
+static size_t tc_smem(int mode, int rp, int stages) {
   const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
-  return (size_t)stages * ((size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2) +
-         (size_t)qstages * tc::Q_BYTES + 1024 + tc_staging(rp);
+  return (size_t)stages * ((size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2) + 1024 +
+         tc_staging(rp);
 }
 
-// FP8 form: two BF16 stages (the converter fills one while the MMAs read
-// the other) and as deep an FP8 tile ring as the rest of 227 KB allows
-// (2 to 8 tiles; 4 at rank pad 64, 7 at 32).
-static int tc_qstages(int mode, int rp) {
-  const size_t budget = 227 * 1024 - 1024 - 1024 - tc_staging(rp);
+// FP8 form: two BF16 A stages (the converter fills one while the MMAs read
+// the other), a ring of factor tiles (2 x rp x 128 BF16 pairs per unit; 3
+// slots from rank pad 48 up, else 4) and as deep an FP8 tile ring as the
+// rest of 227 KB allows (2 to 8 tiles): rank pad 64 -> 3 + 2, 48 -> 3 + 4,
+// 32 -> 4 + 5, 16 -> 4 + 7.
+static void tc_xq_plan(int mode, int rp, int* bstages, int* qstages, size_t* smem) {
   const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
-  const size_t st = (size_t)tc::TILE * kb * 2 + 2 * (size_t)rp * kb * 2;
-  const int q = (int)((budget - 2 * st) / tc::Q_BYTES);
-  return q > 8 ? 8 : (q < 2 ? 2 : q);
+  const size_t a = (size_t)tc::TILE * kb * 2, bslot = 2 * (size_t)rp * kb * 2;
+  const size_t budget = 227 * 1024 - 1024 - 1024 - tc_staging(rp) - 2 * a;
+  const int nb = bslot >= 24576 ? 3 : 4;
+  int q = (int)((budget - nb * bslot) / tc::Q_BYTES);
+  q = q > 8 ? 8 : q;
+  *bstages = nb;
+  *qstages = q;
+  *smem = 2 * a + nb * bslot + (size_t)q * tc::Q_BYTES + 1024 + tc_staging(rp);
 }
 
 // As many stages as fit in 227 KB per CTA (less 1 KB for static shared
@@ -1013,12 +1023,13 @@ template <int MODE, int RP, bool XQ>
 static void launch_tc(const SweepProb* probs, int np, int64_t W, float* part, int* counters,
                       int grid, int fixup, int* err, cudaStream_t s) {
   const int stages = XQ ? 2 : tc_stages(MODE, RP);
-  const int qstages = XQ ? tc_qstages(MODE, RP) : 0;
-  const size_t smem = tc_smem(MODE, RP, stages, qstages);
+  int qstages = 0, bstages = 0;
+  size_t smem = tc_smem(MODE, RP, stages);
+  if (XQ) tc_xq_plan(MODE, RP, &bstages, &qstages, &smem);
   cudaFuncSetAttribute(tc::sweep_tc_kernel<MODE, RP, XQ>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   tc::sweep_tc_kernel<MODE, RP, XQ><<<grid, XQ ? tc::THREADS_XQ : tc::THREADS, smem, s>>>(
-      probs, np, W, stages, part, counters, fixup, err, qstages);
+      probs, np, W, stages, part, counters, fixup, err, qstages, bstages);
 }
 
 void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
