@@ -234,6 +234,17 @@ def replica_throughput(total_ms, steps, world, device="cpu"):
 FP8_WORKLOAD = "spectrogram 1025x131072 r=64, 200 alternations"
 
 
+def sweep_bytes_all_terms(m, n, r, esize):
+    """Mean algorithmic bytes of one X_hi sweep (X V and X^T U alternate)
+    with every term: X once, the factor's BF16 pair (r rounded up to 16, 32,
+    48 or 64; 4 bytes per entry), the FP32 output and the stored FP32 X_lo
+    term added to it."""
+    rp = 16 if r <= 16 else (32 if r <= 32 else (48 if r <= 48 else 64))
+    xv = m * n * esize + n * rp * 4 + 2 * m * r * 4
+    xtu = m * n * esize + m * rp * 4 + 2 * n * r * 4
+    return (xv + xtu) / 2.0
+
+
 def fp8_leg(forms=("fp8", "bf16", "f32")):
     """Precision form, large: the spectrogram-shaped workload (1025 x 131072,
     r = 64; harmonic templates x sparse activations, Gamma(0.5) modulation)
@@ -284,9 +295,13 @@ def fp8_leg(forms=("fp8", "bf16", "f32")):
             if sweeps:
                 us = 1e3 * sweep_ms / sweeps
                 gbs = m * n * esize / (us * 1e-6) / 1e9
+                allb = sweep_bytes_all_terms(m, n, r, esize)
                 rec.update({"sweep_us_avg": us, "sweeps_timed": sweeps,
                             "sweep_achieved_gbs": gbs, "sweep_frac_of_measured_hbm": gbs / hbm,
-                            "algorithmic_bytes_per_sweep": m * n * esize})
+                            "algorithmic_bytes_per_sweep": m * n * esize,
+                            "all_terms_bytes_per_sweep": allb,
+                            "all_terms_achieved_gbs": allb / (us * 1e-6) / 1e9,
+                            "all_terms_frac_of_measured_hbm": allb / (us * 1e-6) / 1e9 / hbm})
         out[name] = rec
         s.close()
     if "f32" in out:
