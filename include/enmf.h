@@ -91,7 +91,7 @@ typedef struct {
                     /*   ENMF_E4M3 with F32 X: the FP8 form -- X_hi is e4m3   */
                     /*   codes with a power-of-two scale per 128 x 128 tile   */
                     /*   and X_lo = bf16(X - X_hi) (see enmf_stage_x); X must */
-                    /*   stay <= 448 * 2^100.                                 */
+                    /*   stay <= 448 * 2^100; m <= 65535 * 128.               */
 } enmf_problem;
 
 typedef struct enmf_ctx enmf_ctx;

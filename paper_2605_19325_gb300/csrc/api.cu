@@ -56,7 +56,9 @@ static bool valid_problem(const enmf_problem* p) {
     if (p->f_dtype != ENMF_F32) return false;
     // F32 X (split into a 16-bit pair) or X already of the stream type
     if (p->x_dtype != ENMF_F32 && p->x_dtype != p->stream_dtype) return false;
-    // the FP8 form is staged from F32 X only
+    // the FP8 form is staged from F32 X only, one staging block per 128 x 128
+    // tile (at most 65535 tile rows in the grid's y dimension)
+    if (p->stream_dtype == ENMF_E4M3 && (p->m + 127) / 128 > 65535) return false;
     if (p->x_dtype != ENMF_F32 && (p->ldx % 8) != 0) return false;
     if (p->m > 0x7fffffffLL || p->n > 0x7fffffffLL) return false;
   } else if (p->stream_dtype != 0 && p->stream_dtype != p->x_dtype) {

@@ -85,7 +85,8 @@ def test_fp8_form_problem_rules_and_footprint(libpath):
     for bad in (B.enmf_problem(m, n, n, 64, B.ENMF_BF16, B.ENMF_F32, B.ENMF_E4M3),
                 B.enmf_problem(m, n, n, 64, B.ENMF_F64, B.ENMF_F64, B.ENMF_E4M3),
                 B.enmf_problem(m, n, n, 64, B.ENMF_F32, B.ENMF_F64, B.ENMF_E4M3),
-                B.enmf_problem(m, n, n, 64, B.ENMF_E4M3, B.ENMF_F32, B.ENMF_E4M3)):
+                B.enmf_problem(m, n, n, 64, B.ENMF_E4M3, B.ENMF_F32, B.ENMF_E4M3),
+                B.enmf_problem(65535 * 128 + 1, 64, 64, 4, B.ENMF_F32, B.ENMF_F32, B.ENMF_E4M3)):
         assert ws(bad)[0] == 1
     c8, s8 = ws(B.enmf_problem(m, n, n, 64, B.ENMF_F32, B.ENMF_F32, B.ENMF_E4M3))
     c16, s16 = ws(B.enmf_problem(m, n, n, 64, B.ENMF_F32, B.ENMF_F32, B.ENMF_BF16))
