@@ -14,7 +14,7 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # GPU tests need the device; they are selected with -m gpu on the GPU machine.
+    # GPU tests need a CUDA device; they are selected with -m gpu.
     try:
         import torch
         has_gpu = torch.cuda.is_available()
