@@ -968,16 +968,15 @@ static size_t tc_smem(int mode, int rp, int stages) {
 }
 
 // FP8 form: two BF16 A stages (the converter fills one while the MMAs read
-// the other), a ring of factor tiles (2 x rp x 128 BF16 pairs per unit) and
-// as deep an FP8 tile ring as the rest of 227 KB allows (2 to 8 tiles):
-// rank pad 64 -> 2 + 4, 48 -> 3 + 4, 32 -> 4 + 5, 16 -> 4 + 7.  The FP8 ring
-// waits on DRAM and is refilled only after a slot's codes are converted, so
-// it gets the depth; factor tiles come from L2.
+// the other), a ring of factor tiles (2 x rp x 128 BF16 pairs per unit; 3
+// slots from rank pad 48 up, else 4) and as deep an FP8 tile ring as the
+// rest of 227 KB allows (2 to 8 tiles): rank pad 64 -> 3 + 2, 48 -> 3 + 4,
+// 32 -> 4 + 5, 16 -> 4 + 7.
 static void tc_xq_plan(int mode, int rp, int* bstages, int* qstages, size_t* smem) {
   const int kb = mode == 0 ? tc::KB_XV : tc::KB_XT;
   const size_t a = (size_t)tc::TILE * kb * 2, bslot = 2 * (size_t)rp * kb * 2;
   const size_t budget = 227 * 1024 - 1024 - 1024 - tc_staging(rp) - 2 * a;
-  const int nb = bslot >= 32768 ? 2 : (bslot >= 24576 ? 3 : 4);
+  const int nb = bslot >= 24576 ? 3 : 4;
   int q = (int)((budget - nb * bslot) / tc::Q_BYTES);
   q = q > 8 ? 8 : q;
   *bstages = nb;
