@@ -67,6 +67,7 @@ def test_status_strings_and_invalid_arguments(libpath):
         assert lib.enmf_create(ctypes.byref(p), None, ctypes.byref(h)) == 1
     # null context
     assert lib.enmf_iterate(None, None, None, None, None, None) == 1
+    assert lib.enmf_stage_copy(None, None, None, None) == 1
 
 
 def test_fp8_form_problem_rules_and_footprint(libpath):
