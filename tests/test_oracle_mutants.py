@@ -1,0 +1,280 @@
+"""Planted mistakes in the oracle, each caught by a pin (CPU only).
+
+Every case replaces one oracle function with a plausible wrong version: a
+dropped term, a wrong sign or index, a transposed operand, an off-by-one, a
+wrong rounding rule. It then runs the pins of tests/test_oracle_pins.py that
+should notice, and requires at least one of them to fail. The mistakes live
+only in this file and only for the duration of one case (monkeypatch); the
+oracle itself is untouched.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import test_oracle_pins as P
+from oracle import enmf_oracle as O
+
+ORIG = {name: getattr(O, name) for name in (
+    "truncated_svd", "prox_h", "procrustes", "rotate", "shift_step", "shift_negative",
+    "pbcd", "hals_update", "kkt", "objective", "e4m3_round", "bf16_round", "tile_exponent",
+    "quantize_fp8_tiles", "xtu_sharded")}
+
+
+# ------------------------------------------------------------------ mutants
+def svd_unbalanced(X, r):
+    """S given to U only (U* = U_r S, V* = V_r) instead of S^(1/2) to both."""
+    Ur, s, Vt = np.linalg.svd(X, full_matrices=False)
+    Us, Vs = Ur[:, :r] * s[:r], Vt[:r].T.copy()
+    flip = (Us.sum(0) + Vs.sum(0)) < 0
+    Us[:, flip] *= -1
+    Vs[:, flip] *= -1
+    return Us, Vs, s
+
+
+def svd_sign_inverted(X, r):
+    Us, Vs, s = ORIG["truncated_svd"](X, r)
+    return -Us, -Vs, s
+
+
+def svd_off_by_one(X, r):
+    """Singular triplets 2..r+1 instead of 1..r."""
+    Ur, s, Vt = np.linalg.svd(X, full_matrices=False)
+    root = np.sqrt(s[1:r + 1])
+    Us, Vs = Ur[:, 1:r + 1] * root, Vt[1:r + 1].T * root
+    return Us, Vs, s
+
+
+def prox_half_threshold(b, rho):
+    return np.where(b > 0, b, np.where(b >= -0.5 / rho, 0.0, b + 0.5 / rho))
+
+
+def prox_wrong_sign(b, rho):
+    return np.where(b > 0, b, np.where(b >= -1.0 / rho, 0.0, b - 1.0 / rho))
+
+
+def procrustes_transposed(M):
+    return ORIG["procrustes"](M).T
+
+
+def rotate_identity(Us, Vs, **kw):
+    r = Us.shape[1]
+    return Us.copy(), Vs.copy(), np.eye(r), O.RotateInfo(steps=0)
+
+
+def rotate_y_sign(Us, Vs, rho=None, R0=None, Y0=None, max_iter=O.ADMM_MAX_ITER, tol=O.ADMM_TOL):
+    """Algorithm 1 with the multiplier update's sign flipped."""
+    W = np.vstack([Us, Vs])
+    r = W.shape[1]
+    rho = rho or O.RHO_SCALE / math.sqrt(float(np.mean(W * W)))
+    R, Y = np.eye(r), np.zeros_like(W)
+    for _ in range(max_iter):
+        Z = O.prox_h(W @ R - Y / rho, rho)
+        R = O.procrustes(W.T @ (Z + Y / rho))
+        Y = Y - rho * (Z - W @ R)
+    return Us @ R, Vs @ R, R, O.RotateInfo(steps=max_iter)
+
+
+def shift_all_entries(F, s):
+    return F + s
+
+
+def shift_step_more(F, n_shift=O.N_SHIFT):
+    return ORIG["shift_step"](F, n_shift + 1)
+
+
+def pbcd_unsquared_numerator(X, U, V, mask, eps=O.PBCD_EPS, max_iter=O.PBCD_MAX_ITER):
+    """d_i = ||g_i|| / ||g_i V^T||^2 (the square on the numerator dropped)."""
+    U = np.array(U, dtype=np.float64)
+    Mk = mask.astype(np.float64)
+    for t in range(max_iter):
+        g = Mk * ((U @ V.T - X) @ V)
+        num = np.sqrt(np.sum(g * g, axis=1))
+        den = np.sum((g @ V.T) ** 2, axis=1)
+        d = np.where(den > 0, num / np.where(den > 0, den, 1), 0.0)
+        U = np.where(mask, np.maximum(U - d[:, None] * g, 0.0), U)
+    return U, O.PbcdInfo(iters=max_iter)
+
+
+def pbcd_ignores_mask(X, U, V, mask, eps=O.PBCD_EPS, max_iter=O.PBCD_MAX_ITER):
+    return ORIG["pbcd"](X, U, V, np.ones_like(mask, dtype=bool), eps, max_iter)
+
+
+def pbcd_gradient_sign(X, U, V, mask, eps=O.PBCD_EPS, max_iter=O.PBCD_MAX_ITER):
+    """Steps along +grad (the gradient of X - U V^T taken with the wrong sign)."""
+    return ORIG["pbcd"](-X, -U, V, mask, eps, max_iter)
+
+
+def hals_no_diagonal(X, U, V):
+    """The column update without the division by B_jj."""
+    U = np.array(U, dtype=np.float64)
+    A, B = X @ V, V.T @ V
+    for j in range(U.shape[1]):
+        U[:, j] = np.maximum(0.0, U[:, j] + (A[:, j] - U @ B[:, j]))
+    return U
+
+
+def hals_no_floor(X, U, V):
+    U = np.array(U, dtype=np.float64)
+    A, B = X @ V, V.T @ V
+    for j in range(U.shape[1]):
+        U[:, j] = U[:, j] + (A[:, j] - U @ B[:, j]) / B[j, j]
+    return U
+
+
+def kkt_wrong_projection(X, U, V):
+    """Projected gradient taking max(0, grad) where W = 0."""
+    rep = ORIG["kkt"](X, U, V)
+    E = U @ V.T - X
+    W = np.vstack([U, V])
+    G = np.vstack([E @ V, E.T @ U])
+    P_ = np.where(W > 0, G, np.maximum(G, 0.0))
+    rep.pg_norm = float(np.linalg.norm(P_))
+    rep.pg_rel = rep.pg_norm / (np.linalg.norm(X @ V) + np.linalg.norm(X.T @ U))
+    return rep
+
+
+def objective_without_half(X, U, V):
+    return 2.0 * ORIG["objective"](X, U, V)
+
+
+def e4m3_ties_away(v):
+    v = np.asarray(v, dtype=np.float64)
+    sub = v < 2.0 ** -6
+    e = np.floor(np.log2(np.where(sub, 1.0, v)))
+    q = np.where(sub, 2.0 ** -9, 2.0 ** (e - 3))
+    return np.minimum(np.floor(v / q + 0.5) * q, 448.0)
+
+
+def e4m3_no_saturation(v):
+    v = np.asarray(v, dtype=np.float64)
+    out = ORIG["e4m3_round"](np.minimum(v, 448.0))
+    return np.where(v > 464.0, v, out)
+
+
+def bf16_truncate(x32):
+    b = np.asarray(x32, dtype=np.float32).view(np.uint32) & np.uint32(0xFFFF0000)
+    return b.view(np.float32).astype(np.float64)
+
+
+def tile_exponent_plus_one(amax):
+    k = ORIG["tile_exponent"](amax)
+    return k + 1 if amax > 0 else k
+
+
+def fp8_split_no_flush(X32, tile=128):
+    """The split without flushing codes below the smallest normal."""
+    X32 = np.asarray(X32, dtype=np.float32)
+    m, n = X32.shape
+    X = X32.astype(np.float64)
+    ti, tj = -(-m // tile), -(-n // tile)
+    K = np.zeros((ti, tj), dtype=np.int64)
+    Q = np.zeros_like(X)
+    for I in range(ti):
+        for J in range(tj):
+            blk = X[I * tile:(I + 1) * tile, J * tile:(J + 1) * tile]
+            k = O.tile_exponent(float(blk.max()))
+            K[I, J] = k
+            Q[I * tile:(I + 1) * tile, J * tile:(J + 1) * tile] = O.e4m3_round(blk * 2.0 ** -k)
+    Xh = Q * 2.0 ** np.repeat(np.repeat(K, tile, 0), tile, 1)[:m, :n]
+    return O.e4m3_code(Q), K, Xh, O.bf16_round((X - Xh).astype(np.float32))
+
+
+def fp8_split_unrounded_lo(X32, tile=128):
+    """X_lo kept in full precision instead of BF16."""
+    codes, K, Xh, _ = ORIG["quantize_fp8_tiles"](X32, tile)
+    X = np.asarray(X32, dtype=np.float32).astype(np.float64)
+    return codes, K, Xh, X - Xh
+
+
+def fp8_split_transposed_tiles(X32, tile=128):
+    """Tile exponents indexed (J, I) when applied."""
+    codes, K, Xh, Xl = ORIG["quantize_fp8_tiles"](X32, tile)
+    X = np.asarray(X32, dtype=np.float32).astype(np.float64)
+    m, n = X.shape
+    if K.shape[0] == K.shape[1]:
+        Kt = K.T
+    else:
+        Kt = np.resize(K.T, K.shape)
+    kk = np.repeat(np.repeat(Kt, tile, 0), tile, 1)[:m, :n].astype(float)
+    Q = Xh / 2.0 ** np.repeat(np.repeat(K, tile, 0), tile, 1)[:m, :n]
+    Xh2 = Q * 2.0 ** kk
+    return codes, Kt, Xh2, O.bf16_round((X - Xh2).astype(np.float32))
+
+
+def xtu_sharded_overlap(X, U, P):
+    """Row panels that overlap by one row."""
+    bounds = np.linspace(0, X.shape[0], P + 1).astype(int)
+    out = np.zeros((X.shape[1], U.shape[1]))
+    for p in range(P):
+        a, b = max(bounds[p] - 1, 0), bounds[p + 1]
+        out = out + X[a:b].T @ U[a:b]
+    return out
+
+
+MUTANTS = [
+    ("svd S on U only", "truncated_svd", svd_unbalanced,
+     [P.test_svd_start_balanced_factors, P.test_svd_start_rank_one_closed_form]),
+    ("svd signs inverted", "truncated_svd", svd_sign_inverted,
+     [P.test_svd_sign_rule, P.test_svd_start_rank_one_closed_form]),
+    ("svd triplets off by one", "truncated_svd", svd_off_by_one,
+     [P.test_svd_start_eckart_young_tail]),
+    ("prox threshold halved", "prox_h", prox_half_threshold,
+     [P.test_prox_matches_dense_1d_minimisation]),
+    ("prox shift sign", "prox_h", prox_wrong_sign, [P.test_prox_matches_dense_1d_minimisation]),
+    ("procrustes transposed", "procrustes", procrustes_transposed,
+     [P.test_procrustes_matches_brute_force_r2]),
+    ("rotation skipped", "rotate", rotate_identity,
+     [P.test_rotation_keeps_level_set_and_orthogonality, P.test_rotation_brute_force_r2]),
+    ("ADMM multiplier sign", "rotate", rotate_y_sign,
+     [P.test_rotation_keeps_level_set_and_orthogonality, P.test_rotation_brute_force_r2]),
+    ("shift moves every entry", "shift_negative", shift_all_entries,
+     [P.test_shift_step_and_count, P.test_pbcd_decreases_objective_and_keeps_mask,
+      P.test_ascent_stage_ends_in_n_shift_iterations]),
+    ("shift step one count too small", "shift_step", shift_step_more,
+     [P.test_shift_step_and_count, P.test_ascent_stage_ends_in_n_shift_iterations]),
+    ("PBCD step numerator unsquared", "pbcd", pbcd_unsquared_numerator,
+     [P.test_row_step_matches_line_search]),
+    ("PBCD ignores the mask", "pbcd", pbcd_ignores_mask,
+     [P.test_pbcd_decreases_objective_and_keeps_mask]),
+    ("PBCD gradient sign", "pbcd", pbcd_gradient_sign,
+     [P.test_row_step_matches_line_search, P.test_pbcd_decreases_objective_and_keeps_mask]),
+    ("HALS without 1/B_jj", "hals_update", hals_no_diagonal,
+     [P.test_hals_half_steps_are_monotone, P.test_hals_column_is_exact_nnls_minimiser]),
+    ("HALS without the floor", "hals_update", hals_no_floor,
+     [P.test_hals_column_is_exact_nnls_minimiser, P.test_enmf_reaches_kkt_point]),
+    ("KKT projection at W = 0", "kkt", kkt_wrong_projection, [P.test_enmf_reaches_kkt_point]),
+    ("objective without 1/2", "objective", objective_without_half,
+     [P.test_svd_start_eckart_young_tail]),
+    ("E4M3 ties away from zero", "e4m3_round", e4m3_ties_away,
+     [P.test_e4m3_round_is_nearest_with_ties_to_even]),
+    ("E4M3 without saturation", "e4m3_round", e4m3_no_saturation,
+     [P.test_e4m3_round_is_nearest_with_ties_to_even]),
+    ("BF16 truncated", "bf16_round", bf16_truncate,
+     [P.test_bf16_round_is_nearest_with_ties_to_even]),
+    ("tile exponent one too large", "tile_exponent", tile_exponent_plus_one,
+     [P.test_tile_exponent_is_least_power_covering_the_tile,
+      P.test_fp8_tile_split_bounds_and_per_tile_scales]),
+    ("FP8 split without the subnormal flush", "quantize_fp8_tiles", fp8_split_no_flush,
+     [P.test_fp8_tile_split_bounds_and_per_tile_scales]),
+    ("FP8 split with X_lo unrounded", "quantize_fp8_tiles", fp8_split_unrounded_lo,
+     [P.test_fp8_tile_split_bounds_and_per_tile_scales]),
+    ("FP8 split with tile exponents transposed", "quantize_fp8_tiles",
+     fp8_split_transposed_tiles, [P.test_fp8_tile_split_bounds_and_per_tile_scales]),
+    ("shard panels overlap", "xtu_sharded", xtu_sharded_overlap,
+     [P.test_sharded_xtu_is_rank_ordered_sum]),
+]
+
+
+@pytest.mark.parametrize("name,attr,fn,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(monkeypatch, name, attr, fn, pins):
+    monkeypatch.setattr(O, attr, fn)
+    failures = []
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, ValueError, FloatingPointError, np.linalg.LinAlgError,
+                IndexError) as e:
+            failures.append((pin.__name__, type(e).__name__))
+            break
+    assert failures, f"planted mistake '{name}' passed every pin in {[p.__name__ for p in pins]}"

@@ -27,6 +27,8 @@ def test_svd_start_eckart_young_tail():
     Us, Vs, s = O.truncated_svd(X, r)
     err = np.sum((X - Us @ Vs.T) ** 2)
     assert err == pytest.approx(np.sum(s[r:] ** 2), rel=1e-10)
+    # Eq. 1's objective is half the squared error
+    assert O.objective(X, Us, Vs) == pytest.approx(0.5 * np.sum(s[r:] ** 2), rel=1e-10)
 
 
 def test_svd_start_balanced_factors():
@@ -98,6 +100,14 @@ def test_procrustes_matches_brute_force_r2():
             best = min(best, np.sum((B - W @ Q) ** 2))
     assert np.sum((B - W @ R) ** 2) <= best + 1e-8
     np.testing.assert_allclose(R.T @ R, np.eye(2), atol=1e-14)
+    # B = W Q0 exactly, Q0 a proper rotation of r = 3: the minimiser is Q0
+    # itself (zero residual; not its transpose)
+    W3 = rng.standard_normal((30, 3))
+    a, b = 0.7, -0.4
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, math.cos(b), -math.sin(b)], [0, math.sin(b), math.cos(b)]])
+    Q0 = Rz @ Rx
+    np.testing.assert_allclose(O.procrustes(W3.T @ (W3 @ Q0)), Q0, atol=1e-12)
 
 
 def test_rotation_keeps_level_set_and_orthogonality():
@@ -198,12 +208,15 @@ def test_shift_step_and_count():
     """Eq. 8 with reading R5: the worst entry needs exactly N_SHIFT shifts."""
     rng = _rng(8)
     U = rng.standard_normal((50, 5))
+    U0 = U.copy()
     s = O.shift_step(U)
     k = 0
     while np.any(U < 0):
         U = O.shift_negative(U, s)
         k += 1
     assert k == O.N_SHIFT
+    # Eq. 8 moves the negative entries only: entries that start >= 0 never move
+    np.testing.assert_array_equal(U[U0 >= 0], U0[U0 >= 0])
 
 
 # ---------------------------------------------------------------- HALS
@@ -414,5 +427,9 @@ def test_fp8_tile_split_bounds_and_per_tile_scales():
     assert np.all(codes[~normal] == 0) and np.all(Xh[~normal] == 0)
     assert np.all(Xd[~normal] < 2.0 ** (kk[~normal] - 6))
     assert np.all(np.abs(Xd - Xh - Xl) <= 2.0 ** -8 * err)   # BF16: 8 significant bits
+    # X_lo is a BF16 number: an FP32 value whose low 16 bits are zero
+    Xl32 = Xl.astype(np.float32)
+    assert np.array_equal(Xl32.astype(np.float64), Xl)
+    assert np.all((Xl32.view(np.uint32) & 0xFFFF) == 0)
     # decoding the codes gives X_hi
     np.testing.assert_array_equal(_e4m3_grid()[codes] * 2.0 ** kk, Xh)
