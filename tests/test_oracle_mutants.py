@@ -18,7 +18,7 @@ from oracle import enmf_oracle as O
 ORIG = {name: getattr(O, name) for name in (
     "truncated_svd", "prox_h", "procrustes", "rotate", "shift_step", "shift_negative",
     "pbcd", "hals_update", "kkt", "objective", "e4m3_round", "bf16_round", "tile_exponent",
-    "quantize_fp8_tiles", "xtu_sharded")}
+    "quantize_fp8_tiles", "xtu_sharded", "rel_err", "h", "enmf", "e4m3_code", "iterate")}
 
 
 # ------------------------------------------------------------------ mutants
@@ -212,6 +212,73 @@ def xtu_sharded_overlap(X, U, P):
     return out
 
 
+def kkt_abs_delta(X, U, V):
+    """delta as max |grad o W| instead of the signed max of Table 10."""
+    rep = ORIG["kkt"](X, U, V)
+    E = U @ V.T - X
+    W = np.vstack([U, V])
+    G = np.vstack([E @ V, E.T @ U])
+    rep.delta = float(np.abs(G * W).max())
+    return rep
+
+
+def kkt_gradient_sign(X, U, V):
+    """The gradient of X - U V^T instead of U V^T - X."""
+    return ORIG["kkt"](-X, -U, V)
+
+
+def rel_err_squared(X, U, V):
+    return 2.0 * O.objective(X, U, V) / float(np.linalg.norm(X)) ** 2
+
+
+def hals_jacobi(X, U, V):
+    """All columns updated from the old U (no Gauss-Seidel sweep)."""
+    U0 = np.array(U, dtype=np.float64)
+    U = U0.copy()
+    A, B = X @ V, V.T @ V
+    for j in range(U.shape[1]):
+        if B[j, j] > 0:
+            U[:, j] = np.maximum(0.0, U0[:, j] + (A[:, j] - U0 @ B[:, j]) / B[j, j])
+    return U
+
+
+def negative_part_sign(q):
+    return np.maximum(0.0, q)
+
+
+def rotate_rho_times_rms(Us, Vs, rho=None, **kw):
+    W = np.vstack([Us, Vs])
+    rms = math.sqrt(float(np.mean(W * W)))
+    return ORIG["rotate"](Us, Vs, rho=O.RHO_SCALE * rms if rho is None else rho, **kw)
+
+
+def shift_step_from_max(F, n_shift=O.N_SHIFT):
+    return float(max(0.0, F.max())) / (n_shift - 0.5)
+
+
+def enmf_without_rotation(X, r, n_iter, **kw):
+    X = O._check(X, r)
+    Us, Vs, s = O.truncated_svd(X, r)
+    U, V, tr, st = O.iterate(X, Us, Vs, n_iter)
+    return O.EnmfResult(U, V, Us, Vs, s, np.eye(r), O.RotateInfo(), tr, st)
+
+
+def e4m3_code_bias(q):
+    c = ORIG["e4m3_code"](q).astype(np.int64)
+    return np.where(c >= 8, c + 8, c).astype(np.uint8)
+
+
+def iterate_v_first(X, U, V, n_iter, state=None, **kw):
+    V2, U2, tr, st = ORIG["iterate"](np.asarray(X).T, V, U, n_iter, state, **kw)
+    return U2, V2, tr, st
+
+
+def iterate_hals_first(X, U, V, n_iter, state=None, **kw):
+    st = state if state is not None else O.IterState()
+    st.stage = "hals"
+    return ORIG["iterate"](X, U, V, n_iter, st, **kw)
+
+
 MUTANTS = [
     ("svd S on U only", "truncated_svd", svd_unbalanced,
      [P.test_svd_start_balanced_factors, P.test_svd_start_rank_one_closed_form]),
@@ -263,6 +330,26 @@ MUTANTS = [
      fp8_split_transposed_tiles, [P.test_fp8_tile_split_bounds_and_per_tile_scales]),
     ("shard panels overlap", "xtu_sharded", xtu_sharded_overlap,
      [P.test_sharded_xtu_is_rank_ordered_sum]),
+    ("KKT delta unsigned", "kkt", kkt_abs_delta,
+     [P.test_kkt_measures_against_finite_difference_gradient]),
+    ("KKT gradient sign", "kkt", kkt_gradient_sign,
+     [P.test_kkt_measures_against_finite_difference_gradient]),
+    ("relative error squared", "rel_err", rel_err_squared, [P.test_svd_start_eckart_young_tail]),
+    ("HALS Jacobi instead of Gauss-Seidel", "hals_update", hals_jacobi,
+     [P.test_hals_half_steps_are_monotone, P.test_enmf_reaches_kkt_point]),
+    ("negative part sign", "h", negative_part_sign,
+     [P.test_rotation_keeps_level_set_and_orthogonality, P.test_rotation_brute_force_r2]),
+    ("rho times RMS", "rotate", rotate_rho_times_rms, [P.test_rotation_brute_force_r2]),
+    ("shift step from the max", "shift_step", shift_step_from_max,
+     [P.test_shift_step_and_count, P.test_ascent_stage_ends_in_n_shift_iterations]),
+    ("enmf without the rotation", "enmf", enmf_without_rotation,
+     [P.test_enmf_starts_from_the_rotated_svd_and_alternates_u_then_v]),
+    ("E4M3 code exponent bias", "e4m3_code", e4m3_code_bias,
+     [P.test_e4m3_round_is_nearest_with_ties_to_even]),
+    ("V-half before U-half", "iterate", iterate_v_first,
+     [P.test_enmf_starts_from_the_rotated_svd_and_alternates_u_then_v]),
+    ("HALS before the ascent stage", "iterate", iterate_hals_first,
+     [P.test_ascent_stage_ends_in_n_shift_iterations]),
 ]
 
 

@@ -27,8 +27,11 @@ def test_svd_start_eckart_young_tail():
     Us, Vs, s = O.truncated_svd(X, r)
     err = np.sum((X - Us @ Vs.T) ** 2)
     assert err == pytest.approx(np.sum(s[r:] ** 2), rel=1e-10)
-    # Eq. 1's objective is half the squared error
+    # Eq. 1's objective is half the squared error; the relative error of App. D
+    # is the error's norm over ||X||_F
     assert O.objective(X, Us, Vs) == pytest.approx(0.5 * np.sum(s[r:] ** 2), rel=1e-10)
+    assert O.rel_err(X, Us, Vs) == pytest.approx(
+        math.sqrt(np.sum(s[r:] ** 2)) / math.sqrt(np.sum(s ** 2)), rel=1e-10)
 
 
 def test_svd_start_balanced_factors():
@@ -257,7 +260,69 @@ def test_hals_column_is_exact_nnls_minimiser():
         assert U1[i, 0] == pytest.approx(bestv, abs=2e-4)
 
 
+def test_kkt_measures_against_finite_difference_gradient():
+    """App. G / Table 10 at a point that is not stationary: the gradient of
+    f = 1/2 ||X - U V^T||^2 by central differences (exact up to rounding for a
+    quadratic), then delta = max(grad o W) (signed), sigma = sum(grad o W),
+    min grad, min W and the projected gradient of reading R11."""
+    rng = _rng(12)
+    U0 = rng.random((6, 2)) + 0.5
+    V0 = rng.random((5, 2)) + 0.5
+    X = U0 @ V0.T
+    # column 0 of U overshoots and column 1 undershoots the planted factors,
+    # so grad o W has both signs and its most negative entry is the largest
+    U = U0 * np.array([1.1, 0.3])
+    U[0, 0] = 0.0                                   # an entry at the bound
+    V = V0.copy()
+    h = 1e-3
+
+    def grad(F, which):
+        G = np.zeros_like(F)
+        for idx in np.ndindex(F.shape):
+            Fp, Fm = F.copy(), F.copy()
+            Fp[idx] += h
+            Fm[idx] -= h
+            fp = 0.5 * np.sum((X - (Fp @ V.T if which == 0 else U @ Fp.T)) ** 2)
+            fm = 0.5 * np.sum((X - (Fm @ V.T if which == 0 else U @ Fm.T)) ** 2)
+            G[idx] = (fp - fm) / (2 * h)
+        return G
+
+    W = np.vstack([U, V])
+    G = np.vstack([grad(U, 0), grad(V, 1)])
+    prod = G * W
+    assert prod.max() != np.abs(prod).max()        # the signed max is the one asked for
+    P_ = np.where(W > 0, G, np.minimum(G, 0.0))
+    rep = O.kkt(X, U, V)
+    assert rep.delta == pytest.approx(prod.max(), rel=1e-8)
+    assert rep.sigma == pytest.approx(prod.sum(), rel=1e-8)
+    assert rep.min_grad == pytest.approx(G.min(), rel=1e-8)
+    assert rep.min_w == W.min()
+    assert rep.pg_norm == pytest.approx(np.linalg.norm(P_), rel=1e-8)
+
+
 # ---------------------------------------------------------------- whole method
+def test_enmf_starts_from_the_rotated_svd_and_alternates_u_then_v():
+    """Algorithm 3: the iteration starts from Algorithm 1's output on the SVD
+    start, and one alternation is the U-half (V fixed) then the V-half with
+    the new U; in the HALS stage those are the HALS sweeps (Sec. 4.3)."""
+    X, r = synth.config_small(0)
+    res = O.enmf(X, r, 0)
+    Us, Vs, _ = O.truncated_svd(X, r)
+    U1, V1, R1, _ = O.rotate(Us, Vs)
+    np.testing.assert_allclose(res.U, U1, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(res.V, V1, rtol=0, atol=1e-13)
+    assert np.linalg.norm(res.R - np.eye(r)) > 1e-3
+    rng = _rng(13)
+    U = rng.random((X.shape[0], r))
+    V = rng.random((X.shape[1], r))
+    Ua, Va, tr, st = O.iterate(X, U, V, 1, state=O.IterState(stage="hals"))
+    Ub = O.hals_update(X, U, V)
+    Vb = O.hals_update(X.T, V, Ub)
+    np.testing.assert_array_equal(Ua, Ub)
+    np.testing.assert_array_equal(Va, Vb)
+    assert tr[0] == O.objective(X, Ub, Vb)
+
+
 def test_enmf_reaches_kkt_point():
     """App. G, Table 10: at the end of eNMF the KKT conditions hold."""
     X, r = synth.config_small(0)
