@@ -309,6 +309,27 @@ enmf_status enmf_batch_step(enmf_batch* b, int32_t n_alt);
 enmf_status enmf_batch_member(enmf_batch* b, int32_t slot, enmf_iter_info* info, double* f);
 enmf_status enmf_batch_tune(enmf_batch* b, int32_t* grid, float* ms);
 
+/* ---- Checkpoint of the iteration state (no counterpart in the paper) -----
+ * Algorithm 3's loop carries state between alternations, beside U and V:
+ *   - the stage (ascent, lines 5-11, or HALS, line 12);
+ *   - the fixed shift steps of Eq. 8 / 9 and the negative maxima they came from;
+ *   - the alternation counters and the last objective.
+ * enmf_state_export writes that state into a host buffer of ENMF_STATE_BYTES
+ * bytes. The buffer is a fixed little-endian layout, versioned, carrying the
+ * problem's sizes and types. enmf_state_import loads such a buffer into a
+ * context of the same problem; enmf_iterate with reset = 0 then continues the
+ * iteration from the caller's U and V (which the caller saves and restores
+ * itself) as the exporting context would have.
+ * Both synchronise the context stream.
+ * enmf_state_export: *bytes >= ENMF_STATE_BYTES on entry (set to the size
+ * written on return); ENMF_ESTATE when no iteration has run since the last
+ * svd_init / rotate (nothing to export).
+ * enmf_state_import: ENMF_EINVAL for a short buffer, an unknown layout or a
+ * different problem (m, n, r, types). */
+#define ENMF_STATE_BYTES 128
+enmf_status enmf_state_export(enmf_ctx* ctx, void* buf, size_t* bytes);
+enmf_status enmf_state_import(enmf_ctx* ctx, const void* buf, size_t bytes);
+
 /* ---- Measurement (no counterpart in the paper) ---------------------------
  * enmf_profile: every > 0 records CUDA events around the X V and X^T U sweep
  * kernels (the main pass over X alone: not the factor split or the X_lo

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libenmf.so")
 ENMF_F64, ENMF_F32, ENMF_BF16, ENMF_F16, ENMF_E4M3 = 0, 1, 2, 3, 4
 ENMF_MAX_RANK = 64
 ENMF_RESIDUAL_NOALLOC_MAX_ROWS = 262144
+ENMF_STATE_BYTES = 128
 
 STATUS = {0: "ok", 1: "EINVAL", 2: "EDOMAIN", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT",
           6: "ENOTCONV", 7: "EBUSY", 8: "ESTATE"}
@@ -89,6 +90,8 @@ _SIGS = {
                              C.POINTER(enmf_iter_opts), C.POINTER(C.c_double)]),
     "enmf_stage_x": (C.c_int, [C.c_void_p, C.c_void_p]),
     "enmf_stage_copy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "enmf_state_export": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "enmf_state_import": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "enmf_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_int32]),
     "enmf_profile": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -194,6 +197,20 @@ def enmf_stage_copy(ctx, hi=None, lo=None, tile_exp=None):
     """Copy the staged X_hi / X_lo (m x n dense) and, in the FP8 form, the
     per-tile exponents (int32) into the given tensors (any may be None)."""
     check(lib().enmf_stage_copy(ctx, _ptr(hi), _ptr(lo), _ptr(tile_exp)), "enmf_stage_copy")
+
+
+def enmf_state_export(ctx):
+    """The context's iteration state as ENMF_STATE_BYTES bytes."""
+    buf = (C.c_char * ENMF_STATE_BYTES)()
+    n = C.c_size_t(ENMF_STATE_BYTES)
+    check(lib().enmf_state_export(ctx, buf, C.byref(n)), "enmf_state_export")
+    return bytes(buf[:n.value])
+
+
+def enmf_state_import(ctx, blob):
+    """Load an exported iteration state into a context of the same problem."""
+    buf = C.create_string_buffer(bytes(blob), len(blob))
+    check(lib().enmf_state_import(ctx, buf, len(blob)), "enmf_state_import")
 
 
 def enmf_sweep(ctx, X, U, V, XV=None, XtU=None, exact=1):

@@ -757,6 +757,91 @@ static enmf_status check_staged(enmf_ctx* ctx, const void* X) {
   return ENMF_OK;
 }
 
+// ------------------------------------------------------- state checkpoint
+// Fixed host layout of the exported iteration state (ENMF_STATE_BYTES).
+struct StateBlob {
+  uint32_t magic, version;
+  int64_t m, n;
+  int32_t r, x_dtype, f_dtype, stream_dtype;
+  int32_t stage, k, asc_iters, hals_iters, negU, negV;
+  double s_u, s_v, maxneg_u, maxneg_v, f_last;
+  unsigned char reserved_[ENMF_STATE_BYTES - 104];
+};
+static_assert(sizeof(StateBlob) == ENMF_STATE_BYTES, "state blob layout");
+static constexpr uint32_t STATE_MAGIC = 0x534D4E45u;   // "ENMS"
+static constexpr uint32_t STATE_VERSION = 1;
+
+extern "C" enmf_status enmf_state_export(enmf_ctx* ctx, void* buf, size_t* bytes) {
+  GUARD(ctx);
+  if (!buf || !bytes || *bytes < sizeof(StateBlob)) {
+    if (bytes) *bytes = sizeof(StateBlob);
+    return ENMF_EINVAL;
+  }
+  if (!ctx->state_valid) return ENMF_ESTATE;
+  DevState hst;
+  CK(cudaMemcpyAsync(&hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+  enmf_status rc = sync_status(ctx);
+  if (rc) return rc;
+  StateBlob b;
+  memset(&b, 0, sizeof(b));
+  b.magic = STATE_MAGIC;
+  b.version = STATE_VERSION;
+  b.m = ctx->p.m;
+  b.n = ctx->p.n;
+  b.r = ctx->p.r;
+  b.x_dtype = ctx->p.x_dtype;
+  b.f_dtype = ctx->p.f_dtype;
+  b.stream_dtype = ctx->p.stream_dtype;
+  b.stage = hst.stage;
+  b.k = hst.k;
+  b.asc_iters = hst.asc_iters;
+  b.hals_iters = hst.hals_iters;
+  b.negU = hst.negU;
+  b.negV = hst.negV;
+  b.s_u = hst.s_u;
+  b.s_v = hst.s_v;
+  b.maxneg_u = hst.maxneg_u;
+  b.maxneg_v = hst.maxneg_v;
+  b.f_last = hst.f_last;
+  memcpy(buf, &b, sizeof(b));
+  *bytes = sizeof(b);
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_state_import(enmf_ctx* ctx, const void* buf, size_t bytes) {
+  GUARD(ctx);
+  if (!buf || bytes < sizeof(StateBlob)) return ENMF_EINVAL;
+  StateBlob b;
+  memcpy(&b, buf, sizeof(b));
+  const enmf_problem& p = ctx->p;
+  if (b.magic != STATE_MAGIC || b.version != STATE_VERSION || b.m != p.m || b.n != p.n ||
+      b.r != p.r || b.x_dtype != p.x_dtype || b.f_dtype != p.f_dtype ||
+      b.stream_dtype != p.stream_dtype)
+    return ENMF_EINVAL;
+  if (b.stage < 0 || b.stage > 1 || b.k < 0) return ENMF_EINVAL;
+  // the device state keeps its own grid barrier word and scratch scalars
+  DevState hst;
+  CK(cudaMemcpyAsync(&hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+  enmf_status rc = sync_status(ctx);
+  if (rc) return rc;
+  hst.stage = b.stage;
+  hst.k = b.k;
+  hst.asc_iters = b.asc_iters;
+  hst.hals_iters = b.hals_iters;
+  hst.negU = b.negU;
+  hst.negV = b.negV;
+  hst.s_u = b.s_u;
+  hst.s_v = b.s_v;
+  hst.maxneg_u = b.maxneg_u;
+  hst.maxneg_v = b.maxneg_v;
+  hst.f_last = b.f_last;
+  CK(cudaMemcpyAsync(ctx->st, &hst, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
+  rc = sync_status(ctx);
+  if (rc) return rc;
+  ctx->state_valid = true;
+  return ENMF_OK;
+}
+
 // The staged decomposition, copied out densely (inspection and tests).
 extern "C" enmf_status enmf_stage_copy(enmf_ctx* ctx, void* hi, void* lo, int32_t* tile_exp) {
   GUARD(ctx);

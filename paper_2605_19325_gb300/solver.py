@@ -107,6 +107,15 @@ class Solver:
         B.enmf_sweep(self.ctx, self.X, U, V, XV, XtU, exact)
         return XV, XtU
 
+    def export_state(self):
+        """The iteration state (stage, shift steps, counters) as bytes; with
+        copies of U and V it resumes the iteration in another Solver of the
+        same problem (import_state, then iterate(..., reset=0))."""
+        return B.enmf_state_export(self.ctx)
+
+    def import_state(self, blob):
+        B.enmf_state_import(self.ctx, blob)
+
     def staged(self):
         """The staged decomposition of X (tensor-core forms): X_hi (e4m3 codes
         as uint8 in the FP8 form, else BF16 / FP16), X_lo (16-bit, None when X

@@ -68,6 +68,10 @@ def test_status_strings_and_invalid_arguments(libpath):
     # null context
     assert lib.enmf_iterate(None, None, None, None, None, None) == 1
     assert lib.enmf_stage_copy(None, None, None, None) == 1
+    size = ctypes.c_size_t(B.ENMF_STATE_BYTES)
+    buf = ctypes.create_string_buffer(B.ENMF_STATE_BYTES)
+    assert lib.enmf_state_export(None, buf, ctypes.byref(size)) == 1
+    assert lib.enmf_state_import(None, buf, B.ENMF_STATE_BYTES) == 1
 
 
 def test_fp8_form_problem_rules_and_footprint(libpath):
@@ -94,3 +98,10 @@ def test_fp8_form_problem_rules_and_footprint(libpath):
     assert c8 == 0 and c16 == 0
     assert s16 - s8 >= m * n - 2 ** 20
     assert s8 >= m * n + 2 * m * n + ((m + 127) // 128) * ((n + 127) // 128) * 4
+
+
+def test_state_blob_size_matches_header(libpath):
+    from paper_2605_19325_gb300 import binding as B
+    text = open(os.path.join(ROOT, "include", "enmf.h")).read()
+    m = re.search(r"#define ENMF_STATE_BYTES (\d+)", text)
+    assert m and int(m.group(1)) == B.ENMF_STATE_BYTES
