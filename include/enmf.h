@@ -276,6 +276,8 @@ enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V, int32_t n
  * Members are contexts of the tensor-core form (stream_dtype ENMF_BF16, FP32
  * factors) with X staged, whose U and V (device, caller-owned) are the
  * starting point -- normally the output of enmf_svd_init and enmf_rotate.
+ * A context of the FP8 form (stream_dtype ENMF_E4M3) is rejected with
+ * ENMF_EINVAL: it iterates alone.
  * All members of a batch share the padded rank (r rounded up to 16, 32, 48
  * or 64); a member of another padded rank is rejected with ENMF_EINVAL.
  * The iteration options (pbcd_max_iter, eps, n_shift, correct_every; the
