@@ -59,11 +59,13 @@ typedef enum {
   ENMF_ESTATE = 8       /* call out of order (e.g. rotate before svd_init)    */
 } enmf_status;
 
-/* Element types.  The "form" of a problem is (x_dtype, f_dtype):
+/* Element types.  The "form" of a problem is (x_dtype, f_dtype, stream_dtype):
  *   plain FP64:  X F64, factors F64 (all arithmetic FP64);
  *   FP32:        X F32, factors F32 (FP32 arithmetic, FP64 scalar sums);
- *   BF16 / F16:  X BF16 or F16, factors F32; X products on the tensor cores
- *                with FP32 accumulation. */
+ *   BF16 / F16:  X BF16 or F16 (given, or staged from F32), factors F32; X
+ *                products on the tensor cores with FP32 accumulation;
+ *   FP8:         X F32 staged to E4M3 codes with per-tile scales, factors
+ *                F32, tensor cores as for BF16. */
 typedef enum { ENMF_F64 = 0, ENMF_F32 = 1, ENMF_BF16 = 2, ENMF_F16 = 3,
                ENMF_E4M3 = 4 /* stream type only: OCP FP8 E4M3 codes */ } enmf_dtype;
 
