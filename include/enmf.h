@@ -349,9 +349,28 @@ enmf_status enmf_profile_read(enmf_ctx* ctx, double* sweep_ms, int64_t* sweeps, 
 enmf_status enmf_probe_fma_peak(int32_t dtype, double* flops_per_s);
 long long enmf_launch_count(void);
 
+/* ---- Bounded device waits (no counterpart in the paper) ------------------
+ * Every device-side wait of the library is bounded; an expired wait records
+ * a timeout in the context's status word, the kernel goes on without the
+ * awaited data (results are then meaningless, never out of bounds), and the
+ * next synchronising call returns ENMF_ETIMEOUT and poisons the context.
+ * enmf_set_wait_limit sets the spin limit, in SM clock cycles, of the grid
+ * barriers of the context's cooperative kernels (half steps, PBCD stop test,
+ * ADMM loop): 0 restores the default (about 2 s); at most 4e9.  A small
+ * limit makes barriers expire on purpose: for tests of the failure path and
+ * for callers that prefer an early error to a long stall.  Synchronises.
+ * enmf_probe_wait launches one thread that waits, bounded by `cycles`, for
+ * an event that never occurs -- kind 0: a global flag that nothing sets (the
+ * barriers' spin); kind 1: a shared-memory mbarrier phase that nothing
+ * completes (the tensor-core sweeps' pipeline waits) -- and sets *status to
+ * ENMF_ETIMEOUT when the wait gave up as it must (ENMF_OK otherwise).  It
+ * uses no context; the CUDA context stays usable.  Synchronises the device. */
+enmf_status enmf_set_wait_limit(enmf_ctx* ctx, int64_t cycles);
+enmf_status enmf_probe_wait(int32_t kind, int64_t cycles, int32_t* status);
+
 /* ---- Allocation-free residual (no counterpart in the paper) --------------
  * The paper has no such call.  enmf_residual_noalloc computes the three
- * numbers of enmf_residual with direct = 1 (Eq. 1):
+ * numbers of enmf_residual with direct = 1:
  *   out3[0] = f = 1/2 ||X - U V^T||_F^2,
  *   out3[1] = ||X - U V^T||_F / ||X||_F   (0 when ||X|| = 0),
  *   out3[2] = ||X||_F^2,

@@ -99,6 +99,8 @@ _SIGS = {
                                     C.c_int32]),
     "enmf_probe_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
     "enmf_launch_count": (C.c_longlong, []),
+    "enmf_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
+    "enmf_probe_wait": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(C.c_int32)]),
     "enmf_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "enmf_batch_destroy": (None, [C.c_void_p]),
     "enmf_batch_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -314,6 +316,18 @@ def enmf_batch_tune(b):
     return g.value, ms.value
 
 
+def enmf_set_wait_limit(ctx, cycles):
+    """Spin limit (SM cycles) of the context's grid barriers; 0 = default."""
+    check(lib().enmf_set_wait_limit(ctx, int(cycles)), "enmf_set_wait_limit")
+
+
+def enmf_probe_wait(kind, cycles):
+    """Status (0 ok, 5 ETIMEOUT) of a bounded wait on an event that never occurs."""
+    st = C.c_int32(-1)
+    check(lib().enmf_probe_wait(int(kind), int(cycles), C.byref(st)), "enmf_probe_wait")
+    return st.value
+
+
 def enmf_solve(ctx, X_ptr, U_ptr, V_ptr, n_iter):
     """Whole Algorithm 3 through one call; pointers may be host or device."""
     out = (C.c_double * 3)()
@@ -336,20 +350,65 @@ def _dtype_code(t):
     return _TORCH_DT[t.dtype]
 
 
+def _noalloc_args(X, U, V, out3):
+    """Host-side checks of enmf_residual_noalloc's tensors.
+
+    The C entry point sees only pointers and sizes, so a wrong shape, a
+    transposed or strided factor, or a short or mistyped out3 would become an
+    out-of-bounds device access.  Every such case raises ValueError here,
+    before the library is called.  Returns (m, n, ldx, r)."""
+    if X.dim() != 2:
+        raise ValueError("X must be a matrix")
+    m, n = X.shape
+    if U.dim() != 2 or V.dim() != 2:
+        raise ValueError("U and V must be matrices")
+    r = U.shape[1]
+    if tuple(U.shape) != (m, r):
+        raise ValueError(f"U has shape {tuple(U.shape)}, expected ({m}, r)")
+    if tuple(V.shape) != (n, r):
+        raise ValueError(f"V has shape {tuple(V.shape)}, expected ({n}, {r})")
+    if U.dtype != V.dtype:
+        raise ValueError(f"U and V differ in dtype ({U.dtype} vs {V.dtype})")
+    if not (U.is_contiguous() and V.is_contiguous()):
+        raise ValueError("U and V must be contiguous (row-major, leading dimension r)")
+    if m > 0 and n > 0:
+        if n > 1 and X.stride(1) != 1:
+            raise ValueError("X must be a row-major matrix (unit column stride)")
+        if m > 1 and X.stride(0) < n:
+            raise ValueError(f"X row stride {X.stride(0)} is below n = {n} (rows overlap)")
+    ldx = X.stride(0) if m > 1 else n
+    ldx = max(ldx, n)
+    if out3.dtype != _float64() or not out3.is_contiguous() or out3.numel() < 3:
+        raise ValueError("out3 must be a contiguous float64 tensor of at least 3 elements")
+    _dtype_code(X)
+    _dtype_code(U)
+    return m, n, ldx, r
+
+
+def _float64():
+    import torch
+    return torch.float64
+
+
 def enmf_residual_noalloc(X, U, V, out3, stream=None):
     """Allocation-free residual into the device tensor out3 (3 doubles).
 
     Enqueues on `stream` (default: the current torch stream) and returns
     without synchronising.  X is (m, n) with unit column stride; U (m, r) and
-    V (n, r) are contiguous."""
-    m, n = X.shape
-    r = U.shape[1]
-    if X.stride(1) != 1 and n > 1:
-        raise ValueError("X must be a row-major matrix (unit column stride)")
+    V (n, r) are contiguous and of one dtype; out3 is a contiguous float64
+    tensor; all four live on the current CUDA device.  Bad arguments raise
+    ValueError (or EnmfError for m beyond the row limit) before any launch."""
+    import torch
+    m, n, ldx, r = _noalloc_args(X, U, V, out3)
+    if m > ENMF_RESIDUAL_NOALLOC_MAX_ROWS:
+        raise EnmfError(1, f"enmf_residual_noalloc: m = {m} exceeds "
+                           f"ENMF_RESIDUAL_NOALLOC_MAX_ROWS = {ENMF_RESIDUAL_NOALLOC_MAX_ROWS}")
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for name, t in (("X", X), ("U", U), ("V", V), ("out3", out3)):
+        if t.device.type != "cuda" or t.device.index != dev:
+            raise ValueError(f"{name} must be on the current CUDA device (cuda:{dev}), "
+                             f"not {t.device}")
     code = lib().enmf_residual_noalloc(
-        _ptr(X), _dtype_code(X), m, n, max(X.stride(0), n), _ptr(U), _ptr(V), r,
+        _ptr(X), _dtype_code(X), m, n, ldx, _ptr(U), _ptr(V), r,
         _dtype_code(U), _ptr(out3), _stream(stream))
-    if code == 1 and m > ENMF_RESIDUAL_NOALLOC_MAX_ROWS:
-        raise EnmfError(code, f"enmf_residual_noalloc: m = {m} exceeds "
-                              f"ENMF_RESIDUAL_NOALLOC_MAX_ROWS = {ENMF_RESIDUAL_NOALLOC_MAX_ROWS}")
     check(code, "enmf_residual_noalloc")

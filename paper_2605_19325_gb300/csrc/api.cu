@@ -819,6 +819,15 @@ extern "C" enmf_status enmf_state_import(enmf_ctx* ctx, const void* buf, size_t 
       b.stream_dtype != p.stream_dtype)
     return ENMF_EINVAL;
   if (b.stage < 0 || b.stage > 1 || b.k < 0) return ENMF_EINVAL;
+  // counters consistent, flags boolean, shift steps and negative maxima finite
+  // and nonnegative, objective finite: anything else is a corrupt buffer
+  if (b.asc_iters < 0 || b.hals_iters < 0 || (int64_t)b.asc_iters + b.hals_iters > b.k)
+    return ENMF_EINVAL;
+  if ((b.negU != 0 && b.negU != 1) || (b.negV != 0 && b.negV != 1)) return ENMF_EINVAL;
+  const double nonneg[4] = {b.s_u, b.s_v, b.maxneg_u, b.maxneg_v};
+  for (double v : nonneg)
+    if (!(v >= 0.0) || isinf(v)) return ENMF_EINVAL;
+  if (!isfinite(b.f_last)) return ENMF_EINVAL;
   // the device state keeps its own grid barrier word and scratch scalars
   DevState hst;
   CK(cudaMemcpyAsync(&hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1031,6 +1040,14 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
     return rc;
   }
   return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_set_wait_limit(enmf_ctx* ctx, int64_t cycles) {
+  GUARD(ctx);
+  if (cycles < 0 || cycles > 4000000000LL) return ENMF_EINVAL;
+  const unsigned int v = (unsigned int)cycles;
+  CK(cudaMemcpyAsync(&ctx->st->bar.spin, &v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+  return sync_status(ctx);
 }
 
 extern "C" enmf_status enmf_profile(enmf_ctx* ctx, int32_t every) {

@@ -86,7 +86,7 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 // Grid-wide barrier state of the cooperative kernels (zero at creation).
 struct GridBarrier {
   unsigned int word;
-  unsigned int unused;
+  unsigned int spin;   // spin limit in cycles; 0 = SPIN_BUDGET_CYCLES
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
@@ -102,18 +102,21 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
 // follow).  Thread 0 of each block arrives after a fence that publishes the
 // block's writes (ordered by the preceding __syncthreads) and spins on an
 // acquire load until bit 31 differs from the value its own atomic returned.
-// The spin is bounded: past SPIN_BUDGET_CYCLES it records ERR_TIMEOUT.
+// The spin is bounded: past bar->spin cycles (SPIN_BUDGET_CYCLES when 0) it
+// records ERR_TIMEOUT and the block goes on.
 __device__ __forceinline__ void grid_sync(GridBarrier* bar, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
     const bool lead = blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
     const unsigned int inc = lead ? 0x80000000u - (nb - 1u) : 1u;
+    const unsigned int lim = *(volatile unsigned int*)&bar->spin;
+    const long long budget = lim ? (long long)lim : SPIN_BUDGET_CYCLES;
     __threadfence();
     const unsigned int old = atomicAdd(&bar->word, inc);
     const long long t0 = clock64();
     while (((ld_acquire_gpu(&bar->word) ^ old) & 0x80000000u) == 0u) {
-      if (clock64() - t0 > SPIN_BUDGET_CYCLES) {
+      if (clock64() - t0 > budget) {
         atomicOr(err, ERR_TIMEOUT);
         break;
       }

@@ -1,5 +1,6 @@
-// Allocation-free residual: the direct residual of Eq. 1 (the same three
-// numbers enmf_residual returns with direct = 1) for callers that hold no
+// Allocation-free residual: f = 1/2 ||X - U V^T||_F^2, the relative error
+// and ||X||_F^2 (the three numbers enmf_residual returns with direct = 1),
+// formed entry by entry, for callers that hold no
 // context and must not allocate device memory.  Its reduction scratch is a
 // fixed array in the library's static device memory, so the call makes no
 // allocation of any kind.

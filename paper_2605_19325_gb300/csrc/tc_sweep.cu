@@ -36,6 +36,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace enmf {
 
@@ -48,112 +49,7 @@ constexpr int THREADS = 192;  // warp 0 TMA producer, warp 1 MMA issuer, warps 2
 constexpr int THREADS_XQ = 320;  // the same, plus warps 6-9 converting FP8 tiles to BF16
 constexpr int NCW = 4;           // converter warps of the FP8 form
 constexpr uint32_t Q_BYTES = 128 * 128;  // one FP8 X tile (128 x 128 codes)
-constexpr long long WAIT_BUDGET = 4000000000LL;  // cycles (~2 s)
 constexpr int MAX_GRID = 256;  // CTAs of the persistent sweep at most
-
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(saddr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: false (and ERR_TIMEOUT recorded) if the phase never completes.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  long long t0 = clock64();
-  while (!mbar_try(bar, parity)) {
-    if (clock64() - t0 > WAIT_BUDGET) {
-      atomicOr(err, ERR_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                         int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%3, %4}], [%2];" ::"r"(saddr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor, 128-byte swizzle (tcgen05 layout):
-// start address, leading / stride byte offsets (all >> 4), version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor, kind::f16: FP32 accumulate, A and B both BF16 (type
-// code 1) or both FP16 (type code 0), M x N.
-__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, int a_mn_major, int f16) {
-  return (1u << 4) | ((uint32_t)(f16 ? 0 : 1) << 7) | ((uint32_t)(f16 ? 0 : 1) << 10) |
-         ((uint32_t)a_mn_major << 15) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16kind(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          saddr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
-  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
 
 // Work split (stream-K): the work of all problems, each problem's (tile,
 // k-block) units tile-major and the problems one after another, is cut into
@@ -911,6 +807,29 @@ __global__ void __launch_bounds__(256) quant_x_kernel(const float* __restrict__ 
   if (bad) atomicOr(err, ERR_DOMAIN);
 }
 
+// Bounded-wait probe: one thread waits for something that never happens --
+// kind 0: a global flag that nothing sets (the spin form of the grid
+// barriers); kind 1: phase 0 of a shared-memory mbarrier that nothing arrives
+// at (the form of the sweep's pipeline waits, through mbar_wait).  Both give
+// up after `budget` cycles and record ERR_TIMEOUT in *err.
+__global__ void probe_wait_kernel(int kind, long long budget, const unsigned int* flag, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  if (kind == 0) {
+    const long long t0 = clock64();
+    while (ld_acquire_gpu(flag) == 0u) {
+      if (clock64() - t0 > budget) {
+        atomicOr(err, ERR_TIMEOUT);
+        break;
+      }
+    }
+  } else {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(&bar, 0u, err, budget);
+  }
+}
+
 }  // namespace tc
 
 // ------------------------------------------------------------------- host
@@ -1085,3 +1004,32 @@ void launch_quant_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xq,
 }
 
 }  // namespace enmf
+
+using namespace enmf;
+
+// Launches the bounded-wait probe and reports what its device status word says.
+extern "C" enmf_status enmf_probe_wait(int32_t kind, int64_t cycles, int32_t* status) {
+  if (!status || (kind != 0 && kind != 1) || cycles < 1 || cycles > 4000000000LL)
+    return ENMF_EINVAL;
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, 64) != cudaSuccess) {
+    cudaGetLastError();
+    return ENMF_ENOMEM;
+  }
+  int err = 0;
+  cudaError_t e = cudaMemset(buf, 0, 64);
+  if (e == cudaSuccess) {
+    note_launch(1);
+    tc::probe_wait_kernel<<<1, 32>>>(kind, cycles, (const unsigned int*)buf, (int*)buf + 4);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&err, (int*)buf + 4, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ENMF_ECUDA;
+  }
+  *status = (err & ERR_TIMEOUT) ? ENMF_ETIMEOUT : ENMF_OK;
+  return ENMF_OK;
+}

@@ -78,6 +78,48 @@ def test_noalloc_matches_context_residual(m, n, r, xdt, fdt, ldx):
     assert a[0] > 0 and a[2] > 0
 
 
+def _oracle_bound(X, U, V, f_dtype):
+    """f of Eq. 1 by the oracle on the tensors' exact values, and a bound on
+    the allowed difference: the entries x - u.v are formed with a dot product
+    in the factors' type (r fused multiply-adds: each entry within
+    gamma_r (|U| |V|^T)_ij of exact, gamma_r = r u / (1 - r u)), so f moves by at
+    most gamma_r sum |E| (|U||V|^T) + gamma_r^2 sum (|U||V|^T)^2 / 2; the FP64
+    sums of m n terms add 2 m n 2^-53 f."""
+    from oracle import enmf_oracle as O
+    Xh = X.double().cpu().numpy()
+    Uh = U.double().cpu().numpy()
+    Vh = V.double().cpu().numpy()
+    m, n = Xh.shape
+    r = Uh.shape[1]
+    f = O.objective(Xh, Uh, Vh)
+    u = 2.0 ** -24 if f_dtype == torch.float32 else 2.0 ** -53
+    g = r * u / (1 - r * u)
+    P = np.abs(Uh) @ np.abs(Vh).T
+    E = Xh - Uh @ Vh.T
+    bound = g * float(np.sum(np.abs(E) * P)) + 0.5 * g * g * float(np.sum(P * P))
+    return f, O.rel_err(Xh, Uh, Vh), float(np.sum(Xh * Xh)), bound + 2 * m * n * 2.0 ** -53 * f
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("m,n,r,xdt,fdt,ldx", CASES)
+def test_noalloc_matches_the_oracle(m, n, r, xdt, fdt, ldx):
+    """The allocation-free residual against the oracle's f of Eq. 1, computed
+    in FP64 from the same (exactly converted) X, U and V, within the rounding
+    bound of the factors' dot product; two calls in a row."""
+    from paper_2605_19325_gb300 import binding as B
+    X, U, V = _inputs(m, n, r, xdt, fdt, ldx, seed=3)
+    f, rel, nx2, bound = _oracle_bound(X, U, V, fdt)
+    for _ in range(2):
+        out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+        B.enmf_residual_noalloc(X, U, V, out)
+        torch.cuda.synchronize()
+        a = out.cpu().numpy()
+        assert abs(a[0] - f) <= bound, (a[0], f, bound)
+        assert abs(a[2] - nx2) <= 2 * m * n * 2.0 ** -53 * nx2, (a[2], nx2)
+        # rel = sqrt(2 f) / ||X||: the relative bound halves through the root
+        assert abs(a[1] - rel) <= (0.5 * bound / f + 4 * m * n * 2.0 ** -53) * rel, (a[1], rel)
+
+
 @pytest.mark.gpu
 def test_noalloc_calls_leave_free_memory_unchanged():
     from paper_2605_19325_gb300 import binding as B
@@ -129,3 +171,36 @@ def test_noalloc_rejects_bad_arguments_before_any_launch():
 
 class _FakeStream:
     cuda_stream = 0
+
+
+def test_noalloc_wrapper_checks_tensors_before_calling_the_library(monkeypatch):
+    """Each malformed tensor argument is refused on the host: the C entry point
+    sees only pointers, so these would otherwise read or write out of bounds."""
+    from paper_2605_19325_gb300 import binding as B
+
+    def no_call():
+        raise AssertionError("the library was called")
+
+    monkeypatch.setattr(B, "lib", no_call)
+    f64, f32 = torch.float64, torch.float32
+    X = torch.zeros((10, 6), dtype=f64)
+    U = torch.zeros((10, 3), dtype=f64)
+    V = torch.zeros((6, 3), dtype=f64)
+    out = torch.zeros(3, dtype=f64)
+    bad = [
+        (X, U.t().contiguous().t(), V, out),                    # U not contiguous
+        (X, torch.zeros((3, 10), dtype=f64), V, out),           # U transposed shape
+        (X, U, torch.zeros((5, 3), dtype=f64), out),            # V too short
+        (X, U, torch.zeros((6, 4), dtype=f64), out),            # rank mismatch
+        (X, U, V.to(f32), out),                                 # mixed factor dtypes
+        (X, U, V, torch.zeros(3, dtype=f32)),                   # out3 not float64
+        (X, U, V, torch.zeros(2, dtype=f64)),                   # out3 too short
+        (X, U, V, torch.zeros(6, dtype=f64)[::2]),              # out3 strided
+        (X.t(), torch.zeros((6, 3), dtype=f64), torch.zeros((10, 3), dtype=f64), out),
+        (torch.zeros(1, 6, dtype=f64).expand(10, 6), U, V, out),   # row stride 0 < n
+        (torch.zeros(60, dtype=f64), U, V, out),                # X not a matrix
+        (X, U, V, out),                                         # tensors not on the GPU
+    ]
+    for args in bad:
+        with pytest.raises(ValueError):
+            B.enmf_residual_noalloc(*args)
