@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-f32", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-fp8", action="store_true")
+    ap.add_argument("--no-image", action="store_true")
     ap.add_argument("--only-fp8", action="store_true",
                     help="run the FP8-form leg alone (rank 0) and print its JSON")
     ap.add_argument("--fp8-forms", default="fp8,bf16,f32",
@@ -124,13 +125,13 @@ def make_inputs():
     return X, r
 
 
-def sweep_traffic():
-    """DRAM bytes per launch of the tensor-core sweep, from the committed ncu
-    summary, if that summary was taken on the current kernel source (its
-    recorded SHA-256 of tc_sweep.cu matches); else None."""
+def sweep_traffic(src_name="tc_sweep.cu", summary="sweep_tc_kernel_8192x6144_r32.md"):
+    """DRAM bytes per launch of a kernel, from its committed ncu summary, if
+    that summary was taken on the current kernel source (its recorded SHA-256
+    of the source file matches); else None."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2605_19325_gb300", "csrc", "tc_sweep.cu")
-    summ = os.path.join(ROOT, "profiles", "sweep_tc_kernel_8192x6144_r32.md")
+    src = os.path.join(ROOT, "paper_2605_19325_gb300", "csrc", src_name)
+    summ = os.path.join(ROOT, "profiles", summary)
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
         fields = {}
@@ -138,7 +139,7 @@ def sweep_traffic():
             if ":" in line and line.startswith("- "):
                 key, val = line[2:].split(":", 1)
                 fields[key.strip()] = val.strip().strip("`")
-        if fields.get("tc_sweep.cu sha256") != digest:
+        if fields.get(src_name + " sha256") != digest:
             return None
         return float(fields["dram bytes per launch (read + write)"])
     except (OSError, KeyError, ValueError):
@@ -157,7 +158,7 @@ def peaks():
 def cpu_oracle_sample(X, r, U_feas=None, V_feas=None):
     """Time the oracle on a bounded sample of the workload and scale to one
     solve: the SVD on a 2048 x 1536 block (scaled by m n min(m, n)), 3 ADMM
-    steps on the full W, 2 HALS alternations on the full X."""
+    steps on the full W, 1 HALS alternation on the full X."""
     from oracle import enmf_oracle as O
     m, n = X.shape
     t0 = time.perf_counter()
@@ -174,31 +175,37 @@ def cpu_oracle_sample(X, r, U_feas=None, V_feas=None):
         U_feas = np.abs(rng.standard_normal((m, r)))
         V_feas = np.abs(rng.standard_normal((n, r)))
     t0 = time.perf_counter()
-    O.iterate(X, U_feas, V_feas, 2)
-    t_it = (time.perf_counter() - t0) / 2
+    O.iterate(X, U_feas, V_feas, 1)
+    t_it = time.perf_counter() - t0
     solve_s = t_svd + 200 * t_admm + ITERS * t_it
     return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"SVD of a 2048x1536 block scaled by mn*min(m,n) ({t_svd:.1f} s), "
                        f"3 ADMM steps ({t_admm * 1e3:.0f} ms/step, x200), "
-                       f"2 HALS alternations on the full X ({t_it:.2f} s each, x{ITERS})"),
+                       f"1 HALS alternation on the full X ({t_it:.2f} s, x{ITERS})"),
             "solve_s_estimate": solve_s}
 
 
 def run_reference(args):
+    """The oracle arm: each step is one bounded sample of a solve of the same
+    workload (see cpu_oracle_sample); ms_per_step is the sample's wall time
+    and value the solves/s its component timings extrapolate to."""
     rank, world, local = dist_env()
     if world > 1 and rank != 0:
         return
     X, r = make_inputs()
-    times = []
+    est, wall = [], []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         cb = cpu_oracle_sample(X, r)
-        dt = cb["solve_s_estimate"]
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            times.append(dt)
-    ms = 1e3 * statistics.mean(times)
-    val = 1e3 / ms
+            est.append(cb["solve_s_estimate"])
+            wall.append(dt)
+    val = 1.0 / statistics.mean(est)
+    ms = 1e3 * statistics.mean(wall)
     cb["value"] = val
+    cb["step"] = ("one bounded sample per step; ms_per_step is its wall time, value the "
+                  "whole-solve rate extrapolated from it (%.1f s per solve)" % statistics.mean(est))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -314,6 +321,74 @@ def fp8_leg(forms=("fp8", "bf16", "f32")):
     return out
 
 
+IMAGE_WORKLOAD = "image stack 10304x4096 (92x112 images) r=49, 500 alternations"
+
+
+def image_leg(iters=500):
+    """Precision form on the image-stack workload (10304 x 4096, r = 49 padded
+    to 64 on the device; columns are 92 x 112 images of a nonnegative mixture
+    of 49 Gaussian bumps, scaled to [0, 1], + Uniform[0, 0.02] noise): the BF16
+    form (fused single pass in the HALS stage) timed over one solve after a
+    warm one, its main X kernel timed live with CUDA events (every fourth
+    alternation) as achieved GB/s of m n x 2 bytes, the two-pass sweep of the
+    same form for comparison, and the final relative-error gap to the plain
+    FP64 GPU form on the same matrix."""
+    import torch
+
+    import synth
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+
+    X, r = synth.image_stack(seed=0, dtype=np.float32)
+    m, n = X.shape
+    hbm = peaks().get("hbm_gbs", 6800.0)
+    Xd = torch.as_tensor(X, device="cuda")
+    out = {"workload": IMAGE_WORKLOAD, "m": m, "n": n, "r": r, "iterations": iters,
+           "target": "X read at >= 0.8 of measured HBM: <= %.1f us per read of X" %
+                     (m * n * 2 / (0.8 * hbm * 1e9) * 1e6)}
+
+    def solve(s):
+        s.svd_init()
+        s.rotate()
+        s.iterate(iters, trace=False, reset=1, sync_info=0)
+        return s.residual(direct=True)[1]
+
+    s = Solver(Xd, r, x_stream=torch.bfloat16)
+    for name, fused in (("bf16_fused", 1), ("bf16_two_pass", 0)):
+        avail = B.enmf_set_fused(s.ctx, fused)
+        if fused and not avail:
+            continue
+        solve(s)
+        torch.cuda.synchronize()
+        B.enmf_profile(s.ctx, 4)
+        B.enmf_profile_read(s.ctx, reset=1)
+        t0 = time.perf_counter()
+        rel = solve(s)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        kms, kn = B.enmf_profile_read(s.ctx, reset=1)
+        B.enmf_profile(s.ctx, 0)
+        us = 1e3 * kms / max(kn, 1)
+        gbs = m * n * 2 / (us * 1e-6) / 1e9
+        out[name] = {"ms_per_solve": ms, "rel_err": rel, "kernel_us_avg": us, "kernels_timed": kn,
+                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / hbm,
+                     "kernel": "fused single pass (X read once per alternation)" if fused
+                     else "one of the two tensor-core sweeps (X read twice per alternation)"}
+    s.close()
+    del Xd
+    X64 = torch.as_tensor(X.astype(np.float64), device="cuda")
+    s = Solver(X64, r)
+    t0 = time.perf_counter()
+    rel64 = solve(s)
+    torch.cuda.synchronize()
+    out["f64"] = {"ms_per_solve": 1e3 * (time.perf_counter() - t0), "rel_err": rel64}
+    s.close()
+    for name in ("bf16_fused", "bf16_two_pass"):
+        if name in out:
+            out[name]["rel_err_gap_vs_f64"] = abs(out[name]["rel_err"] - rel64) / rel64
+    return out
+
+
 def serving_leg(n_req):
     """Serving + batching workload: a Poisson stream of NMF requests with m, n
     log-uniform in [64, 4096] and r uniform in {4, 8, 16, 32, 64}, planted
@@ -420,12 +495,13 @@ def run_ours(args):
         return Solver(Xd32, r, x_stream=torch.bfloat16 if sdt == "bf16" else None)
 
     def solve_once(s, n_iter):
+        # one step: SVD start, rotation, n_iter alternations, direct residual
+        # (the same work as one enmf_solve call of the e2e leg)
         s.svd_init()
         s.rotate()
         s.iterate(n_iter, trace=False, reset=1, sync_info=0)
         f, rel, _ = s.residual(direct=True)
-        kk = s.kkt()
-        return rel, kk
+        return rel
 
     form = args.form
     s = make_solver(form)
@@ -447,7 +523,7 @@ def run_ours(args):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        rel, kk = solve_once(s, ITERS)
+        rel = solve_once(s, ITERS)
         b.record(stream)
         b.synchronize()
         step_ms.append(a.elapsed_time(b))
@@ -461,8 +537,29 @@ def run_ours(args):
     B.enmf_profile(s.ctx, 0)
     total_ms, value = replica_throughput(total_ms, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
+    kk = s.kkt()                       # the final KKT check, once, after the timed region
+    fused_on = bool(FORMS[form][2] == "bf16" and B.enmf_set_fused(s.ctx, 1))
     U_host = s.U.double().cpu().numpy()
     V_host = s.V.double().cpu().numpy()
+    # the same solve with the two-pass sweeps (X read twice per alternation),
+    # for comparison with the fused single pass
+    two_pass = None
+    if fused_on:
+        B.enmf_set_fused(s.ctx, 0)
+        solve_once(s, ITERS)
+        torch.cuda.synchronize()
+        B.enmf_profile(s.ctx, 4)
+        B.enmf_profile_read(s.ctx, reset=1)
+        t0 = time.perf_counter()
+        rel_tp = solve_once(s, ITERS)
+        torch.cuda.synchronize()
+        tp_ms = 1e3 * (time.perf_counter() - t0)
+        tms, tn = B.enmf_profile_read(s.ctx, reset=1)
+        B.enmf_profile(s.ctx, 0)
+        two_pass = {"ms_per_solve": tp_ms, "rel_err": rel_tp,
+                    "sweep_us_avg": 1e3 * tms / max(tn, 1), "sweeps_timed": tn,
+                    "note": "X V and X^T U as separate tensor-core sweeps, two reads of X per "
+                            "alternation; sweep_us_avg is one of them"}
     s.close()
 
     # the other forms, timed once after one warm solve each: the plain FP64
@@ -474,11 +571,27 @@ def run_ours(args):
         so = make_solver(other)
         solve_once(so, ITERS)
         torch.cuda.synchronize()
+        B.enmf_profile(so.ctx, 4)
+        B.enmf_profile_read(so.ctx, reset=1)
         t0 = time.perf_counter()
-        rel_o, kk_o = solve_once(so, ITERS)
+        rel_o = solve_once(so, ITERS)
         torch.cuda.synchronize()
-        others[other] = {"ms_per_solve": 1e3 * (time.perf_counter() - t0), "rel_err": rel_o,
-                         "kkt_pg_rel": kk_o.pg_rel}
+        oms, on = B.enmf_profile_read(so.ctx, reset=1)
+        B.enmf_profile(so.ctx, 0)
+        kk_o = so.kkt()
+        rec = {"ms_per_solve": 1e3 * (time.perf_counter() - t0), "rel_err": rel_o,
+               "kkt_pg_rel": kk_o.pg_rel}
+        if on:
+            # the SIMT sweeps are bound by the FMA pipe: 2 m n r flops per sweep
+            us = 1e3 * oms / on
+            tf = 2.0 * M * N * r / (us * 1e-6) / 1e12
+            pk_probe = B.enmf_probe_fma_peak(B.ENMF_F64 if other == "f64" else B.ENMF_F32) / 1e12
+            rec["sweep_roofline"] = {"bound": "alu", "sweep_us_avg": us, "sweeps_timed": on,
+                                     "achieved": tf, "unit": "TFLOP/s", "peak": pk_probe,
+                                     "frac": tf / pk_probe,
+                                     "peak_source": "measured %s FMA probe (enmf_probe_fma_peak)"
+                                                    % other.upper()}
+        others[other] = rec
         so.close()
 
     # end to end through the C ABI with host buffers (pinned), one call per solve
@@ -518,13 +631,22 @@ def run_ours(args):
         bytes_per_sweep = M * N * esize
         achieved = bytes_per_sweep / avg_sweep_s / 1e9 if sweeps else None
         peak = pk.get("hbm_gbs", 6800.0)
-        roof = {"kernel": "tensor-core X sweep (TMA + tcgen05, BF16 X)", "bound": "hbm",
+        if fused_on:
+            kname = ("fused single-pass HALS alternation (TMA + tcgen05 + cluster DSMEM, BF16 X): "
+                     "X V, U-half, X^T U_new in one read of X")
+            traffic = sweep_traffic("fused.cu", "fused_hals_kernel_8192x6144_r32.md")
+            span = "one fused kernel per HALS alternation (X_hi read once)"
+        else:
+            kname = "tensor-core X sweep (TMA + tcgen05, BF16 X)"
+            traffic = sweep_traffic()
+            span = "one tensor-core sweep kernel (X_hi pass incl. stream-K fix-up)"
+        roof = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": sweep_traffic(),
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "algorithmic_bytes_per_launch": bytes_per_sweep,
                 "sweep_us_avg": avg_sweep_s * 1e6, "sweeps_timed": sweeps,
                 "peak_source": "measured HBM copy (burst)" + (" [fallback]" if pk.get("fallback") else ""),
-                "timed_span": "one tensor-core sweep kernel (X_hi pass incl. stream-K fix-up)"}
+                "timed_span": span}
     else:
         flops_per_sweep = 2.0 * M * N * r
         achieved = flops_per_sweep / avg_sweep_s / 1e12 if sweeps else None
@@ -547,6 +669,9 @@ def run_ours(args):
     fp8 = None
     if world == 1 and not args.no_fp8:
         fp8 = fp8_leg(tuple(args.fp8_forms.split(",")))
+    image = None
+    if world == 1 and not args.no_image:
+        image = image_leg()
 
     ttt = None
     if "f64" in others or form == "f64":
@@ -570,7 +695,8 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "p50_ms": statistics.median(step_ms), "p99_ms": p99,
             "time_to_target": ttt, "final": {"rel_err": rel, "kkt_pg_rel": kk.pg_rel},
-            "other_forms": others, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+            "other_forms": others, "two_pass": two_pass, "roofline": roof, "cpu_baseline": cb,
+            "e2e": e2e, "image_stack": image,
             "clocks": clk, "gpu_launches": launches, "serving": serving, "fp8_form": fp8}
     print(json.dumps(line))
     if world > 1:

@@ -171,7 +171,8 @@ enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* R,
  * (Algorithm 2) with d_i = ||g_i||^2 / (g_i G g_i^T) (Eq. 10/11), stopping at
  * ||M+ o grad|| < eps ||grad_init|| or pbcd_max_iter sweeps.  Afterwards it is
  * a HALS sweep of U's columns then V's columns.  Each alternation reads X
- * once for X V and once for X^T U.  trace (device, FP64, n_iter entries, may
+ * once for X V and once for X^T U (in the HALS stage of the tensor-core
+ * forms optionally once for both, see enmf_set_fused).  trace (device, FP64, n_iter entries, may
  * be NULL) receives f(U, V) of Eq. 1 after every V-half, from the expansion
  * 1/2 ||X||^2 - <X^T U, V> + 1/2 <U^T U, V^T V> summed in FP64. */
 typedef struct {
@@ -348,6 +349,37 @@ enmf_status enmf_profile(enmf_ctx* ctx, int32_t every);
 enmf_status enmf_profile_read(enmf_ctx* ctx, double* sweep_ms, int64_t* sweeps, int32_t reset);
 enmf_status enmf_probe_fma_peak(int32_t dtype, double* flops_per_s);
 long long enmf_launch_count(void);
+
+/* ---- The fused single-pass alternation (no counterpart in the paper) -----
+ * In the HALS stage of the BF16 / FP16 tensor-core forms (rank padded to 32
+ * or 64, and X narrow enough that a cluster of CTAs holds V's column slices
+ * in shared memory: n up to about 12,000 at rank pad 32), enmf_iterate runs
+ * each alternation as one pass over X: per 128-row panel, X V, the HALS
+ * update of the panel's rows of U (Sec. 4.3) and X_panel^T U_new for the
+ * V-half, so X is read once per alternation instead of twice.  From a fresh
+ * ascent stage the first n_shift alternations (the ascent stage, which ends
+ * within them) use the two-pass sweeps, and the call then synchronises once
+ * to read the stage.  The fused pass is OFF by default: on a GB300 its
+ * exchange across the cluster for every 128-row panel is latency-bound, and
+ * at the measured shapes the two-pass sweeps are faster.  enmf_set_fused(ctx,
+ * 1) turns it on, 0 off; *available (may be NULL) tells whether the context
+ * can run it at all. */
+enmf_status enmf_set_fused(enmf_ctx* ctx, int32_t on, int32_t* available);
+/* The fused pass's launch shape, for reports: shape[0] = 1 if available,
+ * shape[1] = CTAs per cluster, [2] = clusters, [3] = columns of X per CTA,
+ * [4] = X stages in shared memory, [5] = dynamic shared memory per CTA (KB). */
+enmf_status enmf_fused_shape(enmf_ctx* ctx, int32_t* shape);
+/* Diagnostics: with the environment variable ENMF_FUSED_STAMPS set when the
+ * context is created, the fused pass records %globaltimer stamps (ns) of its
+ * phases, per CTA and panel, overwritten by every launch.  *count receives the
+ * number of 64-bit stamps; they are copied to the host buffer out when
+ * cap >= *count (then the call synchronises).  Layout: stamp e (0..7) of local
+ * panel p of CTA c at (c (P + 1) + p) 8 + e, P = 32 (later panels are not
+ * recorded); panel slot P holds the CTA's start (e = 0) and end (e = 1).  Events: 0 X V
+ * accumulator ready, 1 every CTA staged its partial, 2 rows summed, 3 HALS
+ * done, 4 panel buffer free, 5 rows pushed, 6 (MMA thread) panel's U ready,
+ * 7 X^T U issued.  *count = 0 when not recording. */
+enmf_status enmf_fused_stamps(enmf_ctx* ctx, long long* out, int64_t cap, int64_t* count);
 
 /* ---- Bounded device waits (no counterpart in the paper) ------------------
  * Every device-side wait of the library is bounded; an expired wait records

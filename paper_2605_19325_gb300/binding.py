@@ -100,6 +100,9 @@ _SIGS = {
     "enmf_probe_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
     "enmf_launch_count": (C.c_longlong, []),
     "enmf_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
+    "enmf_set_fused": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "enmf_fused_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "enmf_fused_stamps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "enmf_probe_wait": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(C.c_int32)]),
     "enmf_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "enmf_batch_destroy": (None, [C.c_void_p]),
@@ -319,6 +322,32 @@ def enmf_batch_tune(b):
 def enmf_set_wait_limit(ctx, cycles):
     """Spin limit (SM cycles) of the context's grid barriers; 0 = default."""
     check(lib().enmf_set_wait_limit(ctx, int(cycles)), "enmf_set_wait_limit")
+
+
+def enmf_set_fused(ctx, on):
+    """Use the fused single-pass HALS alternation (1, default) or not (0);
+    returns whether the context can run it."""
+    av = C.c_int32(0)
+    check(lib().enmf_set_fused(ctx, 1 if on else 0, C.byref(av)), "enmf_set_fused")
+    return bool(av.value)
+
+
+def enmf_fused_shape(ctx):
+    """(available, CTAs per cluster, clusters, columns per CTA, stages, smem KB)."""
+    out = (C.c_int32 * 6)()
+    check(lib().enmf_fused_shape(ctx, out), "enmf_fused_shape")
+    return tuple(out)
+
+
+def enmf_fused_stamps(ctx):
+    """The fused pass's phase stamps (ns) as a list, empty when not recorded."""
+    n = C.c_int64(0)
+    check(lib().enmf_fused_stamps(ctx, None, 0, C.byref(n)), "enmf_fused_stamps")
+    if n.value == 0:
+        return []
+    buf = (C.c_longlong * n.value)()
+    check(lib().enmf_fused_stamps(ctx, buf, n.value, C.byref(n)), "enmf_fused_stamps")
+    return list(buf)
 
 
 def enmf_probe_wait(kind, cycles):

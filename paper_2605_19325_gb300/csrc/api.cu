@@ -158,6 +158,12 @@ extern "C" enmf_status enmf_workspace_size(const enmf_problem* p, size_t* bytes)
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   *bytes = plan(p, sms, nullptr) + tc_plan(p, sms).total;
+  if (tc_form(p) && p->stream_dtype != ENMF_E4M3) {
+    const FusedPlan fp = fused_plan(p->m, p->n, tc_rank_pad(p->r));
+    if (fp.ok)
+      *bytes += al256(sizeof(FusedDesc)) + al256((size_t)fp.Q * p->n * p->r * 4) +
+                al256((size_t)fp.Q * fp.C * p->r * p->r * 8) + 256;
+  }
   return ENMF_OK;
 }
 
@@ -315,7 +321,52 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
       return ENMF_ECUDA;
     }
   }
+  // the fused single-pass HALS alternation (fused.cu), when the shape fits
+  if (ctx->tc && !ctx->xq) {
+    const FusedPlan fp = fused_plan(p->m, p->n, ctx->rp);
+    if (fp.ok) {
+      const size_t xtu = (size_t)fp.Q * p->n * p->r * 4;
+      const size_t gp = (size_t)fp.Q * fp.C * p->r * p->r * 8;
+      const size_t bytes = al256(sizeof(FusedDesc)) + al256(xtu) + al256(gp) + 256;
+      if (cudaMalloc(&ctx->fzws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->tcws) cudaFree(ctx->tcws);
+        cudaFree(ctx->ws);
+        delete ctx;
+        return ENMF_ENOMEM;
+      }
+      cudaMemsetAsync(ctx->fzws, 0, bytes, ctx->stream);
+      char* f = (char*)ctx->fzws;
+      ctx->dfz = (FusedDesc*)f;
+      f += al256(sizeof(FusedDesc));
+      ctx->fz_xtu = (float*)f;
+      f += al256(xtu);
+      ctx->fz_gpart = (double*)f;
+      f += al256(gp);
+      ctx->fz_counter = (int*)f;
+      ctx->fz_plan = fp;
+      if (getenv("ENMF_FUSED_STAMPS")) {
+        ctx->fz_stamp_panels = 32;   // per CTA, recorded in shared memory
+        const size_t sb = (size_t)fp.Q * fp.C * (ctx->fz_stamp_panels + 1) * 8 * 8;
+        if (cudaMalloc(&ctx->fz_stamps, sb) != cudaSuccess) {
+          cudaGetLastError();
+          ctx->fz_stamps = nullptr;
+        } else {
+          cudaMemsetAsync(ctx->fz_stamps, 0, sb, ctx->stream);
+        }
+      }
+    }
+  }
+  // The fused pass is built and checked but, on this GPU, slower than the two
+  // passes at the measured shapes (its per-panel exchange across the cluster
+  // is latency-bound): off unless enmf_set_fused asks for it.
+  ctx->fz_enabled = 0;
+  {
+    const char* e = getenv("ENMF_L2_KEEP");   // diagnostics: 0 = normal L2 policy for X_hi
+    ctx->l2_keep = (e && atoi(e) == 0) ? 0 : 1;
+  }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    if (ctx->fzws) cudaFree(ctx->fzws);
     if (ctx->tcws) cudaFree(ctx->tcws);
     cudaFree(ctx->ws);
     delete ctx;
@@ -374,7 +425,10 @@ extern "C" void enmf_destroy(enmf_ctx* ctx) {
   if (ctx->tcws) cudaFree(ctx->tcws);
   if (ctx->prof_every >= 0 && ctx->pev[0])
     for (int i = 0; i < 2 * PROF_PAIRS; ++i) cudaEventDestroy(ctx->pev[i]);
-  if (ctx->iter_graph) cudaGraphExecDestroy(ctx->iter_graph);
+  for (int g = 0; g < 2; ++g)
+    if (ctx->iter_graph[g]) cudaGraphExecDestroy(ctx->iter_graph[g]);
+  if (ctx->fzws) cudaFree(ctx->fzws);
+  if (ctx->fz_stamps) cudaFree(ctx->fz_stamps);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
@@ -485,6 +539,7 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
     info->residual = res;
   }
   ctx->state_valid = false;
+  ctx->hals_known = false;
   if (rc) return rc;
   return res <= o.tol ? ENMF_OK : ENMF_ENOTCONV;
 }
@@ -577,6 +632,7 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
     info->neg_mass_out = nm_out;
   }
   ctx->state_valid = false;
+  ctx->hals_known = false;
   return rc;
 }
 
@@ -665,6 +721,7 @@ static const SweepProb* tc_desc(enmf_ctx* ctx, int slot, int mode, bool lo, floa
   d.out = out;
   d.corr = corr;
   d.f16 = ctx->tf16;
+  d.l2hint = lo ? 2 : ctx->l2_keep;
   if (ctx->xq && !lo) {
     d.xq = 1;
     d.ntj = (int)((p.n + 127) / 128);
@@ -848,6 +905,7 @@ extern "C" enmf_status enmf_state_import(enmf_ctx* ctx, const void* buf, size_t 
   rc = sync_status(ctx);
   if (rc) return rc;
   ctx->state_valid = true;
+  ctx->hals_known = false;
   return ENMF_OK;
 }
 
@@ -891,12 +949,12 @@ extern "C" enmf_status enmf_sweep(enmf_ctx* ctx, const void* X, const void* U, c
 // key is unchanged.  Returns false (nothing enqueued) when graphs cannot be
 // used, so the caller launches the loop directly.
 template <typename Loop>
-static bool replay_iteration(enmf_ctx* ctx, const enmf_ctx::IterKey& key, Loop&& loop) {
+static bool replay_iteration(enmf_ctx* ctx, int slot, const enmf_ctx::IterKey& key, Loop&& loop) {
   if (ctx->no_graph || key.n_iter < 4) return false;
-  if (!ctx->iter_graph || !(ctx->iter_key == key)) {
-    if (ctx->iter_graph) {
-      cudaGraphExecDestroy(ctx->iter_graph);
-      ctx->iter_graph = nullptr;
+  if (!ctx->iter_graph[slot] || !(ctx->iter_key[slot] == key)) {
+    if (ctx->iter_graph[slot]) {
+      cudaGraphExecDestroy(ctx->iter_graph[slot]);
+      ctx->iter_graph[slot] = nullptr;
     }
     if (!ctx->cap_stream &&
         cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -928,18 +986,18 @@ static bool replay_iteration(enmf_ctx* ctx, const enmf_ctx::IterKey& key, Loop&&
       ctx->no_graph = true;
       return false;
     }
-    ctx->iter_graph = exec;
-    ctx->iter_key = key;
-    ctx->iter_graph_kernels = kernels;
-    ctx->iter_graph_npev = npev;
+    ctx->iter_graph[slot] = exec;
+    ctx->iter_key[slot] = key;
+    ctx->iter_graph_kernels[slot] = kernels;
+    ctx->iter_graph_npev[slot] = npev;
   }
-  if (cudaGraphLaunch(ctx->iter_graph, ctx->stream) != cudaSuccess) {
+  if (cudaGraphLaunch(ctx->iter_graph[slot], ctx->stream) != cudaSuccess) {
     cudaGetLastError();
     ctx->no_graph = true;
     return false;
   }
-  note_launch(ctx->iter_graph_kernels);
-  ctx->npev += ctx->iter_graph_npev;
+  note_launch(ctx->iter_graph_kernels[slot]);
+  ctx->npev += ctx->iter_graph_npev[slot];
   return true;
 }
 
@@ -994,6 +1052,7 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
   cudaStream_t s = ctx->stream;
   enmf_status rc = check_staged(ctx, X);
   if (rc) return rc;
+  const bool fresh = o.reset != 0 || !ctx->state_valid;   // a new ascent stage starts
   ctx_iter_prologue(ctx, X, U, V, o.n_shift, o.reset != 0);
   if (ctx->tc) {
     // the iteration's sweep descriptors, current before any capture
@@ -1002,9 +1061,10 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
     tc_desc(ctx, 2, 1, false, (float*)ctx->N0, ctx->xl ? ctx->cu : nullptr);
     tc_desc(ctx, 3, 1, true, ctx->cu, nullptr);
   }
-  // the alternations: everything on the device, nothing read back
-  auto loop = [&]() {
-    for (int it = 0; it < o.n_iter; ++it) {
+  // the alternations: everything on the device, nothing read back (except
+  // the stage once, below)
+  auto general = [&](int it0, int it1) {
+    for (int it = it0; it < it1; ++it) {
       // precision form: refresh the X_lo terms every correct_every alternations
       const int corr = (it % o.correct_every == 0) ? 2 : 1;
       const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
@@ -1015,10 +1075,98 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
       run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu, o.trace, it);
     }
   };
-  if (!replay_iteration(ctx, {X, U, V, o.trace, o.n_iter, o.pbcd_max_iter, o.n_shift,
-                              o.correct_every, ctx->prof_every, o.eps},
-                        loop))
-    loop();
+  // HALS stage, tensor-core form: one fused pass over X per alternation
+  // (fused.cu) for the U-half and both products, then the V-half over the
+  // clusters' X^T U partials; the X_lo passes of a correction alternation run
+  // before (X_lo V) and after (X_lo^T U, with the new U) the fused pass.
+  auto fused = [&](int it0, int it1) {
+    const int rp = ctx->rp;
+    for (int it = it0; it < it1; ++it) {
+      const int corr = (it % o.correct_every == 0) ? 2 : 1;
+      const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
+                       ctx->npev + 2 <= 2 * PROF_PAIRS;
+      if (corr == 2 && ctx->xl)
+        launch_tc_group(0, rp, ctx->dprob + 1, 1, tc_units(ctx, 0), ctx->tcpart, ctx->tccount,
+                        ctx->num_sms, ctx->err, s);
+      prof_mark(ctx, rec);
+      launch_fused(ctx->dfz, ctx->fz_plan, rp, s);
+      prof_mark(ctx, rec);
+      if (corr == 2 && ctx->xl)
+        launch_tc_group(1, rp, ctx->dprob + 3, 1, tc_units(ctx, 1), ctx->tcpart, ctx->tccount,
+                        ctx->num_sms, ctx->err, s);
+      HalfArgs a = ctx_half_args(ctx, 1, V, nullptr, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu,
+                                 o.trace, it);
+      a.sum_part = ctx->fz_xtu;
+      a.sum_n = ctx->fz_plan.Q;
+      a.cut_corr = ctx->xl ? ctx->cu : nullptr;
+      launch_half_step(a, ctx->grid_v, s);
+    }
+  };
+  auto run = [&](int slot, int it0, int it1) {
+    if (it1 <= it0) return;
+    enmf_ctx::IterKey key = {X, U, V, o.trace, it1 - it0, o.pbcd_max_iter, o.n_shift,
+                             o.correct_every, ctx->prof_every, o.eps, it0};
+    auto body = [&]() {
+      if (slot == 0) general(it0, it1);
+      else fused(it0, it1);
+    };
+    if (!replay_iteration(ctx, slot, key, body)) body();
+  };
+  const bool fz_ok = ctx->tc && ctx->fz_plan.ok && ctx->fz_enabled && ctx->fzws;
+  if (fresh) ctx->hals_known = false;
+  int it = 0;
+  if (fz_ok && !ctx->hals_known && o.n_iter > 0) {
+    // From a reset the ascent stage ends within n_shift alternations (the
+    // worst negative entry is nonnegative after n_shift shifts of
+    // max(-F) / (n_shift - 1/2)); run those with the two-pass sweeps, then
+    // read the stage once.
+    const int pre = fresh ? (o.n_iter < o.n_shift ? o.n_iter : o.n_shift) : 0;
+    run(0, 0, pre);
+    rc = check_launch(ctx);
+    if (rc) return rc;
+    int stage = 0;
+    CK(cudaMemcpyAsync(&stage, &ctx->st->stage, sizeof(int), cudaMemcpyDeviceToHost, s));
+    rc = sync_status(ctx);
+    if (rc) return rc;
+    ctx->hals_known = stage == 1;
+    it = pre;
+  }
+  if (fz_ok && ctx->hals_known && it < o.n_iter) {
+    FusedDesc d;
+    memset(&d, 0, sizeof(d));
+    memcpy(d.mapX, ctx->maps[MAP_XH], sizeof(d.mapX));
+    memcpy(d.mapVh, ctx->maps[MAP_VH], sizeof(d.mapVh));
+    memcpy(d.mapVl, ctx->maps[MAP_VL], sizeof(d.mapVl));
+    d.m = m;
+    d.n = n;
+    d.ldm = ctx->ldm;
+    d.r = p.r;
+    d.S = ctx->fz_plan.S;
+    d.T = ctx->fz_plan.T;
+    d.C = ctx->fz_plan.C;
+    d.Q = ctx->fz_plan.Q;
+    d.npanels = ctx->fz_plan.npanels;
+    d.f16 = ctx->tf16;
+    d.Gv = ctx->Gv;
+    d.cv = ctx->xl ? ctx->cv : nullptr;
+    d.U = (float*)U;
+    d.uth = ctx->uth;
+    d.utl = ctx->utl;
+    d.xtu = ctx->fz_xtu;
+    d.gpart = ctx->fz_gpart;
+    d.Gu = ctx->Gu;
+    d.counter = ctx->fz_counter;
+    d.err = ctx->err;
+    d.stamps = ctx->fz_stamps;
+    d.stamp_panels = ctx->fz_stamp_panels;
+    if (memcmp(&d, &ctx->hfz, sizeof(d)) != 0) {
+      ctx->hfz = d;
+      CK(cudaMemcpyAsync(ctx->dfz, &ctx->hfz, sizeof(d), cudaMemcpyHostToDevice, s));
+    }
+    run(1, it, o.n_iter);
+  } else {
+    run(0, it, o.n_iter);
+  }
   rc = check_launch(ctx);
   if (rc) return rc;
   if (ctx->npev > 0) {
@@ -1038,6 +1186,44 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
       info->s_v = hst.s_v;
     }
     return rc;
+  }
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_set_fused(enmf_ctx* ctx, int32_t on, int32_t* available) {
+  GUARD(ctx);
+  if (on != 0 && on != 1) return ENMF_EINVAL;
+  ctx->fz_enabled = on;
+  if (available) *available = (ctx->tc && ctx->fz_plan.ok && ctx->fzws) ? 1 : 0;
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_fused_shape(enmf_ctx* ctx, int32_t* shape) {
+  GUARD(ctx);
+  if (!shape) return ENMF_EINVAL;
+  const FusedPlan& f = ctx->fz_plan;
+  shape[0] = f.ok && ctx->fzws ? 1 : 0;
+  shape[1] = f.C;
+  shape[2] = f.Q;
+  shape[3] = f.S;
+  shape[4] = f.nst;
+  shape[5] = (int32_t)(f.smem / 1024);
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_fused_stamps(enmf_ctx* ctx, long long* out, int64_t cap,
+                                         int64_t* count) {
+  GUARD(ctx);
+  if (!count) return ENMF_EINVAL;
+  if (!ctx->fz_stamps) {
+    *count = 0;
+    return ENMF_OK;
+  }
+  const int64_t n = (int64_t)ctx->fz_plan.Q * ctx->fz_plan.C * (ctx->fz_stamp_panels + 1) * 8;
+  *count = n;
+  if (out && cap >= n) {
+    CK(cudaMemcpyAsync(out, ctx->fz_stamps, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    return sync_status(ctx);
   }
   return ENMF_OK;
 }

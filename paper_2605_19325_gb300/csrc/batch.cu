@@ -121,6 +121,7 @@ enmf_status rebuild(enmf_batch* b) {
       d.out = lo ? lo_out : main_out;
       d.corr = (!lo && ctx->xl) ? lo_out : nullptr;
       d.f16 = ctx->tf16;
+      d.l2hint = lo ? 2 : 0;   // X_lo is read once per correction period
       b->h_sw[q].push_back(d);
       b->W[q] += units;
       tiles[q] += t;

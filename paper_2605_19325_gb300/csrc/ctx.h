@@ -55,18 +55,35 @@ struct enmf_ctx {
     double* trace;
     int n_iter, pbcd_max_iter, n_shift, correct_every, prof_every;
     double eps;
+    int it0;                // first alternation index of the captured range
     bool operator==(const IterKey& o) const {
       return X == o.X && U == o.U && V == o.V && trace == o.trace && n_iter == o.n_iter &&
              pbcd_max_iter == o.pbcd_max_iter && n_shift == o.n_shift &&
-             correct_every == o.correct_every && prof_every == o.prof_every && eps == o.eps;
+             correct_every == o.correct_every && prof_every == o.prof_every && eps == o.eps &&
+             it0 == o.it0;
     }
   };
+  // slot 0: the alternation loop with the two-pass sweeps (any stage);
+  // slot 1: the fused single-pass loop (HALS stage, fused.cu)
   cudaStream_t cap_stream;
-  cudaGraphExec_t iter_graph;
-  IterKey iter_key;
-  int iter_graph_kernels;   // kernel launches per replay
-  int iter_graph_npev;      // profiling events recorded per replay
+  cudaGraphExec_t iter_graph[2];
+  IterKey iter_key[2];
+  int iter_graph_kernels[2];   // kernel launches per replay
+  int iter_graph_npev[2];      // profiling events recorded per replay
   bool no_graph;            // capture failed once: launch eagerly
+  // fused single-pass HALS alternation (fused.cu); fz_plan.ok = 0: not used
+  FusedPlan fz_plan;
+  int fz_enabled;           // enmf_set_fused (default 1)
+  int l2_keep;              // L2 policy of X_hi tiles (1 evict_last; ENMF_L2_KEEP=0 for normal)
+  bool hals_known;          // the device state is known to be in the HALS stage
+  void* fzws;               // its buffers: descriptor, X^T U partials, Gram partials, counter
+  FusedDesc* dfz;
+  FusedDesc hfz;
+  float* fz_xtu;
+  double* fz_gpart;
+  int* fz_counter;
+  long long* fz_stamps;     // diagnostics (ENMF_FUSED_STAMPS set at creation), else null
+  int fz_stamp_panels;
   // event timing of the X sweeps (enmf_profile)
   int prof_every;
   int npev;

@@ -100,6 +100,42 @@ template <typename TF, int E>
 __device__ __forceinline__ void load_a_row(const HalfArgs& a, const TF* A, int64_t i, bool live,
                                            int k, int sub, TF (&v)[E]) {
   if constexpr (sizeof(TF) == 4) {
+    if (a.sum_part) {
+      // the fused kernel's per-cluster partials, summed in cluster order
+      // (every load issued before the first add)
+      float acc[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[e] = 0.f;
+      const int64_t stride = a.rows * (int64_t)k;
+      const float* src = a.sum_part + i * k;
+      int qq = 0;
+      for (; qq + 4 <= a.sum_n; qq += 4) {
+        float t[4][E];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int l = sub + LPR * e;
+            t[u][e] = (live && l < k) ? __ldcg(src + (qq + u) * stride + l) : 0.f;
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int e = 0; e < E; ++e) acc[e] += t[u][e];
+      }
+      for (; qq < a.sum_n; ++qq)
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int l = sub + LPR * e;
+          if (live && l < k) acc[e] += __ldcg(src + qq * stride + l);
+        }
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int l = sub + LPR * e;
+        v[e] = (live && l < k) ? (a.cut_corr ? acc[e] + a.cut_corr[i * k + l] : acc[e]) : TF(0);
+      }
+      return;
+    }
     if (a.cut_part && live) {
       const int64_t W = a.cut_W, G = a.cut_G;
       const int64_t tile = i / 128;

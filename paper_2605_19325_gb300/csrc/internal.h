@@ -131,6 +131,11 @@ struct HalfArgs {
   const float* cut_corr;
   int64_t cut_W, cut_G;   // the sweep's work units and grid
   int cut_nkb, cut_rp;    // k-blocks per tile, slot row stride
+  // A came from the fused kernel (fused.cu): row i is the sum over the
+  // clusters q < sum_n, in cluster order, of sum_part[(q rows + i) k + l],
+  // plus cut_corr (the X_lo term) when given.  Null: not used.
+  const float* sum_part;
+  int sum_n;
 };
 // hstep.cu: one cooperative launch per half step; grid <= half_step_grid().
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);
@@ -223,6 +228,8 @@ struct alignas(64) SweepProb {
   int xq;           // X as e4m3 codes with per-tile exponents (the FP8 form)
   int ntj;          // FP8 form: column tiles of X (exponent row stride)
   const int* xexp;  // FP8 form: exponent k of each 128 x 128 tile of X
+  int l2hint;       // X tiles' L2 policy: 0 normal, 1 evict_last (X_hi, read
+                    // every alternation), 2 evict_first (X_lo, read rarely)
 };
 // Fills the sizes of d (maps and pointers set by the caller) and returns its
 // work units (tiles x k-blocks) and tiles through *units / *tiles.
@@ -259,6 +266,39 @@ void launch_split_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xh,
 void launch_quant_x(const float* X, int64_t m, int64_t n, int64_t ldx, void* xq, int64_t ldq,
                     void* xl, int64_t ldh, int* xexp, int* err, cudaStream_t s);
 constexpr int TC_KB_XV = 128, TC_KB_XT = 128;
+
+// ---------------------------------------------------------------- fused.cu
+// The single-pass HALS U-half (fused.cu), in device memory.  X_hi and the V^T
+// pair are read through TMA maps (X: box 64 x 128; V^T hi / lo: box 64 x rp).
+struct alignas(64) FusedDesc {
+  unsigned char mapX[128];
+  unsigned char mapVh[128];
+  unsigned char mapVl[128];
+  int64_t m, n, ldm;
+  int r, S, T, C, Q, npanels, f16;
+  const double* Gv;   // V^T V (r x r)
+  const float* cv;    // X_lo V (m x r) added to X V, or null
+  float* U;           // m x r, updated in place
+  void* uth;          // U^T pair written for the X_lo pass (rp x ldm, 16-bit)
+  void* utl;
+  float* xtu;         // Q x n x r: each cluster's X^T U partial
+  double* gpart;      // (Q C) x r x r: each CTA's U^T U partial
+  double* Gu;         // r x r: U^T U, summed by the last CTA
+  int* counter;       // arrival counter, zero between launches
+  int* err;
+  // diagnostics: %globaltimer stamps per CTA and panel (null: none recorded);
+  // slot (cta * (stamp_panels + 1) + panel) * 8 + event
+  long long* stamps;
+  int stamp_panels;
+};
+// Launch shape: clusters of C CTAs, slice width S = T x 128 columns, ring
+// depth nst, Q clusters (ok = 0: the shape does not fit; use the two passes).
+struct FusedPlan {
+  int ok, C, S, T, nst, Q, npanels;
+  size_t smem;
+};
+FusedPlan fused_plan(int64_t m, int64_t n, int rp);
+cudaError_t launch_fused(const FusedDesc* fd, const FusedPlan& pl, int rp, cudaStream_t s);
 
 // KKT finalisation: combine the two factors' partial measures.
 void launch_kkt_final(const double* pu, const double* pv, double* out, cudaStream_t s);

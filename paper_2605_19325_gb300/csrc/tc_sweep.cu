@@ -190,9 +190,11 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       pv.load(probs, np, p, W);
       int64_t i = 0;
       int64_t q_issued = 0, b_issued = 0;   // XQ: units whose copies were requested
+      uint64_t xpol = l2_policy(pv.d->l2hint);
       for (int64_t w = w0; w < w1 && !*(volatile int*)&aborted; ++w, ++i) {
         if (w >= pv.we) {
           pv.load(probs, np, ++p, W);
+          xpol = l2_policy(pv.d->l2hint);
           prefetch_map(reinterpret_cast<const CUtensorMap*>(pv.d->mapX));
           prefetch_map(reinterpret_cast<const CUtensorMap*>(pv.d->mapBh));
           prefetch_map(reinterpret_cast<const CUtensorMap*>(pv.d->mapBl));
@@ -213,8 +215,8 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
           const int k0 = (int)((lw % pv.nkb) * KB);
           uint8_t* sq = qring + (size_t)q * Q_BYTES;
           mbar_expect_tx(&qfull_bar[q], Q_BYTES);
-          if (MODE == 0) tma_load(sq, mapX, &qfull_bar[q], k0, t0);
-          else tma_load(sq, mapX, &qfull_bar[q], t0, k0);
+          if (MODE == 0) tma_load_hint(sq, mapX, &qfull_bar[q], k0, t0, xpol);
+          else tma_load_hint(sq, mapX, &qfull_bar[q], t0, k0, xpol);
           q_issued = i + 1;
           const int bs = (int)(i % bstages);
           const uint32_t bph = (uint32_t)(i / bstages) & 1u;
@@ -251,11 +253,11 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
         mbar_expect_tx(&full_bar[s], STAGE);
         if (MODE == 0) {
           // two adjacent 64-column boxes: 256 contiguous bytes of each X row
-          tma_load(sa, mapX, &full_bar[s], k0, t0);
-          tma_load(sa + A_BYTES / 2, mapX, &full_bar[s], k0 + 64, t0);
+          tma_load_hint(sa, mapX, &full_bar[s], k0, t0, xpol);
+          tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[s], k0 + 64, t0, xpol);
         } else {
-          tma_load(sa, mapX, &full_bar[s], t0, k0);
-          tma_load(sa + A_BYTES / 2, mapX, &full_bar[s], t0 + 64, k0);
+          tma_load_hint(sa, mapX, &full_bar[s], t0, k0, xpol);
+          tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[s], t0 + 64, k0, xpol);
         }
         tma_load(sbh, mapBh, &full_bar[s], k0, 0);
         tma_load(sbh + B_BYTES / 2, mapBh, &full_bar[s], k0 + 64, 0);
