@@ -447,3 +447,215 @@ def quantize_fp8_tiles(X32, tile=128):
     X_hi = Q * scale
     X_lo = bf16_round((X - X_hi).astype(np.float32))
     return e4m3_code(Q), K, X_hi, X_lo
+
+
+# --------------------------------------------------------------------------
+# Equivalence of two factorisations (Sec. 5, App. F and App. H).
+def _cosines(A, B):
+    """cos(A_i, B_j) for all column pairs; a zero column has cosine 0."""
+    na = np.linalg.norm(A, axis=0)
+    nb = np.linalg.norm(B, axis=0)
+    G = A.T @ B
+    den = np.outer(na, nb)
+    return np.where(den > 0, G / np.where(den > 0, den, 1.0), 0.0)
+
+
+@dataclass
+class GeneralTransform:
+    R1: np.ndarray
+    lam: np.ndarray      # diagonal of Lambda, descending
+    R2: np.ndarray
+    delta_u: float       # ||U_alg - U_e R1 Lambda R2^T||_F
+    delta_v: float       # ||V_alg - V_e R1 Lambda^-1 R2^T||_F
+
+
+def generalized_transform(Ue, Ve, Ualg, Valg):
+    """App. F: R1, Lambda, R2 with U_alg ~ U_e R1 Lambda R2^T and
+    V_alg ~ V_e R1 Lambda^-1 R2^T.
+
+    With the thin SVD U_e = P Gamma Q^T, the matrix Z = Q Gamma^-1 P^T U_alg
+    (the least-squares map from U_e to U_alg) has the SVD Z = R1 Lambda R2^T;
+    the residuals measure how far (U_alg, V_alg) is from such a transform of
+    (U_e, V_e) (zero when the two factorisations are equivalent, Sec. 5).
+    """
+    P, g, Qt = np.linalg.svd(Ue, full_matrices=False)
+    Z = Qt.T @ np.diag(1.0 / g) @ P.T @ Ualg
+    R1, lam, R2t = np.linalg.svd(Z)
+    R2 = R2t.T
+    du = float(np.linalg.norm(Ualg - Ue @ R1 @ np.diag(lam) @ R2.T))
+    dv = float(np.linalg.norm(Valg - Ve @ R1 @ np.diag(1.0 / lam) @ R2.T))
+    return GeneralTransform(R1, lam, R2, du, dv)
+
+
+def round1(x):
+    """Rounding to one decimal place, as the integer k with k / 10 the
+    rounded value: floor(10 x + 1/2) (reading of App. H; the paper names no
+    tie rule)."""
+    return np.floor(10.0 * np.asarray(x, dtype=np.float64) + 0.5).astype(np.int64)
+
+
+def permutation_check(UA, UB, eps=0.05, keep_frac=0.9):
+    """App. H: the columns of U_B that are scaled permutations of columns of U_A.
+
+    Step 1 (candidates): column i of U_A pairs with the column j of U_B of
+    largest cos(U_A^(i), U_B^(j)) when that cosine is >= 1 - eps.  Reading: the
+    pairs are one to one, taken greedily in decreasing cosine (ties by lower
+    i, then lower j).
+    Step 2 (cross-similarity pruning): on the candidate columns (in the order
+    of U_A's indices) M = cos(U_Asub, U_Asub), N = cos(U_Bsub, U_Bsub) and
+    S = cos(U_Asub, U_Bsub); each column of the three is sorted in descending
+    order and rounded to one decimal (round1); candidate c is kept when the
+    entries of M's column c equal those of N's and S's column c at more than
+    keep_frac of the positions.  Reading: every candidate is judged on the
+    initial candidate set and the rejected ones are removed together.
+    Returns (a_idx, b_idx): the kept pairs, in increasing a_idx.
+    """
+    S0 = _cosines(UA, UB)
+    r = S0.shape[0]
+    order = sorted(((S0[i, j], i, j) for i in range(r) for j in range(S0.shape[1])),
+                   key=lambda t: (-t[0], t[1], t[2]))
+    used_a, used_b, pairs = set(), set(), []
+    for c, i, j in order:
+        if c < 1.0 - eps:
+            break
+        if i in used_a or j in used_b:
+            continue
+        used_a.add(i)
+        used_b.add(j)
+        pairs.append((i, j))
+    pairs.sort()
+    if not pairs:
+        return np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64)
+    a = np.array([p[0] for p in pairs])
+    b = np.array([p[1] for p in pairs])
+    M = round1(-np.sort(-_cosines(UA[:, a], UA[:, a]), axis=0))
+    N = round1(-np.sort(-_cosines(UB[:, b], UB[:, b]), axis=0))
+    S = round1(-np.sort(-_cosines(UA[:, a], UB[:, b]), axis=0))
+    keep = [c for c in range(len(a))
+            if np.mean((M[:, c] == N[:, c]) & (M[:, c] == S[:, c])) > keep_frac]
+    return a[keep], b[keep]
+
+
+# --------------------------------------------------------------------------
+# App. A.2, Eq. 5, Algorithm 4: the generalized rotation U* R1 Lambda R2.
+def quartic_lambda(w11, w21n, w12, w22n, lam_prev):
+    """Lambda update of Algorithm 4 for one column: the minimiser over
+    lambda > 0 of g(l) = |w21n - l w11|^2 + |w22n - w12 / l|^2, where w21n =
+    W21(:,i) + N1(:,i) and w22n = W22(:,i) + N2(:,i).  g'(l) = 0 is the
+    quartic a l^4 - b l^3 + c l - d = 0 with a = |w11|^2, b = w21n . w11,
+    c = w22n . w12, d = |w12|^2 (App. A.2).  Reading: of its positive real
+    roots (numpy's companion-matrix roots, imaginary part below 1e-9 of the
+    magnitude), the one with the smallest g; lam_prev when there is none
+    (a zero column)."""
+    a = float(w11 @ w11)
+    b = float(w21n @ w11)
+    c = float(w22n @ w12)
+    d = float(w12 @ w12)
+    if not (a > 0.0 and d > 0.0):
+        return lam_prev
+    roots = np.roots([a, -b, 0.0, c, -d])
+    cand = [z.real for z in roots if abs(z.imag) <= 1e-9 * max(abs(z), 1e-300) and z.real > 0.0]
+    if not cand:
+        return lam_prev
+
+    def g(lv):
+        return float(np.sum((w21n - lv * w11) ** 2) + np.sum((w22n - w12 / lv) ** 2))
+    return min(cand, key=g)
+
+
+def general_w1_update(Ws, m, R1, M, W2, N, lam, rho, gamma):
+    """W1 = [W11; W12] of Algorithm 4 (closed forms of App. A.2, per column j):
+    W11 = (rho (U* R1 - M1) + gamma lambda_j (W21 + N1)) / (rho + gamma lambda_j^2),
+    W12 = (rho (V* R1 - M2) + (gamma / lambda_j) (W22 + N2)) / (rho + gamma / lambda_j^2).
+    Rows 0..m-1 are the U block, the rest the V block."""
+    W1 = np.empty_like(Ws)
+    W1[:m] = (rho * (Ws[:m] @ R1 - M[:m]) + gamma * lam * (W2[:m] + N[:m])) / (rho + gamma * lam ** 2)
+    W1[m:] = (rho * (Ws[m:] @ R1 - M[m:]) + (gamma / lam) * (W2[m:] + N[m:])) / (
+        rho + gamma / lam ** 2)
+    return W1
+
+
+def general_w2_update(W1, m, N, W3, P, R2, lam, gamma, t):
+    """W2 = [W21; W22] of Algorithm 4 (closed forms of App. A.2):
+    W21 = (gamma W11 Lambda - gamma N1 + t (W31 + P1) R2^T) / (gamma + t),
+    W22 = (gamma W12 Lambda^-1 - gamma N2 + t (W32 + P2) R2^T) / (gamma + t)."""
+    W2 = np.empty_like(W1)
+    W2[:m] = (gamma * W1[:m] * lam - gamma * N[:m] + t * (W3[:m] + P[:m]) @ R2.T) / (gamma + t)
+    W2[m:] = (gamma * W1[m:] / lam - gamma * N[m:] + t * (W3[m:] + P[m:]) @ R2.T) / (gamma + t)
+    return W2
+
+
+@dataclass
+class GeneralRotateInfo:
+    steps: int = 0
+    converged: bool = False
+    rho: float = 0.0
+    change: float = 0.0
+
+
+def rotate_general(Us, Vs, rho=None, max_iter=ADMM_MAX_ITER, tol=ADMM_TOL):
+    """Algorithm 4: ADMM for Eq. 5 -- orthogonal R1, R2 and diagonal Lambda > 0
+    with U* R1 Lambda R2 and V* R1 Lambda^-1 R2 as close to the nonnegative
+    orthant as the heuristic gets (App. A.2).
+
+    Splitting (App. A.2): W1 = W_svd R1, W2 = [W11 Lambda; W12 Lambda^-1],
+    W3 = W2 R2, with scaled duals M, N, P.  One step, in the order of
+    Algorithm 4:
+      W3 = prox(W2 R2 - P) with threshold 1/t (the Eq. 7 form);
+      W11, W12 from their closed forms (per column j, with lambda_j);
+      R1 = polar(W_svd^T (W1 + M));  W21, W22 from their closed forms;
+      R2 = polar(W2^T (W3 + P));  each lambda_i from its quartic;
+      M += W1 - W_svd R1;  N += W2 - [W11 Lambda; W12 Lambda^-1];
+      P += W3 - W2 R2.
+    Readings: R1 = R2 = I, Lambda = I, W1 = W2 = W3 = W_svd and zero duals at
+    the start; rho = gamma = t = RHO_SCALE / RMS(W_svd) (the scale-free choice
+    of Algorithm 1); stop when |R1 - R1'| + |R2 - R2'| + |lambda - lambda'|
+    <= tol sqrt(r), or after max_iter steps.  Eq. 5 writes R2 where App. A.1
+    writes R2^T; both are orthogonal, and this follows Eq. 5 and Algorithm 4
+    (W3 = W2 R2).  Returns (U* R1 Lambda R2, V* R1 Lambda^-1 R2, R1, lambda,
+    R2, info).
+    """
+    Us = np.asarray(Us, dtype=np.float64)
+    Vs = np.asarray(Vs, dtype=np.float64)
+    m, r = Us.shape
+    Ws = np.vstack([Us, Vs])
+    if rho is None:
+        rms = math.sqrt(float(np.mean(Ws * Ws)))
+        rho = RHO_SCALE / rms if rms > 0 else 1.0
+    gamma = t = rho
+    R1 = np.eye(r)
+    R2 = np.eye(r)
+    lam = np.ones(r)
+    W1 = Ws.copy()
+    W2 = Ws.copy()
+    W3 = Ws.copy()
+    M = np.zeros_like(Ws)
+    N = np.zeros_like(Ws)
+    P = np.zeros_like(Ws)
+    info = GeneralRotateInfo(rho=rho)
+    for k in range(max_iter):
+        R1o, R2o, lamo = R1, R2, lam.copy()
+        # f1: W3 and W1
+        W3 = prox_h(W2 @ R2 - P, t)
+        W1 = general_w1_update(Ws, m, R1, M, W2, N, lam, rho, gamma)
+        # f2: R1 and W2
+        R1 = procrustes(Ws.T @ (W1 + M))
+        W2 = general_w2_update(W1, m, N, W3, P, R2, lam, gamma, t)
+        # f3: R2 and Lambda
+        R2 = procrustes(W2.T @ (W3 + P))
+        lam = np.array([quartic_lambda(W1[:m, i], W2[:m, i] + N[:m, i], W1[m:, i],
+                                       W2[m:, i] + N[m:, i], lam[i]) for i in range(r)])
+        # duals
+        M = M + W1 - Ws @ R1
+        N[:m] = N[:m] + W2[:m] - W1[:m] * lam
+        N[m:] = N[m:] + W2[m:] - W1[m:] / lam
+        P = P + W3 - W2 @ R2
+        info.change = float(np.linalg.norm(R1 - R1o) + np.linalg.norm(R2 - R2o)
+                            + np.linalg.norm(lam - lamo))
+        info.steps = k + 1
+        if info.change <= tol * math.sqrt(r):
+            info.converged = True
+            break
+    T1 = R1 * lam          # R1 Lambda
+    T2 = R1 / lam          # R1 Lambda^-1
+    return Us @ T1 @ R2, Vs @ T2 @ R2, R1, lam, R2, info

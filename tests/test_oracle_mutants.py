@@ -365,3 +365,97 @@ def test_planted_mistake_is_caught(monkeypatch, name, attr, fn, pins):
             failures.append((pin.__name__, type(e).__name__))
             break
     assert failures, f"planted mistake '{name}' passed every pin in {[p.__name__ for p in pins]}"
+
+
+# ------------------------- equivalence tools (App. F, H) and Algorithm 4
+import test_oracle_equiv as E  # noqa: E402
+import test_oracle_general as GR  # noqa: E402
+
+ORIG2 = {name: getattr(O, name) for name in (
+    "general_w1_update", "general_w2_update", "quartic_lambda", "generalized_transform",
+    "permutation_check", "_cosines", "round1")}
+
+
+def w1_without_coupling(Ws, m, R1, M, W2, N, lam, rho, gamma):
+    """The gamma term (the W2 coupling) dropped from the W1 update."""
+    return ORIG2["general_w1_update"](Ws, m, R1, M, W2, N, lam, rho, 0.0)
+
+
+def w2_scales_swapped(W1, m, N, W3, P, R2, lam, gamma, t):
+    """Lambda and Lambda^-1 exchanged between the two blocks."""
+    return ORIG2["general_w2_update"](W1, m, N, W3, P, R2, 1.0 / lam, gamma, t)
+
+
+def w2_without_transpose(W1, m, N, W3, P, R2, lam, gamma, t):
+    return ORIG2["general_w2_update"](W1, m, N, W3, P, R2.T, lam, gamma, t)
+
+
+def quartic_c_sign(w11, w21n, w12, w22n, lam_prev):
+    """The V-block cross term enters with the wrong sign."""
+    return ORIG2["quartic_lambda"](w11, w21n, -w12, w22n, lam_prev)
+
+
+def transform_r2_untransposed(Ue, Ve, Ualg, Valg):
+    g = ORIG2["generalized_transform"](Ue, Ve, Ualg, Valg)
+    return O.GeneralTransform(g.R1, g.lam, g.R2.T, g.delta_u, g.delta_v)
+
+
+def transform_inverse_map(Ue, Ve, Ualg, Valg):
+    """The map of U_alg onto U_e instead of U_e onto U_alg."""
+    return ORIG2["generalized_transform"](Ualg, Valg, Ue, Ve)
+
+
+def perm_without_pruning(UA, UB, eps=0.05, keep_frac=0.9):
+    return ORIG2["permutation_check"](UA, UB, eps, 0.0)
+
+
+def perm_threshold_halved(UA, UB, eps=0.05, keep_frac=0.9):
+    return ORIG2["permutation_check"](UA, UB, eps / 2, keep_frac)
+
+
+def cosines_unnormalised(A, B):
+    return A.T @ B
+
+
+def round1_truncates(x):
+    return np.floor(10.0 * np.asarray(x, dtype=np.float64)).astype(np.int64)
+
+
+MUTANTS2 = [
+    ("Algorithm 4 W1 without the W2 coupling", "general_w1_update", w1_without_coupling,
+     [GR.test_w1_closed_form_minimises_its_subproblem]),
+    ("Algorithm 4 W2 scales swapped", "general_w2_update", w2_scales_swapped,
+     [GR.test_w2_closed_form_minimises_its_subproblem]),
+    ("Algorithm 4 W2 with R2 instead of R2^T", "general_w2_update", w2_without_transpose,
+     [GR.test_w2_closed_form_minimises_its_subproblem]),
+    ("Algorithm 4 quartic cross-term sign", "quartic_lambda", quartic_c_sign,
+     [lambda: GR.test_lambda_is_the_one_dimensional_minimiser(0),
+      lambda: GR.test_lambda_is_the_one_dimensional_minimiser(1)]),
+    ("App. F R2 untransposed", "generalized_transform", transform_r2_untransposed,
+     [E.test_transform_recovers_an_invertible_map]),
+    ("App. F inverse map", "generalized_transform", transform_inverse_map,
+     [E.test_transform_recovers_an_invertible_map, E.test_transform_of_a_scaled_permutation]),
+    ("App. H without pruning", "permutation_check", perm_without_pruning,
+     [E.test_pruning_drops_changed_cross_similarity]),
+    ("App. H threshold halved", "permutation_check", perm_threshold_halved,
+     [E.test_threshold_is_one_minus_eps]),
+    ("App. H cosines unnormalised", "_cosines", cosines_unnormalised,
+     [E.test_permutation_found_whole, E.test_threshold_is_one_minus_eps]),
+    ("App. H rounding truncates", "round1", round1_truncates,
+     [E.test_round1_is_half_up_to_one_decimal]),
+]
+
+
+@pytest.mark.parametrize("name,attr,fn,pins", MUTANTS2, ids=[m[0] for m in MUTANTS2])
+def test_planted_mistake_in_the_equivalence_and_general_rotation_is_caught(monkeypatch, name,
+                                                                           attr, fn, pins):
+    monkeypatch.setattr(O, attr, fn)
+    failures = []
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, ValueError, FloatingPointError, np.linalg.LinAlgError,
+                IndexError) as e:
+            failures.append(type(e).__name__)
+            break
+    assert failures, f"planted mistake '{name}' passed its pins"
