@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--no-image", action="store_true")
     ap.add_argument("--only-fp8", action="store_true",
                     help="run the FP8-form leg alone (rank 0) and print its JSON")
-    ap.add_argument("--fp8-forms", default="fp8,bf16,f32",
+    ap.add_argument("--fp8-forms", default="fp8,bf16,f32,f64",
                     help="forms of the FP8 leg, comma separated (the gap needs f32)")
-    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-open-requests", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -252,7 +253,7 @@ def sweep_bytes_all_terms(m, n, r, esize):
     return (xv + xtu) / 2.0
 
 
-def fp8_leg(forms=("fp8", "bf16", "f32")):
+def fp8_leg(forms=("fp8", "bf16", "f32", "f64")):
     """Precision form, large: the spectrogram-shaped workload (1025 x 131072,
     r = 64; harmonic templates x sparse activations, Gamma(0.5) modulation)
     solved with X streamed as FP8 (E4M3 codes, per-tile power-of-two scales,
@@ -275,10 +276,15 @@ def fp8_leg(forms=("fp8", "bf16", "f32")):
     hbm = pk.get("hbm_gbs", 6800.0)
     out = {"workload": FP8_WORKLOAD, "m": m, "n": n, "r": r, "iterations": 200}
     for name, xs, esize in (("fp8", torch.float8_e4m3fn, 1), ("bf16", torch.bfloat16, 2),
-                            ("f32", None, 4)):
+                            ("f32", None, 4), ("f64", None, 8)):
         if name not in forms:
             continue
-        s = Solver(Xd, r, x_stream=xs)
+        if name == "f64":
+            # the plain FP64 form (per-iteration parity with the FP64 oracle)
+            # on the same values, as the reference of the error gaps
+            s = Solver(torch.as_tensor(X.astype(np.float64), device="cuda"), r)
+        else:
+            s = Solver(Xd, r, x_stream=xs)
 
         def solve():
             s.svd_init()
@@ -316,6 +322,11 @@ def fp8_leg(forms=("fp8", "bf16", "f32")):
         for name in ("fp8", "bf16"):
             if name in out:
                 out[name]["rel_err_gap_vs_f32"] = abs(out[name]["rel_err"] - ref) / ref
+    if "f64" in out:
+        ref = out["f64"]["rel_err"]
+        for name in ("fp8", "bf16", "f32"):
+            if name in out:
+                out[name]["rel_err_gap_vs_f64"] = abs(out[name]["rel_err"] - ref) / ref
     if "fp8" in out and "bf16" in out:
         out["speedup_fp8_vs_bf16"] = out["bf16"]["ms_per_solve"] / out["fp8"]["ms_per_solve"]
     return out
@@ -354,7 +365,7 @@ def image_leg(iters=500):
         return s.residual(direct=True)[1]
 
     s = Solver(Xd, r, x_stream=torch.bfloat16)
-    for name, fused in (("bf16_fused", 1), ("bf16_two_pass", 0)):
+    for name, fused in (("bf16_two_pass", 0), ("bf16_fused", 1)):
         avail = B.enmf_set_fused(s.ctx, fused)
         if fused and not avail:
             continue
@@ -389,7 +400,7 @@ def image_leg(iters=500):
     return out
 
 
-def serving_leg(n_req):
+def serving_leg(n_req, n_open, n_cmp=16):
     """Serving + batching workload: a Poisson stream of NMF requests with m, n
     log-uniform in [64, 4096] and r uniform in {4, 8, 16, 32, 64}, planted
     inputs (BF16 X, FP32 accumulate), each solved until its objective settles.
@@ -419,15 +430,18 @@ def serving_leg(n_req):
     srv.close()
     sat = stats(res, wall)
     rate = 0.7 * sat["solves_per_s"]
-    open_reqs = load(synth.request_stream(n_req, seed=1, rate_per_s=rate))
+    open_reqs = load(synth.request_stream(n_open, seed=1, rate_per_s=rate))
     srv = Server(chunk=10, tol=1e-6, max_iter=500)
     t0 = time.perf_counter()
     res_o = srv.run(open_reqs)
     wall_o = time.perf_counter() - t0
     srv.close()
     ol = stats(res_o, wall_o)
-    # the plain FP64 GPU form, one request at a time, on the first requests
-    k = min(8, n_req)
+    # the plain FP64 GPU form, one request at a time, on the first requests;
+    # then again from its SVD start multiplied entrywise by 1 + 1e-12 g (g
+    # standard normal): how far the method itself moves the final error under a
+    # start difference far below any reduced-precision rounding
+    k = min(n_cmp, n_req)
     t0 = time.perf_counter()
     f64_rel = []
     for q in sat_reqs[:k]:
@@ -440,12 +454,25 @@ def serving_leg(n_req):
         s.close()
     torch.cuda.synchronize()
     f64_sps = k / (time.perf_counter() - t0)
+    f64_pert = []
+    gen = torch.Generator(device="cuda").manual_seed(12)
+    for q in sat_reqs[:k]:
+        X64 = torch.as_tensor(q.X.astype(np.float64), device="cuda")
+        s = Solver(X64, q.r)
+        s.svd_init()
+        for F in (s.U, s.V):
+            F.mul_(1 + 1e-12 * torch.randn(F.shape, generator=gen, device="cuda", dtype=F.dtype))
+        s.rotate()
+        s.iterate(500, trace=False, reset=1)
+        f64_pert.append(s.residual()[1])
+        s.close()
     by = {r.rid: r for r in res}
     # target (per request): served rel. error <= (1 + 1e-3) x the FP64 form's
-    excess = [(by[q.rid].rel_err / e - 1.0, by[q.rid].iters, by[q.rid].rel_err, e)
-              for q, e in zip(sat_reqs[:k], f64_rel) if q.rid in by]
+    excess = [(by[q.rid].rel_err / e - 1.0, by[q.rid].iters, by[q.rid].rel_err, e, ep / e - 1.0)
+              for q, e, ep in zip(sat_reqs[:k], f64_rel, f64_pert) if q.rid in by]
     return {"workload": "Poisson NMF requests, m,n log-uniform [64,4096], r in {4,8,16,32,64}, "
-                        "planted inputs, BF16 X / FP32 accumulate, %d requests per run" % n_req,
+                        "planted inputs, BF16 X / FP32 accumulate; saturation %d requests, "
+                        "open loop %d" % (n_req, n_open),
             "saturation": {"solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"],
                            "p99_ms": sat["p99_ms"], "wall_s": wall, "host_time_s": split},
             "open_loop": {"rate_per_s": rate, "solves_per_s": ol["solves_per_s"],
@@ -455,7 +482,13 @@ def serving_leg(n_req):
             "rel_err_vs_f64": {"max_excess": max(x[0] for x in excess) if excess else None,
                                "meet_1e-3": sum(x[0] <= 1e-3 for x in excess),
                                "compared": len(excess),
-                               "per_request": [[round(x[0], 6), x[1]] for x in excess]},
+                               "f64_self_spread_1e-12": [round(x[4], 6) for x in excess],
+                               "meet_1e-3_or_within_f64_spread":
+                                   sum(x[0] <= max(1e-3, abs(x[4])) for x in excess),
+                               "per_request": [[round(x[0], 6), x[1]] for x in excess],
+                               "note": "excess = served rel. error / FP64 form's - 1; "
+                                       "f64_self_spread = the FP64 form's own change under a "
+                                       "1e-12 start perturbation"},
             "iters_served": {"median": float(np.median([r.iters for r in res])),
                              "max": int(max(r.iters for r in res))}}
 
@@ -538,28 +571,34 @@ def run_ours(args):
     total_ms, value = replica_throughput(total_ms, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
     kk = s.kkt()                       # the final KKT check, once, after the timed region
-    fused_on = bool(FORMS[form][2] == "bf16" and B.enmf_set_fused(s.ctx, 1))
     U_host = s.U.double().cpu().numpy()
     V_host = s.V.double().cpu().numpy()
-    # the same solve with the two-pass sweeps (X read twice per alternation),
-    # for comparison with the fused single pass
-    two_pass = None
-    if fused_on:
-        B.enmf_set_fused(s.ctx, 0)
+    # the same solve with the fused single pass (X read once per HALS
+    # alternation; opt-in), for comparison with the two-pass sweeps timed above
+    fused = None
+    if FORMS[form][2] == "bf16" and B.enmf_set_fused(s.ctx, 1):
+        shape = B.enmf_fused_shape(s.ctx)
         solve_once(s, ITERS)
         torch.cuda.synchronize()
         B.enmf_profile(s.ctx, 4)
         B.enmf_profile_read(s.ctx, reset=1)
         t0 = time.perf_counter()
-        rel_tp = solve_once(s, ITERS)
+        rel_fz = solve_once(s, ITERS)
         torch.cuda.synchronize()
-        tp_ms = 1e3 * (time.perf_counter() - t0)
-        tms, tn = B.enmf_profile_read(s.ctx, reset=1)
+        fz_ms = 1e3 * (time.perf_counter() - t0)
+        fms, fn = B.enmf_profile_read(s.ctx, reset=1)
         B.enmf_profile(s.ctx, 0)
-        two_pass = {"ms_per_solve": tp_ms, "rel_err": rel_tp,
-                    "sweep_us_avg": 1e3 * tms / max(tn, 1), "sweeps_timed": tn,
-                    "note": "X V and X^T U as separate tensor-core sweeps, two reads of X per "
-                            "alternation; sweep_us_avg is one of them"}
+        B.enmf_set_fused(s.ctx, 0)
+        fus = 1e3 * fms / max(fn, 1)
+        gbs = M * N * 2 / (fus * 1e-6) / 1e9
+        fused = {"ms_per_solve": fz_ms, "rel_err": rel_fz, "kernel_us_avg": fus,
+                 "kernels_timed": fn, "achieved_gbs": gbs,
+                 "frac_of_measured_hbm": gbs / peaks().get("hbm_gbs", 6800.0),
+                 "launch": {"ctas_per_cluster": shape[1], "clusters": shape[2],
+                            "columns_per_cta": shape[3], "stages": shape[4],
+                            "smem_kb": shape[5]},
+                 "note": "one kernel per HALS alternation: X V, U-half, X^T U_new; the V-half "
+                         "is a separate launch; kernel_us_avg is the fused kernel alone"}
     s.close()
 
     # the other forms, timed once after one warm solve each: the plain FP64
@@ -631,15 +670,9 @@ def run_ours(args):
         bytes_per_sweep = M * N * esize
         achieved = bytes_per_sweep / avg_sweep_s / 1e9 if sweeps else None
         peak = pk.get("hbm_gbs", 6800.0)
-        if fused_on:
-            kname = ("fused single-pass HALS alternation (TMA + tcgen05 + cluster DSMEM, BF16 X): "
-                     "X V, U-half, X^T U_new in one read of X")
-            traffic = sweep_traffic("fused.cu", "fused_hals_kernel_8192x6144_r32.md")
-            span = "one fused kernel per HALS alternation (X_hi read once)"
-        else:
-            kname = "tensor-core X sweep (TMA + tcgen05, BF16 X)"
-            traffic = sweep_traffic()
-            span = "one tensor-core sweep kernel (X_hi pass incl. stream-K fix-up)"
+        kname = "tensor-core X sweep (TMA + tcgen05, BF16 X)"
+        traffic = sweep_traffic()
+        span = "one tensor-core sweep kernel (X_hi pass incl. stream-K fix-up)"
         roof = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -665,7 +698,7 @@ def run_ours(args):
         cb = cpu_oracle_sample(X64, r, np.maximum(U_host, 0), np.maximum(V_host, 0))
     serving = None
     if world == 1 and not args.no_serve and args.serve_requests > 0:
-        serving = serving_leg(args.serve_requests)
+        serving = serving_leg(args.serve_requests, args.serve_open_requests)
     fp8 = None
     if world == 1 and not args.no_fp8:
         fp8 = fp8_leg(tuple(args.fp8_forms.split(",")))
@@ -695,7 +728,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "p50_ms": statistics.median(step_ms), "p99_ms": p99,
             "time_to_target": ttt, "final": {"rel_err": rel, "kkt_pg_rel": kk.pg_rel},
-            "other_forms": others, "two_pass": two_pass, "roofline": roof, "cpu_baseline": cb,
+            "other_forms": others, "fused_single_pass": fused, "roofline": roof, "cpu_baseline": cb,
             "e2e": e2e, "image_stack": image,
             "clocks": clk, "gpu_launches": launches, "serving": serving, "fp8_form": fp8}
     print(json.dumps(line))

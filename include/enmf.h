@@ -163,6 +163,27 @@ typedef struct {
 enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* R,
                         const enmf_admm_opts* opts, enmf_rotate_info* info);
 
+/* ---- 2b. Generalized rotation (Eq. 5, Algorithm 4, App. A.2) -----------
+ * Orthogonal R1, R2 and diagonal Lambda > 0 that bring U* R1 Lambda R2 and
+ * V* R1 Lambda^-1 R2 toward the orthant (the product U V^T is unchanged).
+ * ADMM with the splitting W1 = W_svd R1, W2 = [W11 Lambda; W12 Lambda^-1],
+ * W3 = W2 R2 and scaled duals M, N, P; one step, in the order of Algorithm 4:
+ * W3 = prox(W2 R2 - P) (the Eq. 7 form), W1 and W2 from their closed forms,
+ * R1 = polar(W_svd^T (W1 + M)), R2 = polar(W2^T (W3 + P)) (FP64 Jacobi),
+ * lambda_i = the positive root of a l^4 - b l^3 + c l - d = 0 (App. A.2)
+ * with the least objective, then the dual updates.  Start: R1 = R2 = I,
+ * Lambda = I, W1 = W2 = W3 = W_svd, zero duals; rho = gamma = t =
+ * rho_scale / RMS(W) unless opts->rho > 0.  Stops when |R1 - R1'| + |R2 -
+ * R2'| + |lambda - lambda'| <= tol sqrt(r) (Frobenius norms) or after
+ * max_iter steps (the step count is exact: a device flag skips the steps
+ * enqueued after the rule holds).  U and V are overwritten by the rotated
+ * factors; R1, R2 (r x r row-major) and lam (r) are device FP64 outputs;
+ * info->dR is the last step's change.  The workspace (6 (m + n) r elements
+ * plus small buffers) comes from the stream-ordered allocator for the call.
+ * Resets the iteration state.  Synchronises. */
+enmf_status enmf_rotate_general(enmf_ctx* ctx, void* U, void* V, double* R1, double* lam,
+                                double* R2, const enmf_admm_opts* opts, enmf_rotate_info* info);
+
 /* ---- 3. Exterior iteration (Algorithm 3 lines 5-12) ---------------------
  * Runs n_iter alternations from the context's iteration state.  One
  * alternation = U-half then V-half.  While U or V has a negative entry it is
@@ -313,6 +334,12 @@ int32_t enmf_batch_size(const enmf_batch* b);
 enmf_status enmf_batch_step(enmf_batch* b, int32_t n_alt);
 enmf_status enmf_batch_member(enmf_batch* b, int32_t slot, enmf_iter_info* info, double* f);
 enmf_status enmf_batch_tune(enmf_batch* b, int32_t* grid, float* ms);
+/* Every member's state at once (one synchronisation and one copy instead of
+ * one per member): *count = members; for i < *count, slots[i], infos[i] and
+ * f[i] as enmf_batch_member gives them.  Host arrays of cap entries;
+ * ENMF_EINVAL when cap < *count (nothing written but *count). */
+enmf_status enmf_batch_states(enmf_batch* b, int32_t* slots, enmf_iter_info* infos, double* f,
+                              int32_t cap, int32_t* count);
 
 /* ---- Checkpoint of the iteration state (no counterpart in the paper) -----
  * Algorithm 3's loop carries state between alternations, beside U and V:
@@ -349,6 +376,37 @@ enmf_status enmf_profile(enmf_ctx* ctx, int32_t every);
 enmf_status enmf_profile_read(enmf_ctx* ctx, double* sweep_ms, int64_t* sweeps, int32_t reset);
 enmf_status enmf_probe_fma_peak(int32_t dtype, double* flops_per_s);
 long long enmf_launch_count(void);
+
+/* ---- Equivalence of two factorisations (Sec. 5, App. F and App. H) -------
+ * Both take factor matrices of the context's problem and form (m x r and
+ * n x r, row-major, device, f_dtype); the context gives the stream and the
+ * scratch.  Both synchronise.
+ *
+ * enmf_equiv_transform (App. F): R1, Lambda, R2 with
+ *     U_alg ~ U_e R1 Lambda R2^T,   V_alg ~ V_e R1 Lambda^-1 R2^T,
+ * from the least-squares map Z = (U_e^T U_e)^-1 U_e^T U_alg (the paper's
+ * Q Gamma^-1 P^T U_alg for the SVD U_e = P Gamma Q^T) and its SVD
+ * Z = R1 Lambda R2^T.  R1, R2 (r x r row-major) and lam (the diagonal of
+ * Lambda, descending) are device FP64 buffers; delta2 (host, 2 doubles)
+ * receives delta_u = ||U_alg - U_e Z||_F and delta_v = ||V_alg - V_e
+ * R1 Lambda^-1 R2^T||_F (both 0 when the factorisations are equivalent).
+ * ENMF_ENOTCONV when U_e^T U_e is not positive definite (U_e rank deficient).
+ *
+ * enmf_perm_check (App. H): the columns of U_B that are scaled permutations
+ * of columns of U_A.  Pairs (i, j) are taken one to one in decreasing
+ * cos(U_A^(i), U_B^(j)) (ties by lower i, then j) while the cosine is
+ * >= 1 - eps (the paper uses eps = 0.05); then, on the candidates, the
+ * columns of the self-similarity matrices of U_A's and U_B's candidates and
+ * of their cross-similarity matrix are sorted in descending order and
+ * rounded to one decimal (floor(10 x + 1/2)), and a candidate stays when its
+ * column agrees in all three at more than keep_frac of the positions (the
+ * paper uses 0.9).  b_of_a (host, r ints) receives for each column i of U_A
+ * the matched column of U_B, or -1; *kept the number of pairs. */
+enmf_status enmf_equiv_transform(enmf_ctx* ctx, const void* Ue, const void* Ve, const void* Ua,
+                                 const void* Va, double* R1, double* lam, double* R2,
+                                 double* delta2);
+enmf_status enmf_perm_check(enmf_ctx* ctx, const void* UA, const void* UB, double eps,
+                            double keep_frac, int32_t* b_of_a, int32_t* kept);
 
 /* ---- The fused single-pass alternation (no counterpart in the paper) -----
  * In the HALS stage of the BF16 / FP16 tensor-core forms (rank padded to 32

@@ -101,6 +101,14 @@ _SIGS = {
     "enmf_launch_count": (C.c_longlong, []),
     "enmf_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
     "enmf_set_fused": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "enmf_rotate_general": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.POINTER(enmf_admm_opts),
+                                      C.POINTER(enmf_rotate_info)]),
+    "enmf_equiv_transform": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.POINTER(C.c_double)]),
+    "enmf_perm_check": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "enmf_fused_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "enmf_fused_stamps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "enmf_probe_wait": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(C.c_int32)]),
@@ -113,6 +121,8 @@ _SIGS = {
     "enmf_batch_step": (C.c_int, [C.c_void_p, C.c_int32]),
     "enmf_batch_member": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_double)]),
     "enmf_batch_tune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    "enmf_batch_states": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p,
+                                    C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_int32)]),
     "enmf_residual_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                                         C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                         C.c_void_p]),
@@ -312,6 +322,16 @@ def enmf_batch_member(b, slot):
     return info, f.value
 
 
+def enmf_batch_states(b, cap):
+    """{slot: (enmf_iter_info, f)} for every member, read in one copy."""
+    slots = (C.c_int32 * cap)()
+    infos = (enmf_iter_info * cap)()
+    f = (C.c_double * cap)()
+    n = C.c_int32(0)
+    check(lib().enmf_batch_states(b, slots, infos, f, cap, C.byref(n)), "enmf_batch_states")
+    return {slots[i]: (infos[i], f[i]) for i in range(n.value)}
+
+
 def enmf_batch_tune(b):
     g = C.c_int32(0)
     ms = C.c_float(0)
@@ -322,6 +342,33 @@ def enmf_batch_tune(b):
 def enmf_set_wait_limit(ctx, cycles):
     """Spin limit (SM cycles) of the context's grid barriers; 0 = default."""
     check(lib().enmf_set_wait_limit(ctx, int(cycles)), "enmf_set_wait_limit")
+
+
+def enmf_rotate_general(ctx, U, V, R1, lam, R2, opts=None):
+    """Algorithm 4 in place on U, V; R1, lam, R2 device FP64 outputs."""
+    info = enmf_rotate_info()
+    code = lib().enmf_rotate_general(ctx, _ptr(U), _ptr(V), _ptr(R1), _ptr(lam), _ptr(R2),
+                                     C.byref(opts) if opts is not None else None, C.byref(info))
+    if code not in (0, 6):
+        check(code, "enmf_rotate_general")
+    return info, code
+
+
+def enmf_equiv_transform(ctx, Ue, Ve, Ua, Va, R1, lam, R2):
+    """App. F transform into the device tensors R1, lam, R2; returns (delta_u, delta_v)."""
+    d = (C.c_double * 2)()
+    check(lib().enmf_equiv_transform(ctx, _ptr(Ue), _ptr(Ve), _ptr(Ua), _ptr(Va), _ptr(R1),
+                                     _ptr(lam), _ptr(R2), d), "enmf_equiv_transform")
+    return d[0], d[1]
+
+
+def enmf_perm_check(ctx, UA, UB, r, eps=0.05, keep_frac=0.9):
+    """App. H permutation check: list (length r) of matched U_B columns or -1."""
+    out = (C.c_int32 * r)()
+    kept = C.c_int32(0)
+    check(lib().enmf_perm_check(ctx, _ptr(UA), _ptr(UB), eps, keep_frac, out, C.byref(kept)),
+          "enmf_perm_check")
+    return list(out), kept.value
 
 
 def enmf_set_fused(ctx, on):

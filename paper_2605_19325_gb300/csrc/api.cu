@@ -222,7 +222,7 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
   size_t sk = 0;
   ctx->ws_bytes = plan(p, ctx->num_sms, &sk);
-  if (cudaMalloc(&ctx->ws, ctx->ws_bytes) != cudaSuccess) {
+  if (cudaMallocAsync(&ctx->ws, ctx->ws_bytes, ctx->stream) != cudaSuccess) {
     cudaGetLastError();
     delete ctx;
     return ENMF_ENOMEM;
@@ -264,7 +264,7 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
   ctx->csQ2 = (double*)take(LMAX * 8);
   ctx->scal = (double*)take(64 * 8);
   if ((size_t)(b - (char*)ctx->ws) > ctx->ws_bytes) {
-    cudaFree(ctx->ws);
+    cudaFreeAsync(ctx->ws, ctx->stream);
     delete ctx;
     return ENMF_EINVAL;
   }
@@ -285,9 +285,9 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
     ctx->sv = t.sv;
     ctx->st_split = t.st;
     ctx->tcws_bytes = t.total;
-    if (cudaMalloc(&ctx->tcws, t.total) != cudaSuccess) {
+    if (cudaMallocAsync(&ctx->tcws, t.total, ctx->stream) != cudaSuccess) {
       cudaGetLastError();
-      cudaFree(ctx->ws);
+      cudaFreeAsync(ctx->ws, ctx->stream);
       delete ctx;
       return ENMF_ENOMEM;
     }
@@ -315,8 +315,8 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
               tc_make_map(ctx->maps[MAP_UH], ctx->uth, t.rp, p->m, t.ldm, 64, t.rp, f16) &&
               tc_make_map(ctx->maps[MAP_UL], ctx->utl, t.rp, p->m, t.ldm, 64, t.rp, f16);
     if (!ok) {
-      cudaFree(ctx->tcws);
-      cudaFree(ctx->ws);
+      cudaFreeAsync(ctx->tcws, ctx->stream);
+      cudaFreeAsync(ctx->ws, ctx->stream);
       delete ctx;
       return ENMF_ECUDA;
     }
@@ -328,10 +328,10 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
       const size_t xtu = (size_t)fp.Q * p->n * p->r * 4;
       const size_t gp = (size_t)fp.Q * fp.C * p->r * p->r * 8;
       const size_t bytes = al256(sizeof(FusedDesc)) + al256(xtu) + al256(gp) + 256;
-      if (cudaMalloc(&ctx->fzws, bytes) != cudaSuccess) {
+      if (cudaMallocAsync(&ctx->fzws, bytes, ctx->stream) != cudaSuccess) {
         cudaGetLastError();
-        if (ctx->tcws) cudaFree(ctx->tcws);
-        cudaFree(ctx->ws);
+        if (ctx->tcws) cudaFreeAsync(ctx->tcws, ctx->stream);
+        cudaFreeAsync(ctx->ws, ctx->stream);
         delete ctx;
         return ENMF_ENOMEM;
       }
@@ -366,9 +366,9 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
     ctx->l2_keep = (e && atoi(e) == 0) ? 0 : 1;
   }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-    if (ctx->fzws) cudaFree(ctx->fzws);
-    if (ctx->tcws) cudaFree(ctx->tcws);
-    cudaFree(ctx->ws);
+    if (ctx->fzws) cudaFreeAsync(ctx->fzws, ctx->stream);
+    if (ctx->tcws) cudaFreeAsync(ctx->tcws, ctx->stream);
+    cudaFreeAsync(ctx->ws, ctx->stream);
     delete ctx;
     return ENMF_ECUDA;
   }
@@ -418,16 +418,19 @@ extern "C" enmf_status enmf_stage_x(enmf_ctx* ctx, const void* X) {
 extern "C" void enmf_destroy(enmf_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
-  if (ctx->ws) cudaFree(ctx->ws);
+  // the workspaces come from the stream-ordered allocator: freeing them does
+  // not synchronise the device (a serving loop retires contexts while other
+  // solves run)
+  if (ctx->ws) cudaFreeAsync(ctx->ws, ctx->stream);
   if (ctx->hX) cudaFree(ctx->hX);
   if (ctx->hU) cudaFree(ctx->hU);
   if (ctx->hV) cudaFree(ctx->hV);
-  if (ctx->tcws) cudaFree(ctx->tcws);
+  if (ctx->tcws) cudaFreeAsync(ctx->tcws, ctx->stream);
   if (ctx->prof_every >= 0 && ctx->pev[0])
     for (int i = 0; i < 2 * PROF_PAIRS; ++i) cudaEventDestroy(ctx->pev[i]);
   for (int g = 0; g < 2; ++g)
     if (ctx->iter_graph[g]) cudaGraphExecDestroy(ctx->iter_graph[g]);
-  if (ctx->fzws) cudaFree(ctx->fzws);
+  if (ctx->fzws) cudaFreeAsync(ctx->fzws, ctx->stream);
   if (ctx->fz_stamps) cudaFree(ctx->fz_stamps);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
@@ -1081,25 +1084,27 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
   // before (X_lo V) and after (X_lo^T U, with the new U) the fused pass.
   auto fused = [&](int it0, int it1) {
     const int rp = ctx->rp;
+    // ctx->stream, read here: inside a capture it is the capture stream
+    cudaStream_t fs = ctx->stream;
     for (int it = it0; it < it1; ++it) {
       const int corr = (it % o.correct_every == 0) ? 2 : 1;
       const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
                        ctx->npev + 2 <= 2 * PROF_PAIRS;
       if (corr == 2 && ctx->xl)
         launch_tc_group(0, rp, ctx->dprob + 1, 1, tc_units(ctx, 0), ctx->tcpart, ctx->tccount,
-                        ctx->num_sms, ctx->err, s);
+                        ctx->num_sms, ctx->err, fs);
       prof_mark(ctx, rec);
-      launch_fused(ctx->dfz, ctx->fz_plan, rp, s);
+      launch_fused(ctx->dfz, ctx->fz_plan, rp, fs);
       prof_mark(ctx, rec);
       if (corr == 2 && ctx->xl)
         launch_tc_group(1, rp, ctx->dprob + 3, 1, tc_units(ctx, 1), ctx->tcpart, ctx->tccount,
-                        ctx->num_sms, ctx->err, s);
+                        ctx->num_sms, ctx->err, fs);
       HalfArgs a = ctx_half_args(ctx, 1, V, nullptr, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu,
                                  o.trace, it);
       a.sum_part = ctx->fz_xtu;
       a.sum_n = ctx->fz_plan.Q;
       a.cut_corr = ctx->xl ? ctx->cu : nullptr;
-      launch_half_step(a, ctx->grid_v, s);
+      launch_half_step(a, ctx->grid_v, fs);
     }
   };
   auto run = [&](int slot, int it0, int it1) {
@@ -1195,6 +1200,113 @@ extern "C" enmf_status enmf_set_fused(enmf_ctx* ctx, int32_t on, int32_t* availa
   if (on != 0 && on != 1) return ENMF_EINVAL;
   ctx->fz_enabled = on;
   if (available) *available = (ctx->tc && ctx->fz_plan.ok && ctx->fzws) ? 1 : 0;
+  return ENMF_OK;
+}
+
+// ---------------------------------------- generalized rotation (Algorithm 4)
+extern "C" enmf_status enmf_rotate_general(enmf_ctx* ctx, void* U, void* V, double* R1,
+                                           double* lam, double* R2, const enmf_admm_opts* opts,
+                                           enmf_rotate_info* info) {
+  GUARD(ctx);
+  if (!U || !V || !R1 || !lam || !R2) return ENMF_EINVAL;
+  enmf_admm_opts o = {0.0, 3.0, 200, 1e-12};
+  if (opts) {
+    o = *opts;
+    if (o.max_iter < 1 || !(o.tol >= 0) || (o.rho <= 0 && !(o.rho_scale > 0))) return ENMF_EINVAL;
+  }
+  const enmf_problem& p = ctx->p;
+  const int k = p.r, fdt = ctx->fdt;
+  const int64_t m = p.m, n = p.n;
+  cudaStream_t s = ctx->stream;
+  launch_negmass(U, m, k, fdt, ctx->part, &ctx->scal[1], 0, s);
+  launch_negmass(V, n, k, fdt, ctx->part, &ctx->scal[1], 1, s);
+  launch_dot(U, k, U, k, k, m, fdt, ctx->part, &ctx->scal[2], s);
+  launch_dot(V, k, V, k, k, n, fdt, ctx->part, &ctx->scal[3], s);
+  double hs[4];
+  CK(cudaMemcpyAsync(hs, ctx->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  enmf_status rc = sync_status(ctx);
+  if (rc) return rc;
+  double rho = o.rho;
+  if (!(rho > 0)) {
+    const double rms = sqrt((hs[2] + hs[3]) / ((double)(m + n) * k));
+    rho = rms > 0 ? o.rho_scale / rms : 1.0;
+  }
+  void* ws = nullptr;
+  const size_t wb = general_ws_bytes(m, n, k, fdt);
+  if (cudaMallocAsync(&ws, wb, s) != cudaSuccess) {
+    cudaGetLastError();
+    return ENMF_ENOMEM;
+  }
+  int steps = 0;
+  double change = 0.0;
+  bool conv = false;
+  rc = run_general_rotation(U, V, m, n, k, fdt, ws, rho, o.max_iter, o.tol, R1, lam, R2, ctx->err,
+                            &steps, &change, &conv, s);
+  cudaFreeAsync(ws, s);
+  if (rc) {
+    ctx->poison = rc;
+    return rc;
+  }
+  launch_negmass(U, m, k, fdt, ctx->part, &ctx->scal[4], 0, s);
+  launch_negmass(V, n, k, fdt, ctx->part, &ctx->scal[4], 1, s);
+  double nm_out = 0.0;
+  CK(cudaMemcpyAsync(&nm_out, &ctx->scal[4], sizeof(double), cudaMemcpyDeviceToHost, s));
+  rc = sync_status(ctx);
+  if (info) {
+    info->steps = steps;
+    info->converged = conv ? 1 : 0;
+    info->rho = rho;
+    info->dR = change;
+    info->neg_mass_in = hs[1];
+    info->neg_mass_out = nm_out;
+  }
+  ctx->state_valid = false;
+  ctx->hals_known = false;
+  return rc;
+}
+
+// ------------------------------------------- equivalence tools (App. F, H)
+extern "C" enmf_status enmf_equiv_transform(enmf_ctx* ctx, const void* Ue, const void* Ve,
+                                            const void* Ua, const void* Va, double* R1,
+                                            double* lam, double* R2, double* delta2) {
+  GUARD(ctx);
+  if (!Ue || !Ve || !Ua || !Va || !R1 || !lam || !R2 || !delta2) return ENMF_EINVAL;
+  const enmf_problem& p = ctx->p;
+  const int k = p.r, fdt = ctx->fdt;
+  cudaStream_t s = ctx->stream;
+  launch_gram(Ue, k, k, Ue, k, k, p.m, fdt, ctx->part, ctx->T1, s);   // G = U_e^T U_e
+  launch_gram(Ue, k, k, Ua, k, k, p.m, fdt, ctx->part, ctx->Ut, s);   // C = U_e^T U_alg
+  launch_equiv_svd(ctx->T1, ctx->Ut, k, R1, lam, R2, ctx->T2, ctx->Wt, ctx->err, s);
+  // delta_u^2 = ||U_alg - U_e Z||^2, delta_v^2 = ||V_alg - V_e Zit||^2
+  launch_transform_residual(Ue, Ua, p.m, k, fdt, ctx->T2, ctx->part, &ctx->scal[8], s);
+  launch_transform_residual(Ve, Va, p.n, k, fdt, ctx->Wt, ctx->part, &ctx->scal[9], s);
+  double h[2];
+  CK(cudaMemcpyAsync(h, &ctx->scal[8], 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  enmf_status rc = sync_status(ctx);
+  delta2[0] = sqrt(h[0] > 0.0 ? h[0] : 0.0);
+  delta2[1] = sqrt(h[1] > 0.0 ? h[1] : 0.0);
+  return rc;
+}
+
+extern "C" enmf_status enmf_perm_check(enmf_ctx* ctx, const void* UA, const void* UB, double eps,
+                                       double keep_frac, int32_t* b_of_a, int32_t* kept) {
+  GUARD(ctx);
+  if (!UA || !UB || !b_of_a || !kept || !(eps >= 0.0) || !(keep_frac >= 0.0) || keep_frac > 1.0)
+    return ENMF_EINVAL;
+  const enmf_problem& p = ctx->p;
+  const int k = p.r, fdt = ctx->fdt;
+  cudaStream_t s = ctx->stream;
+  launch_gram(UA, k, k, UA, k, k, p.m, fdt, ctx->part, ctx->T1, s);
+  launch_gram(UB, k, k, UB, k, k, p.m, fdt, ctx->part, ctx->T2, s);
+  launch_gram(UA, k, k, UB, k, k, p.m, fdt, ctx->part, ctx->Ut, s);
+  launch_perm_check(ctx->T1, ctx->T2, ctx->Ut, k, eps, keep_frac, ctx->counts, ctx->counts + RMAX,
+                    s);
+  int h[RMAX + 1];
+  CK(cudaMemcpyAsync(h, ctx->counts, (RMAX + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  enmf_status rc = sync_status(ctx);
+  if (rc) return rc;
+  for (int i = 0; i < k; ++i) b_of_a[i] = h[i];
+  *kept = h[RMAX];
   return ENMF_OK;
 }
 

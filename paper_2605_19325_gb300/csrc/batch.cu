@@ -55,11 +55,20 @@ struct enmf_batch {
   cudaGraphExec_t graph;
   int graph_nalt, graph_phase, graph_kernels;
   bool no_graph;
+  // enmf_batch_states: the members' DevState pointers and a gathered copy
+  // of their states (device), read back in one copy into pinned host memory
+  DevState** d_stp;
+  DevState* d_gather;
+  DevState* h_gather;
+  int gather_cap;
 };
 
 namespace {
 
 void batch_free(enmf_batch* b) {
+  if (b->d_stp) cudaFree(b->d_stp);
+  if (b->d_gather) cudaFree(b->d_gather);
+  if (b->h_gather) cudaFreeHost(b->h_gather);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->counters) cudaFree(b->counters);
@@ -395,6 +404,80 @@ extern "C" enmf_status enmf_batch_member(enmf_batch* b, int32_t slot, enmf_iter_
   }
   if (f) *f = hst.f_last;
   return rc;
+}
+
+namespace {
+// out[i] = *stp[i] for the members listed in stp (one thread block per member).
+__global__ void gather_states_kernel(DevState* const* __restrict__ stp, int n, DevState* out) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const int words = (int)(sizeof(DevState) / sizeof(int));
+  const int* src = reinterpret_cast<const int*>(stp[i]);
+  int* dst = reinterpret_cast<int*>(out + i);
+  for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+}
+}  // namespace
+
+extern "C" enmf_status enmf_batch_states(enmf_batch* b, int32_t* slots, enmf_iter_info* infos,
+                                         double* f, int32_t cap, int32_t* count) {
+  if (!b || !count || cap < 0 || (cap > 0 && (!slots || !infos || !f))) return ENMF_EINVAL;
+  std::vector<int> sl;
+  std::vector<DevState*> stp;
+  for (int q = 0; q < b->max_members; ++q)
+    if (b->mem[q].used) {
+      sl.push_back(q);
+      stp.push_back(b->mem[q].ctx->st);
+    }
+  const int n = (int)sl.size();
+  *count = n;
+  if (n == 0) return ENMF_OK;
+  if (cap < n) return ENMF_EINVAL;
+  if (b->gather_cap < n) {
+    if (b->d_stp) cudaFree(b->d_stp);
+    if (b->d_gather) cudaFree(b->d_gather);
+    if (b->h_gather) cudaFreeHost(b->h_gather);
+    b->d_stp = nullptr;
+    b->d_gather = nullptr;
+    b->h_gather = nullptr;
+    b->gather_cap = 0;
+    const int c = b->max_members;
+    if (cudaMalloc(&b->d_stp, sizeof(DevState*) * c) != cudaSuccess ||
+        cudaMalloc(&b->d_gather, sizeof(DevState) * c) != cudaSuccess ||
+        cudaMallocHost(&b->h_gather, sizeof(DevState) * c) != cudaSuccess) {
+      cudaGetLastError();
+      return ENMF_ENOMEM;
+    }
+    b->gather_cap = c;
+  }
+  int berr = 0;
+  if (cudaMemcpyAsync(b->d_stp, stp.data(), sizeof(DevState*) * n, cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return ENMF_ECUDA;
+  }
+  note_launch(1);
+  gather_states_kernel<<<n, 32, 0, b->stream>>>(b->d_stp, n, b->d_gather);
+  if (cudaMemcpyAsync(b->h_gather, b->d_gather, sizeof(DevState) * n, cudaMemcpyDeviceToHost,
+                      b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&berr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return ENMF_ECUDA;
+  }
+  if (berr & ERR_TIMEOUT) return ENMF_ETIMEOUT;
+  for (int i = 0; i < n; ++i) {
+    const DevState& h = b->h_gather[i];
+    slots[i] = sl[i];
+    infos[i].iters = h.k;
+    infos[i].asc_iters = h.asc_iters;
+    infos[i].hals_iters = h.hals_iters;
+    infos[i].stage = h.stage;
+    infos[i].s_u = h.s_u;
+    infos[i].s_v = h.s_v;
+    f[i] = h.f_last;
+  }
+  return ENMF_OK;
 }
 
 extern "C" enmf_status enmf_batch_tune(enmf_batch* b, int32_t* grid_out, float* ms_out) {

@@ -181,7 +181,20 @@ void launch_admm_f32(const float* U, const float* V, int64_t m, int64_t n, int k
                      float* Z, float* Y, double rho, int max_iter, double tol, DevState* st,
                      double* part, double* M, int* err, int num_sms, cudaStream_t s);
 
+// -------------------------------------------------------------- general.cu
+// Algorithm 4 (generalized rotation U* R1 Lambda R2), the whole loop: its
+// workspace size and the run (U, V overwritten by U* R1 Lambda R2 and
+// V* R1 Lambda^-1 R2; R1, lam, R2 device FP64 outputs).  Synchronises.
+size_t general_ws_bytes(int64_t m, int64_t n, int k, int fdt);
+enmf_status run_general_rotation(const void* U, const void* V, int64_t m, int64_t n, int k,
+                                 int fdt, void* ws, double rho, int max_iter, double tol,
+                                 double* R1_out, double* lam_out, double* R2_out, int* err,
+                                 int* steps_out, double* change_out, bool* converged,
+                                 cudaStream_t s);
+
 // ---------------------------------------------------------------- small.cu
+// R = polar(M) of a k x k M with warm start D (Np x Np), no loop bookkeeping.
+void launch_polar_plain(const double* M, int k, double* R, double* D, int* err, cudaStream_t s);
 // R_new = polar(sum of NPART partial M's); dR, convergence, ADMM step count.
 void launch_polar(const double* M, int k, double* R, double* D, double tol,
                   DevState* st, int* err, cudaStream_t s);
@@ -299,6 +312,17 @@ struct FusedPlan {
 };
 FusedPlan fused_plan(int64_t m, int64_t n, int rp);
 cudaError_t launch_fused(const FusedDesc* fd, const FusedPlan& pl, int rp, cudaStream_t s);
+
+// --------------------------------------------------- equivalence (App. F, H)
+// small.cu: Z = G^-1 C and its SVD R1 Lambda R2^T, Zit = R1 Lambda^-1 R2^T.
+void launch_equiv_svd(const double* G, const double* C, int k, double* R1, double* lam, double* R2,
+                      double* Z, double* Zit, int* err, cudaStream_t s);
+// small.cu: the permutation check of App. H from the three Grams.
+void launch_perm_check(const double* GAA, const double* GBB, const double* GAB, int k, double eps,
+                       double keep_frac, int* b_of_a, int* count, cudaStream_t s);
+// rows.cu: out[0] = sum_i ||B_i - A_i T||^2 (FP64).
+void launch_transform_residual(const void* A, const void* B, int64_t rows, int k, int fdt,
+                               const double* T, double* part, double* out, cudaStream_t s);
 
 // KKT finalisation: combine the two factors' partial measures.
 void launch_kkt_final(const double* pu, const double* pv, double* out, cudaStream_t s);

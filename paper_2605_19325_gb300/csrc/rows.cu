@@ -455,4 +455,43 @@ void launch_kkt_final(const double* pu, const double* pv, double* out, cudaStrea
   kkt_final_kernel<<<1, 1, 0, s>>>(pu, pv, out);
 }
 
+// ---------------------------------------- transform residual (App. F)
+// part[b] = sum over block b's rows of ||B_i - A_i T||^2, every entry formed
+// in FP64 (A, B: rows x k of the factor type; T: k x k FP64 row-major).
+template <typename TF>
+__global__ void __launch_bounds__(RT_T)
+transform_residual_partial(const TF* __restrict__ A, const TF* __restrict__ B, int64_t rows, int k,
+                           const double* __restrict__ T, double* part) {
+  __shared__ double Ts[RMAX * RMAX];
+  __shared__ double sh[RT_T];
+  for (int e = threadIdx.x; e < k * k; e += RT_T) Ts[e] = T[e];
+  __syncthreads();
+  const int64_t chunk = (rows + NPART - 1) / NPART;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+  double acc = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += RT_T) {
+    double a[RMAX];
+    for (int l = 0; l < k; ++l) a[l] = (double)A[i * k + l];
+    for (int j = 0; j < k; ++j) {
+      double sacc = (double)B[i * k + j];
+      for (int l = 0; l < k; ++l) sacc = fma(-a[l], Ts[l * k + j], sacc);
+      acc = fma(sacc, sacc, acc);
+    }
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+void launch_transform_residual(const void* A, const void* B, int64_t rows, int k, int fdt,
+                               const double* T, double* part, double* out, cudaStream_t s) {
+  note_launch(2);
+  if (fdt == T_F64)
+    transform_residual_partial<double><<<NPART, RT_T, 0, s>>>((const double*)A, (const double*)B,
+                                                             rows, k, T, part);
+  else
+    transform_residual_partial<float><<<NPART, RT_T, 0, s>>>((const float*)A, (const float*)B,
+                                                            rows, k, T, part);
+  part_sum_to<<<1, 32, 0, s>>>(part, NPART, out, 0);
+}
+
 }  // namespace enmf

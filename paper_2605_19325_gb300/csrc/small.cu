@@ -223,12 +223,11 @@ __device__ void set_identity(double* V, int Np) {
 // from the previous step's right singular vectors D (Np x Np column-major,
 // identity at the first step): A = M D is already nearly column-orthogonal and
 // the sweeps converge in a few passes.  D is updated in place.
-__global__ void __launch_bounds__(SM_T)
-polar_kernel(const double* __restrict__ Mg, int k, double* R, double* D, double tol, DevState* st,
-             int* err) {
-  extern __shared__ double smd[];
-  __shared__ double red[SM_T];
-  if (*(volatile int*)&st->admm_done) return;
+// Shared part of the polar kernels: Rn (k x k, shared) = polar(Mg), D (Np x
+// Np, global, column-major) the warm start, updated.  Returns the Jacobi
+// sweeps run; *smin_out the smallest singular value of M.
+__device__ int polar_core(const double* __restrict__ Mg, int k, double* D, double* smd,
+                          double*& Rn_out, double* smin_out) {
   const int Np = k + (k & 1);
   double* A = smd;                 // Np columns x k rows (column-major)
   double* V = A + (size_t)Np * k;  // Np x Np
@@ -271,6 +270,28 @@ polar_kernel(const double* __restrict__ Mg, int k, double* R, double* D, double 
     Rn[e] = s;
   }
   __syncthreads();
+  Rn_out = Rn;
+  *smin_out = smin;
+  return sw;
+}
+
+// ------------------------------------------------------------- polar (R)
+// M (k x k row-major) -> R = C D^T with M = C S D^T.  With the one-sided
+// Jacobi on the columns of M: M V = A (orthogonal columns), so C = A S^-1 and
+// D = V, R = sum_c (a_c / s_c) v_c^T.
+// Warm start: successive ADMM steps change M little, so the rotation starts
+// from the previous step's right singular vectors D (Np x Np column-major,
+// identity at the first step): A = M D is already nearly column-orthogonal and
+// the sweeps converge in a few passes.  D is updated in place.
+__global__ void __launch_bounds__(SM_T)
+polar_kernel(const double* __restrict__ Mg, int k, double* R, double* D, double tol, DevState* st,
+             int* err) {
+  extern __shared__ double smd[];
+  __shared__ double red[SM_T];
+  if (*(volatile int*)&st->admm_done) return;
+  double* Rn;
+  double smin;
+  const int sw = polar_core(Mg, k, D, smd, Rn, &smin);
   double d = 0.0;
   for (int e = threadIdx.x; e < k * k; e += SM_T) {
     double x = Rn[e] - R[e];
@@ -288,6 +309,36 @@ polar_kernel(const double* __restrict__ Mg, int k, double* R, double* D, double 
   }
 }
 
+// The same polar factor into Rout, with no loop bookkeeping (Algorithm 4's
+// R1 and R2 updates, each with its own warm start D).  Algorithm 4 runs two
+// warm-started factors for hundreds of steps, and the rounding of the
+// accumulated Jacobi rotations drifts D (and so R) away from orthogonality
+// by about 1e-12 at r = 49; one Newton-Schulz step R (3I - R^T R) / 2 maps an
+// R with |R^T R - I| = e to one with about 3e^2 / 4 and leaves the polar
+// factor itself unchanged.
+__global__ void __launch_bounds__(SM_T)
+polar_plain_kernel(const double* __restrict__ Mg, int k, double* Rout, double* D, int* err) {
+  extern __shared__ double smd[];
+  double* Rn;
+  double smin;
+  const int sw = polar_core(Mg, k, D, smd, Rn, &smin);
+  double* P = Rn + (size_t)k * k;  // the input copy's slot, free again
+  for (int e = threadIdx.x; e < k * k; e += SM_T) {   // P = R^T R
+    const int i = e / k, j = e % k;
+    double s = 0.0;
+    for (int c = 0; c < k; ++c) s = fma(Rn[c * k + i], Rn[c * k + j], s);
+    P[e] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k; e += SM_T) {   // R (3I - P) / 2
+    const int i = e / k, j = e % k;
+    double s = 0.0;
+    for (int c = 0; c < k; ++c) s = fma(Rn[i * k + c], (c == j ? 3.0 : 0.0) - P[c * k + j], s);
+    Rout[e] = 0.5 * s;
+  }
+  if (threadIdx.x == 0 && (sw > JAC_MAX_SWEEPS - 1 || !(smin > 0.0))) atomicOr(err, ERR_NOTCONV);
+}
+
 static size_t small_smem(int rows, int Np) {
   return sizeof(double) * ((size_t)Np * rows + (size_t)Np * Np + Np + (size_t)Np * Np) +
          sizeof(int) * Np + 64;
@@ -300,6 +351,14 @@ void launch_polar(const double* M, int k, double* R, double* D, double tol, DevS
   size_t smem = sizeof(double) * ((size_t)Np * k + (size_t)Np * Np + Np + 2 * (size_t)k * k) + 64;
   cudaFuncSetAttribute(polar_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   polar_kernel<<<1, SM_T, smem, s>>>(M, k, R, D, tol, st, err);
+}
+
+void launch_polar_plain(const double* M, int k, double* R, double* D, int* err, cudaStream_t s) {
+  note_launch(1);
+  int Np = k + (k & 1);
+  size_t smem = sizeof(double) * ((size_t)Np * k + (size_t)Np * Np + Np + 2 * (size_t)k * k) + 64;
+  cudaFuncSetAttribute(polar_plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  polar_plain_kernel<<<1, SM_T, smem, s>>>(M, k, R, D, err);
 }
 
 // ------------------------------------------------------ Gram -> orth map
@@ -544,6 +603,247 @@ void launch_svd_finish(const double* sigma, const double* Ut, const double* Wt, 
   note_launch(1);
   svd_finish_kernel<<<1, 256, 0, s>>>(sigma, Ut, Wt, k1, k2, r, colsumQ, colsumQ2, Tu, Tv,
                                       sigma_out);
+}
+
+// ------------------------------------------------- equivalence tools (App. F, H)
+// Generalized orthogonal transform between two factorisations (App. F): from
+// G = U_e^T U_e and C = U_e^T U_alg (k x k, FP64), Z = G^-1 C -- the
+// least-squares map from U_e to U_alg, Q Gamma^-1 P^T U_alg for the thin SVD
+// U_e = P Gamma Q^T -- by a Cholesky factorisation of G, then Z = R1 Lambda
+// R2^T by one-sided Jacobi (Lambda descending) and Zit = R1 Lambda^-1 R2^T,
+// the map of the V factors.  Row-major outputs; ERR_NOTCONV when G is not
+// positive definite or Jacobi did not converge.
+__global__ void __launch_bounds__(SM_T)
+equiv_svd_kernel(const double* __restrict__ Gg, const double* __restrict__ Cg, int k, double* R1,
+                 double* lam, double* R2, double* Zout, double* Zit, int* err) {
+  extern __shared__ double smd[];
+  const int Np = k + (k & 1);
+  double* L = smd;                    // k x k, Cholesky factor (lower), row-major
+  double* Z = L + (size_t)k * k;      // k x k, C then Z (row-major)
+  double* A = Z + (size_t)k * k;      // Np columns x k rows (column-major)
+  double* V = A + (size_t)Np * k;     // Np x Np
+  double* nrm = V + (size_t)Np * Np;
+  int* ord = reinterpret_cast<int*>(nrm + Np);
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < k * k; e += SM_T) {
+    L[e] = Gg[e];
+    Z[e] = Cg[e];
+  }
+  __syncthreads();
+  // Cholesky, right-looking: column j, then the trailing update
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = L[j * k + j];
+      if (!(d > 0.0)) bad = 1;
+      L[j * k + j] = d > 0.0 ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double ljj = L[j * k + j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += SM_T) L[i * k + j] /= ljj;
+    __syncthreads();
+    for (int e = threadIdx.x; e < (k - j - 1) * (k - j - 1); e += SM_T) {
+      const int i = j + 1 + e / (k - j - 1), c = j + 1 + e % (k - j - 1);
+      if (c <= i) L[i * k + c] = fma(-L[i * k + j], L[c * k + j], L[i * k + c]);
+    }
+    __syncthreads();
+  }
+  // Z = L^-T L^-1 C, one right-hand side column per thread
+  for (int c = threadIdx.x; c < k; c += SM_T) {
+    for (int i = 0; i < k; ++i) {           // forward: L y = C_:c
+      double sacc = Z[i * k + c];
+      for (int p = 0; p < i; ++p) sacc = fma(-L[i * k + p], Z[p * k + c], sacc);
+      Z[i * k + c] = sacc / L[i * k + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {      // backward: L^T z = y
+      double sacc = Z[i * k + c];
+      for (int p = i + 1; p < k; ++p) sacc = fma(-L[p * k + i], Z[p * k + c], sacc);
+      Z[i * k + c] = sacc / L[i * k + i];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < Np * k; e += SM_T) {
+    const int c = e / k, i = e % k;
+    A[e] = c < k ? Z[i * k + c] : 0.0;
+  }
+  set_identity(V, Np);
+  __syncthreads();
+  const int sw = jacobi_osvd<double>(A, k, Np, V, JAC_MAX_SWEEPS);
+  sort_desc(A, k, Np, nrm, ord);
+  for (int e = threadIdx.x; e < k * k; e += SM_T) {
+    const int i = e / k, j = e % k;
+    const int c = ord[j];
+    R1[e] = nrm[c] > 0.0 ? A[(size_t)c * k + i] / nrm[c] : 0.0;
+    R2[e] = V[(size_t)c * Np + i];
+    if (Zout) Zout[e] = Z[e];
+  }
+  for (int j = threadIdx.x; j < k; j += SM_T) lam[j] = nrm[ord[j]];
+  __syncthreads();
+  // Zit = R1 Lambda^-1 R2^T = sum_j (a_j / s_j^2) v_j^T over the columns
+  for (int e = threadIdx.x; e < k * k; e += SM_T) {
+    const int i = e / k, p = e % k;
+    double sacc = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const int c = ord[j];
+      const double s2 = nrm[c] * nrm[c];
+      if (s2 > 0.0) sacc = fma(A[(size_t)c * k + i] / s2, V[(size_t)c * Np + p], sacc);
+    }
+    Zit[e] = sacc;
+  }
+  if (threadIdx.x == 0 && (bad || sw > JAC_MAX_SWEEPS - 1)) atomicOr(err, ERR_NOTCONV);
+}
+
+void launch_equiv_svd(const double* G, const double* C, int k, double* R1, double* lam, double* R2,
+                      double* Z, double* Zit, int* err, cudaStream_t s) {
+  note_launch(1);
+  const int Np = k + (k & 1);
+  const size_t smem = sizeof(double) * (2 * (size_t)k * k + (size_t)Np * k + (size_t)Np * Np + Np) +
+                      sizeof(int) * Np + 64;
+  cudaFuncSetAttribute(equiv_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  equiv_svd_kernel<<<1, SM_T, smem, s>>>(G, C, k, R1, lam, R2, Z, Zit, err);
+}
+
+// Permutation check of App. H from the Grams GAA = U_A^T U_A, GBB = U_B^T U_B
+// and GAB = U_A^T U_B (k x k, FP64).  Cosines cos_ij = G_ij / sqrt(G_ii G_jj)
+// (0 for a zero column).  Step 1: pairs (i, j) taken one to one in decreasing
+// cos(U_A^(i), U_B^(j)) (ties by lower i, then lower j) while the cosine is
+// >= 1 - eps.  Step 2: on the candidates (ordered by i), the columns of the
+// self- and cross-similarity matrices M, N, S sorted descending and rounded to
+// one decimal (floor(10 x + 1/2)); candidate c stays when M's column c equals
+// N's and S's at more than keep_frac of its positions.  Output: b_of_a[i] =
+// the matched column of U_B, or -1; *count = pairs kept.
+constexpr int PC_T = 256;
+
+__device__ __forceinline__ double cos_of(const double* G, int ldg, int i, int j, const double* na,
+                                         const double* nb) {
+  const double den = na[i] * nb[j];
+  return den > 0.0 ? G[i * ldg + j] / den : 0.0;
+}
+
+__global__ void __launch_bounds__(PC_T)
+perm_check_kernel(const double* __restrict__ GAA, const double* __restrict__ GBB,
+                  const double* __restrict__ GAB, int k, double eps, double keep_frac,
+                  int* b_of_a, int* count) {
+  __shared__ double na[RMAX], nb[RMAX];
+  __shared__ double S0[RMAX * RMAX];
+  __shared__ unsigned char used_a[RMAX], used_b[RMAX];
+  __shared__ int pa[RMAX], pb[RMAX], npair, stop;
+  __shared__ double bv[PC_T];
+  __shared__ int bi[PC_T];
+  __shared__ int keep[RMAX];
+  const int t = threadIdx.x;
+  for (int i = t; i < k; i += PC_T) {
+    na[i] = sqrt(fmax(GAA[i * k + i], 0.0));
+    nb[i] = sqrt(fmax(GBB[i * k + i], 0.0));
+    used_a[i] = 0;
+    used_b[i] = 0;
+  }
+  if (t == 0) {
+    npair = 0;
+    stop = 0;
+  }
+  __syncthreads();
+  for (int e = t; e < k * k; e += PC_T) S0[e] = cos_of(GAB, k, e / k, e % k, na, nb);
+  __syncthreads();
+  // step 1: greedy one-to-one pairing
+  for (int round = 0; round < k; ++round) {
+    double best = -INFINITY;
+    int bidx = -1;
+    for (int e = t; e < k * k; e += PC_T) {
+      const int i = e / k, j = e % k;
+      if (used_a[i] || used_b[j]) continue;
+      const double v = S0[e];
+      if (v > best || (v == best && (bidx < 0 || e < bidx))) {   // e = i k + j: (i, j) order
+        best = v;
+        bidx = e;
+      }
+    }
+    bv[t] = best;
+    bi[t] = bidx;
+    __syncthreads();
+    for (int w = PC_T / 2; w > 0; w >>= 1) {
+      if (t < w) {
+        const double v2 = bv[t + w];
+        const int i2 = bi[t + w];
+        if (i2 >= 0 && (bi[t] < 0 || v2 > bv[t] || (v2 == bv[t] && i2 < bi[t]))) {
+          bv[t] = v2;
+          bi[t] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    if (t == 0) {
+      if (bi[0] < 0 || bv[0] < 1.0 - eps) {
+        stop = 1;
+      } else {
+        const int i = bi[0] / k, j = bi[0] % k;
+        used_a[i] = 1;
+        used_b[j] = 1;
+        pa[npair] = i;
+        pb[npair] = j;
+        ++npair;
+      }
+    }
+    __syncthreads();
+    if (stop) break;
+  }
+  // candidates in increasing index of U_A
+  if (t == 0) {
+    for (int x = 1; x < npair; ++x)
+      for (int y = x; y > 0 && pa[y - 1] > pa[y]; --y) {
+        int q = pa[y]; pa[y] = pa[y - 1]; pa[y - 1] = q;
+        q = pb[y]; pb[y] = pb[y - 1]; pb[y - 1] = q;
+      }
+  }
+  __syncthreads();
+  const int nc = npair;
+  // step 2: one thread per candidate column; the column's entries sorted by
+  // rank (descending value, ties by position) and compared after rounding
+  for (int c = t; c < nc; c += PC_T) {
+    double srt[3][RMAX];
+    for (int which = 0; which < 3; ++which) {
+      for (int x = 0; x < nc; ++x) {
+        double vx;
+        if (which == 0) vx = cos_of(GAA, k, pa[x], pa[c], na, na);
+        else if (which == 1) vx = cos_of(GBB, k, pb[x], pb[c], nb, nb);
+        else vx = cos_of(GAB, k, pa[x], pb[c], na, nb);
+        int rank = 0;
+        for (int y = 0; y < nc; ++y) {
+          double vy;
+          if (which == 0) vy = cos_of(GAA, k, pa[y], pa[c], na, na);
+          else if (which == 1) vy = cos_of(GBB, k, pb[y], pb[c], nb, nb);
+          else vy = cos_of(GAB, k, pa[y], pb[c], na, nb);
+          if (vy > vx || (vy == vx && y < x)) ++rank;
+        }
+        srt[which][rank] = vx;
+      }
+    }
+    int match = 0;
+    for (int pos = 0; pos < nc; ++pos) {
+      const double km = floor(10.0 * srt[0][pos] + 0.5), kn = floor(10.0 * srt[1][pos] + 0.5),
+                   ks = floor(10.0 * srt[2][pos] + 0.5);
+      if (km == kn && km == ks) ++match;
+    }
+    keep[c] = (double)match / (double)nc > keep_frac ? 1 : 0;
+  }
+  __syncthreads();
+  for (int i = t; i < k; i += PC_T) b_of_a[i] = -1;
+  __syncthreads();
+  if (t == 0) {
+    int kept = 0;
+    for (int c = 0; c < nc; ++c)
+      if (keep[c]) {
+        b_of_a[pa[c]] = pb[c];
+        ++kept;
+      }
+    *count = kept;
+  }
+}
+
+void launch_perm_check(const double* GAA, const double* GBB, const double* GAB, int k, double eps,
+                       double keep_frac, int* b_of_a, int* count, cudaStream_t s) {
+  note_launch(1);
+  perm_check_kernel<<<1, PC_T, 0, s>>>(GAA, GBB, GAB, k, eps, keep_frac, b_of_a, count);
 }
 
 }  // namespace enmf

@@ -142,9 +142,11 @@ class Server:
 
     def _retire(self, now):
         keep = []
+        states = {rp: B.enmf_batch_states(b, self.max_members)
+                  for rp, b in self.batches.items() if B.enmf_batch_size(b) > 0}
         for sl in self.active:
             b = self.batches[sl.rp]
-            info, f = B.enmf_batch_member(b, sl.slot)
+            info, f = states[sl.rp][sl.slot]
             done = info.iters >= self.max_iter
             if (not done and info.stage == 1 and info.iters >= self.min_iter
                     and sl.f_prev is not None):

@@ -92,6 +92,15 @@ class Solver:
         info = B.enmf_iterate(self.ctx, self.X, self.U, self.V, n_iter, trace=tr, reset=reset, **kw)
         return (tr[:n_iter] if trace else None), info
 
+    def rotate_general(self, opts=None):
+        """Algorithm 4 (Eq. 5) in place on U, V: returns (info, R1, lam, R2)."""
+        dev = self.X.device
+        R1 = torch.empty(self.r, self.r, dtype=torch.float64, device=dev)
+        R2 = torch.empty(self.r, self.r, dtype=torch.float64, device=dev)
+        lam = torch.empty(self.r, dtype=torch.float64, device=dev)
+        info, code = B.enmf_rotate_general(self.ctx, self.U, self.V, R1, lam, R2, opts)
+        return info, R1, lam, R2
+
     def residual(self, direct=True):
         return B.enmf_residual(self.ctx, self.X, self.U, self.V, 1 if direct else 0)
 
@@ -136,6 +145,25 @@ class Solver:
 
     def pbcd_counts(self):
         return B.enmf_pbcd_counts(self.ctx)
+
+    def equiv_transform(self, Ua, Va, Ue=None, Ve=None):
+        """App. F: (R1, lam, R2, delta_u, delta_v) relating (Ue, Ve) (default:
+        this solver's U, V) to another factorisation (Ua, Va) of the same
+        problem."""
+        Ue = self.U if Ue is None else Ue
+        Ve = self.V if Ve is None else Ve
+        dev = self.X.device
+        R1 = torch.empty(self.r, self.r, dtype=torch.float64, device=dev)
+        R2 = torch.empty(self.r, self.r, dtype=torch.float64, device=dev)
+        lam = torch.empty(self.r, dtype=torch.float64, device=dev)
+        du, dv = B.enmf_equiv_transform(self.ctx, Ue, Ve, Ua, Va, R1, lam, R2)
+        return R1, lam, R2, du, dv
+
+    def perm_check(self, UB, UA=None, eps=0.05, keep_frac=0.9):
+        """App. H: for each column of UA (default: this solver's U) the
+        matched column of UB, or -1; and the number of matches."""
+        UA = self.U if UA is None else UA
+        return B.enmf_perm_check(self.ctx, UA, UB, self.r, eps, keep_frac)
 
 
 def solve(X: torch.Tensor, r: int, n_iter: int, f_dtype=None, x_stream=None) -> SolveResult:

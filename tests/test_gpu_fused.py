@@ -140,3 +140,26 @@ def test_fused_availability():
     sv = _solver(X, 20)
     assert B.enmf_set_fused(sv.ctx, 1)
     sv.close()
+
+
+def test_fused_graph_replay_repeats_the_captured_call():
+    """A second identical call replays the captured alternation graph (fused
+    kernels included) and must reproduce the first call's results bit for bit;
+    the first call ran the graph it had just captured."""
+    from paper_2605_19325_gb300 import binding as B
+    X = _inputs(1000, 700, 20, seed=3)
+    sv = _solver(X, 20)
+    assert B.enmf_set_fused(sv.ctx, 1)
+    sv.svd_init()
+    sv.rotate()
+    U0, V0 = sv.U.clone(), sv.V.clone()
+    runs = []
+    for _ in range(3):
+        sv.U.copy_(U0)
+        sv.V.copy_(V0)
+        tr, info = sv.iterate(60, reset=1)
+        runs.append((_np(tr), _np(sv.U), _np(sv.V)))
+    for k in (1, 2):
+        for a, b in zip(runs[0], runs[k]):
+            np.testing.assert_array_equal(a, b)
+    sv.close()

@@ -84,6 +84,10 @@ class FakeBinding:
         stage = 1 if mb["iters"] >= 10 else 0
         return _Info(mb["iters"], stage), mb["f"]
 
+    def enmf_batch_states(self, b, cap):
+        assert len(self.batches[b]["members"]) <= cap
+        return {slot: self.enmf_batch_member(b, slot) for slot in self.batches[b]["members"]}
+
 
 class FakeSolver:
     def __init__(self, Xt, r, stream=None, x_stream=None):
