@@ -7,7 +7,9 @@ does, and it shares no code with the CUDA kernels.
 
 Convention (App. I): X is m x n and nonnegative, U is m x r, V is n x r and
 X ~ U V^T.  All arithmetic is IEEE double.  Library primitives used as steps:
-``numpy`` matrix products and ``numpy.linalg.svd`` (the LAPACK SVD).
+``numpy`` matrix products, ``numpy.linalg.svd`` (the LAPACK SVD),
+``numpy.linalg.solve`` (the masked least-squares rows of App. C) and
+``numpy.roots`` (the quartic of Algorithm 4).
 
 Sections and equations cited are those of "An Exterior Method for Nonnegative
 Matrix Factorization" (ICML 2026).  Where the paper leaves a value open, the
@@ -15,7 +17,9 @@ reading taken is named in the function's docstring (readings R1..R12; the
 same list is kept with the design notes of the repository).
 
 Parity status: every function below is pinned by a CPU test against a closed
-form, an invariant or brute force (tests/test_oracle_pins.py), except the
+form, an invariant, an independent library or brute force
+(tests/test_oracle_pins.py, test_oracle_equiv.py, test_oracle_general.py,
+test_oracle_sparse.py), except the
 exact ADMM and PBCD trajectories, which the paper does not print; those are
 pinned only through their invariants (orthogonality, level-set invariance,
 brute force at r = 2, optimal step size by line search).
@@ -659,3 +663,161 @@ def rotate_general(Us, Vs, rho=None, max_iter=ADMM_MAX_ITER, tol=ADMM_TOL):
     T1 = R1 * lam          # R1 Lambda
     T2 = R1 / lam          # R1 Lambda^-1
     return Us @ T1 @ R2, Vs @ T2 @ R2, R1, lam, R2, info
+
+
+# --------------------------------------------------------------------------
+# Sparse X (Sec. 5, the Reuters experiment): X given by its stored entries in
+# compressed-row form -- row_ptr (m + 1), col and val (nnz), the entries of
+# row i at positions row_ptr[i] .. row_ptr[i+1] - 1 with strictly increasing
+# columns.  The method is Algorithm 3 on the matrix these entries define;
+# only the products X V and X^T U touch the entries.
+def csr_dense(m, n, row_ptr, col, val):
+    """The m x n matrix with X[i, col[p]] = val[p] for the stored entries of
+    row i and zeros elsewhere."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    rows = np.repeat(np.arange(m), np.diff(row_ptr))
+    X = np.zeros((m, n))
+    X[rows, np.asarray(col, dtype=np.int64)] = np.asarray(val, dtype=np.float64)
+    return X
+
+
+def csr_rows_times(row_ptr, col, val, rows, B):
+    """(X B)[i, :] for each listed row i, summed over row i's stored entries:
+    sum_p val[p] B[col[p], :]."""
+    B = np.asarray(B, dtype=np.float64)
+    out = np.zeros((len(rows), B.shape[1]))
+    for t, i in enumerate(rows):
+        a, b = int(row_ptr[i]), int(row_ptr[i + 1])
+        c = np.asarray(col[a:b], dtype=np.int64)
+        out[t] = np.asarray(val[a:b], dtype=np.float64) @ B[c]
+    return out
+
+
+def csr_cols_times(row_ptr, col, val, cols, B):
+    """(X^T B)[j, :] for each listed column j: sum over the stored entries
+    (i, j) of val B[i, :]."""
+    B = np.asarray(B, dtype=np.float64)
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    rows = np.repeat(np.arange(len(row_ptr) - 1), np.diff(row_ptr))
+    col = np.asarray(col, dtype=np.int64)
+    val = np.asarray(val, dtype=np.float64)
+    out = np.zeros((len(cols), B.shape[1]))
+    for t, j in enumerate(cols):
+        sel = col == j
+        out[t] = val[sel] @ B[rows[sel]]
+    return out
+
+
+def csr_sumsq(val):
+    """||X||_F^2 from the stored entries."""
+    v = np.asarray(val, dtype=np.float64)
+    return float(v @ v)
+
+
+# --------------------------------------------------------------------------
+# Matrix completion (App. C, Algorithm eNMC): only the entries in the mask
+# M_E (here: the stored entries of a compressed-row pattern, M_E[i, j] = 1
+# for a stored (i, j)) are known.
+def objective_masked(X, M, U, V):
+    """f^(U, V) = 1/2 ||M_E o (X - U V^T)||_F^2 (App. C)."""
+    E = M * (X - U @ V.T)
+    return 0.5 * float(np.sum(E * E))
+
+
+def grad_masked(X, M, U, V):
+    """grad_U f^ = (M_E o (U V^T - X)) V (App. C); grad_V is the same with
+    X^T, M_E^T and the factors swapped."""
+    return (M * (U @ V.T - X)) @ V
+
+
+def pbcd_masked(X, M, U, V, mask, eps=PBCD_EPS, max_iter=PBCD_MAX_ITER):
+    """Algorithm 2 with the mask M_E (App. C): PBCD on U's rows, V fixed.
+
+    g = M_U+ o ((M_E o (U V^T - X)) V).  Reading (the paper changes only the
+    gradients): the row step is the exact minimiser of the masked objective
+    along -g_i, d_i = ||g_i||^2 / sum_j M_E[i, j] (g_i . v_j)^2, which is
+    Eq. 10 when M_E is all ones; d_i = 0 for a zero numerator or denominator.
+    U_i <- max(0, U_i - d_i g_i) on the mask; stop when ||g|| < eps ||g_init||
+    or after max_iter sweeps (or at an exactly zero gradient).
+    """
+    U = np.array(U, dtype=np.float64)
+    Mk = np.asarray(mask, dtype=np.float64)
+    g = Mk * grad_masked(X, M, U, V)
+    info = PbcdInfo(g0=float(np.linalg.norm(g)))
+    for t in range(max_iter):
+        num = np.sum(g * g, axis=1)
+        den = np.sum(M * (g @ V.T) ** 2, axis=1)
+        d = np.where((num > 0) & (den > 0), num / np.where(den > 0, den, 1.0), 0.0)
+        step = np.maximum(U - d[:, None] * g, 0.0)
+        U = np.where(Mk > 0, step, U)
+        g = Mk * grad_masked(X, M, U, V)
+        info.pg = float(np.linalg.norm(g))
+        info.iters = t + 1
+        if info.pg < eps * info.g0 or info.pg == 0.0:
+            break
+    return U, info
+
+
+def masked_als(X, M, r, sweeps=50, lam=1e-9, tol=1e-10):
+    """Unconstrained start of Algorithm eNMC: a local minimum of f^ over all
+    U, V (App. C computes it with softImpute-ALS).  Reading: softImpute-ALS at
+    a vanishing ridge -- alternating exact row least squares
+        u_i = (sum_j M_E[i, j] v_j v_j^T + lam c I)^-1 sum_j M_E[i, j] x_ij v_j
+    (c = mean of the Gram's diagonal, lam = 1e-9: a guard for rows with fewer
+    than r known entries), then the same for V, from the balanced truncated
+    SVD of the zero-filled X; stop when f^ changes by <= tol relative or after
+    `sweeps` sweeps.  Returns (U, V, sweeps_run)."""
+    Xz = M * X
+    U, V, _ = truncated_svd(Xz, r)
+    f_old = objective_masked(X, M, U, V)
+    k = 0
+    for k in range(1, sweeps + 1):
+        for side in (0, 1):
+            F, G, Xs, Ms = (U, V, X, M) if side == 0 else (V, U, X.T, M.T)
+            Fn = np.empty_like(F)
+            for i in range(F.shape[0]):
+                sel = Ms[i] > 0
+                Gi = G[sel].T @ G[sel]
+                c = float(np.trace(Gi)) / r if Gi.size else 0.0
+                A = Gi + lam * (c if c > 0 else 1.0) * np.eye(r)
+                Fn[i] = np.linalg.solve(A, G[sel].T @ Xs[i, sel])
+            if side == 0:
+                U = Fn
+            else:
+                V = Fn
+        f = objective_masked(X, M, U, V)
+        if abs(f_old - f) <= tol * abs(f):
+            break
+        f_old = f
+    return U, V, k
+
+
+@dataclass
+class EnmcResult:
+    U: np.ndarray
+    V: np.ndarray
+    trace: list
+    sweeps: int
+
+
+def enmc(X, M, r, n_iter, eps=PBCD_EPS, pbcd_max_iter=PBCD_MAX_ITER, n_shift=N_SHIFT,
+         als_sweeps=50):
+    """Algorithm eNMC (App. C): the masked-ALS start, Algorithm 1's rotation
+    (unchanged), then n_iter rounds of: shift U's negative entries (Eq. 8),
+    mask, PBCD on U with M_E; the same for V.  Shift steps as in Algorithm 3
+    (reading R5: fixed at the first round with a negative entry).  trace: f^
+    after every round."""
+    X = np.asarray(X, dtype=np.float64)
+    M = np.asarray(M, dtype=np.float64)
+    U0, V0, sw = masked_als(X, M, r, sweeps=als_sweeps)
+    U, V, _, _ = rotate(U0, V0)
+    su = shift_step(U, n_shift) if np.any(U < 0) else 0.0
+    sv = shift_step(V, n_shift) if np.any(V < 0) else 0.0
+    trace = []
+    for _ in range(n_iter):
+        U = shift_negative(U, su)
+        U, _ = pbcd_masked(X, M, U, V, (U >= 0).astype(np.float64), eps, pbcd_max_iter)
+        V = shift_negative(V, sv)
+        V, _ = pbcd_masked(X.T, M.T, V, U, (V >= 0).astype(np.float64), eps, pbcd_max_iter)
+        trace.append(objective_masked(X, M, U, V))
+    return EnmcResult(U, V, trace, sw)

@@ -20,6 +20,13 @@ Workloads (sizes, distributions):
   templates times sparse activations (stands in for the Audio data of
   Sec. 5.1).
 * ``request_stream`` -- a Poisson stream of mixed-size planted problems.
+* ``sparse_docs`` -- a document-term matrix in compressed-row form: lognormal
+  document lengths, Zipf term frequencies, tf-idf weights with unit rows
+  (stands in for the Reuters matrix, 804,414 x 47,236 at 99.84 % sparsity, and
+  at 282 x 1,528 / 97.3 % for the Verb data of Sec. 5).
+* ``ratings`` -- a user-item rating matrix with a known-entry pattern
+  (power-law user activity and item popularity, ratings 1..5 from a planted
+  low-rank score); stands in for MovieLens 1M (App. C).
 """
 from __future__ import annotations
 
@@ -159,3 +166,89 @@ def request_matrix(req, dtype=np.float64):
     X, _, _ = planted(req.m, req.n, req.r, seed=req.seed, dist="uniform",
                       zero_frac=0.3, noise=0.01, dtype=dtype)
     return X
+
+
+def sparse_docs(m, n, density, seed=0, dtype=np.float32, zipf_s=1.05, len_sigma=0.9):
+    """Document-term matrix in compressed-row form (row_ptr int64 (m + 1),
+    col int32 (nnz), val (nnz)); columns strictly increasing within a row.
+
+    Draw order: document lengths (lognormal, sigma ``len_sigma``), a random
+    permutation of the terms, then every document's term draws (Zipf
+    exponent ``zipf_s`` over the permuted terms, with replacement).  Repeated
+    terms of a document merge into one entry with count tf; the weight is
+    (1 + ln tf) * idf, idf = ln((1 + m) / (1 + df)) + 1, and every row is
+    scaled to unit norm.  Lengths are rescaled twice so that the stored entries
+    after merging come to about density * m * n.
+    """
+    rng = np.random.default_rng(seed)
+    L0 = rng.lognormal(0.0, len_sigma, m)
+    perm = rng.permutation(n)
+    p = np.arange(1, n + 1, dtype=np.float64) ** -zipf_s
+    cdf = np.cumsum(p / p.sum())
+    target = density * m * n
+    u_state = rng.bit_generator.state
+
+    def draw(scale):
+        rng.bit_generator.state = u_state
+        L = np.maximum(1, np.rint(L0 * scale)).astype(np.int64)
+        L = np.minimum(L, n)
+        u = rng.random(int(L.sum()))
+        terms = perm[np.minimum(np.searchsorted(cdf, u, side="right"), n - 1)]
+        rows = np.repeat(np.arange(m, dtype=np.int64), L)
+        key, tf = np.unique(rows * n + terms, return_counts=True)
+        return key, tf
+
+    scale = target / L0.sum()
+    key, tf = draw(scale)
+    for _ in range(2):
+        scale *= target / max(1, key.size)
+        key, tf = draw(scale)
+    r_i = key // n
+    c_j = (key % n).astype(np.int32)
+    df = np.bincount(c_j, minlength=n)
+    idf = np.log((1.0 + m) / (1.0 + df)) + 1.0
+    w = (1.0 + np.log(tf)) * idf[c_j]
+    nrm = np.sqrt(np.bincount(r_i, weights=w * w, minlength=m))
+    w = w / nrm[r_i]
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.bincount(r_i, minlength=m))
+    return row_ptr, c_j, w.astype(dtype)
+
+
+def ratings(m=6040, n=3706, known=0.045, r0=8, seed=0, dtype=np.float32):
+    """User-item ratings with a known-entry pattern, in compressed-row form
+    (row_ptr, col, val); the known entries are the mask M_E of App. C.
+
+    Draw order: user activity (Pareto 1.2, scaled), item popularity (Pareto
+    1.0), user and item factors (Exponential(1), rank r0), per-entry noise.
+    User i rates about known * n * activity_i items (rescaled once so that
+    the total is about known * m * n) drawn without replacement
+    in proportion to popularity (at least 5); the rating of (i, j) is the
+    planted score u_i . v_j mapped to 1..5 by quantiles of all scores plus
+    Gaussian noise (sigma 0.5), rounded and clipped to 1..5.
+    """
+    rng = np.random.default_rng(seed)
+    act = rng.pareto(1.2, m) + 1.0
+    pop = rng.pareto(1.0, n) + 1.0
+    Uf = rng.exponential(1.0, (m, r0))
+    Vf = rng.exponential(1.0, (n, r0))
+    base = act / act.mean() * known * n
+    cnt = np.clip(np.rint(base), 5, n)
+    cnt = np.clip(np.rint(base * (known * m * n / cnt.sum())), 5, n).astype(np.int64)
+    w = pop / pop.sum()
+    rows, cols = [], []
+    for i in range(m):
+        # Gumbel top-k: k items without replacement, in proportion to w
+        g = np.log(w) - np.log(-np.log(rng.random(n)))
+        sel = np.sort(np.argpartition(-g, cnt[i] - 1)[:cnt[i]])
+        rows.append(np.full(sel.size, i, dtype=np.int64))
+        cols.append(sel)
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols).astype(np.int32)
+    score = np.einsum("ij,ij->i", Uf[rows], Vf[cols])
+    q = np.quantile(score, [0.06, 0.17, 0.43, 0.78])
+    val = 1.0 + np.searchsorted(q, score) + rng.normal(0.0, 0.5, score.size)
+    val = np.clip(np.rint(val), 1.0, 5.0)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.bincount(rows, minlength=m))
+    return row_ptr, cols, val.astype(dtype)

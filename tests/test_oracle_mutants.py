@@ -459,3 +459,85 @@ def test_planted_mistake_in_the_equivalence_and_general_rotation_is_caught(monke
             failures.append(type(e).__name__)
             break
     assert failures, f"planted mistake '{name}' passed its pins"
+
+
+# ------------------------------------------- sparse X and matrix completion
+import test_oracle_sparse as SP  # noqa: E402
+
+ORIG3 = {name: getattr(O, name) for name in (
+    "csr_dense", "csr_rows_times", "grad_masked", "pbcd_masked", "masked_als")}
+
+
+def csr_dense_row_shift(m, n, row_ptr, col, val):
+    """Entries of row i placed in row i + 1 (row_ptr read one off)."""
+    X = ORIG3["csr_dense"](m, n, row_ptr, col, val)
+    return np.roll(X, 1, axis=0)
+
+
+def csr_rows_times_unweighted(row_ptr, col, val, rows, B):
+    """Values dropped: the pattern's sum of B rows."""
+    return ORIG3["csr_rows_times"](row_ptr, col, np.ones_like(np.asarray(val)), rows, B)
+
+
+def grad_masked_unmasked(X, M, U, V):
+    """The mask dropped from the gradient (unknown entries taken as zeros)."""
+    return (U @ V.T - X) @ V
+
+
+def pbcd_masked_full_denominator(X, M, U, V, mask, eps=O.PBCD_EPS, max_iter=O.PBCD_MAX_ITER):
+    """Eq. 10's unmasked denominator g_i V^T V g_i^T kept under the mask."""
+    U = np.array(U, dtype=np.float64)
+    Mk = np.asarray(mask, dtype=np.float64)
+    g = Mk * O.grad_masked(X, M, U, V)
+    info = O.PbcdInfo(g0=float(np.linalg.norm(g)))
+    for t in range(max_iter):
+        num = np.sum(g * g, axis=1)
+        den = np.sum((g @ V.T) ** 2, axis=1)
+        d = np.where((num > 0) & (den > 0), num / np.where(den > 0, den, 1.0), 0.0)
+        U = np.where(Mk > 0, np.maximum(U - d[:, None] * g, 0.0), U)
+        g = Mk * O.grad_masked(X, M, U, V)
+        info.pg = float(np.linalg.norm(g))
+        info.iters = t + 1
+        if info.pg < eps * info.g0 or info.pg == 0.0:
+            break
+    return U, info
+
+
+def masked_als_unmasked_gram(X, M, r, sweeps=50, lam=1e-9, tol=1e-10):
+    """Row least squares with the full Gram V^T V instead of the known
+    entries' Gram."""
+    U, V, _ = O.truncated_svd(M * X, r)
+    k = 0
+    for k in range(1, sweeps + 1):
+        U = np.linalg.solve(V.T @ V + lam * np.eye(r), V.T @ (M * X).T).T
+        V = np.linalg.solve(U.T @ U + lam * np.eye(r), U.T @ (M * X)).T
+    return U, V, k
+
+
+MUTANTS3 = [
+    ("compressed rows placed one row down", "csr_dense", csr_dense_row_shift,
+     [SP.test_csr_dense_matches_scipy]),
+    ("compressed-row product without the values", "csr_rows_times", csr_rows_times_unweighted,
+     [SP.test_csr_products_match_scipy]),
+    ("App. C gradient without the mask", "grad_masked", grad_masked_unmasked,
+     [SP.test_masked_gradient_is_the_derivative]),
+    ("masked PBCD with the unmasked step denominator", "pbcd_masked",
+     pbcd_masked_full_denominator, [SP.test_masked_step_is_the_exact_line_minimiser]),
+    ("masked ALS with the full Gram", "masked_als", masked_als_unmasked_gram,
+     [SP.test_masked_als_reaches_a_stationary_point]),
+]
+
+
+@pytest.mark.parametrize("name,attr,fn,pins", MUTANTS3, ids=[m[0] for m in MUTANTS3])
+def test_planted_mistake_in_the_sparse_and_completion_oracle_is_caught(monkeypatch, name, attr,
+                                                                       fn, pins):
+    monkeypatch.setattr(O, attr, fn)
+    failures = []
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, ValueError, FloatingPointError, np.linalg.LinAlgError,
+                IndexError) as e:
+            failures.append(type(e).__name__)
+            break
+    assert failures, f"planted mistake '{name}' passed its pins"
