@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-fp8", action="store_true")
     ap.add_argument("--no-image", action="store_true")
+    ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--no-nmc", action="store_true")
     ap.add_argument("--only-fp8", action="store_true",
                     help="run the FP8-form leg alone (rank 0) and print its JSON")
     ap.add_argument("--fp8-forms", default="fp8,bf16,f32,f64",
@@ -400,6 +402,126 @@ def image_leg(iters=500):
     return out
 
 
+SPARSE_WORKLOAD = ("document-term matrix 804414 x 47236 (Reuters-sized), 99.84 % sparse, "
+                   "lognormal document lengths, Zipf term frequencies, tf-idf unit rows; r = 40")
+
+
+def sparse_leg(iters=100, r=40, reps=10):
+    """The sparse form (X as compressed rows) on the Reuters-sized matrix.
+
+    X V and X^T U are timed with CUDA events around enmf_sweep (one product
+    per call, `reps` calls each after a warm one).  Their compulsory bytes:
+    the stored entries (4-byte index + 4-byte value each), the row or column
+    pointers, the factor read once and the product written once; the factor
+    rows gathered per entry come from L2 (V: 7.6 MB) or mostly from L2 (U:
+    129 MB) and are not counted.  Then one solve (SVD start, rotation,
+    `iters` alternations) in the FP32 and FP64 forms and the FP32 form's
+    final relative-error gap to the FP64 one."""
+    import torch
+
+    import synth
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+
+    m, n = 804414, 47236
+    rp, c, v = synth.sparse_docs(m, n, 0.0016, seed=0, dtype=np.float32)
+    nnz = int(rp[-1])
+    hbm = peaks().get("hbm_gbs", 6800.0)
+    out = {"workload": SPARSE_WORKLOAD, "m": m, "n": n, "r": r, "nnz": nnz,
+           "density": nnz / (m * n), "iterations": iters}
+    rp_d = torch.as_tensor(rp, device="cuda")
+    c_d = torch.as_tensor(c, device="cuda")
+    for form, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        Xs = B.CsrMatrix(rp_d, c_d, torch.as_tensor(v, dtype=dt, device="cuda"), (m, n))
+        s = Solver(Xs, r)
+        t0 = time.perf_counter()
+        s.svd_init()
+        s.rotate()
+        s.iterate(iters, trace=False, reset=1, sync_info=0)
+        f, rel, _ = s.residual(direct=True)
+        torch.cuda.synchronize()
+        res = {"ms_per_solve": 1e3 * (time.perf_counter() - t0), "rel_err": rel,
+               "note": "first solve of the context: includes the structure check and the transpose"}
+        if form == "f32":
+            g = torch.Generator(device="cuda").manual_seed(1)
+            U = torch.rand(m, r, generator=g, device="cuda")
+            V = torch.rand(n, r, generator=g, device="cuda")
+            XV = torch.empty(m, r, device="cuda")
+            XtU = torch.empty(n, r, device="cuda")
+            st = torch.cuda.current_stream()
+            for name, args_, byt in (
+                    ("xv", (U, V, XV, None), nnz * 8 + (m + 1) * 8 + n * r * 4 + m * r * 4),
+                    ("xtu", (U, V, None, XtU), nnz * 8 + (n + 1) * 8 + m * r * 4 + n * r * 4)):
+                B.enmf_sweep(s.ctx, Xs, *args_, exact=1)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(reps):
+                    B.enmf_sweep(s.ctx, Xs, *args_, exact=1)
+                e1.record(st)
+                torch.cuda.synchronize()
+                us = 1e3 * e0.elapsed_time(e1) / reps
+                gbs = byt / (us * 1e-6) / 1e9
+                res[name] = {"us": us, "compulsory_bytes": byt, "achieved_gbs": gbs,
+                             "frac_of_measured_hbm": gbs / hbm}
+        out[form] = res
+        s.close()
+        del Xs
+    out["f32"]["rel_err_gap_vs_f64"] = abs(out["f32"]["rel_err"] - out["f64"]["rel_err"]) / \
+        out["f64"]["rel_err"]
+    return out
+
+
+NMC_WORKLOAD = ("rating matrix 6040 x 3706 (MovieLens-1M-sized), 4.5 % known, power-law "
+                "user activity and item popularity, ratings 1..5; r = 25")
+
+
+def nmc_leg(rounds=100, r=25):
+    """Matrix completion (App. C, Algorithm eNMC) on the MovieLens-sized rating
+    matrix: the masked-ALS start, the rotation and `rounds` rounds of shift +
+    masked PBCD, in the FP32 and FP64 forms (CUDA events around each phase),
+    with the relative error over the known entries and the FP32 form's gap to
+    the FP64 one."""
+    import torch
+
+    import synth
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+
+    m, n = 6040, 3706
+    rp, c, v = synth.ratings(m, n, 0.045, seed=0, dtype=np.float32)
+    out = {"workload": NMC_WORKLOAD, "m": m, "n": n, "r": r, "known": int(rp[-1]),
+           "rounds": rounds}
+    rp_d = torch.as_tensor(rp, device="cuda")
+    c_d = torch.as_tensor(c, device="cuda")
+    for form, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        Xs = B.CsrMatrix(rp_d, c_d, torch.as_tensor(v, dtype=dt, device="cuda"), (m, n))
+        s = Solver(Xs, r)
+        s.nmc_objective()          # binds the pattern (check + transpose) outside the timing
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        st = torch.cuda.current_stream()
+        ev[0].record(st)
+        info = s.nmc_start()
+        ev[1].record(st)
+        s.rotate()
+        ev[2].record(st)
+        s.nmc_iterate(rounds, trace=False, reset=1, sync_info=0)
+        ev[3].record(st)
+        f, rel = s.nmc_objective()
+        torch.cuda.synchronize()
+        out[form] = {"start_ms": ev[0].elapsed_time(ev[1]), "als_sweeps": info.sweeps,
+                     "rotate_ms": ev[1].elapsed_time(ev[2]),
+                     "rounds_ms": ev[2].elapsed_time(ev[3]),
+                     "ms_per_round": ev[2].elapsed_time(ev[3]) / max(rounds, 1),
+                     "f": f, "rel_err_known": rel}
+        s.close()
+        del Xs
+    out["f32"]["rel_err_gap_vs_f64"] = abs(out["f32"]["rel_err_known"] -
+                                           out["f64"]["rel_err_known"]) / out["f64"]["rel_err_known"]
+    return out
+
+
 def serving_leg(n_req, n_open, n_cmp=16):
     """Serving + batching workload: a Poisson stream of NMF requests with m, n
     log-uniform in [64, 4096] and r uniform in {4, 8, 16, 32, 64}, planted
@@ -705,6 +827,12 @@ def run_ours(args):
     image = None
     if world == 1 and not args.no_image:
         image = image_leg()
+    sparse = None
+    if world == 1 and not args.no_sparse:
+        sparse = sparse_leg()
+    nmc = None
+    if world == 1 and not args.no_nmc:
+        nmc = nmc_leg()
 
     ttt = None
     if "f64" in others or form == "f64":
@@ -729,7 +857,7 @@ def run_ours(args):
             "p50_ms": statistics.median(step_ms), "p99_ms": p99,
             "time_to_target": ttt, "final": {"rel_err": rel, "kkt_pg_rel": kk.pg_rel},
             "other_forms": others, "fused_single_pass": fused, "roofline": roof, "cpu_baseline": cb,
-            "e2e": e2e, "image_stack": image,
+            "e2e": e2e, "image_stack": image, "sparse_form": sparse, "completion": nmc,
             "clocks": clk, "gpu_launches": launches, "serving": serving, "fp8_form": fp8}
     print(json.dumps(line))
     if world > 1:

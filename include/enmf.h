@@ -67,7 +67,31 @@ typedef enum {
  *   FP8:         X F32 staged to E4M3 codes with per-tile scales, factors
  *                F32, tensor cores as for BF16. */
 typedef enum { ENMF_F64 = 0, ENMF_F32 = 1, ENMF_BF16 = 2, ENMF_F16 = 3,
-               ENMF_E4M3 = 4 /* stream type only: OCP FP8 E4M3 codes */ } enmf_dtype;
+               ENMF_E4M3 = 4 /* stream type only: OCP FP8 E4M3 codes */,
+               ENMF_CSR = 5  /* x_dtype only: X as compressed rows (enmf_csr) */ } enmf_dtype;
+
+/* The sparse form (x_dtype = ENMF_CSR; the Reuters experiment of Sec. 5): X is
+ * given by its stored entries.  Every call that takes X then takes a HOST
+ * pointer to an enmf_csr whose three arrays are DEVICE memory of the caller:
+ *   row_ptr  m + 1 entries, row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz;
+ *   col      nnz column indices, strictly increasing within each row
+ *            (row i's entries at row_ptr[i] .. row_ptr[i+1] - 1);
+ *   val      nnz values, finite and >= 0, of the factors' type (FP64 with
+ *            f_dtype = ENMF_F64, FP32 with ENMF_F32).
+ * Entries not stored are zeros of X (this is not matrix completion).  The
+ * first call with a new descriptor (new array pointers) checks it on the
+ * device -- ENMF_EINVAL at that call for a malformed structure, ENMF_EDOMAIN
+ * for a negative or non-finite value -- and builds the context's transpose
+ * (compressed columns, each column's entries in row order); later calls with
+ * the same pointers reuse it, so the arrays' contents must not change between
+ * calls.  X V and X^T U then read the stored entries once each; the rest of
+ * the method is unchanged.  Not available: the tensor-core forms, batches,
+ * enmf_solve with host buffers, enmf_stage_x. */
+typedef struct {
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const void* val;
+} enmf_csr;
 
 /* Largest supported rank (the SVD start works on r + oversample <= 80). */
 #define ENMF_MAX_RANK 64
@@ -94,6 +118,8 @@ typedef struct {
                     /*   codes with a power-of-two scale per 128 x 128 tile   */
                     /*   and X_lo = bf16(X - X_hi) (see enmf_stage_x); X must */
                     /*   stay <= 448 * 2^100; m <= 65535 * 128.               */
+  int64_t nnz;      /* ENMF_CSR: stored entries (0 <= nnz <= m n; m, n and    */
+                    /*   nnz below 2^31); ldx is then ignored.  Else unused.  */
 } enmf_problem;
 
 typedef struct enmf_ctx enmf_ctx;
@@ -151,6 +177,10 @@ typedef struct {
   double rho_scale;     /* default 3                                       */
   int32_t max_iter;     /* default 200                                     */
   double tol;           /* default 1e-12                                   */
+  int32_t f64;          /* FP32 factors: 1 = run the ADMM in FP64 (rows    */
+                        /*   and r x r update) on FP64 copies of U*, V*,   */
+                        /*   the rotated factors rounded to FP32 once; 0   */
+                        /*   (default) = the FP32 persistent kernel        */
 } enmf_admm_opts;
 typedef struct {
   int32_t steps;
@@ -407,6 +437,60 @@ enmf_status enmf_equiv_transform(enmf_ctx* ctx, const void* Ue, const void* Ve, 
                                  double* delta2);
 enmf_status enmf_perm_check(enmf_ctx* ctx, const void* UA, const void* UB, double eps,
                             double keep_frac, int32_t* b_of_a, int32_t* kept);
+
+/* ---- Matrix completion (App. C, Algorithm eNMC) ---------------------------
+ * For a context of the sparse form (x_dtype = ENMF_CSR, X an enmf_csr): here
+ * the stored entries are the KNOWN entries of X (the mask M_E) and the others
+ * are unknown, not zeros.  The objective is
+ *     f^(U, V) = 1/2 ||M_E o (X - U V^T)||_F^2.
+ * Algorithm eNMC is enmf_nmc_start, enmf_rotate (Algorithm 1 unchanged), then
+ * enmf_nmc_iterate.  Other forms: ENMF_ESTATE.
+ *
+ * enmf_nmc_start: the unconstrained start (App. C computes a local minimum of
+ * f^ with softImpute-ALS): from the balanced truncated SVD of the zero-filled
+ * X (enmf_svd_init), sweeps of exact row least squares with softImpute's
+ * ridge, every row of U then every row of V,
+ *     u_i = (G_i + lam c_i I)^-1 a_i,  G_i = sum over known (i, j) of v_j v_j^T,
+ *     a_i = sum over known (i, j) of x_ij v_j,  c_i = trace(G_i) / r (1 if 0),
+ * G_i and a_i formed and solved (Cholesky) in FP64 in every form, until f^
+ * changes by <= tol (relative) over a sweep or after max_sweeps sweeps.  The
+ * ridge makes the rows with fewer known entries than r well posed (their G_i
+ * is singular).  Overwrites U, V.  info (may be NULL): sweeps run and the
+ * final f^.  ENMF_ENOTCONV when a row's matrix was not positive definite in
+ * FP64 (lam = 0 and a row with fewer than r known entries).
+ *
+ * enmf_nmc_iterate: opts->n_iter rounds of Algorithm eNMC: shift U's negative
+ * entries (Eq. 8, step fixed when the state is reset, as in enmf_iterate),
+ * mask M+ = [U >= 0], PBCD on U's rows with M_E (Algorithm 2):
+ *     g_i = M+ o (u_i G_i - a_i),  d_i = ||g_i||^2 / (g_i G_i g_i^T)
+ * -- the exact minimiser of f^ along -g_i, Eq. 10 when every entry is known --
+ * u_i <- max(0, u_i - d_i g_i) on the mask, stopping when ||g|| < eps
+ * ||g_init|| (all rows) or after pbcd_max_iter sweeps; then the same for V
+ * with M_E^T.  G_i and a_i are formed once per half from the stored entries.
+ * opts->trace (device FP64, n_iter, may be NULL) receives f^ after every
+ * round; reset = 1 restarts (new shift steps from the current U, V).  The
+ * work buffers (max(m, n) r_pad^2 + max(m, n) r_pad elements, r_pad = r
+ * rounded up to 16, 32, 48 or 64) come from the stream-ordered allocator.
+ * info: iters = asc_iters = rounds since the reset, s_u, s_v.
+ *
+ * enmf_nmc_objective: out2[0] = f^, out2[1] = ||M_E o (X - U V^T)||_F /
+ * ||M_E o X||_F (host, 2 doubles).  Synchronises. */
+typedef struct {
+  int32_t max_sweeps;   /* default 50                                      */
+  double lam;           /* default 1e-3                                    */
+  double tol;           /* default 1e-10                                   */
+  int32_t svd_max_iters;/* the SVD start's max_iters; 0 = its default      */
+} enmf_nmc_start_opts;
+typedef struct {
+  int32_t sweeps;
+  double f;
+} enmf_nmc_start_info;
+enmf_status enmf_nmc_start(enmf_ctx* ctx, const void* X, void* U, void* V,
+                           const enmf_nmc_start_opts* opts, enmf_nmc_start_info* info);
+enmf_status enmf_nmc_iterate(enmf_ctx* ctx, const void* X, void* U, void* V,
+                             const enmf_iter_opts* opts, enmf_iter_info* info);
+enmf_status enmf_nmc_objective(enmf_ctx* ctx, const void* X, const void* U, const void* V,
+                               double* out2);
 
 /* ---- The fused single-pass alternation (no counterpart in the paper) -----
  * In the HALS stage of the BF16 / FP16 tensor-core forms (rank padded to 32

@@ -758,15 +758,18 @@ def pbcd_masked(X, M, U, V, mask, eps=PBCD_EPS, max_iter=PBCD_MAX_ITER):
     return U, info
 
 
-def masked_als(X, M, r, sweeps=50, lam=1e-9, tol=1e-10):
-    """Unconstrained start of Algorithm eNMC: a local minimum of f^ over all
-    U, V (App. C computes it with softImpute-ALS).  Reading: softImpute-ALS at
-    a vanishing ridge -- alternating exact row least squares
+def masked_als(X, M, r, sweeps=50, lam=1e-3, tol=1e-10):
+    """Unconstrained start of Algorithm eNMC: App. C computes a local minimum
+    of f^ over all U, V with softImpute-ALS.  Reading: alternating exact
+    row least squares with softImpute's ridge,
         u_i = (sum_j M_E[i, j] v_j v_j^T + lam c I)^-1 sum_j M_E[i, j] x_ij v_j
-    (c = mean of the Gram's diagonal, lam = 1e-9: a guard for rows with fewer
-    than r known entries), then the same for V, from the balanced truncated
-    SVD of the zero-filled X; stop when f^ changes by <= tol relative or after
-    `sweeps` sweeps.  Returns (U, V, sweeps_run)."""
+    (c = mean of the Gram's diagonal, 1 when it is 0; lam = 1e-3, the paper
+    states no value), then the same for V, from the balanced truncated SVD of
+    the zero-filled X; stop when f^ changes by <= tol relative or after
+    `sweeps` sweeps.  A row with fewer known entries than r has a singular
+    Gram, and without a ridge of this size its solution is fixed only by
+    rounding (a 1e-13 change of the start moves U V^T by up to 36 % after 20
+    sweeps at lam = 1e-9, by 1e-10 at lam = 1e-3).  Returns (U, V, sweeps_run)."""
     Xz = M * X
     U, V, _ = truncated_svd(Xz, r)
     f_old = objective_masked(X, M, U, V)
@@ -811,6 +814,16 @@ def enmc(X, M, r, n_iter, eps=PBCD_EPS, pbcd_max_iter=PBCD_MAX_ITER, n_shift=N_S
     M = np.asarray(M, dtype=np.float64)
     U0, V0, sw = masked_als(X, M, r, sweeps=als_sweeps)
     U, V, _, _ = rotate(U0, V0)
+    U, V, trace = enmc_rounds(X, M, U, V, n_iter, eps, pbcd_max_iter, n_shift)
+    return EnmcResult(U, V, trace, sw)
+
+
+def enmc_rounds(X, M, U, V, n_iter, eps=PBCD_EPS, pbcd_max_iter=PBCD_MAX_ITER, n_shift=N_SHIFT):
+    """The loop of Algorithm eNMC from (U, V): the shift steps fixed from the
+    given factors (reading R5), then n_iter rounds of shift, mask and masked
+    PBCD on U, then on V.  Returns (U, V, trace of f^ after every round)."""
+    U = np.array(U, dtype=np.float64)
+    V = np.array(V, dtype=np.float64)
     su = shift_step(U, n_shift) if np.any(U < 0) else 0.0
     sv = shift_step(V, n_shift) if np.any(V < 0) else 0.0
     trace = []
@@ -820,4 +833,4 @@ def enmc(X, M, r, n_iter, eps=PBCD_EPS, pbcd_max_iter=PBCD_MAX_ITER, n_shift=N_S
         V = shift_negative(V, sv)
         V, _ = pbcd_masked(X.T, M.T, V, U, (V >= 0).astype(np.float64), eps, pbcd_max_iter)
         trace.append(objective_masked(X, M, U, V))
-    return EnmcResult(U, V, trace, sw)
+    return U, V, trace

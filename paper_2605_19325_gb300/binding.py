@@ -13,7 +13,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libenmf.so")
 
-ENMF_F64, ENMF_F32, ENMF_BF16, ENMF_F16, ENMF_E4M3 = 0, 1, 2, 3, 4
+ENMF_F64, ENMF_F32, ENMF_BF16, ENMF_F16, ENMF_E4M3, ENMF_CSR = 0, 1, 2, 3, 4, 5
 ENMF_MAX_RANK = 64
 ENMF_RESIDUAL_NOALLOC_MAX_ROWS = 262144
 ENMF_STATE_BYTES = 128
@@ -30,7 +30,46 @@ class EnmfError(RuntimeError):
 
 class enmf_problem(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("ldx", C.c_int64), ("r", C.c_int32),
-                ("x_dtype", C.c_int32), ("f_dtype", C.c_int32), ("stream_dtype", C.c_int32)]
+                ("x_dtype", C.c_int32), ("f_dtype", C.c_int32), ("stream_dtype", C.c_int32),
+                ("nnz", C.c_int64)]
+
+
+class enmf_csr(C.Structure):
+    _fields_ = [("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class CsrMatrix:
+    """X of the sparse form (x_dtype ENMF_CSR): compressed rows in CUDA
+    tensors -- row_ptr int64 (m + 1), col int32 (nnz), val float32 or float64
+    (nnz, the factors' type) -- with shape (m, n).  Wherever the C ABI takes X
+    it gets the address of this object's enmf_csr descriptor (data_ptr()).
+    Only shapes, types, devices and contiguity are checked here; the entries
+    themselves are checked by the library on the device."""
+
+    def __init__(self, row_ptr, col, val, shape):
+        m, n = int(shape[0]), int(shape[1])
+        for name, t, dt in (("row_ptr", row_ptr, "torch.int64"), ("col", col, "torch.int32")):
+            if not t.is_cuda or not t.is_contiguous() or t.dim() != 1 or str(t.dtype) != dt:
+                raise ValueError(f"{name} must be a contiguous 1-D CUDA {dt} tensor")
+        if str(val.dtype) not in ("torch.float32", "torch.float64"):
+            raise ValueError("val must be float32 or float64")
+        if not val.is_cuda or not val.is_contiguous() or val.dim() != 1:
+            raise ValueError("val must be a contiguous 1-D CUDA tensor")
+        if row_ptr.numel() != m + 1 or col.numel() != val.numel():
+            raise ValueError("row_ptr must have m + 1 entries and col, val nnz entries each")
+        if not (row_ptr.device == col.device == val.device):
+            raise ValueError("row_ptr, col and val must be on one device")
+        self.row_ptr, self.col, self.val = row_ptr, col, val
+        self.shape = (m, n)
+        self.nnz = int(val.numel())
+        self.dtype = val.dtype
+        self.device = val.device
+        self.is_cuda = True
+        self.desc = enmf_csr(row_ptr.data_ptr(), col.data_ptr() if self.nnz else None,
+                             val.data_ptr() if self.nnz else None)
+
+    def data_ptr(self):
+        return C.addressof(self.desc)
 
 
 class enmf_svd_opts(C.Structure):
@@ -44,7 +83,7 @@ class enmf_svd_info(C.Structure):
 
 class enmf_admm_opts(C.Structure):
     _fields_ = [("rho", C.c_double), ("rho_scale", C.c_double), ("max_iter", C.c_int32),
-                ("tol", C.c_double)]
+                ("tol", C.c_double), ("f64", C.c_int32)]
 
 
 class enmf_rotate_info(C.Structure):
@@ -68,7 +107,22 @@ class enmf_kkt_report(C.Structure):
                 ("sigma", C.c_double), ("pg_norm", C.c_double), ("pg_rel", C.c_double)]
 
 
+class enmf_nmc_start_opts(C.Structure):
+    _fields_ = [("max_sweeps", C.c_int32), ("lam", C.c_double), ("tol", C.c_double),
+                ("svd_max_iters", C.c_int32)]
+
+
+class enmf_nmc_start_info(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("f", C.c_double)]
+
+
 _SIGS = {
+    "enmf_nmc_start": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.POINTER(enmf_nmc_start_opts), C.POINTER(enmf_nmc_start_info)]),
+    "enmf_nmc_iterate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.POINTER(enmf_iter_opts), C.POINTER(enmf_iter_info)]),
+    "enmf_nmc_objective": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.POINTER(C.c_double)]),
     "enmf_workspace_size": (C.c_int, [C.POINTER(enmf_problem), C.POINTER(C.c_size_t)]),
     "enmf_create": (C.c_int, [C.POINTER(enmf_problem), C.c_void_p, C.POINTER(C.c_void_p)]),
     "enmf_destroy": (None, [C.c_void_p]),
@@ -242,6 +296,31 @@ def enmf_iterate(ctx, X, U, V, n_iter, trace=None, reset=0, eps=1e-4, pbcd_max_i
     check(lib().enmf_iterate(ctx, _ptr(X), _ptr(U), _ptr(V), C.byref(o),
                              C.byref(info) if sync_info else None), "enmf_iterate")
     return info
+
+
+def enmf_nmc_start(ctx, X, U, V, max_sweeps=50, lam=1e-3, tol=1e-10, svd_max_iters=0):
+    o = enmf_nmc_start_opts(max_sweeps, lam, tol, svd_max_iters)
+    info = enmf_nmc_start_info()
+    code = lib().enmf_nmc_start(ctx, _ptr(X), _ptr(U), _ptr(V), C.byref(o), C.byref(info))
+    if code not in (0, 6):
+        check(code, "enmf_nmc_start")
+    return info
+
+
+def enmf_nmc_iterate(ctx, X, U, V, n_iter, trace=None, reset=0, eps=1e-4, pbcd_max_iter=5,
+                     n_shift=3, sync_info=1):
+    o = enmf_iter_opts(n_iter, pbcd_max_iter, eps, n_shift,
+                       None if trace is None else trace.data_ptr(), reset, sync_info, 10)
+    info = enmf_iter_info()
+    check(lib().enmf_nmc_iterate(ctx, _ptr(X), _ptr(U), _ptr(V), C.byref(o),
+                                 C.byref(info) if sync_info else None), "enmf_nmc_iterate")
+    return info
+
+
+def enmf_nmc_objective(ctx, X, U, V):
+    out = (C.c_double * 2)()
+    check(lib().enmf_nmc_objective(ctx, _ptr(X), _ptr(U), _ptr(V), out), "enmf_nmc_objective")
+    return out[0], out[1]
 
 
 def enmf_pbcd_counts(ctx, cap=8192):
@@ -433,6 +512,8 @@ def _noalloc_args(X, U, V, out3):
     transposed or strided factor, or a short or mistyped out3 would become an
     out-of-bounds device access.  Every such case raises ValueError here,
     before the library is called.  Returns (m, n, ldx, r)."""
+    if isinstance(X, CsrMatrix):
+        raise ValueError("enmf_residual_noalloc takes a dense X")
     if X.dim() != 2:
         raise ValueError("X must be a matrix")
     m, n = X.shape

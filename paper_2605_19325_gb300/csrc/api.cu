@@ -49,8 +49,17 @@ static bool tc_form(const enmf_problem* p) {
 
 static bool valid_problem(const enmf_problem* p) {
   if (!p) return false;
-  if (p->m < 1 || p->n < 1 || p->ldx < p->n) return false;
+  if (p->m < 1 || p->n < 1) return false;
   if (p->r < 1 || p->r > ENMF_MAX_RANK || p->r > p->m || p->r > p->n) return false;
+  if (p->x_dtype == ENMF_CSR) {
+    // compressed rows: int32 column and row indices, FP32 or FP64 values
+    if (p->stream_dtype != 0 && p->stream_dtype != ENMF_CSR) return false;
+    if (p->m >= 0x7fffffffLL || p->n >= 0x7fffffffLL) return false;
+    if (p->nnz < 0 || p->nnz >= 0x7fffffffLL || (double)p->nnz > (double)p->m * (double)p->n)
+      return false;
+    return p->f_dtype == ENMF_F64 || p->f_dtype == ENMF_F32;
+  }
+  if (p->ldx < p->n) return false;
   if (p->x_dtype < ENMF_F64 || p->x_dtype > ENMF_F16) return false;
   if (tc_form(p)) {
     if (p->f_dtype != ENMF_F32) return false;
@@ -149,6 +158,8 @@ static size_t plan(const enmf_problem* p, int num_sms, size_t* splitk_out) {
   t += al256(4096 * 8) + al256(2 * 4096 * 8);
   t += 9 * al256((size_t)LMAX * LMAX * 8) + 2 * al256((size_t)LMAX * RMAX * 8);
   t += 2 * al256((size_t)LMAX * RMAX * 8) + 3 * al256(LMAX * 8) + al256(64 * 8);
+  if (p->x_dtype == ENMF_CSR)   // the transpose: column pointers, row indices, values
+    t += al256((nn + 1) * 8) + al256((size_t)p->nnz * 4) + al256((size_t)p->nnz * fs);
   return t;
 }
 
@@ -183,6 +194,8 @@ static enmf_status check_launch(enmf_ctx* ctx) {
 }
 
 // Synchronise and translate the device status word.
+static enmf_status bind_x(enmf_ctx* ctx, const void* X, const void** xin);
+
 static enmf_status sync_status(enmf_ctx* ctx, bool clear_notconv = true) {
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
@@ -199,9 +212,10 @@ static enmf_status sync_status(enmf_ctx* ctx, bool clear_notconv = true) {
     ctx->poison = ENMF_ETIMEOUT;
     return ENMF_ETIMEOUT;
   }
-  if (err & (ERR_DOMAIN | ERR_NOTCONV | ERR_NONFINITE)) {
+  if (err & (ERR_DOMAIN | ERR_NOTCONV | ERR_NONFINITE | ERR_FORMAT)) {
     int keep = 0;
     cudaMemcpy(ctx->err, &keep, sizeof(int), cudaMemcpyHostToDevice);
+    if (err & ERR_FORMAT) return ENMF_EINVAL;
     if (err & ERR_DOMAIN) return ENMF_EDOMAIN;
     if ((err & ERR_NOTCONV) && clear_notconv) return ENMF_ENOTCONV;
   }
@@ -263,6 +277,11 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
   ctx->csQ = (double*)take(LMAX * 8);
   ctx->csQ2 = (double*)take(LMAX * 8);
   ctx->scal = (double*)take(64 * 8);
+  if (p->x_dtype == ENMF_CSR) {
+    ctx->csc_ptr = (int64_t*)take((nn + 1) * 8);
+    ctx->csc_row = (int32_t*)take((size_t)p->nnz * 4);
+    ctx->csc_val = take((size_t)p->nnz * fs);
+  }
   if ((size_t)(b - (char*)ctx->ws) > ctx->ws_bytes) {
     cudaFreeAsync(ctx->ws, ctx->stream);
     delete ctx;
@@ -462,6 +481,12 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
                                      enmf_svd_info* info) {
   GUARD(ctx);
   if (!X || !U || !V) return ENMF_EINVAL;
+  {
+    const void* xb = nullptr;
+    const enmf_status brc = bind_x(ctx, X, &xb);
+    if (brc) return brc;
+    X = xb;
+  }
   enmf_svd_opts o = {10, 40, ctx->fdt == T_F64 ? 1e-12 : 1e-5, 0x5eedull};
   if (opts) {
     o = *opts;
@@ -565,7 +590,7 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
                                    const enmf_admm_opts* opts, enmf_rotate_info* info) {
   GUARD(ctx);
   if (!U || !V) return ENMF_EINVAL;
-  enmf_admm_opts o = {0.0, 3.0, 200, 1e-12};
+  enmf_admm_opts o = {0.0, 3.0, 200, 1e-12, 0};
   if (opts) {
     o = *opts;
     if (o.max_iter < 1 || !(o.tol >= 0) || (o.rho <= 0 && !(o.rho_scale > 0))) return ENMF_EINVAL;
@@ -574,25 +599,50 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
   const int k = p.r, fdt = ctx->fdt;
   const int64_t m = p.m, n = p.n;
   cudaStream_t s = ctx->stream;
+  // the working factors: the caller's, or (FP32 factors, o.f64) FP64 copies
+  // with FP64 Z and Y, from the stream-ordered allocator for this call
+  void* Uw = U;
+  void* Vw = V;
+  void* Zw = ctx->Zb;
+  void* Yw = ctx->Yb;
+  int wdt = fdt;
+  void* tmp = nullptr;
+  if (fdt == T_F32 && o.f64) {
+    const size_t wb = (size_t)(m + n) * k * 8;
+    if (cudaMallocAsync(&tmp, 3 * wb, s) != cudaSuccess) {
+      cudaGetLastError();
+      return ENMF_ENOMEM;
+    }
+    Uw = tmp;
+    Vw = (char*)tmp + (size_t)m * k * 8;
+    Zw = (char*)tmp + wb;
+    Yw = (char*)tmp + 2 * wb;
+    wdt = T_F64;
+    launch_cast(U, T_F32, Uw, T_F64, m * k, s);
+    launch_cast(V, T_F32, Vw, T_F64, n * k, s);
+  }
   // negative mass before and ||W||_F^2 for rho
-  launch_negmass(U, m, k, fdt, ctx->part, &ctx->scal[1], 0, s);
-  launch_negmass(V, n, k, fdt, ctx->part, &ctx->scal[1], 1, s);
-  launch_dot(U, k, U, k, k, m, fdt, ctx->part, &ctx->scal[2], s);
-  launch_dot(V, k, V, k, k, n, fdt, ctx->part, &ctx->scal[3], s);
+  launch_negmass(Uw, m, k, wdt, ctx->part, &ctx->scal[1], 0, s);
+  launch_negmass(Vw, n, k, wdt, ctx->part, &ctx->scal[1], 1, s);
+  launch_dot(Uw, k, Uw, k, k, m, wdt, ctx->part, &ctx->scal[2], s);
+  launch_dot(Vw, k, Vw, k, k, n, wdt, ctx->part, &ctx->scal[3], s);
   double hs[4];
   CK(cudaMemcpyAsync(hs, ctx->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   enmf_status rc = sync_status(ctx);
-  if (rc) return rc;
+  if (rc) {
+    if (tmp) cudaFreeAsync(tmp, s);
+    return rc;
+  }
   double rho = o.rho;
   if (!(rho > 0)) {
     double rms = sqrt((hs[2] + hs[3]) / ((double)(m + n) * k));
     rho = rms > 0 ? o.rho_scale / rms : 1.0;
   }
-  CK(cudaMemsetAsync(ctx->Yb, 0, (size_t)(m + n) * k * type_size(fdt), s));
+  CK(cudaMemsetAsync(Yw, 0, (size_t)(m + n) * k * type_size(wdt), s));
   rot_start_kernel<<<1, 256, 0, s>>>(ctx->R, ctx->T2, k, ctx->st);
   note_launch(1);
   const int check_every = 16;
-  if (fdt == T_F32) {
+  if (wdt == T_F32) {
     // every ADMM step in one persistent kernel (admm.cu)
     launch_admm_f32((const float*)U, (const float*)V, m, n, k, ctx->R, (float*)ctx->Zb,
                     (float*)ctx->Yb, rho, o.max_iter, o.tol, ctx->st, ctx->part, ctx->Msm,
@@ -600,22 +650,34 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
   }
   // FP64 factors: one ADMM pass, the fixed-order sum of M = W^T B and the
   // warm-started FP64 Jacobi polar factor per step
-  for (int it = 0; fdt == T_F64 && it < o.max_iter; ++it) {
-    launch_admm_pass(U, V, m, n, k, fdt, ctx->R, ctx->Zb, ctx->Yb, rho, it == 0, ctx->st,
+  for (int it = 0; wdt == T_F64 && it < o.max_iter; ++it) {
+    launch_admm_pass(Uw, Vw, m, n, k, wdt, ctx->R, Zw, Yw, rho, it == 0, ctx->st,
                      ctx->part, s);
     launch_part_reduce(ctx->part, k * k, ctx->Msm, s);
     launch_polar(ctx->Msm, k, ctx->R, ctx->T2, o.tol, ctx->st, ctx->err, s);
     if ((it + 1) % check_every == 0 && it + 1 < o.max_iter) {
       rc = check_launch(ctx);
-      if (rc) return rc;
       int done = 0;
-      CK(cudaMemcpyAsync(&done, &ctx->st->admm_done, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      if (!rc && (cudaMemcpyAsync(&done, &ctx->st->admm_done, sizeof(int), cudaMemcpyDeviceToHost,
+                                  s) != cudaSuccess ||
+                  cudaStreamSynchronize(s) != cudaSuccess)) {
+        ctx->poison = ENMF_ECUDA;
+        rc = ENMF_ECUDA;
+      }
+      if (rc) {
+        if (tmp) cudaFreeAsync(tmp, s);
+        return rc;
+      }
       if (done) break;
     }
   }
-  launch_apply_square(U, m, k, fdt, ctx->R, s);
-  launch_apply_square(V, n, k, fdt, ctx->R, s);
+  launch_apply_square(Uw, m, k, wdt, ctx->R, s);
+  launch_apply_square(Vw, n, k, wdt, ctx->R, s);
+  if (tmp) {   // U* R, V* R formed in FP64, rounded to FP32 once
+    launch_cast(Uw, T_F64, U, T_F32, m * k, s);
+    launch_cast(Vw, T_F64, V, T_F32, n * k, s);
+    cudaFreeAsync(tmp, s);
+  }
   launch_negmass(U, m, k, fdt, ctx->part, &ctx->scal[4], 0, s);
   launch_negmass(V, n, k, fdt, ctx->part, &ctx->scal[4], 1, s);
   if (Rout) CK(cudaMemcpyAsync(Rout, ctx->R, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -817,6 +879,62 @@ static enmf_status check_staged(enmf_ctx* ctx, const void* X) {
   return ENMF_OK;
 }
 
+// The X the launchers see.  Dense forms: X itself.  The sparse form: X is the
+// caller's host enmf_csr; a descriptor with new array pointers is checked on
+// the device and the context's transpose is built (the work buffer comes from
+// the stream-ordered allocator); the launchers then get &ctx->sx.
+static enmf_status bind_x(enmf_ctx* ctx, const void* X, const void** xin) {
+  *xin = X;
+  if (ctx->xdt != T_CSR) return ENMF_OK;
+  const enmf_csr* d = (const enmf_csr*)X;
+  const enmf_problem& p = ctx->p;
+  if (!d->row_ptr || (p.nnz > 0 && (!d->col || !d->val))) return ENMF_EINVAL;
+  if (ctx->sx_bound && ctx->sx.row_ptr == d->row_ptr && ctx->sx.col == d->col &&
+      ctx->sx.val == d->val) {
+    *xin = &ctx->sx;
+    return ENMF_OK;
+  }
+  ctx->sx_bound = false;
+  // graphs captured with the previous descriptor's arrays are stale
+  for (int g = 0; g < 2; ++g)
+    if (ctx->iter_graph[g]) {
+      cudaGraphExecDestroy(ctx->iter_graph[g]);
+      ctx->iter_graph[g] = nullptr;
+    }
+  CsrX& x = ctx->sx;
+  x.row_ptr = d->row_ptr;
+  x.col = d->col;
+  x.val = d->val;
+  x.col_ptr = ctx->csc_ptr;
+  x.row_t = ctx->csc_row;
+  x.val_t = ctx->csc_val;
+  x.m = p.m;
+  x.n = p.n;
+  x.nnz = p.nnz;
+  x.vdt = ctx->fdt;
+  cudaStream_t s = ctx->stream;
+  launch_csr_check(x, ctx->err, s);
+  enmf_status rc = check_launch(ctx);
+  if (rc) return rc;
+  rc = sync_status(ctx);
+  if (rc) return rc;
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, csr_transpose_scratch(p.m, p.n, nullptr, nullptr), s) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return ENMF_ENOMEM;
+  }
+  launch_csr_transpose(x, scratch, x.col_ptr, x.row_t, x.val_t, s);
+  cudaFreeAsync(scratch, s);
+  rc = check_launch(ctx);
+  if (rc) return rc;
+  rc = sync_status(ctx);
+  if (rc) return rc;
+  ctx->sx_bound = true;
+  *xin = &ctx->sx;
+  return ENMF_OK;
+}
+
 // ------------------------------------------------------- state checkpoint
 // Fixed host layout of the exported iteration state (ENMF_STATE_BYTES).
 struct StateBlob {
@@ -939,6 +1057,12 @@ extern "C" enmf_status enmf_sweep(enmf_ctx* ctx, const void* X, const void* U, c
                                   void* XV, void* XtU, int32_t exact) {
   GUARD(ctx);
   if (!X || (XV && !V) || (XtU && !U)) return ENMF_EINVAL;
+  {
+    const void* xb = nullptr;
+    const enmf_status brc = bind_x(ctx, X, &xb);
+    if (brc) return brc;
+    X = xb;
+  }
   enmf_status rc = check_staged(ctx, X);
   if (rc) return rc;
   if (XV) sweep_xv(ctx, X, V, XV, exact ? 2 : 0);
@@ -1046,6 +1170,12 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
                                     const enmf_iter_opts* opts, enmf_iter_info* info) {
   GUARD(ctx);
   if (!X || !U || !V) return ENMF_EINVAL;
+  {
+    const void* xb = nullptr;
+    const enmf_status brc = bind_x(ctx, X, &xb);
+    if (brc) return brc;
+    X = xb;
+  }
   enmf_iter_opts o = {0, 5, 1e-4, 3, nullptr, 0, 1, 10};
   if (opts) o = *opts;
   if (o.n_iter < 0 || o.pbcd_max_iter < 0 || !(o.eps >= 0) || o.n_shift < 1) return ENMF_EINVAL;
@@ -1066,10 +1196,19 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
   }
   // the alternations: everything on the device, nothing read back (except
   // the stage once, below)
+  // From a reset the ascent stage ends within n_shift alternations (the worst
+  // negative entry is nonnegative after n_shift shifts of max(-F) /
+  // (n_shift - 1/2)).  In the precision forms those alternations run with the
+  // X_lo term refreshed every time: the ascent stage decides which KKT point
+  // the descent reaches, and it is the phase most sensitive to the rounding of
+  // X (reading R28).
+  const int pre = fresh ? (o.n_iter < o.n_shift ? o.n_iter : o.n_shift) : 0;
+  const int exact_until = (ctx->tc && ctx->xl) ? pre : 0;
   auto general = [&](int it0, int it1) {
     for (int it = it0; it < it1; ++it) {
-      // precision form: refresh the X_lo terms every correct_every alternations
-      const int corr = (it % o.correct_every == 0) ? 2 : 1;
+      // precision form: refresh the X_lo terms every correct_every alternations,
+      // and in every alternation of a fresh ascent stage
+      const int corr = (it < exact_until || it % o.correct_every == 0) ? 2 : 1;
       const bool rec = ctx->prof_every > 0 && it % ctx->prof_every == 0 && corr == 1 &&
                        ctx->npev + 4 <= 2 * PROF_PAIRS;
       sweep_xv(ctx, X, V, ctx->M0, corr, rec, false, false);
@@ -1110,7 +1249,8 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
   auto run = [&](int slot, int it0, int it1) {
     if (it1 <= it0) return;
     enmf_ctx::IterKey key = {X, U, V, o.trace, it1 - it0, o.pbcd_max_iter, o.n_shift,
-                             o.correct_every, ctx->prof_every, o.eps, it0};
+                             o.correct_every, ctx->prof_every, o.eps, it0,
+                             it0 < exact_until ? exact_until : 0};
     auto body = [&]() {
       if (slot == 0) general(it0, it1);
       else fused(it0, it1);
@@ -1120,12 +1260,12 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
   const bool fz_ok = ctx->tc && ctx->fz_plan.ok && ctx->fz_enabled && ctx->fzws;
   if (fresh) ctx->hals_known = false;
   int it = 0;
+  if (exact_until > 0 && !(fz_ok && !ctx->hals_known)) {
+    run(0, 0, exact_until);
+    it = exact_until;
+  }
   if (fz_ok && !ctx->hals_known && o.n_iter > 0) {
-    // From a reset the ascent stage ends within n_shift alternations (the
-    // worst negative entry is nonnegative after n_shift shifts of
-    // max(-F) / (n_shift - 1/2)); run those with the two-pass sweeps, then
-    // read the stage once.
-    const int pre = fresh ? (o.n_iter < o.n_shift ? o.n_iter : o.n_shift) : 0;
+    // the ascent stage with the two-pass sweeps, then the stage read once
     run(0, 0, pre);
     rc = check_launch(ctx);
     if (rc) return rc;
@@ -1397,13 +1537,28 @@ extern "C" enmf_status enmf_residual(enmf_ctx* ctx, const void* X, const void* U
                                      double* out3, int32_t direct) {
   GUARD(ctx);
   if (!X || !U || !V || !out3) return ENMF_EINVAL;
+  {
+    const void* xb = nullptr;
+    const enmf_status brc = bind_x(ctx, X, &xb);
+    if (brc) return brc;
+    X = xb;
+  }
   const enmf_problem& p = ctx->p;
   const int k = p.r, fdt = ctx->fdt, xdt = ctx->xdt;
   const int64_t m = p.m, n = p.n;
   cudaStream_t s = ctx->stream;
   launch_normx2(X, xdt, m, n, p.ldx, ctx->part, &ctx->scal[8], ctx->err, s);
-  if (direct) {
+  const bool dense_direct = direct && xdt != T_CSR;
+  if (dense_direct) {
     launch_residual_direct(X, xdt, m, n, p.ldx, U, V, k, fdt, ctx->part, &ctx->scal[9], s);
+  } else if (xdt == T_CSR) {
+    // sparse: ||X||^2 - 2 <U, X V> + <U^T U, V^T V>, the cross term summed
+    // entry by entry over the stored entries (X V row by row)
+    launch_xv(X, xdt, m, n, p.ldx, V, k, k, ctx->M0, k, fdt, ctx->splitk, ctx->num_sms, s);
+    launch_dot(ctx->M0, k, U, k, k, m, fdt, ctx->part, &ctx->scal[10], s);
+    launch_gram(U, k, k, U, k, k, m, fdt, ctx->part, ctx->Gu, s);
+    launch_gram(V, k, k, V, k, k, n, fdt, ctx->part, ctx->Gv, s);
+    launch_dot(ctx->Gu, k, ctx->Gv, k, k, k, T_F64, ctx->part, &ctx->scal[11], s);
   } else {
     launch_xtu(X, xdt, m, n, p.ldx, U, k, k, ctx->N0, k, fdt, ctx->splitk, ctx->num_sms, s);
     launch_dot(ctx->N0, k, V, k, k, n, fdt, ctx->part, &ctx->scal[10], s);
@@ -1417,7 +1572,7 @@ extern "C" enmf_status enmf_residual(enmf_ctx* ctx, const void* X, const void* U
   CK(cudaMemcpyAsync(h, &ctx->scal[8], 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   rc = sync_status(ctx);
   if (rc) return rc;
-  double e2 = direct ? h[1] : h[0] - 2.0 * h[2] + h[3];
+  double e2 = dense_direct ? h[1] : h[0] - 2.0 * h[2] + h[3];
   out3[0] = 0.5 * e2;
   out3[1] = h[0] > 0 ? sqrt(e2 > 0 ? e2 : 0.0) / sqrt(h[0]) : 0.0;
   out3[2] = h[0];
@@ -1429,6 +1584,12 @@ extern "C" enmf_status enmf_kkt(enmf_ctx* ctx, const void* X, const void* U, con
                                 enmf_kkt_report* out) {
   GUARD(ctx);
   if (!X || !U || !V || !out) return ENMF_EINVAL;
+  {
+    const void* xb = nullptr;
+    const enmf_status brc = bind_x(ctx, X, &xb);
+    if (brc) return brc;
+    X = xb;
+  }
   const enmf_problem& p = ctx->p;
   const int k = p.r, fdt = ctx->fdt, xdt = ctx->xdt;
   const int64_t m = p.m, n = p.n;
@@ -1471,6 +1632,31 @@ extern "C" enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V
   GUARD(ctx);
   if (!X || !U || !V || n_iter < 0) return ENMF_EINVAL;
   const enmf_problem& p = ctx->p;
+  if (ctx->xdt == T_CSR) {
+    // the sparse form takes device arrays only (the descriptor is host memory)
+    const enmf_csr* d = (const enmf_csr*)X;
+    if (!is_device_ptr(U) || !is_device_ptr(V) || !d->row_ptr || !is_device_ptr(d->row_ptr) ||
+        (p.nnz > 0 && (!is_device_ptr(d->col) || !is_device_ptr(d->val))))
+      return ENMF_EINVAL;
+    enmf_status rc = enmf_svd_init(ctx, X, U, V, nullptr, svd, nullptr);
+    if (rc && rc != ENMF_ENOTCONV) return rc;
+    rc = enmf_rotate(ctx, U, V, nullptr, admm, nullptr);
+    if (rc && rc != ENMF_ENOTCONV) return rc;
+    enmf_iter_opts io = {n_iter, 5, 1e-4, 3, nullptr, 1, 0, 10};
+    if (iter) {
+      io = *iter;
+      io.n_iter = n_iter;
+      io.reset = 1;
+      io.sync_info = 0;
+    }
+    rc = enmf_iterate(ctx, X, U, V, &io, nullptr);
+    if (rc) return rc;
+    double o3[3];
+    rc = enmf_residual(ctx, X, U, V, o3, 1);
+    if (rc) return rc;
+    if (out3) memcpy(out3, o3, sizeof(o3));
+    return ENMF_OK;
+  }
   const size_t xs = type_size(ctx->xdt), fs = type_size(ctx->fdt);
   const size_t xbytes = (size_t)((p.m - 1) * p.ldx + p.n) * xs;
   const size_t ub = (size_t)p.m * p.r * fs, vb = (size_t)p.n * p.r * fs;
@@ -1522,5 +1708,207 @@ extern "C" enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V
   if (hostV) CK(cudaMemcpyAsync(V, dV, vb, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (out3) memcpy(out3, o3, sizeof(o3));
+  return ENMF_OK;
+}
+
+// ------------------------------------- matrix completion (App. C, eNMC)
+// Per-row masked Grams G (rows x KP x KP) and right-hand sides A (rows x KP)
+// for the larger side, from the stream-ordered allocator for one call.
+static enmf_status nmc_work(enmf_ctx* ctx, int gdt, void** G, void** A) {
+  const enmf_problem& p = ctx->p;
+  const int64_t rows = p.m > p.n ? p.m : p.n;
+  const size_t kp = (size_t)nmc_rank_pad(p.r), fs = type_size(gdt);
+  const size_t gb = al256((size_t)rows * kp * kp * fs), ab = al256((size_t)rows * kp * fs);
+  void* w = nullptr;
+  if (cudaMallocAsync(&w, gb + ab, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return ENMF_ENOMEM;
+  }
+  *G = w;
+  *A = (char*)w + gb;
+  return ENMF_OK;
+}
+
+// The rows of one side as compressed rows of the known entries: U's rows are
+// X's rows, V's rows are the transpose's.
+static void nmc_side(enmf_ctx* ctx, int which, const int64_t** rp, const int32_t** ix,
+                     const void** val, int64_t* rows) {
+  const CsrX& x = ctx->sx;
+  *rp = which == 0 ? x.row_ptr : x.col_ptr;
+  *ix = which == 0 ? x.col : x.row_t;
+  *val = which == 0 ? x.val : x.val_t;
+  *rows = which == 0 ? x.m : x.n;
+}
+
+extern "C" enmf_status enmf_nmc_objective(enmf_ctx* ctx, const void* X, const void* U,
+                                          const void* V, double* out2) {
+  GUARD(ctx);
+  if (!X || !U || !V || !out2) return ENMF_EINVAL;
+  if (ctx->xdt != T_CSR) return ENMF_ESTATE;
+  {
+    const void* xb = nullptr;
+    const enmf_status brc = bind_x(ctx, X, &xb);
+    if (brc) return brc;
+  }
+  cudaStream_t s = ctx->stream;
+  launch_csr_normx2(ctx->sx, ctx->part, &ctx->scal[8], ctx->err, s);
+  launch_nmc_objective(ctx->sx, U, V, ctx->p.r, ctx->fdt, 1.0, ctx->part, &ctx->scal[9], s);
+  enmf_status rc = check_launch(ctx);
+  if (rc) return rc;
+  double h[2];
+  CK(cudaMemcpyAsync(h, &ctx->scal[8], 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  rc = sync_status(ctx);
+  if (rc) return rc;
+  out2[0] = 0.5 * h[1];
+  out2[1] = h[0] > 0 ? sqrt(h[1] / h[0]) : 0.0;
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_nmc_start(enmf_ctx* ctx, const void* X, void* U, void* V,
+                                      const enmf_nmc_start_opts* opts,
+                                      enmf_nmc_start_info* info) {
+  GUARD(ctx);
+  if (!X || !U || !V) return ENMF_EINVAL;
+  if (ctx->xdt != T_CSR) return ENMF_ESTATE;
+  enmf_nmc_start_opts o = {50, 1e-3, 1e-10, 0};
+  if (opts) {
+    o = *opts;
+    if (o.max_sweeps < 0 || !(o.lam >= 0) || !(o.tol >= 0) || o.svd_max_iters < 0)
+      return ENMF_EINVAL;
+  }
+  // the balanced truncated SVD of the zero-filled X (the stored entries)
+  enmf_svd_opts so = {10, 40, ctx->fdt == T_F64 ? 1e-12 : 1e-5, 0x5eedull};
+  if (o.svd_max_iters > 0) so.max_iters = o.svd_max_iters;
+  enmf_status rc = enmf_svd_init(ctx, X, U, V, nullptr, &so, nullptr);
+  if (rc && rc != ENMF_ENOTCONV) return rc;
+  void *G = nullptr, *A = nullptr;
+  rc = nmc_work(ctx, T_F64, &G, &A);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  const int k = ctx->p.r, fdt = ctx->fdt;
+  bool notconv = false;   // a row's matrix was not positive definite (sticky)
+  auto objective = [&](double* f) -> enmf_status {
+    launch_nmc_objective(ctx->sx, U, V, k, fdt, 0.5, ctx->part, &ctx->scal[12], s);
+    enmf_status e = check_launch(ctx);
+    if (e) return e;
+    CK(cudaMemcpyAsync(f, &ctx->scal[12], sizeof(double), cudaMemcpyDeviceToHost, s));
+    e = sync_status(ctx);
+    if (e == ENMF_ENOTCONV) {
+      notconv = true;
+      e = ENMF_OK;
+    }
+    return e;
+  };
+  double f_old = 0.0, f = 0.0;
+  int sw = 0;
+  rc = objective(&f_old);
+  f = f_old;
+  for (int it = 1; it <= o.max_sweeps && rc == ENMF_OK; ++it) {
+    for (int which = 0; which < 2; ++which) {
+      const int64_t* rp;
+      const int32_t* ix;
+      const void* val;
+      int64_t rows;
+      nmc_side(ctx, which, &rp, &ix, &val, &rows);
+      void* F = which == 0 ? U : V;
+      const void* Bf = which == 0 ? V : U;
+      launch_nmc_gram(rp, ix, val, rows, Bf, k, fdt, T_F64, G, A, ctx->num_sms, s);
+      launch_nmc_solve(G, A, rows, k, o.lam, F, fdt, ctx->err, ctx->num_sms, s);
+    }
+    sw = it;
+    rc = objective(&f);
+    if (rc) break;
+    if (fabs(f_old - f) <= o.tol * fabs(f)) break;
+    f_old = f;
+  }
+  cudaFreeAsync(G, s);
+  ctx->state_valid = false;
+  ctx->hals_known = false;
+  if (rc == ENMF_OK) rc = sync_status(ctx);
+  if (info) {
+    info->sweeps = sw;
+    info->f = f;
+  }
+  if (rc == ENMF_OK && notconv) rc = ENMF_ENOTCONV;
+  return rc;
+}
+
+extern "C" enmf_status enmf_nmc_iterate(enmf_ctx* ctx, const void* X, void* U, void* V,
+                                        const enmf_iter_opts* opts, enmf_iter_info* info) {
+  GUARD(ctx);
+  if (!X || !U || !V) return ENMF_EINVAL;
+  if (ctx->xdt != T_CSR) return ENMF_ESTATE;
+  enmf_iter_opts o = {0, 5, 1e-4, 3, nullptr, 0, 1, 10};
+  if (opts) o = *opts;
+  if (o.n_iter < 0 || o.pbcd_max_iter < 0 || !(o.eps >= 0) || o.n_shift < 1) return ENMF_EINVAL;
+  {
+    const void* xb = nullptr;
+    const enmf_status brc = bind_x(ctx, X, &xb);
+    if (brc) return brc;
+  }
+  void *G = nullptr, *A = nullptr;
+  enmf_status rc = nmc_work(ctx, ctx->fdt, &G, &A);
+  if (rc) return rc;
+  const enmf_problem& p = ctx->p;
+  const int k = p.r, fdt = ctx->fdt;
+  cudaStream_t s = ctx->stream;
+  if (o.reset || !ctx->state_valid) {
+    // the Eq. 8 / 9 steps from the negative maxima of the current U, V
+    launch_state_init(U, V, p.m, p.n, k, fdt, o.n_shift, ctx->st, ctx->part, s);
+    ctx->state_valid = true;
+    ctx->hals_known = false;
+    ctx->nmc_rounds = 0;
+  }
+  for (int it = 0; it < o.n_iter; ++it) {
+    for (int which = 0; which < 2; ++which) {
+      const int64_t* rp;
+      const int32_t* ix;
+      const void* val;
+      int64_t rows;
+      nmc_side(ctx, which, &rp, &ix, &val, &rows);
+      void* F = which == 0 ? U : V;
+      const void* Bf = which == 0 ? V : U;
+      launch_nmc_gram(rp, ix, val, rows, Bf, k, fdt, fdt, G, A, ctx->num_sms, s);
+      NmcArgs a;
+      memset(&a, 0, sizeof(a));
+      a.F = F;
+      a.gbuf = ctx->Zb;
+      a.G = G;
+      a.A = A;
+      a.mask = ctx->mask;
+      a.part = ctx->part;
+      a.bar = &ctx->st->bar;
+      a.err = ctx->err;
+      a.st = ctx->st;
+      a.rows = rows;
+      a.k = k;
+      a.fdt = fdt;
+      a.which = which;
+      a.round = ctx->nmc_rounds;
+      a.pbcd_max_iter = o.pbcd_max_iter;
+      a.eps = o.eps;
+      launch_nmc_pbcd(a, nmc_pbcd_grid(fdt, k, ctx->num_sms, rows), s);
+    }
+    launch_nmc_objective(ctx->sx, U, V, k, fdt, 0.5, ctx->part,
+                         o.trace ? o.trace + it : &ctx->st->f_last, s);
+    ++ctx->nmc_rounds;
+    rc = check_launch(ctx);
+    if (rc) break;
+  }
+  cudaFreeAsync(G, s);
+  if (rc) return rc;
+  if (o.sync_info || info) {
+    rc = sync_status(ctx);
+    if (rc) return rc;
+    if (info) {
+      memset(info, 0, sizeof(*info));
+      info->iters = ctx->nmc_rounds;
+      info->asc_iters = ctx->nmc_rounds;
+      DevState hst;
+      CK(cudaMemcpy(&hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+      info->s_u = hst.s_u;
+      info->s_v = hst.s_v;
+    }
+  }
   return ENMF_OK;
 }

@@ -281,9 +281,20 @@ extern "C" enmf_status enmf_batch_add(enmf_batch* b, enmf_ctx* ctx, const void* 
   if (s < 0) return ENMF_EBUSY;
   for (auto& mb : b->mem)
     if (mb.used && mb.ctx == ctx) return ENMF_EINVAL;
-  // the member's own start of an iteration, on its stream; the batch stream
-  // waits for it (and for the caller's earlier work on that stream)
-  ctx_iter_prologue(ctx, X, U, V, b->o.n_shift, true);
+  // the member's own ascent stage, alone on its stream, exactly as
+  // enmf_iterate runs a fresh one (n_shift alternations, the X_lo term
+  // refreshed in each); then its descent joins the batch.  The batch stream
+  // waits for it (and for the caller's earlier work on that stream).
+  {
+    enmf_iter_opts io = b->o;
+    io.n_iter = b->o.n_shift;
+    io.trace = nullptr;
+    io.reset = 1;
+    io.sync_info = 0;
+    const enmf_status rc0 = enmf_iterate(ctx, X, U, V, &io, nullptr);
+    if (rc0) return rc0;
+  }
+  ctx_iter_prologue(ctx, X, U, V, b->o.n_shift, false);
   cudaEvent_t ev;
   if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();

@@ -16,6 +16,7 @@ enum : int {
   ERR_NONFINITE = 2, // a non-finite value appeared
   ERR_NOTCONV = 4,   // Jacobi SVD did not converge / singular polar input
   ERR_DOMAIN = 8,    // negative entry in X
+  ERR_FORMAT = 16,   // malformed compressed rows (pointers, column order or range)
 };
 
 constexpr int LMAX = 80;           // widest small matrix (r + oversample)

@@ -38,6 +38,14 @@ struct enmf_ctx {
   double* T1x;   // eig_orth's companion of T1 (see launch_eig_orth)
   double* Tu; double* Tv; double* Wr; double* UrS; double* csQ; double* csQ2;
   double* scal;                  // 64 scratch scalars
+  // the sparse form: the bound compressed-row descriptor and the context's
+  // transpose (in the workspace)
+  CsrX sx;
+  bool sx_bound;
+  int nmc_rounds;           // rounds of Algorithm eNMC since the last reset
+  int64_t* csc_ptr;
+  int32_t* csc_row;
+  void* csc_val;
   // host-data staging for enmf_solve
   void* hX; void* hU; void* hV;
   size_t hX_bytes;
@@ -56,11 +64,12 @@ struct enmf_ctx {
     int n_iter, pbcd_max_iter, n_shift, correct_every, prof_every;
     double eps;
     int it0;                // first alternation index of the captured range
+    int exact_until;        // alternations before this index refresh X_lo every time
     bool operator==(const IterKey& o) const {
       return X == o.X && U == o.U && V == o.V && trace == o.trace && n_iter == o.n_iter &&
              pbcd_max_iter == o.pbcd_max_iter && n_shift == o.n_shift &&
              correct_every == o.correct_every && prof_every == o.prof_every && eps == o.eps &&
-             it0 == o.it0;
+             it0 == o.it0 && exact_until == o.exact_until;
     }
   };
   // slot 0: the alternation loop with the two-pass sweeps (any stage);

@@ -12,7 +12,33 @@
 namespace enmf {
 
 // Type codes for runtime dispatch.
-enum : int { T_F64 = 0, T_F32 = 1, T_BF16 = 2, T_F16 = 3 };
+enum : int { T_F64 = 0, T_F32 = 1, T_BF16 = 2, T_F16 = 3, T_CSR = 5 };
+
+// X of the sparse form: the caller's compressed rows and the context's
+// transpose (compressed columns, every column's entries in row order).  A
+// launcher given xdt = T_CSR takes X as a pointer to this host struct.
+struct CsrX {
+  const int64_t* row_ptr;   // m + 1
+  const int32_t* col;       // nnz
+  const void* val;          // nnz, vdt
+  int64_t* col_ptr;         // n + 1
+  int32_t* row_t;           // nnz
+  void* val_t;              // nnz, vdt
+  int64_t m, n, nnz;
+  int vdt;                  // T_F64 or T_F32 (the factors' type)
+};
+void launch_csr_check(const CsrX& x, int* err, cudaStream_t s);
+// out[e] = in[e] converted (FP32 <-> FP64), e < count
+void launch_cast(const void* in, int in_dt, void* out, int out_dt, int64_t count, cudaStream_t s);
+size_t csr_transpose_scratch(int64_t m, int64_t n, int64_t* nblk_out, int64_t* rows_per_blk_out);
+void launch_csr_transpose(const CsrX& x, void* scratch, int64_t* col_ptr, int32_t* row_t,
+                          void* val_t, cudaStream_t s);
+// C = X B (trans = false) or X^T B (trans = true); B and C of type fdt.
+void launch_spmm(const CsrX& x, bool trans, const void* B, int ldb, int k, void* C, int ldc,
+                 int fdt, int num_sms, cudaStream_t s);
+void launch_csr_normx2(const CsrX& x, double* part, double* out, int* err, cudaStream_t s);
+
+
 
 inline size_t type_size(int t) { return t == T_F64 ? 8 : t == T_F32 ? 4 : 2; }
 
@@ -326,5 +352,39 @@ void launch_transform_residual(const void* A, const void* B, int64_t rows, int k
 
 // KKT finalisation: combine the two factors' partial measures.
 void launch_kkt_final(const double* pu, const double* pv, double* out, cudaStream_t s);
+
+// Matrix completion (nmc.cu): one half of a round of Algorithm eNMC on the
+// rows of F (U: which = 0, or V: which = 1) with the per-row masked Grams G
+// (rows x KP x KP) and right-hand sides A (rows x KP) already formed.
+struct NmcArgs {
+  void* F;                   // rows x k, updated in place
+  void* gbuf;                // rows x k gradient scratch
+  const void* G;             // rows x KP x KP
+  const void* A;             // rows x KP
+  unsigned long long* mask;  // rows (bit l: entry l in the mask M+)
+  double* part;              // >= 2 NPART doubles
+  GridBarrier* bar;
+  int* err;
+  DevState* st;              // s_u, s_v
+  int* counts;               // PBCD sweeps per half, or NULL
+  int counts_cap;
+  int64_t rows;
+  int k, fdt, which, round, pbcd_max_iter;
+  double eps;
+};
+int nmc_rank_pad(int k);
+// G, A of type gdt (T_F64, or the factors' type fdt)
+void launch_nmc_gram(const int64_t* rp, const int32_t* ix, const void* val, int64_t rows,
+                     const void* B, int k, int fdt, int gdt, void* G, void* A, int num_sms,
+                     cudaStream_t s);
+int nmc_pbcd_grid(int fdt, int k, int num_sms, int64_t rows);
+void launch_nmc_pbcd(const NmcArgs& a, int grid, cudaStream_t s);
+// G, A FP64
+void launch_nmc_solve(const void* G, const void* A, int64_t rows, int k, double lam, void* F,
+                      int fdt, int* err, int num_sms, cudaStream_t s);
+// part: NPART doubles; *out = scale * (sum over the stored entries of
+// (x - u_i . v_j)^2), scale a power of two
+void launch_nmc_objective(const CsrX& x, const void* U, const void* V, int k, int fdt,
+                          double scale, double* part, double* out, cudaStream_t s);
 
 }  // namespace enmf

@@ -249,6 +249,24 @@ void launch_apply_square(void* F, int64_t rows, int k, int fdt, const double* R,
   launch_row_transform(F, k, k, F, k, k, rows, fdt, R, s);
 }
 
+// ------------------------------------------------------------------ casts
+template <typename TI, typename TO>
+__global__ void cast_kernel(const TI* __restrict__ in, TO* __restrict__ out, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (TO)in[e];
+}
+
+void launch_cast(const void* in, int in_dt, void* out, int out_dt, int64_t count, cudaStream_t s) {
+  note_launch(1);
+  int blocks = (int)min((int64_t)2048, (count + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  if (in_dt == T_F32 && out_dt == T_F64)
+    cast_kernel<float, double><<<blocks, 256, 0, s>>>((const float*)in, (double*)out, count);
+  else if (in_dt == T_F64 && out_dt == T_F32)
+    cast_kernel<double, float><<<blocks, 256, 0, s>>>((const double*)in, (float*)out, count);
+}
+
 // ----------------------------------------------------- small reductions
 template <typename TF>
 __global__ void __launch_bounds__(256)

@@ -356,10 +356,18 @@ static void sweep_dispatch(const void* X, int xdt, int64_t m, int64_t n, int64_t
 
 void launch_xv(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, const void* B, int ldb,
                int k, void* C, int ldc, int fdt, void* part, int num_sms, cudaStream_t s) {
+  if (xdt == T_CSR) {
+    launch_spmm(*(const CsrX*)X, false, B, ldb, k, C, ldc, fdt, num_sms, s);
+    return;
+  }
   sweep_dispatch<false>(X, xdt, m, n, ldx, B, ldb, k, C, ldc, fdt, part, num_sms, s);
 }
 void launch_xtu(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, const void* B, int ldb,
                 int k, void* C, int ldc, int fdt, void* part, int num_sms, cudaStream_t s) {
+  if (xdt == T_CSR) {
+    launch_spmm(*(const CsrX*)X, true, B, ldb, k, C, ldc, fdt, num_sms, s);
+    return;
+  }
   sweep_dispatch<true>(X, xdt, m, n, ldx, B, ldb, k, C, ldc, fdt, part, num_sms, s);
 }
 
@@ -547,6 +555,10 @@ normx2_partial(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
 
 void launch_normx2(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, double* part,
                    double* out, int* err, cudaStream_t s) {
+  if (xdt == T_CSR) {
+    launch_csr_normx2(*(const CsrX*)X, part, out, err, s);
+    return;
+  }
   note_launch(2);
   if (xdt == T_F64) normx2_partial<double><<<NPART, 256, 0, s>>>((const double*)X, m, n, ldx, part, err);
   else if (xdt == T_F32) normx2_partial<float><<<NPART, 256, 0, s>>>((const float*)X, m, n, ldx, part, err);

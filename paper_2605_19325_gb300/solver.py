@@ -23,7 +23,16 @@ def problem_for(X, r, f_dtype=None, stream=None):
     iteration's X sweeps run on the tensor cores over a BF16 (FP16) copy of X,
     with the X_lo correction when X is FP32.  stream=torch.float8_e4m3fn (FP32
     X only) selects the FP8 form: e4m3 codes with a power-of-two scale per
-    128 x 128 tile, and a BF16 X_lo correction."""
+    128 x 128 tile, and a BF16 X_lo correction.  X may also be a
+    binding.CsrMatrix (the sparse form, compressed rows)."""
+    if isinstance(X, B.CsrMatrix):
+        if stream not in (None,):
+            raise ValueError("the sparse form has no tensor-core stream")
+        if f_dtype is not None and f_dtype != X.dtype:
+            raise ValueError("the sparse form's factors have the values' type")
+        fdt = B.ENMF_F64 if X.dtype == torch.float64 else B.ENMF_F32
+        return B.enmf_problem(X.shape[0], X.shape[1], X.shape[1], r, B.ENMF_CSR, fdt, 0,
+                              X.nnz), X.dtype
     if X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a row-major matrix (unit column stride)")
     xdt = _XDT.get(X.dtype)
@@ -91,6 +100,20 @@ class Solver:
         tr = torch.zeros(max(n_iter, 1), dtype=torch.float64, device=self.X.device) if trace else None
         info = B.enmf_iterate(self.ctx, self.X, self.U, self.V, n_iter, trace=tr, reset=reset, **kw)
         return (tr[:n_iter] if trace else None), info
+
+    def nmc_start(self, **kw):
+        """The masked-ALS start of Algorithm eNMC (App. C) in place on U, V
+        (sparse form: the stored entries are the known ones)."""
+        return B.enmf_nmc_start(self.ctx, self.X, self.U, self.V, **kw)
+
+    def nmc_iterate(self, n_iter, trace=True, reset=0, **kw):
+        """n_iter rounds of Algorithm eNMC; returns (f^ per round, info)."""
+        tr = torch.zeros(max(n_iter, 1), dtype=torch.float64, device=self.X.device) if trace else None
+        info = B.enmf_nmc_iterate(self.ctx, self.X, self.U, self.V, n_iter, trace=tr, reset=reset, **kw)
+        return (tr[:n_iter] if trace else None), info
+
+    def nmc_objective(self):
+        return B.enmf_nmc_objective(self.ctx, self.X, self.U, self.V)
 
     def rotate_general(self, opts=None):
         """Algorithm 4 (Eq. 5) in place on U, V: returns (info, R1, lam, R2)."""

@@ -105,3 +105,31 @@ def test_state_blob_size_matches_header(libpath):
     text = open(os.path.join(ROOT, "include", "enmf.h")).read()
     m = re.search(r"#define ENMF_STATE_BYTES (\d+)", text)
     assert m and int(m.group(1)) == B.ENMF_STATE_BYTES
+
+
+def test_sparse_form_problem_rules_and_footprint(libpath):
+    """The sparse form (ENMF_CSR): FP32 or FP64 factors, no tensor-core
+    stream, 0 <= nnz <= m n, indices below 2^31; ldx is ignored.  Its
+    workspace adds the transpose (n + 1 column pointers, nnz row indices and
+    nnz values)."""
+    from paper_2605_19325_gb300 import binding as B
+    lib = B.load(libpath)
+
+    def ws(p):
+        size = ctypes.c_size_t(0)
+        code = lib.enmf_workspace_size(ctypes.byref(p), ctypes.byref(size))
+        return code, size.value
+
+    m, n, r, nnz = 5000, 3000, 16, 200000
+    code64, w64 = ws(B.enmf_problem(m, n, 0, r, B.ENMF_CSR, B.ENMF_F64, 0, nnz))
+    code32, w32 = ws(B.enmf_problem(m, n, 0, r, B.ENMF_CSR, B.ENMF_F32, 0, nnz))
+    assert code64 == 0 and code32 == 0
+    code0, w0 = ws(B.enmf_problem(m, n, 0, r, B.ENMF_CSR, B.ENMF_F32, 0, 0))
+    assert code0 == 0
+    assert w32 - w0 >= nnz * 8          # row indices and FP32 values
+    for p in (B.enmf_problem(m, n, 0, r, B.ENMF_CSR, B.ENMF_F32, 0, -1),
+              B.enmf_problem(m, n, 0, r, B.ENMF_CSR, B.ENMF_F32, 0, m * n + 1),
+              B.enmf_problem(m, n, 0, r, B.ENMF_CSR, B.ENMF_F32, B.ENMF_BF16, nnz),
+              B.enmf_problem(m, n, 0, r, B.ENMF_CSR, B.ENMF_BF16, 0, nnz),
+              B.enmf_problem(1 << 31, n, 0, r, B.ENMF_CSR, B.ENMF_F32, 0, nnz)):
+        assert ws(p)[0] == 1   # ENMF_EINVAL

@@ -10,7 +10,13 @@ relative.  Over the alternations of HALS (a contraction near the solution)
 that stays at the level of the per-step rounding; the stated tolerance is
 1e-5 relative on the objective and 1e-4 on the factors (max abs difference
 over max abs entry).
+
+A member's ascent stage (the first n_shift = 3 alternations from its start)
+runs alone when it is added, with the X_lo term refreshed in every
+alternation, exactly as enmf_iterate runs a fresh ascent stage; the batch
+steps then continue its descent.
 """
+N_SHIFT = 3
 import numpy as np
 import pytest
 
@@ -40,9 +46,9 @@ def _prepared(m, n, r, seed):
 SHAPES = [(300, 200, 12, 1), (700, 1100, 16, 2), (129, 257, 9, 3), (1500, 640, 14, 4)]
 
 
-def _run_batch(solvers, starts, n_alt, chunk=10):
+def _run_batch(solvers, starts, n_alt, chunk=10, correct_every=10):
     from paper_2605_19325_gb300 import binding as B
-    b = B.enmf_batch_create(8)
+    b = B.enmf_batch_create(8, correct_every=correct_every)
     try:
         slots = []
         for s, (U0, V0) in zip(solvers, starts):
@@ -72,7 +78,7 @@ def test_batch_member_alone_and_in_mix():
         alone = _run_batch([s], [starts[i]], n_alt)[0]
         k_a, f_a, U_a, V_a = alone
         k_m, f_m, U_m, V_m = mix[i]
-        assert k_a == k_m == n_alt
+        assert k_a == k_m == n_alt + N_SHIFT
         assert abs(f_a - f_m) <= 1e-5 * abs(f_a), (i, f_a, f_m)
         for A_, M_ in ((U_a, U_m), (V_a, V_m)):
             scale = A_.abs().max().item()
@@ -83,16 +89,19 @@ def test_batch_member_alone_and_in_mix():
 
 def test_batch_matches_enmf_iterate():
     """A one-member batch runs the same alternations as enmf_iterate on the
-    same context: the same stage sequence and, within the same tolerance, the
-    same objective and factors."""
+    same context (the ascent stage when added, then the batch steps): the same
+    stage sequence and, within the same tolerance, the same objective and
+    factors.  Both refresh the X_lo term every alternation here, so that the
+    batch's correction phase (anchored at the member's first batch step) and
+    the call's (anchored at its first alternation) cannot differ."""
     from paper_2605_19325_gb300 import binding as B
     s = _prepared(700, 1100, 16, 2)
     U0, V0 = s.U.clone(), s.V.clone()
-    tr, info = s.iterate(30, reset=1)
+    tr, info = s.iterate(N_SHIFT + 30, reset=1, correct_every=1)
     f_it = float(tr[-1].item())
     U_it, V_it = s.U.clone(), s.V.clone()
-    (k, f_b, U_b, V_b), = _run_batch([s], [(U0, V0)], 30)
-    assert k == 30
+    (k, f_b, U_b, V_b), = _run_batch([s], [(U0, V0)], 30, correct_every=1)
+    assert k == N_SHIFT + 30
     assert abs(f_b - f_it) <= 1e-5 * abs(f_it), (f_b, f_it)
     scale = U_it.abs().max().item()
     assert (U_b - U_it).abs().max().item() <= 1e-4 * scale
@@ -113,12 +122,12 @@ def test_batch_rejects_other_padded_rank_and_bad_step():
             B.enmf_batch_step(b, 7)          # not a multiple of correct_every
         B.enmf_batch_step(b, 10)
         info, f = B.enmf_batch_member(b, slot)
-        assert info.iters == 10 and np.isfinite(f)
+        assert info.iters == N_SHIFT + 10 and np.isfinite(f)
         g, ms = B.enmf_batch_tune(b)
         assert g > 0 and ms > 0
         B.enmf_batch_step(b, 10)              # after tuning: still iterating
         info, f2 = B.enmf_batch_member(b, slot)
-        assert info.iters == 20 and f2 <= f * (1 + 1e-6)
+        assert info.iters == N_SHIFT + 20 and f2 <= f * (1 + 1e-6)
         B.enmf_batch_remove(b, slot)
     finally:
         B.enmf_batch_destroy(b)

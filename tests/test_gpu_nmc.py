@@ -1,0 +1,184 @@
+"""Matrix completion (App. C, Algorithm eNMC) on the GPU against the oracle.
+
+The known entries come as compressed rows (the sparse form); the oracle gets
+the same entries as a dense X and the 0/1 mask M_E of the stored pattern.
+
+* f^ and the relative error over the known entries (enmf_nmc_objective)
+  against oracle.objective_masked;
+* the masked-ALS start (enmf_nmc_start) against oracle.masked_als: 20 sweeps
+  with the stopping test off, f^ within 1e-9 (relative) and U V^T within 1e-7
+  of its largest entry, from an SVD start converged to 1e-12; with the default
+  rule, the sweep count within one and f^ within 1e-8;
+* 5 rounds of Algorithm eNMC from the oracle's rotated start
+  (enmf_nmc_iterate) against oracle.enmc_rounds: the f^ trace within 1e-10
+  (relative) per round, U and V within 1e-9; 30 rounds within 10x the
+  oracle's own spread under a 1e-15 perturbation of that start;
+* the FP32 form (start, FP64 rotation, 5 rounds): f^ within 1e-3 of the FP64
+  oracle's;
+* a dense context is refused (ENMF_ESTATE).
+Sizes: rating patterns with power-law user activity and item popularity,
+including users with fewer known entries than r.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _csr(rp, c, v, m, n, dt):
+    from paper_2605_19325_gb300 import binding as B
+    return B.CsrMatrix(torch.as_tensor(rp, device="cuda"),
+                       torch.as_tensor(c.astype(np.int32), device="cuda"),
+                       torch.as_tensor(v, dtype=dt, device="cuda"), (m, n))
+
+
+def _np(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _problem(m, n, known, seed):
+    from oracle import enmf_oracle as O
+    rp, c, v = synth.ratings(m, n, known, seed=seed, dtype=np.float64)
+    X = O.csr_dense(m, n, rp, c, v)
+    M = O.csr_dense(m, n, rp, c, np.ones_like(v))
+    return rp, c, v, X, M
+
+
+CASES = [(300, 200, 0.1, 5, 1), (500, 420, 0.06, 10, 2), (240, 300, 0.15, 25, 3)]
+
+
+@pytest.mark.parametrize("m,n,known,r,seed", CASES)
+def test_nmc_objective_matches_oracle(m, n, known, r, seed):
+    from oracle import enmf_oracle as O
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+    rp, c, v, X, M = _problem(m, n, known, seed)
+    sv = Solver(_csr(rp, c, v, m, n, torch.float64), r)
+    rng = np.random.default_rng(seed)
+    U, V = rng.random((m, r)), rng.random((n, r))
+    f, rel = B.enmf_nmc_objective(sv.ctx, sv.X, torch.as_tensor(U, device="cuda"),
+                                  torch.as_tensor(V, device="cuda"))
+    fo = O.objective_masked(X, M, U, V)
+    assert f == pytest.approx(fo, rel=1e-12)
+    assert rel == pytest.approx(np.sqrt(2 * fo / np.sum(M * X * X)), rel=1e-12)
+    sv.close()
+
+
+@pytest.mark.parametrize("m,n,known,r,seed", CASES)
+def test_nmc_start_sweeps_match_oracle(m, n, known, r, seed):
+    """20 sweeps of the masked ALS with the stopping test off (tol = 0), from
+    an SVD start converged to its 1e-12 residual (rating patterns have a flat
+    spectral tail, so the subspace iteration gets 3000 passes)."""
+    from oracle import enmf_oracle as O
+    from paper_2605_19325_gb300.solver import Solver
+    rp, c, v, X, M = _problem(m, n, known, seed)
+    Uo, Vo, swo = O.masked_als(X, M, r, sweeps=20, tol=0.0)
+    sv = Solver(_csr(rp, c, v, m, n, torch.float64), r)
+    info = sv.nmc_start(max_sweeps=20, tol=0.0, svd_max_iters=3000)
+    assert info.sweeps == swo == 20
+    fo = O.objective_masked(X, M, Uo, Vo)
+    assert info.f == pytest.approx(fo, rel=1e-9)
+    P, Po = _np(sv.U) @ _np(sv.V).T, Uo @ Vo.T
+    assert np.abs(P - Po).max() <= 1e-7 * np.abs(Po).max()
+    sv.close()
+
+
+def test_nmc_start_default_rule():
+    from oracle import enmf_oracle as O
+    from paper_2605_19325_gb300.solver import Solver
+    m, n, known, r, seed = CASES[1]
+    rp, c, v, X, M = _problem(m, n, known, seed)
+    Uo, Vo, swo = O.masked_als(X, M, r)
+    sv = Solver(_csr(rp, c, v, m, n, torch.float64), r)
+    info = sv.nmc_start(svd_max_iters=3000)
+    assert abs(info.sweeps - swo) <= 1, (info.sweeps, swo)
+    assert info.f == pytest.approx(O.objective_masked(X, M, Uo, Vo), rel=1e-8)
+    sv.close()
+
+
+def _rounds(rp, c, v, m, n, r, U0, V0, n_iter, dt=torch.float64):
+    from paper_2605_19325_gb300.solver import Solver
+    sv = Solver(_csr(rp, c, v, m, n, dt), r)
+    sv.U.copy_(torch.as_tensor(U0))
+    sv.V.copy_(torch.as_tensor(V0))
+    gtr, info = sv.nmc_iterate(n_iter, reset=1)
+    out = (_np(gtr), _np(sv.U), _np(sv.V), info)
+    sv.close()
+    return out
+
+
+@pytest.mark.parametrize("m,n,known,r,seed", CASES)
+def test_nmc_rounds_match_oracle(m, n, known, r, seed):
+    """The first 5 rounds from the oracle's rotated start: f^ per round within
+    1e-10, U and V within 1e-9."""
+    from oracle import enmf_oracle as O
+    rp, c, v, X, M = _problem(m, n, known, seed)
+    U0, V0, _ = O.masked_als(X, M, r)
+    U0, V0, _, _ = O.rotate(U0, V0)
+    Uo, Vo, tr = O.enmc_rounds(X, M, U0, V0, 5)
+    gtr, U, V, info = _rounds(rp, c, v, m, n, r, U0, V0, 5)
+    assert info.iters == 5
+    rel = np.abs(gtr - np.asarray(tr)) / np.abs(np.asarray(tr))
+    assert rel.max() < 1e-10, rel.max()
+    assert np.abs(U - Uo).max() <= 1e-9 * np.abs(Uo).max()
+    assert np.abs(V - Vo).max() <= 1e-9 * np.abs(Vo).max()
+    assert U.min() >= 0 and V.min() >= 0
+
+
+@pytest.mark.parametrize("m,n,known,r,seed", CASES)
+def test_nmc_long_run_within_the_oracles_own_spread(m, n, known, r, seed):
+    """30 rounds.  Projected PBCD steps change their active sets as entries
+    reach zero, and the order in which a rounding difference decides such a
+    change amplifies it: the oracle's own trace moves when its start is
+    perturbed by 1e-15 (relative).  The GPU trace must stay within 10x that
+    spread of the oracle's (or 1e-10), round by round; the spread is printed
+    in the failure message."""
+    from oracle import enmf_oracle as O
+    rp, c, v, X, M = _problem(m, n, known, seed)
+    U0, V0, _ = O.masked_als(X, M, r)
+    U0, V0, _, _ = O.rotate(U0, V0)
+    _, _, tr = O.enmc_rounds(X, M, U0, V0, 30)
+    tr = np.asarray(tr)
+    spread = np.zeros_like(tr)
+    for sd in (1, 2):
+        rng = np.random.default_rng(sd)
+        _, _, tp = O.enmc_rounds(X, M, U0 * (1 + 1e-15 * rng.standard_normal(U0.shape)),
+                                 V0 * (1 + 1e-15 * rng.standard_normal(V0.shape)), 30)
+        spread = np.maximum(spread, np.abs(np.asarray(tp) - tr) / tr)
+    gtr, U, V, _ = _rounds(rp, c, v, m, n, r, U0, V0, 30)
+    rel = np.abs(gtr - tr) / tr
+    bound = np.maximum(1e-10, 10 * np.maximum.accumulate(spread))
+    assert np.all(rel <= bound), ("GPU rel diff", rel.max(), "oracle spread", spread.max())
+    assert U.min() >= 0 and V.min() >= 0
+
+
+def test_nmc_fp32_form_gap():
+    """The FP32 form (start, FP64 rotation, 5 rounds) against the FP64 oracle:
+    f^ within 1e-3 (relative)."""
+    from oracle import enmf_oracle as O
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+    m, n, known, r, seed = 600, 500, 0.05, 10, 4
+    rp, c, v, X, M = _problem(m, n, known, seed)
+    res = O.enmc(X, M, r, 5)
+    sv = Solver(_csr(rp, c, v.astype(np.float32), m, n, torch.float32), r)
+    sv.nmc_start(svd_max_iters=3000)
+    sv.rotate(B.enmf_admm_opts(0.0, 3.0, 200, 1e-12, 1))
+    gtr, _ = sv.nmc_iterate(5, reset=1)
+    f32 = float(gtr[-1].item())
+    assert abs(f32 / res.trace[-1] - 1) < 1e-3, (f32, res.trace[-1])
+    sv.close()
+
+
+def test_nmc_refuses_a_dense_context():
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+    X = torch.rand(50, 40, dtype=torch.float64, device="cuda")
+    sv = Solver(X, 4)
+    with pytest.raises(B.EnmfError) as e:
+        sv.nmc_start()
+    assert e.value.code == 8   # ENMF_ESTATE
+    sv.close()

@@ -44,7 +44,7 @@ def test_serve_mix_matches_alone():
         (a,) = alone.run([type(q)(q.rid, q.X, q.r, 0.0)])
         alone.close()
         m = res[q.rid]
-        assert a.iters == m.iters == 40
+        assert a.iters == m.iters == 43   # 3 ascent alternations on admission + 40
         assert abs(a.f - m.f) <= 1e-5 * abs(a.f), (q.rid, a.f, m.f)
         for A_, M_ in ((a.U, m.U), (a.V, m.V)):
             assert (A_ - M_).abs().max().item() <= 1e-4 * A_.abs().max().item(), q.rid
@@ -96,3 +96,36 @@ def test_footprint_counts_x_pair_factors_and_workspace():
     ws = B.enmf_workspace_size(p)
     assert footprint(m, n, r) == m * n * 8 + (m + n) * r * 4 + ws
     assert footprint(2 * m, n, r) > footprint(m, n, r)
+
+
+@pytest.mark.gpu
+def test_serve_stream_meets_the_oracle_target():
+    """The first 16 requests of the seed-0 stream (m, n up to 3127, r up to
+    64), served together in the BF16 form to convergence (tol 1e-6, at most
+    500 alternations).  Each served relative error must be within 1e-3 of the
+    FP64 oracle's after 500 alternations (stored by
+    tests/golden/make_serve_targets.py), or no higher than (1 + 1e-3) times the
+    worst the oracle itself reaches from an SVD start perturbed at FP32
+    rounding size (1e-7, four seeds): on some rank-64 requests that
+    perturbation alone moves the oracle's result by percents, and a form whose
+    factors round at 1e-7 cannot be held closer than that."""
+    import json
+    import os
+    from paper_2605_19325_gb300.serve import Request, Server
+    path = os.path.join(os.path.dirname(__file__), "golden", "serve_targets_seed0_16.json")
+    golden = json.load(open(path))
+    qs = synth.request_stream(16, seed=0)
+    reqs = [Request(q.rid, synth.request_matrix(q, dtype=np.float32), q.r, 0.0) for q in qs]
+    srv = Server(chunk=10, tol=1e-6, max_iter=golden["n_alt"])
+    res = {r.rid: r for r in srv.run(reqs)}
+    srv.close()
+    rows, misses = [], []
+    for g in golden["requests"]:
+        q = qs[g["rid"]]
+        assert (q.m, q.n, q.r) == (g["m"], g["n"], g["r"])
+        served = res[g["rid"]].rel_err
+        band = max([g["rel_f64"]] + g["rel_perturbed"])
+        rows.append((g["rid"], q.r, served / g["rel_f64"] - 1, band / g["rel_f64"] - 1))
+        if served > (1 + 1e-3) * g["rel_f64"] and served > (1 + 1e-3) * band:
+            misses.append(rows[-1])
+    assert not misses, ("(rid, r, excess, oracle band)", misses, rows)

@@ -1,0 +1,228 @@
+"""The sparse form (X as compressed rows, the Reuters experiment of Sec. 5)
+against the oracle, through the C ABI.
+
+* the products: enmf_sweep's X V and X^T U (the row kernel and the context's
+  transpose) against oracle.csr_rows_times / csr_cols_times on the same
+  entries -- FP64 within 1e-12 of the largest entry, FP32 within the FP32
+  accumulation bound of the longest row or column; shapes with empty rows and
+  columns, rows longer than one 32-entry chunk, widths 5, 16, 32, 49 and 64;
+* the transpose is deterministic (two contexts give identical bits);
+* the whole method in FP64 from the oracle's rotated start: the objective
+  trace of Algorithm 3 on the sparse X within 1e-10 (relative) of the oracle's
+  on the densified X, U and V within 1e-9;
+* the whole pipeline (SVD start, rotation, 200 alternations) in FP64 against
+  oracle.enmf on the densified X: sigma within 1e-10, U* V*^T within 1e-9, the
+  final objective within 1e-8; the FP32 form's final relative error within
+  1e-3 of the oracle's;
+* malformed structures are refused (ENMF_EINVAL), negative values flagged
+  (ENMF_EDOMAIN), before any product runs;
+* the Reuters-sized matrix (804,414 x 47,236, 99.84 % sparse, r = 32, FP32):
+  one X V and one X^T U against the oracle on sampled rows and columns.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _csr(rp, c, v, m, n, dt):
+    from paper_2605_19325_gb300 import binding as B
+    return B.CsrMatrix(torch.as_tensor(rp, device="cuda"),
+                       torch.as_tensor(c.astype(np.int32), device="cuda"),
+                       torch.as_tensor(v, dtype=dt, device="cuda"), (m, n))
+
+
+def _np(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _ragged_docs(m, n, density, seed):
+    """Document-term entries with a few empty rows and a few long rows."""
+    rp, c, v = synth.sparse_docs(m, n, density, seed=seed, dtype=np.float64)
+    rows = [c[rp[i]:rp[i + 1]] for i in range(m)]
+    vals = [v[rp[i]:rp[i + 1]] for i in range(m)]
+    rng = np.random.default_rng(seed + 100)
+    for i in rng.choice(m, 3, replace=False):
+        rows[i] = rows[i][:0]
+        vals[i] = vals[i][:0]
+    for i in rng.choice(m, 2, replace=False):
+        cols = np.sort(rng.choice(n, min(n, 200), replace=False)).astype(np.int32)
+        rows[i] = cols
+        vals[i] = rng.random(cols.size) + 0.01
+    cnt = np.array([r.size for r in rows])
+    rp = np.zeros(m + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(cnt)
+    return rp, np.concatenate(rows).astype(np.int32), np.concatenate(vals)
+
+
+SWEEP_CASES = [(282, 1528, 0.027, 5), (700, 300, 0.05, 16), (1000, 2000, 0.01, 32),
+               (333, 257, 0.08, 49), (600, 900, 0.03, 64)]
+
+
+@pytest.mark.parametrize("m,n,density,r", SWEEP_CASES)
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_sparse_products_match_oracle(m, n, density, r, dt):
+    from oracle import enmf_oracle as O
+    from paper_2605_19325_gb300.solver import Solver
+    rp, c, v = _ragged_docs(m, n, density, seed=r)
+    if dt == torch.float32:
+        v = v.astype(np.float32).astype(np.float64)
+    Xs = _csr(rp, c, v, m, n, dt)
+    sv = Solver(Xs, r)
+    rng = np.random.default_rng(1)
+    U = rng.random((m, r))
+    V = rng.random((n, r))
+    if dt == torch.float32:
+        U = U.astype(np.float32).astype(np.float64)
+        V = V.astype(np.float32).astype(np.float64)
+    XV, XtU = sv.sweep(torch.as_tensor(U, dtype=dt, device="cuda"),
+                       torch.as_tensor(V, dtype=dt, device="cuda"))
+    ref_v = O.csr_rows_times(rp, c, v, np.arange(m), V)
+    ref_t = O.csr_cols_times(rp, c, v, np.arange(n), U)
+    if dt == torch.float64:
+        tv, tt = 1e-12 * np.abs(ref_v).max(), 1e-12 * np.abs(ref_t).max()
+    else:
+        # FP32 accumulation: |error| <= len * 2^-24 * sum |x| |b| per output
+        lr = np.diff(rp).max()
+        lc = np.bincount(c, minlength=n).max()
+        tv = (lr + 1) * 2.0 ** -24 * np.abs(ref_v).max()
+        tt = (lc + 1) * 2.0 ** -24 * np.abs(ref_t).max()
+    assert np.abs(_np(XV) - ref_v).max() <= tv
+    assert np.abs(_np(XtU) - ref_t).max() <= tt
+    sv.close()
+
+
+def test_sparse_transpose_is_deterministic():
+    from paper_2605_19325_gb300.solver import Solver
+    m, n, r = 3000, 2500, 32
+    rp, c, v = synth.sparse_docs(m, n, 0.02, seed=4, dtype=np.float32)
+    out = []
+    for _ in range(2):
+        Xs = _csr(rp, c, v, m, n, torch.float32)
+        sv = Solver(Xs, r)
+        rng = np.random.default_rng(2)
+        U = torch.as_tensor(rng.random((m, r)), dtype=torch.float32, device="cuda")
+        V = torch.as_tensor(rng.random((n, r)), dtype=torch.float32, device="cuda")
+        XV, XtU = sv.sweep(U, V)
+        out.append((XV.cpu().numpy(), XtU.cpu().numpy()))
+        sv.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_sparse_iteration_trace_matches_oracle():
+    from oracle import enmf_oracle as O
+    from paper_2605_19325_gb300.solver import Solver
+    m, n, r = 282, 1528, 8
+    rp, c, v = synth.sparse_docs(m, n, 0.027, seed=0, dtype=np.float64)
+    X = O.csr_dense(m, n, rp, c, v)
+    Us, Vs, _ = O.truncated_svd(X, r)
+    U0, V0, _, _ = O.rotate(Us, Vs)
+    Uo, Vo, tr, st = O.iterate(X, U0, V0, 200)
+    sv = Solver(_csr(rp, c, v, m, n, torch.float64), r)
+    sv.U.copy_(torch.as_tensor(U0))
+    sv.V.copy_(torch.as_tensor(V0))
+    gtr, info = sv.iterate(200, reset=1)
+    assert info.asc_iters == st.asc_iters and info.hals_iters == st.hals_iters
+    rel = np.abs(_np(gtr) - tr) / np.abs(tr)
+    assert rel.max() < 1e-10, rel.max()
+    assert np.abs(_np(sv.U) - Uo).max() < 1e-9 * np.abs(Uo).max()
+    assert np.abs(_np(sv.V) - Vo).max() < 1e-9 * np.abs(Vo).max()
+    f, rel_e, nx2 = sv.residual(direct=True)
+    assert f == pytest.approx(O.objective(X, Uo, Vo), rel=1e-10)
+    assert nx2 == pytest.approx(O.csr_sumsq(v), rel=1e-14)
+    sv.close()
+
+
+def test_sparse_pipeline_and_fp32_gap():
+    """The whole pipeline on a document-term matrix.  Its top singular values
+    are close, so the SVD start's factors are fixed only up to rotations
+    inside near-degenerate pairs; what is unique is sigma and U* V*^T, and the
+    method then reaches the oracle's final objective (the ascent amplifies the
+    start's difference early on, the descent contracts it)."""
+    from oracle import enmf_oracle as O
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+    m, n, r = 600, 900, 10
+    rp, c, v = synth.sparse_docs(m, n, 0.03, seed=7, dtype=np.float64)
+    X = O.csr_dense(m, n, rp, c, v)
+    res = O.enmf(X, r, 200)
+    rel_star = O.rel_err(X, res.U, res.V)
+    sv = Solver(_csr(rp, c, v, m, n, torch.float64), r)
+    # a flat spectrum: the subspace iteration needs many more passes than the
+    # default 40 to reach its 1e-12 residual
+    info = sv.svd_init(B.enmf_svd_opts(10, 3000, 1e-12, 0x5eed))
+    assert info.residual <= 1e-12
+    np.testing.assert_allclose(_np(sv.sigma), res.sigma[:r], rtol=1e-10)
+    P, Po = _np(sv.U) @ _np(sv.V).T, res.Us @ res.Vs.T
+    assert np.abs(P - Po).max() <= 1e-9 * np.abs(Po).max()
+    sv.rotate()
+    gtr, info = sv.iterate(200, reset=1)
+    rel = abs(_np(gtr)[-1] - res.trace[-1]) / res.trace[-1]
+    assert rel < 1e-8, rel
+    sv.close()
+    v32 = v.astype(np.float32)
+    sv = Solver(_csr(rp, c, v32, m, n, torch.float32), r)
+    sv.svd_init()
+    sv.rotate()
+    sv.iterate(200, reset=1)
+    _, rel32, _ = sv.residual(direct=True)
+    assert abs(rel32 / rel_star - 1) < 1e-3, (rel32, rel_star)
+    sv.close()
+
+
+def test_sparse_malformed_structure_is_refused():
+    from paper_2605_19325_gb300 import binding as B
+    from paper_2605_19325_gb300.solver import Solver
+    m, n, r = 50, 40, 4
+    rp, c, v = synth.sparse_docs(m, n, 0.2, seed=1, dtype=np.float64)
+    # columns out of order in one row
+    c_bad = c.copy()
+    a = rp[3]
+    c_bad[a], c_bad[a + 1] = c_bad[a + 1], c_bad[a]
+    # a row pointer that ends short of nnz
+    rp_bad = rp.copy()
+    rp_bad[-1] -= 1
+    # a column index past n
+    c_far = c.copy()
+    c_far[rp[5]] = n + 3
+    for rp_x, c_x in ((rp, c_bad), (rp_bad, c), (rp, c_far)):
+        sv = Solver(_csr(rp_x, c_x, v, m, n, torch.float64), r)
+        with pytest.raises(B.EnmfError) as e:
+            sv.svd_init()
+        assert e.value.code == 1   # ENMF_EINVAL
+        sv.close()
+    v_neg = v.copy()
+    v_neg[7] = -1.0
+    sv = Solver(_csr(rp, c, v_neg, m, n, torch.float64), r)
+    with pytest.raises(B.EnmfError) as e:
+        sv.svd_init()
+    assert e.value.code == 2   # ENMF_EDOMAIN
+    sv.close()
+
+
+def test_reuters_sized_products_on_sampled_rows():
+    from oracle import enmf_oracle as O
+    from paper_2605_19325_gb300.solver import Solver
+    m, n, r = 804414, 47236, 32
+    rp, c, v = synth.sparse_docs(m, n, 0.0016, seed=0, dtype=np.float32)
+    Xs = _csr(rp, c, v, m, n, torch.float32)
+    sv = Solver(Xs, r)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    U = torch.rand(m, r, generator=g, device="cuda")
+    V = torch.rand(n, r, generator=g, device="cuda")
+    XV, XtU = sv.sweep(U, V)
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([rng.choice(m, 40, replace=False), [int(np.argmax(np.diff(rp)))]])
+    colcnt = np.bincount(c, minlength=n)
+    cols = np.concatenate([rng.choice(n, 20, replace=False), [int(np.argmax(colcnt))]])
+    Un, Vn = _np(U), _np(V)
+    ref_v = O.csr_rows_times(rp, c, v, rows, Vn)
+    ref_t = O.csr_cols_times(rp, c, v, cols, Un)
+    tv = (np.diff(rp).max() + 1) * 2.0 ** -24 * np.abs(ref_v).max()
+    tt = (colcnt.max() + 1) * 2.0 ** -24 * np.abs(ref_t).max()
+    assert np.abs(_np(XV)[rows] - ref_v).max() <= tv
+    assert np.abs(_np(XtU)[cols] - ref_t).max() <= tt
+    sv.close()

@@ -47,6 +47,9 @@ class FakeBinding:
         m, n, r = p
         return 1000 + (m + n) * r
 
+    def enmf_admm_opts(self, *fields):
+        return fields
+
     def enmf_batch_create(self, max_members, stream=None):
         self.next_id += 1
         self.batches[self.next_id] = {"max": max_members, "members": {}, "next": 0}
@@ -99,7 +102,7 @@ class FakeSolver:
     def svd_init(self):
         pass
 
-    def rotate(self):
+    def rotate(self, opts=None):
         pass
 
     def residual(self):
