@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-nmc", action="store_true")
     ap.add_argument("--only-fp8", action="store_true",
                     help="run the FP8-form leg alone (rank 0) and print its JSON")
+    ap.add_argument("--only-sparse", action="store_true",
+                    help="run the sparse-form leg alone (rank 0) and print its JSON")
+    ap.add_argument("--only-nmc", action="store_true",
+                    help="run the matrix-completion leg alone (rank 0) and print its JSON")
     ap.add_argument("--fp8-forms", default="fp8,bf16,f32,f64",
                     help="forms of the FP8 leg, comma separated (the gap needs f32)")
     ap.add_argument("--serve-requests", type=int, default=4096)
@@ -871,6 +875,16 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         print(json.dumps({"fp8_form": fp8_leg(tuple(args.fp8_forms.split(",")))}))
+        return
+    if args.only_sparse or args.only_nmc:
+        import __graft_entry__
+        __graft_entry__.build()
+        out = {}
+        if args.only_sparse:
+            out["sparse_form"] = sparse_leg()
+        if args.only_nmc:
+            out["completion"] = nmc_leg()
+        print(json.dumps(out))
         return
     if args.impl == "reference":
         run_reference(args)
