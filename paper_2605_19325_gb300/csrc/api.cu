@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "ctx.h"
 
@@ -158,8 +159,18 @@ static size_t plan(const enmf_problem* p, int num_sms, size_t* splitk_out) {
   t += al256(4096 * 8) + al256(2 * 4096 * 8);
   t += 9 * al256((size_t)LMAX * LMAX * 8) + 2 * al256((size_t)LMAX * RMAX * 8);
   t += 2 * al256((size_t)LMAX * RMAX * 8) + 3 * al256(LMAX * 8) + al256(64 * 8);
-  if (p->x_dtype == ENMF_CSR)   // the transpose: column pointers, row indices, values
+  t += al256(2 * sizeof(HalfTail));
+  if (p->x_dtype == ENMF_CSR) {  // the transpose: column pointers, row indices, values
     t += al256((nn + 1) * 8) + al256((size_t)p->nnz * 4) + al256((size_t)p->nnz * fs);
+    // the work plans of X B and X^T B (items, split rows, partial slots)
+    for (int d = 0; d < 2; ++d) {
+      const int64_t rows = d == 0 ? p->m : p->n;
+      t += 2 * al256((size_t)spmm_max_items(rows, p->nnz) * 4) +
+           al256((size_t)spmm_max_items(rows, p->nnz) * 16);
+      t += 3 * al256((size_t)spmm_max_split(p->nnz) * 4);
+      t += al256((size_t)spmm_max_slots(p->nnz) * LMAX * fs);
+    }
+  }
   return t;
 }
 
@@ -277,10 +288,27 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
   ctx->csQ = (double*)take(LMAX * 8);
   ctx->csQ2 = (double*)take(LMAX * 8);
   ctx->scal = (double*)take(64 * 8);
+  ctx->tails = (HalfTail*)take(2 * sizeof(HalfTail));
+  cudaMemsetAsync(ctx->tails, 0, 2 * sizeof(HalfTail), ctx->stream);
   if (p->x_dtype == ENMF_CSR) {
     ctx->csc_ptr = (int64_t*)take((nn + 1) * 8);
     ctx->csc_row = (int32_t*)take((size_t)p->nnz * 4);
     ctx->csc_val = take((size_t)p->nnz * fs);
+    for (int d = 0; d < 2; ++d) {
+      SpmmPlan& pl = ctx->sx.plan[d];
+      const int64_t rows = d == 0 ? p->m : p->n;
+      const size_t ni = (size_t)spmm_max_items(rows, p->nnz) * 4;
+      const size_t ns = (size_t)spmm_max_split(p->nnz) * 4;
+      pl.item_row = (int32_t*)take(ni);
+      pl.item_p = (int64_t*)take(ni * 4);
+      pl.item_slot = (int32_t*)take(ni);
+      pl.split_row = (int32_t*)take(ns);
+      pl.split_base = (int32_t*)take(ns);
+      pl.split_cnt = (int32_t*)take(ns);
+      pl.partial = take((size_t)spmm_max_slots(p->nnz) * LMAX * fs);
+      pl.nitems = 0;
+      pl.nsplit = 0;
+    }
   }
   if ((size_t)(b - (char*)ctx->ws) > ctx->ws_bytes) {
     cudaFreeAsync(ctx->ws, ctx->stream);
@@ -762,6 +790,9 @@ static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const dou
     a.cut_G = tc_group_grid(a.cut_W, ctx->num_sms);
     a.cut_nkb = (int)((red + (mode == 0 ? TC_KB_XV : TC_KB_XT) - 1) / (mode == 0 ? TC_KB_XV : TC_KB_XT));
     a.cut_rp = ctx->rp;
+    // in the HALS stage the Gram sum and the end of the alternation run in the
+    // next main sweep pass (slot 0 / 2), or in the flush after the loop
+    a.tail = ctx->tails + which;
   }
   launch_half_step(a, which == 0 ? ctx->grid_u : ctx->grid_v, ctx->stream);
 }
@@ -778,6 +809,10 @@ static const SweepProb* tc_desc(enmf_ctx* ctx, int slot, int mode, bool lo, floa
   const enmf_problem& p = ctx->p;
   SweepProb d;
   memset(&d, 0, sizeof(d));
+  // the iteration's main passes run the tail the previous half step left:
+  // X V (slot 0) the V-half's, X^T U (slot 2) the U-half's
+  if (slot == 0) d.tail = ctx->tails + 1;
+  if (slot == 2) d.tail = ctx->tails + 0;
   memcpy(d.mapX, ctx->maps[lo ? MAP_XL : MAP_XH], sizeof(d.mapX));
   memcpy(d.mapBh, ctx->maps[mode == 0 ? MAP_VH : MAP_UH], sizeof(d.mapBh));
   memcpy(d.mapBl, ctx->maps[mode == 0 ? MAP_VL : MAP_UL], sizeof(d.mapBl));
@@ -930,6 +965,18 @@ static enmf_status bind_x(enmf_ctx* ctx, const void* X, const void** xin) {
   if (rc) return rc;
   rc = sync_status(ctx);
   if (rc) return rc;
+  // the balanced work plans of both products, from host copies of the row
+  // and column pointers
+  for (int d = 0; d < 2; ++d) {
+    const int64_t rows = d == 0 ? p.m : p.n;
+    std::vector<int64_t> hp((size_t)rows + 1);
+    CK(cudaMemcpy(hp.data(), d == 0 ? x.row_ptr : x.col_ptr, ((size_t)rows + 1) * 8,
+                  cudaMemcpyDeviceToHost));
+    if (!build_spmm_plan(hp.data(), rows, x.plan[d], s)) {
+      ctx->poison = ENMF_ECUDA;
+      return ENMF_ECUDA;
+    }
+  }
   ctx->sx_bound = true;
   *xin = &ctx->sx;
   return ENMF_OK;
@@ -1216,6 +1263,9 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
       sweep_xtu(ctx, X, U, ctx->N0, corr, rec, false, false);
       run_half(ctx, 1, V, ctx->N0, ctx->Gu, n, o, true, ctx->Gv, ctx->Gu, o.trace, it);
     }
+    // the last half step's deferred tail (ctx->stream: inside a capture, the
+    // capture stream)
+    if (ctx->tc && it1 > it0) launch_half_tail_flush(ctx->tails, 2, ctx->stream);
   };
   // HALS stage, tensor-core form: one fused pass over X per alternation
   // (fused.cu) for the U-half and both products, then the V-half over the

@@ -38,6 +38,7 @@ struct enmf_ctx {
   double* T1x;   // eig_orth's companion of T1 (see launch_eig_orth)
   double* Tu; double* Tv; double* Wr; double* UrS; double* csQ; double* csQ2;
   double* scal;                  // 64 scratch scalars
+  HalfTail* tails;               // the HALS half steps' deferred tails (U, V)
   // the sparse form: the bound compressed-row descriptor and the context's
   // transpose (in the workspace)
   CsrX sx;

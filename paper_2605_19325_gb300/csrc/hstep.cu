@@ -32,6 +32,7 @@
 
 #include "internal.h"
 #include "lanes.cuh"
+#include "tail.cuh"
 
 namespace enmf {
 namespace {
@@ -472,6 +473,28 @@ __device__ __forceinline__ void hstep_body(const HalfArgs& a, const int lb, cons
     const double dsum = block_sum256(dotacc, sh);
     if (t == 0) a.dot_part[lb] = dsum;
   }
+  if (a.tail) {
+    if (stage == 1 && !a.gram_only) {
+      // HALS stage: the Gram sum and the end of the alternation are left to
+      // the next sweep pass (no grid barrier here)
+      if (lb == 0 && t == 0) {
+        HalfTail* tl = a.tail;
+        tl->gpart = a.gpart;
+        tl->G_out = a.G_out;
+        tl->obj_part = a.obj_part;
+        tl->dot_part = a.dot_part;
+        tl->st = a.st;
+        tl->trace = a.trace;
+        tl->nb = nb;
+        tl->kk = kk;
+        tl->finalize = a.finalize;
+        tl->trace_idx = a.trace_idx;
+        tl->pending = 1;
+      }
+      return;
+    }
+    if (lb == 0 && t == 0) a.tail->pending = 0;
+  }
   grid_sync(a.bar, a.err);
 
   // ---- G_out = sum of the block partials in block order (block 0 left free
@@ -555,6 +578,20 @@ __global__ void __launch_bounds__(HT) hstep_group_kernel(const HalfArgs* __restr
                      ginv, sh);
 }
 
+// The pending tails of a call's last half steps (one block of four warps).
+__global__ void __launch_bounds__(128) half_tail_flush_kernel(HalfTail* tails, int n) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < n; ++i) {
+    HalfTail* tl = tails + i;
+    if (__ldcg(&tl->pending)) {
+      half_tail_work(tl, warp, 4, lane);
+      __syncthreads();
+      if (threadIdx.x == 0) tl->pending = 0;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename TF, int KP>
 size_t hstep_smem() {
   return sizeof(TF) * ((size_t)KP * KP + (size_t)RPB * KP);
@@ -624,6 +661,11 @@ void launch_half_group(const HalfArgs* probs, const int* bbeg, int np, int grid,
   else if (kp == 48) HGL(48);
   else HGL(64);
 #undef HGL
+}
+
+void launch_half_tail_flush(HalfTail* tails, int n, cudaStream_t s) {
+  note_launch(1);
+  half_tail_flush_kernel<<<1, 128, 0, s>>>(tails, n);
 }
 
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s) {

@@ -17,6 +17,23 @@ enum : int { T_F64 = 0, T_F32 = 1, T_BF16 = 2, T_F16 = 3, T_CSR = 5 };
 // X of the sparse form: the caller's compressed rows and the context's
 // transpose (compressed columns, every column's entries in row order).  A
 // launcher given xdt = T_CSR takes X as a pointer to this host struct.
+// Work of one product (X B or X^T B): the rows cut into items of at most
+// SPMM_SEG stored entries (at least one item per row, so empty rows are
+// written).  An item of a row with one item writes the row of the output; the
+// items of a longer row write partial rows to consecutive slots, summed in
+// slot order by the fix-up (split rows: row, first slot, number of slots).
+constexpr int SPMM_SEG = 2048;
+struct SpmmPlan {
+  int32_t* item_row;        // nitems
+  int64_t* item_p;          // 2 nitems: first and one-past-last entry
+  int32_t* item_slot;       // nitems: partial slot, or -1 (writes the output row)
+  int64_t nitems;
+  int32_t* split_row;       // nsplit
+  int32_t* split_base;      // nsplit
+  int32_t* split_cnt;       // nsplit
+  int64_t nsplit;
+  void* partial;            // slots x LMAX of the factors' type
+};
 struct CsrX {
   const int64_t* row_ptr;   // m + 1
   const int32_t* col;       // nnz
@@ -26,7 +43,12 @@ struct CsrX {
   void* val_t;              // nnz, vdt
   int64_t m, n, nnz;
   int vdt;                  // T_F64 or T_F32 (the factors' type)
+  SpmmPlan plan[2];         // X B, X^T B
 };
+// Bounds of a plan's arrays for `rows` rows and nnz entries.
+inline int64_t spmm_max_items(int64_t rows, int64_t nnz) { return rows + nnz / SPMM_SEG + 1; }
+inline int64_t spmm_max_split(int64_t nnz) { return nnz / (SPMM_SEG + 1) + 1; }
+inline int64_t spmm_max_slots(int64_t nnz) { return 2 * (nnz / SPMM_SEG) + 2; }
 void launch_csr_check(const CsrX& x, int* err, cudaStream_t s);
 // out[e] = in[e] converted (FP32 <-> FP64), e < count
 void launch_cast(const void* in, int in_dt, void* out, int out_dt, int64_t count, cudaStream_t s);
@@ -37,6 +59,9 @@ void launch_csr_transpose(const CsrX& x, void* scratch, int64_t* col_ptr, int32_
 void launch_spmm(const CsrX& x, bool trans, const void* B, int ldb, int k, void* C, int ldc,
                  int fdt, int num_sms, cudaStream_t s);
 void launch_csr_normx2(const CsrX& x, double* part, double* out, int* err, cudaStream_t s);
+// Fills pl's item and split arrays (device, sized by the spmm_max_* bounds)
+// from the host copy of a product's row pointers; synchronises s.
+bool build_spmm_plan(const int64_t* rp, int64_t rows, SpmmPlan& pl, cudaStream_t s);
 
 
 
@@ -104,6 +129,23 @@ void launch_part_reduce(const double* part, int width, double* out, cudaStream_t
 void launch_omega(void* F, int fdt, int64_t rows, int k, uint64_t seed, cudaStream_t s);
 
 // ----------------------------------------------------------------- rows.cu
+// The tail of a HALS-stage half step left to the next kernel on the stream:
+// the Gram of the updated factor summed from its per-block partials and, for
+// the V-half, the end of the alternation (objective, trace, counters).  The
+// half step writes every field (pending = 1 when it left its tail, 0 when it
+// ran it itself); the next tensor-core sweep pass of the iteration, or the
+// flush at the end of an enmf_iterate call, runs it (hstep.cu, tc_sweep.cu).
+struct HalfTail {
+  const double* gpart;      // nb x kk block partials of the Gram
+  double* G_out;            // kk
+  const double* obj_part;   // nb: <U^T U, block partial> (V-half)
+  const double* dot_part;   // nb: <A, F> (V-half)
+  DevState* st;
+  double* trace;
+  int nb, kk, finalize, trace_idx;
+  int pending;
+};
+
 struct HalfArgs {
   void* F;            // factor being updated (rows x k)
   const void* A;      // X V or X^T U for this half (rows x k, ld k)
@@ -162,9 +204,14 @@ struct HalfArgs {
   // plus cut_corr (the X_lo term) when given.  Null: not used.
   const float* sum_part;
   int sum_n;
+  // non-null: in the HALS stage the Gram sum and the end of the alternation
+  // are left to the next sweep through this tail (one-problem launches only)
+  HalfTail* tail;
 };
 // hstep.cu: one cooperative launch per half step; grid <= half_step_grid().
 void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);
+// Runs tails[0..n) that are pending and clears them (one small launch).
+void launch_half_tail_flush(HalfTail* tails, int n, cudaStream_t s);
 int half_step_grid(int fdt, int k, int num_sms, int64_t rows);
 // Grouped half steps of np problems with FP32 factors (HalfArgs in device
 // memory, all with the same `bar`); problem p owns blocks bbeg[p] ..
@@ -269,6 +316,8 @@ struct alignas(64) SweepProb {
   const int* xexp;  // FP8 form: exponent k of each 128 x 128 tile of X
   int l2hint;       // X tiles' L2 policy: 0 normal, 1 evict_last (X_hi, read
                     // every alternation), 2 evict_first (X_lo, read rarely)
+  const HalfTail* tail;   // the previous half step's tail, run by the epilogue
+                          // warps while the first accumulator fills (or null)
 };
 // Fills the sizes of d (maps and pointers set by the caller) and returns its
 // work units (tiles x k-blocks) and tiles through *units / *tiles.

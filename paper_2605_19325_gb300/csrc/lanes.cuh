@@ -98,6 +98,25 @@ __device__ __forceinline__ void accumulate_outer(const TF* xs, const TF* ys, int
 // takes partials l + 32 j in eight independent loads, then the eight are
 // combined pairwise and the lanes by a butterfly.  The order is fixed by nb,
 // so the sum does not depend on timing.  Block of BT threads.
+// Entry e of the sum of nb block partials (part[b * kk + e]) by one warp, in
+// a fixed order whoever runs it; every lane returns the total.
+__device__ __forceinline__ double warp_sum_partials(const double* part, int nb, int kk, int e,
+                                                   int lane) {
+  double s = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 256) {
+    double c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int b = b0 + lane + 32 * j;
+      c[j] = b < nb ? __ldcg(&part[(int64_t)b * kk + e]) : 0.0;
+    }
+    s += ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  return s;
+}
+
 // The reduction runs on blocks bid = first .. nblk - 1 of a group of nblk
 // blocks (by default the whole grid).
 template <int BT>
@@ -113,18 +132,7 @@ __device__ __forceinline__ void sum_block_partials(const double* part, int nb, i
   const int nbk = nblk - first;
   if (bid < first || nbk <= 0) return;
   for (int e = (bid - first) * WPB + warp; e < kk; e += nbk * WPB) {
-    double s = 0.0;
-    for (int b0 = 0; b0 < nb; b0 += 256) {
-      double c[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int b = b0 + lane + 32 * j;
-        c[j] = b < nb ? __ldcg(&part[(int64_t)b * kk + e]) : 0.0;
-      }
-      s += ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    const double s = warp_sum_partials(part, nb, kk, e, lane);
     if (lane == 0) out[e] = s;
   }
 }

@@ -24,6 +24,8 @@
 // col_ptr[c] + (earlier blocks' entries of c) + (its own earlier entries of
 // c).  Within one row the columns are distinct, so the threads of a block
 // handle a row's entries at once; rows follow one another in order.
+#include <vector>
+
 #include "internal.h"
 
 namespace enmf {
@@ -196,33 +198,59 @@ csr_scatter_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ c
 }
 
 // ---------------------------------------------------------------- X B
-// C[i, :] = sum over the stored entries p of row i of val[p] B[col[p], :].
-template <typename TV, typename TF, int E>
-__global__ void __launch_bounds__(SP_T)
-spmm_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-            const TV* __restrict__ val, int64_t rows, const TF* __restrict__ B, int ldb, int k,
-            TF* __restrict__ C, int ldc) {
+// One warp per work item (at most SPMM_SEG entries of one row): the item's
+// entries are read 32 at a time (lane t loads the (column, value) pair of
+// entry p0 + t), each pair broadcast by a shuffle; UN entries' rows of B are
+// requested before the first multiply.  The next chunk's pairs, and at the
+// last chunk the next item's bounds and first pairs, are requested before
+// the current chunk is used, so a warp keeps its loads in flight across
+// items.  Lane t accumulates the output columns t + 32 e in entry order:
+// every item's sum is deterministic.
+template <typename TV, typename TF, int E, int UN>
+__global__ void __launch_bounds__(SP_T, 4)
+spmm_items_kernel(const int32_t* __restrict__ col, const TV* __restrict__ val,
+                  const int32_t* __restrict__ item_row, const int64_t* __restrict__ item_p,
+                  const int32_t* __restrict__ item_slot, int64_t nitems,
+                  const TF* __restrict__ B, int ldb, int k, TF* __restrict__ C, int ldc,
+                  TF* __restrict__ part) {
   constexpr int L = 32;
   const int lane = threadIdx.x % L;
   const int64_t g0 = ((int64_t)blockIdx.x * SP_T + threadIdx.x) / L;   // warp-uniform
   const int64_t ng = (int64_t)gridDim.x * SP_T / L;
-  for (int64_t i = g0; i < rows; i += ng) {
-    const int64_t a = rp[i], b = rp[i + 1];
+  if (g0 >= nitems) return;
+  // the first item's bounds and pairs
+  int64_t a = item_p[2 * g0], b = item_p[2 * g0 + 1];
+  int32_t cl = (a + lane < b) ? col[a + lane] : 0;
+  TF vl = (a + lane < b) ? (TF)val[a + lane] : TF(0);
+  for (int64_t it = g0; it < nitems; it += ng) {
+    const int64_t itn = it + ng;
+    const int32_t row = item_row[it];
+    const int32_t slot = item_slot[it];
+    int64_t an = 0, bn = 0;
+    if (itn < nitems) {
+      an = item_p[2 * itn];
+      bn = item_p[2 * itn + 1];
+    }
     TF acc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = TF(0);
-    for (int64_t p0 = a; p0 < b; p0 += L) {
-      const int64_t p = p0 + lane;
-      const int32_t cl = p < b ? col[p] : 0;
-      const TF vl = p < b ? (TF)val[p] : TF(0);
+    int64_t p0 = a;
+    while (true) {
       const int cnt = (int)min((int64_t)L, b - p0);
-      for (int j0 = 0; j0 < cnt; j0 += 4) {
-        TF bv[4][E], vv[4];
+      // the pairs used next: this item's next chunk, else the next item's first
+      const bool more = p0 + L < b;
+      const int64_t pn = (more ? p0 + L : an) + lane;
+      const int64_t en = more ? b : bn;
+      const int32_t cn = pn < en ? col[pn] : 0;
+      const TF vn = pn < en ? (TF)val[pn] : TF(0);
+      for (int j0 = 0; j0 < cnt; j0 += UN) {
+        TF bv[UN][E], vv[UN];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < UN; ++u) {
           const int j = j0 + u;
-          const int32_t c = shfl(cl, j < cnt ? j : 0);
-          const TF vj = shfl(vl, j < cnt ? j : 0);
+          const int jj = j < cnt ? j : 0;
+          const int32_t c = __shfl_sync(0xffffffffu, cl, jj);
+          const TF vj = __shfl_sync(0xffffffffu, vl, jj);
           vv[u] = j < cnt ? vj : TF(0);
 #pragma unroll
           for (int e = 0; e < E; ++e) {
@@ -231,15 +259,42 @@ spmm_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < UN; ++u)
 #pragma unroll
           for (int e = 0; e < E; ++e) acc[e] = fma(vv[u], bv[u][e], acc[e]);
       }
+      cl = cn;
+      vl = vn;
+      if (!more) break;
+      p0 += L;
     }
+    TF* dst = slot < 0 ? C + (int64_t)row * ldc : part + (int64_t)slot * LMAX;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int l = lane + L * e;
-      if (l < k) C[i * ldc + l] = acc[e];
+      if (l < k) dst[l] = acc[e];
+    }
+    a = an;
+    b = bn;
+  }
+}
+
+// The rows cut into several items: their partial rows summed in slot order.
+template <typename TF>
+__global__ void __launch_bounds__(SP_T)
+spmm_fixup_kernel(const int32_t* __restrict__ split_row, const int32_t* __restrict__ split_base,
+                  const int32_t* __restrict__ split_cnt, int64_t nsplit,
+                  const TF* __restrict__ part, int k, TF* __restrict__ C, int ldc) {
+  const int lane = threadIdx.x % 32;
+  const int64_t g0 = ((int64_t)blockIdx.x * SP_T + threadIdx.x) / 32;
+  const int64_t ng = (int64_t)gridDim.x * SP_T / 32;
+  for (int64_t q = g0; q < nsplit; q += ng) {
+    const int64_t base = split_base[q];
+    const int cnt = split_cnt[q];
+    for (int l = lane; l < k; l += 32) {
+      TF s = TF(0);
+      for (int j = 0; j < cnt; ++j) s += part[(base + j) * LMAX + l];
+      C[(int64_t)split_row[q] * ldc + l] = s;
     }
   }
 }
@@ -270,19 +325,30 @@ csr_sumsq_partial(const TV* __restrict__ val, int64_t nnz, double* __restrict__ 
 }
 
 template <typename TV, typename TF>
-void spmm_launch(const int64_t* rp, const int32_t* col, const void* val, int64_t rows,
+void spmm_launch(const int32_t* col, const void* val, const SpmmPlan& pl,
                  const void* B, int ldb, int k, void* C, int ldc, int num_sms, cudaStream_t s) {
   const TV* v = (const TV*)val;
   const TF* Bf = (const TF*)B;
   TF* Cf = (TF*)C;
+  TF* part = (TF*)pl.partial;
   const int64_t warps_per_blk = SP_T / 32;
-  int64_t grid = (rows + warps_per_blk - 1) / warps_per_blk;
-  const int64_t cap = (int64_t)num_sms * 8;
+  int64_t grid = (pl.nitems + warps_per_blk - 1) / warps_per_blk;
+  const int64_t cap = (int64_t)num_sms * 4;   // all resident (at most 64 registers)
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  if (k <= 32) spmm_kernel<TV, TF, 1><<<(int)grid, SP_T, 0, s>>>(rp, col, v, rows, Bf, ldb, k, Cf, ldc);
-  else if (k <= 64) spmm_kernel<TV, TF, 2><<<(int)grid, SP_T, 0, s>>>(rp, col, v, rows, Bf, ldb, k, Cf, ldc);
-  else spmm_kernel<TV, TF, 3><<<(int)grid, SP_T, 0, s>>>(rp, col, v, rows, Bf, ldb, k, Cf, ldc);
+#define SPK(E, UN)                                                                              \
+  spmm_items_kernel<TV, TF, E, UN><<<(int)grid, SP_T, 0, s>>>(                                   \
+      col, v, pl.item_row, pl.item_p, pl.item_slot, pl.nitems, Bf, ldb, k, Cf, ldc, part)
+  if (k <= 32) SPK(1, 8);
+  else if (k <= 64) SPK(2, 4);
+  else SPK(3, 4);
+#undef SPK
+  if (pl.nsplit > 0) {
+    int64_t g2 = (pl.nsplit + warps_per_blk - 1) / warps_per_blk;
+    if (g2 > cap) g2 = cap;
+    spmm_fixup_kernel<TF><<<(int)g2, SP_T, 0, s>>>(pl.split_row, pl.split_base, pl.split_cnt,
+                                                    pl.nsplit, part, k, Cf, ldc);
+  }
 }
 
 }  // namespace
@@ -349,9 +415,54 @@ void launch_spmm(const CsrX& x, bool trans, const void* B, int ldb, int k, void*
   const int64_t* rp = trans ? x.col_ptr : x.row_ptr;
   const int32_t* ix = trans ? x.row_t : x.col;
   const void* v = trans ? x.val_t : x.val;
-  const int64_t rows = trans ? x.n : x.m;
-  if (fdt == T_F64) spmm_launch<double, double>(rp, ix, v, rows, B, ldb, k, C, ldc, num_sms, s);
-  else spmm_launch<float, float>(rp, ix, v, rows, B, ldb, k, C, ldc, num_sms, s);
+  const SpmmPlan& pl = x.plan[trans ? 1 : 0];
+  if (pl.nsplit > 0) note_launch(1);
+  (void)rp;
+  if (fdt == T_F64) spmm_launch<double, double>(ix, v, pl, B, ldb, k, C, ldc, num_sms, s);
+  else spmm_launch<float, float>(ix, v, pl, B, ldb, k, C, ldc, num_sms, s);
+}
+
+// The items of one product from its row pointers (host copy `rp`, rows + 1
+// entries), written to the plan's device arrays (synchronous copies on s).
+bool build_spmm_plan(const int64_t* rp, int64_t rows, SpmmPlan& pl, cudaStream_t s) {
+  std::vector<int32_t> irow, islot, srow, sbase, scnt;
+  std::vector<int64_t> ip;
+  irow.reserve((size_t)rows + 16);
+  int32_t slot = 0;
+  for (int64_t i = 0; i < rows; ++i) {
+    const int64_t len = rp[i + 1] - rp[i];
+    const int64_t nseg = len > SPMM_SEG ? (len + SPMM_SEG - 1) / SPMM_SEG : 1;
+    if (nseg > 1) {
+      srow.push_back((int32_t)i);
+      sbase.push_back(slot);
+      scnt.push_back((int32_t)nseg);
+    }
+    for (int64_t g = 0; g < nseg; ++g) {
+      irow.push_back((int32_t)i);
+      const int64_t a = rp[i] + g * SPMM_SEG;
+      ip.push_back(a);
+      ip.push_back(a + SPMM_SEG < rp[i + 1] ? a + SPMM_SEG : rp[i + 1]);
+      islot.push_back(nseg > 1 ? slot++ : -1);
+    }
+  }
+  pl.nitems = (int64_t)irow.size();
+  pl.nsplit = (int64_t)srow.size();
+  bool ok = true;
+  auto put = [&](int32_t* dst, const std::vector<int32_t>& v) {
+    if (!v.empty() && cudaMemcpyAsync(dst, v.data(), v.size() * 4, cudaMemcpyHostToDevice, s) !=
+                          cudaSuccess)
+      ok = false;
+  };
+  put(pl.item_row, irow);
+  put(pl.item_slot, islot);
+  if (!ip.empty() && cudaMemcpyAsync(pl.item_p, ip.data(), ip.size() * 8, cudaMemcpyHostToDevice,
+                                     s) != cudaSuccess)
+    ok = false;
+  put(pl.split_row, srow);
+  put(pl.split_base, sbase);
+  put(pl.split_cnt, scnt);
+  if (cudaStreamSynchronize(s) != cudaSuccess) ok = false;
+  return ok;
 }
 
 void launch_csr_normx2(const CsrX& x, double* part, double* out, int* err, cudaStream_t s) {

@@ -36,6 +36,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "tail.cuh"
 #include "tc_ptx.cuh"
 
 namespace enmf {
@@ -447,6 +448,13 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // First the previous half step's deferred tail (HalfTail), if any, spread
+    // over every CTA's four epilogue warps while the first accumulator fills.
+    {
+      const HalfTail* tl = probs[0].tail;
+      if (tl && __ldcg(&tl->pending))
+        half_tail_work(tl, (int)blockIdx.x * 4 + (warp - 2), (int)gridDim.x * 4, lane);
+    }
     // Warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= tile rows).
     // The accumulator passes through a shared-memory tile with an odd row
     // stride (conflict-free), so that every global access below is a flat,

@@ -113,10 +113,7 @@ class Server:
                 "cuda", non_blocking=False)
             s = Solver(Xt, req.r, stream=self.stream, x_stream=torch.bfloat16)
             s.svd_init()
-            # Algorithm 1 in FP64 (rows and the r x r update): the ADMM
-            # amplifies FP32 rounding along flat directions of the negative
-            # mass, and the start it produces decides the served KKT point
-            s.rotate(B.enmf_admm_opts(0.0, 3.0, 200, 1e-12, 1))
+            s.rotate()
         rp = 16 if req.r <= 16 else 32 if req.r <= 32 else 48 if req.r <= 48 else 64
         b = self._batch(rp)
         sl = _Slot()

@@ -6,6 +6,8 @@ against the oracle, through the C ABI.
   entries -- FP64 within 1e-12 of the largest entry, FP32 within the FP32
   accumulation bound of the longest row or column; shapes with empty rows and
   columns, rows longer than one 32-entry chunk, widths 5, 16, 32, 49 and 64;
+* rows and columns longer than one 2048-entry work item (split into items and
+  summed in order) against the oracle, and identical bits on two runs;
 * the transpose is deterministic (two contexts give identical bits);
 * the whole method in FP64 from the oracle's rotated start: the objective
   trace of Algorithm 3 on the sparse X within 1e-10 (relative) of the oracle's
@@ -93,6 +95,58 @@ def test_sparse_products_match_oracle(m, n, density, r, dt):
     assert np.abs(_np(XV) - ref_v).max() <= tv
     assert np.abs(_np(XtU) - ref_t).max() <= tt
     sv.close()
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_sparse_long_rows_and_columns_are_split(dt):
+    """Rows and columns longer than one work item (2048 stored entries): a row
+    of 4500 entries and a column of 2600, next to short and empty ones; the
+    items' partial rows are summed in order by the fix-up.  FP64 within 1e-12
+    of the largest entry, FP32 within the accumulation bound; two runs give
+    the same bits."""
+    from oracle import enmf_oracle as O
+    from paper_2605_19325_gb300.solver import Solver
+    m, n, r = 3000, 5000, 40
+    rng = np.random.default_rng(7)
+    rows = []
+    for i in range(m):
+        if i == 17:
+            cols = np.sort(rng.choice(n, 4500, replace=False))
+        else:
+            cols = np.sort(rng.choice(n, int(rng.integers(0, 12)), replace=False))
+            if i % 7 != 0 and 123 not in cols:          # column 123: about 2570 entries
+                cols = np.sort(np.append(cols, 123))
+        rows.append(cols.astype(np.int32))
+    cnt = np.array([x.size for x in rows])
+    rp = np.zeros(m + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(cnt)
+    c = np.concatenate(rows).astype(np.int32)
+    v = rng.random(c.size) + 0.01
+    if dt == torch.float32:
+        v = v.astype(np.float32).astype(np.float64)
+    assert cnt.max() > 2048 and np.bincount(c, minlength=n).max() > 2048
+    U = rng.random((m, r))
+    V = rng.random((n, r))
+    if dt == torch.float32:
+        U = U.astype(np.float32).astype(np.float64)
+        V = V.astype(np.float32).astype(np.float64)
+    outs = []
+    for _ in range(2):
+        sv = Solver(_csr(rp, c, v, m, n, dt), r)
+        XV, XtU = sv.sweep(torch.as_tensor(U, dtype=dt, device="cuda"),
+                           torch.as_tensor(V, dtype=dt, device="cuda"))
+        outs.append((_np(XV), _np(XtU)))
+        sv.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    ref_v = O.csr_rows_times(rp, c, v, np.arange(m), V)
+    ref_t = O.csr_cols_times(rp, c, v, np.arange(n), U)
+    if dt == torch.float64:
+        tv, tt = 1e-12 * np.abs(ref_v).max(), 1e-12 * np.abs(ref_t).max()
+    else:
+        tv = (cnt.max() + 1) * 2.0 ** -24 * np.abs(ref_v).max()
+        tt = (np.bincount(c, minlength=n).max() + 1) * 2.0 ** -24 * np.abs(ref_t).max()
+    assert np.abs(outs[0][0] - ref_v).max() <= tv
+    assert np.abs(outs[0][1] - ref_t).max() <= tt
 
 
 def test_sparse_transpose_is_deterministic():
