@@ -349,8 +349,11 @@ enmf_status enmf_solve(enmf_ctx* ctx, const void* X, void* U, void* V, int32_t n
  * its X_lo terms at the same alternations as it would alone.  enmf_batch_member synchronises the batch stream and reports a
  * member's alternation count, stage and objective f (Eq. 1) after its last
  * alternation.  enmf_batch_tune times the grouped sweeps of the current
- * membership at several stream-K grid sizes and keeps the fastest (*grid,
- * and the time of one X V + X^T U pair in ms); it synchronises.  A context
+ * membership at several stream-K grid sizes (a quarter, half, three quarters
+ * and all of the SMs) and depths of their shared-memory ring of X stages (2,
+ * 3, or as deep as fits) and keeps the fastest pair (*grid, and the time of
+ * one X V + X^T U pair in ms); it synchronises.  The serving loop re-tunes
+ * when a batch's membership has changed by half since the last tuning.  A context
  * may be in one batch at a time, and must not be used by other calls while
  * it is a member. */
 typedef struct enmf_batch enmf_batch;

@@ -50,6 +50,7 @@ struct enmf_batch {
   int64_t W[4];
   int half_grid[2];
   int sweep_grid;         // 0: one CTA per SM (or fewer); else the tuned grid
+  int sweep_stages;       // X ring depth of the sweeps: 0 = as deep as fits; else tuned
   // the captured step
   cudaStream_t cap;
   cudaGraphExec_t graph;
@@ -189,20 +190,20 @@ enmf_status rebuild(enmf_batch* b) {
   return ENMF_OK;
 }
 
-void sweep(enmf_batch* b, int q, int grid) {
+void sweep(enmf_batch* b, int q, int grid, int stages) {
   if (!b->np[q]) return;
   launch_tc_group(q < 2 ? 0 : 1, b->rp, b->d_sw[q], b->np[q], b->W[q], b->part, b->counters,
-                  grid > 0 ? grid : b->num_sms, b->d_err, b->stream);
+                  grid > 0 ? grid : b->num_sms, b->d_err, b->stream, 1, 0, stages);
 }
 
 // One alternation of every member (refreshing the X_lo terms when corr).
 void alternation(enmf_batch* b, bool corr) {
   const int np = (int)b->h_half[0].size();
-  if (corr) sweep(b, 1, b->sweep_grid);
-  sweep(b, 0, b->sweep_grid);
+  if (corr) sweep(b, 1, b->sweep_grid, b->sweep_stages);
+  sweep(b, 0, b->sweep_grid, b->sweep_stages);
   launch_half_group(b->d_half[0], b->d_bbeg[0], np, b->half_grid[0], b->rp, b->stream);
-  if (corr) sweep(b, 3, b->sweep_grid);
-  sweep(b, 2, b->sweep_grid);
+  if (corr) sweep(b, 3, b->sweep_grid, b->sweep_stages);
+  sweep(b, 2, b->sweep_grid, b->sweep_stages);
   launch_half_group(b->d_half[1], b->d_bbeg[1], np, b->half_grid[1], b->rp, b->stream);
 }
 
@@ -498,41 +499,48 @@ extern "C" enmf_status enmf_batch_tune(enmf_batch* b, int32_t* grid_out, float* 
     enmf_status rc = rebuild(b);
     if (rc) return rc;
   }
-  // candidates: the stream-K grid of the grouped sweeps
-  const int cands[5] = {b->num_sms / 4, b->num_sms / 2, (3 * b->num_sms) / 4, b->num_sms, 0};
+  // candidates: the stream-K grid of the grouped sweeps x the depth of their
+  // shared-memory ring of X stages (2, 3, or as deep as fits)
+  const int cands[4] = {b->num_sms / 4, b->num_sms / 2, (3 * b->num_sms) / 4, b->num_sms};
+  const int st_cands[3] = {2, 3, 0};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
     return ENMF_ECUDA;
   }
-  int best = 0;
+  int best = 0, best_st = 0;
   float best_ms = 1e30f;
-  for (int c = 0; c < 4; ++c) {
-    const int g = cands[c] < 1 ? 1 : cands[c];
-    // X V and X^T U sweeps alone: they read the current factors and write
-    // the members' sweep outputs, which the next alternation overwrites
-    sweep(b, 0, g);
-    sweep(b, 2, g);
-    cudaEventRecord(e0, b->stream);
-    for (int rep = 0; rep < 3; ++rep) {
-      sweep(b, 0, g);
-      sweep(b, 2, g);
+  for (int c = 0; c < 4; ++c)
+    for (int si = 0; si < 3; ++si) {
+      const int g = cands[c] < 1 ? 1 : cands[c];
+      const int st = st_cands[si];
+      // X V and X^T U sweeps alone: they read the current factors and write
+      // the members' sweep outputs, which the next alternation overwrites
+      sweep(b, 0, g, st);
+      sweep(b, 2, g, st);
+      cudaEventRecord(e0, b->stream);
+      for (int rep = 0; rep < 3; ++rep) {
+        sweep(b, 0, g, st);
+        sweep(b, 2, g, st);
+      }
+      cudaEventRecord(e1, b->stream);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = g;
+        best_st = st;
+      }
     }
-    cudaEventRecord(e1, b->stream);
-    float ms = 0.f;
-    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = g;
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best > 0 && best != b->sweep_grid) {
+  if (best > 0 && (best != b->sweep_grid || best_st != b->sweep_stages)) {
     b->sweep_grid = best;
+    b->sweep_stages = best_st;
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;

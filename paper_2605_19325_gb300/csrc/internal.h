@@ -329,9 +329,10 @@ void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r,
 // fixup = 0 (one problem only): tiles cut by the stream-K ranges are left as
 // partial slots for the consumer (see CutTiles).
 // xq = 1: the FP8-form kernel (every descriptor's X is e4m3 codes).
+// stages: X stages of the shared-memory ring, 0 = as many as fit (2..8).
 void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
                      int* counters, int num_sms, int* err, cudaStream_t s, int fixup = 1,
-                     int xq = 0);
+                     int xq = 0, int stages = 0);
 int tc_group_grid(int64_t W, int num_sms);
 // 2D BF16 tensor map (CUtensorMap, 128 bytes at `map`) over a row-major
 // (rows x cols, ld) array, box box_cols x box_rows, 128-byte swizzle.

@@ -950,8 +950,9 @@ void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r,
 
 template <int MODE, int RP, bool XQ>
 static void launch_tc(const SweepProb* probs, int np, int64_t W, float* part, int* counters,
-                      int grid, int fixup, int* err, cudaStream_t s) {
-  const int stages = XQ ? 2 : tc_stages(MODE, RP);
+                      int grid, int fixup, int* err, cudaStream_t s, int want_stages) {
+  const int max_st = tc_stages(MODE, RP);
+  const int stages = XQ ? 2 : (want_stages >= 2 && want_stages < max_st ? want_stages : max_st);
   int qstages = 0, bstages = 0;
   size_t smem = tc_smem(MODE, RP, stages);
   if (XQ) tc_xq_plan(MODE, RP, &bstages, &qstages, &smem);
@@ -962,13 +963,14 @@ static void launch_tc(const SweepProb* probs, int np, int64_t W, float* part, in
 }
 
 void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
-                     int* counters, int num_sms, int* err, cudaStream_t s, int fixup, int xq) {
+                     int* counters, int num_sms, int* err, cudaStream_t s, int fixup, int xq,
+                     int stages) {
   if (np < 1 || W < 1) return;
   const int grid = tc_group_grid(W, num_sms);
   note_launch(1);
-#define TCL(M, P)                                                             \
-  (xq ? launch_tc<M, P, true>(probs, np, W, part, counters, grid, fixup, err, s) \
-      : launch_tc<M, P, false>(probs, np, W, part, counters, grid, fixup, err, s))
+#define TCL(M, P)                                                                       \
+  (xq ? launch_tc<M, P, true>(probs, np, W, part, counters, grid, fixup, err, s, stages) \
+      : launch_tc<M, P, false>(probs, np, W, part, counters, grid, fixup, err, s, stages))
   if (mode == 0) {
     if (rp == 16) TCL(0, 16); else if (rp == 32) TCL(0, 32); else if (rp == 48) TCL(0, 48); else TCL(0, 64);
   } else {

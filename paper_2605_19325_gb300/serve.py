@@ -85,7 +85,7 @@ class Server:
         self.tune = tune
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.batches = {}            # padded rank -> batch handle
-        self.tuned = set()
+        self.tuned = {}      # padded rank -> batch size when its sweeps were last tuned
         self.pending = collections.deque()
         self.active = []
         self.used = 0
@@ -186,11 +186,15 @@ class Server:
                 continue
             t = time.perf_counter()
             for rp, b in self.batches.items():
-                if B.enmf_batch_size(b) == 0:
+                size = B.enmf_batch_size(b)
+                if size == 0:
                     continue
-                if self.tune and rp not in self.tuned:
+                # (re)tune the grouped sweeps when the batch is new or its
+                # membership has changed by half since the last tuning
+                last = self.tuned.get(rp)
+                if self.tune and (last is None or abs(size - last) * 2 > max(last, 4)):
                     B.enmf_batch_tune(b)
-                    self.tuned.add(rp)
+                    self.tuned[rp] = size
                 B.enmf_batch_step(b, self.chunk)
             self.steps += 1
             t2 = time.perf_counter()
