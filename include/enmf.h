@@ -510,6 +510,23 @@ enmf_status enmf_nmc_objective(enmf_ctx* ctx, const void* X, const void* U, cons
  * 1) turns it on, 0 off; *available (may be NULL) tells whether the context
  * can run it at all. */
 enmf_status enmf_set_fused(enmf_ctx* ctx, int32_t on, int32_t* available);
+
+/* ---- Overlap of consecutive kernels (no counterpart in the paper) ---------
+ * In the captured alternation loop of the tensor-core forms, a kernel may be
+ * launched as a programmatic dependent of the one before it: it starts while
+ * that kernel still runs, and waits for its completion before touching
+ * anything it shares with it.  flags bit 0: each X sweep after a half step
+ * (its CTAs request their first X tiles early; X is not written inside the
+ * loop); bit 1: each half step after a sweep (its launch overlaps the sweep's
+ * last CTAs).  Results are bit-identical either way.  Default 1: on a GB300
+ * (dense 8192 x 6144, r = 32, 500 alternations) bit 0 took 40.3 ms against
+ * 40.7 ms without, bit 1 41.9 ms and both 45.3 ms (a half step's blocks that
+ * start early run on SMs whose shared memory is configured for the sweep,
+ * with less L1 cache).  flags < 0
+ * leaves the setting unchanged; flags > 3 is ENMF_EINVAL.  *in_effect (may be
+ * NULL) receives the flags in effect: a capture that the driver refuses with
+ * the attribute is redone without it and the flags drop to 0. */
+enmf_status enmf_set_overlap(enmf_ctx* ctx, int32_t flags, int32_t* in_effect);
 /* The fused pass's launch shape, for reports: shape[0] = 1 if available,
  * shape[1] = CTAs per cluster, [2] = clusters, [3] = columns of X per CTA,
  * [4] = X stages in shared memory, [5] = dynamic shared memory per CTA (KB). */

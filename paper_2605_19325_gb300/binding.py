@@ -155,6 +155,7 @@ _SIGS = {
     "enmf_launch_count": (C.c_longlong, []),
     "enmf_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
     "enmf_set_fused": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "enmf_set_overlap": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "enmf_rotate_general": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(enmf_admm_opts),
                                       C.POINTER(enmf_rotate_info)]),
@@ -451,11 +452,20 @@ def enmf_perm_check(ctx, UA, UB, r, eps=0.05, keep_frac=0.9):
 
 
 def enmf_set_fused(ctx, on):
-    """Use the fused single-pass HALS alternation (1, default) or not (0);
+    """Use the fused single-pass HALS alternation (1) or not (0, default);
     returns whether the context can run it."""
     av = C.c_int32(0)
     check(lib().enmf_set_fused(ctx, 1 if on else 0, C.byref(av)), "enmf_set_fused")
     return bool(av.value)
+
+
+def enmf_set_overlap(ctx, flags=-1):
+    """Programmatic dependent launches in the captured loop (bit 0: sweeps
+    after half steps, bit 1: half steps after sweeps); flags < 0 only reads.
+    Returns the flags in effect."""
+    cur = C.c_int32(0)
+    check(lib().enmf_set_overlap(ctx, int(flags), C.byref(cur)), "enmf_set_overlap")
+    return cur.value
 
 
 def enmf_fused_shape(ctx):

@@ -408,6 +408,7 @@ extern "C" enmf_status enmf_create(const enmf_problem* p, void* stream, enmf_ctx
   // passes at the measured shapes (its per-panel exchange across the cluster
   // is latency-bound): off unless enmf_set_fused asks for it.
   ctx->fz_enabled = 0;
+  ctx->overlap = 1;   // (enmf_set_overlap: the measured best)
   {
     const char* e = getenv("ENMF_L2_KEEP");   // diagnostics: 0 = normal L2 policy for X_hi
     ctx->l2_keep = (e && atoi(e) == 0) ? 0 : 1;
@@ -774,6 +775,16 @@ HalfArgs ctx_half_args(enmf_ctx* ctx, int which, void* F, const void* A, const d
 
 static int64_t tc_units(enmf_ctx* ctx, int mode);
 
+// Programmatic dependent launch for the next kernel of the captured loop:
+// only while capturing, with the flag `bit` of enmf_set_overlap set, and when
+// the node before it is a kernel of the loop (no event, copy or graph start
+// in between).  Every launch of the loop marks itself as such a node.
+static int pdl_next(enmf_ctx* ctx, int bit) {
+  const int on = (ctx->capturing && ctx->adj && (ctx->overlap & bit)) ? 1 : 0;
+  ctx->adj = ctx->capturing;
+  return on;
+}
+
 // The half steps of enmf_iterate: in the tensor-core form, A comes from a
 // main sweep pass run without fix-up, so the half step assembles its cut
 // tiles (HalfArgs::cut_part).
@@ -794,7 +805,8 @@ static void run_half(enmf_ctx* ctx, int which, void* F, const void* A, const dou
     // next main sweep pass (slot 0 / 2), or in the flush after the loop
     a.tail = ctx->tails + which;
   }
-  launch_half_step(a, which == 0 ? ctx->grid_u : ctx->grid_v, ctx->stream);
+  launch_half_step(a, which == 0 ? ctx->grid_u : ctx->grid_v, ctx->stream,
+                   ctx->tc ? pdl_next(ctx, 2) : 0);
 }
 
 // ------------------------------------------------------------ the sweeps
@@ -831,6 +843,7 @@ static const SweepProb* tc_desc(enmf_ctx* ctx, int slot, int mode, bool lo, floa
     ctx->hprob[slot] = d;
     cudaMemcpyAsync(ctx->dprob + slot, &ctx->hprob[slot], sizeof(d), cudaMemcpyHostToDevice,
                     ctx->stream);
+    ctx->adj = false;
   }
   return ctx->dprob + slot;
 }
@@ -848,8 +861,12 @@ static int64_t tc_units(enmf_ctx* ctx, int mode) {
 // factor split or the X_lo correction pass).
 static void prof_mark(enmf_ctx* ctx, bool rec) {
   // (external: inside a captured graph the record is a real event node)
-  if (rec) cudaEventRecordWithFlags(ctx->pev[ctx->npev++], ctx->stream, cudaEventRecordExternal);
+  if (rec) {
+    cudaEventRecordWithFlags(ctx->pev[ctx->npev++], ctx->stream, cudaEventRecordExternal);
+    ctx->adj = false;
+  }
 }
+
 
 // split = false: the BF16 pair of the factor is already current (written by
 // the half step that produced the factor).
@@ -872,13 +889,13 @@ static void sweep_xv(enmf_ctx* ctx, const void* X, const void* V, void* out, int
   if (corr == 2 && ctx->xl) {
     const SweepProb* d = tc_desc(ctx, base + 1, 0, true, ctx->cv, nullptr);
     launch_tc_group(0, ctx->rp, d, 1, tc_units(ctx, 0), ctx->tcpart, ctx->tccount, ctx->num_sms,
-                    ctx->err, s);
+                    ctx->err, s, 1, 0, 0, pdl_next(ctx, 1));
   }
   const SweepProb* d = tc_desc(ctx, base, 0, false, (float*)out,
                                (corr >= 1 && ctx->xl) ? ctx->cv : nullptr);
   prof_mark(ctx, rec);
   launch_tc_group(0, ctx->rp, d, 1, tc_units(ctx, 0), ctx->tcpart, ctx->tccount, ctx->num_sms,
-                  ctx->err, s, fixup ? 1 : 0, ctx->xq);
+                  ctx->err, s, fixup ? 1 : 0, ctx->xq, 0, pdl_next(ctx, 1));
   prof_mark(ctx, rec);
 }
 
@@ -899,13 +916,13 @@ static void sweep_xtu(enmf_ctx* ctx, const void* X, const void* U, void* out, in
   if (corr == 2 && ctx->xl) {
     const SweepProb* d = tc_desc(ctx, base + 1, 1, true, ctx->cu, nullptr);
     launch_tc_group(1, ctx->rp, d, 1, tc_units(ctx, 1), ctx->tcpart, ctx->tccount, ctx->num_sms,
-                    ctx->err, s);
+                    ctx->err, s, 1, 0, 0, pdl_next(ctx, 1));
   }
   const SweepProb* d = tc_desc(ctx, base, 1, false, (float*)out,
                                (corr >= 1 && ctx->xl) ? ctx->cu : nullptr);
   prof_mark(ctx, rec);
   launch_tc_group(1, ctx->rp, d, 1, tc_units(ctx, 1), ctx->tcpart, ctx->tccount, ctx->num_sms,
-                  ctx->err, s, fixup ? 1 : 0, ctx->xq);
+                  ctx->err, s, fixup ? 1 : 0, ctx->xq, 0, pdl_next(ctx, 1));
   prof_mark(ctx, rec);
 }
 
@@ -1144,7 +1161,10 @@ static bool replay_iteration(enmf_ctx* ctx, int slot, const enmf_ctx::IterKey& k
               cudaSuccess;
     if (ok) {
       ctx->stream = ctx->cap_stream;
+      ctx->capturing = true;
+      ctx->adj = false;
       loop();
+      ctx->capturing = false;
       ctx->stream = user;
       ok = cudaStreamEndCapture(ctx->cap_stream, &g) == cudaSuccess && g;
     }
@@ -1157,6 +1177,14 @@ static bool replay_iteration(enmf_ctx* ctx, int slot, const enmf_ctx::IterKey& k
     if (g) cudaGraphDestroy(g);
     if (!ok) {
       cudaGetLastError();
+      if (ctx->overlap) {
+        // capture again without programmatic dependent launches (the flags
+        // in effect read back through enmf_set_overlap)
+        ctx->overlap = 0;
+        enmf_ctx::IterKey k2 = key;
+        k2.overlap = 0;
+        return replay_iteration(ctx, slot, k2, loop);
+      }
       ctx->no_graph = true;
       return false;
     }
@@ -1265,7 +1293,7 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
     }
     // the last half step's deferred tail (ctx->stream: inside a capture, the
     // capture stream)
-    if (ctx->tc && it1 > it0) launch_half_tail_flush(ctx->tails, 2, ctx->stream);
+    if (ctx->tc && it1 > it0) launch_half_tail_flush(ctx->tails, 2, ctx->num_sms, ctx->stream);
   };
   // HALS stage, tensor-core form: one fused pass over X per alternation
   // (fused.cu) for the U-half and both products, then the V-half over the
@@ -1300,7 +1328,7 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
     if (it1 <= it0) return;
     enmf_ctx::IterKey key = {X, U, V, o.trace, it1 - it0, o.pbcd_max_iter, o.n_shift,
                              o.correct_every, ctx->prof_every, o.eps, it0,
-                             it0 < exact_until ? exact_until : 0};
+                             it0 < exact_until ? exact_until : 0, ctx->overlap};
     auto body = [&]() {
       if (slot == 0) general(it0, it1);
       else fused(it0, it1);
@@ -1382,6 +1410,16 @@ extern "C" enmf_status enmf_iterate(enmf_ctx* ctx, const void* X, void* U, void*
     }
     return rc;
   }
+  return ENMF_OK;
+}
+
+extern "C" enmf_status enmf_set_overlap(enmf_ctx* ctx, int32_t flags, int32_t* in_effect) {
+  GUARD(ctx);
+  if (flags >= 0) {
+    if (flags > 3) return ENMF_EINVAL;
+    ctx->overlap = flags;
+  }
+  if (in_effect) *in_effect = ctx->overlap;
   return ENMF_OK;
 }
 

@@ -23,6 +23,18 @@ constexpr int LMAX = 80;           // widest small matrix (r + oversample)
 constexpr int RMAX = 64;           // widest factor (rank)
 constexpr long long SPIN_BUDGET_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
+// ------------------------------------------- programmatic dependent launch
+// A kernel launched as a programmatic dependent of the previous kernel on its
+// stream may start while that kernel still runs; griddep_wait() returns once
+// the previous kernel has completed and its writes are visible (at once when
+// the kernel was launched without the attribute).  griddep_launch() lets the
+// next kernel on the stream, if launched with the attribute, be scheduled
+// early; every thread of a block calls it.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // --------------------------------------------------------------- conversion
 template <typename T> __device__ __forceinline__ double to_d(T v);
 template <> __device__ __forceinline__ double to_d<double>(double v) { return v; }

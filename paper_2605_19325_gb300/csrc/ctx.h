@@ -66,11 +66,12 @@ struct enmf_ctx {
     double eps;
     int it0;                // first alternation index of the captured range
     int exact_until;        // alternations before this index refresh X_lo every time
+    int overlap;            // the enmf_set_overlap flags the graph was captured with
     bool operator==(const IterKey& o) const {
       return X == o.X && U == o.U && V == o.V && trace == o.trace && n_iter == o.n_iter &&
              pbcd_max_iter == o.pbcd_max_iter && n_shift == o.n_shift &&
              correct_every == o.correct_every && prof_every == o.prof_every && eps == o.eps &&
-             it0 == o.it0 && exact_until == o.exact_until;
+             it0 == o.it0 && exact_until == o.exact_until && overlap == o.overlap;
     }
   };
   // slot 0: the alternation loop with the two-pass sweeps (any stage);
@@ -81,6 +82,11 @@ struct enmf_ctx {
   int iter_graph_kernels[2];   // kernel launches per replay
   int iter_graph_npev[2];      // profiling events recorded per replay
   bool no_graph;            // capture failed once: launch eagerly
+  // programmatic dependent launches inside the captured loop (enmf_set_overlap):
+  // bit 0 the sweeps after a half step, bit 1 the half steps after a sweep
+  int overlap;
+  bool capturing;           // the loop is being captured
+  bool adj;                 // the last captured node is one of the loop's kernels
   // fused single-pass HALS alternation (fused.cu); fz_plan.ok = 0: not used
   FusedPlan fz_plan;
   int fz_enabled;           // enmf_set_fused (default 1)

@@ -543,6 +543,10 @@ __global__ void __launch_bounds__(HT) hstep_kernel(HalfArgs a) {
   TF* us = Gs + KP * KP;                   // RPB x KP rows of the current pass
   __shared__ double sh[HT];
   __shared__ TF ginv[KP];                  // 1 / G_jj (0 where G_jj <= 0)
+  // (a programmatic dependent of the sweep it reads: nothing before the wait;
+  // then the next sweep may start requesting its X tiles)
+  griddep_wait();
+  griddep_launch();
   hstep_body<TF, KP>(a, (int)blockIdx.x, (int)gridDim.x, -1, Gs, us, ginv, sh);
 }
 
@@ -579,17 +583,18 @@ __global__ void __launch_bounds__(HT) hstep_group_kernel(const HalfArgs* __restr
 }
 
 // The pending tails of a call's last half steps (one block of four warps).
-__global__ void __launch_bounds__(128) half_tail_flush_kernel(HalfTail* tails, int n) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i < n; ++i) {
-    HalfTail* tl = tails + i;
-    if (__ldcg(&tl->pending)) {
-      half_tail_work(tl, warp, 4, lane);
-      __syncthreads();
-      if (threadIdx.x == 0) tl->pending = 0;
-    }
-    __syncthreads();
-  }
+// The flush spreads each pending tail's Gram entries over every warp of the
+// grid; the pending flags are cleared by a second launch, once all of them are
+// done.
+__global__ void __launch_bounds__(128) half_tail_flush_kernel(const HalfTail* tails, int n) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 4 + (threadIdx.x >> 5), ngw = gridDim.x * 4;
+  for (int i = 0; i < n; ++i)
+    if (__ldcg(&tails[i].pending)) half_tail_work(tails + i, gw, ngw, lane);
+}
+
+__global__ void half_tail_clear_kernel(HalfTail* tails, int n) {
+  if (threadIdx.x < n) tails[threadIdx.x].pending = 0;
 }
 
 template <typename TF, int KP>
@@ -607,10 +612,21 @@ int hstep_capacity(int num_sms) {
 }
 
 template <typename TF, int KP>
-void hstep_launch(const HalfArgs& a, int grid, cudaStream_t s) {
-  void* args[] = {(void*)&a};
-  cudaLaunchCooperativeKernel((void*)hstep_kernel<TF, KP>, dim3(grid), dim3(HT), args,
-                              hstep_smem<TF, KP>(), s);
+void hstep_launch(const HalfArgs& a, int grid, cudaStream_t s, int pdl) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(HT);
+  cfg.dynamicSmemBytes = hstep_smem<TF, KP>();
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 2 : 1;
+  cudaLaunchKernelEx(&cfg, hstep_kernel<TF, KP>, a);
 }
 
 }  // namespace
@@ -663,27 +679,28 @@ void launch_half_group(const HalfArgs* probs, const int* bbeg, int np, int grid,
 #undef HGL
 }
 
-void launch_half_tail_flush(HalfTail* tails, int n, cudaStream_t s) {
-  note_launch(1);
-  half_tail_flush_kernel<<<1, 128, 0, s>>>(tails, n);
+void launch_half_tail_flush(HalfTail* tails, int n, int num_sms, cudaStream_t s) {
+  note_launch(2);
+  half_tail_flush_kernel<<<num_sms, 128, 0, s>>>(tails, n);
+  half_tail_clear_kernel<<<1, 32, 0, s>>>(tails, n);
 }
 
-void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s) {
+void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s, int pdl) {
   note_launch(1);
   const int64_t need = (a.rows + RPB - 1) / RPB;
   if ((int64_t)grid > need) grid = (int)need;
   if (grid < 1) grid = 1;
   const int kp = rank_pad16(a.k);
   if (a.fdt == T_F64) {
-    if (kp == 16) hstep_launch<double, 16>(a, grid, s);
-    else if (kp == 32) hstep_launch<double, 32>(a, grid, s);
-    else if (kp == 48) hstep_launch<double, 48>(a, grid, s);
-    else hstep_launch<double, 64>(a, grid, s);
+    if (kp == 16) hstep_launch<double, 16>(a, grid, s, pdl);
+    else if (kp == 32) hstep_launch<double, 32>(a, grid, s, pdl);
+    else if (kp == 48) hstep_launch<double, 48>(a, grid, s, pdl);
+    else hstep_launch<double, 64>(a, grid, s, pdl);
   } else {
-    if (kp == 16) hstep_launch<float, 16>(a, grid, s);
-    else if (kp == 32) hstep_launch<float, 32>(a, grid, s);
-    else if (kp == 48) hstep_launch<float, 48>(a, grid, s);
-    else hstep_launch<float, 64>(a, grid, s);
+    if (kp == 16) hstep_launch<float, 16>(a, grid, s, pdl);
+    else if (kp == 32) hstep_launch<float, 32>(a, grid, s, pdl);
+    else if (kp == 48) hstep_launch<float, 48>(a, grid, s, pdl);
+    else hstep_launch<float, 64>(a, grid, s, pdl);
   }
 }
 

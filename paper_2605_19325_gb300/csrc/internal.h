@@ -209,9 +209,11 @@ struct HalfArgs {
   HalfTail* tail;
 };
 // hstep.cu: one cooperative launch per half step; grid <= half_step_grid().
-void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s);
+// pdl = 1: launched as a programmatic dependent of the previous kernel on s
+// (the blocks wait for its completion before any access).
+void launch_half_step(const HalfArgs& a, int grid, cudaStream_t s, int pdl = 0);
 // Runs tails[0..n) that are pending and clears them (one small launch).
-void launch_half_tail_flush(HalfTail* tails, int n, cudaStream_t s);
+void launch_half_tail_flush(HalfTail* tails, int n, int num_sms, cudaStream_t s);
 int half_step_grid(int fdt, int k, int num_sms, int64_t rows);
 // Grouped half steps of np problems with FP32 factors (HalfArgs in device
 // memory, all with the same `bar`); problem p owns blocks bbeg[p] ..
@@ -330,9 +332,13 @@ void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r,
 // partial slots for the consumer (see CutTiles).
 // xq = 1: the FP8-form kernel (every descriptor's X is e4m3 codes).
 // stages: X stages of the shared-memory ring, 0 = as many as fit (2..8).
+// pdl = 1: launched as a programmatic dependent of the previous kernel on s
+// (the CTAs start while it runs and request their first X tiles; nothing else
+// is read or written before it has completed).  Only where that kernel does
+// not write X.
 void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
                      int* counters, int num_sms, int* err, cudaStream_t s, int fixup = 1,
-                     int xq = 0, int stages = 0);
+                     int xq = 0, int stages = 0, int pdl = 0);
 int tc_group_grid(int64_t W, int num_sms);
 // 2D BF16 tensor map (CUtensorMap, 128 bytes at `map`) over a row-major
 // (rows x cols, ld) array, box box_cols x box_rows, 128-byte swizzle.

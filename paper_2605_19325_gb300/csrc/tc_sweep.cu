@@ -182,6 +182,10 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  // Launched as a programmatic dependent (of the half step that wrote the
+  // factor), the CTA gets here while that kernel may still run: only X, which
+  // no kernel of the iteration writes, is read before griddep_wait().
+  griddep_launch();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -192,7 +196,32 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       int64_t i = 0;
       int64_t q_issued = 0, b_issued = 0;   // XQ: units whose copies were requested
       uint64_t xpol = l2_policy(pv.d->l2hint);
-      for (int64_t w = w0; w < w1 && !*(volatile int*)&aborted; ++w, ++i) {
+      // The X tiles of the first `stages` units (of the first problem) are
+      // requested before the wait; their factor tiles, after it (the stage's
+      // transaction count covers both).  The ring's first pass needs no
+      // empty-slot wait.
+      int64_t pre = 0;
+      if constexpr (!XQ) {
+        const CUtensorMap* mapX = reinterpret_cast<const CUtensorMap*>(pv.d->mapX);
+        for (int64_t w = w0; w < w1 && w < pv.we && pre < stages; ++w, ++pre) {
+          const int64_t lw = w - pv.wb;
+          const int t0 = (int)((lw / pv.nkb) * TILE);
+          const int k0 = (int)((lw % pv.nkb) * KB);
+          uint8_t* sa = smem + (size_t)pre * STAGE;
+          mbar_expect_tx(&full_bar[pre], STAGE);
+          if (MODE == 0) {
+            tma_load_hint(sa, mapX, &full_bar[pre], k0, t0, xpol);
+            tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[pre], k0 + 64, t0, xpol);
+          } else {
+            tma_load_hint(sa, mapX, &full_bar[pre], t0, k0, xpol);
+            tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[pre], t0 + 64, k0, xpol);
+          }
+        }
+      }
+      griddep_wait();
+      // (the prefetched units always get their factor tiles, so that every
+      // stage with copies in flight completes)
+      for (int64_t w = w0; w < w1 && (i < pre || !*(volatile int*)&aborted); ++w, ++i) {
         if (w >= pv.we) {
           pv.load(probs, np, ++p, W);
           xpol = l2_policy(pv.d->l2hint);
@@ -240,7 +269,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
         const CUtensorMap* mapBl = reinterpret_cast<const CUtensorMap*>(pv.d->mapBl);
         const int s = (int)(i % stages);
         const uint32_t ph = (uint32_t)(i / stages) & 1u;
-        if (!mbar_wait(&empty_bar[s], ph ^ 1u, err)) {
+        if (i >= pre && !mbar_wait(&empty_bar[s], ph ^ 1u, err)) {
           aborted = 1;
           break;
         }
@@ -251,14 +280,16 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
         uint8_t* sa = smem + (size_t)s * STAGE;
         uint8_t* sbh = sa + A_BYTES;
         uint8_t* sbl = sbh + B_BYTES;
-        mbar_expect_tx(&full_bar[s], STAGE);
-        if (MODE == 0) {
-          // two adjacent 64-column boxes: 256 contiguous bytes of each X row
-          tma_load_hint(sa, mapX, &full_bar[s], k0, t0, xpol);
-          tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[s], k0 + 64, t0, xpol);
-        } else {
-          tma_load_hint(sa, mapX, &full_bar[s], t0, k0, xpol);
-          tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[s], t0 + 64, k0, xpol);
+        if (i >= pre) {
+          mbar_expect_tx(&full_bar[s], STAGE);
+          if (MODE == 0) {
+            // two adjacent 64-column boxes: 256 contiguous bytes of each X row
+            tma_load_hint(sa, mapX, &full_bar[s], k0, t0, xpol);
+            tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[s], k0 + 64, t0, xpol);
+          } else {
+            tma_load_hint(sa, mapX, &full_bar[s], t0, k0, xpol);
+            tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[s], t0 + 64, k0, xpol);
+          }
         }
         tma_load(sbh, mapBh, &full_bar[s], k0, 0);
         tma_load(sbh + B_BYTES / 2, mapBh, &full_bar[s], k0 + 64, 0);
@@ -282,6 +313,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
   } else if (warp == 1) {
     if (lane == 0) {
       // --------------------------------------------------------- MMA issue
+      griddep_wait();   // (its bounded waits start once the factor can land)
       int p = p0;
       ProbView<KB> pv;
       pv.load(probs, np, p, W);
@@ -380,6 +412,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
     // (c << 4) + ((120 + k) << 7): exponent e + 120 + k, mantissa m << 4.
     // Two codes are converted per 32-bit word as 16-bit lanes; the exponent
     // term is added only in lanes whose code is >= 8.
+    griddep_wait();
     const int ct = threadIdx.x - 192;
     const int sw = ct & 7;
     int p = p0;
@@ -450,6 +483,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
     // ------------------------------------------------------------ epilogue
     // First the previous half step's deferred tail (HalfTail), if any, spread
     // over every CTA's four epilogue warps while the first accumulator fills.
+    griddep_wait();   // the tail, out, corr, part and counters are shared
     {
       const HalfTail* tl = probs[0].tail;
       if (tl && __ldcg(&tl->pending))
@@ -950,7 +984,7 @@ void tc_prob_sizes(int mode, SweepProb* d, int64_t rows_out, int64_t red, int r,
 
 template <int MODE, int RP, bool XQ>
 static void launch_tc(const SweepProb* probs, int np, int64_t W, float* part, int* counters,
-                      int grid, int fixup, int* err, cudaStream_t s, int want_stages) {
+                      int grid, int fixup, int* err, cudaStream_t s, int want_stages, int pdl) {
   const int max_st = tc_stages(MODE, RP);
   const int stages = XQ ? 2 : (want_stages >= 2 && want_stages < max_st ? want_stages : max_st);
   int qstages = 0, bstages = 0;
@@ -958,19 +992,30 @@ static void launch_tc(const SweepProb* probs, int np, int64_t W, float* part, in
   if (XQ) tc_xq_plan(MODE, RP, &bstages, &qstages, &smem);
   cudaFuncSetAttribute(tc::sweep_tc_kernel<MODE, RP, XQ>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  tc::sweep_tc_kernel<MODE, RP, XQ><<<grid, XQ ? tc::THREADS_XQ : tc::THREADS, smem, s>>>(
-      probs, np, W, stages, part, counters, fixup, err, qstages, bstages);
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(XQ ? tc::THREADS_XQ : tc::THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, tc::sweep_tc_kernel<MODE, RP, XQ>, probs, np, W, stages, part, counters,
+                     fixup, err, qstages, bstages);
 }
 
 void launch_tc_group(int mode, int rp, const SweepProb* probs, int np, int64_t W, float* part,
                      int* counters, int num_sms, int* err, cudaStream_t s, int fixup, int xq,
-                     int stages) {
+                     int stages, int pdl) {
   if (np < 1 || W < 1) return;
   const int grid = tc_group_grid(W, num_sms);
   note_launch(1);
 #define TCL(M, P)                                                                       \
-  (xq ? launch_tc<M, P, true>(probs, np, W, part, counters, grid, fixup, err, s, stages) \
-      : launch_tc<M, P, false>(probs, np, W, part, counters, grid, fixup, err, s, stages))
+  (xq ? launch_tc<M, P, true>(probs, np, W, part, counters, grid, fixup, err, s, stages, pdl) \
+      : launch_tc<M, P, false>(probs, np, W, part, counters, grid, fixup, err, s, stages, pdl))
   if (mode == 0) {
     if (rp == 16) TCL(0, 16); else if (rp == 32) TCL(0, 32); else if (rp == 48) TCL(0, 48); else TCL(0, 64);
   } else {
