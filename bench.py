@@ -36,6 +36,12 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "dense planted 8192x6144 r=32, 500 alternations"
 M, N, R, ITERS = 8192, 6144, 32, 500
+# CUDA events bracket the main X pass of every PROF_EVERY-th alternation
+# (enmf_profile).  Each pair of event nodes in the replayed graph costs about
+# 10 us of stream time (measured: 500 alternations 40.2 ms without events,
+# 42.8 ms with a pair around both sweeps of every 4th alternation), so the
+# sample is kept to every 16th: 62 sweeps per solve.
+PROF_EVERY = 16
 METRIC = "eNMF solves/s (time to the FP64-GPU target rel. Frobenius error; p50/p99 ms)"
 
 
@@ -301,7 +307,7 @@ def fp8_leg(forms=("fp8", "bf16", "f32", "f64")):
         solve()
         torch.cuda.synchronize()
         if xs is not None:
-            B.enmf_profile(s.ctx, 4)
+            B.enmf_profile(s.ctx, PROF_EVERY)
             B.enmf_profile_read(s.ctx, reset=1)
         t0 = time.perf_counter()
         rel = solve()
@@ -377,7 +383,7 @@ def image_leg(iters=500):
             continue
         solve(s)
         torch.cuda.synchronize()
-        B.enmf_profile(s.ctx, 4)
+        B.enmf_profile(s.ctx, PROF_EVERY)
         B.enmf_profile_read(s.ctx, reset=1)
         t0 = time.perf_counter()
         rel = solve(s)
@@ -667,7 +673,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         solve_once(s, ITERS)
     torch.cuda.synchronize()
-    B.enmf_profile(s.ctx, 4)
+    B.enmf_profile(s.ctx, PROF_EVERY)
     B.enmf_profile_read(s.ctx, reset=1)
     clocks = ClockSampler(local)
     clocks.start()
@@ -706,7 +712,7 @@ def run_ours(args):
         shape = B.enmf_fused_shape(s.ctx)
         solve_once(s, ITERS)
         torch.cuda.synchronize()
-        B.enmf_profile(s.ctx, 4)
+        B.enmf_profile(s.ctx, PROF_EVERY)
         B.enmf_profile_read(s.ctx, reset=1)
         t0 = time.perf_counter()
         rel_fz = solve_once(s, ITERS)
@@ -736,7 +742,7 @@ def run_ours(args):
         so = make_solver(other)
         solve_once(so, ITERS)
         torch.cuda.synchronize()
-        B.enmf_profile(so.ctx, 4)
+        B.enmf_profile(so.ctx, PROF_EVERY)
         B.enmf_profile_read(so.ctx, reset=1)
         t0 = time.perf_counter()
         rel_o = solve_once(so, ITERS)

@@ -283,12 +283,16 @@ negmass_partial(const TF* __restrict__ F, int64_t total, double* part) {
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// One warp: lane l sums partials l, l + 32, ... in order, then a fixed xor
+// tree (every lane ends with the same sum).
 __global__ void part_sum_to(const double* part, int count, double* out, int accumulate) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < count; ++b) s += part[b];
-    out[0] = accumulate ? out[0] + s : s;
-  }
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = lane; b < count; b += 32) s += __ldcg(part + b);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[0] = accumulate ? out[0] + s : s;
 }
 
 void launch_negmass(const void* F, int64_t rows, int k, int fdt, double* part, double* out,

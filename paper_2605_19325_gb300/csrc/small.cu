@@ -133,6 +133,66 @@ __device__ int jacobi_osvd(T* A, int rows, int Np, T* V, int max_sweeps) {
   return sweep;
 }
 
+// FP32 instance, where the FP32 rate leaves the syncs as the cost: one warp
+// per pair of a round forms the three dot products (a fixed xor tree, so
+// every lane holds the same sums), computes the rotation and applies it, and
+// a round is one __syncthreads.  The same rotation rule and tolerance as
+// jacobi_osvd.
+__device__ int jacobi_osvd_f32(float* A, int rows, int Np, float* V, int max_sweeps) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int npairs = Np / 2;
+  const float tol = 1e-6f * (float)(rows > 8 ? rows : 8);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) jac_rotated = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < Np - 1; ++rnd) {
+      for (int pi = warp; pi < npairs; pi += SM_WARPS) {
+        int p, q;
+        rr_pair(pi, rnd, Np, p, q);
+        float* ap = A + (size_t)p * rows;
+        float* aq = A + (size_t)q * rows;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int i = lane; i < rows; i += 32) {
+          const float x = ap[i], y = aq[i];
+          al = fmaf(x, x, al);
+          be = fmaf(y, y, be);
+          ga = fmaf(x, y, ga);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
+          const float z = (be - al) / (2.f * ga);
+          const float t = (z >= 0.f ? 1.f : -1.f) / (fabsf(z) + sqrtf(1.f + z * z));
+          const float c = 1.f / sqrtf(1.f + t * t);
+          const float sn = c * t;
+          if (lane == 0) jac_rotated = 1;
+          for (int i = lane; i < rows; i += 32) {
+            const float x = ap[i], y = aq[i];
+            ap[i] = c * x - sn * y;
+            aq[i] = sn * x + c * y;
+          }
+          float* vp = V + (size_t)p * Np;
+          float* vq = V + (size_t)q * Np;
+          for (int i = lane; i < Np; i += 32) {
+            const float x = vp[i], y = vq[i];
+            vp[i] = c * x - sn * y;
+            vq[i] = sn * x + c * y;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!jac_rotated) break;
+    __syncthreads();
+  }
+  return sweep;
+}
+
 // The same one-sided Jacobi in two precisions: sweeps in FP32 (64 times the
 // FP64 rate on this GPU) to single-precision orthogonality of A's columns,
 // then the accumulated rotation V32 -- orthogonal only to FP32 rounding -- is
@@ -147,7 +207,7 @@ __device__ int jacobi_osvd_mixed(double* A, int rows, int Np, double* V, float* 
   for (int e = threadIdx.x; e < Np * rows; e += SM_T) A32[e] = (float)A[e];
   for (int e = threadIdx.x; e < Np * Np; e += SM_T) V32[e] = (e / Np == e % Np) ? 1.f : 0.f;
   __syncthreads();
-  jacobi_osvd<float>(A32, rows, Np, V32, JAC_MAX_SWEEPS);
+  jacobi_osvd_f32(A32, rows, Np, V32, JAC_MAX_SWEEPS);
   // two Newton-Schulz steps V <- V (3 I - V^T V) / 2 in FP64 from V = V32
   // (an orthogonality error e becomes about e^2 per step); V^T V goes to T,
   // the new V to registers first (column-major: V[c * Np + i] is entry (i, c))
@@ -525,7 +585,7 @@ rr_svd_kernel(const double* __restrict__ P, int k2, int k1, double* sigma, doubl
     for (int e = threadIdx.x; e < Np * k1; e += SM_T) A32[e] = (float)A[e];
     for (int e = threadIdx.x; e < Np * Np; e += SM_T) V32[e] = (e / Np == e % Np) ? 1.f : 0.f;
     __syncthreads();
-    sw = jacobi_osvd<float>(A32, k1, Np, V32, JAC_MAX_SWEEPS);
+    sw = jacobi_osvd_f32(A32, k1, Np, V32, JAC_MAX_SWEEPS);
     for (int e = threadIdx.x; e < Np * k1; e += SM_T) A[e] = (double)A32[e];
     for (int e = threadIdx.x; e < Np * Np; e += SM_T) V[e] = (double)V32[e];
     __syncthreads();

@@ -426,20 +426,38 @@ gram_partial(const TF* __restrict__ A, int lda, int ka, const TF* __restrict__ B
 // Eight interleaved accumulators (partial b goes to accumulator b % 8), then a
 // fixed pairwise combine: the order is fixed, so the sum is reproducible, and
 // the eight independent chains hide the load latency.
-__global__ void part_reduce(const double* __restrict__ part, int width, double* __restrict__ out) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < width; e += gridDim.x * blockDim.x) {
-    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll 4
-    for (int b = 0; b < NPART; b += 8)
+// Fixed-order sum of the NPART block partials of each of `width` entries:
+// block b takes entries 32 b .. 32 b + 31 (one per lane), warp w sums
+// partials 32 w .. 32 w + 31 of its lane's entry in four chains, and the
+// eight warp sums are added in a fixed tree.
+static_assert(NPART == 256, "part_reduce: eight warps of 32 partials");
+__global__ void __launch_bounds__(256)
+part_reduce(const double* __restrict__ part, int width, double* __restrict__ out) {
+  __shared__ double ws[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  if (e < width) {
+    const double* p = part + (int64_t)(w * 32) * width + e;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) a[q] += part[(int64_t)(b + q) * width + e];
-    out[e] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    for (int b = 0; b < 32; b += 4)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] += __ldcg(p + (int64_t)(b + q) * width);
   }
+  ws[w][lane] = (a[0] + a[1]) + (a[2] + a[3]);
+  __syncthreads();
+  if (w == 0 && e < width)
+    out[e] = ((ws[0][lane] + ws[1][lane]) + (ws[2][lane] + ws[3][lane])) +
+             ((ws[4][lane] + ws[5][lane]) + (ws[6][lane] + ws[7][lane]));
+}
+
+static void part_reduce_launch(const double* part, int width, double* out, cudaStream_t s) {
+  part_reduce<<<(width + 31) / 32, 256, 0, s>>>(part, width, out);
 }
 
 void launch_part_reduce(const double* part, int width, double* out, cudaStream_t s) {
   note_launch(1);
-  part_reduce<<<(width + 255) / 256, 256, 0, s>>>(part, width, out);
+  part_reduce_launch(part, width, out, s);
 }
 
 void launch_gram(const void* A, int lda, int ka, const void* B, int ldb, int kb, int64_t rows,
@@ -450,7 +468,7 @@ void launch_gram(const void* A, int lda, int ka, const void* B, int ldb, int kb,
   else
     gram_partial<float><<<NPART, GRAM_T, 0, s>>>((const float*)A, lda, ka, (const float*)B, ldb, kb, rows, part);
   int w = ka * kb;
-  part_reduce<<<(w + 255) / 256, 256, 0, s>>>(part, w, G);
+  part_reduce_launch(part, w, G, s);
 }
 
 // ------------------------------------------------------------ dot product
@@ -479,7 +497,7 @@ void launch_dot(const void* A, int lda, const void* B, int ldb, int k, int64_t r
     dot_partial<double><<<NPART, 256, 0, s>>>((const double*)A, lda, (const double*)B, ldb, k, rows, part);
   else
     dot_partial<float><<<NPART, 256, 0, s>>>((const float*)A, lda, (const float*)B, ldb, k, rows, part);
-  part_reduce<<<1, 32, 0, s>>>(part, 1, out);
+  part_reduce_launch(part, 1, out, s);
 }
 
 // ---------------------------------------------------------------- ||X||^2
@@ -553,6 +571,59 @@ normx2_partial(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// FP32 X with 16-byte aligned rows: the same sums, each thread reading four
+// adjacent entries of eight rows per step (128 bytes in flight per thread
+// instead of 32; the scalar form left the pass latency-bound at about a
+// seventh of the memory bandwidth).  The four entries go into the row's pair
+// in column order.
+__device__ __forceinline__ void sq4(const float4 v, float& hi, float& lo, int& bad) {
+  const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (!(e[c] >= 0.f) || isinf(e[c])) bad = 1;
+    two_sum_sq(e[c], hi, lo);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+normx2_partial_f4(const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
+                  double* __restrict__ part, int* err) {
+  __shared__ double sh[256];
+  const int64_t chunk = (m + NPART - 1) / NPART;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(m, r0 + chunk);
+  const int64_t n4 = n / 4;
+  int bad = 0;
+  float hi[8], lo[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) hi[u] = lo[u] = 0.f;
+  for (int64_t i = r0; i < r1; i += 8) {
+    for (int64_t j4 = threadIdx.x; j4 < n4; j4 += blockDim.x) {
+      float4 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        x[u] = i + u < r1 ? __ldg(reinterpret_cast<const float4*>(X + (i + u) * ldx) + j4)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sq4(x[u], hi[u], lo[u], bad);
+    }
+    for (int64_t j = 4 * n4 + threadIdx.x; j < n; j += blockDim.x) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float x = i + u < r1 ? X[(i + u) * ldx + j] : 0.f;
+        if (!(x >= 0.f) || isinf(x)) bad = 1;
+        two_sum_sq(x, hi[u], lo[u]);
+      }
+    }
+  }
+  double d8[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) d8[u] = (double)hi[u] + (double)lo[u];
+  double sum = ((d8[0] + d8[1]) + (d8[2] + d8[3])) + ((d8[4] + d8[5]) + (d8[6] + d8[7]));
+  if (bad) atomicOr(err, ERR_DOMAIN);
+  sum = block_sum(sum, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = sum;
+}
+
 void launch_normx2(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, double* part,
                    double* out, int* err, cudaStream_t s) {
   if (xdt == T_CSR) {
@@ -561,10 +632,12 @@ void launch_normx2(const void* X, int xdt, int64_t m, int64_t n, int64_t ldx, do
   }
   note_launch(2);
   if (xdt == T_F64) normx2_partial<double><<<NPART, 256, 0, s>>>((const double*)X, m, n, ldx, part, err);
+  else if (xdt == T_F32 && ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0)
+    normx2_partial_f4<<<NPART, 256, 0, s>>>((const float*)X, m, n, ldx, part, err);
   else if (xdt == T_F32) normx2_partial<float><<<NPART, 256, 0, s>>>((const float*)X, m, n, ldx, part, err);
   else if (xdt == T_BF16) normx2_partial<__nv_bfloat16><<<NPART, 256, 0, s>>>((const __nv_bfloat16*)X, m, n, ldx, part, err);
   else normx2_partial<__half><<<NPART, 256, 0, s>>>((const __half*)X, m, n, ldx, part, err);
-  part_reduce<<<1, 32, 0, s>>>(part, 1, out);
+  part_reduce_launch(part, 1, out, s);
 }
 
 // ------------------------------------------------------- direct residual
@@ -727,7 +800,7 @@ void launch_residual_direct(const void* X, int xdt, int64_t m, int64_t n, int64_
     else residual32_launch<__half>(X, m, n, ldx, U, V, r, part, s);
   }
 #undef RD_LAUNCH
-  part_reduce<<<1, 32, 0, s>>>(part, 1, out);
+  part_reduce_launch(part, 1, out, s);
 }
 
 // ------------------------------------------------------------------ Omega

@@ -105,6 +105,13 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
   constexpr uint32_t A_BYTES = TILE * KB * 2;                 // 16 KB or 32 KB
   constexpr uint32_t B_BYTES = RP * KB * 2;                   // one of hi / lo
   constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
+  // non-FP8 forms: X V's X tile is KB / 64 boxes of 64 columns side by side;
+  // the factor's hi and lo tiles are KB / 64 boxes of 64 K elements each
+  constexpr int NBOX = KB / 64;
+  constexpr uint32_t BOXA = TILE * 64 * 2;
+  constexpr uint32_t BOXB = RP * 64 * 2;
+  static_assert(KB % 64 == 0 && (MODE == 0 || KB == 128) && (!XQ || KB == 128),
+                "X^T U and the FP8 form take 128-row stages");
   // XQ: the factor tiles live in a ring of their own, so a stage is A only
   constexpr uint32_t ASTAGE = XQ ? A_BYTES : STAGE;
   constexpr uint32_t BSLOT = 2 * B_BYTES;   // [hi | lo | hi | lo] boxes of one unit
@@ -142,6 +149,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
   const int64_t w0 = sk_begin(blockIdx.x, W, G), w1 = sk_begin(blockIdx.x + 1, W, G);
   const int p0 = w0 < w1 ? prob_find(probs, np, w0) : 0;
 
+  int64_t pre = 0;   // (thread 0) units whose X tiles were requested in the prologue
   if (threadIdx.x == 0) {
     if (w0 < w1) {
       prefetch_map(reinterpret_cast<const CUtensorMap*>(probs[p0].mapX));
@@ -170,6 +178,34 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
     mbar_init(&drain_bar, 1);
     aborted = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // Thread 0 is the producer.  The X tiles of the first `stages` units (of
+    // the first problem) are requested now, before the tensor-memory
+    // allocation and before the wait for the previous kernel; their factor
+    // tiles after that wait (the stage's transaction count covers both).
+    // The ring's first pass needs no empty-slot wait.
+    if constexpr (!XQ) {
+      if (w0 < w1) {
+        ProbView<KB> pv;
+        pv.load(probs, np, p0, W);
+        const uint64_t xpol = l2_policy(pv.d->l2hint);
+        const CUtensorMap* mapX = reinterpret_cast<const CUtensorMap*>(pv.d->mapX);
+        for (int64_t w = w0; w < w1 && w < pv.we && pre < stages; ++w, ++pre) {
+          const int64_t lw = w - pv.wb;
+          const int t0 = (int)((lw / pv.nkb) * TILE);
+          const int k0 = (int)((lw % pv.nkb) * KB);
+          uint8_t* sa = smem + (size_t)pre * STAGE;
+          mbar_expect_tx(&full_bar[pre], STAGE);
+          if (MODE == 0) {
+#pragma unroll
+            for (int bx = 0; bx < NBOX; ++bx)
+              tma_load_hint(sa + bx * BOXA, mapX, &full_bar[pre], k0 + 64 * bx, t0, xpol);
+          } else {
+            tma_load_hint(sa, mapX, &full_bar[pre], t0, k0, xpol);
+            tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[pre], t0 + 64, k0, xpol);
+          }
+        }
+      }
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -196,28 +232,6 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
       int64_t i = 0;
       int64_t q_issued = 0, b_issued = 0;   // XQ: units whose copies were requested
       uint64_t xpol = l2_policy(pv.d->l2hint);
-      // The X tiles of the first `stages` units (of the first problem) are
-      // requested before the wait; their factor tiles, after it (the stage's
-      // transaction count covers both).  The ring's first pass needs no
-      // empty-slot wait.
-      int64_t pre = 0;
-      if constexpr (!XQ) {
-        const CUtensorMap* mapX = reinterpret_cast<const CUtensorMap*>(pv.d->mapX);
-        for (int64_t w = w0; w < w1 && w < pv.we && pre < stages; ++w, ++pre) {
-          const int64_t lw = w - pv.wb;
-          const int t0 = (int)((lw / pv.nkb) * TILE);
-          const int k0 = (int)((lw % pv.nkb) * KB);
-          uint8_t* sa = smem + (size_t)pre * STAGE;
-          mbar_expect_tx(&full_bar[pre], STAGE);
-          if (MODE == 0) {
-            tma_load_hint(sa, mapX, &full_bar[pre], k0, t0, xpol);
-            tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[pre], k0 + 64, t0, xpol);
-          } else {
-            tma_load_hint(sa, mapX, &full_bar[pre], t0, k0, xpol);
-            tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[pre], t0 + 64, k0, xpol);
-          }
-        }
-      }
       griddep_wait();
       // (the prefetched units always get their factor tiles, so that every
       // stage with copies in flight completes)
@@ -283,18 +297,20 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
         if (i >= pre) {
           mbar_expect_tx(&full_bar[s], STAGE);
           if (MODE == 0) {
-            // two adjacent 64-column boxes: 256 contiguous bytes of each X row
-            tma_load_hint(sa, mapX, &full_bar[s], k0, t0, xpol);
-            tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[s], k0 + 64, t0, xpol);
+            // adjacent 64-column boxes: KB * 2 contiguous bytes of each X row
+#pragma unroll
+            for (int bx = 0; bx < NBOX; ++bx)
+              tma_load_hint(sa + bx * BOXA, mapX, &full_bar[s], k0 + 64 * bx, t0, xpol);
           } else {
             tma_load_hint(sa, mapX, &full_bar[s], t0, k0, xpol);
             tma_load_hint(sa + A_BYTES / 2, mapX, &full_bar[s], t0 + 64, k0, xpol);
           }
         }
-        tma_load(sbh, mapBh, &full_bar[s], k0, 0);
-        tma_load(sbh + B_BYTES / 2, mapBh, &full_bar[s], k0 + 64, 0);
-        tma_load(sbl, mapBl, &full_bar[s], k0, 0);
-        tma_load(sbl + B_BYTES / 2, mapBl, &full_bar[s], k0 + 64, 0);
+#pragma unroll
+        for (int bx = 0; bx < NBOX; ++bx) {
+          tma_load(sbh + bx * BOXB, mapBh, &full_bar[s], k0 + 64 * bx, 0);
+          tma_load(sbl + bx * BOXB, mapBl, &full_bar[s], k0 + 64 * bx, 0);
+        }
       }
       if (aborted) {
         // let copies already issued land before the CTA can exit
@@ -372,8 +388,8 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
             if (MODE == 0) {
               // K-major A and B: 16 elements = 32 bytes along the swizzled row;
               // K steps 4..7 live in the second 64-column box
-              const uint32_t aoff = (uint32_t)(kk / 4) * (A_BYTES / 2) + (uint32_t)(kk % 4) * 32;
-              const uint32_t boff = (uint32_t)(kk / 4) * (B_BYTES / 2) + (uint32_t)(kk % 4) * 32;
+              const uint32_t aoff = (uint32_t)(kk / 4) * BOXA + (uint32_t)(kk % 4) * 32;
+              const uint32_t boff = (uint32_t)(kk / 4) * BOXB + (uint32_t)(kk % 4) * 32;
               da = sdesc(a0 + aoff, 16, 1024);
               dbh = sdesc(bh0 + boff, 16, 1024);
               dbl = sdesc(bl0 + boff, 16, 1024);
@@ -381,7 +397,7 @@ sweep_tc_kernel(const SweepProb* __restrict__ probs, int np, int64_t W, int stag
               // MN-major A: 16 reduction rows = 2 x 1024 B; two 64-wide atoms
               // along the output index, 16 KB apart.  B: 64-element K atoms.
               da = sdesc(a0 + kk * 2048, A_BYTES / 2, 1024);
-              const uint32_t boff = (uint32_t)(kk / 4) * (B_BYTES / 2) + (uint32_t)(kk % 4) * 32;
+              const uint32_t boff = (uint32_t)(kk / 4) * BOXB + (uint32_t)(kk % 4) * 32;
               dbh = sdesc(bh0 + boff, 16, 1024);
               dbl = sdesc(bl0 + boff, 16, 1024);
             }
