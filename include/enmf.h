@@ -193,6 +193,25 @@ typedef struct {
 enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* R,
                         const enmf_admm_opts* opts, enmf_rotate_info* info);
 
+/* The rotation of Algorithm 1 for `count` problems at once (no counterpart in
+ * the paper; a serving aid): ctxs[i] with its factors U[i], V[i] (device),
+ * each exactly as enmf_rotate(ctxs[i], U[i], V[i], NULL, opts, &infos[i])
+ * would leave them, bit for bit, but the FP32 ADMM steps of many problems
+ * run in one cooperative grid: problem i gets the blocks its own launch
+ * would have, its polar factor is formed on its own first block, so the
+ * per-step polar factors of the problems are formed side by side.  Problems
+ * are packed into as few grids as the device holds.  Every context must have
+ * FP32 factors, the same rank pad (16, 32, 48 or 64) and the same stream;
+ * opts->f64 must be 0; no context may appear twice (else ENMF_EINVAL, before
+ * any launch).  infos (may be NULL) receives count records.  Synchronises
+ * twice per call (the rho inputs, then the results).  Returns the first
+ * non-OK status of the problems in order; ENMF_ENOTCONV (a polar iteration
+ * that did not settle) leaves results and infos as enmf_rotate does, a
+ * device-side failure poisons the contexts whose problems it concerns. */
+enmf_status enmf_rotate_group(enmf_ctx* const* ctxs, void* const* U, void* const* V,
+                              int32_t count, const enmf_admm_opts* opts,
+                              enmf_rotate_info* infos);
+
 /* ---- 2b. Generalized rotation (Eq. 5, Algorithm 4, App. A.2) -----------
  * Orthogonal R1, R2 and diagonal Lambda > 0 that bring U* R1 Lambda R2 and
  * V* R1 Lambda^-1 R2 toward the orthant (the product U V^T is unchanged).

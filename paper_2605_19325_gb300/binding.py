@@ -131,6 +131,9 @@ _SIGS = {
                                 C.POINTER(enmf_svd_opts), C.POINTER(enmf_svd_info)]),
     "enmf_rotate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.POINTER(enmf_admm_opts), C.POINTER(enmf_rotate_info)]),
+    "enmf_rotate_group": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                    C.POINTER(C.c_void_p), C.c_int32,
+                                    C.POINTER(enmf_admm_opts), C.POINTER(enmf_rotate_info)]),
     "enmf_iterate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.POINTER(enmf_iter_opts), C.POINTER(enmf_iter_info)]),
     "enmf_pbcd_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
@@ -257,6 +260,22 @@ def enmf_rotate(ctx, U, V, R=None, opts=None):
     if code not in (0, 6):
         check(code, "enmf_rotate")
     return info, code
+
+
+def enmf_rotate_group(ctxs, Us, Vs, opts=None):
+    """Algorithm 1 for several contexts at once (FP32 factors, one rank pad,
+    one stream); returns (per-problem infos, status), status 0 or ENOTCONV
+    (6) as enmf_rotate."""
+    n = len(ctxs)
+    cs = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    us = (C.c_void_p * n)(*[U.data_ptr() for U in Us])
+    vs = (C.c_void_p * n)(*[V.data_ptr() for V in Vs])
+    infos = (enmf_rotate_info * n)()
+    code = lib().enmf_rotate_group(cs, us, vs, n, C.byref(opts) if opts is not None else None,
+                                   infos)
+    if code not in (0, 6):
+        check(code, "enmf_rotate_group")
+    return list(infos), code
 
 
 def enmf_stage_x(ctx, X):

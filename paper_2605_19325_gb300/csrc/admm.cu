@@ -311,27 +311,15 @@ __device__ void polar_block(const double* __restrict__ Mg, int k, double* R, dou
   }
 }
 
-struct AdmmArgs {
-  const float* U;
-  const float* V;
-  int64_t m, n;
-  int k;
-  double* R;       // k x k FP64, R_k in, R at exit out
-  float* Z;        // (m + n) x k
-  float* Y;        // (m + n) x k, zero at entry
-  double rho;
-  int max_iter;
-  double tol;
-  DevState* st;
-  double* part;    // grid x k x k FP64
-  double* M;       // k x k FP64
-  int* err;
-};
-
-template <int KP>
-__global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) {
+// The steps of one problem on its blocks lb = 0 .. nb - 1 (a whole grid, or
+// a problem's share of a grouped grid); every grid barrier is `bar`, which
+// all blocks of the grid pass.  GROUP: other problems share the grid, so a
+// problem whose stop rule held keeps passing the barriers (without work)
+// until max_iter instead of leaving the loop.
+template <int KP, bool GROUP>
+__device__ __forceinline__ void admm_body(const AdmmArgs& a, int lb, int nb, GridBarrier* bar,
+                                          unsigned char* smraw, double* sh, float* pv) {
   constexpr int E = KP / LPR, S = KP / 16;
-  extern __shared__ __align__(16) unsigned char smraw[];
   float* Rs = reinterpret_cast<float*>(smraw);
   float* ws = Rs + KP * KP;
   float* bs = ws + ARPB * KP;
@@ -341,8 +329,6 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
   float* Y = Rs;                       // region A, polar only
   float* YT = Y + KP * polar_ld<KP>();
   float* wz = P + KP * polar_ld<KP>();  // resident rows: w | z | y, ARPB x KP each
-  __shared__ double sh[AT];
-  __shared__ float pv[KP + 1];
 
   const int k = a.k, kk = k * k;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -350,7 +336,7 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
   const int rloc = warp * (32 / LPR) + lane / LPR;
   DevState* st = a.st;
   const int64_t m = a.m, rows = a.m + a.n;
-  const int64_t passes = (rows + (int64_t)gridDim.x * ARPB - 1) / ((int64_t)gridDim.x * ARPB);
+  const int64_t passes = (rows + (int64_t)nb * ARPB - 1) / ((int64_t)nb * ARPB);
   const float rho = (float)a.rho;
   const float thr = -1.f / rho;
 
@@ -364,7 +350,7 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
   float* zrow = wrow + ARPB * KP;
   float* yrow = zrow + ARPB * KP;
   if (resident) {
-    const int64_t i = (int64_t)blockIdx.x * ARPB + rloc;
+    const int64_t i = (int64_t)lb * ARPB + rloc;
     const bool live = i < rows;
     float w[E], z[E], y[E];
     if (i < m) load_row(a.U, i, live, k, sub, w);
@@ -387,7 +373,14 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
       const int e = t + AT * q, i = e / KP, j = e % KP;
       rv[q] = (e < KP * KP && i < k && j < k) ? (float)__ldcg(&a.R[i * k + j]) : 0.f;
     }
-    if (done) break;
+    if (done) {
+      if (!GROUP) break;
+      // (the three barriers of the step, without its work)
+      grid_sync(bar, a.err);
+      grid_sync(bar, a.err);
+      grid_sync(bar, a.err);
+      continue;
+    }
 #pragma unroll
     for (int q = 0; q < NR; ++q)
       if (t + AT * q < KP * KP) Rs[t + AT * q] = rv[q];
@@ -398,7 +391,7 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
 #pragma unroll
       for (int s2 = 0; s2 < S; ++s2) acc[s1][s2] = 0.f;
     for (int64_t ps = 0; ps < passes; ++ps) {
-      const int64_t i = (ps * gridDim.x + blockIdx.x) * ARPB + rloc;
+      const int64_t i = (ps * nb + lb) * ARPB + rloc;
       const bool live = i < rows;
       float w[E], z[E], y[E], p[E], bv[E];
       if (resident) {
@@ -451,18 +444,17 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
 #pragma unroll
         for (int s2 = 0; s2 < S; ++s2) {
           const int pr = bi * S + s1, pc = bj * S + s2;
-          if (pr < k && pc < k) a.part[(int64_t)blockIdx.x * kk + pr * k + pc] = (double)acc[s1][s2];
+          if (pr < k && pc < k) a.part[(int64_t)lb * kk + pr * k + pc] = (double)acc[s1][s2];
         }
     }
-    grid_sync(&st->bar, a.err);
-    sum_block_partials<AT>(a.part, (int)gridDim.x, kk, a.M);
-    grid_sync(&st->bar, a.err);
-    if (blockIdx.x == 0)
-      polar_block<KP>(a.M, k, a.R, a.tol, st, a.err, X, XT, Y, YT, P, pv, step, sh);
-    grid_sync(&st->bar, a.err);
+    grid_sync(bar, a.err);
+    sum_block_partials<AT>(a.part, nb, kk, a.M, 0, lb, nb);
+    grid_sync(bar, a.err);
+    if (lb == 0) polar_block<KP>(a.M, k, a.R, a.tol, st, a.err, X, XT, Y, YT, P, pv, step, sh);
+    grid_sync(bar, a.err);
   }
   if (resident) {
-    const int64_t i = (int64_t)blockIdx.x * ARPB + rloc;
+    const int64_t i = (int64_t)lb * ARPB + rloc;
     float z[E], y[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -472,6 +464,41 @@ __global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) 
     store_row(a.Z, i, i < rows, k, sub, z);
     store_row(a.Y, i, i < rows, k, sub, y);
   }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2) admm_kernel(AdmmArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[AT];
+  __shared__ float pv[KP + 1];
+  admm_body<KP, false>(a, (int)blockIdx.x, (int)gridDim.x, &a.st->bar, smraw, sh, pv);
+}
+
+// Several problems of one rank pad in one cooperative grid: problem p owns
+// blocks bbeg[p] .. bbeg[p + 1] - 1, as many as its own launch would have,
+// so every problem's arithmetic (row partition, partial sums, polar) is that
+// of its own launch; the barriers are `bar` for all.
+template <int KP>
+__global__ void __launch_bounds__(AT, KP <= 32 ? 3 : 2)
+admm_group_kernel(const AdmmArgs* __restrict__ probs, const int* __restrict__ bbeg, int np,
+                  GridBarrier* bar) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[AT];
+  __shared__ float pv[KP + 1];
+  __shared__ int p_s;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (bbeg[mid] <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    p_s = lo;
+  }
+  __syncthreads();
+  const int p = p_s;
+  const AdmmArgs a = probs[p];
+  admm_body<KP, true>(a, (int)blockIdx.x - bbeg[p], bbeg[p + 1] - bbeg[p], bar, smraw, sh, pv);
 }
 
 template <int KP>
@@ -495,7 +522,39 @@ void admm_launch(const AdmmArgs& a, int num_sms, cudaStream_t s) {
                               admm_smem<KP>(), s);
 }
 
+template <int KP>
+void admm_group_launch(const AdmmArgs* probs, const int* bbeg, int np, int grid,
+                       GridBarrier* bar, cudaStream_t s) {
+  cudaFuncSetAttribute(admm_group_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)admm_smem<KP>());
+  void* args[] = {(void*)&probs, (void*)&bbeg, (void*)&np, (void*)&bar};
+  cudaLaunchCooperativeKernel((void*)admm_group_kernel<KP>, dim3((unsigned)grid), dim3(AT), args,
+                              admm_smem<KP>(), s);
+}
+
 }  // namespace
+
+int admm_group_capacity(int kp, int num_sms) {
+  return kp == 16 ? admm_capacity<16>(num_sms) : kp == 32 ? admm_capacity<32>(num_sms)
+         : kp == 48 ? admm_capacity<48>(num_sms) : admm_capacity<64>(num_sms);
+}
+
+int admm_blocks(int kp, int64_t rows, int num_sms) {
+  const int64_t need = (rows + ARPB - 1) / ARPB;
+  int64_t grid = admm_group_capacity(kp, num_sms);
+  if (grid > NPART) grid = NPART;
+  if (grid > need) grid = need;
+  return grid < 1 ? 1 : (int)grid;
+}
+
+void launch_admm_group(const AdmmArgs* probs, const int* bbeg, int np, int grid, int kp,
+                       GridBarrier* bar, cudaStream_t s) {
+  note_launch(1);
+  if (kp == 16) admm_group_launch<16>(probs, bbeg, np, grid, bar, s);
+  else if (kp == 32) admm_group_launch<32>(probs, bbeg, np, grid, bar, s);
+  else if (kp == 48) admm_group_launch<48>(probs, bbeg, np, grid, bar, s);
+  else admm_group_launch<64>(probs, bbeg, np, grid, bar, s);
+}
 
 void launch_admm_f32(const float* U, const float* V, int64_t m, int64_t n, int k, double* R,
                      float* Z, float* Y, double rho, int max_iter, double tol, DevState* st,

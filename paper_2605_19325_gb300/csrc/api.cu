@@ -730,6 +730,153 @@ extern "C" enmf_status enmf_rotate(enmf_ctx* ctx, void* U, void* V, double* Rout
   return rc;
 }
 
+extern "C" enmf_status enmf_rotate_group(enmf_ctx* const* ctxs, void* const* U, void* const* V,
+                                         int32_t count, const enmf_admm_opts* opts,
+                                         enmf_rotate_info* infos) {
+  if (!ctxs || !U || !V || count < 1) return ENMF_EINVAL;
+  enmf_admm_opts o = {0.0, 3.0, 200, 1e-12, 0};
+  if (opts) {
+    o = *opts;
+    if (o.max_iter < 1 || !(o.tol >= 0) || (o.rho <= 0 && !(o.rho_scale > 0)) || o.f64)
+      return ENMF_EINVAL;
+  }
+  if (!ctxs[0]) return ENMF_EINVAL;
+  cudaStream_t s = ctxs[0]->stream;
+  const int kp = tc_rank_pad(ctxs[0]->p.r);
+  for (int i = 0; i < count; ++i) {
+    enmf_ctx* ctx = ctxs[i];
+    if (!ctx || !U[i] || !V[i]) return ENMF_EINVAL;
+    if (ctx->poison) return ctx->poison;
+    if (ctx->fdt != T_F32 || ctx->stream != s || ctx->device != ctxs[0]->device ||
+        tc_rank_pad(ctx->p.r) != kp)
+      return ENMF_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctx) return ENMF_EINVAL;
+  }
+  // a failed CUDA call poisons every context of the group
+  auto fail = [&](cudaError_t e) {
+    if (e == cudaSuccess) return false;
+    for (int i = 0; i < count; ++i) ctxs[i]->poison = ENMF_ECUDA;
+    return true;
+  };
+  // negative mass before and ||W||_F^2 for rho, all problems, one round trip
+  for (int i = 0; i < count; ++i) {
+    enmf_ctx* ctx = ctxs[i];
+    const int64_t m = ctx->p.m, n = ctx->p.n;
+    const int k = ctx->p.r;
+    launch_negmass(U[i], m, k, T_F32, ctx->part, &ctx->scal[1], 0, s);
+    launch_negmass(V[i], n, k, T_F32, ctx->part, &ctx->scal[1], 1, s);
+    launch_dot(U[i], k, U[i], k, k, m, T_F32, ctx->part, &ctx->scal[2], s);
+    launch_dot(V[i], k, V[i], k, k, n, T_F32, ctx->part, &ctx->scal[3], s);
+  }
+  for (int i = 0; i < count; ++i) {
+    const enmf_status rc = check_launch(ctxs[i]);
+    if (rc) return rc;
+  }
+  std::vector<double> hs((size_t)count * 4);
+  for (int i = 0; i < count; ++i)
+    if (fail(cudaMemcpyAsync(&hs[(size_t)i * 4], ctxs[i]->scal, 4 * sizeof(double),
+                             cudaMemcpyDeviceToHost, s)))
+      return ENMF_ECUDA;
+  for (int i = 0; i < count; ++i) {
+    const enmf_status rc = sync_status(ctxs[i]);
+    if (rc) return rc;
+  }
+  // the problems' descriptors, packed into grids of at most `cap` blocks
+  const int cap = admm_group_capacity(kp, ctxs[0]->num_sms);
+  std::vector<AdmmArgs> hp((size_t)count);
+  std::vector<int> nbk((size_t)count);
+  std::vector<double> rhos((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    enmf_ctx* ctx = ctxs[i];
+    const int64_t m = ctx->p.m, n = ctx->p.n;
+    const int k = ctx->p.r;
+    double rho = o.rho;
+    if (!(rho > 0)) {
+      const double rms = sqrt((hs[(size_t)i * 4 + 2] + hs[(size_t)i * 4 + 3]) / ((double)(m + n) * k));
+      rho = rms > 0 ? o.rho_scale / rms : 1.0;
+    }
+    rhos[i] = rho;
+    if (fail(cudaMemsetAsync(ctx->Yb, 0, (size_t)(m + n) * k * sizeof(float), s)))
+      return ENMF_ECUDA;
+    rot_start_kernel<<<1, 256, 0, s>>>(ctx->R, ctx->T2, k, ctx->st);
+    note_launch(1);
+    hp[i] = AdmmArgs{(const float*)U[i], (const float*)V[i], m, n, k, ctx->R, (float*)ctx->Zb,
+                     (float*)ctx->Yb, rho, o.max_iter, o.tol, ctx->st, ctx->part, ctx->Msm,
+                     ctx->err};
+    nbk[i] = admm_blocks(kp, m + n, ctx->num_sms);
+  }
+  std::vector<int> hb;            // per grid: its problems' block offsets (np + 1 each)
+  std::vector<int> seg_first, seg_np, seg_grid, seg_b;
+  for (int i = 0; i < count;) {
+    int used = 0, j = i;
+    seg_b.push_back((int)hb.size());
+    while (j < count && (j == i || used + nbk[j] <= cap)) {
+      hb.push_back(used);
+      used += nbk[j];
+      ++j;
+    }
+    hb.push_back(used);
+    seg_first.push_back(i);
+    seg_np.push_back(j - i);
+    seg_grid.push_back(used);
+    i = j;
+  }
+  const size_t pbytes = sizeof(AdmmArgs) * (size_t)count;
+  void* dbuf = nullptr;
+  if (cudaMallocAsync(&dbuf, pbytes + sizeof(int) * hb.size(), s) != cudaSuccess) {
+    cudaGetLastError();
+    return ENMF_ENOMEM;
+  }
+  AdmmArgs* dp = (AdmmArgs*)dbuf;
+  int* db = (int*)((char*)dbuf + pbytes);
+  if (fail(cudaMemcpyAsync(dp, hp.data(), pbytes, cudaMemcpyHostToDevice, s)) ||
+      fail(cudaMemcpyAsync(db, hb.data(), sizeof(int) * hb.size(), cudaMemcpyHostToDevice, s)))
+    return ENMF_ECUDA;
+  for (size_t g = 0; g < seg_first.size(); ++g)
+    launch_admm_group(dp + seg_first[g], db + seg_b[g], seg_np[g], seg_grid[g], kp,
+                      &ctxs[seg_first[g]]->st->bar, s);
+  cudaFreeAsync(dbuf, s);
+  // U* R, V* R and the negative mass after
+  for (int i = 0; i < count; ++i) {
+    enmf_ctx* ctx = ctxs[i];
+    const int64_t m = ctx->p.m, n = ctx->p.n;
+    const int k = ctx->p.r;
+    launch_apply_square(U[i], m, k, T_F32, ctx->R, s);
+    launch_apply_square(V[i], n, k, T_F32, ctx->R, s);
+    launch_negmass(U[i], m, k, T_F32, ctx->part, &ctx->scal[4], 0, s);
+    launch_negmass(V[i], n, k, T_F32, ctx->part, &ctx->scal[4], 1, s);
+  }
+  enmf_status first = ENMF_OK;
+  for (int i = 0; i < count; ++i) {
+    const enmf_status rc = check_launch(ctxs[i]);
+    if (rc && !first) first = rc;
+  }
+  if (first) return first;
+  for (int i = 0; i < count; ++i) {
+    enmf_ctx* ctx = ctxs[i];
+    const enmf_status rc = sync_status(ctx);
+    ctx->state_valid = false;
+    ctx->hals_known = false;
+    if (rc && !first) first = rc;
+    if (rc && rc != ENMF_ENOTCONV) continue;   // (ENOTCONV: results stand, as in enmf_rotate)
+    if (infos) {
+      DevState hst;
+      double nm_out = 0;
+      if (fail(cudaMemcpy(&hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost)) ||
+          fail(cudaMemcpy(&nm_out, &ctx->scal[4], sizeof(double), cudaMemcpyDeviceToHost)))
+        return ENMF_ECUDA;
+      infos[i].steps = hst.admm_steps;
+      infos[i].converged = hst.admm_done;
+      infos[i].rho = rhos[i];
+      infos[i].dR = hst.dR;
+      infos[i].neg_mass_in = hs[(size_t)i * 4 + 1];
+      infos[i].neg_mass_out = nm_out;
+    }
+  }
+  return first;
+}
+
 // ------------------------------------------------------------ 3. iterate
 // One half of an alternation: the row updates of F (U or V), the Gram of the
 // new F into G_out and, for the V-half, the end-of-alternation bookkeeping.

@@ -247,6 +247,32 @@ void launch_rr_residual(const void* Y, int ldy, int ky, const void* Q, int ldq, 
 void launch_kkt_rows(const void* F, const void* A, const double* G, int64_t rows, int k, int fdt,
                      double* part, double* out, cudaStream_t s);
 
+// One problem of the FP32-factor ADMM rotation (admm.cu).
+struct AdmmArgs {
+  const float* U;
+  const float* V;
+  int64_t m, n;
+  int k;
+  double* R;       // k x k FP64, R_k in, R at exit out
+  float* Z;        // (m + n) x k
+  float* Y;        // (m + n) x k, zero at entry
+  double rho;
+  int max_iter;
+  double tol;
+  DevState* st;
+  double* part;    // (the problem's blocks) x k x k FP64
+  double* M;       // k x k FP64
+  int* err;
+};
+// Blocks of a cooperative ADMM grid at rank pad kp (all resident), and the
+// blocks one problem of rows = m + n rows gets (its own launch's grid).
+int admm_group_capacity(int kp, int num_sms);
+int admm_blocks(int kp, int64_t rows, int num_sms);
+// np problems of rank pad kp in one cooperative grid of `grid` blocks:
+// problem p on blocks bbeg[p] .. bbeg[p + 1] - 1 (device arrays), every grid
+// barrier on `bar`; each problem's results are those of its own launch.
+void launch_admm_group(const AdmmArgs* probs, const int* bbeg, int np, int grid, int kp,
+                       GridBarrier* bar, cudaStream_t s);
 // ----------------------------------------------------------------- admm.cu
 // All steps of Algorithm 1 for FP32 factors in one cooperative launch: W =
 // [U; V], R (k x k FP64) from R_0 in / final R out, Z, Y ((m + n) x k, Y zero

@@ -4,8 +4,10 @@ Requests (X, r) arrive over time.  A request is admitted when its device
 footprint fits the memory budget:
   X in FP32, its BF16 pair X_hi / X_lo, U and V, and the context workspace
   (enmf_workspace_size).
-On admission it gets the SVD start and the rotation, and then joins the batch
-of its padded rank (16, 32, 48 or 64).  Every batch advances all its members
+On admission it gets the SVD start and the rotation -- the rotations of all
+requests admitted in one step run together, one grouped launch per padded
+rank (enmf_rotate_group) -- and then joins the batch of its padded rank (16,
+32, 48 or 64).  Every batch advances all its members
 together, `chunk` alternations per step, in grouped launches under a
 replayed CUDA graph (enmf_batch_step).  So requests that arrive while others
 are running share the device with them, and each finished request frees its
@@ -88,6 +90,7 @@ class Server:
         self.tuned = {}      # padded rank -> batch size when its sweeps were last tuned
         self.pending = collections.deque()
         self.active = []
+        self._new = []
         self.used = 0
         self.results = []
         self.steps = 0
@@ -106,39 +109,53 @@ class Server:
             self.batches[rp] = b
         return b
 
-    def _admit_one(self, req, now):
+    @staticmethod
+    def _rank_pad(r):
+        return 16 if r <= 16 else 32 if r <= 32 else 48 if r <= 48 else 64
+
+    def _prepare(self, req, now):
+        """Device copy of X, the context and the SVD start of one request."""
         m, n = req.X.shape
         with torch.cuda.stream(self.stream):
             Xt = torch.from_numpy(np.ascontiguousarray(req.X, dtype=np.float32)).to(
                 "cuda", non_blocking=False)
             s = Solver(Xt, req.r, stream=self.stream, x_stream=torch.bfloat16)
             s.svd_init()
-            s.rotate()
-        rp = 16 if req.r <= 16 else 32 if req.r <= 32 else 48 if req.r <= 48 else 64
-        b = self._batch(rp)
         sl = _Slot()
         sl.req = req
         sl.solver = s
-        sl.rp = rp
-        sl.slot = B.enmf_batch_add(b, s.ctx, s.X, s.U, s.V)
+        sl.rp = self._rank_pad(req.r)
         sl.bytes = footprint(m, n, req.r)
         sl.f_prev = None
         sl.admitted_s = now
         self.used += sl.bytes
-        self.active.append(sl)
+        return sl
 
     def _admit(self, now):
+        new = self._new = []            # prepared in this step, not yet in a batch
+        joining = collections.Counter()
         while self.pending and self.pending[0].arrival_s <= now:
             req = self.pending[0]
             need = footprint(req.X.shape[0], req.X.shape[1], req.r)
-            if self.active and self.used + need > self.budget:
+            if (self.active or new) and self.used + need > self.budget:
                 break                   # wait for memory to free up
-            rp = 16 if req.r <= 16 else 32 if req.r <= 32 else 48 if req.r <= 48 else 64
+            rp = self._rank_pad(req.r)
             b = self.batches.get(rp)
-            if b is not None and B.enmf_batch_size(b) >= self.max_members:
+            if (B.enmf_batch_size(b) if b is not None else 0) + joining[rp] >= self.max_members:
                 break
             self.pending.popleft()
-            self._admit_one(req, now)
+            new.append(self._prepare(req, now))
+            joining[rp] += 1
+        # the rotations of the step's new requests, grouped by padded rank
+        for rp in sorted(joining):
+            sls = [sl for sl in new if sl.rp == rp]
+            B.enmf_rotate_group([sl.solver.ctx for sl in sls], [sl.solver.U for sl in sls],
+                                [sl.solver.V for sl in sls])
+        for sl in new:
+            sl.slot = B.enmf_batch_add(self._batch(sl.rp), sl.solver.ctx, sl.solver.X,
+                                       sl.solver.U, sl.solver.V)
+            self.active.append(sl)
+        self._new = []
 
     def _retire(self, now):
         keep = []

@@ -58,13 +58,14 @@ def test_serve_admits_by_footprint():
     budget = 2 * max(sizes)
     srv = Server(budget_bytes=budget, chunk=10, tol=0.0, max_iter=20)
     peak = 0
-    orig = srv._admit_one
+    orig = srv._prepare
 
     def tracked(req, now):
         nonlocal peak
-        orig(req, now)
+        sl = orig(req, now)
         peak = max(peak, srv.used)
-    srv._admit_one = tracked
+        return sl
+    srv._prepare = tracked
     res = srv.run(reqs)
     srv.close()
     assert len(res) == len(reqs)

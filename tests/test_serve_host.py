@@ -39,6 +39,7 @@ class FakeBinding:
         self.batches = {}
         self.next_id = 0
         self.max_seen = {}
+        self.rotated = []               # request ids, in grouped-rotation order
 
     def enmf_problem(self, m, n, ldx, r, *dtypes):
         return (m, n, r)
@@ -75,6 +76,10 @@ class FakeBinding:
 
     def enmf_batch_tune(self, b):
         return None
+
+    def enmf_rotate_group(self, ctxs, Us, Vs, opts=None):
+        self.rotated.extend(ctxs)
+        return []
 
     def enmf_batch_step(self, b, n_alt):
         # the objective approaches 0.5 geometrically: f = 0.5 + 0.5 rate^iters
@@ -144,14 +149,16 @@ def _run(monkeypatch, reqs, rates, budget, max_members=128, chunk=10, tol=1e-5, 
     srv = serve.Server(budget_bytes=budget, max_members=max_members, chunk=chunk, tol=tol,
                        max_iter=max_iter, stream=object(), tune=True)
     admitted, used_after = [], []
-    orig = srv._admit_one
+    orig = srv._prepare
 
     def spy(req, now):
-        orig(req, now)
+        sl = orig(req, now)
         admitted.append(req.rid)
-        used_after.append((srv.used, len(srv.active)))
+        # footprint in use and requests on the device once this one is prepared
+        used_after.append((srv.used, len(srv.active) + len(srv._new) + 1))
+        return sl
 
-    srv._admit_one = spy
+    srv._prepare = spy
     results = srv.run(reqs)
     srv.close()
     return srv, B, results, admitted, used_after
@@ -176,6 +183,7 @@ def test_admission_keeps_within_budget_and_fifo(monkeypatch):
     rates = {q.rid: 0.5 for q in reqs}
     srv, B, results, admitted, used_after = _run(monkeypatch, reqs, rates, budget)
     assert admitted == [q.rid for q in reqs]                    # FIFO
+    assert sorted(B.rotated) == sorted(admitted)                # every admission rotated once
     assert all(u <= budget for u, _ in used_after)
     assert sorted(r.rid for r in results) == [q.rid for q in reqs]
     assert srv.used == 0 and not srv.active
