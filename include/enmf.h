@@ -150,8 +150,12 @@ const char* enmf_status_string(enmf_status s);
 typedef struct {
   int32_t oversample;   /* p, default 10                                   */
   int32_t max_iters;    /* default 40                                      */
-  double tol;           /* default 1e-12                                   */
+  double tol;           /* default 1e-12 (FP32 factors: 1e-5)              */
   uint64_t seed;        /* default 0x5eed                                  */
+  int32_t fp32_finish;  /* FP32 factors: 1 = the start from the FP32       */
+                        /*   Jacobi SVD of the last Rayleigh-Ritz matrix   */
+                        /*   (the one the stopping test used); 0 (default) */
+                        /*   = that SVD finished by FP64 sweeps            */
 } enmf_svd_opts;
 typedef struct {
   int32_t iters;        /* power iterations taken                          */

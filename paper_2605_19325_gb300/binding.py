@@ -74,7 +74,7 @@ class CsrMatrix:
 
 class enmf_svd_opts(C.Structure):
     _fields_ = [("oversample", C.c_int32), ("max_iters", C.c_int32), ("tol", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("fp32_finish", C.c_int32)]
 
 
 class enmf_svd_info(C.Structure):

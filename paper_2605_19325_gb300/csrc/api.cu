@@ -516,7 +516,7 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
     if (brc) return brc;
     X = xb;
   }
-  enmf_svd_opts o = {10, 40, ctx->fdt == T_F64 ? 1e-12 : 1e-5, 0x5eedull};
+  enmf_svd_opts o = {10, 40, ctx->fdt == T_F64 ? 1e-12 : 1e-5, 0x5eedull, 0};
   if (opts) {
     o = *opts;
     if (o.oversample < 0 || o.max_iters < 1 || !(o.tol >= 0)) return ENMF_EINVAL;
@@ -577,7 +577,8 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
       launch_row_orth(ctx->M2, LMAX, ctx->M0, LMAX, l, m, fdt, ctx->T1, ctx->T1x, s);
     }
   }
-  if (fdt == T_F32) launch_rr_svd(ctx->Msm, l, l, ctx->sig, ctx->Ut, ctx->Wt, 0, ctx->err, s);
+  if (fdt == T_F32 && !o.fp32_finish)
+    launch_rr_svd(ctx->Msm, l, l, ctx->sig, ctx->Ut, ctx->Wt, 0, ctx->err, s);
   // U* = Q Tu, V* = Q2 Tv with the sign rule
   launch_colsum(ctx->M0, m, LMAX, l, fdt, ctx->part, ctx->csQ, s);
   launch_colsum(ctx->N2, n, LMAX, l, fdt, ctx->part, ctx->csQ2, s);

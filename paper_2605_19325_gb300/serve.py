@@ -120,7 +120,9 @@ class Server:
             Xt = torch.from_numpy(np.ascontiguousarray(req.X, dtype=np.float32)).to(
                 "cuda", non_blocking=False)
             s = Solver(Xt, req.r, stream=self.stream, x_stream=torch.bfloat16)
-            s.svd_init()
+            # the start from the FP32 Jacobi SVD alone (no FP64 sweeps): the
+            # request's factors are FP32 and its X BF16 pairs
+            s.svd_init(B.enmf_svd_opts(10, 40, 1e-5, 0x5eed, 1))
         sl = _Slot()
         sl.req = req
         sl.solver = s

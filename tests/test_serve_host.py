@@ -51,6 +51,9 @@ class FakeBinding:
     def enmf_admm_opts(self, *fields):
         return fields
 
+    def enmf_svd_opts(self, *fields):
+        return fields
+
     def enmf_batch_create(self, max_members, stream=None):
         self.next_id += 1
         self.batches[self.next_id] = {"max": max_members, "members": {}, "next": 0}
@@ -104,7 +107,7 @@ class FakeSolver:
         self.U = torch.zeros(Xt.shape[0], r)
         self.V = torch.zeros(Xt.shape[1], r)
 
-    def svd_init(self):
+    def svd_init(self, opts=None):
         pass
 
     def rotate(self, opts=None):
