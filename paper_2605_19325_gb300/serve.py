@@ -74,7 +74,7 @@ class _Slot:
 
 class Server:
     def __init__(self, budget_bytes=None, max_members=128, chunk=10, tol=1e-5, max_iter=500,
-                 min_iter=20, stream=None, tune=True):
+                 min_iter=20, stream=None, tune=True, fp32_finish=0):
         if budget_bytes is None:
             free, _ = torch.cuda.mem_get_info()
             budget_bytes = int(0.6 * free)
@@ -85,6 +85,7 @@ class Server:
         self.max_iter = max_iter
         self.min_iter = min_iter
         self.tune = tune
+        self.fp32_finish = fp32_finish   # enmf_svd_opts.fp32_finish of the SVD starts
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.batches = {}            # padded rank -> batch handle
         self.tuned = {}      # padded rank -> batch size when its sweeps were last tuned
@@ -120,9 +121,9 @@ class Server:
             Xt = torch.from_numpy(np.ascontiguousarray(req.X, dtype=np.float32)).to(
                 "cuda", non_blocking=False)
             s = Solver(Xt, req.r, stream=self.stream, x_stream=torch.bfloat16)
-            # the start from the FP32 Jacobi SVD alone (no FP64 sweeps): the
-            # request's factors are FP32 and its X BF16 pairs
-            s.svd_init(B.enmf_svd_opts(10, 40, 1e-5, 0x5eed, 1))
+            # (the FP64-finished start: with fp32_finish the stream's chaotic
+            # requests land elsewhere often enough to cost served accuracy)
+            s.svd_init(B.enmf_svd_opts(10, 40, 1e-5, 0x5eed, self.fp32_finish))
         sl = _Slot()
         sl.req = req
         sl.solver = s
