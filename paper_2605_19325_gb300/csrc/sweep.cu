@@ -147,19 +147,24 @@ static void sweep_launch(const void* X, int64_t m, int64_t n, int64_t ldx, const
 
 // ------------------------------------------------ FP32-factor sweep (SIMT)
 // C[rows_out x k] = op(X) B with FP32 factors and FP32 or 16-bit X (exact in
-// FP32), FP32 products and sums.  One CTA owns SW_BM output rows and SW_KT
-// columns (every column of the SVD start's widths up to 64 in one pass over
-// X) over a range of the reduction: 256 threads as 16 x 16, thread (tr, tc)
-// owning rows tr + 16 i (i < 8) and columns 4 tc .. 4 tc + 3.  Stages of
+// FP32), FP32 products and sums.  One CTA owns BM output rows and KT columns
+// over a range of the reduction: KT = 64 (BM = 128) for widths above 32 --
+// every column of the SVD start's widths up to 64 in one pass over X -- and
+// KT = 32 (BM = 256) up to 32, so that no FMA multiplies a padding column.
+// 256 threads as (256 / (KT / 4)) x (KT / 4), thread (tr, tc) owning rows
+// tr + (256 / (KT / 4)) i (i < 8) and columns 4 tc .. 4 tc + 3.  Stages of
 // SW_BK reduction steps: the next stage's X and B values are loaded into
 // registers while the current stage is multiplied out of shared memory (two
 // buffers, one barrier per stage).  X sits in shared memory reduction-major.
 // Per output the products are summed in reduction order, then the split-K
 // partials in split order, so results are bitwise reproducible.
-constexpr int SW_BM = 128, SW_BK = 16, SW_KT = 64, SW_T = 256;
+constexpr int SW_BK = 16, SW_T = 256;
+__host__ __device__ constexpr int sw_bm(int kt) { return kt == 32 ? 256 : 128; }
+static int sw_kt(int k) { return k <= 32 ? 32 : 64; }
 
 int sweep_splits_f32(int64_t rows_out, int64_t red_len, int k, int num_sms) {
-  const int64_t tiles = ((rows_out + SW_BM - 1) / SW_BM) * ((k + SW_KT - 1) / SW_KT);
+  const int kt = sw_kt(k), bm = sw_bm(kt);
+  const int64_t tiles = ((rows_out + bm - 1) / bm) * ((k + kt - 1) / kt);
   const int64_t target = 2LL * (num_sms > 0 ? num_sms : 152);
   int64_t splits = (target + tiles - 1) / tiles;
   const int64_t max_by_len = red_len / 256;
@@ -206,44 +211,49 @@ __device__ __forceinline__ float4 load4(const TX* p, int64_t lim) {
   return v;
 }
 
-template <typename TX, bool TRANS, bool VEC>
+template <typename TX, bool TRANS, bool VEC, int KT>
 __global__ void __launch_bounds__(SW_T)
 sweep32_kernel(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
                const float* __restrict__ B, int ldb, int k, float* __restrict__ C, int ldc,
                int64_t red_per_split, float* __restrict__ part) {
-  constexpr int BM = SW_BM, BK = SW_BK, KT = SW_KT, XLD = BM + 4;
+  constexpr int BM = sw_bm(KT), BK = SW_BK, XLD = BM + 4;
+  constexpr int TCN = KT / 4, TRN = SW_T / TCN;   // thread grid: TRN rows x TCN column groups
+  constexpr int NV = BM * BK / 4 / SW_T;          // X float4s per thread per stage
+  constexpr int BQ = BM / 4;                      // float4s across a reduction row (X^T U)
+  static_assert(TRN * 8 == BM, "eight rows per thread");
   __shared__ __align__(16) float Xs[2][BK][XLD];
   __shared__ __align__(16) float Bs[2][BK][KT];
-  const int t = threadIdx.x, tr = t / 16, tc = t % 16;
+  const int t = threadIdx.x, tr = t / TCN, tc = t % TCN;
   const int64_t rows_out = TRANS ? n : m;
   const int64_t row0 = (int64_t)blockIdx.x * BM;
   const int col0 = blockIdx.y * KT;
   const int64_t kb = (int64_t)blockIdx.z * red_per_split;
   const int64_t ke = min(TRANS ? m : n, kb + red_per_split);
 
-  float4 xr[2], br;
+  float4 xr[NV], br;
+  const bool bload = t < BK * TCN;   // threads holding one B float4 of a stage
   // global -> registers for the stage starting at k0
   auto fetch = [&](int64_t k0) {
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < NV; ++v) {
       const int q = t + SW_T * v;
       if (!TRANS) {   // X rows row0 + q / 4, reduction columns k0 + 4 (q % 4) ..
         const int64_t gr = row0 + q / 4, gc = k0 + 4 * (q % 4);
         xr[v] = gr < m ? load4<TX, VEC>(X + gr * ldx + gc, ke - gc) : make_float4(0.f, 0.f, 0.f, 0.f);
-      } else {        // X row k0 + q / 32 (reduction), columns row0 + 4 (q % 32) ..
-        const int64_t gr = k0 + q / 32, gc = row0 + 4 * (q % 32);
+      } else {        // X row k0 + q / BQ (reduction), columns row0 + 4 (q % BQ) ..
+        const int64_t gr = k0 + q / BQ, gc = row0 + 4 * (q % BQ);
         xr[v] = gr < ke ? load4<TX, VEC>(X + gr * ldx + gc, n - gc) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    {   // B rows k0 + t / 16, columns col0 + 4 (t % 16) ..
-      const int64_t gr = k0 + t / 16;
-      const int gc = col0 + 4 * (t % 16);
+    if (bload) {   // B rows k0 + t / TCN, columns col0 + 4 (t % TCN) ..
+      const int64_t gr = k0 + t / TCN;
+      const int gc = col0 + 4 * (t % TCN);
       br = gr < ke ? load4<float, VEC>(B + gr * ldb + gc, k - gc) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
   auto stash = [&](int b) {
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < NV; ++v) {
       const int q = t + SW_T * v;
       if (!TRANS) {
         const int rr = q / 4, c4 = 4 * (q % 4);
@@ -252,10 +262,10 @@ sweep32_kernel(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
         Xs[b][c4 + 2][rr] = xr[v].z;
         Xs[b][c4 + 3][rr] = xr[v].w;
       } else {
-        *reinterpret_cast<float4*>(&Xs[b][q / 32][4 * (q % 32)]) = xr[v];
+        *reinterpret_cast<float4*>(&Xs[b][q / BQ][4 * (q % BQ)]) = xr[v];
       }
     }
-    *reinterpret_cast<float4*>(&Bs[b][t / 16][4 * (t % 16)]) = br;
+    if (bload) *reinterpret_cast<float4*>(&Bs[b][t / TCN][4 * (t % TCN)]) = br;
   };
 
   float acc[8][4];
@@ -277,7 +287,7 @@ sweep32_kernel(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
     for (int kk = 0; kk < BK; ++kk) {
       float a[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = Xs[buf][kk][tr + 16 * i];
+      for (int i = 0; i < 8; ++i) a[i] = Xs[buf][kk][tr + TRN * i];
       const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tc]);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -293,7 +303,7 @@ sweep32_kernel(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int64_t gr = row0 + tr + 16 * i;
+    const int64_t gr = row0 + tr + TRN * i;
     if (gr >= rows_out) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -315,7 +325,8 @@ static void sweep32_launch(const void* X, int64_t m, int64_t n, int64_t ldx, con
   int64_t per = (red + splits - 1) / splits;
   per = ((per + SW_BK - 1) / SW_BK) * SW_BK;
   splits = (int)((red + per - 1) / per);
-  dim3 grid((unsigned)((rows_out + SW_BM - 1) / SW_BM), (k + SW_KT - 1) / SW_KT, splits);
+  const int kt = sw_kt(k), bm = sw_bm(kt);
+  dim3 grid((unsigned)((rows_out + bm - 1) / bm), (k + kt - 1) / kt, splits);
   float* p = splits > 1 ? (float*)part : nullptr;
   // whole-vector loads need every row start and the base 16-byte (float) /
   // 8-byte (16-bit) aligned
@@ -323,12 +334,17 @@ static void sweep32_launch(const void* X, int64_t m, int64_t n, int64_t ldx, con
   const bool vec = (ldx * (int64_t)sizeof(TX)) % (int64_t)xa == 0 && ((uintptr_t)X % xa) == 0 &&
                    (ldb % 4) == 0 && ((uintptr_t)B % 16) == 0;
   note_launch(splits > 1 ? 2 : 1);
-  if (vec)
-    sweep32_kernel<TX, TRANS, true><<<grid, SW_T, 0, s>>>((const TX*)X, m, n, ldx, (const float*)B,
-                                                          ldb, k, (float*)C, ldc, per, p);
-  else
-    sweep32_kernel<TX, TRANS, false><<<grid, SW_T, 0, s>>>((const TX*)X, m, n, ldx, (const float*)B,
-                                                           ldb, k, (float*)C, ldc, per, p);
+#define SW32(V, K)                                                                         \
+  sweep32_kernel<TX, TRANS, V, K><<<grid, SW_T, 0, s>>>((const TX*)X, m, n, ldx, (const float*)B, \
+                                                        ldb, k, (float*)C, ldc, per, p)
+  if (kt == 32) {
+    if (vec) SW32(true, 32);
+    else SW32(false, 32);
+  } else {
+    if (vec) SW32(true, 64);
+    else SW32(false, 64);
+  }
+#undef SW32
   if (splits > 1) {
     const int64_t total = rows_out * k;
     int blocks = (int)((total + 255) / 256);
