@@ -152,7 +152,7 @@ static void sweep_launch(const void* X, int64_t m, int64_t n, int64_t ldx, const
 // every column of the SVD start's widths up to 64 in one pass over X -- and
 // KT = 32 (BM = 256) up to 32, so that no FMA multiplies a padding column.
 // 256 threads as (256 / (KT / 4)) x (KT / 4), thread (tr, tc) owning rows
-// tr + (256 / (KT / 4)) i (i < 8) and columns 4 tc .. 4 tc + 3.  Stages of
+// 8 tr .. 8 tr + 7 and columns 4 tc .. 4 tc + 3.  Stages of
 // SW_BK reduction steps: the next stage's X and B values are loaded into
 // registers while the current stage is multiplied out of shared memory (two
 // buffers, one barrier per stage).  X sits in shared memory reduction-major.
@@ -285,9 +285,10 @@ sweep32_kernel(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
     if (more) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      float a[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = Xs[buf][kk][tr + TRN * i];
+      // the thread's eight rows are consecutive: two 16-byte loads
+      const float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][kk][8 * tr]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Xs[buf][kk][8 * tr + 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tc]);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -303,7 +304,7 @@ sweep32_kernel(const TX* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int64_t gr = row0 + tr + TRN * i;
+    const int64_t gr = row0 + 8 * tr + i;
     if (gr >= rows_out) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
