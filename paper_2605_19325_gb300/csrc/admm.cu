@@ -523,6 +523,15 @@ void admm_launch(const AdmmArgs& a, int num_sms, cudaStream_t s) {
 }
 
 template <int KP>
+int admm_group_capacity_k(int num_sms) {
+  const size_t smem = admm_smem<KP>();
+  cudaFuncSetAttribute(admm_group_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, admm_group_kernel<KP>, AT, smem);
+  return (per < 1 ? 1 : per) * num_sms;
+}
+
+template <int KP>
 void admm_group_launch(const AdmmArgs* probs, const int* bbeg, int np, int grid,
                        GridBarrier* bar, cudaStream_t s) {
   cudaFuncSetAttribute(admm_group_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -535,13 +544,14 @@ void admm_group_launch(const AdmmArgs* probs, const int* bbeg, int np, int grid,
 }  // namespace
 
 int admm_group_capacity(int kp, int num_sms) {
-  return kp == 16 ? admm_capacity<16>(num_sms) : kp == 32 ? admm_capacity<32>(num_sms)
-         : kp == 48 ? admm_capacity<48>(num_sms) : admm_capacity<64>(num_sms);
+  return kp == 16 ? admm_group_capacity_k<16>(num_sms) : kp == 32 ? admm_group_capacity_k<32>(num_sms)
+         : kp == 48 ? admm_group_capacity_k<48>(num_sms) : admm_group_capacity_k<64>(num_sms);
 }
 
 int admm_blocks(int kp, int64_t rows, int num_sms) {
   const int64_t need = (rows + ARPB - 1) / ARPB;
-  int64_t grid = admm_group_capacity(kp, num_sms);
+  int64_t grid = kp == 16 ? admm_capacity<16>(num_sms) : kp == 32 ? admm_capacity<32>(num_sms)
+                 : kp == 48 ? admm_capacity<48>(num_sms) : admm_capacity<64>(num_sms);
   if (grid > NPART) grid = NPART;
   if (grid > need) grid = need;
   return grid < 1 ? 1 : (int)grid;

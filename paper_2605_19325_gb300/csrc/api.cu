@@ -807,12 +807,23 @@ extern "C" enmf_status enmf_rotate_group(enmf_ctx* const* ctxs, void* const* U, 
                      ctx->err};
     nbk[i] = admm_blocks(kp, m + n, ctx->num_sms);
   }
+  // (a problem whose own grid exceeds a grouped grid's -- not the case on a
+  // GB300, where both kernels keep the same occupancy -- runs alone through
+  // launch_admm_f32: seg_np = 0 marks it)
   std::vector<int> hb;            // per grid: its problems' block offsets (np + 1 each)
   std::vector<int> seg_first, seg_np, seg_grid, seg_b;
   for (int i = 0; i < count;) {
+    if (nbk[i] > cap) {
+      seg_b.push_back((int)hb.size());
+      seg_first.push_back(i);
+      seg_np.push_back(0);
+      seg_grid.push_back(0);
+      ++i;
+      continue;
+    }
     int used = 0, j = i;
     seg_b.push_back((int)hb.size());
-    while (j < count && (j == i || used + nbk[j] <= cap)) {
+    while (j < count && nbk[j] <= cap && (j == i || used + nbk[j] <= cap)) {
       hb.push_back(used);
       used += nbk[j];
       ++j;
@@ -834,9 +845,16 @@ extern "C" enmf_status enmf_rotate_group(enmf_ctx* const* ctxs, void* const* U, 
   if (fail(cudaMemcpyAsync(dp, hp.data(), pbytes, cudaMemcpyHostToDevice, s)) ||
       fail(cudaMemcpyAsync(db, hb.data(), sizeof(int) * hb.size(), cudaMemcpyHostToDevice, s)))
     return ENMF_ECUDA;
-  for (size_t g = 0; g < seg_first.size(); ++g)
+  for (size_t g = 0; g < seg_first.size(); ++g) {
+    if (seg_np[g] == 0) {
+      const AdmmArgs& a = hp[seg_first[g]];
+      launch_admm_f32(a.U, a.V, a.m, a.n, a.k, a.R, a.Z, a.Y, a.rho, a.max_iter, a.tol, a.st,
+                      a.part, a.M, a.err, ctxs[seg_first[g]]->num_sms, s);
+      continue;
+    }
     launch_admm_group(dp + seg_first[g], db + seg_b[g], seg_np[g], seg_grid[g], kp,
                       &ctxs[seg_first[g]]->st->bar, s);
+  }
   cudaFreeAsync(dbuf, s);
   // U* R, V* R and the negative mass after
   for (int i = 0; i < count; ++i) {

@@ -264,8 +264,9 @@ struct AdmmArgs {
   double* M;       // k x k FP64
   int* err;
 };
-// Blocks of a cooperative ADMM grid at rank pad kp (all resident), and the
-// blocks one problem of rows = m + n rows gets (its own launch's grid).
+// Blocks of a cooperative grouped ADMM grid at rank pad kp (all resident),
+// and the blocks one problem of rows = m + n rows gets (its own launch's
+// grid, launch_admm_f32).
 int admm_group_capacity(int kp, int num_sms);
 int admm_blocks(int kp, int64_t rows, int num_sms);
 // np problems of rank pad kp in one cooperative grid of `grid` blocks:
