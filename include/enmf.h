@@ -166,6 +166,22 @@ enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void* V, double
                           const enmf_svd_opts* opts /* NULL = defaults */,
                           enmf_svd_info* info /* NULL ok */);
 
+/* The SVD start for `count` contexts at once (no counterpart in the paper; a
+ * serving aid): each problem exactly as enmf_svd_init(ctxs[i], X[i], U[i],
+ * V[i], sigma ? sigma[i] : NULL, opts, &infos[i]) would leave it, bit for
+ * bit, but the FP32-then-FP64 Rayleigh-Ritz SVDs that finish the FP32-factor
+ * starts run in one launch, one CTA per problem (each is a single-CTA FP64
+ * computation: side by side they take the time of the largest).  The power
+ * iterations run per problem, as in enmf_svd_init.  All contexts must share
+ * one stream and device and appear once (else ENMF_EINVAL, before any
+ * launch); forms may differ.  status (may be NULL) receives each problem's
+ * status (ENMF_OK or ENMF_ENOTCONV as enmf_svd_init returns them); the call
+ * returns the first status other than those, else ENMF_OK. */
+enmf_status enmf_svd_init_group(enmf_ctx* const* ctxs, const void* const* X, void* const* U,
+                                void* const* V, double* const* sigma, int32_t count,
+                                const enmf_svd_opts* opts, enmf_svd_info* infos,
+                                enmf_status* status);
+
 /* ---- 2. Rotation toward the orthant (Algorithm 1) -----------------------
  * W = [U; V].  Each ADMM step: b = W R - Y / rho; Z = prox(b) (Eq. 7);
  * M = W^T (Z + Y / rho); R = polar(M) = C D^T from M = C S D^T (Procrustes;

@@ -131,6 +131,11 @@ _SIGS = {
                                 C.POINTER(enmf_svd_opts), C.POINTER(enmf_svd_info)]),
     "enmf_rotate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.POINTER(enmf_admm_opts), C.POINTER(enmf_rotate_info)]),
+    "enmf_svd_init_group": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), C.c_int32,
+                                      C.POINTER(enmf_svd_opts), C.POINTER(enmf_svd_info),
+                                      C.POINTER(C.c_int)]),
     "enmf_rotate_group": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                     C.POINTER(C.c_void_p), C.c_int32,
                                     C.POINTER(enmf_admm_opts), C.POINTER(enmf_rotate_info)]),
@@ -260,6 +265,27 @@ def enmf_rotate(ctx, U, V, R=None, opts=None):
     if code not in (0, 6):
         check(code, "enmf_rotate")
     return info, code
+
+
+def enmf_svd_init_group(ctxs, Xs, Us, Vs, sigmas=None, opts=None):
+    """The SVD start for several contexts (one stream); returns (infos,
+    per-problem status codes)."""
+    n = len(ctxs)
+    cs = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    xs = (C.c_void_p * n)(*[X.data_ptr() for X in Xs])
+    us = (C.c_void_p * n)(*[U.data_ptr() for U in Us])
+    vs = (C.c_void_p * n)(*[V.data_ptr() for V in Vs])
+    ss = (C.c_void_p * n)(*[(s.data_ptr() if s is not None else None) for s in sigmas]) \
+        if sigmas is not None else None
+    infos = (enmf_svd_info * n)()
+    status = (C.c_int * n)()
+    check(lib().enmf_svd_init_group(cs, xs, us, vs, ss, n,
+                                    C.byref(opts) if opts is not None else None, infos, status),
+          "enmf_svd_init_group")
+    for code in status:
+        if code not in (0, 6):
+            check(code, "enmf_svd_init_group")
+    return list(infos), list(status)
 
 
 def enmf_rotate_group(ctxs, Us, Vs, opts=None):

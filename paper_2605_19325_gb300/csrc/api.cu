@@ -505,11 +505,18 @@ static void orth2(enmf_ctx* ctx, void* F, void* tmp, int64_t rows, int k) {
 }
 
 // ------------------------------------------------------------------ 1. SVD
-extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void* V,
-                                     double* sigma, const enmf_svd_opts* opts,
-                                     enmf_svd_info* info) {
-  GUARD(ctx);
-  if (!X || !U || !V) return ENMF_EINVAL;
+// The SVD start in two parts, so that a group of contexts can share the
+// FP64-finished Rayleigh-Ritz SVD launch (enmf_svd_init_group).  Part 1: the
+// power iterations with their stopping test, leaving the last P (ctx->Msm)
+// and its SVD (FP64-finished for FP64 factors, FP32 otherwise); *finish =
+// whether the FP32-then-FP64 SVD of that P is still owed.
+struct SvdRun {
+  int l, it, r;
+  double res, tol;
+  bool finish;
+};
+
+static enmf_status svd_part1(enmf_ctx* ctx, const void*& X, const enmf_svd_opts* opts, SvdRun& sr) {
   {
     const void* xb = nullptr;
     const enmf_status brc = bind_x(ctx, X, &xb);
@@ -551,7 +558,8 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
     launch_gram(ctx->N2, LMAX, l, ctx->N1, LMAX, l, n, fdt, ctx->part, ctx->Msm, s);
     // with FP32 factors the stopping test below takes the FP32 Jacobi SVD
     // (its residual sits far below the FP32 tolerance); the start itself is
-    // made from the FP64-finished SVD of the last P, after the loop
+    // made from the FP64-finished SVD of the last P, after the loop, unless
+    // opts->fp32_finish
     launch_rr_svd(ctx->Msm, l, l, ctx->sig, ctx->Ut, ctx->Wt, fdt == T_F32 ? 1 : 0, ctx->err, s);
     // Y = X Q2 (the next power iterate) and the residual ||Y W_r - Q U_r S_r||
     launch_xv(X, xdt, m, n, p.ldx, ctx->N2, LMAX, l, ctx->M1, LMAX, fdt, ctx->splitk, ctx->num_sms, s);
@@ -577,29 +585,107 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
       launch_row_orth(ctx->M2, LMAX, ctx->M0, LMAX, l, m, fdt, ctx->T1, ctx->T1x, s);
     }
   }
-  if (fdt == T_F32 && !o.fp32_finish)
-    launch_rr_svd(ctx->Msm, l, l, ctx->sig, ctx->Ut, ctx->Wt, 0, ctx->err, s);
-  // U* = Q Tu, V* = Q2 Tv with the sign rule
+  sr.l = l;
+  sr.it = it;
+  sr.r = r;
+  sr.res = res;
+  sr.finish = fdt == T_F32 && !o.fp32_finish;
+  sr.tol = o.tol;
+  return ENMF_OK;
+}
+
+// Part 2: U* = Q Tu, V* = Q2 Tv with the sign rule, the rank kept, the status.
+static enmf_status svd_part2(enmf_ctx* ctx, void* U, void* V, double* sigma, const SvdRun& sr,
+                             enmf_svd_info* info) {
+  const enmf_problem& p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  const int fdt = ctx->fdt, l = sr.l, r = sr.r;
+  const int64_t m = p.m, n = p.n;
   launch_colsum(ctx->M0, m, LMAX, l, fdt, ctx->part, ctx->csQ, s);
   launch_colsum(ctx->N2, n, LMAX, l, fdt, ctx->part, ctx->csQ2, s);
   launch_svd_finish(ctx->sig, ctx->Ut, ctx->Wt, l, l, r, ctx->csQ, ctx->csQ2, ctx->Tu, ctx->Tv,
                     sigma, s);
   launch_row_transform(ctx->M0, LMAX, l, U, r, r, m, fdt, ctx->Tu, s);
   launch_row_transform(ctx->N2, LMAX, l, V, r, r, n, fdt, ctx->Tv, s);
-  rc = check_launch(ctx);
+  enmf_status rc = check_launch(ctx);
   if (rc) return rc;
   int kept = l;
   CK(cudaMemcpyAsync(&kept, ctx->kept, sizeof(int), cudaMemcpyDeviceToHost, s));
   rc = sync_status(ctx);
   if (info) {
-    info->iters = it;
+    info->iters = sr.it;
     info->rank = kept;
-    info->residual = res;
+    info->residual = sr.res;
   }
   ctx->state_valid = false;
   ctx->hals_known = false;
   if (rc) return rc;
-  return res <= o.tol ? ENMF_OK : ENMF_ENOTCONV;
+  return sr.res <= sr.tol ? ENMF_OK : ENMF_ENOTCONV;
+}
+
+// ------------------------------------------------------------------ 1. SVD
+extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void* V,
+                                     double* sigma, const enmf_svd_opts* opts,
+                                     enmf_svd_info* info) {
+  GUARD(ctx);
+  if (!X || !U || !V) return ENMF_EINVAL;
+  SvdRun sr;
+  enmf_status rc = svd_part1(ctx, X, opts, sr);
+  if (rc) return rc;
+  if (sr.finish)
+    launch_rr_svd(ctx->Msm, sr.l, sr.l, ctx->sig, ctx->Ut, ctx->Wt, 0, ctx->err, ctx->stream);
+  return svd_part2(ctx, U, V, sigma, sr, info);
+}
+
+extern "C" enmf_status enmf_svd_init_group(enmf_ctx* const* ctxs, const void* const* X,
+                                           void* const* U, void* const* V, double* const* sigma,
+                                           int32_t count, const enmf_svd_opts* opts,
+                                           enmf_svd_info* infos, enmf_status* status) {
+  if (!ctxs || !X || !U || !V || count < 1) return ENMF_EINVAL;
+  if (!ctxs[0]) return ENMF_EINVAL;
+  cudaStream_t s = ctxs[0]->stream;
+  for (int i = 0; i < count; ++i) {
+    enmf_ctx* ctx = ctxs[i];
+    if (!ctx || !X[i] || !U[i] || !V[i]) return ENMF_EINVAL;
+    if (ctx->poison) return ctx->poison;
+    if (ctx->stream != s || ctx->device != ctxs[0]->device) return ENMF_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctx) return ENMF_EINVAL;
+  }
+  std::vector<SvdRun> sr((size_t)count);
+  std::vector<enmf_status> st((size_t)count, ENMF_OK);
+  std::vector<RrSvdProb> hp;
+  int mk = 0;
+  for (int i = 0; i < count; ++i) {
+    const void* Xi = X[i];
+    st[i] = svd_part1(ctxs[i], Xi, opts, sr[i]);
+    if (st[i] || !sr[i].finish) continue;
+    enmf_ctx* ctx = ctxs[i];
+    hp.push_back(RrSvdProb{ctx->Msm, sr[i].l, sr[i].l, ctx->sig, ctx->Ut, ctx->Wt, 0, ctx->err});
+    if (sr[i].l > mk) mk = sr[i].l;
+  }
+  if (!hp.empty()) {
+    void* d = nullptr;
+    const size_t bytes = sizeof(RrSvdProb) * hp.size();
+    if (cudaMallocAsync(&d, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      return ENMF_ENOMEM;
+    }
+    if (cudaMemcpyAsync(d, hp.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      for (int i = 0; i < count; ++i) ctxs[i]->poison = ENMF_ECUDA;
+      return ENMF_ECUDA;
+    }
+    launch_rr_svd_group((const RrSvdProb*)d, (int)hp.size(), mk, mk, s);
+    cudaFreeAsync(d, s);
+  }
+  enmf_status first = ENMF_OK;
+  for (int i = 0; i < count; ++i) {
+    if (!st[i]) st[i] = svd_part2(ctxs[i], U[i], V[i], sigma ? sigma[i] : nullptr, sr[i],
+                                  infos ? &infos[i] : nullptr);
+    if (status) status[i] = st[i];
+    if (st[i] && st[i] != ENMF_ENOTCONV && !first) first = st[i];
+  }
+  return first;
 }
 
 // ------------------------------------------------------------- 2. rotation

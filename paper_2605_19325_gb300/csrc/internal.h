@@ -317,6 +317,21 @@ void launch_row_orth(const void* in, int ld_in, void* out, int ld_out, int k, in
 // only (for FP32-accurate P), else FP32 sweeps finished in FP64.
 void launch_rr_svd(const double* P, int k2, int k1, double* sigma, double* Ut, double* Wt,
                    int fp32_only, int* err, cudaStream_t s);
+// One Rayleigh-Ritz SVD of a group (launch_rr_svd's arguments).
+struct RrSvdProb {
+  const double* P;
+  int k2, k1;
+  double* sigma;
+  double* Ut;
+  double* Wt;
+  int fp32_only;
+  int* err;
+};
+// count SVDs in one launch, one CTA each (probs in device memory; max_k2 and
+// max_k1 bound every problem's k2 and k1), each with the arithmetic of its own
+// launch_rr_svd.
+void launch_rr_svd_group(const RrSvdProb* probs, int count, int max_k2, int max_k1,
+                         cudaStream_t s);
 // Final SVD-start transforms with the sign rule (see small.cu).
 void launch_svd_finish(const double* sigma, const double* Ut, const double* Wt, int k1, int k2,
                        int r, const double* colsumQ, const double* colsumQ2, double* Tu,

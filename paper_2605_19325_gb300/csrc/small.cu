@@ -563,10 +563,9 @@ void launch_eig_orth(const double* G, int k, double tau, double* T, double* Tx, 
 // row c of P, so P's memory is P^T in column-major order.
 // fp32_only (the forms with FP32 factors, whose range-finder bases and P are
 // FP32-accurate): the FP32 sweeps alone, their A and V taken to FP64.
-__global__ void __launch_bounds__(SM_T)
-rr_svd_kernel(const double* __restrict__ P, int k2, int k1, double* sigma, double* Ut, double* Wt,
-              int fp32_only, int* err) {
-  extern __shared__ double smd[];
+__device__ __forceinline__ void rr_svd_body(const double* __restrict__ P, int k2, int k1,
+                                            double* sigma, double* Ut, double* Wt, int fp32_only,
+                                            int* err, double* smd) {
   const int Np = k2 + (k2 & 1);
   double* A = smd;                  // Np columns x k1 rows
   double* V = A + (size_t)Np * k1;  // Np x Np
@@ -606,14 +605,42 @@ rr_svd_kernel(const double* __restrict__ P, int k2, int k1, double* sigma, doubl
   if (threadIdx.x == 0 && sw > JAC_MAX_SWEEPS - 1) atomicOr(err, ERR_NOTCONV);
 }
 
+__global__ void __launch_bounds__(SM_T)
+rr_svd_kernel(const double* __restrict__ P, int k2, int k1, double* sigma, double* Ut, double* Wt,
+              int fp32_only, int* err) {
+  extern __shared__ double smd[];
+  rr_svd_body(P, k2, k1, sigma, Ut, Wt, fp32_only, err, smd);
+}
+
+// One CTA per problem: problem b's SVD on block b, the same arithmetic as its
+// own rr_svd_kernel launch.
+__global__ void __launch_bounds__(SM_T) rr_svd_group_kernel(const RrSvdProb* __restrict__ probs) {
+  extern __shared__ double smd[];
+  const RrSvdProb q = probs[blockIdx.x];
+  rr_svd_body(q.P, q.k2, q.k1, q.sigma, q.Ut, q.Wt, q.fp32_only, q.err, smd);
+}
+
+static size_t rr_svd_smem(int k2, int k1) {
+  const int Np = k2 + (k2 & 1);
+  // FP64 panels plus the FP32 copies of the mixed-precision Jacobi
+  return small_smem(k1 > Np ? k1 : Np, Np) + sizeof(float) * ((size_t)Np * k1 + (size_t)Np * Np);
+}
+
 void launch_rr_svd(const double* P, int k2, int k1, double* sigma, double* Ut, double* Wt,
                    int fp32_only, int* err, cudaStream_t s) {
   note_launch(1);
-  int Np = k2 + (k2 & 1);
-  // FP64 panels plus the FP32 copies of the mixed-precision Jacobi
-  size_t smem = small_smem(k1 > Np ? k1 : Np, Np) + sizeof(float) * ((size_t)Np * k1 + (size_t)Np * Np);
+  const size_t smem = rr_svd_smem(k2, k1);
   cudaFuncSetAttribute(rr_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   rr_svd_kernel<<<1, SM_T, smem, s>>>(P, k2, k1, sigma, Ut, Wt, fp32_only, err);
+}
+
+void launch_rr_svd_group(const RrSvdProb* probs, int count, int max_k2, int max_k1,
+                         cudaStream_t s) {
+  if (count < 1) return;
+  note_launch(1);
+  const size_t smem = rr_svd_smem(max_k2, max_k1);
+  cudaFuncSetAttribute(rr_svd_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  rr_svd_group_kernel<<<count, SM_T, smem, s>>>(probs);
 }
 
 // Residual inputs: Wr = Wt[:, :r] (k2 x r), UrS = Ut[:, :r] S_r (k1 x r).

@@ -4,10 +4,10 @@ Requests (X, r) arrive over time.  A request is admitted when its device
 footprint fits the memory budget:
   X in FP32, its BF16 pair X_hi / X_lo, U and V, and the context workspace
   (enmf_workspace_size).
-On admission it gets the SVD start and the rotation -- the rotations of all
-requests admitted in one step run together, one grouped launch per padded
-rank (enmf_rotate_group) -- and then joins the batch of its padded rank (16,
-32, 48 or 64).  Every batch advances all its members
+On admission it gets the SVD start and the rotation -- for all requests
+admitted in one step together: one enmf_svd_init_group call, then one grouped
+rotation launch per padded rank (enmf_rotate_group) -- and then joins the
+batch of its padded rank (16, 32, 48 or 64).  Every batch advances all its members
 together, `chunk` alternations per step, in grouped launches under a
 replayed CUDA graph (enmf_batch_step).  So requests that arrive while others
 are running share the device with them, and each finished request frees its
@@ -115,15 +115,13 @@ class Server:
         return 16 if r <= 16 else 32 if r <= 32 else 48 if r <= 48 else 64
 
     def _prepare(self, req, now):
-        """Device copy of X, the context and the SVD start of one request."""
+        """Device copy of X and the context of one request (its SVD start runs
+        with the step's other admissions, in _admit)."""
         m, n = req.X.shape
         with torch.cuda.stream(self.stream):
             Xt = torch.from_numpy(np.ascontiguousarray(req.X, dtype=np.float32)).to(
                 "cuda", non_blocking=False)
             s = Solver(Xt, req.r, stream=self.stream, x_stream=torch.bfloat16)
-            # (the FP64-finished start: with fp32_finish the stream's chaotic
-            # requests land elsewhere often enough to cost served accuracy)
-            s.svd_init(B.enmf_svd_opts(10, 40, 1e-5, 0x5eed, self.fp32_finish))
         sl = _Slot()
         sl.req = req
         sl.solver = s
@@ -149,7 +147,15 @@ class Server:
             self.pending.popleft()
             new.append(self._prepare(req, now))
             joining[rp] += 1
-        # the rotations of the step's new requests, grouped by padded rank
+        # the SVD starts of the step's new requests in one call (their
+        # FP64-finished Rayleigh-Ritz SVDs side by side; with fp32_finish the
+        # stream's chaotic requests land elsewhere often enough to cost served
+        # accuracy, so it is off by default), then their rotations, grouped
+        # by padded rank
+        if new:
+            B.enmf_svd_init_group([sl.solver.ctx for sl in new], [sl.solver.X for sl in new],
+                                  [sl.solver.U for sl in new], [sl.solver.V for sl in new],
+                                  None, B.enmf_svd_opts(10, 40, 1e-5, 0x5eed, self.fp32_finish))
         for rp in sorted(joining):
             sls = [sl for sl in new if sl.rp == rp]
             B.enmf_rotate_group([sl.solver.ctx for sl in sls], [sl.solver.U for sl in sls],

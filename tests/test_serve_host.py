@@ -40,6 +40,7 @@ class FakeBinding:
         self.next_id = 0
         self.max_seen = {}
         self.rotated = []               # request ids, in grouped-rotation order
+        self.started = []               # request ids, in grouped SVD-start order
 
     def enmf_problem(self, m, n, ldx, r, *dtypes):
         return (m, n, r)
@@ -79,6 +80,10 @@ class FakeBinding:
 
     def enmf_batch_tune(self, b):
         return None
+
+    def enmf_svd_init_group(self, ctxs, Xs, Us, Vs, sigmas=None, opts=None):
+        self.started.extend(ctxs)
+        return [], []
 
     def enmf_rotate_group(self, ctxs, Us, Vs, opts=None):
         self.rotated.extend(ctxs)
@@ -187,6 +192,7 @@ def test_admission_keeps_within_budget_and_fifo(monkeypatch):
     srv, B, results, admitted, used_after = _run(monkeypatch, reqs, rates, budget)
     assert admitted == [q.rid for q in reqs]                    # FIFO
     assert sorted(B.rotated) == sorted(admitted)                # every admission rotated once
+    assert B.started == admitted                                # and started once, in order
     assert all(u <= budget for u, _ in used_after)
     assert sorted(r.rid for r in results) == [q.rid for q in reqs]
     assert srv.used == 0 and not srv.active
