@@ -637,6 +637,194 @@ extern "C" enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void
   return svd_part2(ctx, U, V, sigma, sr, info);
 }
 
+// Part 1 for a group, in lockstep: every problem runs exactly the kernels of
+// its own svd_part1 in the same order, but the single-CTA steps (the Gram
+// eigen maps and the stopping test's Rayleigh-Ritz SVD) of all problems run
+// in one launch each, and one synchronisation per power iteration serves all
+// the stopping tests.  st[i] != ENMF_OK marks a problem that failed.
+template <typename P>
+static P* upload_group(const std::vector<P>& h, cudaStream_t s) {
+  void* d = nullptr;
+  if (h.empty() || cudaMallocAsync(&d, sizeof(P) * h.size(), s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (cudaMemcpyAsync(d, h.data(), sizeof(P) * h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaFreeAsync(d, s);
+    return nullptr;
+  }
+  return (P*)d;
+}
+
+static enmf_status svd_part1_group(enmf_ctx* const* ctxs, const void* const* Xin, int count,
+                                   const enmf_svd_opts* opts, std::vector<SvdRun>& sr,
+                                   std::vector<enmf_status>& st) {
+  cudaStream_t s = ctxs[0]->stream;
+  std::vector<const void*> X((size_t)count);
+  std::vector<enmf_svd_opts> os((size_t)count);
+  std::vector<int> live;
+  for (int i = 0; i < count; ++i) {
+    enmf_ctx* ctx = ctxs[i];
+    X[i] = Xin[i];
+    const void* xb = nullptr;
+    st[i] = bind_x(ctx, X[i], &xb);
+    if (st[i]) continue;
+    X[i] = xb;
+    enmf_svd_opts o = {10, 40, ctx->fdt == T_F64 ? 1e-12 : 1e-5, 0x5eedull, 0};
+    if (opts) {
+      o = *opts;
+      if (o.oversample < 0 || o.max_iters < 1 || !(o.tol >= 0)) {
+        st[i] = ENMF_EINVAL;
+        continue;
+      }
+    }
+    os[i] = o;
+    const enmf_problem& p = ctx->p;
+    int l = p.r + o.oversample;
+    if (l > LMAX) l = LMAX;
+    if (l > p.m) l = (int)p.m;
+    if (l > p.n) l = (int)p.n;
+    sr[i].l = l;
+    sr[i].r = p.r;
+    sr[i].it = 0;
+    sr[i].res = INFINITY;
+    sr[i].tol = o.tol;
+    sr[i].finish = ctx->fdt == T_F32 && !o.fp32_finish;
+    live.push_back(i);
+  }
+  auto tau = [&](int i) { return ctxs[i]->fdt == T_F64 ? 1e-13 : 1e-11; };
+  auto eig_group = [&](const std::vector<int>& idx) {
+    std::vector<EigOrthProb> h;
+    int mk = 0;
+    for (int i : idx) {
+      enmf_ctx* c = ctxs[i];
+      h.push_back(EigOrthProb{c->Gu, sr[i].l, tau(i), c->T1, c->T1x, c->kept, c->err});
+      if (sr[i].l > mk) mk = sr[i].l;
+    }
+    EigOrthProb* d = upload_group(h, s);
+    if (!d) return false;
+    launch_eig_orth_group(d, (int)h.size(), mk, s);
+    cudaFreeAsync(d, s);
+    return true;
+  };
+  // in -> (Gram, eigen map) -> tmp -> (Gram, eigen map) -> out, per problem
+  // the buffers sel(i) gives, as orth2 and the loop's orthonormalisations
+  auto orth_two = [&](const std::vector<int>& idx, auto sel) {
+    for (int i : idx) {
+      enmf_ctx* c = ctxs[i];
+      void *in, *tmp, *out;
+      int64_t rows;
+      sel(c, in, tmp, out, rows);
+      launch_gram(in, LMAX, sr[i].l, in, LMAX, sr[i].l, rows, c->fdt, c->part, c->Gu, s);
+    }
+    if (!eig_group(idx)) return false;
+    for (int i : idx) {
+      enmf_ctx* c = ctxs[i];
+      void *in, *tmp, *out;
+      int64_t rows;
+      sel(c, in, tmp, out, rows);
+      launch_row_orth(in, LMAX, tmp, LMAX, sr[i].l, rows, c->fdt, c->T1, c->T1x, s);
+      launch_gram(tmp, LMAX, sr[i].l, tmp, LMAX, sr[i].l, rows, c->fdt, c->part, c->Gu, s);
+    }
+    if (!eig_group(idx)) return false;
+    for (int i : idx) {
+      enmf_ctx* c = ctxs[i];
+      void *in, *tmp, *out;
+      int64_t rows;
+      sel(c, in, tmp, out, rows);
+      launch_row_orth(tmp, LMAX, out, LMAX, sr[i].l, rows, c->fdt, c->T1, c->T1x, s);
+    }
+    return true;
+  };
+  // Q = orth(X Omega)
+  for (int i : live) {
+    enmf_ctx* c = ctxs[i];
+    const enmf_problem& p = c->p;
+    launch_normx2(X[i], c->xdt, p.m, p.n, p.ldx, c->part, &c->st->normX2, c->err, s);
+    launch_omega(c->N0, c->fdt, p.n, LMAX, os[i].seed, s);
+    launch_xv(X[i], c->xdt, p.m, p.n, p.ldx, c->N0, LMAX, sr[i].l, c->M0, LMAX, c->fdt, c->splitk,
+              c->num_sms, s);
+  }
+  if (!orth_two(live, [](enmf_ctx* c, void*& in, void*& tmp, void*& out, int64_t& rows) {
+        in = c->M0; tmp = c->M1; out = c->M0; rows = c->p.m; }))
+    return ENMF_ENOMEM;
+  for (int i : live) {
+    st[i] = check_launch(ctxs[i]);
+  }
+  std::vector<int> act;
+  for (int i : live)
+    if (!st[i]) act.push_back(i);
+  while (!act.empty()) {
+    // Bt = X^T Q ; Q2 = orth(Bt) ; P = Q2^T Bt
+    for (int i : act) {
+      enmf_ctx* c = ctxs[i];
+      const enmf_problem& p = c->p;
+      launch_xtu(X[i], c->xdt, p.m, p.n, p.ldx, c->M0, LMAX, sr[i].l, c->N1, LMAX, c->fdt, c->splitk,
+                 c->num_sms, s);
+    }
+    if (!orth_two(act, [](enmf_ctx* c, void*& in, void*& tmp, void*& out, int64_t& rows) {
+          in = c->N1; tmp = c->N0; out = c->N2; rows = c->p.n; }))
+      return ENMF_ENOMEM;
+    std::vector<RrSvdProb> h;
+    int mk = 0;
+    for (int i : act) {
+      enmf_ctx* c = ctxs[i];
+      const int l = sr[i].l;
+      launch_gram(c->N2, LMAX, l, c->N1, LMAX, l, c->p.n, c->fdt, c->part, c->Msm, s);
+      h.push_back(RrSvdProb{c->Msm, l, l, c->sig, c->Ut, c->Wt, c->fdt == T_F32 ? 1 : 0, c->err});
+      if (l > mk) mk = l;
+    }
+    RrSvdProb* d = upload_group(h, s);
+    if (!d) return ENMF_ENOMEM;
+    launch_rr_svd_group(d, (int)h.size(), mk, mk, s);
+    cudaFreeAsync(d, s);
+    // Y = X Q2 (the next power iterate) and the residual ||Y W_r - Q U_r S_r||
+    for (int i : act) {
+      enmf_ctx* c = ctxs[i];
+      const enmf_problem& p = c->p;
+      const int l = sr[i].l, r = sr[i].r;
+      launch_xv(X[i], c->xdt, p.m, p.n, p.ldx, c->N2, LMAX, l, c->M1, LMAX, c->fdt, c->splitk,
+                c->num_sms, s);
+      launch_rr_prep(c->sig, c->Ut, c->Wt, l, l, r, c->Wr, c->UrS, c->st, s);
+      launch_rr_residual(c->M1, LMAX, l, c->M0, LMAX, l, p.m, r, c->fdt, c->Wr, c->UrS, c->part,
+                         &c->scal[0], s);
+    }
+    std::vector<int> next, orth;
+    for (int i : act) {
+      enmf_ctx* c = ctxs[i];
+      st[i] = check_launch(c);
+      if (st[i]) continue;
+      double hv[2];
+      if (cudaMemcpyAsync(&hv[0], &c->scal[0], sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaMemcpyAsync(&hv[1], &c->st->sigma1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+        c->poison = ENMF_ECUDA;
+        st[i] = ENMF_ECUDA;
+        continue;
+      }
+      const enmf_status rc = sync_status(c, false);
+      if (rc && rc != ENMF_ENOTCONV) {
+        st[i] = rc;
+        continue;
+      }
+      sr[i].res = hv[1] > 0 ? sqrt(hv[0]) / hv[1] : 0.0;
+      if (sr[i].res <= os[i].tol) {
+        ++sr[i].it;
+        continue;
+      }
+      if (sr[i].it + 1 < os[i].max_iters) orth.push_back(i);
+      ++sr[i].it;
+      if (sr[i].it < os[i].max_iters) next.push_back(i);
+    }
+    // Q = orth(Y)
+    if (!orth.empty() &&
+        !orth_two(orth, [](enmf_ctx* c, void*& in, void*& tmp, void*& out, int64_t& rows) {
+          in = c->M1; tmp = c->M2; out = c->M0; rows = c->p.m; }))
+      return ENMF_ENOMEM;
+    act.swap(next);
+  }
+  return ENMF_OK;
+}
+
 extern "C" enmf_status enmf_svd_init_group(enmf_ctx* const* ctxs, const void* const* X,
                                            void* const* U, void* const* V, double* const* sigma,
                                            int32_t count, const enmf_svd_opts* opts,
@@ -654,11 +842,11 @@ extern "C" enmf_status enmf_svd_init_group(enmf_ctx* const* ctxs, const void* co
   }
   std::vector<SvdRun> sr((size_t)count);
   std::vector<enmf_status> st((size_t)count, ENMF_OK);
+  const enmf_status grc = svd_part1_group(ctxs, X, count, opts, sr, st);
+  if (grc) return grc;
   std::vector<RrSvdProb> hp;
   int mk = 0;
   for (int i = 0; i < count; ++i) {
-    const void* Xi = X[i];
-    st[i] = svd_part1(ctxs[i], Xi, opts, sr[i]);
     if (st[i] || !sr[i].finish) continue;
     enmf_ctx* ctx = ctxs[i];
     hp.push_back(RrSvdProb{ctx->Msm, sr[i].l, sr[i].l, ctx->sig, ctx->Ut, ctx->Wt, 0, ctx->err});

@@ -307,6 +307,19 @@ void launch_polar(const double* M, int k, double* R, double* D, double tol,
 // Tx: 2 LMAX + 1 doubles.  Writes *kept.
 void launch_eig_orth(const double* G, int k, double tau, double* T, double* Tx, int* kept, int* err,
                      cudaStream_t s);
+// One orthonormalising transform of a group (launch_eig_orth's arguments).
+struct EigOrthProb {
+  const double* G;
+  int k;
+  double tau;
+  double* T;
+  double* Tx;
+  int* kept;
+  int* err;
+};
+// count transforms in one launch, one CTA each (probs in device memory,
+// max_k >= every k), each with the arithmetic of its own launch_eig_orth.
+void launch_eig_orth_group(const EigOrthProb* probs, int count, int max_k, cudaStream_t s);
 // out = in mapped by eig_orth's (T, Tx) row by row (rows x k, leading
 // dimensions ld_in / ld_out; in place is safe).
 void launch_row_orth(const void* in, int ld_in, void* out, int ld_out, int k, int64_t rows, int fdt,

@@ -509,10 +509,9 @@ __device__ bool chol_orth(const double* __restrict__ G, int k, double tau, doubl
   return true;
 }
 
-__global__ void __launch_bounds__(SM_T)
-eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, double* Tx, int* kept,
-                int* err) {
-  extern __shared__ double smd[];
+__device__ __forceinline__ void eig_orth_body(const double* __restrict__ G, int k, double tau,
+                                              double* T, double* Tx, int* kept, int* err,
+                                              double* smd) {
   const int Np = k + (k & 1);
   double* A = smd;
   double* V = A + (size_t)Np * k;
@@ -548,6 +547,21 @@ eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, doub
   }
 }
 
+__global__ void __launch_bounds__(SM_T)
+eig_orth_kernel(const double* __restrict__ G, int k, double tau, double* T, double* Tx, int* kept,
+                int* err) {
+  extern __shared__ double smd[];
+  eig_orth_body(G, k, tau, T, Tx, kept, err, smd);
+}
+
+// One CTA per problem: problem b's transform on block b, the same arithmetic
+// as its own eig_orth_kernel launch.
+__global__ void __launch_bounds__(SM_T) eig_orth_group_kernel(const EigOrthProb* __restrict__ probs) {
+  extern __shared__ double smd[];
+  const EigOrthProb q = probs[blockIdx.x];
+  eig_orth_body(q.G, q.k, q.tau, q.T, q.Tx, q.kept, q.err, smd);
+}
+
 void launch_eig_orth(const double* G, int k, double tau, double* T, double* Tx, int* kept, int* err,
                      cudaStream_t s) {
   note_launch(1);
@@ -555,6 +569,15 @@ void launch_eig_orth(const double* G, int k, double tau, double* T, double* Tx, 
   size_t smem = small_smem(k, Np);
   cudaFuncSetAttribute(eig_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   eig_orth_kernel<<<1, SM_T, smem, s>>>(G, k, tau, T, Tx, kept, err);
+}
+
+void launch_eig_orth_group(const EigOrthProb* probs, int count, int max_k, cudaStream_t s) {
+  if (count < 1) return;
+  note_launch(1);
+  const int Np = max_k + (max_k & 1);
+  const size_t smem = small_smem(max_k, Np);
+  cudaFuncSetAttribute(eig_orth_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  eig_orth_group_kernel<<<count, SM_T, smem, s>>>(probs);
 }
 
 // ------------------------------------------------------ Rayleigh-Ritz SVD
