@@ -169,10 +169,12 @@ enmf_status enmf_svd_init(enmf_ctx* ctx, const void* X, void* U, void* V, double
 /* The SVD start for `count` contexts at once (no counterpart in the paper; a
  * serving aid): each problem exactly as enmf_svd_init(ctxs[i], X[i], U[i],
  * V[i], sigma ? sigma[i] : NULL, opts, &infos[i]) would leave it, bit for
- * bit, but the FP32-then-FP64 Rayleigh-Ritz SVDs that finish the FP32-factor
- * starts run in one launch, one CTA per problem (each is a single-CTA FP64
- * computation: side by side they take the time of the largest).  The power
- * iterations run per problem, as in enmf_svd_init.  All contexts must share
+ * bit.  The problems' power iterations run in lockstep, each problem's kernels
+ * in its own order; the single-CTA steps of all problems (the range finder's
+ * Gram eigen maps, the stopping test's Rayleigh-Ritz SVDs and the
+ * FP32-then-FP64 SVDs that finish the FP32-factor starts) run in one launch
+ * each, one CTA per problem, and one synchronisation per power iteration
+ * serves every stopping test.  All contexts must share
  * one stream and device and appear once (else ENMF_EINVAL, before any
  * launch); forms may differ.  status (may be NULL) receives each problem's
  * status (ENMF_OK or ENMF_ENOTCONV as enmf_svd_init returns them); the call
