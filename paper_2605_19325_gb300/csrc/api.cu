@@ -694,6 +694,7 @@ static enmf_status svd_part1_group(enmf_ctx* const* ctxs, const void* const* Xin
   }
   auto tau = [&](int i) { return ctxs[i]->fdt == T_F64 ? 1e-13 : 1e-11; };
   auto eig_group = [&](const std::vector<int>& idx) {
+    if (idx.empty()) return true;
     std::vector<EigOrthProb> h;
     int mk = 0;
     for (int i : idx) {
