@@ -73,3 +73,18 @@ def test_group_start_argument_checks():
     assert torch.equal(a.U, U0)
     a.close()
     b.close()
+
+
+@pytest.mark.gpu
+def test_group_start_bad_options_fail_every_problem():
+    from paper_2605_19325_gb300 import binding as B
+    a = _solver(100, 80, 8, np.float32, 0)
+    b = _solver(90, 70, 4, np.float32, 1)
+    U0 = a.U.clone()
+    with pytest.raises(B.EnmfError) as ei:
+        B.enmf_svd_init_group([a.ctx, b.ctx], [a.X, b.X], [a.U, b.U], [a.V, b.V],
+                              opts=B.enmf_svd_opts(10, 0, 1e-5, 0x5eed, 0))
+    assert ei.value.code == 1
+    assert torch.equal(a.U, U0)
+    a.close()
+    b.close()
